@@ -1,0 +1,210 @@
+"""FP64 CPU oracle of the PUSCH receive hot path (arXiv 2210.09196) -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may import this
+package. The product path (``paper_2210_09196_gb300``) never imports it and shares no code with it.
+
+This module is argument marshalling around ``pusch_oracle.c`` (plain C, double precision), which carries the
+definitions and their citations. Arrays are numpy complex128 in the layouts documented in the C file.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from pathlib import Path
+
+import numpy as np
+
+_HERE = Path(__file__).resolve().parent
+_SRC = _HERE / "pusch_oracle.c"
+_BUILD = _HERE / "_build"
+_LIB_PATH = _BUILD / "liboracle.so"
+_lib = None
+
+DMRS_SYMBOLS = (2, 11)
+
+
+def build(force: bool = False) -> Path:
+    """Compile the oracle with gcc (portable C99, no architecture flags)."""
+    _BUILD.mkdir(exist_ok=True)
+    if force or not _LIB_PATH.exists() or _LIB_PATH.stat().st_mtime < _SRC.stat().st_mtime:
+        tmp = _BUILD / f"liboracle.{os.getpid()}.so"
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", str(_SRC), "-o", str(tmp), "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(str(_LIB_PATH))
+        P, I, D, LL = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+        sig = {
+            "orc_dft": (None, [P, I, P]),
+            "orc_fft": (I, [P, I, P]),
+            "orc_ofdm_demod": (I, [P, I, I, I, I, P, I, P]),
+            "orc_beamform": (None, [P, P, I, I, I, I, P]),
+            "orc_chest_ls": (I, [P, I, I, I, P, I, P, P, I, P, P, P]),
+            "orc_gram": (None, [P, I, I, D, P]),
+            "orc_cholesky": (I, [P, I, P]),
+            "orc_chol_solve": (None, [P, I, P, P]),
+            "orc_mmse": (I, [P, P, I, I, I, P, I, D, D, P, I, P]),
+            "orc_demap": (None, [P, LL, I, I, P]),
+            "orc_op_counts": (None, [I, I, I, I, I, I, P]),
+            "orc_slot": (I, [P, I, I, I, I, P, I, P, I, P, P, I, I, D, D, P, P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _c128(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def _i32(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def dft(x) -> np.ndarray:
+    x = _c128(x)
+    X = np.empty_like(x)
+    lib().orc_dft(_p(x), x.size, _p(X))
+    return X
+
+
+def fft(x) -> np.ndarray:
+    x = _c128(x)
+    X = np.empty_like(x)
+    if lib().orc_fft(_p(x), x.size, _p(X)) != 0:
+        raise ValueError("orc_fft needs a power-of-two length")
+    return X
+
+
+def ofdm_demod(time, n_sc: int, pairs=None) -> np.ndarray:
+    """time [S, R, N_F] -> freq [S, R, N_SC] (only the listed (symbol, antenna) rows when pairs is given)."""
+    time = _c128(time)
+    S, R, N = time.shape
+    freq = np.zeros((S, R, n_sc), dtype=np.complex128)
+    if pairs is None:
+        rc = lib().orc_ofdm_demod(_p(time), S, R, N, n_sc, None, 0, _p(freq))
+    else:
+        pr = _i32(pairs).reshape(-1, 2)
+        rc = lib().orc_ofdm_demod(_p(time), S, R, N, n_sc, _p(pr), pr.shape[0], _p(freq))
+    if rc != 0:
+        raise ValueError(f"orc_ofdm_demod failed ({rc})")
+    return freq
+
+
+def beamform(freq, W) -> np.ndarray:
+    """freq [S, R, N_SC], W [R, B] -> beam [S, N_SC, B] = W^H x."""
+    freq, W = _c128(freq), _c128(W)
+    S, R, n_sc = freq.shape
+    B = W.shape[1]
+    beam = np.empty((S, n_sc, B), dtype=np.complex128)
+    lib().orc_beamform(_p(freq), _p(W), S, R, n_sc, B, _p(beam))
+    return beam
+
+
+def chest_ls(beam, pilots, ports, comb: int, sc_start=None, sc_count=None, dmrs=DMRS_SYMBOLS) -> np.ndarray:
+    """beam [S, N_SC, B], pilots [L, 2, N_SC] -> H [N_SC, L, B] (zeros outside each layer's range)."""
+    beam, pilots = _c128(beam), _c128(pilots)
+    S, n_sc, B = beam.shape
+    L = pilots.shape[0]
+    st = _i32(np.zeros(L) if sc_start is None else sc_start)
+    ct = _i32(np.full(L, n_sc) if sc_count is None else sc_count)
+    H = np.zeros((n_sc, L, B), dtype=np.complex128)
+    rc = lib().orc_chest_ls(_p(beam), S, n_sc, B, _p(_i32(dmrs)), L, _p(pilots), _p(_i32(ports)), comb,
+                            _p(st), _p(ct), _p(H))
+    if rc != 0:
+        raise ValueError(f"orc_chest_ls: layer {-rc - 1} has no pilot in its range")
+    return H
+
+
+def gram(Hs, load: float) -> np.ndarray:
+    """Hs [L, B] (row l = column l of H) -> G = H^H H + load I."""
+    Hs = _c128(Hs)
+    L, B = Hs.shape
+    G = np.empty((L, L), dtype=np.complex128)
+    lib().orc_gram(_p(Hs), L, B, load, _p(G))
+    return G
+
+
+def cholesky(G):
+    """Returns (L, status); status = 0 or the 1-based index of the first non-positive pivot."""
+    G = _c128(G)
+    n = G.shape[0]
+    L = np.empty_like(G)
+    st = lib().orc_cholesky(_p(G), n, _p(L))
+    return L, int(st)
+
+
+def chol_solve(L, r) -> np.ndarray:
+    L, r = _c128(L), _c128(r)
+    x = np.empty_like(r)
+    lib().orc_chol_solve(_p(L), L.shape[0], _p(r), _p(x))
+    return x
+
+
+def data_symbols(n_sym: int = 14, dmrs=DMRS_SYMBOLS) -> np.ndarray:
+    return np.array([s for s in range(n_sym) if s not in dmrs], dtype=np.int32)
+
+
+def mmse(H, beam, noise_var: float, loading: float = 0.0, sc_list=None, data_sym=None):
+    """H [N_SC, L, B], beam [S, N_SC, B] -> (xhat [L, n_data, N_SC], n_failed)."""
+    H, beam = _c128(H), _c128(beam)
+    n_sc, L, B = H.shape
+    S = beam.shape[0]
+    ds = data_symbols(S) if data_sym is None else _i32(data_sym)
+    xhat = np.zeros((L, ds.size, n_sc), dtype=np.complex128)
+    if sc_list is None:
+        fails = lib().orc_mmse(_p(H), _p(beam), n_sc, B, L, _p(ds), ds.size, noise_var, loading, None, 0, _p(xhat))
+    else:
+        sl = _i32(sc_list)
+        fails = lib().orc_mmse(_p(H), _p(beam), n_sc, B, L, _p(ds), ds.size, noise_var, loading, _p(sl), sl.size,
+                               _p(xhat))
+    return xhat, int(fails)
+
+
+def demap(x, qam_bits: int, f32: bool = False) -> np.ndarray:
+    x = _c128(x)
+    bits = np.empty(x.shape, dtype=np.uint8)
+    lib().orc_demap(_p(x), x.size, qam_bits, 1 if f32 else 0, _p(bits))
+    return bits
+
+
+def op_counts(n_symb: int, n_pilot: int, n_r: int, n_sc: int, n_b: int, n_l: int) -> dict:
+    out = np.zeros(5, dtype=np.float64)
+    lib().orc_op_counts(n_symb, n_pilot, n_r, n_sc, n_b, n_l, _p(out))
+    return dict(zip(("ofdm", "bf", "mimo", "che", "ne"), out.tolist()))
+
+
+def slot(time, W, pilots, ports, comb: int, n_sc: int, qam_bits: int, noise_var: float, loading: float = 0.0,
+         dmrs=DMRS_SYMBOLS):
+    """The whole chain for one slot -> (xhat [L, 12, N_SC], bits [L, 12, N_SC], n_failed)."""
+    time, W, pilots = _c128(time), _c128(W), _c128(pilots)
+    S, R, N = time.shape
+    B = W.shape[1]
+    L = pilots.shape[0]
+    n_data = S - 2
+    xhat = np.zeros((L, n_data, n_sc), dtype=np.complex128)
+    bits = np.zeros((L, n_data, n_sc), dtype=np.uint8)
+    rc = lib().orc_slot(_p(time), S, R, N, n_sc, _p(W), B, _p(_i32(dmrs)), L, _p(pilots), _p(_i32(ports)), comb,
+                        qam_bits, noise_var, loading, _p(xhat), _p(bits))
+    if rc < 0:
+        raise ValueError(f"orc_slot failed ({rc})")
+    return xhat, bits, rc
+
+
+def run_slot(s, loading: float = 0.0):
+    """Convenience: run the chain on a generated slot object (paper_2210_09196_gb300.synth.Slot)."""
+    return slot(s.time_as_complex128(), s.W, s.pilots, s.ports, s.cfg.comb, s.cfg.n_sc, s.cfg.qam_bits,
+                s.noise_var, loading)

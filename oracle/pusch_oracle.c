@@ -1,0 +1,392 @@
+/*
+ * pusch_oracle.c -- plain, slow, FP64 CPU oracle of the PUSCH receive hot path of
+ * "Efficient Parallelization of 5G-PUSCH on a Scalable RISC-V Many-core Processor" (arXiv 2210.09196).
+ *
+ * TEST INFRASTRUCTURE ONLY. Only the test-suite, the smoke check and the CPU-baseline leg of the benchmark
+ * may load this library. The CUDA path shares no code, header, table or helper with it.
+ *
+ * Every function writes out the definition it follows, in double precision, with no blocking, fusion or
+ * reordering beyond the definition:
+ *   orc_dft         Section II "OFDM demodulation ... via a FFT": the DFT definition itself.
+ *   orc_fft         textbook recursive radix-2 decimation-in-time FFT (pinned against orc_dft).
+ *   orc_ofdm_demod  Section II: one FFT per antenna and OFDM symbol, keep the N_SC active bins.
+ *   orc_beamform    Section II: "a MMM with known coefficients", y = W^H x per subcarrier and symbol.
+ *   orc_chest_ls    Section II: LS estimate = element-wise division of the received pilot REs by the
+ *                   pilots (block-type pilots on whole OFDM symbols), averaged over the two DMRS
+ *                   symbols, then linear interpolation between a layer's pilot subcarriers.
+ *   orc_gram        Eq. 2: G = H^H H + sigma^2 I.
+ *   orc_cholesky    Section V-C: Cholesky-Crout, L computed column by column, G = L L^H.
+ *   orc_mmse        Eq. 2 via Section II's Cholesky + two triangular solves, per data symbol and
+ *                   subcarrier (the paper's accounting in Table I).
+ *   orc_demap       Gray hard decisions of 3GPP TS 38.211 5.1.3/5.1.4 (QPSK/16-QAM).
+ *   orc_op_counts   Table I complex-MAC model.
+ *
+ * Layouts (complex values interleaved re,im; C99 double complex):
+ *   time  [n_sym][n_rx][n_fft]     freq [n_sym][n_rx][n_sc]     beam [n_sym][n_sc][n_beams]
+ *   W     [n_rx][n_beams]          pilots [n_layers][2][n_sc]   H [n_sc][n_layers][n_beams]
+ *   xhat  [n_layers][n_data][n_sc] bits [n_layers][n_data][n_sc] (bit j of the byte = b_j)
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef double complex cplx;
+
+static const double ORC_PI = 3.14159265358979323846264338327950288;
+
+/* ---------------------------------------------------------------- FFT ---- */
+
+/* X[k] = sum_n x[n] exp(-2 pi i k n / N): the definition, O(N^2). */
+void orc_dft(const cplx *x, int n, cplx *X)
+{
+    for (int k = 0; k < n; ++k) {
+        cplx acc = 0;
+        for (int t = 0; t < n; ++t) {
+            /* reduce k*t mod n first so the angle stays small and exact in double */
+            long long kt = ((long long)k * t) % n;
+            acc += x[t] * cexp(-2.0 * I * ORC_PI * (double)kt / (double)n);
+        }
+        X[k] = acc;
+    }
+}
+
+/* Textbook recursive radix-2 DIT: X[k] = E[k] + w^k O[k], X[k + N/2] = E[k] - w^k O[k]. */
+static void fft_rec(const cplx *x, int stride, int n, cplx *out)
+{
+    if (n == 1) {
+        out[0] = x[0];
+        return;
+    }
+    int h = n / 2;
+    fft_rec(x, 2 * stride, h, out);              /* even samples -> out[0, h)  */
+    fft_rec(x + stride, 2 * stride, h, out + h); /* odd samples  -> out[h, n)  */
+    for (int k = 0; k < h; ++k) {
+        cplx e = out[k];
+        cplx o = out[k + h] * cexp(-2.0 * I * ORC_PI * (double)k / (double)n);
+        out[k] = e + o;
+        out[k + h] = e - o;
+    }
+}
+
+/* Returns 0, or -1 if n is not a power of two. */
+int orc_fft(const cplx *x, int n, cplx *X)
+{
+    if (n <= 0 || (n & (n - 1)) != 0) return -1;
+    fft_rec(x, 1, n, X);
+    return 0;
+}
+
+/* FFT bin of active subcarrier a: (a - n_sc/2) mod n_fft (centred band, DC included). */
+static int active_bin(int a, int n_sc, int n_fft)
+{
+    int b = a - n_sc / 2;
+    b %= n_fft;
+    if (b < 0) b += n_fft;
+    return b;
+}
+
+/* One FFT per (symbol, antenna) listed in `pairs` (pairs[2i] = symbol, pairs[2i+1] = antenna), or all
+ * n_sym*n_rx pairs when pairs == NULL. Only the listed rows of freq are written. */
+int orc_ofdm_demod(const cplx *time, int n_sym, int n_rx, int n_fft, int n_sc,
+                   const int *pairs, int n_pairs, cplx *freq)
+{
+    if (n_sc > n_fft || n_sc < 0) return -1;
+    cplx *X = malloc(sizeof(cplx) * (size_t)n_fft);
+    if (!X) return -2;
+    int total = pairs ? n_pairs : n_sym * n_rx;
+    int rc = 0;
+    for (int i = 0; i < total && rc == 0; ++i) {
+        int s = pairs ? pairs[2 * i] : i / n_rx;
+        int r = pairs ? pairs[2 * i + 1] : i % n_rx;
+        const cplx *x = time + ((size_t)s * n_rx + r) * n_fft;
+        rc = orc_fft(x, n_fft, X);
+        cplx *f = freq + ((size_t)s * n_rx + r) * n_sc;
+        for (int a = 0; a < n_sc; ++a) f[a] = X[active_bin(a, n_sc, n_fft)];
+    }
+    free(X);
+    return rc;
+}
+
+/* ---------------------------------------------------------- beamforming ---- */
+
+/* beam[s][a][b] = sum_r conj(W[r][b]) * freq[s][r][a]   (y = W^H x, a triple loop). */
+void orc_beamform(const cplx *freq, const cplx *W, int n_sym, int n_rx, int n_sc, int n_beams,
+                  cplx *beam)
+{
+    for (int s = 0; s < n_sym; ++s)
+        for (int a = 0; a < n_sc; ++a)
+            for (int b = 0; b < n_beams; ++b) {
+                cplx acc = 0;
+                for (int r = 0; r < n_rx; ++r)
+                    acc += conj(W[(size_t)r * n_beams + b]) * freq[((size_t)s * n_rx + r) * n_sc + a];
+                beam[((size_t)s * n_sc + a) * n_beams + b] = acc;
+            }
+}
+
+/* ------------------------------------------------------ LS channel estimate ---- */
+
+/*
+ * Layer l occupies subcarriers [sc_start[l], sc_start[l] + sc_count[l]) and carries its pilots on the
+ * subcarriers a of that range with a % comb == port[l]. For each of those pilot subcarriers q:
+ *     LS[q][b] = 1/2 * sum_{j in {0,1}} beam[dmrs_sym[j]][q][b] / pilots[l][j][q]
+ * and for each subcarrier a of the range:
+ *     a at or before the first pilot   -> LS[first]
+ *     a at or after the last pilot     -> LS[last]
+ *     otherwise, with lo <= a < hi the neighbouring pilots:
+ *         H = LS[lo] + (a - lo) / (hi - lo) * (LS[hi] - LS[lo])
+ * Subcarriers outside the range are left untouched.
+ * Returns 0, or -(l+1) when layer l has no pilot in its range.
+ */
+int orc_chest_ls(const cplx *beam, int n_sym, int n_sc, int n_beams, const int *dmrs_sym,
+                 int n_layers, const cplx *pilots, const int *port, int comb,
+                 const int *sc_start, const int *sc_count, cplx *H)
+{
+    (void)n_sym;
+    for (int l = 0; l < n_layers; ++l) {
+        int a0 = sc_start[l], a1 = sc_start[l] + sc_count[l];
+        int first = -1, last = -1;
+        for (int a = a0; a < a1; ++a)
+            if (a % comb == port[l]) {
+                if (first < 0) first = a;
+                last = a;
+            }
+        if (first < 0) return -(l + 1);
+        for (int a = a0; a < a1; ++a) {
+            int lo, hi;
+            if (a <= first) {
+                lo = hi = first;
+            } else if (a >= last) {
+                lo = hi = last;
+            } else {
+                lo = a;
+                while (lo % comb != port[l]) --lo;
+                hi = lo + comb;
+                if (lo == a) hi = lo;
+            }
+            for (int b = 0; b < n_beams; ++b) {
+                cplx ls_lo = 0, ls_hi = 0;
+                for (int j = 0; j < 2; ++j) {
+                    const cplx *y = beam + (size_t)dmrs_sym[j] * n_sc * n_beams;
+                    const cplx *p = pilots + ((size_t)l * 2 + j) * n_sc;
+                    ls_lo += 0.5 * y[(size_t)lo * n_beams + b] / p[lo];
+                    ls_hi += 0.5 * y[(size_t)hi * n_beams + b] / p[hi];
+                }
+                cplx h = ls_lo;
+                if (hi != lo) h = ls_lo + ((double)(a - lo) / (double)(hi - lo)) * (ls_hi - ls_lo);
+                H[((size_t)a * n_layers + l) * n_beams + b] = h;
+            }
+        }
+    }
+    return 0;
+}
+
+/* --------------------------------------------------------------- MMSE ---- */
+
+/* G = H^H H + load * I for one subcarrier; Hs is stored [n_layers][n_beams] (row l = column l of H). */
+void orc_gram(const cplx *Hs, int n_layers, int n_beams, double load, cplx *G)
+{
+    for (int i = 0; i < n_layers; ++i)
+        for (int j = 0; j < n_layers; ++j) {
+            cplx acc = 0;
+            for (int b = 0; b < n_beams; ++b)
+                acc += conj(Hs[(size_t)i * n_beams + b]) * Hs[(size_t)j * n_beams + b];
+            G[(size_t)i * n_layers + j] = acc + (i == j ? load : 0.0);
+        }
+}
+
+/*
+ * Cholesky-Crout, column by column: for j = 0..n-1
+ *     L[j][j] = sqrt(G[j][j] - sum_{k<j} |L[j][k]|^2)
+ *     L[i][j] = (G[i][j] - sum_{k<j} L[i][k] conj(L[j][k])) / L[j][j],   i > j
+ * Only the lower triangle of G is read; the strict upper triangle of L is set to zero.
+ * Returns 0, or j+1 when the j-th pivot is not a positive finite number.
+ */
+int orc_cholesky(const cplx *G, int n, cplx *L)
+{
+    for (int i = 0; i < n * n; ++i) L[i] = 0;
+    for (int j = 0; j < n; ++j) {
+        double d = creal(G[(size_t)j * n + j]);
+        for (int k = 0; k < j; ++k) {
+            cplx v = L[(size_t)j * n + k];
+            d -= creal(v) * creal(v) + cimag(v) * cimag(v);
+        }
+        if (!(d > 0.0) || !isfinite(d)) return j + 1;
+        double ljj = sqrt(d);
+        L[(size_t)j * n + j] = ljj;
+        for (int i = j + 1; i < n; ++i) {
+            cplx acc = G[(size_t)i * n + j];
+            for (int k = 0; k < j; ++k) acc -= L[(size_t)i * n + k] * conj(L[(size_t)j * n + k]);
+            L[(size_t)i * n + j] = acc / ljj;
+        }
+    }
+    return 0;
+}
+
+/* Solve L z = r (forward) then L^H x = z (back); L lower triangular with real positive diagonal. */
+void orc_chol_solve(const cplx *L, int n, const cplx *r, cplx *x)
+{
+    cplx *z = malloc(sizeof(cplx) * (size_t)n);
+    for (int i = 0; i < n; ++i) {
+        cplx acc = r[i];
+        for (int k = 0; k < i; ++k) acc -= L[(size_t)i * n + k] * z[k];
+        z[i] = acc / L[(size_t)i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        cplx acc = z[i];
+        for (int k = i + 1; k < n; ++k) acc -= conj(L[(size_t)k * n + i]) * x[k];
+        x[i] = acc / conj(L[(size_t)i * n + i]);
+    }
+    free(z);
+}
+
+/*
+ * Eq. 2 for every listed subcarrier (sc_list, or all when NULL) and every data symbol d:
+ *     G = H^H H + (noise_var + loading) I ;  G = L L^H ;  L z = H^H y ;  L^H x = z
+ * with y = beam[data_sym[d]][a][:]. The Gram and its factor are formed anew for each data symbol, as the
+ * paper counts them (Table I: per subcarrier and per data symbol).
+ * xhat[l][d][a] receives x_l. Returns the number of (subcarrier, symbol) pairs whose factorisation failed
+ * (their xhat entries are set to 0).
+ */
+int orc_mmse(const cplx *H, const cplx *beam, int n_sc, int n_beams, int n_layers,
+             const int *data_sym, int n_data, double noise_var, double loading,
+             const int *sc_list, int n_list, cplx *xhat)
+{
+    int nl = n_layers;
+    cplx *G = malloc(sizeof(cplx) * (size_t)nl * nl);
+    cplx *L = malloc(sizeof(cplx) * (size_t)nl * nl);
+    cplx *r = malloc(sizeof(cplx) * (size_t)nl);
+    cplx *x = malloc(sizeof(cplx) * (size_t)nl);
+    int fails = 0;
+    int total = sc_list ? n_list : n_sc;
+    for (int ii = 0; ii < total; ++ii) {
+        int a = sc_list ? sc_list[ii] : ii;
+        const cplx *Hs = H + (size_t)a * nl * n_beams;
+        for (int d = 0; d < n_data; ++d) {
+            const cplx *y = beam + ((size_t)data_sym[d] * n_sc + a) * n_beams;
+            orc_gram(Hs, nl, n_beams, noise_var + loading, G);
+            int st = orc_cholesky(G, nl, L);
+            if (st != 0) {
+                ++fails;
+                for (int l = 0; l < nl; ++l) xhat[((size_t)l * n_data + d) * n_sc + a] = 0;
+                continue;
+            }
+            for (int i = 0; i < nl; ++i) {
+                cplx acc = 0;
+                for (int b = 0; b < n_beams; ++b) acc += conj(Hs[(size_t)i * n_beams + b]) * y[b];
+                r[i] = acc;
+            }
+            orc_chol_solve(L, nl, r, x);
+            for (int l = 0; l < nl; ++l) xhat[((size_t)l * n_data + d) * n_sc + a] = x[l];
+        }
+    }
+    free(G);
+    free(L);
+    free(r);
+    free(x);
+    return fails;
+}
+
+/* ------------------------------------------------------------- demapper ---- */
+
+/*
+ * Gray hard decisions (3GPP TS 38.211 5.1.3 / 5.1.4), tie -> bit 0:
+ *   QPSK : b0 = Re < 0, b1 = Im < 0
+ *   16QAM: b0 = Re < 0, b1 = Im < 0, b2 = |Re| > 2/sqrt(10), b3 = |Im| > 2/sqrt(10)
+ * With f32 != 0 the comparisons are taken in single precision (component and threshold rounded to
+ * float), so that decisions can be compared bit for bit with a single-precision detector.
+ */
+void orc_demap(const cplx *x, long long n, int qam_bits, int f32, uint8_t *bits)
+{
+    const double thr = 2.0 / sqrt(10.0);
+    const float thr_f = (float)(2.0 / sqrt(10.0));
+    for (long long i = 0; i < n; ++i) {
+        double re = creal(x[i]), im = cimag(x[i]);
+        uint8_t v = 0;
+        if (f32) {
+            float rf = (float)re, imf = (float)im;
+            v |= (uint8_t)(rf < 0.0f) << 0;
+            v |= (uint8_t)(imf < 0.0f) << 1;
+            if (qam_bits == 4) {
+                v |= (uint8_t)(fabsf(rf) > thr_f) << 2;
+                v |= (uint8_t)(fabsf(imf) > thr_f) << 3;
+            }
+        } else {
+            v |= (uint8_t)(re < 0.0) << 0;
+            v |= (uint8_t)(im < 0.0) << 1;
+            if (qam_bits == 4) {
+                v |= (uint8_t)(fabs(re) > thr) << 2;
+                v |= (uint8_t)(fabs(im) > thr) << 3;
+            }
+        }
+        bits[i] = v;
+    }
+}
+
+/* --------------------------------------------------------- complexity ---- */
+
+/*
+ * Table I complex-MAC counts (log taken base 2; the MIMO entry read as N_L^3/3 + 2 N_L^2):
+ *   out[0] OFDM  N_symb * N_R * N_SC * log2(N_SC)
+ *   out[1] BF    N_symb * N_SC * N_R * N_B
+ *   out[2] MIMO  N_data * N_SC * (N_L^3/3 + 2 N_L^2)
+ *   out[3] CHE   N_pilot * N_SC * N_B * N_L
+ *   out[4] NE    N_pilot * N_SC * 2 N_B * N_L
+ */
+void orc_op_counts(int n_symb, int n_pilot, int n_r, int n_sc, int n_b, int n_l, double *out)
+{
+    int n_data = n_symb - n_pilot;
+    out[0] = (double)n_symb * n_r * n_sc * log2((double)n_sc);
+    out[1] = (double)n_symb * n_sc * n_r * n_b;
+    out[2] = (double)n_data * n_sc * ((double)n_l * n_l * n_l / 3.0 + 2.0 * n_l * n_l);
+    out[3] = (double)n_pilot * n_sc * n_b * n_l;
+    out[4] = (double)n_pilot * n_sc * 2.0 * n_b * n_l;
+}
+
+/* ----------------------------------------------------------- full slot ---- */
+
+/*
+ * The chain of Fig. 1 for one slot: OFDM demodulation -> beamforming -> LS channel estimation on the
+ * DMRS symbols -> MMSE detection of the data symbols -> hard decisions.
+ * Every layer spans the whole band [0, n_sc). Returns the number of failed factorisations, or < 0 on
+ * an argument error.
+ */
+int orc_slot(const cplx *time, int n_sym, int n_rx, int n_fft, int n_sc, const cplx *W, int n_beams,
+             const int *dmrs_sym, int n_layers, const cplx *pilots, const int *port, int comb,
+             int qam_bits, double noise_var, double loading, cplx *xhat, uint8_t *bits)
+{
+    int n_data = 0;
+    int data_sym[64];
+    for (int s = 0; s < n_sym && n_data < 64; ++s)
+        if (s != dmrs_sym[0] && s != dmrs_sym[1]) data_sym[n_data++] = s;
+
+    cplx *freq = malloc(sizeof(cplx) * (size_t)n_sym * n_rx * n_sc);
+    cplx *beam = malloc(sizeof(cplx) * (size_t)n_sym * n_sc * n_beams);
+    cplx *H = malloc(sizeof(cplx) * (size_t)n_sc * n_layers * n_beams);
+    int *start = malloc(sizeof(int) * (size_t)n_layers);
+    int *count = malloc(sizeof(int) * (size_t)n_layers);
+    int rc = 0;
+    if (!freq || !beam || !H || !start || !count) {
+        rc = -2;
+        goto done;
+    }
+    for (int l = 0; l < n_layers; ++l) {
+        start[l] = 0;
+        count[l] = n_sc;
+    }
+    rc = orc_ofdm_demod(time, n_sym, n_rx, n_fft, n_sc, NULL, 0, freq);
+    if (rc) goto done;
+    orc_beamform(freq, W, n_sym, n_rx, n_sc, n_beams, beam);
+    rc = orc_chest_ls(beam, n_sym, n_sc, n_beams, dmrs_sym, n_layers, pilots, port, comb, start, count, H);
+    if (rc) goto done;
+    rc = orc_mmse(H, beam, n_sc, n_beams, n_layers, data_sym, n_data, noise_var, loading, NULL, 0, xhat);
+    orc_demap(xhat, (long long)n_layers * n_data * n_sc, qam_bits, 0, bits);
+done:
+    free(freq);
+    free(beam);
+    free(H);
+    free(start);
+    free(count);
+    return rc;
+}

@@ -1,0 +1,208 @@
+"""Seeded synthetic PUSCH slots (transmitter + channel side only).
+
+This module produces the inputs of the receive chain of "Efficient Parallelization of 5G-PUSCH on a Scalable
+RISC-V Many-core Processor" (arXiv 2210.09196): time-domain samples per (symbol, antenna), the beam matrix W,
+the DMRS pilots and the noise variance, plus the ground truth (channel, symbols, bits) for quality metrics.
+
+It holds none of the receiver's arithmetic: no FFT of received samples, no beamforming, no channel
+estimation, no detection and no demapping. The transmitter's OFDM modulation uses ``numpy.fft.ifft``.
+Both the CUDA path and the FP64 oracle consume exactly the arrays returned here.
+
+Model (Section II, Eq. 1, Fig. 2):
+  * OFDMA grid of N_SC active subcarriers x 14 symbols, block-type DMRS on symbols 2 and 11 (two whole
+    pilot OFDM symbols per slot, Section II); the 12 remaining symbols carry data.
+  * Active subcarrier a sits at FFT bin (a - N_SC//2) mod N_F (centred band, DC included, no CP).
+  * N_L single-layer users; user l sends its QPSK pilot on the subcarriers a with a % comb == port[l]
+    (frequency comb of size comb = N_L) and nothing on the other REs of the DMRS symbols.
+  * Antenna-domain received RE: X[s, r, a] = sum_l Hant[a, r, l] t_l[s, a] + n,  n ~ CN(0, sigma^2),
+    sigma^2 = 10^(-SNR/10) with unit-variance channel entries and unit-energy symbols.
+  * Time samples: x[s, r, :] = ifft(spectrum) (numpy's 1/N_F normalisation), so the receiver's
+    unnormalised forward FFT returns X exactly; optionally rounded to complex FP16.
+  * Beam matrix W [N_R, N_B]: identity, or DFT columns W[r, b] = exp(-2 pi i r b / N_R) / sqrt(N_R).
+"""
+from __future__ import annotations
+
+import dataclasses
+from dataclasses import dataclass, field
+
+import numpy as np
+
+N_SYM = 14
+DMRS_SYMBOLS = (2, 11)
+DATA_SYMBOLS = tuple(s for s in range(N_SYM) if s not in DMRS_SYMBOLS)
+
+_SCS_HZ = 30e3
+
+
+@dataclass(frozen=True)
+class CellConfig:
+    """One cell's slot shape. Names follow the paper's notation (N_R, N_SC, N_B, N_L)."""
+
+    name: str
+    n_rx: int            # N_R receive antennas
+    n_fft: int           # N_F FFT size
+    n_sc: int            # N_SC active subcarriers
+    n_beams: int         # N_B beams
+    n_layers: int        # N_L single-layer users detected jointly
+    qam_bits: int        # 2 = QPSK, 4 = 16-QAM
+    snr_db: float
+    channel: str         # "iid" (CN(0,1) per subcarrier), "flat" (CN(0,1), same on every subcarrier)
+                         # or "pdp" (16-tap exponential power-delay profile)
+    beam: str            # "identity" or "dft"
+    in_fp16: bool        # time samples stored as complex FP16
+    delay_spread_s: float = 300e-9
+    n_taps: int = 16
+    tap_spacing_s: float = 60e-9
+    seed: int = 0
+
+    @property
+    def comb(self) -> int:
+        return self.n_layers
+
+    def with_(self, **kw) -> "CellConfig":
+        return dataclasses.replace(self, **kw)
+
+
+# Workload presets. Sizes follow the paper's use case (Section II: 100 MHz, 30 kHz SCS, 3276 subcarriers,
+# 14 symbols, 2 pilot symbols, 64 antennas, 32 beams) and the small/massive variants around it.
+SMALL_FP32 = CellConfig("small-16rx-512fft-4ue", n_rx=16, n_fft=512, n_sc=300, n_beams=16, n_layers=4,
+                        qam_bits=2, snr_db=20.0, channel="iid", beam="identity", in_fp16=False, seed=1)
+DEPLOY = CellConfig("deploy-64rx-4096fft-32beam-16ue", n_rx=64, n_fft=4096, n_sc=3276, n_beams=32,
+                    n_layers=16, qam_bits=4, snr_db=30.0, channel="pdp", beam="dft", in_fp16=True, seed=2)
+MASSIVE = CellConfig("massive-256rx-4096fft-64beam-32ue", n_rx=256, n_fft=4096, n_sc=3276, n_beams=64,
+                     n_layers=32, qam_bits=4, snr_db=25.0, channel="pdp", beam="dft", in_fp16=True, seed=5)
+
+PRESETS = {"small": SMALL_FP32, "deploy": DEPLOY, "massive": MASSIVE}
+
+
+def active_bins(n_sc: int, n_fft: int) -> np.ndarray:
+    """FFT bin of each active subcarrier a: (a - n_sc//2) mod n_fft."""
+    a = np.arange(n_sc)
+    return (a - n_sc // 2) % n_fft
+
+
+def beam_matrix(cfg: CellConfig) -> np.ndarray:
+    """W [N_R, N_B] complex64: identity, or the first N_B orthonormal DFT columns."""
+    if cfg.beam == "identity":
+        if cfg.n_beams != cfg.n_rx:
+            raise ValueError("identity beamforming needs n_beams == n_rx")
+        return np.eye(cfg.n_rx, dtype=np.complex64)
+    r = np.arange(cfg.n_rx)[:, None]
+    b = np.arange(cfg.n_beams)[None, :]
+    return (np.exp(-2j * np.pi * r * b / cfg.n_rx) / np.sqrt(cfg.n_rx)).astype(np.complex64)
+
+
+def qam_map(bits: np.ndarray, qam_bits: int) -> np.ndarray:
+    """Gray mapping of 3GPP TS 38.211 5.1.3 (QPSK) / 5.1.4 (16-QAM); bits[..., q] -> complex128."""
+    b = bits.astype(np.int64)
+    if qam_bits == 2:
+        return ((1 - 2 * b[..., 0]) + 1j * (1 - 2 * b[..., 1])) / np.sqrt(2.0)
+    if qam_bits == 4:
+        re = (1 - 2 * b[..., 0]) * (2 - (1 - 2 * b[..., 2]))
+        im = (1 - 2 * b[..., 1]) * (2 - (1 - 2 * b[..., 3]))
+        return (re + 1j * im) / np.sqrt(10.0)
+    raise ValueError("qam_bits must be 2 or 4")
+
+
+def pack_bits(bits: np.ndarray) -> np.ndarray:
+    """bits[..., q] (0/1) -> one byte per symbol, bit j of the byte = b_j."""
+    q = bits.shape[-1]
+    out = np.zeros(bits.shape[:-1], dtype=np.uint8)
+    for j in range(q):
+        out |= (bits[..., j].astype(np.uint8) << j)
+    return out
+
+
+def _channel(cfg: CellConfig, rng: np.random.Generator) -> np.ndarray:
+    """Antenna-domain channel Hant [N_SC, N_R, N_L] complex128, unit average power per entry."""
+    R, L, n_sc = cfg.n_rx, cfg.n_layers, cfg.n_sc
+    if cfg.channel == "iid":
+        return (rng.standard_normal((n_sc, R, L)) + 1j * rng.standard_normal((n_sc, R, L))) / np.sqrt(2.0)
+    if cfg.channel == "flat":
+        h = (rng.standard_normal((R, L)) + 1j * rng.standard_normal((R, L))) / np.sqrt(2.0)
+        return np.broadcast_to(h, (n_sc, R, L)).copy()
+    if cfg.channel == "pdp":
+        ts = 1.0 / (cfg.n_fft * _SCS_HZ)
+        i = np.arange(cfg.n_taps)
+        delays = np.round(i * cfg.tap_spacing_s / ts)                      # samples
+        power = np.exp(-i * cfg.tap_spacing_s / cfg.delay_spread_s)
+        power = power / power.sum()
+        taps = (rng.standard_normal((R, L, cfg.n_taps)) + 1j * rng.standard_normal((R, L, cfg.n_taps)))
+        taps *= np.sqrt(power / 2.0)
+        k = (np.arange(n_sc) - n_sc // 2)[:, None]                       # signed frequency index
+        F = np.exp(-2j * np.pi * k * delays[None, :] / cfg.n_fft)         # [N_SC, taps]
+        return np.einsum("at,rlt->arl", F, taps)
+    raise ValueError(f"unknown channel model {cfg.channel}")
+
+
+@dataclass
+class Slot:
+    cfg: CellConfig
+    time_in: np.ndarray      # [S, N_R, N_F] complex64, or [S, N_R, N_F, 2] float16 when cfg.in_fp16
+    W: np.ndarray            # [N_R, N_B] complex64
+    pilots: np.ndarray       # [N_L, 2, N_SC] complex64 (zero off the layer's comb)
+    ports: np.ndarray        # [N_L] int32 comb offsets
+    noise_var: float
+    H_beam: np.ndarray = field(repr=False)   # truth: [N_SC, N_L, N_B] complex128 = (W^H Hant)^T per subcarrier
+    x: np.ndarray = field(repr=False)        # truth: [N_L, 12, N_SC] complex128 transmitted data symbols
+    bits: np.ndarray = field(repr=False)     # truth: [N_L, 12, N_SC] uint8 packed (bit j = b_j)
+
+    def time_as_complex128(self) -> np.ndarray:
+        """The exact values the receiver sees, widened to complex128."""
+        t = self.time_in
+        if t.dtype == np.float16:
+            return t[..., 0].astype(np.float64) + 1j * t[..., 1].astype(np.float64)
+        return t.astype(np.complex128)
+
+
+def make_slot(cfg: CellConfig, slot_index: int = 0, seed: int | None = None) -> Slot:
+    """Generate one slot deterministically from (seed, slot_index)."""
+    rng = np.random.default_rng([cfg.seed if seed is None else seed, slot_index])
+    R, L, n_sc, N = cfg.n_rx, cfg.n_layers, cfg.n_sc, cfg.n_fft
+    q = cfg.qam_bits
+    if L > cfg.n_beams:
+        raise ValueError("more layers than beams")
+    comb = cfg.comb
+    ports = np.arange(L, dtype=np.int32) % comb
+
+    Hant = _channel(cfg, rng)                                            # [N_SC, R, L]
+    W = beam_matrix(cfg)
+    noise_var = float(10.0 ** (-cfg.snr_db / 10.0))
+
+    # DMRS: QPSK on each layer's comb, zero elsewhere.
+    pb = rng.integers(0, 2, size=(L, 2, n_sc, 2))
+    pil = qam_map(pb, 2)
+    a = np.arange(n_sc)
+    mask = (a[None, :] % comb) == ports[:, None]                          # [L, N_SC]
+    pil = pil * mask[:, None, :]
+    pilots = pil.astype(np.complex64)
+
+    bits = rng.integers(0, 2, size=(L, len(DATA_SYMBOLS), n_sc, q)).astype(np.uint8)
+    x = qam_map(bits, q)                                                  # [L, 12, N_SC]
+
+    # Transmitted grid t[l, s, a]; the pilots as the receiver knows them (complex64) are what is sent.
+    t = np.zeros((L, N_SYM, n_sc), dtype=np.complex128)
+    for j, s in enumerate(DMRS_SYMBOLS):
+        t[:, s, :] = pilots[:, j, :].astype(np.complex128)
+    for j, s in enumerate(DATA_SYMBOLS):
+        t[:, s, :] = x[:, j, :]
+
+    X = np.einsum("arl,lsa->sra", Hant, t)                                # [S, R, N_SC]
+    noise = (rng.standard_normal(X.shape) + 1j * rng.standard_normal(X.shape)) * np.sqrt(noise_var / 2.0)
+    X = X + noise
+
+    spec = np.zeros((N_SYM, R, N), dtype=np.complex128)
+    spec[:, :, active_bins(n_sc, N)] = X
+    time = np.fft.ifft(spec, axis=-1)
+    if cfg.in_fp16:
+        time_in = np.stack([time.real, time.imag], axis=-1).astype(np.float16)
+    else:
+        time_in = time.astype(np.complex64)
+
+    H_beam = np.einsum("rb,arl->alb", W.astype(np.complex128).conj(), Hant)   # [N_SC, L, B]
+    return Slot(cfg=cfg, time_in=time_in, W=W, pilots=pilots, ports=ports, noise_var=noise_var,
+                H_beam=H_beam, x=x, bits=pack_bits(bits))
+
+
+def make_slots(cfg: CellConfig, n: int, first: int = 0, seed: int | None = None) -> list[Slot]:
+    return [make_slot(cfg, first + i, seed) for i in range(n)]
