@@ -1,0 +1,423 @@
+"""Throughput benchmark of the PUSCH receive hot path on GB300: slots/s of the whole chain
+(OFDM FFT -> beamforming -> LS channel estimation -> MMSE detection) on the deployment cell
+(64 antennas, 4096-point FFT, 3276 subcarriers, 32 DFT beams, 16 single-layer 16-QAM users, 30 dB).
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--slots B] [--form mixed|fp32]
+
+A step is one pass of the whole chain over a batch of B distinct synthetic slots already resident in HBM
+(B = 16 -> 235 MB of FP16 time samples per step, more than the 129 MB L2, so every step streams from HBM).
+Rank 0 prints one JSON line. --impl reference times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PUSCH slots/s per GB300, mixed-prec+batched vs FP32, at EVM <= -40 dB vs FP64"
+UNIT = "slots/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--slots", type=int, default=16)
+    ap.add_argument("--form", default="auto", choices=["auto", "mixed", "fp32"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------------------- distributed
+def dist_init(n_gpus):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    mx = float(p[2])
+                except ValueError:
+                    continue
+                for n, v in zip(names, p[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------------------- workload
+def workload(n_slots):
+    from paper_2210_09196_gb300 import synth
+    cell = synth.DEPLOY
+    slots = synth.make_slots(cell, n_slots)
+    return cell, slots
+
+
+def stage_bytes(cell, form, n):
+    """Algorithmic bytes per launch of each stage for a batch of n slots (read + write once)."""
+    S, R, N, sc, Bm, L = 14, cell.n_rx, cell.n_fft, cell.n_sc, cell.n_beams, cell.n_layers
+    t_in = S * R * N * (4 if cell.in_fp16 else 8)
+    f_out = S * R * sc * (4 if form == "mixed" else 8)
+    beam = S * sc * Bm * 8
+    W = R * Bm * 8
+    H = sc * L * Bm * 8
+    pil = L * 2 * sc * 8
+    dmrs = 2 * sc * Bm * 8
+    data = 12 * sc * Bm * 8
+    xh = L * 12 * sc * 8
+    bits = L * 12 * sc
+    return {
+        "fft": n * (t_in + f_out),
+        "beamform": n * (f_out + beam) + W,
+        "chest": n * (dmrs + pil + H),
+        "mmse": n * (H + data + xh + bits),
+    }
+
+
+def stage_flops(cell, n):
+    S, R, sc, Bm, L = 14, cell.n_rx, cell.n_sc, cell.n_beams, cell.n_layers
+    return {"beamform": n * 8.0 * S * sc * R * Bm}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return {"hbm_gbs": float(p["hbm_gbs"]), "bf16_tflops": float(p["bf16_tflops"]),
+                "bf16_tflops_sustained": float(p.get("bf16_tflops_sustained", p["bf16_tflops"])),
+                "src": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "src": "fallback"}
+
+
+def fp32_alu_peak_tflops(sm_mhz):
+    # 152 SMs x 128 FP32 lanes x 2 flop per FMA x clock
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+# ------------------------------------------------------------------------------------------ our arm
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    from paper_2210_09196_gb300 import binding as B
+    from paper_2210_09196_gb300 import host
+
+    torch.cuda.set_device(local)
+    cell, slots = workload(args.slots)
+    form = args.form
+    if form == "auto":
+        cfg_m = host.cfg_for(cell, B.PUSCH_FORM_MIXED)
+        try:
+            B.pusch_workspace_size(cfg_m, 1)
+            form = "mixed"
+        except B.PuschError:
+            form = "fp32"
+    n = args.slots
+    time_d = host.time_tensor(slots)
+    pil_d = host.pilot_tensor(slots)
+    W = host.beam_tensor(slots[0].W)
+
+    def make_rx(f):
+        return host.Receiver(host.cfg_for(cell, B.PUSCH_FORM_MIXED if f == "mixed" else B.PUSCH_FORM_FP32), n)
+
+    def timed(rx, steps, warmup, per_stage):
+        """Time `steps` chain passes; per_stage -> events between the four stage launches."""
+        st = torch.cuda.current_stream()
+        freq, beam, H = rx.freq_buffer(n), rx.beam_buffer(n), rx.H_buffer(n)
+        x, b, stat = rx.xhat_buffer(n), rx.bits_buffer(n), rx.status_buffer()
+
+        def step(ev=None):
+            if ev is not None:
+                ev[0].record(st)
+            B.pusch_ofdm_fft(rx.h, n, time_d, freq, st)
+            if ev is not None:
+                ev[1].record(st)
+            B.pusch_beamform(rx.h, n, freq, W, beam, st)
+            if ev is not None:
+                ev[2].record(st)
+            B.pusch_chest_ls(rx.h, n, beam, pil_d, H, st)
+            if ev is not None:
+                ev[3].record(st)
+            B.pusch_mmse_detect(rx.h, n, H, beam, x, b, stat, st)
+            if ev is not None:
+                ev[4].record(st)
+
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(steps)] if per_stage else None
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier(world)
+        torch.cuda.synchronize()
+        start.record(st)
+        for k in range(steps):
+            step(evs[k] if per_stage else None)
+        end.record(st)
+        torch.cuda.synchronize()
+        barrier(world)
+        total_ms = start.elapsed_time(end)
+        stages = None
+        if per_stage:
+            names = ["fft", "beamform", "chest", "mmse"]
+            stages = {nm: sum(e[i].elapsed_time(e[i + 1]) for e in evs) / steps for i, nm in enumerate(names)}
+        return total_ms, stages, (x, b, stat)
+
+    # headline form, timed with per-stage events inside the timed region
+    rx = make_rx(form)
+    sampler = ClockSampler(local)
+    sampler.start()
+    total_ms, stages, outs = timed(rx, args.steps, args.warmup, per_stage=True)
+    clocks = sampler.stop()
+    t_max = max_over_ranks(total_ms, world)
+    value = n * args.steps * world / (t_max / 1e3)
+    stat = outs[2].cpu().numpy()
+
+    # plain FP32 form beside it (same steps)
+    fp32 = None
+    if form == "mixed":
+        rx32 = make_rx("fp32")
+        t32, st32, _ = timed(rx32, args.steps, args.warmup, per_stage=True)
+        t32 = max_over_ranks(t32, world)
+        fp32 = {"value": n * args.steps * world / (t32 / 1e3), "ms_per_step": t32 / args.steps,
+                "stage_ms": st32}
+        rx32.close()
+
+    # end to end through pusch_slot_host with page-locked host buffers
+    e2e = None
+    if not args.no_e2e:
+        t_h = host.time_tensor(slots, "cpu", pin=True)
+        p_h = host.pilot_tensor(slots, "cpu", pin=True)
+        out_h = (rx.xhat_buffer(n, "cpu").pin_memory(), rx.bits_buffer(n, "cpu").pin_memory(),
+                 rx.status_buffer("cpu").pin_memory())
+        e_steps = max(3, min(args.steps, 50))
+        for _ in range(max(3, args.warmup)):
+            rx.slot_host(t_h, W, p_h, out_h)
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e_steps):
+            rx.slot_host(t_h, W, p_h, out_h)
+        torch.cuda.synchronize()
+        dt = max_over_ranks(time.perf_counter() - t0, world)
+        h2d = t_h.numel() * t_h.element_size() + p_h.numel() * p_h.element_size()
+        d2h = sum(t.numel() * t.element_size() for t in out_h)
+        e2e = {"value": n * e_steps * world / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "steps": e_steps}
+
+    if rank != 0:
+        rx.close()
+        return None
+
+    pk = peaks()
+    sb = stage_bytes(cell, form, n)
+    dom = max(stages, key=stages.get)
+    dom_ms = stages[dom]
+    sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    if dom == "beamform" and form == "fp32":
+        fl = stage_flops(cell, n)["beamform"]
+        ach = fl / (dom_ms / 1e3) / 1e12
+        peak = fp32_alu_peak_tflops(2070.0)
+        roof = {"kernel": "beamform_fp32_kernel", "bound": "alu", "achieved": round(ach, 2), "peak": round(peak, 1),
+                "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": None,
+                "peak_src": "FP32 FMA issue rate 152 SMs x 128 lanes x 2 x 2070 MHz"}
+    else:
+        kname = {"fft": "fft_kernel", "beamform": "beamform_tc_kernel", "chest": "chest_ls_kernel",
+                 "mmse": "mmse_kernel"}[dom]
+        ach = sb[dom] / (dom_ms / 1e3) / 1e9
+        roof = {"kernel": kname, "bound": "hbm", "achieved": round(ach, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": round(ach / pk["hbm_gbs"], 4), "traffic": None, "peak_src": pk["src"]}
+    per_stage = {k: {"ms": round(v, 4), "GB/s": round(sb[k] / (v / 1e3) / 1e9, 1),
+                     "hbm_frac": round(sb[k] / (v / 1e3) / 1e9 / pk["hbm_gbs"], 4)} for k, v in stages.items()}
+    per_stage["beamform"]["TFLOP/s"] = round(stage_flops(cell, n)["beamform"] / (stages["beamform"] / 1e3) / 1e12, 2)
+
+    cpu = None
+    if not args.no_cpu_baseline and world >= 1:
+        cpu = cpu_baseline(slots, budget_s=12.0)
+
+    launches_per_step = 5 + (1 if form == "mixed" else 0)
+    out = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "fp16+f32" if form == "mixed" else "f32",
+        "data": "synthetic (seeded generator: 16-tap exponential PDP channel, 16-QAM, 30 dB)",
+        "config": {"workload": cell.name, "form": form, "slots_per_step": n, "n_rx": cell.n_rx,
+                   "n_fft": cell.n_fft, "n_sc": cell.n_sc, "n_beams": cell.n_beams, "n_layers": cell.n_layers,
+                   "time_input": "complex fp16",
+                   "l2": f"inputs larger than L2 ({sb['fft'] // 2**20} MiB FFT traffic per step)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": roof,
+        "stages": per_stage,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+        "device_status": [int(v) & 0xffffffff for v in stat],
+    }
+    if fp32 is not None:
+        out["fp32_form"] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in fp32.items()}
+    rx.close()
+    return out
+
+
+# ---------------------------------------------------------------------------------------- oracle arm
+def cpu_baseline(slots, budget_s):
+    import oracle
+    oracle.build()
+    done, t0 = 0, time.perf_counter()
+    for s in slots:
+        oracle.run_slot(s)
+        done += 1
+        if time.perf_counter() - t0 > budget_s and done >= 2:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": round(done / dt, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{done} whole deployment slots through the FP64 C oracle (single thread), {dt:.1f} s"}
+
+
+def reference_step(oracle, s, frac, rng):
+    """The FP64 oracle chain on a bounded sample of one slot: a fraction `frac` of the FFT rows and a
+    contiguous `frac` of the subcarriers for beamforming, channel estimation and detection."""
+    import numpy as np
+    cell = s.cfg
+    S, R = 14, cell.n_rx
+    n_rows = max(1, int(round(frac * S * R)))
+    rows = rng.choice(S * R, n_rows, replace=False)
+    pairs = np.stack([rows // R, rows % R], axis=1)
+    freq = oracle.ofdm_demod(s.time_as_complex128(), cell.n_sc, pairs=pairs)
+    n_sc = max(cell.comb, int(round(frac * cell.n_sc)))
+    a0 = int(rng.integers(0, cell.n_sc - n_sc + 1))
+    sl = slice(a0, a0 + n_sc)
+    beam = oracle.beamform(freq[:, :, sl], s.W)
+    ports = [(p - a0) % cell.comb for p in s.ports]
+    H = oracle.chest_ls(beam, s.pilots[:, :, sl], ports, cell.comb)
+    x, _ = oracle.mmse(H, beam, s.noise_var)
+    oracle.demap(x, cell.qam_bits)
+    return 0.5 * (n_rows / (S * R) + n_sc / cell.n_sc)  # fraction of a slot processed
+
+
+def run_reference(args, rank, world):
+    import numpy as np
+    import oracle
+    oracle.build()
+    if rank != 0:
+        return None
+    from paper_2210_09196_gb300 import synth
+    cell = synth.DEPLOY
+    s = synth.make_slot(cell, 0)
+    rng = np.random.default_rng(0)
+    # calibrate: time of a 1/16 sample, then size the per-step sample so K + W steps take ~120 s
+    t0 = time.perf_counter()
+    f0 = reference_step(oracle, s, 1 / 16, rng)
+    t_slot = (time.perf_counter() - t0) / f0
+    frac = min(1.0, max(1 / 64, 120.0 / max(1, args.steps + args.warmup) / t_slot))
+    for _ in range(args.warmup):
+        reference_step(oracle, s, frac, rng)
+    done, t0 = 0.0, time.perf_counter()
+    for _ in range(args.steps):
+        done += reference_step(oracle, s, frac, rng)
+    dt = time.perf_counter() - t0
+    value = done / dt
+    return {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded generator)",
+        "config": {"workload": cell.name, "form": "fp64 oracle", "slots_per_step": round(frac, 5)},
+        "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "kind": "oracle", "cores": 1,
+                         "sample": f"per step {frac:.4f} of a deployment slot (FFT rows and subcarriers sampled)"},
+        "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_init(args.gpus)
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_ours(args, rank, world, local)
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,172 @@
+/*
+ * pusch.h -- C ABI of the GB300 (sm_103a) PUSCH receive hot path.
+ *
+ * The path is the lower-PHY PUSCH receive chain of "Efficient Parallelization of 5G-PUSCH on a Scalable
+ * RISC-V Many-core Processor" (arXiv 2210.09196), Section II and Fig. 1:
+ *   OFDM demodulation (one FFT per antenna and symbol) -> beamforming (y = W^H x per subcarrier)
+ *   -> LS channel estimation on the DMRS symbols -> MMSE MIMO detection (Eq. 2) by Gram matrix,
+ *   Cholesky factorisation (Section V-C) and two triangular solves -> hard decisions.
+ *
+ * Conventions shared by every entry point
+ *   - Complex numbers are interleaved (re, im). "c64" = two floats (torch.complex64); "c16" = two IEEE
+ *     binary16 values (torch.complex32 / half2).
+ *   - Every data pointer is a DEVICE pointer owned by the caller, except in pusch_slot_host, which takes
+ *     host pointers. The library never frees caller memory. `stream` is a cudaStream_t (NULL = legacy
+ *     default stream). Calls are asynchronous on that stream; outputs are valid once it reaches them.
+ *   - A batch of n_slots slots of the same cell is processed by one call; arrays carry a leading
+ *     [n_slots] dimension that is not repeated in the layouts below.
+ *   - Arguments are validated on the host before any launch; an invalid call returns PUSCH_ERR_ARG (or
+ *     PUSCH_ERR_UNSUPPORTED for a shape outside the supported range) and launches nothing.
+ *     pusch_last_error() then returns a message (thread-local, valid until the next call on the thread).
+ *   - Numeric failures inside a kernel (a non-positive Cholesky pivot, a non-finite value) do not change
+ *     the return value; they are reported through the caller's device status words (see PUSCH_STATUS_*).
+ *   - No C++ exception crosses this interface.
+ *
+ * Supported shapes: n_fft a power of two in [64, 4096]; 1 <= n_sc <= n_fft; 1 <= n_beams <= 64;
+ * 1 <= n_layers <= 32 and n_layers <= n_beams; 1 <= comb <= n_sc; n_sym = 14 with two distinct DMRS
+ * symbols; 1 <= n_rx <= 1024; qam_bits 2 (QPSK) or 4 (16-QAM).
+ */
+#ifndef PUSCH_H
+#define PUSCH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PUSCH_OK = 0,
+    PUSCH_ERR_ARG = -1,         /* invalid argument (null pointer, size out of range, bad config)   */
+    PUSCH_ERR_CUDA = -2,        /* a CUDA runtime call failed; the message names it                 */
+    PUSCH_ERR_NUMERIC = -3,     /* only from pusch_status_check: the status words report a failure  */
+    PUSCH_ERR_TIMEOUT = -4,     /* a bounded device wait expired                                    */
+    PUSCH_ERR_UNSUPPORTED = -5  /* valid but outside the shapes this build implements               */
+} pusch_status;
+
+/* Arithmetic form of the chain. */
+typedef enum {
+    PUSCH_FORM_FP32 = 0,   /* plain: FFT and beamforming in FP32, intermediates stored as c64           */
+    PUSCH_FORM_MIXED = 1   /* FFT in FP32 registers with its output stored as FP16; beamforming on the
+                              tcgen05 tensor cores with FP16 operands and FP32 accumulation. Channel
+                              estimation and detection stay FP32 in both forms.                          */
+} pusch_form;
+
+/* Device status words written by the detection kernels (uint32_t status[4]):
+ *   status[0] bit field of PUSCH_STATUS_* flags
+ *   status[1] number of (slot, subcarrier) factorisations whose pivot was not a positive finite number
+ *   status[2] smallest failing (slot * n_sc + subcarrier) index, 0xFFFFFFFF if none
+ *   status[3] reserved (0)
+ * The entry points that take `status` reset it to {0, 0, 0xFFFFFFFF, 0} on the stream first. */
+#define PUSCH_STATUS_PIVOT 0x1u     /* Cholesky met a non-positive or non-finite pivot            */
+#define PUSCH_STATUS_NONFINITE 0x2u /* a detected symbol came out non-finite                      */
+
+typedef struct {
+    int n_rx;          /* N_R receive antennas                                                   */
+    int n_fft;         /* N_F FFT size                                                           */
+    int n_sc;          /* N_SC active subcarriers; subcarrier a is FFT bin (a - n_sc/2) mod n_fft */
+    int n_beams;       /* N_B beams                                                              */
+    int n_layers;      /* N_L layers (single-layer users) detected jointly on every subcarrier   */
+    int comb;          /* DMRS comb size: layer l has pilots on subcarriers a, a % comb == port[l] */
+    int port[32];      /* comb offset of each layer, 0 <= port[l] < comb                          */
+    int qam_bits;      /* 2 = QPSK, 4 = 16-QAM (Gray, 3GPP TS 38.211 5.1.3/5.1.4)                 */
+    int in_fp16;       /* 1: time samples are c16; 0: c64                                        */
+    int form;          /* pusch_form                                                             */
+    int n_sym;         /* OFDM symbols per slot, 14                                              */
+    int dmrs_sym[2];   /* the two DMRS (pilot) symbols, e.g. {2, 11}                             */
+    float noise_var;   /* sigma^2 of Eq. 2                                                       */
+    float loading;     /* extra diagonal loading added to sigma^2 (0 = the plain Eq. 2)          */
+} pusch_cell_cfg;
+
+typedef struct pusch_handle pusch_handle;   /* opaque: owns the twiddle table and workspace   */
+
+/* Creates a handle for one cell configuration and batches of up to max_slots slots. Allocates device
+ * memory for the FFT twiddle table, the beam-matrix operand and the chain's intermediates (see
+ * pusch_workspace_size) on the current device. Synchronous. */
+pusch_status pusch_create(pusch_handle **h, const pusch_cell_cfg *cfg, int max_slots);
+
+/* Frees everything the handle owns. Synchronises the device first. NULL is accepted. */
+pusch_status pusch_destroy(pusch_handle *h);
+
+/* Bytes of device workspace pusch_create allocates for (cfg, max_slots). */
+pusch_status pusch_workspace_size(const pusch_cell_cfg *cfg, int max_slots, size_t *bytes);
+
+/* Number of c16 elements between the re and im planes of one mixed-form FFT output row
+ * (n_sc rounded up to a multiple of 8, so that every row starts on a 16-byte boundary). */
+int pusch_sc_pitch(const pusch_cell_cfg *cfg);
+
+/*
+ * OFDM demodulation (Section II; Table I "OFDM dem."): for every slot, symbol s and antenna r,
+ *     X[s][r][a] = sum_n x[s][r][n] exp(-2 pi i k n / N_F),  k = (a - N_SC/2) mod N_F,  a < N_SC.
+ * time_in : [n_sym][n_rx][n_fft] c64 (cfg.in_fp16 = 0) or c16 (cfg.in_fp16 = 1).
+ * freq_out: FP32 form  -> [n_sym][n_rx][n_sc] c64.
+ *           mixed form -> [n_sym][n_rx][2][pitch] binary16: plane 0 = re, plane 1 = im of bins 0..n_sc-1
+ *                         (pitch = pusch_sc_pitch(cfg); elements n_sc..pitch-1 are written as 0).
+ */
+pusch_status pusch_ofdm_fft(pusch_handle *h, int n_slots, const void *time_in, void *freq_out, void *stream);
+
+/*
+ * Beamforming (Section II, Table I "BF": a matrix-matrix product with known coefficients):
+ *     Y[s][a][b] = sum_r conj(W[r][b]) X[s][r][a]      (y = W^H x per subcarrier and symbol)
+ * freq_in : the layout pusch_ofdm_fft writes for cfg.form.
+ * W       : [n_rx][n_beams] c64.
+ * beam_out: [n_sym][n_sc][n_beams] c64 (all symbols, DMRS included).
+ */
+pusch_status pusch_beamform(pusch_handle *h, int n_slots, const void *freq_in, const void *W, void *beam_out,
+                            void *stream);
+
+/*
+ * LS channel estimation (Section II: block-type pilots filling whole OFDM symbols; LS is an element-wise
+ * division). For layer l and each of its pilot subcarriers q (q % comb == port[l]):
+ *     LS[q][l][b] = 1/2 sum_{j=0,1} Y[dmrs_sym[j]][q][b] / P[l][j][q]
+ * and every subcarrier a is linearly interpolated between the neighbouring pilot subcarriers of the
+ * layer, holding the first/last pilot's value outside them.
+ * beam   : [n_sym][n_sc][n_beams] c64 (only the DMRS symbols are read).
+ * pilots : [n_layers][2][n_sc] c64 (entries off the layer's comb are not read).
+ * H_hat  : [n_sc][n_layers][n_beams] c64.
+ */
+pusch_status pusch_chest_ls(pusch_handle *h, int n_slots, const void *beam, const void *pilots, void *H_hat,
+                            void *stream);
+
+/*
+ * MMSE detection (Eq. 2 with Section II's Cholesky + two triangular solves), per subcarrier a:
+ *     G = H^H H + (noise_var + loading) I,  G = L L^H,  L z = H^H y,  L^H x = z
+ * for the 12 data symbols (all symbols other than dmrs_sym, in increasing order); hard decisions by
+ * Gray demapping with ties to bit 0. G and L are formed once per subcarrier (the estimate does not change
+ * within the slot, so this equals forming them per data symbol).
+ * H_hat : [n_sc][n_layers][n_beams] c64;  beam : [n_sym][n_sc][n_beams] c64.
+ * x_hat : [n_layers][n_sym-2][n_sc] c64;  bits : [n_layers][n_sym-2][n_sc] uint8 (bit j = b_j).
+ * status: uint32_t[4] device status words (may be NULL to skip reporting).
+ */
+pusch_status pusch_mmse_detect(pusch_handle *h, int n_slots, const void *H_hat, const void *beam, void *x_hat,
+                               uint8_t *bits, uint32_t *status, void *stream);
+
+/*
+ * The whole chain for n_slots slots: pusch_ofdm_fft -> pusch_beamform -> pusch_chest_ls ->
+ * pusch_mmse_detect, with the intermediates in the handle's workspace (n_slots <= max_slots).
+ * time_in, W, pilots, x_hat, bits, status: as in the stage entry points.
+ */
+pusch_status pusch_slot(pusch_handle *h, int n_slots, const void *time_in, const void *W, const void *pilots,
+                        void *x_hat, uint8_t *bits, uint32_t *status, void *stream);
+
+/*
+ * pusch_slot on HOST buffers: copies time_in and pilots host->device into handle-owned staging buffers,
+ * runs the chain, copies x_hat, bits and status device->host, all on `stream`, then waits for the stream.
+ * W is a DEVICE pointer (it is fixed per cell). Host buffers should be page-locked for full speed.
+ */
+pusch_status pusch_slot_host(pusch_handle *h, int n_slots, const void *time_in_host, const void *W,
+                             const void *pilots_host, void *x_hat_host, uint8_t *bits_host, uint32_t *status_host,
+                             void *stream);
+
+/* Message of the last non-OK status returned on this thread ("" if none). */
+const char *pusch_last_error(void);
+
+/* Library version string. */
+const char *pusch_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PUSCH_H */

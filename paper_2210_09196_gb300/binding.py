@@ -1,0 +1,177 @@
+"""Thin ctypes binding of libpusch (include/pusch.h): argument marshalling only.
+
+Every computation runs in the CUDA kernels of libpusch.so. There is no CPU or PyTorch fallback: if the
+library is missing or cannot be loaded, every entry point raises.
+
+Functions keep the C names. Buffers may be passed as torch tensors (their ``data_ptr()`` is used; device
+tensors for device pointers, CPU tensors for the host buffers of ``pusch_slot_host``) or as raw integer
+addresses. ``stream`` may be a ``torch.cuda.Stream``, an integer cudaStream_t or None (the current torch
+stream).
+"""
+from __future__ import annotations
+
+import ctypes
+from pathlib import Path
+
+_PKG = Path(__file__).resolve().parent
+LIB_PATH = _PKG / "_build" / "libpusch.so"
+
+PUSCH_OK = 0
+PUSCH_ERR_ARG = -1
+PUSCH_ERR_CUDA = -2
+PUSCH_ERR_NUMERIC = -3
+PUSCH_ERR_TIMEOUT = -4
+PUSCH_ERR_UNSUPPORTED = -5
+
+PUSCH_FORM_FP32 = 0
+PUSCH_FORM_MIXED = 1
+
+PUSCH_STATUS_PIVOT = 0x1
+PUSCH_STATUS_NONFINITE = 0x2
+
+# every symbol include/pusch.h declares
+EXPORTS = (
+    "pusch_create", "pusch_destroy", "pusch_workspace_size", "pusch_sc_pitch", "pusch_ofdm_fft", "pusch_beamform",
+    "pusch_chest_ls", "pusch_mmse_detect", "pusch_slot", "pusch_slot_host", "pusch_last_error", "pusch_version",
+)
+
+
+class PuschError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where} failed with status {code}: {msg}")
+        self.code = code
+
+
+class pusch_cell_cfg(ctypes.Structure):
+    _fields_ = [
+        ("n_rx", ctypes.c_int), ("n_fft", ctypes.c_int), ("n_sc", ctypes.c_int), ("n_beams", ctypes.c_int),
+        ("n_layers", ctypes.c_int), ("comb", ctypes.c_int), ("port", ctypes.c_int * 32),
+        ("qam_bits", ctypes.c_int), ("in_fp16", ctypes.c_int), ("form", ctypes.c_int), ("n_sym", ctypes.c_int),
+        ("dmrs_sym", ctypes.c_int * 2), ("noise_var", ctypes.c_float), ("loading", ctypes.c_float),
+    ]
+
+
+def make_cfg(*, n_rx, n_fft, n_sc, n_beams, n_layers, comb=None, ports=None, qam_bits=2, in_fp16=False,
+             form=PUSCH_FORM_FP32, noise_var=0.0, loading=0.0, n_sym=14, dmrs_sym=(2, 11)) -> pusch_cell_cfg:
+    c = pusch_cell_cfg()
+    c.n_rx, c.n_fft, c.n_sc, c.n_beams, c.n_layers = n_rx, n_fft, n_sc, n_beams, n_layers
+    c.comb = n_layers if comb is None else comb
+    ports = list(range(n_layers)) if ports is None else list(ports)
+    for i, p in enumerate(ports[:32]):
+        c.port[i] = int(p)
+    c.qam_bits, c.in_fp16, c.form, c.n_sym = qam_bits, int(bool(in_fp16)), int(form), n_sym
+    c.dmrs_sym[0], c.dmrs_sym[1] = dmrs_sym
+    c.noise_var, c.loading = float(noise_var), float(loading)
+    return c
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not LIB_PATH.exists():
+            raise RuntimeError(f"libpusch.so is not built ({LIB_PATH}); run __graft_entry__.build() first")
+        L = ctypes.CDLL(str(LIB_PATH))
+        P, I = ctypes.c_void_p, ctypes.c_int
+        sig = {
+            "pusch_create": (I, [ctypes.POINTER(P), ctypes.POINTER(pusch_cell_cfg), I]),
+            "pusch_destroy": (I, [P]),
+            "pusch_workspace_size": (I, [ctypes.POINTER(pusch_cell_cfg), I, ctypes.POINTER(ctypes.c_size_t)]),
+            "pusch_sc_pitch": (I, [ctypes.POINTER(pusch_cell_cfg)]),
+            "pusch_ofdm_fft": (I, [P, I, P, P, P]),
+            "pusch_beamform": (I, [P, I, P, P, P, P]),
+            "pusch_chest_ls": (I, [P, I, P, P, P, P]),
+            "pusch_mmse_detect": (I, [P, I, P, P, P, P, P, P]),
+            "pusch_slot": (I, [P, I, P, P, P, P, P, P, P]),
+            "pusch_slot_host": (I, [P, I, P, P, P, P, P, P, P]),
+            "pusch_last_error": (ctypes.c_char_p, []),
+            "pusch_version": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(s):
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _check(code: int, where: str):
+    if code != PUSCH_OK:
+        raise PuschError(code, where, lib().pusch_last_error().decode())
+
+
+def pusch_version() -> str:
+    return lib().pusch_version().decode()
+
+
+def pusch_last_error() -> str:
+    return lib().pusch_last_error().decode()
+
+
+def pusch_sc_pitch(cfg: pusch_cell_cfg) -> int:
+    return lib().pusch_sc_pitch(ctypes.byref(cfg))
+
+
+def pusch_workspace_size(cfg: pusch_cell_cfg, max_slots: int) -> int:
+    out = ctypes.c_size_t()
+    _check(lib().pusch_workspace_size(ctypes.byref(cfg), max_slots, ctypes.byref(out)), "pusch_workspace_size")
+    return out.value
+
+
+def pusch_create(cfg: pusch_cell_cfg, max_slots: int) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().pusch_create(ctypes.byref(h), ctypes.byref(cfg), max_slots), "pusch_create")
+    return h.value
+
+
+def pusch_destroy(h) -> None:
+    _check(lib().pusch_destroy(h), "pusch_destroy")
+
+
+def pusch_ofdm_fft(h, n_slots, time_in, freq_out, stream=None) -> None:
+    _check(lib().pusch_ofdm_fft(h, n_slots, _ptr(time_in), _ptr(freq_out), _stream(stream)), "pusch_ofdm_fft")
+
+
+def pusch_beamform(h, n_slots, freq_in, W, beam_out, stream=None) -> None:
+    _check(lib().pusch_beamform(h, n_slots, _ptr(freq_in), _ptr(W), _ptr(beam_out), _stream(stream)),
+           "pusch_beamform")
+
+
+def pusch_chest_ls(h, n_slots, beam, pilots, H_hat, stream=None) -> None:
+    _check(lib().pusch_chest_ls(h, n_slots, _ptr(beam), _ptr(pilots), _ptr(H_hat), _stream(stream)),
+           "pusch_chest_ls")
+
+
+def pusch_mmse_detect(h, n_slots, H_hat, beam, x_hat, bits, status=None, stream=None) -> None:
+    _check(lib().pusch_mmse_detect(h, n_slots, _ptr(H_hat), _ptr(beam), _ptr(x_hat), _ptr(bits), _ptr(status),
+                                   _stream(stream)), "pusch_mmse_detect")
+
+
+def pusch_slot(h, n_slots, time_in, W, pilots, x_hat, bits, status=None, stream=None) -> None:
+    _check(lib().pusch_slot(h, n_slots, _ptr(time_in), _ptr(W), _ptr(pilots), _ptr(x_hat), _ptr(bits), _ptr(status),
+                            _stream(stream)), "pusch_slot")
+
+
+def pusch_slot_host(h, n_slots, time_in_host, W, pilots_host, x_hat_host, bits_host, status_host=None,
+                    stream=None) -> None:
+    _check(lib().pusch_slot_host(h, n_slots, _ptr(time_in_host), _ptr(W), _ptr(pilots_host), _ptr(x_hat_host),
+                                 _ptr(bits_host), _ptr(status_host), _stream(stream)), "pusch_slot_host")

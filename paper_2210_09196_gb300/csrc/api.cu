@@ -1,0 +1,354 @@
+// C ABI of libpusch: handle management, host-side validation and the stage / chain entry points.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "internal.cuh"
+
+struct pusch_handle {
+    pusch_cell_cfg cfg;
+    pusch::Geometry geo;
+    int max_slots = 0;
+    int device = 0;
+    float2 *twiddle = nullptr;      // exp(-2 pi i q / n_fft), q < n_fft
+    void *bf_operand = nullptr;     // mixed form: beam-matrix tensor-core operand
+    void *freq = nullptr;           // workspace: FFT output
+    float2 *beam = nullptr;         // workspace: beamformed grid
+    float2 *H = nullptr;            // workspace: channel estimate
+    uint32_t *status_sink = nullptr;  // status words used when the caller passes NULL
+    // staging for pusch_slot_host (allocated on first use)
+    void *h_time = nullptr;
+    float2 *h_pilots = nullptr;
+    float2 *h_xhat = nullptr;
+    uint8_t *h_bits = nullptr;
+    uint32_t *h_status = nullptr;
+};
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+pusch_status fail(pusch_status st, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+pusch_status ok() {
+    g_err[0] = '\0';
+    return PUSCH_OK;
+}
+
+pusch_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(PUSCH_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+pusch_status validate_cfg(const pusch_cell_cfg *c) {
+    if (!c) return fail(PUSCH_ERR_ARG, "cfg is NULL");
+    if (!is_pow2(c->n_fft) || c->n_fft < 64 || c->n_fft > 4096)
+        return fail(PUSCH_ERR_UNSUPPORTED, "n_fft=%d: must be a power of two in [64, 4096]", c->n_fft);
+    if (c->n_sc < 1 || c->n_sc > c->n_fft) return fail(PUSCH_ERR_ARG, "n_sc=%d out of [1, n_fft]", c->n_sc);
+    if (c->n_rx < 1 || c->n_rx > 1024) return fail(PUSCH_ERR_UNSUPPORTED, "n_rx=%d out of [1, 1024]", c->n_rx);
+    if (c->n_beams < 1 || c->n_beams > 64)
+        return fail(PUSCH_ERR_UNSUPPORTED, "n_beams=%d out of [1, 64]", c->n_beams);
+    if (c->n_layers < 1 || c->n_layers > 32 || c->n_layers > c->n_beams)
+        return fail(PUSCH_ERR_ARG, "n_layers=%d out of [1, min(32, n_beams)]", c->n_layers);
+    if (c->comb < 1 || c->comb > c->n_sc) return fail(PUSCH_ERR_ARG, "comb=%d out of [1, n_sc]", c->comb);
+    for (int l = 0; l < c->n_layers; ++l)
+        if (c->port[l] < 0 || c->port[l] >= c->comb)
+            return fail(PUSCH_ERR_ARG, "port[%d]=%d out of [0, comb)", l, c->port[l]);
+    if (c->qam_bits != 2 && c->qam_bits != 4) return fail(PUSCH_ERR_ARG, "qam_bits=%d: 2 or 4", c->qam_bits);
+    if (c->in_fp16 != 0 && c->in_fp16 != 1) return fail(PUSCH_ERR_ARG, "in_fp16 must be 0 or 1");
+    if (c->form != PUSCH_FORM_FP32 && c->form != PUSCH_FORM_MIXED) return fail(PUSCH_ERR_ARG, "unknown form %d", c->form);
+    if (c->n_sym < 3 || c->n_sym > 16) return fail(PUSCH_ERR_ARG, "n_sym=%d out of [3, 16]", c->n_sym);
+    if (c->dmrs_sym[0] < 0 || c->dmrs_sym[0] >= c->n_sym || c->dmrs_sym[1] < 0 || c->dmrs_sym[1] >= c->n_sym ||
+        c->dmrs_sym[0] == c->dmrs_sym[1])
+        return fail(PUSCH_ERR_ARG, "dmrs_sym must be two distinct symbols of the slot");
+    if (!(c->noise_var >= 0.f) || !isfinite(c->noise_var)) return fail(PUSCH_ERR_ARG, "noise_var must be >= 0");
+    if (!(c->loading >= 0.f) || !isfinite(c->loading)) return fail(PUSCH_ERR_ARG, "loading must be >= 0");
+    if (c->form == PUSCH_FORM_MIXED) {
+        pusch::Geometry g = pusch::make_geometry(*c);
+        if (!pusch::bf_tc_supported(g))
+            return fail(PUSCH_ERR_UNSUPPORTED,
+                        "mixed form needs n_beams a multiple of 8 and n_rx in {8,16,...,128} (multiple of 8)");
+    }
+    return PUSCH_OK;
+}
+
+size_t freq_bytes(const pusch::Geometry &g, int n_slots) {
+    const size_t rows = (size_t)n_slots * g.n_sym * g.n_rx;
+    return g.form == PUSCH_FORM_MIXED ? rows * 2 * g.sc_pitch * sizeof(__half) : rows * g.n_sc * sizeof(float2);
+}
+size_t beam_bytes(const pusch::Geometry &g, int n_slots) {
+    return (size_t)n_slots * g.n_sym * g.n_sc * g.n_beams * sizeof(float2);
+}
+size_t H_bytes(const pusch::Geometry &g, int n_slots) {
+    return (size_t)n_slots * g.n_sc * g.n_layers * g.n_beams * sizeof(float2);
+}
+size_t time_bytes(const pusch::Geometry &g, int n_slots) {
+    return (size_t)n_slots * g.n_sym * g.n_rx * g.n_fft * (g.in_fp16 ? 4 : 8);
+}
+size_t pilot_bytes(const pusch::Geometry &g, int n_slots) {
+    return (size_t)n_slots * g.n_layers * 2 * g.n_sc * sizeof(float2);
+}
+size_t xhat_count(const pusch::Geometry &g, int n_slots) {
+    return (size_t)n_slots * g.n_layers * g.n_data * g.n_sc;
+}
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+size_t workspace_bytes(const pusch::Geometry &g, int max_slots) {
+    size_t b = align256(g.n_fft * sizeof(float2));
+    if (g.form == PUSCH_FORM_MIXED) b += align256(pusch::bf_tc_operand_bytes(g));
+    b += align256(freq_bytes(g, max_slots)) + align256(beam_bytes(g, max_slots)) + align256(H_bytes(g, max_slots));
+    return b;
+}
+
+pusch_status check_handle(const pusch_handle *h, int n_slots) {
+    if (!h) return fail(PUSCH_ERR_ARG, "handle is NULL");
+    if (n_slots < 0 || n_slots > h->max_slots)
+        return fail(PUSCH_ERR_ARG, "n_slots=%d out of [0, max_slots=%d]", n_slots, h->max_slots);
+    return PUSCH_OK;
+}
+
+__global__ void status_init_kernel(uint32_t *status) {
+    status[0] = 0u;
+    status[1] = 0u;
+    status[2] = 0xffffffffu;
+    status[3] = 0u;
+}
+
+pusch_status reset_status(uint32_t *status, cudaStream_t st) {
+    status_init_kernel<<<1, 1, 0, st>>>(status);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "status reset");
+    return PUSCH_OK;
+}
+
+}  // namespace
+
+namespace pusch {
+
+Geometry make_geometry(const pusch_cell_cfg &c) {
+    Geometry g;
+    memset(&g, 0, sizeof g);
+    g.n_rx = c.n_rx;
+    g.n_fft = c.n_fft;
+    g.n_sc = c.n_sc;
+    g.n_beams = c.n_beams;
+    g.n_layers = c.n_layers;
+    g.comb = c.comb;
+    g.qam_bits = c.qam_bits;
+    g.in_fp16 = c.in_fp16;
+    g.form = c.form;
+    g.n_sym = c.n_sym;
+    g.dmrs0 = c.dmrs_sym[0];
+    g.dmrs1 = c.dmrs_sym[1];
+    g.noise_var = c.noise_var;
+    g.loading = c.loading;
+    g.sc_pitch = (c.n_sc + 7) & ~7;
+    for (int l = 0; l < 32; ++l) g.port[l] = l < c.n_layers ? c.port[l] : 0;
+    int nd = 0;
+    for (int s = 0; s < c.n_sym; ++s)
+        if (s != g.dmrs0 && s != g.dmrs1 && nd < 16) g.data_sym[nd++] = s;
+    g.n_data = nd;
+    return g;
+}
+
+}  // namespace pusch
+
+extern "C" {
+
+const char *pusch_last_error(void) { return g_err; }
+
+const char *pusch_version(void) { return "pusch-gb300 0.1 (sm_103a)"; }
+
+int pusch_sc_pitch(const pusch_cell_cfg *cfg) { return cfg ? (cfg->n_sc + 7) & ~7 : 0; }
+
+pusch_status pusch_workspace_size(const pusch_cell_cfg *cfg, int max_slots, size_t *bytes) {
+    pusch_status st = validate_cfg(cfg);
+    if (st != PUSCH_OK) return st;
+    if (max_slots < 1) return fail(PUSCH_ERR_ARG, "max_slots must be >= 1");
+    if (!bytes) return fail(PUSCH_ERR_ARG, "bytes is NULL");
+    *bytes = workspace_bytes(pusch::make_geometry(*cfg), max_slots);
+    return ok();
+}
+
+pusch_status pusch_create(pusch_handle **out, const pusch_cell_cfg *cfg, int max_slots) {
+    if (!out) return fail(PUSCH_ERR_ARG, "handle output pointer is NULL");
+    *out = nullptr;
+    pusch_status st = validate_cfg(cfg);
+    if (st != PUSCH_OK) return st;
+    if (max_slots < 1) return fail(PUSCH_ERR_ARG, "max_slots must be >= 1");
+    pusch_handle *h = new (std::nothrow) pusch_handle();
+    if (!h) return fail(PUSCH_ERR_ARG, "out of host memory");
+    h->cfg = *cfg;
+    h->geo = pusch::make_geometry(*cfg);
+    h->max_slots = max_slots;
+    cudaGetDevice(&h->device);
+    const pusch::Geometry &g = h->geo;
+
+    cudaError_t e;
+    std::vector<float2> tw(g.n_fft);
+    for (int q = 0; q < g.n_fft; ++q) {
+        const double ang = -2.0 * 3.14159265358979323846 * (double)q / (double)g.n_fft;
+        tw[q] = make_float2((float)cos(ang), (float)sin(ang));
+    }
+    if ((e = cudaMalloc(&h->twiddle, g.n_fft * sizeof(float2))) != cudaSuccess) goto cuda_error;
+    if ((e = cudaMemcpy(h->twiddle, tw.data(), g.n_fft * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess)
+        goto cuda_error;
+    if (g.form == PUSCH_FORM_MIXED) {
+        if ((e = cudaMalloc(&h->bf_operand, pusch::bf_tc_operand_bytes(g))) != cudaSuccess) goto cuda_error;
+    }
+    if ((e = cudaMalloc(&h->freq, freq_bytes(g, max_slots))) != cudaSuccess) goto cuda_error;
+    if ((e = cudaMalloc((void **)&h->beam, beam_bytes(g, max_slots))) != cudaSuccess) goto cuda_error;
+    if ((e = cudaMalloc((void **)&h->H, H_bytes(g, max_slots))) != cudaSuccess) goto cuda_error;
+    if ((e = cudaMalloc((void **)&h->status_sink, 4 * sizeof(uint32_t))) != cudaSuccess) goto cuda_error;
+    *out = h;
+    return ok();
+cuda_error:
+    pusch_destroy(h);
+    return cuda_fail(e, "pusch_create allocation");
+}
+
+pusch_status pusch_destroy(pusch_handle *h) {
+    if (!h) return ok();
+    cudaDeviceSynchronize();
+    cudaFree(h->twiddle);
+    cudaFree(h->bf_operand);
+    cudaFree(h->freq);
+    cudaFree(h->beam);
+    cudaFree(h->H);
+    cudaFree(h->status_sink);
+    cudaFree(h->h_time);
+    cudaFree(h->h_pilots);
+    cudaFree(h->h_xhat);
+    cudaFree(h->h_bits);
+    cudaFree(h->h_status);
+    delete h;
+    return ok();
+}
+
+pusch_status pusch_ofdm_fft(pusch_handle *h, int n_slots, const void *time_in, void *freq_out, void *stream) {
+    pusch_status st = check_handle(h, n_slots);
+    if (st != PUSCH_OK) return st;
+    if (n_slots == 0) return ok();
+    if (!time_in || !freq_out) return fail(PUSCH_ERR_ARG, "pusch_ofdm_fft: NULL buffer");
+    cudaError_t e = pusch::launch_fft(h->geo, n_slots, time_in, freq_out, h->twiddle, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "fft launch");
+    return ok();
+}
+
+pusch_status pusch_beamform(pusch_handle *h, int n_slots, const void *freq_in, const void *W, void *beam_out,
+                            void *stream) {
+    pusch_status st = check_handle(h, n_slots);
+    if (st != PUSCH_OK) return st;
+    if (n_slots == 0) return ok();
+    if (!freq_in || !W || !beam_out) return fail(PUSCH_ERR_ARG, "pusch_beamform: NULL buffer");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
+    if (h->geo.form == PUSCH_FORM_MIXED) {
+        if ((e = pusch::launch_bf_tc_prepare(h->geo, (const float2 *)W, h->bf_operand, s)) != cudaSuccess)
+            return cuda_fail(e, "beam operand launch");
+        e = pusch::launch_beamform_tc(h->geo, n_slots, (const __half *)freq_in, h->bf_operand, (float2 *)beam_out, s);
+    } else {
+        e = pusch::launch_beamform_fp32(h->geo, n_slots, (const float2 *)freq_in, (const float2 *)W,
+                                        (float2 *)beam_out, s);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "beamforming launch");
+    return ok();
+}
+
+pusch_status pusch_chest_ls(pusch_handle *h, int n_slots, const void *beam, const void *pilots, void *H_hat,
+                            void *stream) {
+    pusch_status st = check_handle(h, n_slots);
+    if (st != PUSCH_OK) return st;
+    if (n_slots == 0) return ok();
+    if (!beam || !pilots || !H_hat) return fail(PUSCH_ERR_ARG, "pusch_chest_ls: NULL buffer");
+    cudaError_t e = pusch::launch_chest_ls(h->geo, n_slots, (const float2 *)beam, (const float2 *)pilots,
+                                           (float2 *)H_hat, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "channel estimation launch");
+    return ok();
+}
+
+pusch_status pusch_mmse_detect(pusch_handle *h, int n_slots, const void *H_hat, const void *beam, void *x_hat,
+                               uint8_t *bits, uint32_t *status, void *stream) {
+    pusch_status st = check_handle(h, n_slots);
+    if (st != PUSCH_OK) return st;
+    if (!H_hat || !beam || !x_hat || !bits) {
+        if (n_slots == 0) return ok();
+        return fail(PUSCH_ERR_ARG, "pusch_mmse_detect: NULL buffer");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    uint32_t *stat = status ? status : h->status_sink;
+    if ((st = reset_status(stat, s)) != PUSCH_OK) return st;
+    if (n_slots == 0) return ok();
+    cudaError_t e = pusch::launch_mmse(h->geo, n_slots, (const float2 *)H_hat, (const float2 *)beam, (float2 *)x_hat,
+                                       bits, stat, s);
+    if (e != cudaSuccess) return cuda_fail(e, "detection launch");
+    return ok();
+}
+
+pusch_status pusch_slot(pusch_handle *h, int n_slots, const void *time_in, const void *W, const void *pilots,
+                        void *x_hat, uint8_t *bits, uint32_t *status, void *stream) {
+    pusch_status st = check_handle(h, n_slots);
+    if (st != PUSCH_OK) return st;
+    if (n_slots == 0) return ok();
+    if (!time_in || !W || !pilots || !x_hat || !bits) return fail(PUSCH_ERR_ARG, "pusch_slot: NULL buffer");
+    if ((st = pusch_ofdm_fft(h, n_slots, time_in, h->freq, stream)) != PUSCH_OK) return st;
+    if ((st = pusch_beamform(h, n_slots, h->freq, W, h->beam, stream)) != PUSCH_OK) return st;
+    if ((st = pusch_chest_ls(h, n_slots, h->beam, pilots, h->H, stream)) != PUSCH_OK) return st;
+    return pusch_mmse_detect(h, n_slots, h->H, h->beam, x_hat, bits, status, stream);
+}
+
+pusch_status pusch_slot_host(pusch_handle *h, int n_slots, const void *time_in_host, const void *W,
+                             const void *pilots_host, void *x_hat_host, uint8_t *bits_host, uint32_t *status_host,
+                             void *stream) {
+    pusch_status st = check_handle(h, n_slots);
+    if (st != PUSCH_OK) return st;
+    if (n_slots == 0) return ok();
+    if (!time_in_host || !W || !pilots_host || !x_hat_host || !bits_host)
+        return fail(PUSCH_ERR_ARG, "pusch_slot_host: NULL buffer");
+    const pusch::Geometry &g = h->geo;
+    cudaError_t e;
+    if (!h->h_time) {  // staging buffers, sized for max_slots, allocated on first use
+        if ((e = cudaMalloc(&h->h_time, time_bytes(g, h->max_slots))) != cudaSuccess) return cuda_fail(e, "staging");
+        if ((e = cudaMalloc((void **)&h->h_pilots, pilot_bytes(g, h->max_slots))) != cudaSuccess)
+            return cuda_fail(e, "staging");
+        if ((e = cudaMalloc((void **)&h->h_xhat, xhat_count(g, h->max_slots) * sizeof(float2))) != cudaSuccess)
+            return cuda_fail(e, "staging");
+        if ((e = cudaMalloc((void **)&h->h_bits, xhat_count(g, h->max_slots))) != cudaSuccess)
+            return cuda_fail(e, "staging");
+        if ((e = cudaMalloc((void **)&h->h_status, 4 * sizeof(uint32_t))) != cudaSuccess)
+            return cuda_fail(e, "staging");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((e = cudaMemcpyAsync(h->h_time, time_in_host, time_bytes(g, n_slots), cudaMemcpyHostToDevice, s)) !=
+        cudaSuccess)
+        return cuda_fail(e, "input copy");
+    if ((e = cudaMemcpyAsync(h->h_pilots, pilots_host, pilot_bytes(g, n_slots), cudaMemcpyHostToDevice, s)) !=
+        cudaSuccess)
+        return cuda_fail(e, "pilot copy");
+    st = pusch_slot(h, n_slots, h->h_time, W, h->h_pilots, h->h_xhat, h->h_bits, h->h_status, stream);
+    if (st != PUSCH_OK) return st;
+    const size_t nx = xhat_count(g, n_slots);
+    if ((e = cudaMemcpyAsync(x_hat_host, h->h_xhat, nx * sizeof(float2), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return cuda_fail(e, "output copy");
+    if ((e = cudaMemcpyAsync(bits_host, h->h_bits, nx, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return cuda_fail(e, "output copy");
+    if (status_host &&
+        (e = cudaMemcpyAsync(status_host, h->h_status, 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s)) !=
+            cudaSuccess)
+        return cuda_fail(e, "status copy");
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    return ok();
+}
+
+}  // extern "C"

@@ -1,0 +1,285 @@
+// OFDM demodulation: batched forward FFTs of N_F = 64..4096 points with active-bin extraction
+// (Section II: one FFT per antenna and OFDM symbol; Table I "OFDM dem.").
+//
+// Design (GB300): one FFT per group of T = N/E threads, each thread holding E = 8 or 16 complex values in
+// registers. The transform is a Stockham auto-sort sequence of radix-16/8/4 passes, so that
+//   * pass 1 reads its butterfly inputs straight from global memory (element t + T*e, coalesced),
+//   * the last pass leaves bin t + T*e in register e, written straight to global memory in natural order,
+//   * the passes in between exchange through shared memory padded by one slot per 16 (conflict-free).
+// 4096 = 16*16*16 therefore costs one global read, two shared-memory exchanges and one global write.
+// Twiddles come from a table exp(-2 pi i q / N) (computed on the host in double precision).
+#include "internal.cuh"
+
+namespace pusch {
+namespace {
+
+constexpr float kC8 = 0.70710678118654752440f;   // cos(pi/4)
+constexpr float kC16 = 0.92387953251128675613f;  // cos(pi/8)
+constexpr float kS16 = 0.38268343236508977173f;  // sin(pi/8)
+
+// x * exp(-2 pi i q / 16) for a compile-time q in [0, 16)
+template <int Q>
+__device__ __forceinline__ float2 rot16(float2 x) {
+    constexpr int q = Q & 15;
+    if constexpr (q == 0) return x;
+    else if constexpr (q == 4) return make_float2(x.y, -x.x);
+    else if constexpr (q == 8) return make_float2(-x.x, -x.y);
+    else if constexpr (q == 12) return make_float2(-x.y, x.x);
+    else {
+        constexpr float c[16] = {1.f, kC16, kC8, kS16, 0.f, -kS16, -kC8, -kC16,
+                                 -1.f, -kC16, -kC8, -kS16, 0.f, kS16, kC8, kC16};
+        constexpr float s[16] = {0.f, kS16, kC8, kC16, 1.f, kC16, kC8, kS16,
+                                 0.f, -kS16, -kC8, -kC16, -1.f, -kC16, -kC8, -kS16};
+        // multiply by (c - i s)
+        return make_float2(x.x * c[q] + x.y * s[q], x.y * c[q] - x.x * s[q]);
+    }
+}
+
+__device__ __forceinline__ void dft2(float2 &a, float2 &b) {
+    float2 t = a;
+    a = cadd(t, b);
+    b = csub(t, b);
+}
+
+// forward 4-point DFT in place
+__device__ __forceinline__ void dft4(float2 &x0, float2 &x1, float2 &x2, float2 &x3) {
+    float2 a = cadd(x0, x2), b = csub(x0, x2), c = cadd(x1, x3), d = csub(x1, x3);
+    x0 = cadd(a, c);
+    x2 = csub(a, c);
+    x1 = make_float2(b.x + d.y, b.y - d.x);  // b - i d
+    x3 = make_float2(b.x - d.y, b.y + d.x);  // b + i d
+}
+
+// Forward R-point DFT of x[0..R) in natural order, R in {2, 4, 8, 16}.
+// R = 8 and 16 are split as R = 4 * (R/4): n = (R/4)*n1 + n2, k = k1 + 4*k2.
+template <int R>
+__device__ __forceinline__ void dft(float2 (&x)[R]) {
+    if constexpr (R == 2) {
+        dft2(x[0], x[1]);
+    } else if constexpr (R == 4) {
+        dft4(x[0], x[1], x[2], x[3]);
+    } else if constexpr (R == 8) {
+        // inner DFT-4 over n1 for n2 = 0, 1 (stride-2 samples)
+        dft4(x[0], x[2], x[4], x[6]);
+        dft4(x[1], x[3], x[5], x[7]);
+        float2 a1 = rot16<2>(x[3]), a2 = rot16<4>(x[5]), a3 = rot16<6>(x[7]);
+        float2 y[8];
+        y[0] = cadd(x[0], x[1]); y[4] = csub(x[0], x[1]);
+        y[1] = cadd(x[2], a1);   y[5] = csub(x[2], a1);
+        y[2] = cadd(x[4], a2);   y[6] = csub(x[4], a2);
+        y[3] = cadd(x[6], a3);   y[7] = csub(x[6], a3);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x[i] = y[i];
+    } else if constexpr (R == 16) {
+        // A[n2][k1] = DFT4_{n1}(x[4 n1 + n2]) stored back at x[4 k1 + n2]
+        dft4(x[0], x[4], x[8], x[12]);
+        dft4(x[1], x[5], x[9], x[13]);
+        dft4(x[2], x[6], x[10], x[14]);
+        dft4(x[3], x[7], x[11], x[15]);
+        // twiddle A[n2][k1] by w16^(n2 k1)
+        x[5] = rot16<1>(x[5]);  x[9] = rot16<2>(x[9]);   x[13] = rot16<3>(x[13]);
+        x[6] = rot16<2>(x[6]);  x[10] = rot16<4>(x[10]); x[14] = rot16<6>(x[14]);
+        x[7] = rot16<3>(x[7]);  x[11] = rot16<6>(x[11]); x[15] = rot16<9>(x[15]);
+        // out[k1 + 4 k2] = DFT4_{n2}(A[n2][k1]); A[.][k1] sits at x[4 k1 .. 4 k1 + 3]
+        dft4(x[0], x[1], x[2], x[3]);
+        dft4(x[4], x[5], x[6], x[7]);
+        dft4(x[8], x[9], x[10], x[11]);
+        dft4(x[12], x[13], x[14], x[15]);
+        float2 y[16];
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+            for (int k2 = 0; k2 < 4; ++k2) y[k1 + 4 * k2] = x[4 * k1 + k2];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) x[i] = y[i];
+    }
+}
+
+__device__ __forceinline__ int pad16(int p) { return p + (p >> 4); }
+
+// One Stockham radix-R pass over the E register values of thread t (Ls = product of earlier radices).
+// Butterfly j = t + u*T takes inputs j + m*N/R (register u + m*E/R) and twiddles input m by
+// exp(-2 pi i (j mod Ls) m / (Ls R)).
+template <int N, int E, int R, int LS>
+__device__ __forceinline__ void fft_pass(float2 (&v)[E], const float2 *__restrict__ tw, int t) {
+    constexpr int T = N / E;
+    constexpr int NB = E / R;
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+        const int j = t + u * T;
+        const int k = j & (LS - 1);
+        float2 x[R];
+#pragma unroll
+        for (int m = 0; m < R; ++m) x[m] = v[u + m * NB];
+        if constexpr (LS > 1) {
+#pragma unroll
+            for (int m = 1; m < R; ++m) x[m] = cmul(x[m], __ldg(&tw[(k * m) * (N / (LS * R))]));
+        }
+        dft<R>(x);
+#pragma unroll
+        for (int m = 0; m < R; ++m) v[u + m * NB] = x[m];
+    }
+}
+
+// Stockham output placement of a non-final pass, then gather of the next pass's inputs t + T*e.
+template <int N, int E, int R, int LS>
+__device__ __forceinline__ void fft_exchange(float2 (&v)[E], float2 *sm, int t) {
+    constexpr int T = N / E;
+    constexpr int NB = E / R;
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+        const int j = t + u * T;
+        const int k = j & (LS - 1);
+        const int base = (j - k) * R + k;
+#pragma unroll
+        for (int m = 0; m < R; ++m) sm[pad16(base + m * LS)] = v[u + m * NB];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = sm[pad16(t + T * e)];
+}
+
+template <int N, int E, int LS, int R, int... Rest>
+__device__ __forceinline__ void fft_run(float2 (&v)[E], float2 *sm, const float2 *__restrict__ tw, int t) {
+    fft_pass<N, E, R, LS>(v, tw, t);
+    if constexpr (sizeof...(Rest) > 0) {
+        fft_exchange<N, E, R, LS>(v, sm, t);
+        fft_run<N, E, LS * R, Rest...>(v, sm, tw, t);
+    }
+}
+
+template <int N> struct Plan;
+template <> struct Plan<4096> { static constexpr int E = 16; };
+template <> struct Plan<2048> { static constexpr int E = 16; };
+template <> struct Plan<1024> { static constexpr int E = 16; };
+template <> struct Plan<512> { static constexpr int E = 8; };
+template <> struct Plan<256> { static constexpr int E = 16; };
+template <> struct Plan<128> { static constexpr int E = 16; };
+template <> struct Plan<64> { static constexpr int E = 8; };
+
+template <int N>
+__device__ __forceinline__ void fft_full(float2 (&v)[Plan<N>::E], float2 *sm, const float2 *__restrict__ tw, int t) {
+    constexpr int E = Plan<N>::E;
+    if constexpr (N == 4096) fft_run<N, E, 1, 16, 16, 16>(v, sm, tw, t);
+    else if constexpr (N == 2048) fft_run<N, E, 1, 16, 16, 8>(v, sm, tw, t);
+    else if constexpr (N == 1024) fft_run<N, E, 1, 16, 16, 4>(v, sm, tw, t);
+    else if constexpr (N == 512) fft_run<N, E, 1, 8, 8, 8>(v, sm, tw, t);
+    else if constexpr (N == 256) fft_run<N, E, 1, 16, 16>(v, sm, tw, t);
+    else if constexpr (N == 128) fft_run<N, E, 1, 16, 8>(v, sm, tw, t);
+    else if constexpr (N == 64) fft_run<N, E, 1, 8, 8>(v, sm, tw, t);
+}
+
+__device__ __forceinline__ float2 load_sample(const float2 *p) { return __ldg(p); }
+__device__ __forceinline__ float2 load_sample(const __half2 *p) { return __half22float2(__ldg(p)); }
+
+constexpr int kFftThreads = 256;
+
+template <int N>
+constexpr int ffts_per_cta() {
+    return (kFftThreads / (N / Plan<N>::E)) > 0 ? kFftThreads / (N / Plan<N>::E) : 1;
+}
+
+// rows = n_slots * n_sym * n_rx transforms. out16 = false: c64 [rows][n_sc]; out16 = true: binary16
+// [rows][2][pitch] (re plane, im plane; pad elements zeroed).
+template <int N, typename TIn, bool OUT16>
+__global__ void __launch_bounds__(kFftThreads)
+fft_kernel(const TIn *__restrict__ in, void *__restrict__ out, const float2 *__restrict__ tw, long long rows,
+           int n_sc, int pitch) {
+    constexpr int E = Plan<N>::E;
+    constexpr int T = N / E;
+    constexpr int F = ffts_per_cta<N>();
+    extern __shared__ float2 smem[];
+    const int f = threadIdx.x / T;
+    const int t = threadIdx.x - f * T;
+    const long long row = (long long)blockIdx.x * F + f;
+    const bool valid = (f < F) && (row < rows);
+    float2 *sm = smem + f * (N + N / 16);
+
+    float2 v[E];
+    if (valid) {
+        const TIn *src = in + row * N;
+#pragma unroll
+        for (int e = 0; e < E; ++e) v[e] = load_sample(src + t + T * e);
+    } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) v[e] = make_float2(0.f, 0.f);
+    }
+    fft_full<N>(v, sm, tw, t);
+    if (!valid) return;
+
+    const int h = n_sc >> 1;
+    if constexpr (!OUT16) {
+        float2 *dst = static_cast<float2 *>(out) + row * n_sc;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            int a = t + T * e + h;
+            if (a >= N) a -= N;
+            if (a < n_sc) dst[a] = v[e];
+        }
+    } else {
+        __half *re = static_cast<__half *>(out) + row * 2 * (long long)pitch;
+        __half *im = re + pitch;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            int a = t + T * e + h;
+            if (a >= N) a -= N;
+            if (a < n_sc) {
+                re[a] = __float2half_rn(v[e].x);
+                im[a] = __float2half_rn(v[e].y);
+            }
+        }
+        for (int a = n_sc + t; a < pitch; a += T) {
+            re[a] = __float2half_rn(0.f);
+            im[a] = __float2half_rn(0.f);
+        }
+    }
+}
+
+template <int N, typename TIn, bool OUT16>
+cudaError_t launch_n(long long rows, const void *in, void *out, const float2 *tw, int n_sc, int pitch,
+                     cudaStream_t st) {
+    constexpr int F = ffts_per_cta<N>();
+    const size_t smem = (size_t)F * (N + N / 16) * sizeof(float2);
+    const long long grid = (rows + F - 1) / F;
+    if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    auto k = fft_kernel<N, TIn, OUT16>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k<<<(unsigned)grid, kFftThreads, smem, st>>>(static_cast<const TIn *>(in), out, tw, rows, n_sc, pitch);
+    return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t launch_typed(const Geometry &g, long long rows, const void *in, void *out, const float2 *tw,
+                         cudaStream_t st) {
+    const bool out16 = g.form == PUSCH_FORM_MIXED;
+    if (g.in_fp16) {
+        return out16 ? launch_n<N, __half2, true>(rows, in, out, tw, g.n_sc, g.sc_pitch, st)
+                     : launch_n<N, __half2, false>(rows, in, out, tw, g.n_sc, g.sc_pitch, st);
+    }
+    return out16 ? launch_n<N, float2, true>(rows, in, out, tw, g.n_sc, g.sc_pitch, st)
+                 : launch_n<N, float2, false>(rows, in, out, tw, g.n_sc, g.sc_pitch, st);
+}
+
+}  // namespace
+
+cudaError_t launch_fft(const Geometry &g, int n_slots, const void *time_in, void *freq_out, const float2 *twiddle,
+                       cudaStream_t st) {
+    const long long rows = (long long)n_slots * g.n_sym * g.n_rx;
+    if (rows == 0) return cudaSuccess;
+    switch (g.n_fft) {
+        case 4096: return launch_typed<4096>(g, rows, time_in, freq_out, twiddle, st);
+        case 2048: return launch_typed<2048>(g, rows, time_in, freq_out, twiddle, st);
+        case 1024: return launch_typed<1024>(g, rows, time_in, freq_out, twiddle, st);
+        case 512: return launch_typed<512>(g, rows, time_in, freq_out, twiddle, st);
+        case 256: return launch_typed<256>(g, rows, time_in, freq_out, twiddle, st);
+        case 128: return launch_typed<128>(g, rows, time_in, freq_out, twiddle, st);
+        case 64: return launch_typed<64>(g, rows, time_in, freq_out, twiddle, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace pusch

@@ -1,0 +1,70 @@
+// Internal declarations shared by the CUDA translation units of libpusch (not part of the C ABI).
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/pusch.h"
+
+namespace pusch {
+
+// ------------------------------------------------------------------------------------ complex helpers
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// conj(a) * b
+__host__ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+    return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// acc += a * b
+__device__ __forceinline__ void cfma(float2 &acc, float2 a, float2 b) {
+    acc.x = fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x));
+    acc.y = fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y));
+}
+// acc += conj(a) * b
+__device__ __forceinline__ void cfmac(float2 &acc, float2 a, float2 b) {
+    acc.x = fmaf(a.x, b.x, fmaf(a.y, b.y, acc.x));
+    acc.y = fmaf(a.x, b.y, fmaf(-a.y, b.x, acc.y));
+}
+// acc -= a * b
+__device__ __forceinline__ void cfms(float2 &acc, float2 a, float2 b) {
+    acc.x = fmaf(-a.x, b.x, fmaf(a.y, b.y, acc.x));
+    acc.y = fmaf(-a.x, b.y, fmaf(-a.y, b.x, acc.y));
+}
+
+// ---------------------------------------------------------------------------------- derived geometry
+struct Geometry {
+    int n_rx, n_fft, n_sc, n_beams, n_layers, comb, qam_bits, in_fp16, form, n_sym;
+    int dmrs0, dmrs1;
+    int n_data;
+    int sc_pitch;                 // mixed-form FFT output row pitch (elements)
+    float noise_var, loading;
+    int port[32];
+    int data_sym[16];             // data symbol indices in increasing order
+};
+
+Geometry make_geometry(const pusch_cell_cfg &c);
+
+// ------------------------------------------------------------------------------------------ launchers
+// Each returns cudaSuccess or the launch error. All pointers are device pointers.
+cudaError_t launch_fft(const Geometry &g, int n_slots, const void *time_in, void *freq_out, const float2 *twiddle,
+                       cudaStream_t st);
+cudaError_t launch_beamform_fp32(const Geometry &g, int n_slots, const float2 *freq, const float2 *W, float2 *beam,
+                                 cudaStream_t st);
+cudaError_t launch_chest_ls(const Geometry &g, int n_slots, const float2 *beam, const float2 *pilots, float2 *H,
+                            cudaStream_t st);
+cudaError_t launch_mmse(const Geometry &g, int n_slots, const float2 *H, const float2 *beam, float2 *x_hat,
+                        uint8_t *bits, uint32_t *status, cudaStream_t st);
+
+// Mixed form: beam-matrix operand preparation and the tcgen05 beamforming GEMM.
+size_t bf_tc_operand_bytes(const Geometry &g);
+cudaError_t launch_bf_tc_prepare(const Geometry &g, const float2 *W, void *operand, cudaStream_t st);
+cudaError_t launch_beamform_tc(const Geometry &g, int n_slots, const __half *freq16, const void *operand,
+                               float2 *beam, cudaStream_t st);
+bool bf_tc_supported(const Geometry &g);
+
+}  // namespace pusch

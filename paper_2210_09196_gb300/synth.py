@@ -187,7 +187,7 @@ def make_slot(cfg: CellConfig, slot_index: int = 0, seed: int | None = None) -> 
     for j, s in enumerate(DATA_SYMBOLS):
         t[:, s, :] = x[:, j, :]
 
-    X = np.einsum("arl,lsa->sra", Hant, t)                                # [S, R, N_SC]
+    X = np.matmul(Hant, np.ascontiguousarray(t.transpose(2, 0, 1))).transpose(2, 1, 0)   # [S, R, N_SC]
     noise = (rng.standard_normal(X.shape) + 1j * rng.standard_normal(X.shape)) * np.sqrt(noise_var / 2.0)
     X = X + noise
 
@@ -199,7 +199,7 @@ def make_slot(cfg: CellConfig, slot_index: int = 0, seed: int | None = None) -> 
     else:
         time_in = time.astype(np.complex64)
 
-    H_beam = np.einsum("rb,arl->alb", W.astype(np.complex128).conj(), Hant)   # [N_SC, L, B]
+    H_beam = np.matmul(W.astype(np.complex128).conj().T, Hant).transpose(0, 2, 1)   # [N_SC, L, B]
     return Slot(cfg=cfg, time_in=time_in, W=W, pilots=pilots, ports=ports, noise_var=noise_var,
                 H_beam=H_beam, x=x, bits=pack_bits(bits))
 

@@ -1,0 +1,83 @@
+"""CPU-side checks of the C ABI: the library builds and loads, exports every symbol include/pusch.h
+declares, and rejects invalid configurations on the host (these paths make no CUDA call)."""
+import ctypes
+import re
+from pathlib import Path
+
+import pytest
+
+ROOT = Path(__file__).resolve().parents[1]
+
+
+@pytest.fixture(scope="module")
+def B():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2210_09196_gb300 import binding
+    return binding
+
+
+def declared_functions():
+    text = (ROOT / "include" / "pusch.h").read_text()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(pusch_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_stage_and_chain_entry_points():
+    names = declared_functions()
+    for n in ("pusch_ofdm_fft", "pusch_beamform", "pusch_chest_ls", "pusch_mmse_detect", "pusch_slot"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(B):
+    lib = ctypes.CDLL(str(B.LIB_PATH))
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    assert set(declared_functions()) == set(B.EXPORTS)
+
+
+def test_version_and_pitch(B):
+    assert "sm_103a" in B.pusch_version()
+    cfg = B.make_cfg(n_rx=64, n_fft=4096, n_sc=3276, n_beams=32, n_layers=16)
+    assert B.pusch_sc_pitch(cfg) == 3280
+
+
+def _good(**kw):
+    from paper_2210_09196_gb300 import binding as B
+    base = dict(n_rx=16, n_fft=512, n_sc=300, n_beams=16, n_layers=4, qam_bits=2, noise_var=0.01)
+    base.update(kw)
+    return B.make_cfg(**base)
+
+
+@pytest.mark.parametrize("bad,code", [
+    (dict(n_fft=500), -5), (dict(n_fft=8192), -5), (dict(n_sc=0), -1), (dict(n_sc=600), -1),
+    (dict(n_beams=65), -5), (dict(n_layers=17), -1), (dict(n_layers=33, n_beams=64), -1),
+    (dict(qam_bits=3), -1), (dict(noise_var=-1.0), -1), (dict(noise_var=float("nan")), -1),
+    (dict(comb=0), -1), (dict(ports=[0, 1, 2, 4]), -1), (dict(dmrs_sym=(2, 2)), -1), (dict(dmrs_sym=(2, 14)), -1),
+    (dict(n_sym=2), -1), (dict(form=7), -1), (dict(n_rx=0), -5),
+])
+def test_invalid_configs_are_rejected_on_the_host(B, bad, code):
+    cfg = _good(**bad)
+    out = ctypes.c_size_t()
+    rc = B.lib().pusch_workspace_size(ctypes.byref(cfg), 1, ctypes.byref(out))
+    assert rc == code
+    assert B.pusch_last_error()
+    h = ctypes.c_void_p(123)
+    assert B.lib().pusch_create(ctypes.byref(h), ctypes.byref(cfg), 1) == code
+    assert h.value is None
+
+
+def test_workspace_size(B):
+    cfg = _good()
+    n = B.pusch_workspace_size(cfg, 2)
+    per_slot = 14 * 16 * 300 * 8 + 14 * 300 * 16 * 8 + 300 * 4 * 16 * 8
+    assert n >= 2 * per_slot and n < 2 * per_slot + 64 * 1024
+
+
+def test_null_handle_and_bad_batch_rejected(B):
+    L = B.lib()
+    assert L.pusch_ofdm_fft(None, 1, 1, 1, None) == B.PUSCH_ERR_ARG
+    assert L.pusch_slot(None, 1, 1, 1, 1, 1, 1, None, None) == B.PUSCH_ERR_ARG
+    assert L.pusch_destroy(None) == B.PUSCH_OK
+    with pytest.raises(B.PuschError):
+        B.pusch_ofdm_fft(None, 1, 1, 1, stream=0)
