@@ -15,7 +15,7 @@ struct pusch_handle {
     int max_slots = 0;
     int device = 0;
     float2 *twiddle = nullptr;      // exp(-2 pi i q / n_fft), q < n_fft
-    void *bf_operand = nullptr;     // mixed form: beam-matrix tensor-core operand
+    uint32_t *kernel_err = nullptr;   // bounded-wait expiry flags of the tensor-core kernel
     void *freq = nullptr;           // workspace: FFT output
     float2 *beam = nullptr;         // workspace: beamformed grid
     float2 *H = nullptr;            // workspace: channel estimate
@@ -106,7 +106,6 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 size_t workspace_bytes(const pusch::Geometry &g, int max_slots) {
     size_t b = align256(g.n_fft * sizeof(float2));
-    if (g.form == PUSCH_FORM_MIXED) b += align256(pusch::bf_tc_operand_bytes(g));
     b += align256(freq_bytes(g, max_slots)) + align256(beam_bytes(g, max_slots)) + align256(H_bytes(g, max_slots));
     return b;
 }
@@ -135,6 +134,8 @@ pusch_status reset_status(uint32_t *status, cudaStream_t st) {
 }  // namespace
 
 namespace pusch {
+
+void set_last_error(const char *msg) { snprintf(g_err, sizeof g_err, "%s", msg); }
 
 Geometry make_geometry(const pusch_cell_cfg &c) {
     Geometry g;
@@ -204,9 +205,8 @@ pusch_status pusch_create(pusch_handle **out, const pusch_cell_cfg *cfg, int max
     if ((e = cudaMalloc(&h->twiddle, g.n_fft * sizeof(float2))) != cudaSuccess) goto cuda_error;
     if ((e = cudaMemcpy(h->twiddle, tw.data(), g.n_fft * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess)
         goto cuda_error;
-    if (g.form == PUSCH_FORM_MIXED) {
-        if ((e = cudaMalloc(&h->bf_operand, pusch::bf_tc_operand_bytes(g))) != cudaSuccess) goto cuda_error;
-    }
+    if ((e = cudaMalloc((void **)&h->kernel_err, 16)) != cudaSuccess) goto cuda_error;
+    if ((e = cudaMemset(h->kernel_err, 0, 16)) != cudaSuccess) goto cuda_error;
     if ((e = cudaMalloc(&h->freq, freq_bytes(g, max_slots))) != cudaSuccess) goto cuda_error;
     if ((e = cudaMalloc((void **)&h->beam, beam_bytes(g, max_slots))) != cudaSuccess) goto cuda_error;
     if ((e = cudaMalloc((void **)&h->H, H_bytes(g, max_slots))) != cudaSuccess) goto cuda_error;
@@ -222,7 +222,7 @@ pusch_status pusch_destroy(pusch_handle *h) {
     if (!h) return ok();
     cudaDeviceSynchronize();
     cudaFree(h->twiddle);
-    cudaFree(h->bf_operand);
+    cudaFree(h->kernel_err);
     cudaFree(h->freq);
     cudaFree(h->beam);
     cudaFree(h->H);
@@ -255,9 +255,8 @@ pusch_status pusch_beamform(pusch_handle *h, int n_slots, const void *freq_in, c
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e;
     if (h->geo.form == PUSCH_FORM_MIXED) {
-        if ((e = pusch::launch_bf_tc_prepare(h->geo, (const float2 *)W, h->bf_operand, s)) != cudaSuccess)
-            return cuda_fail(e, "beam operand launch");
-        e = pusch::launch_beamform_tc(h->geo, n_slots, (const __half *)freq_in, h->bf_operand, (float2 *)beam_out, s);
+        e = pusch::launch_beamform_tc(h->geo, n_slots, (const __half *)freq_in, (const float2 *)W, (float2 *)beam_out,
+                                      h->kernel_err, s);
     } else {
         e = pusch::launch_beamform_fp32(h->geo, n_slots, (const float2 *)freq_in, (const float2 *)W,
                                         (float2 *)beam_out, s);

@@ -187,12 +187,12 @@ beamform_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g, const flo
     if (tid == 0)
         for (int s = 0; s < kStages && s < n_my; ++s) issue(s, s);
 
-    const uint64_t deadline = globaltimer() + kWaitNs;
     long long issued = n_my < kStages ? n_my : kStages;
     long long i = 0;
     for (; i < n_my; ++i) {
         const int s = (int)(i % kStages);
         const uint32_t ph = (uint32_t)((i / kStages) & 1);
+        const uint64_t deadline = globaltimer() + kWaitNs;
         int bad = 0;
         if (tid == 0) {
             if (mbar_wait(sBar + 8 * s, ph, deadline)) {
@@ -229,12 +229,14 @@ beamform_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g, const flo
         for (int c0 = 0; c0 < N; c0 += 32) {
             uint32_t r[32];
             tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+            const int ncol = N - c0 < 32 ? N - c0 : 32;  // N is a multiple of 16: 16 or 32 columns here
             if (a < g.n_sc) {
 #pragma unroll
                 for (int j = 0; j < 32; j += 4)
-                    *reinterpret_cast<float4 *>(dst + c0 + j) =
-                        make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]), __uint_as_float(r[j + 2]),
-                                    __uint_as_float(r[j + 3]));
+                    if (j < ncol)
+                        *reinterpret_cast<float4 *>(dst + c0 + j) =
+                            make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]), __uint_as_float(r[j + 2]),
+                                        __uint_as_float(r[j + 3]));
             }
         }
         fence_before_sync();
@@ -281,14 +283,8 @@ bool bf_tc_supported(const Geometry &g) {
            g.n_beams <= 64 && tc_smem_bytes(g) <= 227 * 1024;
 }
 
-size_t bf_tc_operand_bytes(const Geometry &) { return 16; }  // device word for the kernel's timeout flag
-
-cudaError_t launch_bf_tc_prepare(const Geometry &, const float2 *, void *operand, cudaStream_t st) {
-    return cudaMemsetAsync(operand, 0, 16, st);
-}
-
-cudaError_t launch_beamform_tc(const Geometry &g, int n_slots, const __half *freq16, const void *operand,
-                               float2 *beam, cudaStream_t st) {
+cudaError_t launch_beamform_tc(const Geometry &g, int n_slots, const __half *freq16, const float2 *W, float2 *beam,
+                               uint32_t *err_word, cudaStream_t st) {
     if (n_slots == 0) return cudaSuccess;
     if (!bf_tc_supported(g)) return cudaErrorNotSupported;
     if (reinterpret_cast<uintptr_t>(freq16) % 16 != 0 || reinterpret_cast<uintptr_t>(beam) % 16 != 0)
@@ -323,11 +319,7 @@ cudaError_t launch_beamform_tc(const Geometry &g, int n_slots, const __half *fre
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     long long grid = 2LL * sms;
     if (grid > a.total_tiles) grid = a.total_tiles;
-    beamform_tc_kernel<<<(unsigned)grid, kTcThreads, smem, st>>>(map, a, reinterpret_cast<const float2 *>(
-                                                                         reinterpret_cast<const void *>(nullptr)) == nullptr
-                                                                     ? nullptr
-                                                                     : nullptr,
-                                                                 beam, (uint32_t *)operand);
+    beamform_tc_kernel<<<(unsigned)grid, kTcThreads, smem, st>>>(map, a, W, beam, err_word);
     return cudaGetLastError();
 }
 

@@ -49,6 +49,9 @@ struct Geometry {
 
 Geometry make_geometry(const pusch_cell_cfg &c);
 
+// Sets the thread's pusch_last_error() message.
+void set_last_error(const char *msg);
+
 // ------------------------------------------------------------------------------------------ launchers
 // Each returns cudaSuccess or the launch error. All pointers are device pointers.
 cudaError_t launch_fft(const Geometry &g, int n_slots, const void *time_in, void *freq_out, const float2 *twiddle,
@@ -60,11 +63,10 @@ cudaError_t launch_chest_ls(const Geometry &g, int n_slots, const float2 *beam, 
 cudaError_t launch_mmse(const Geometry &g, int n_slots, const float2 *H, const float2 *beam, float2 *x_hat,
                         uint8_t *bits, uint32_t *status, cudaStream_t st);
 
-// Mixed form: beam-matrix operand preparation and the tcgen05 beamforming GEMM.
-size_t bf_tc_operand_bytes(const Geometry &g);
-cudaError_t launch_bf_tc_prepare(const Geometry &g, const float2 *W, void *operand, cudaStream_t st);
-cudaError_t launch_beamform_tc(const Geometry &g, int n_slots, const __half *freq16, const void *operand,
-                               float2 *beam, cudaStream_t st);
+// Mixed form: the tcgen05 beamforming GEMM. err_word (device, one uint32) gets bit 0 set if a bounded
+// wait of the kernel expired.
+cudaError_t launch_beamform_tc(const Geometry &g, int n_slots, const __half *freq16, const float2 *W, float2 *beam,
+                               uint32_t *err_word, cudaStream_t st);
 bool bf_tc_supported(const Geometry &g);
 
 }  // namespace pusch

@@ -1,0 +1,119 @@
+"""GPU parity of the mixed form (FFT output stored as FP16, beamforming on tcgen05 tensor cores with FP16
+operands and FP32 accumulation) against the FP64 oracle.
+
+* FFT: the FP16 planes equal the oracle's spectrum within FP16 rounding (norm-relative <= 1e-3), pads 0.
+* Beamforming, quantisation-exact: the oracle is fed the very FP16 values the tensor cores read (the GPU's
+  FFT planes and W rounded to FP16), so only FP32 accumulation order differs: norm-relative <= 1e-5.
+* Whole chain at the deployment size in the benchmark's batch: EVM <= -40 dB against the FP64 oracle
+  chain at 30 dB SNR and identical hard decisions except on tie-ambiguous symbols.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2210_09196_gb300 import binding as B
+from paper_2210_09196_gb300 import host, synth
+
+pytestmark = pytest.mark.gpu
+
+BENCH_SLOTS = 16  # the batch bench.py times
+
+
+def nrel(a, b):
+    a = np.asarray(a, dtype=np.complex128)
+    b = np.asarray(b, dtype=np.complex128)
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+def evm_db(x, ref):
+    return 10 * np.log10(np.sum(np.abs(x - ref) ** 2) / np.sum(np.abs(ref) ** 2))
+
+
+def planes_to_c128(freq16, n_sc):
+    f = freq16.detach().cpu().numpy().astype(np.float64)
+    return f[..., 0, :n_sc] + 1j * f[..., 1, :n_sc]
+
+
+def w_fp16(W):
+    return W.real.astype(np.float16).astype(np.float64) + 1j * W.imag.astype(np.float16).astype(np.float64)
+
+
+MIXED_SHAPES = [
+    dict(n_rx=8, n_fft=128, n_sc=100, n_beams=8, n_layers=2, qam_bits=2),
+    dict(n_rx=16, n_fft=512, n_sc=300, n_beams=16, n_layers=4, qam_bits=2),
+    dict(n_rx=32, n_fft=1024, n_sc=1000, n_beams=24, n_layers=8, qam_bits=4),
+    dict(n_rx=64, n_fft=4096, n_sc=3276, n_beams=32, n_layers=16, qam_bits=4),
+    dict(n_rx=128, n_fft=2048, n_sc=1638, n_beams=64, n_layers=32, qam_bits=4),
+]
+
+
+@pytest.mark.parametrize("shape", MIXED_SHAPES, ids=lambda d: f"R{d['n_rx']}sc{d['n_sc']}B{d['n_beams']}")
+def test_mixed_fft_and_tensor_core_beamforming(orc, shape):
+    cell = synth.CellConfig("m", snr_db=30.0, channel="pdp", beam="dft", in_fp16=True, seed=21, **shape)
+    slots = synth.make_slots(cell, 3)
+    rx = host.Receiver(host.cfg_for(cell, B.PUSCH_FORM_MIXED), max_slots=3)
+    freq = rx.ofdm_fft(host.time_tensor(slots))
+    beam = rx.beamform(freq, host.beam_tensor(slots[0].W))
+    torch.cuda.synchronize()
+    fr = freq.detach().cpu().numpy()
+    assert np.all(fr[..., cell.n_sc:] == 0)                           # pad elements are zero
+    for i, s in enumerate(slots):
+        f_orc = orc.ofdm_demod(s.time_as_complex128(), cell.n_sc)
+        fg = planes_to_c128(freq[i], cell.n_sc)
+        assert nrel(fg, f_orc) < 1e-3
+        b_orc = orc.beamform(fg, w_fp16(s.W))                           # quantisation-exact reference
+        assert nrel(beam[i].cpu().numpy(), b_orc) < 1e-5
+    rx.close()
+
+
+def test_mixed_beamform_all_tiles_written(orc):
+    """Every (row, subcarrier, beam) of the output is written, none outside: prefill with NaN sentinels."""
+    cell = synth.CellConfig("m", n_rx=16, n_fft=512, n_sc=260, n_beams=16, n_layers=4, qam_bits=2, snr_db=30.0,
+                            channel="pdp", beam="dft", in_fp16=False, seed=5)
+    slots = synth.make_slots(cell, 2)
+    rx = host.Receiver(host.cfg_for(cell, B.PUSCH_FORM_MIXED), max_slots=2)
+    freq = rx.ofdm_fft(host.time_tensor(slots))
+    out = torch.full((2 * 14 * cell.n_sc * cell.n_beams + 64,), float("nan"), dtype=torch.complex64, device="cuda")
+    beam = out[: 2 * 14 * cell.n_sc * cell.n_beams].view(2, 14, cell.n_sc, cell.n_beams)
+    rx.beamform(freq, host.beam_tensor(slots[0].W), beam)
+    torch.cuda.synchronize()
+    o = out.cpu().numpy()
+    assert np.all(np.isfinite(o[: beam.numel()]))
+    assert np.all(np.isnan(o[beam.numel():].real))
+    rx.close()
+
+
+@pytest.fixture(scope="module")
+def deploy_slots():
+    return synth.make_slots(synth.DEPLOY, BENCH_SLOTS)
+
+
+@pytest.mark.parametrize("form", [B.PUSCH_FORM_MIXED, B.PUSCH_FORM_FP32])
+def test_deploy_chain_at_bench_batch(orc, deploy_slots, form):
+    cell = synth.DEPLOY
+    n = len(deploy_slots)
+    rx = host.Receiver(host.cfg_for(cell, form), max_slots=n)
+    x, b, st = rx.slot(host.time_tensor(deploy_slots), host.beam_tensor(deploy_slots[0].W),
+                       host.pilot_tensor(deploy_slots))
+    torch.cuda.synchronize()
+    assert list(st.cpu().numpy()) == [0, 0, -1, 0]
+    for i in (0, n - 1):
+        s = deploy_slots[i]
+        xo, bo, fails = orc.run_slot(s)
+        assert fails == 0
+        xg = x[i].cpu().numpy().astype(np.complex128)
+        e = evm_db(xg, xo)
+        bits = b[i].cpu().numpy()
+        mism = bits != bo
+        # mismatches only where the oracle symbol is within 4x the max error of a decision threshold
+        err = np.max(np.abs(xg - xo))
+        t = 2 / np.sqrt(10)
+        near = np.minimum(np.minimum(np.abs(xo.real), np.abs(np.abs(xo.real) - t)),
+                          np.minimum(np.abs(xo.imag), np.abs(np.abs(xo.imag) - t))) <= 4 * err
+        assert not np.any(mism & ~near)
+        if form == B.PUSCH_FORM_MIXED:
+            assert e <= -40.0, e
+        else:
+            assert e <= -80.0, e                                            # FP32 end to end
+            assert nrel(xg, xo) < 1e-4
+    rx.close()
