@@ -159,6 +159,31 @@ pusch_status pusch_slot_host(pusch_handle *h, int n_slots, const void *time_in_h
                              const void *pilots_host, void *x_hat_host, uint8_t *bits_host, uint32_t *status_host,
                              void *stream);
 
+/*
+ * pusch_slot for callers that cannot allocate device memory.
+ * The paper has no counterpart of this entry point; it exists for integration. Some callers must not call
+ * cudaMalloc: a real-time receiver thread, where the CUDA allocator can synchronise the device and take
+ * an unbounded time within a slot deadline; a plug-in whose host framework owns all device memory and
+ * hands the library only its input and output buffers; a stateless callback that cannot create and
+ * destroy a handle. pusch_slot_noalloc runs the same chain as pusch_slot without a handle and without
+ * allocating: its intermediates, the FFT twiddle table and its spare status words live in one static
+ * device buffer of PUSCH_NOALLOC_SCRATCH_BYTES that is part of the library (every GPU that loads the
+ * library holds it until the process exits). It calls no cudaMalloc or cudaFree.
+ *   - The caller still passes every input and output buffer, with the layouts of pusch_slot.
+ *   - A call whose cell and n_slots need more than PUSCH_NOALLOC_SCRATCH_BYTES of intermediates returns
+ *     PUSCH_ERR_UNSUPPORTED and launches nothing; pusch_last_error() says how many bytes were needed.
+ *     (One 16-antenna, 512-point, 300-subcarrier slot needs about 1.3 MB; a 64-antenna, 4096-point,
+ *     3276-subcarrier slot does not fit.)
+ *   - The first call on a device looks up the buffer's device address (cudaGetSymbolAddress), which may
+ *     load the library's device code; make that first call before any stream capture.
+ *   - All calls share the one buffer, which keeps the last call's contents; each call writes everything
+ *     it reads from it. Calls that overlap on the GPU (other streams, other host threads) race on it:
+ *     serialise them.
+ */
+#define PUSCH_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+pusch_status pusch_slot_noalloc(const pusch_cell_cfg *cfg, int n_slots, const void *time_in, const void *W,
+                                const void *pilots, void *x_hat, uint8_t *bits, uint32_t *status, void *stream);
+
 /* Message of the last non-OK status returned on this thread ("" if none). */
 const char *pusch_last_error(void);
 

@@ -33,6 +33,7 @@ PUSCH_STATUS_NONFINITE = 0x2
 EXPORTS = (
     "pusch_create", "pusch_destroy", "pusch_workspace_size", "pusch_sc_pitch", "pusch_ofdm_fft", "pusch_beamform",
     "pusch_chest_ls", "pusch_mmse_detect", "pusch_slot", "pusch_slot_host", "pusch_last_error", "pusch_version",
+    "pusch_slot_noalloc",
 )
 
 
@@ -86,6 +87,7 @@ def lib():
             "pusch_mmse_detect": (I, [P, I, P, P, P, P, P, P]),
             "pusch_slot": (I, [P, I, P, P, P, P, P, P, P]),
             "pusch_slot_host": (I, [P, I, P, P, P, P, P, P, P]),
+            "pusch_slot_noalloc": (I, [ctypes.POINTER(pusch_cell_cfg), I, P, P, P, P, P, P, P]),
             "pusch_last_error": (ctypes.c_char_p, []),
             "pusch_version": (ctypes.c_char_p, []),
         }
@@ -175,3 +177,10 @@ def pusch_slot_host(h, n_slots, time_in_host, W, pilots_host, x_hat_host, bits_h
                     stream=None) -> None:
     _check(lib().pusch_slot_host(h, n_slots, _ptr(time_in_host), _ptr(W), _ptr(pilots_host), _ptr(x_hat_host),
                                  _ptr(bits_host), _ptr(status_host), _stream(stream)), "pusch_slot_host")
+
+
+def pusch_slot_noalloc(cfg: pusch_cell_cfg, n_slots, time_in, W, pilots, x_hat, bits, status=None,
+                       stream=None) -> None:
+    """pusch_slot without a handle and without device allocation (static library buffer)."""
+    _check(lib().pusch_slot_noalloc(ctypes.byref(cfg), n_slots, _ptr(time_in), _ptr(W), _ptr(pilots), _ptr(x_hat),
+                                    _ptr(bits), _ptr(status), _stream(stream)), "pusch_slot_noalloc")

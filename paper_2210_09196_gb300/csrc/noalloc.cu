@@ -1,0 +1,132 @@
+// pusch_slot_noalloc: the whole receive chain (the kernels of pusch_slot) for callers that cannot allocate
+// device memory. Its intermediates (FFT output, beamformed grid, channel estimate), the FFT twiddle table
+// and its status words live in one file-scope static device buffer of PUSCH_NOALLOC_SCRATCH_BYTES instead
+// of a handle's workspace, so a call performs no cudaMalloc / cudaFree and needs no handle.
+//
+// The buffer is shared by every call in the process on a given device and keeps the last call's
+// contents; everything a call reads from it is written earlier in the same call. Calls whose work
+// overlaps on the GPU (two streams, or two host threads) race on it.
+#include <stdio.h>
+
+#include <mutex>
+
+#include "internal.cuh"
+
+// The static buffer: every GPU that loads this library holds it until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[PUSCH_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxDevices = 256;
+std::mutex g_setup_mutex;
+unsigned char *g_scratch_dev[kMaxDevices] = {};  // device address of g_noalloc_scratch, per device
+
+// Records the message returned by pusch_last_error() on this thread.
+pusch_status na_fail(pusch_status st, const char *msg, cudaError_t e = cudaSuccess) {
+    char buf[512];
+    if (e != cudaSuccess)
+        snprintf(buf, sizeof buf, "%s: %s", msg, cudaGetErrorString(e));
+    else
+        snprintf(buf, sizeof buf, "%s", msg);
+    pusch::set_last_error(buf);
+    return st;
+}
+
+// exp(-2 pi i q / n), computed in double precision and rounded once to float.
+__global__ void noalloc_twiddle_kernel(float2 *tw, int n) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < n) {
+        double s, c;
+        sincospi(-2.0 * (double)q / (double)n, &s, &c);
+        tw[q] = make_float2((float)c, (float)s);
+    }
+}
+
+__global__ void noalloc_status_kernel(uint32_t *status, uint32_t *kernel_err) {
+    status[0] = 0u;
+    status[1] = 0u;
+    status[2] = 0xffffffffu;
+    status[3] = 0u;
+    kernel_err[0] = 0u;
+}
+
+size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Device address of the static buffer on the current device; looked up on the first call per device.
+pusch_status scratch_for_current_device(unsigned char **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return na_fail(PUSCH_ERR_CUDA, "cudaGetDevice", e);
+    if (dev < 0 || dev >= kMaxDevices) return na_fail(PUSCH_ERR_UNSUPPORTED, "device index out of range");
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    if (!g_scratch_dev[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) return na_fail(PUSCH_ERR_CUDA, "cudaGetSymbolAddress of the static buffer", e);
+        g_scratch_dev[dev] = static_cast<unsigned char *>(p);
+    }
+    *out = g_scratch_dev[dev];
+    return PUSCH_OK;
+}
+
+}  // namespace
+
+extern "C" pusch_status pusch_slot_noalloc(const pusch_cell_cfg *cfg, int n_slots, const void *time_in,
+                                           const void *W, const void *pilots, void *x_hat, uint8_t *bits,
+                                           uint32_t *status, void *stream) {
+    if (n_slots < 0) return na_fail(PUSCH_ERR_ARG, "pusch_slot_noalloc: n_slots < 0");
+    size_t ws = 0;
+    pusch_status st = pusch_workspace_size(cfg, n_slots > 0 ? n_slots : 1, &ws);  // validates cfg, no allocation
+    if (st != PUSCH_OK) return st;  // message already set by pusch_workspace_size
+    if (n_slots == 0) return PUSCH_OK;
+    if (!time_in || !W || !pilots || !x_hat || !bits) return na_fail(PUSCH_ERR_ARG, "pusch_slot_noalloc: NULL buffer");
+
+    const pusch::Geometry g = pusch::make_geometry(*cfg);
+    const size_t rows = (size_t)n_slots * g.n_sym * g.n_rx;
+    const size_t tw_b = up256((size_t)g.n_fft * sizeof(float2));
+    const size_t words_b = 256;  // status sink (16 B) + tensor-core timeout word (16 B)
+    const size_t freq_b = up256(g.form == PUSCH_FORM_MIXED ? rows * 2 * g.sc_pitch * sizeof(__half)
+                                                           : rows * g.n_sc * sizeof(float2));
+    const size_t beam_b = up256((size_t)n_slots * g.n_sym * g.n_sc * g.n_beams * sizeof(float2));
+    const size_t H_b = up256((size_t)n_slots * g.n_sc * g.n_layers * g.n_beams * sizeof(float2));
+    const size_t need = tw_b + words_b + freq_b + beam_b + H_b;
+    if (need > (size_t)PUSCH_NOALLOC_SCRATCH_BYTES) {
+        char buf[512];
+        snprintf(buf, sizeof buf,
+                 "pusch_slot_noalloc: %d slot(s) of this cell need %zu bytes of scratch, more than the static "
+                 "buffer's %u bytes; pass fewer slots per call or use pusch_slot with a handle",
+                 n_slots, need, (unsigned)PUSCH_NOALLOC_SCRATCH_BYTES);
+        return na_fail(PUSCH_ERR_UNSUPPORTED, buf);
+    }
+
+    unsigned char *base = nullptr;
+    if ((st = scratch_for_current_device(&base)) != PUSCH_OK) return st;
+    float2 *tw = reinterpret_cast<float2 *>(base);
+    uint32_t *sink = reinterpret_cast<uint32_t *>(base + tw_b);
+    uint32_t *tc_err = sink + 4;
+    void *freq = base + tw_b + words_b;
+    float2 *beam = reinterpret_cast<float2 *>(base + tw_b + words_b + freq_b);
+    float2 *H = reinterpret_cast<float2 *>(base + tw_b + words_b + freq_b + beam_b);
+    uint32_t *stat = status ? status : sink;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+    noalloc_twiddle_kernel<<<(g.n_fft + 255) / 256, 256, 0, s>>>(tw, g.n_fft);
+    noalloc_status_kernel<<<1, 1, 0, s>>>(stat, tc_err);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return na_fail(PUSCH_ERR_CUDA, "pusch_slot_noalloc set-up launch", e);
+    if ((e = pusch::launch_fft(g, n_slots, time_in, freq, tw, s)) != cudaSuccess)
+        return na_fail(PUSCH_ERR_CUDA, "pusch_slot_noalloc fft launch", e);
+    if (g.form == PUSCH_FORM_MIXED)
+        e = pusch::launch_beamform_tc(g, n_slots, static_cast<const __half *>(freq), static_cast<const float2 *>(W),
+                                      beam, tc_err, s);
+    else
+        e = pusch::launch_beamform_fp32(g, n_slots, static_cast<const float2 *>(freq), static_cast<const float2 *>(W),
+                                        beam, s);
+    if (e != cudaSuccess) return na_fail(PUSCH_ERR_CUDA, "pusch_slot_noalloc beamforming launch", e);
+    if ((e = pusch::launch_chest_ls(g, n_slots, beam, static_cast<const float2 *>(pilots), H, s)) != cudaSuccess)
+        return na_fail(PUSCH_ERR_CUDA, "pusch_slot_noalloc channel estimation launch", e);
+    if ((e = pusch::launch_mmse(g, n_slots, H, beam, static_cast<float2 *>(x_hat), bits, stat, s)) != cudaSuccess)
+        return na_fail(PUSCH_ERR_CUDA, "pusch_slot_noalloc detection launch", e);
+    pusch::set_last_error("");
+    return PUSCH_OK;
+}
