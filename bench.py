@@ -129,29 +129,29 @@ def workload(n_slots):
 
 
 def stage_bytes(cell, form, n):
-    """Algorithmic bytes per launch of each stage for a batch of n slots (read + write once)."""
+    """Algorithmic bytes per launch of each pusch_slot stage for a batch of n slots (read + write once)."""
     S, R, N, sc, Bm, L = 14, cell.n_rx, cell.n_fft, cell.n_sc, cell.n_beams, cell.n_layers
     t_in = S * R * N * (4 if cell.in_fp16 else 8)
     f_out = S * R * sc * (4 if form == "mixed" else 8)
     beam = S * sc * Bm * 8
     W = R * Bm * 8
-    H = sc * L * Bm * 8
     pil = L * 2 * sc * 8
-    dmrs = 2 * sc * Bm * 8
-    data = 12 * sc * Bm * 8
     xh = L * 12 * sc * 8
     bits = L * 12 * sc
     return {
         "fft": n * (t_in + f_out),
         "beamform": n * (f_out + beam) + W,
-        "chest": n * (dmrs + pil + H),
-        "mmse": n * (H + data + xh + bits),
+        "detect": n * (beam + pil + xh + bits),   # all 14 beamformed symbols (2 DMRS + 12 data) read once
     }
 
 
 def stage_flops(cell, n):
     S, R, sc, Bm, L = 14, cell.n_rx, cell.n_sc, cell.n_beams, cell.n_layers
     return {"beamform": n * 8.0 * S * sc * R * Bm}
+
+
+KERNELS = {"fft": "fft_kernel", "beamform": {"mixed": "beamform_tc_kernel", "fp32": "beamform_fp32_kernel"},
+           "detect": "mmse_kernel (fused estimation)"}
 
 
 def peaks():
@@ -196,53 +196,33 @@ def run_ours(args, rank, world, local):
     def make_rx(f):
         return host.Receiver(host.cfg_for(cell, B.PUSCH_FORM_MIXED if f == "mixed" else B.PUSCH_FORM_FP32), n)
 
-    def timed(rx, steps, warmup, per_stage):
-        """Time `steps` chain passes; per_stage -> events between the four stage launches."""
+    def timed(rx, steps, warmup):
+        """Time `steps` calls of pusch_slot; the handle records per-stage events inside the timed region."""
         st = torch.cuda.current_stream()
-        freq, beam, H = rx.freq_buffer(n), rx.beam_buffer(n), rx.H_buffer(n)
         x, b, stat = rx.xhat_buffer(n), rx.bits_buffer(n), rx.status_buffer()
-
-        def step(ev=None):
-            if ev is not None:
-                ev[0].record(st)
-            B.pusch_ofdm_fft(rx.h, n, time_d, freq, st)
-            if ev is not None:
-                ev[1].record(st)
-            B.pusch_beamform(rx.h, n, freq, W, beam, st)
-            if ev is not None:
-                ev[2].record(st)
-            B.pusch_chest_ls(rx.h, n, beam, pil_d, H, st)
-            if ev is not None:
-                ev[3].record(st)
-            B.pusch_mmse_detect(rx.h, n, H, beam, x, b, stat, st)
-            if ev is not None:
-                ev[4].record(st)
-
         for _ in range(warmup):
-            step()
+            B.pusch_slot(rx.h, n, time_d, W, pil_d, x, b, stat, st)
         torch.cuda.synchronize()
-        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(steps)] if per_stage else None
+        B.pusch_profile_start(rx.h, steps)
         start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier(world)
         torch.cuda.synchronize()
         start.record(st)
-        for k in range(steps):
-            step(evs[k] if per_stage else None)
+        for _ in range(steps):
+            B.pusch_slot(rx.h, n, time_d, W, pil_d, x, b, stat, st)
         end.record(st)
         torch.cuda.synchronize()
         barrier(world)
         total_ms = start.elapsed_time(end)
-        stages = None
-        if per_stage:
-            names = ["fft", "beamform", "chest", "mmse"]
-            stages = {nm: sum(e[i].elapsed_time(e[i + 1]) for e in evs) / steps for i, nm in enumerate(names)}
+        ms, calls = B.pusch_profile_read(rx.h)
+        stages = {k: v / calls for k, v in ms.items()}
         return total_ms, stages, (x, b, stat)
 
     # headline form, timed with per-stage events inside the timed region
     rx = make_rx(form)
     sampler = ClockSampler(local)
     sampler.start()
-    total_ms, stages, outs = timed(rx, args.steps, args.warmup, per_stage=True)
+    total_ms, stages, outs = timed(rx, args.steps, args.warmup)
     clocks = sampler.stop()
     t_max = max_over_ranks(total_ms, world)
     value = n * args.steps * world / (t_max / 1e3)
@@ -252,7 +232,7 @@ def run_ours(args, rank, world, local):
     fp32 = None
     if form == "mixed":
         rx32 = make_rx("fp32")
-        t32, st32, _ = timed(rx32, args.steps, args.warmup, per_stage=True)
+        t32, st32, _ = timed(rx32, args.steps, args.warmup)
         t32 = max_over_ranks(t32, world)
         fp32 = {"value": n * args.steps * world / (t32 / 1e3), "ms_per_step": t32 / args.steps,
                 "stage_ms": st32}
@@ -288,29 +268,29 @@ def run_ours(args, rank, world, local):
     sb = stage_bytes(cell, form, n)
     dom = max(stages, key=stages.get)
     dom_ms = stages[dom]
-    sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    kname = KERNELS[dom] if dom != "beamform" else KERNELS["beamform"][form]
     if dom == "beamform" and form == "fp32":
         fl = stage_flops(cell, n)["beamform"]
         ach = fl / (dom_ms / 1e3) / 1e12
         peak = fp32_alu_peak_tflops(2070.0)
-        roof = {"kernel": "beamform_fp32_kernel", "bound": "alu", "achieved": round(ach, 2), "peak": round(peak, 1),
+        roof = {"kernel": kname, "bound": "alu", "achieved": round(ach, 2), "peak": round(peak, 1),
                 "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": None,
-                "peak_src": "FP32 FMA issue rate 152 SMs x 128 lanes x 2 x 2070 MHz"}
+                "peak_src": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
     else:
-        kname = {"fft": "fft_kernel", "beamform": "beamform_tc_kernel", "chest": "chest_ls_kernel",
-                 "mmse": "mmse_kernel"}[dom]
         ach = sb[dom] / (dom_ms / 1e3) / 1e9
         roof = {"kernel": kname, "bound": "hbm", "achieved": round(ach, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": round(ach / pk["hbm_gbs"], 4), "traffic": None, "peak_src": pk["src"]}
-    per_stage = {k: {"ms": round(v, 4), "GB/s": round(sb[k] / (v / 1e3) / 1e9, 1),
+    per_stage = {k: {"kernel": KERNELS[k] if k != "beamform" else KERNELS["beamform"][form], "ms": round(v, 4),
+                     "GB/s": round(sb[k] / (v / 1e3) / 1e9, 1),
                      "hbm_frac": round(sb[k] / (v / 1e3) / 1e9 / pk["hbm_gbs"], 4)} for k, v in stages.items()}
     per_stage["beamform"]["TFLOP/s"] = round(stage_flops(cell, n)["beamform"] / (stages["beamform"] / 1e3) / 1e12, 2)
 
-    cpu = None
-    if not args.no_cpu_baseline and world >= 1:
-        cpu = cpu_baseline(slots, budget_s=12.0)
+    cpu, quality = None, None
+    if not args.no_cpu_baseline:
+        cpu, oracle_out = cpu_baseline(slots, budget_s=12.0)
+        quality = evm_gate(outs, oracle_out, cell.qam_bits)
 
-    launches_per_step = 5 + (1 if form == "mixed" else 0)
+    launches_per_step = 4  # FFT, beamforming, status reset, fused estimation + detection
     out = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 4), "higher_is_better": True,
@@ -324,6 +304,7 @@ def run_ours(args, rank, world, local):
         "roofline": roof,
         "stages": per_stage,
         "cpu_baseline": cpu,
+        "quality_vs_fp64": quality,
         "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
@@ -337,17 +318,44 @@ def run_ours(args, rank, world, local):
 
 # ---------------------------------------------------------------------------------------- oracle arm
 def cpu_baseline(slots, budget_s):
+    """The FP64 oracle chain on whole slots of the same batch until budget_s of CPU time has passed."""
     import oracle
     oracle.build()
-    done, t0 = 0, time.perf_counter()
+    outs, t0 = [], time.perf_counter()
     for s in slots:
-        oracle.run_slot(s)
-        done += 1
-        if time.perf_counter() - t0 > budget_s and done >= 2:
+        outs.append(oracle.run_slot(s))
+        if time.perf_counter() - t0 > budget_s and len(outs) >= 2:
             break
     dt = time.perf_counter() - t0
-    return {"value": round(done / dt, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{done} whole deployment slots through the FP64 C oracle (single thread), {dt:.1f} s"}
+    done = len(outs)
+    return ({"value": round(done / dt, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+             "sample": f"{done} whole deployment slots through the FP64 C oracle (single thread), {dt:.1f} s"},
+            outs)
+
+
+def evm_gate(gpu_outs, oracle_outs, q):
+    """EVM of the timed form's symbols vs the FP64 oracle chain and hard-decision mismatches, on the slots
+    the CPU baseline computed."""
+    import numpy as np
+    x, b, _ = gpu_outs
+    err = ref = 0.0
+    mism = hard = total = 0
+    t = 2 / np.sqrt(10)
+    for i, (xo, bo, _) in enumerate(oracle_outs):
+        xg = x[i].cpu().numpy().astype(np.complex128)
+        bg = b[i].cpu().numpy()
+        err += float(np.sum(np.abs(xg - xo) ** 2))
+        ref += float(np.sum(np.abs(xo) ** 2))
+        m = bg != bo
+        tol = 4 * float(np.max(np.abs(xg - xo)))
+        near = np.minimum(np.minimum(np.abs(xo.real), np.abs(np.abs(xo.real) - t)),
+                          np.minimum(np.abs(xo.imag), np.abs(np.abs(xo.imag) - t))) <= tol
+        mism += int(m.sum())
+        hard += int((m & ~near).sum())
+        total += m.size
+    return {"evm_db": round(10 * np.log10(err / ref), 2), "slots": len(oracle_outs), "symbols": total,
+            "hard_bit_mismatches": mism, "mismatches_off_threshold": hard, "gate_evm_db": -40.0,
+            "pass": bool(10 * np.log10(err / ref) <= -40.0 and hard == 0)}
 
 
 def reference_step(oracle, s, frac, rng):

@@ -33,7 +33,7 @@ PUSCH_STATUS_NONFINITE = 0x2
 EXPORTS = (
     "pusch_create", "pusch_destroy", "pusch_workspace_size", "pusch_sc_pitch", "pusch_ofdm_fft", "pusch_beamform",
     "pusch_chest_ls", "pusch_mmse_detect", "pusch_slot", "pusch_slot_host", "pusch_last_error", "pusch_version",
-    "pusch_slot_noalloc",
+    "pusch_slot_noalloc", "pusch_profile_start", "pusch_profile_read",
 )
 
 
@@ -88,6 +88,8 @@ def lib():
             "pusch_slot": (I, [P, I, P, P, P, P, P, P, P]),
             "pusch_slot_host": (I, [P, I, P, P, P, P, P, P, P]),
             "pusch_slot_noalloc": (I, [ctypes.POINTER(pusch_cell_cfg), I, P, P, P, P, P, P, P]),
+            "pusch_profile_start": (I, [P, I]),
+            "pusch_profile_read": (I, [P, ctypes.POINTER(ctypes.c_float), I, ctypes.POINTER(I)]),
             "pusch_last_error": (ctypes.c_char_p, []),
             "pusch_version": (ctypes.c_char_p, []),
         }
@@ -184,3 +186,18 @@ def pusch_slot_noalloc(cfg: pusch_cell_cfg, n_slots, time_in, W, pilots, x_hat, 
     """pusch_slot without a handle and without device allocation (static library buffer)."""
     _check(lib().pusch_slot_noalloc(ctypes.byref(cfg), n_slots, _ptr(time_in), _ptr(W), _ptr(pilots), _ptr(x_hat),
                                     _ptr(bits), _ptr(status), _stream(stream)), "pusch_slot_noalloc")
+
+
+SLOT_STAGES = ("fft", "beamform", "detect")
+
+
+def pusch_profile_start(h, max_calls: int) -> None:
+    _check(lib().pusch_profile_start(h, max_calls), "pusch_profile_start")
+
+
+def pusch_profile_read(h) -> tuple[dict, int]:
+    """(summed milliseconds per pusch_slot stage, number of timed calls)."""
+    ms = (ctypes.c_float * len(SLOT_STAGES))()
+    n = ctypes.c_int()
+    _check(lib().pusch_profile_read(h, ms, len(SLOT_STAGES), ctypes.byref(n)), "pusch_profile_read")
+    return dict(zip(SLOT_STAGES, list(ms))), n.value

@@ -18,7 +18,6 @@ struct pusch_handle {
     uint32_t *kernel_err = nullptr;   // bounded-wait expiry flags of the tensor-core kernel
     void *freq = nullptr;           // workspace: FFT output
     float2 *beam = nullptr;         // workspace: beamformed grid
-    float2 *H = nullptr;            // workspace: channel estimate
     uint32_t *status_sink = nullptr;  // status words used when the caller passes NULL
     // staging for pusch_slot_host (allocated on first use)
     void *h_time = nullptr;
@@ -26,11 +25,17 @@ struct pusch_handle {
     float2 *h_xhat = nullptr;
     uint8_t *h_bits = nullptr;
     uint32_t *h_status = nullptr;
+    // per-stage timing of pusch_slot (pusch_profile_start / pusch_profile_read)
+    std::vector<cudaEvent_t> prof_events;  // [max_calls][kSlotStages + 1]
+    int prof_max_calls = 0;
+    int prof_calls = 0;
 };
 
 namespace {
 
 thread_local char g_err[512] = "";
+
+constexpr int kSlotStages = 3;  // pusch_slot launches: FFT, beamforming, fused estimation + detection
 
 pusch_status fail(pusch_status st, const char *fmt, ...) {
     va_list ap;
@@ -90,9 +95,6 @@ size_t freq_bytes(const pusch::Geometry &g, int n_slots) {
 size_t beam_bytes(const pusch::Geometry &g, int n_slots) {
     return (size_t)n_slots * g.n_sym * g.n_sc * g.n_beams * sizeof(float2);
 }
-size_t H_bytes(const pusch::Geometry &g, int n_slots) {
-    return (size_t)n_slots * g.n_sc * g.n_layers * g.n_beams * sizeof(float2);
-}
 size_t time_bytes(const pusch::Geometry &g, int n_slots) {
     return (size_t)n_slots * g.n_sym * g.n_rx * g.n_fft * (g.in_fp16 ? 4 : 8);
 }
@@ -106,7 +108,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 size_t workspace_bytes(const pusch::Geometry &g, int max_slots) {
     size_t b = align256(g.n_fft * sizeof(float2));
-    b += align256(freq_bytes(g, max_slots)) + align256(beam_bytes(g, max_slots)) + align256(H_bytes(g, max_slots));
+    b += align256(freq_bytes(g, max_slots)) + align256(beam_bytes(g, max_slots));
     return b;
 }
 
@@ -209,7 +211,6 @@ pusch_status pusch_create(pusch_handle **out, const pusch_cell_cfg *cfg, int max
     if ((e = cudaMemset(h->kernel_err, 0, 16)) != cudaSuccess) goto cuda_error;
     if ((e = cudaMalloc(&h->freq, freq_bytes(g, max_slots))) != cudaSuccess) goto cuda_error;
     if ((e = cudaMalloc((void **)&h->beam, beam_bytes(g, max_slots))) != cudaSuccess) goto cuda_error;
-    if ((e = cudaMalloc((void **)&h->H, H_bytes(g, max_slots))) != cudaSuccess) goto cuda_error;
     if ((e = cudaMalloc((void **)&h->status_sink, 4 * sizeof(uint32_t))) != cudaSuccess) goto cuda_error;
     *out = h;
     return ok();
@@ -221,11 +222,11 @@ cuda_error:
 pusch_status pusch_destroy(pusch_handle *h) {
     if (!h) return ok();
     cudaDeviceSynchronize();
+    for (cudaEvent_t ev : h->prof_events) cudaEventDestroy(ev);
     cudaFree(h->twiddle);
     cudaFree(h->kernel_err);
     cudaFree(h->freq);
     cudaFree(h->beam);
-    cudaFree(h->H);
     cudaFree(h->status_sink);
     cudaFree(h->h_time);
     cudaFree(h->h_pilots);
@@ -241,7 +242,8 @@ pusch_status pusch_ofdm_fft(pusch_handle *h, int n_slots, const void *time_in, v
     if (st != PUSCH_OK) return st;
     if (n_slots == 0) return ok();
     if (!time_in || !freq_out) return fail(PUSCH_ERR_ARG, "pusch_ofdm_fft: NULL buffer");
-    cudaError_t e = pusch::launch_fft(h->geo, n_slots, time_in, freq_out, h->twiddle, (cudaStream_t)stream);
+    cudaError_t e = pusch::launch_fft(h->geo, n_slots, time_in, freq_out, h->twiddle, h->kernel_err,
+                                        (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "fft launch");
     return ok();
 }
@@ -301,10 +303,63 @@ pusch_status pusch_slot(pusch_handle *h, int n_slots, const void *time_in, const
     if (st != PUSCH_OK) return st;
     if (n_slots == 0) return ok();
     if (!time_in || !W || !pilots || !x_hat || !bits) return fail(PUSCH_ERR_ARG, "pusch_slot: NULL buffer");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t *ev = nullptr;
+    if (h->prof_calls < h->prof_max_calls) ev = &h->prof_events[(size_t)h->prof_calls++ * (kSlotStages + 1)];
+    if (ev) cudaEventRecord(ev[0], s);
     if ((st = pusch_ofdm_fft(h, n_slots, time_in, h->freq, stream)) != PUSCH_OK) return st;
+    if (ev) cudaEventRecord(ev[1], s);
     if ((st = pusch_beamform(h, n_slots, h->freq, W, h->beam, stream)) != PUSCH_OK) return st;
-    if ((st = pusch_chest_ls(h, n_slots, h->beam, pilots, h->H, stream)) != PUSCH_OK) return st;
-    return pusch_mmse_detect(h, n_slots, h->H, h->beam, x_hat, bits, status, stream);
+    if (ev) cudaEventRecord(ev[2], s);
+    uint32_t *stat = status ? status : h->status_sink;
+    if ((st = reset_status(stat, s)) != PUSCH_OK) return st;
+    cudaError_t e = pusch::launch_mmse_fused(h->geo, n_slots, h->beam, (const float2 *)pilots, (float2 *)x_hat, bits,
+                                             stat, s);
+    if (e != cudaSuccess) return cuda_fail(e, "fused estimation + detection launch");
+    if (ev) cudaEventRecord(ev[3], s);
+    return ok();
+}
+
+pusch_status pusch_profile_start(pusch_handle *h, int max_calls) {
+    if (!h) return fail(PUSCH_ERR_ARG, "handle is NULL");
+    if (max_calls < 0 || max_calls > 1000000) return fail(PUSCH_ERR_ARG, "max_calls out of [0, 1e6]");
+    for (cudaEvent_t ev : h->prof_events) cudaEventDestroy(ev);
+    h->prof_events.assign((size_t)max_calls * (kSlotStages + 1), nullptr);
+    for (auto &ev : h->prof_events) {
+        cudaError_t e = cudaEventCreate(&ev);
+        if (e != cudaSuccess) {
+            h->prof_max_calls = h->prof_calls = 0;
+            return cuda_fail(e, "profiling event");
+        }
+    }
+    h->prof_max_calls = max_calls;
+    h->prof_calls = 0;
+    return ok();
+}
+
+pusch_status pusch_profile_read(pusch_handle *h, float *stage_ms, int n_stages, int *n_calls) {
+    if (!h) return fail(PUSCH_ERR_ARG, "handle is NULL");
+    if (!stage_ms || n_stages < kSlotStages) return fail(PUSCH_ERR_ARG, "stage_ms must hold %d values", kSlotStages);
+    for (int k = 0; k < kSlotStages; ++k) stage_ms[k] = 0.f;
+    const int calls = h->prof_calls;
+    if (calls > 0) {
+        cudaError_t e = cudaEventSynchronize(h->prof_events[(size_t)calls * (kSlotStages + 1) - 1]);
+        if (e != cudaSuccess) return cuda_fail(e, "profiling synchronize");
+    }
+    for (int c = 0; c < calls; ++c) {
+        cudaEvent_t *ev = &h->prof_events[(size_t)c * (kSlotStages + 1)];
+        for (int k = 0; k < kSlotStages; ++k) {
+            float ms = 0.f;
+            cudaError_t e = cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+            if (e != cudaSuccess) return cuda_fail(e, "profiling elapsed time");
+            stage_ms[k] += ms;
+        }
+    }
+    if (n_calls) *n_calls = calls;
+    for (cudaEvent_t ev : h->prof_events) cudaEventDestroy(ev);
+    h->prof_events.clear();
+    h->prof_max_calls = h->prof_calls = 0;
+    return ok();
 }
 
 pusch_status pusch_slot_host(pusch_handle *h, int n_slots, const void *time_in_host, const void *W,

@@ -6,7 +6,7 @@
 // [n_sc][n_layers][n_beams] estimate the detector reads is written with fully coalesced stores. The two
 // pilot REs a thread needs are re-derived per thread (they are read from L1/L2; the DMRS rows are a
 // small fraction of the slot).
-#include "internal.cuh"
+#include "chest_common.cuh"
 
 namespace pusch {
 namespace {
@@ -15,19 +15,6 @@ struct ChestArgs {
     int n_sc, n_beams, n_layers, comb, n_sym, dmrs0, dmrs1;
     int port[32];
 };
-
-// 1/2 sum_j Y_j / P_j, the division done as y * conj(p) / |p|^2.
-__device__ __forceinline__ float2 ls_at(const float2 *__restrict__ y0, const float2 *__restrict__ y1,
-                                        const float2 *__restrict__ p0, const float2 *__restrict__ p1, int q, int nb,
-                                        int b) {
-    const float2 ya = __ldg(&y0[(long long)q * nb + b]);
-    const float2 yb = __ldg(&y1[(long long)q * nb + b]);
-    const float2 pa = __ldg(&p0[q]);
-    const float2 pb = __ldg(&p1[q]);
-    const float2 da = cscale(cmulc(pa, ya), 1.f / (pa.x * pa.x + pa.y * pa.y));
-    const float2 db = cscale(cmulc(pb, yb), 1.f / (pb.x * pb.x + pb.y * pb.y));
-    return cscale(cadd(da, db), 0.5f);
-}
 
 __global__ void __launch_bounds__(256)
 chest_ls_kernel(ChestArgs g, long long total, const float2 *__restrict__ beam, const float2 *__restrict__ pilots,
@@ -43,27 +30,20 @@ chest_ls_kernel(ChestArgs g, long long total, const float2 *__restrict__ beam, c
         const int l = (int)(rem / g.n_beams);
         const int b = (int)(rem - (long long)l * g.n_beams);
 
-        const int port = g.port[l];
-        const int first = port;
-        const int last = port + ((g.n_sc - 1 - port) / g.comb) * g.comb;
         int lo, hi;
-        if (a <= first) {
-            lo = hi = first;
-        } else if (a >= last) {
-            lo = hi = last;
-        } else {
-            lo = port + ((a - port) / g.comb) * g.comb;
-            hi = (lo == a) ? lo : lo + g.comb;
-        }
+        pilot_bracket(a, g.port[l], g.comb, g.n_sc, lo, hi);
         const float2 *y0 = beam + (slot * g.n_sym + g.dmrs0) * (long long)g.n_sc * g.n_beams;
         const float2 *y1 = beam + (slot * g.n_sym + g.dmrs1) * (long long)g.n_sc * g.n_beams;
         const float2 *p0 = pilots + (slot * g.n_layers + l) * 2LL * g.n_sc;
         const float2 *p1 = p0 + g.n_sc;
-        float2 h = ls_at(y0, y1, p0, p1, lo, g.n_beams, b);
+        const float2 h_lo = ls_value(__ldg(&y0[(long long)lo * g.n_beams + b]), __ldg(&y1[(long long)lo * g.n_beams + b]),
+                                     pilot_inverse(__ldg(&p0[lo])), pilot_inverse(__ldg(&p1[lo])));
+        float2 h = h_lo;
         if (hi != lo) {
-            const float2 h1 = ls_at(y0, y1, p0, p1, hi, g.n_beams, b);
-            const float w = (float)(a - lo) / (float)(hi - lo);
-            h = make_float2(fmaf(w, h1.x - h.x, h.x), fmaf(w, h1.y - h.y, h.y));
+            const float2 h_hi =
+                ls_value(__ldg(&y0[(long long)hi * g.n_beams + b]), __ldg(&y1[(long long)hi * g.n_beams + b]),
+                         pilot_inverse(__ldg(&p0[hi])), pilot_inverse(__ldg(&p1[hi])));
+            h = interp(h_lo, h_hi, interp_weight(a, lo, hi));
         }
         H[idx] = h;
     }

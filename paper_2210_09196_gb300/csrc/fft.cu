@@ -3,11 +3,13 @@
 //
 // Design (GB300): one FFT per group of T = N/E threads, each thread holding E = 8 or 16 complex values in
 // registers. The transform is a Stockham auto-sort sequence of radix-16/8/4 passes, so that
-//   * pass 1 reads its butterfly inputs straight from global memory (element t + T*e, coalesced),
-//   * the last pass leaves bin t + T*e in register e, written straight to global memory in natural order,
+//   * pass 1 reads its butterfly inputs (element t + T*e) from the shared-memory copy of the input row,
+//   * the last pass leaves bin t + T*e in register e, written to global memory in natural order,
 //   * the passes in between exchange through shared memory padded by one slot per 16 (conflict-free).
 // 4096 = 16*16*16 therefore costs one global read, two shared-memory exchanges and one global write.
-// Twiddles come from a table exp(-2 pi i q / N) (computed on the host in double precision).
+// CTAs are persistent: the input rows arrive by bulk (TMA) copies into a 2-3 stage ring issued ahead of
+// the transform, so HBM reads overlap the arithmetic. Twiddles come from a table exp(-2 pi i q / N)
+// (computed in double precision).
 #include "internal.cuh"
 
 namespace pusch {
@@ -112,8 +114,24 @@ __device__ __forceinline__ void fft_pass(float2 (&v)[E], const float2 *__restric
 #pragma unroll
         for (int m = 0; m < R; ++m) x[m] = v[u + m * NB];
         if constexpr (LS > 1) {
+            // w^m, m < R, from the table entries w^1..w^4 and at most two more products (<= 3 roundings)
+            constexpr int S = N / (LS * R);
+            float2 w[R];
+            w[0] = make_float2(1.f, 0.f);
 #pragma unroll
-            for (int m = 1; m < R; ++m) x[m] = cmul(x[m], __ldg(&tw[(k * m) * (N / (LS * R))]));
+            for (int m = 1; m < R && m <= 4; ++m) w[m] = __ldg(&tw[(k * m) * S]);
+            if constexpr (R > 5) {
+                const float2 w8 = cmul(w[4], w[4]);
+                const float2 w12 = cmul(w8, w[4]);
+#pragma unroll
+                for (int m = 5; m < R; ++m) {
+                    const int a4 = m >> 2, b = m & 3;
+                    const float2 base = a4 == 1 ? w[4] : (a4 == 2 ? w8 : w12);
+                    w[m] = b == 0 ? base : cmul(base, w[b]);
+                }
+            }
+#pragma unroll
+            for (int m = 1; m < R; ++m) x[m] = cmul(x[m], w[m]);
         }
         dft<R>(x);
 #pragma unroll
@@ -170,8 +188,48 @@ __device__ __forceinline__ void fft_full(float2 (&v)[Plan<N>::E], float2 *sm, co
     else if constexpr (N == 64) fft_run<N, E, 1, 8, 8>(v, sm, tw, t);
 }
 
-__device__ __forceinline__ float2 load_sample(const float2 *p) { return __ldg(p); }
-__device__ __forceinline__ float2 load_sample(const __half2 *p) { return __half22float2(__ldg(p)); }
+__device__ __forceinline__ float2 to_f2(float2 v) { return v; }
+__device__ __forceinline__ float2 to_f2(__half2 v) { return __half22float2(v); }
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait (2 s of %globaltimer); false on expiry.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    const uint64_t deadline = globaltimer() + 2000000000ull;
+    while (!mbar_try_wait(bar, parity))
+        if (globaltimer() > deadline) return false;
+    return true;
+}
+
+// One bulk (TMA, non-tensor) copy global -> shared completing on an mbarrier: 16-byte aligned, size % 16 == 0.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
 
 constexpr int kFftThreads = 256;
 
@@ -180,104 +238,174 @@ constexpr int ffts_per_cta() {
     return (kFftThreads / (N / Plan<N>::E)) > 0 ? kFftThreads / (N / Plan<N>::E) : 1;
 }
 
-// rows = n_slots * n_sym * n_rx transforms. out16 = false: c64 [rows][n_sc]; out16 = true: binary16
-// [rows][2][pitch] (re plane, im plane; pad elements zeroed).
+template <typename TIn>
+constexpr int fft_stages() { return 2; }
+
+template <int N, typename TIn>
+constexpr size_t fft_smem_bytes() {
+    return (size_t)fft_stages<TIn>() * ffts_per_cta<N>() * N * sizeof(TIn)        // input ring
+           + (size_t)ffts_per_cta<N>() * (N + N / 16) * sizeof(float2)             // exchange buffer
+           + 8 * fft_stages<TIn>() + 16;                                           // mbarriers
+}
+
+// Persistent batched FFT. rows = n_slots * n_sym * n_rx transforms; each CTA iterates over blocks of F
+// consecutive rows (one contiguous span of F*N input samples). The spans arrive by bulk copies into a
+// ring of STAGES shared-memory buffers issued STAGES-1 blocks ahead, so HBM reads overlap the passes.
+// out16 = false: c64 [rows][n_sc]; out16 = true: binary16 [rows][2][pitch] (re plane, im plane; pads
+// zeroed), staged through shared memory for 16-byte stores.
+// Three 256-thread CTAs per SM (registers capped at 85; the 2-stage ring keeps shared memory at ~67 KB
+// per CTA for FP16 input): 24 warps hide the exchange barriers while one row per CTA streams in.
 template <int N, typename TIn, bool OUT16>
-__global__ void __launch_bounds__(kFftThreads)
+__global__ void __launch_bounds__(kFftThreads, 3)
 fft_kernel(const TIn *__restrict__ in, void *__restrict__ out, const float2 *__restrict__ tw, long long rows,
-           int n_sc, int pitch) {
+           int n_sc, int pitch, uint32_t *__restrict__ err) {
     constexpr int E = Plan<N>::E;
     constexpr int T = N / E;
     constexpr int F = ffts_per_cta<N>();
-    extern __shared__ float2 smem[];
+    constexpr int STAGES = fft_stages<TIn>();
+    constexpr uint32_t kSpan = (uint32_t)F * N * sizeof(TIn);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TIn *ring = reinterpret_cast<TIn *>(smem_raw);
+    float2 *xbuf = reinterpret_cast<float2 *>(smem_raw + (size_t)STAGES * kSpan);
+    const uint32_t bar0 = smem_u32(smem_raw + (size_t)STAGES * kSpan + (size_t)F * (N + N / 16) * sizeof(float2));
+    __shared__ int s_abort;
+
     const int f = threadIdx.x / T;
     const int t = threadIdx.x - f * T;
-    const long long row = (long long)blockIdx.x * F + f;
-    const bool valid = (f < F) && (row < rows);
-    float2 *sm = smem + f * (N + N / 16);
+    float2 *sm = xbuf + f * (N + N / 16);
+    const long long n_blocks = (rows + F - 1) / F;
+    const long long n_my = n_blocks > blockIdx.x ? (n_blocks - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
 
-    float2 v[E];
-    if (valid) {
-        const TIn *src = in + row * N;
-#pragma unroll
-        for (int e = 0; e < E; ++e) v[e] = load_sample(src + t + T * e);
-    } else {
-#pragma unroll
-        for (int e = 0; e < E; ++e) v[e] = make_float2(0.f, 0.f);
+    auto issue = [&](long long it) {
+        const long long blk = blockIdx.x + it * gridDim.x;
+        const long long r0 = blk * F;
+        const long long nr = rows - r0 < F ? rows - r0 : F;
+        const int s = (int)(it % STAGES);
+        bulk_load(smem_u32(ring) + s * kSpan, in + r0 * N, (uint32_t)(nr * N * sizeof(TIn)), bar0 + 8 * s);
+    };
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) mbar_init(bar0 + 8 * s, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_abort = 0;
     }
-    fft_full<N>(v, sm, tw, t);
-    if (!valid) return;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (long long it = 0; it < STAGES - 1 && it < n_my; ++it) issue(it);
 
     const int h = n_sc >> 1;
-    if constexpr (!OUT16) {
-        float2 *dst = static_cast<float2 *>(out) + row * n_sc;
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-            int a = t + T * e + h;
-            if (a >= N) a -= N;
-            if (a < n_sc) dst[a] = v[e];
+    long long it = 0;
+    for (; it < n_my; ++it) {
+        const int s = (int)(it % STAGES);
+        const bool ok = mbar_wait(bar0 + 8 * s, (uint32_t)((it / STAGES) & 1));
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) {
+                s_abort = 1;
+                if (err) atomicOr(err, 2u);
+            }
+            break;
         }
-    } else {
-        __half *re = static_cast<__half *>(out) + row * 2 * (long long)pitch;
-        __half *im = re + pitch;
+        // the ring slot consumed by the previous block is free (all threads passed a barrier since)
+        if (threadIdx.x == 0 && it + STAGES - 1 < n_my) issue(it + STAGES - 1);
+
+        const long long row = (blockIdx.x + it * gridDim.x) * F + f;
+        const bool valid = row < rows;
+        const TIn *src = ring + (size_t)s * F * N + (size_t)f * N;
+        float2 v[E];
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-            int a = t + T * e + h;
-            if (a >= N) a -= N;
-            if (a < n_sc) {
-                re[a] = __float2half_rn(v[e].x);
-                im[a] = __float2half_rn(v[e].y);
+        for (int e = 0; e < E; ++e) v[e] = to_f2(src[t + T * e]);
+        fft_full<N>(v, sm, tw, t);
+
+        if constexpr (!OUT16) {
+            if (valid) {
+                float2 *dst = static_cast<float2 *>(out) + row * n_sc;
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    int a = t + T * e + h;
+                    if (a >= N) a -= N;
+                    if (a < n_sc) dst[a] = v[e];
+                }
+            }
+        } else {
+            // stage the two planes of this FFT in its exchange buffer (free after the last pass), then
+            // write them with 16-byte stores
+            __syncthreads();
+            __half *pl = reinterpret_cast<__half *>(sm);
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                int a = t + T * e + h;
+                if (a >= N) a -= N;
+                if (a < n_sc) {
+                    pl[a] = __float2half_rn(v[e].x);
+                    pl[pitch + a] = __float2half_rn(v[e].y);
+                }
+            }
+            for (int a = n_sc + t; a < pitch; a += T) {
+                pl[a] = __float2half_rn(0.f);
+                pl[pitch + a] = __float2half_rn(0.f);
+            }
+            __syncthreads();
+            if (valid) {
+                const uint4 *srcv = reinterpret_cast<const uint4 *>(pl);
+                uint4 *dstv = reinterpret_cast<uint4 *>(static_cast<__half *>(out) + row * 2 * (long long)pitch);
+                for (int c = t; c < pitch / 4; c += T) dstv[c] = srcv[c];  // 2 * pitch halves = pitch / 4 x 16 B
             }
         }
-        for (int a = n_sc + t; a < pitch; a += T) {
-            re[a] = __float2half_rn(0.f);
-            im[a] = __float2half_rn(0.f);
-        }
+    }
+    if (s_abort && threadIdx.x == 0) {
+        // drain the copies still in flight (bounded) before the CTA exits
+        for (long long j = it; j < it + STAGES - 1 && j < n_my; ++j)
+            mbar_wait(bar0 + 8 * (int)(j % STAGES), (uint32_t)((j / STAGES) & 1));
     }
 }
 
 template <int N, typename TIn, bool OUT16>
-cudaError_t launch_n(long long rows, const void *in, void *out, const float2 *tw, int n_sc, int pitch,
+cudaError_t launch_n(long long rows, const void *in, void *out, const float2 *tw, int n_sc, int pitch, uint32_t *err,
                      cudaStream_t st) {
     constexpr int F = ffts_per_cta<N>();
-    const size_t smem = (size_t)F * (N + N / 16) * sizeof(float2);
-    const long long grid = (rows + F - 1) / F;
-    if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    constexpr size_t smem = fft_smem_bytes<N, TIn>();
+    static_assert(smem <= 227 * 1024, "FFT shared memory");
     auto k = fft_kernel<N, TIn, OUT16>;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    k<<<(unsigned)grid, kFftThreads, smem, st>>>(static_cast<const TIn *>(in), out, tw, rows, n_sc, pitch);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 152, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kFftThreads, smem);
+    if (per_sm < 1) per_sm = 1;
+    const long long blocks = (rows + F - 1) / F;
+    long long grid = (long long)sms * per_sm;
+    if (grid > blocks) grid = blocks;
+    k<<<(unsigned)grid, kFftThreads, smem, st>>>(static_cast<const TIn *>(in), out, tw, rows, n_sc, pitch, err);
     return cudaGetLastError();
 }
 
 template <int N>
-cudaError_t launch_typed(const Geometry &g, long long rows, const void *in, void *out, const float2 *tw,
+cudaError_t launch_typed(const Geometry &g, long long rows, const void *in, void *out, const float2 *tw, uint32_t *err,
                          cudaStream_t st) {
     const bool out16 = g.form == PUSCH_FORM_MIXED;
     if (g.in_fp16) {
-        return out16 ? launch_n<N, __half2, true>(rows, in, out, tw, g.n_sc, g.sc_pitch, st)
-                     : launch_n<N, __half2, false>(rows, in, out, tw, g.n_sc, g.sc_pitch, st);
+        return out16 ? launch_n<N, __half2, true>(rows, in, out, tw, g.n_sc, g.sc_pitch, err, st)
+                     : launch_n<N, __half2, false>(rows, in, out, tw, g.n_sc, g.sc_pitch, err, st);
     }
-    return out16 ? launch_n<N, float2, true>(rows, in, out, tw, g.n_sc, g.sc_pitch, st)
-                 : launch_n<N, float2, false>(rows, in, out, tw, g.n_sc, g.sc_pitch, st);
+    return out16 ? launch_n<N, float2, true>(rows, in, out, tw, g.n_sc, g.sc_pitch, err, st)
+                 : launch_n<N, float2, false>(rows, in, out, tw, g.n_sc, g.sc_pitch, err, st);
 }
 
 }  // namespace
 
 cudaError_t launch_fft(const Geometry &g, int n_slots, const void *time_in, void *freq_out, const float2 *twiddle,
-                       cudaStream_t st) {
+                       uint32_t *err, cudaStream_t st) {
+    if (reinterpret_cast<uintptr_t>(time_in) % 16 != 0) return cudaErrorMisalignedAddress;
     const long long rows = (long long)n_slots * g.n_sym * g.n_rx;
     if (rows == 0) return cudaSuccess;
     switch (g.n_fft) {
-        case 4096: return launch_typed<4096>(g, rows, time_in, freq_out, twiddle, st);
-        case 2048: return launch_typed<2048>(g, rows, time_in, freq_out, twiddle, st);
-        case 1024: return launch_typed<1024>(g, rows, time_in, freq_out, twiddle, st);
-        case 512: return launch_typed<512>(g, rows, time_in, freq_out, twiddle, st);
-        case 256: return launch_typed<256>(g, rows, time_in, freq_out, twiddle, st);
-        case 128: return launch_typed<128>(g, rows, time_in, freq_out, twiddle, st);
-        case 64: return launch_typed<64>(g, rows, time_in, freq_out, twiddle, st);
+        case 4096: return launch_typed<4096>(g, rows, time_in, freq_out, twiddle, err, st);
+        case 2048: return launch_typed<2048>(g, rows, time_in, freq_out, twiddle, err, st);
+        case 1024: return launch_typed<1024>(g, rows, time_in, freq_out, twiddle, err, st);
+        case 512: return launch_typed<512>(g, rows, time_in, freq_out, twiddle, err, st);
+        case 256: return launch_typed<256>(g, rows, time_in, freq_out, twiddle, err, st);
+        case 128: return launch_typed<128>(g, rows, time_in, freq_out, twiddle, err, st);
+        case 64: return launch_typed<64>(g, rows, time_in, freq_out, twiddle, err, st);
         default: return cudaErrorInvalidValue;
     }
 }

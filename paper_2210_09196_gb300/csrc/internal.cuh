@@ -54,14 +54,19 @@ void set_last_error(const char *msg);
 
 // ------------------------------------------------------------------------------------------ launchers
 // Each returns cudaSuccess or the launch error. All pointers are device pointers.
+// err (device, one uint32): bit 1 is set if a bounded wait of the FFT kernel expired.
 cudaError_t launch_fft(const Geometry &g, int n_slots, const void *time_in, void *freq_out, const float2 *twiddle,
-                       cudaStream_t st);
+                       uint32_t *err, cudaStream_t st);
 cudaError_t launch_beamform_fp32(const Geometry &g, int n_slots, const float2 *freq, const float2 *W, float2 *beam,
                                  cudaStream_t st);
 cudaError_t launch_chest_ls(const Geometry &g, int n_slots, const float2 *beam, const float2 *pilots, float2 *H,
                             cudaStream_t st);
 cudaError_t launch_mmse(const Geometry &g, int n_slots, const float2 *H, const float2 *beam, float2 *x_hat,
                         uint8_t *bits, uint32_t *status, cudaStream_t st);
+// Estimation fused into detection: the estimate is formed from the DMRS symbols of `beam` and the pilots
+// inside the detection kernel and never written to memory.
+cudaError_t launch_mmse_fused(const Geometry &g, int n_slots, const float2 *beam, const float2 *pilots,
+                              float2 *x_hat, uint8_t *bits, uint32_t *status, cudaStream_t st);
 
 // Mixed form: the tcgen05 beamforming GEMM. err_word (device, one uint32) gets bit 0 set if a bounded
 // wait of the kernel expired.

@@ -2,16 +2,23 @@
 // G = L L^H (Section V-C), forward solve L z = H^H y, back solve L^H x = z; then Gray hard decisions.
 //
 // GB300 mapping: a group of NL lanes owns one subcarrier (NL = layer class 2..32, a power of two), so a
-// warp detects 32/NL subcarriers at once. Lane i of a group owns row i of G, then row i of L, in
-// registers. The factorisation is right-looking: at column j, lane j's pivot is broadcast with a warp
-// shuffle, the lanes below scale their entry, and the trailing rows are updated with the column entries
-// broadcast from their owner lanes. The solves run the same way, one shuffle per unknown. L's columns
-// (needed by the back solve) are transposed once through shared memory. The estimate H of the warp's
-// subcarriers is staged in shared memory (rows padded by one element against bank conflicts) and reused
-// for the Gram and for H^H y of all 12 data symbols: G and L are formed once per subcarrier, which gives
-// the same result as forming them per data symbol because the estimate is constant over the slot.
-// Layers beyond n_layers (up to NL) are padded with identity rows and produce nothing.
-#include "internal.cuh"
+// warp detects 32/NL subcarriers at once; lane i of a group owns layer i.
+//   1. The estimate H of the warp's subcarriers is staged in shared memory (rows padded to an even stride):
+//      copied from the caller's buffer with cp.async, or - in the fused variant used by pusch_slot -
+//      formed right here from the DMRS symbols and the pilots (LS division + interpolation, the same
+//      arithmetic as the estimation kernel), so that the estimate never travels to HBM. In the fused
+//      variant the per-row pilot parameters are computed once per (subcarrier, layer), then the DMRS rows
+//      are read with coalesced loads.
+//   2. Lane i forms row i of G from 16-byte shared loads, then r_d = H^H y_d for every data symbol d,
+//      reading y_d with broadcast global loads (all lanes of a group read the same address).
+//   3. Right-looking Cholesky of G in registers: the pivot and column entries are broadcast by warp
+//      shuffles. L is written to shared memory over the (now dead) H tile.
+//   4. Forward and back solves for all data symbols together, one shuffle per unknown and symbol, L read
+//      from shared memory (row i for the forward solve, column i for the back solve).
+// G and L are formed once per subcarrier, which gives the same result as forming them per data symbol
+// because the estimate is constant over the slot. Layers beyond n_layers (up to NL) are padded with
+// identity rows and produce nothing.
+#include "chest_common.cuh"
 
 namespace pusch {
 namespace {
@@ -20,10 +27,21 @@ constexpr int kMmseWarps = 4;
 constexpr unsigned kFull = 0xffffffffu;
 
 struct MmseArgs {
-    int n_sc, n_beams, n_layers, n_sym, n_data, qam_bits;
+    int n_sc, n_beams, n_layers, n_sym, n_data, qam_bits, comb, dmrs0, dmrs1;
     float load;  // sigma^2 + extra loading
     int data_sym[16];
+    int port[32];
 };
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
 
 __device__ __forceinline__ float2 shfl2(float2 v, int src) {
     return make_float2(__shfl_sync(kFull, v.x, src), __shfl_sync(kFull, v.y, src));
@@ -36,27 +54,49 @@ __device__ __forceinline__ uint8_t demap(float2 x, int q) {
     return v;
 }
 
+// Shared memory per subcarrier, in float2 units: the H tile (NL rows of an even stride >= nb + 1), which
+// later holds L ([NL][NL + 1]); in the fused variant also NL row-parameter records.
+__host__ __device__ __forceinline__ int row_stride(int nb) { return (nb + 3) & ~1; }
 template <int NL>
-__host__ __device__ constexpr int mmse_warp_floats2(int nb) {
-    // H rows (padded), L transpose tile, one y vector per subcarrier
-    return (32 / NL) * NL * (nb + 1) + (32 / NL) * NL * (NL + 1) + (32 / NL) * nb;
+__host__ __device__ __forceinline__ int htile(int nb) {
+    const int a = NL * row_stride(nb), b = NL * (NL + 1) + NL / 2;  // L tile + 1/L[k][k] (NL floats)
+    const int m = a > b ? a : b;
+    return (m + 1) & ~1;
 }
 
-template <int NL>
-__global__ void __launch_bounds__(kMmseWarps * 32)
+// Pilot parameters of one (subcarrier, layer) row of the fused estimate.
+struct RowParam {
+    long long y0, y1;     // element offsets of the subcarrier's slot DMRS symbols in the beam grid
+    float2 q0lo, q1lo;    // 1 / pilot at lo on the two DMRS symbols
+    float2 q0hi, q1hi;    // 1 / pilot at hi
+    int lo, hi;           // neighbouring pilot subcarriers (lo == hi: hold)
+    float w;              // interpolation weight
+    int valid;            // 0: row is padding (layer >= n_layers or subcarrier out of range)
+};
+
+template <int NL, bool FUSED>
+__host__ __device__ __forceinline__ size_t warp_smem_bytes(int nb) {
+    return (size_t)(32 / NL) * (htile<NL>(nb) * sizeof(float2) + (FUSED ? NL * sizeof(RowParam) : 0));
+}
+
+// Register cap: five 4-warp CTAs per SM up to 8 layers, four for 16 layers (no spills), none for 32.
+template <int NL, int ND, bool FUSED>
+__global__ void __launch_bounds__(kMmseWarps * 32, NL <= 8 ? 5 : (NL == 16 ? 4 : 1))
 mmse_kernel(MmseArgs g, long long total_sc, const float2 *__restrict__ H, const float2 *__restrict__ beam,
-            float2 *__restrict__ xhat, uint8_t *__restrict__ bits, uint32_t *__restrict__ status) {
+            const float2 *__restrict__ pilots, float2 *__restrict__ xhat, uint8_t *__restrict__ bits,
+            uint32_t *__restrict__ status) {
     constexpr int SPW = 32 / NL;
-    extern __shared__ float2 smem[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int grp = lane / NL, i = lane - grp * NL;
     const int src0 = grp * NL;
     const int nl = g.n_layers, nb = g.n_beams, n_sc = g.n_sc;
-    const int hs = nb + 1;
+    const int nd = ND > 0 ? ND : g.n_data;
+    const int hs = row_stride(nb), ht = htile<NL>(nb);
 
-    float2 *Hsm = smem + (size_t)warp * mmse_warp_floats2<NL>(nb);
-    float2 *Lsm = Hsm + SPW * NL * hs;
-    float2 *ysm = Lsm + SPW * NL * (NL + 1);
+    unsigned char *wbase = smem_raw + (size_t)warp * warp_smem_bytes<NL, FUSED>(nb);
+    float2 *Ht = reinterpret_cast<float2 *>(wbase);  // [SPW][ht]
+    RowParam *rp = reinterpret_cast<RowParam *>(wbase + (size_t)SPW * ht * sizeof(float2));  // [SPW*NL]
 
     const long long sc0 = ((long long)blockIdx.x * kMmseWarps + warp) * SPW;  // first (slot*n_sc + a) of warp
     if (sc0 >= total_sc) return;                                              // whole warp idle
@@ -65,45 +105,156 @@ mmse_kernel(MmseArgs g, long long total_sc, const float2 *__restrict__ H, const 
     const long long slot = my_sc / n_sc;
     const int a = (int)(my_sc - slot * n_sc);
 
-    // ---- stage H of the warp's subcarriers: [SPW][NL][nb] (zero rows beyond n_layers / total_sc)
-    const int per_sc = nl * nb;
-    for (int idx = lane; idx < SPW * NL * nb; idx += 32) {
-        const int gg = idx / (NL * nb);
-        const int rem = idx - gg * NL * nb;
-        const int l = rem / nb, b = rem - l * nb;
-        float2 v = make_float2(0.f, 0.f);
-        if (l < nl && sc0 + gg < total_sc) v = __ldg(&H[(sc0 + gg) * per_sc + (long long)l * nb + b]);
-        Hsm[(gg * NL + l) * hs + b] = v;
+    // ---- 0. the 12 data-symbol rows of y this group reads in step 2b are pulled towards L2 now
+    if (valid && i < nd) {
+        const char *yrow = reinterpret_cast<const char *>(
+            beam + ((slot * g.n_sym + g.data_sym[i]) * (long long)n_sc + a) * nb);
+        for (int off = 0; off < nb * 8; off += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(yrow + off));
+    }
+
+    // ---- 1. channel estimate rows -> shared memory. Element e of the warp's [SPW*NL][nb] tile is handled
+    //         by lane e % 32; (row, b) advance incrementally (no division in the loop).
+    const int rows = SPW * NL;
+    if constexpr (!FUSED) {
+        int r = lane / nb, b = lane - (lane / nb) * nb;
+        const int step_r = 32 / nb, step_b = 32 - (32 / nb) * nb;
+        for (; r < rows;) {
+            const int gg = r / NL, l = r - gg * NL;  // NL is a power of two
+            float2 *dst = Ht + gg * ht + l * hs + b;
+            if (l < nl && sc0 + gg < total_sc)
+                cp_async8(dst, H + ((sc0 + gg) * nl + l) * (long long)nb + b);
+            else
+                *dst = make_float2(0.f, 0.f);
+            r += step_r;
+            b += step_b;
+            if (b >= nb) {
+                b -= nb;
+                ++r;
+            }
+        }
+        cp_async_wait_all();
+    } else {
+        {   // row parameters: lane = row (SPW*NL == 32)
+            RowParam q;
+            q.valid = (valid && i < nl) ? 1 : 0;
+            q.lo = q.hi = 0;
+            q.w = 0.f;
+            q.y0 = (slot * g.n_sym + g.dmrs0) * (long long)n_sc * nb;
+            q.y1 = (slot * g.n_sym + g.dmrs1) * (long long)n_sc * nb;
+            q.q0lo = q.q1lo = q.q0hi = q.q1hi = make_float2(1.f, 0.f);
+            if (q.valid) {
+                pilot_bracket(a, g.port[i], g.comb, n_sc, q.lo, q.hi);
+                const float2 *p0 = pilots + (slot * nl + i) * 2LL * n_sc;
+                const float2 *p1 = p0 + n_sc;
+                q.q0lo = pilot_inverse(__ldg(&p0[q.lo]));
+                q.q1lo = pilot_inverse(__ldg(&p1[q.lo]));
+                q.q0hi = pilot_inverse(__ldg(&p0[q.hi]));
+                q.q1hi = pilot_inverse(__ldg(&p1[q.hi]));
+                q.w = interp_weight(a, q.lo, q.hi);
+            }
+            rp[lane] = q;
+        }
+        __syncwarp();
+        int r = lane / nb, b = lane - (lane / nb) * nb;
+        const int step_r = 32 / nb, step_b = 32 - (32 / nb) * nb;
+        for (; r < rows;) {
+            const int gg = r / NL, l = r - gg * NL;
+            const RowParam &q = rp[r];
+            float2 h = make_float2(0.f, 0.f);
+            if (q.valid) {
+                const float2 *y0 = beam + q.y0;
+                const float2 *y1 = beam + q.y1;
+                h = ls_value(__ldg(&y0[(long long)q.lo * nb + b]), __ldg(&y1[(long long)q.lo * nb + b]), q.q0lo,
+                             q.q1lo);
+                if (q.hi != q.lo) {
+                    const float2 hh = ls_value(__ldg(&y0[(long long)q.hi * nb + b]),
+                                               __ldg(&y1[(long long)q.hi * nb + b]), q.q0hi, q.q1hi);
+                    h = interp(h, hh, q.w);
+                }
+            }
+            Ht[gg * ht + l * hs + b] = h;
+            r += step_r;
+            b += step_b;
+            if (b >= nb) {
+                b -= nb;
+                ++r;
+            }
+        }
     }
     __syncwarp();
 
-    const float2 *hrow = Hsm + (grp * NL + i) * hs;
-    const float2 *hgrp = Hsm + (grp * NL) * hs;
+    const float2 *hr = Ht + grp * ht + i * hs;  // own row
+    const float2 *hg = Ht + grp * ht;           // the group's rows
 
-    // ---- Gram row i: G[j] = sum_b conj(H[i][b]) H[j][b]
+    // ---- 2a. Gram row i: G[j] = sum_b conj(H[i][b]) H[j][b]
     float2 G[NL];
 #pragma unroll
     for (int j = 0; j < NL; ++j) G[j] = make_float2(0.f, 0.f);
-    for (int b = 0; b < nb; ++b) {
-        const float2 hi = hrow[b];
+    int b = 0;
+    for (; b + 1 < nb; b += 2) {
+        const float4 hv = *reinterpret_cast<const float4 *>(hr + b);
+        const float2 h0 = make_float2(hv.x, hv.y), h1 = make_float2(hv.z, hv.w);
 #pragma unroll
-        for (int j = 0; j < NL; ++j) cfmac(G[j], hi, hgrp[j * hs + b]);
+        for (int j = 0; j < NL; ++j) {
+            const float4 gv = *reinterpret_cast<const float4 *>(hg + j * hs + b);
+            cfmac(G[j], h0, make_float2(gv.x, gv.y));
+            cfmac(G[j], h1, make_float2(gv.z, gv.w));
+        }
+    }
+    if (b < nb) {
+        const float2 h0 = hr[b];
+#pragma unroll
+        for (int j = 0; j < NL; ++j) cfmac(G[j], h0, hg[j * hs + b]);
     }
 #pragma unroll
     for (int j = 0; j < NL; ++j)
         if (j == i) G[j] = (i < nl) ? make_float2(G[j].x + g.load, 0.f) : make_float2(1.f, 0.f);
 
-    // ---- Cholesky, right-looking, row i of L replaces row i of G
+    // ---- 2b. right-hand sides r_d = H^H y_d; y_d read with broadcast loads (same address in a group)
+    constexpr int NR = ND > 0 ? ND : 14;
+    float2 acc[NR];
+#pragma unroll
+    for (int d = 0; d < NR; ++d) acc[d] = make_float2(0.f, 0.f);
+    {
+        const long long sl = valid ? slot : 0;
+        const int aa = valid ? a : 0;
+        const float2 *yb = beam + (sl * g.n_sym * (long long)n_sc + aa) * nb;  // symbol s adds s*n_sc*nb
+        const long long sym_stride = (long long)n_sc * nb;
+        // 16-byte loads of y need an even beam count (16-byte aligned rows); odd counts take the scalar tail
+        const int nb2 = (nb & 1) ? 0 : nb;
+#pragma unroll 2
+        for (b = 0; b + 1 < nb2; b += 2) {
+            const float4 hv = *reinterpret_cast<const float4 *>(hr + b);
+            const float2 h0 = make_float2(hv.x, hv.y), h1 = make_float2(hv.z, hv.w);
+#pragma unroll
+            for (int d = 0; d < NR; ++d) {
+                if (ND > 0 || d < nd) {
+                    const float4 yv = __ldg(reinterpret_cast<const float4 *>(yb + g.data_sym[d] * sym_stride + b));
+                    cfmac(acc[d], h0, make_float2(yv.x, yv.y));
+                    cfmac(acc[d], h1, make_float2(yv.z, yv.w));
+                }
+            }
+        }
+        for (; b < nb; ++b) {
+            const float2 h0 = hr[b];
+#pragma unroll
+            for (int d = 0; d < NR; ++d)
+                if (ND > 0 || d < nd) cfmac(acc[d], h0, __ldg(yb + g.data_sym[d] * sym_stride + b));
+        }
+    }
+    __syncwarp();  // the H tile is reused for L below
+
+    // ---- 3. Cholesky, right-looking, row i of L replaces row i of G; then L -> shared memory
     bool bad = false;
     float dinv = 1.f;
 #pragma unroll
     for (int j = 0; j < NL; ++j) {
-        float d = __shfl_sync(kFull, G[j].x, src0 + j);
-        if (!(d > 0.f) || !isfinite(d)) {
+        float dj = __shfl_sync(kFull, G[j].x, src0 + j);
+        if (!(dj > 0.f) || !isfinite(dj)) {
             bad = true;
-            d = 1.f;
+            dj = 1.f;
         }
-        const float ljj = sqrtf(d);
+        const float ljj = sqrtf(dj);
         const float inv = 1.f / ljj;
         if (i > j) G[j] = cscale(G[j], inv);
         else if (i == j) G[j] = make_float2(ljj, 0.f);
@@ -119,15 +270,10 @@ mmse_kernel(MmseArgs g, long long total_sc, const float2 *__restrict__ H, const 
             }
         }
     }
-
-    // ---- transpose: Lc[k] = L[k][i] (k > i) for the back solve
-    float2 *lt = Lsm + grp * NL * (NL + 1);
+    float2 *lt = Ht + grp * ht;  // [NL][NL + 1]
 #pragma unroll
     for (int k = 0; k < NL; ++k) lt[i * (NL + 1) + k] = G[k];
     __syncwarp();
-    float2 Lc[NL];
-#pragma unroll
-    for (int k = 0; k < NL; ++k) Lc[k] = lt[k * (NL + 1) + i];
 
     if (valid && bad && i == 0) {
         atomicAdd(&status[1], 1u);
@@ -135,79 +281,85 @@ mmse_kernel(MmseArgs g, long long total_sc, const float2 *__restrict__ H, const 
         atomicOr(&status[0], (unsigned)PUSCH_STATUS_PIVOT);
     }
 
-    const int n_data = g.n_data;
+    // ---- 4. forward L z = r, then back L^H x = z, for all data symbols, in unit-diagonal form:
+    //         with D = diag(L), u = D z solves (L D^-1) u = r and x solves (D^-1 L^H) x = D^-1 z, so each step
+    //         broadcasts an unknown that is already final (no scaling before the shuffle). Lane i's unknown is
+    //         final at step i and not updated afterwards. dv[k] = 1 / L[k][k] sits after L in shared memory.
+    float *dv = reinterpret_cast<float *>(lt + NL * (NL + 1));
+    dv[i] = dinv;
+    __syncwarp();
+    const float2 *lrow = lt + i * (NL + 1);  // L[i][k]
+#pragma unroll
+    for (int k = 0; k < NL; ++k) {
+        const float2 m = cscale(lrow[k], dv[k]);  // L[i][k] / L[k][k]
+#pragma unroll
+        for (int d = 0; d < NR; ++d) {
+            if (ND > 0 || d < nd) {
+                const float2 uk = shfl2(acc[d], src0 + k);
+                if (i > k) cfms(acc[d], m, uk);
+            }
+        }
+    }
+#pragma unroll
+    for (int d = 0; d < NR; ++d) acc[d] = cscale(acc[d], dinv * dinv);  // z_i / L[i][i]
+#pragma unroll
+    for (int k = NL - 1; k >= 0; --k) {
+        const float2 lki = cscale(lt[k * (NL + 1) + i], dinv);  // L[k][i] / L[i][i]
+#pragma unroll
+        for (int d = 0; d < NR; ++d) {
+            if (ND > 0 || d < nd) {
+                const float2 xk = shfl2(acc[d], src0 + k);
+                if (i < k) {
+                    // acc -= conj(L[k][i] / L[i][i]) x_k
+                    acc[d].x -= lki.x * xk.x + lki.y * xk.y;
+                    acc[d].y -= lki.x * xk.y - lki.y * xk.x;
+                }
+            }
+        }
+    }
     bool nonfinite = false;
-    for (int d = 0; d < n_data; ++d) {
-        const int s = g.data_sym[d];
-        __syncwarp();
-        for (int idx = lane; idx < SPW * nb; idx += 32) {
-            const int gg = idx / nb, b = idx - gg * nb;
-            const long long sc = sc0 + gg;
-            float2 v = make_float2(0.f, 0.f);
-            if (sc < total_sc) {
-                const long long sl = sc / n_sc;
-                const long long aa = sc - sl * n_sc;
-                v = __ldg(&beam[((sl * g.n_sym + s) * n_sc + aa) * nb + b]);
-            }
-            ysm[gg * nb + b] = v;
-        }
-        __syncwarp();
-        const float2 *y = ysm + grp * nb;
-        float2 acc = make_float2(0.f, 0.f);
-        for (int b = 0; b < nb; ++b) cfmac(acc, hrow[b], y[b]);
-
-        // forward: L z = r
-        float2 zi = make_float2(0.f, 0.f);
+    if (valid && i < nl) {
+        const long long o0 = (slot * nl + i) * (long long)nd * n_sc + a;
 #pragma unroll
-        for (int k = 0; k < NL; ++k) {
-            const float2 zk = shfl2(cscale(acc, dinv), src0 + k);
-            if (i == k) zi = zk;
-            if (i > k) cfms(acc, G[k], zk);
-        }
-        // back: L^H x = z
-        acc = zi;
-        float2 xi = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int k = NL - 1; k >= 0; --k) {
-            const float2 xk = shfl2(cscale(acc, dinv), src0 + k);
-            if (i == k) xi = xk;
-            if (i < k) {
-                // acc -= conj(L[k][i]) x_k
-                acc.x -= Lc[k].x * xk.x + Lc[k].y * xk.y;
-                acc.y -= Lc[k].x * xk.y - Lc[k].y * xk.x;
+        for (int d = 0; d < NR; ++d) {
+            if (ND > 0 || d < nd) {
+                const float2 x = acc[d];
+                xhat[o0 + (long long)d * n_sc] = x;
+                bits[o0 + (long long)d * n_sc] = demap(x, g.qam_bits);
+                if (!isfinite(x.x) || !isfinite(x.y)) nonfinite = true;
             }
-        }
-        if (valid && i < nl) {
-            const long long o = ((slot * nl + i) * n_data + d) * (long long)n_sc + a;
-            xhat[o] = xi;
-            bits[o] = demap(xi, g.qam_bits);
-            if (!isfinite(xi.x) || !isfinite(xi.y)) nonfinite = true;
         }
     }
     if (__any_sync(kFull, nonfinite) && lane == 0) atomicOr(&status[0], (unsigned)PUSCH_STATUS_NONFINITE);
 }
 
-template <int NL>
-cudaError_t launch_nl(const MmseArgs &a, long long total_sc, const float2 *H, const float2 *beam, float2 *xhat,
-                      uint8_t *bits, uint32_t *status, cudaStream_t st) {
+template <int NL, int ND, bool FUSED>
+cudaError_t launch_nl(const MmseArgs &a, long long total_sc, const float2 *H, const float2 *beam,
+                      const float2 *pilots, float2 *xhat, uint8_t *bits, uint32_t *status, cudaStream_t st) {
     constexpr int SPW = 32 / NL;
-    const size_t smem = (size_t)kMmseWarps * mmse_warp_floats2<NL>(a.n_beams) * sizeof(float2);
+    const size_t smem = (size_t)kMmseWarps * warp_smem_bytes<NL, FUSED>(a.n_beams);
     const long long per_cta = (long long)kMmseWarps * SPW;
     const long long grid = (total_sc + per_cta - 1) / per_cta;
     if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    auto k = mmse_kernel<NL>;
+    auto k = mmse_kernel<NL, ND, FUSED>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k<<<(unsigned)grid, kMmseWarps * 32, smem, st>>>(a, total_sc, H, beam, xhat, bits, status);
+    k<<<(unsigned)grid, kMmseWarps * 32, smem, st>>>(a, total_sc, H, beam, pilots, xhat, bits, status);
     return cudaGetLastError();
 }
 
-}  // namespace
+template <int NL, bool FUSED>
+cudaError_t launch_nd(const MmseArgs &a, long long total_sc, const float2 *H, const float2 *beam,
+                      const float2 *pilots, float2 *xhat, uint8_t *bits, uint32_t *status, cudaStream_t st) {
+    if (a.n_data == 12) return launch_nl<NL, 12, FUSED>(a, total_sc, H, beam, pilots, xhat, bits, status, st);
+    return launch_nl<NL, 0, FUSED>(a, total_sc, H, beam, pilots, xhat, bits, status, st);
+}
 
-cudaError_t launch_mmse(const Geometry &g, int n_slots, const float2 *H, const float2 *beam, float2 *x_hat,
-                        uint8_t *bits, uint32_t *status, cudaStream_t st) {
+template <bool FUSED>
+cudaError_t launch_any(const Geometry &g, int n_slots, const float2 *H, const float2 *beam, const float2 *pilots,
+                       float2 *x_hat, uint8_t *bits, uint32_t *status, cudaStream_t st) {
     MmseArgs a;
     a.n_sc = g.n_sc;
     a.n_beams = g.n_beams;
@@ -215,16 +367,33 @@ cudaError_t launch_mmse(const Geometry &g, int n_slots, const float2 *H, const f
     a.n_sym = g.n_sym;
     a.n_data = g.n_data;
     a.qam_bits = g.qam_bits;
+    a.comb = g.comb;
+    a.dmrs0 = g.dmrs0;
+    a.dmrs1 = g.dmrs1;
     a.load = g.noise_var + g.loading;
     for (int d = 0; d < 16; ++d) a.data_sym[d] = g.data_sym[d];
+    for (int l = 0; l < 32; ++l) a.port[l] = g.port[l];
+    if (g.n_data > 14) return cudaErrorInvalidValue;
     const long long total_sc = (long long)n_slots * g.n_sc;
     if (total_sc == 0) return cudaSuccess;
     const int nl = g.n_layers;
-    if (nl <= 2) return launch_nl<2>(a, total_sc, H, beam, x_hat, bits, status, st);
-    if (nl <= 4) return launch_nl<4>(a, total_sc, H, beam, x_hat, bits, status, st);
-    if (nl <= 8) return launch_nl<8>(a, total_sc, H, beam, x_hat, bits, status, st);
-    if (nl <= 16) return launch_nl<16>(a, total_sc, H, beam, x_hat, bits, status, st);
-    return launch_nl<32>(a, total_sc, H, beam, x_hat, bits, status, st);
+    if (nl <= 2) return launch_nd<2, FUSED>(a, total_sc, H, beam, pilots, x_hat, bits, status, st);
+    if (nl <= 4) return launch_nd<4, FUSED>(a, total_sc, H, beam, pilots, x_hat, bits, status, st);
+    if (nl <= 8) return launch_nd<8, FUSED>(a, total_sc, H, beam, pilots, x_hat, bits, status, st);
+    if (nl <= 16) return launch_nd<16, FUSED>(a, total_sc, H, beam, pilots, x_hat, bits, status, st);
+    return launch_nd<32, FUSED>(a, total_sc, H, beam, pilots, x_hat, bits, status, st);
+}
+
+}  // namespace
+
+cudaError_t launch_mmse(const Geometry &g, int n_slots, const float2 *H, const float2 *beam, float2 *x_hat,
+                        uint8_t *bits, uint32_t *status, cudaStream_t st) {
+    return launch_any<false>(g, n_slots, H, beam, nullptr, x_hat, bits, status, st);
+}
+
+cudaError_t launch_mmse_fused(const Geometry &g, int n_slots, const float2 *beam, const float2 *pilots,
+                              float2 *x_hat, uint8_t *bits, uint32_t *status, cudaStream_t st) {
+    return launch_any<true>(g, n_slots, nullptr, beam, pilots, x_hat, bits, status, st);
 }
 
 }  // namespace pusch

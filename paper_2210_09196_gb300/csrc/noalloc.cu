@@ -114,7 +114,7 @@ extern "C" pusch_status pusch_slot_noalloc(const pusch_cell_cfg *cfg, int n_slot
     noalloc_status_kernel<<<1, 1, 0, s>>>(stat, tc_err);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return na_fail(PUSCH_ERR_CUDA, "pusch_slot_noalloc set-up launch", e);
-    if ((e = pusch::launch_fft(g, n_slots, time_in, freq, tw, s)) != cudaSuccess)
+    if ((e = pusch::launch_fft(g, n_slots, time_in, freq, tw, tc_err, s)) != cudaSuccess)
         return na_fail(PUSCH_ERR_CUDA, "pusch_slot_noalloc fft launch", e);
     if (g.form == PUSCH_FORM_MIXED)
         e = pusch::launch_beamform_tc(g, n_slots, static_cast<const __half *>(freq), static_cast<const float2 *>(W),

@@ -137,6 +137,34 @@ def test_stage_parity_over_shapes(orc, shape, in_fp16):
     rx.close()
 
 
+def test_fused_chain_equals_staged_estimation_and_detection(orc, small_slots):
+    """pusch_slot forms the estimate inside the detector; it must equal pusch_chest_ls + pusch_mmse_detect."""
+    for cell in (synth.SMALL_FP32, synth.DEPLOY.with_(n_rx=16, n_beams=16, n_layers=8, n_fft=1024, n_sc=600)):
+        slots = small_slots if cell is synth.SMALL_FP32 else synth.make_slots(cell, 2)
+        rx = host.Receiver(host.cfg_for(cell), max_slots=len(slots))
+        freq, beam, H, x, b, st = run_stages(rx, slots, slots[0].W)
+        x2, b2, st2 = rx.slot(host.time_tensor(slots), host.beam_tensor(slots[0].W), host.pilot_tensor(slots))
+        torch.cuda.synchronize()
+        assert nrel(c128(x2), c128(x)) < 1e-6
+        assert torch.equal(st, st2)
+        assert (b2 != b).float().mean().item() < 1e-4
+        rx.close()
+
+
+def test_profile_hooks_time_pusch_slot(orc, small_slots):
+    cell = synth.SMALL_FP32
+    rx = host.Receiver(host.cfg_for(cell), max_slots=3)
+    args = (host.time_tensor(small_slots), host.beam_tensor(small_slots[0].W), host.pilot_tensor(small_slots))
+    B.pusch_profile_start(rx.h, 2)
+    for _ in range(3):
+        rx.slot(*args)
+    ms, n = B.pusch_profile_read(rx.h)
+    assert n == 2 and all(v > 0 for v in ms.values()) and set(ms) == {"fft", "beamform", "detect"}
+    ms, n = B.pusch_profile_read(rx.h)
+    assert n == 0 and all(v == 0 for v in ms.values())
+    rx.close()
+
+
 def test_zero_slots_is_a_no_op(orc):
     cell = synth.SMALL_FP32
     rx = host.Receiver(host.cfg_for(cell), max_slots=1)
