@@ -143,12 +143,12 @@ pusch_status pusch_mmse_detect(pusch_handle *h, int n_slots, const void *H_hat, 
                                uint8_t *bits, uint32_t *status, void *stream);
 
 /*
- * The whole chain for n_slots slots (Fig. 1): OFDM FFT -> beamforming -> LS estimation + MMSE detection.
- * The FFT output and the beamformed grid live in the handle's workspace (n_slots <= max_slots); the
- * channel estimate is formed inside the detection kernel from the DMRS symbols and never stored, with
- * the same arithmetic as pusch_chest_ls (so the result equals pusch_chest_ls + pusch_mmse_detect).
- * Three kernels (plus a one-thread status reset). time_in, W, pilots, x_hat, bits, status: as in the
- * stage entry points.
+ * The whole chain for n_slots slots (Fig. 1): OFDM FFT -> beamforming -> LS division at the pilot
+ * subcarriers -> interpolation + MMSE detection. The FFT output, the beamformed grid and the table of LS
+ * values at the pilot subcarriers live in the handle's workspace (n_slots <= max_slots); the interpolated
+ * estimate is formed inside the detection kernel and never stored, with the same arithmetic as
+ * pusch_chest_ls (so the result equals pusch_chest_ls + pusch_mmse_detect). Four kernels plus a
+ * one-thread status reset. time_in, W, pilots, x_hat, bits, status: as in the stage entry points.
  */
 pusch_status pusch_slot(pusch_handle *h, int n_slots, const void *time_in, const void *W, const void *pilots,
                         void *x_hat, uint8_t *bits, uint32_t *status, void *stream);
@@ -190,10 +190,10 @@ pusch_status pusch_slot_noalloc(const pusch_cell_cfg *cfg, int n_slots, const vo
 /*
  * Per-stage device timing of pusch_slot (measurement aid; no counterpart in the paper).
  * pusch_profile_start arms timing for the next max_calls calls of pusch_slot on this handle: each call
- * records CUDA events on its stream before the FFT, after the FFT, after beamforming and after the fused
- * estimation + detection. pusch_profile_read waits for the last recorded event, writes the summed
- * milliseconds of the three stages to stage_ms[0..2] (n_stages >= 3) and the number of timed calls to
- * *n_calls, and disarms timing.
+ * records CUDA events on its stream before the FFT, after the FFT, after beamforming, after the LS pilot
+ * table and after the detector. pusch_profile_read waits for the last recorded event, writes the summed
+ * milliseconds of the four stages (FFT, beamforming, LS pilot table, detection) to stage_ms[0..3]
+ * (n_stages >= 4) and the number of timed calls to *n_calls, and disarms timing.
  */
 pusch_status pusch_profile_start(pusch_handle *h, int max_calls);
 pusch_status pusch_profile_read(pusch_handle *h, float *stage_ms, int n_stages, int *n_calls);

@@ -188,7 +188,7 @@ def pusch_slot_noalloc(cfg: pusch_cell_cfg, n_slots, time_in, W, pilots, x_hat, 
                                     _ptr(bits), _ptr(status), _stream(stream)), "pusch_slot_noalloc")
 
 
-SLOT_STAGES = ("fft", "beamform", "detect")
+SLOT_STAGES = ("fft", "beamform", "ls", "detect")
 
 
 def pusch_profile_start(h, max_calls: int) -> None:

@@ -18,6 +18,7 @@ struct pusch_handle {
     uint32_t *kernel_err = nullptr;   // bounded-wait expiry flags of the tensor-core kernel
     void *freq = nullptr;           // workspace: FFT output
     float2 *beam = nullptr;         // workspace: beamformed grid
+    float2 *ls = nullptr;           // workspace: LS values at the pilot subcarriers
     uint32_t *status_sink = nullptr;  // status words used when the caller passes NULL
     // staging for pusch_slot_host (allocated on first use)
     void *h_time = nullptr;
@@ -35,7 +36,7 @@ namespace {
 
 thread_local char g_err[512] = "";
 
-constexpr int kSlotStages = 3;  // pusch_slot launches: FFT, beamforming, fused estimation + detection
+constexpr int kSlotStages = 4;  // pusch_slot stages: FFT, beamforming, LS pilot table, detection
 
 pusch_status fail(pusch_status st, const char *fmt, ...) {
     va_list ap;
@@ -95,6 +96,9 @@ size_t freq_bytes(const pusch::Geometry &g, int n_slots) {
 size_t beam_bytes(const pusch::Geometry &g, int n_slots) {
     return (size_t)n_slots * g.n_sym * g.n_sc * g.n_beams * sizeof(float2);
 }
+size_t ls_bytes(const pusch::Geometry &g, int n_slots) {
+    return (size_t)n_slots * g.n_layers * pusch::ls_pilots_per_layer(g) * g.n_beams * sizeof(float2);
+}
 size_t time_bytes(const pusch::Geometry &g, int n_slots) {
     return (size_t)n_slots * g.n_sym * g.n_rx * g.n_fft * (g.in_fp16 ? 4 : 8);
 }
@@ -108,7 +112,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 size_t workspace_bytes(const pusch::Geometry &g, int max_slots) {
     size_t b = align256(g.n_fft * sizeof(float2));
-    b += align256(freq_bytes(g, max_slots)) + align256(beam_bytes(g, max_slots));
+    b += align256(freq_bytes(g, max_slots)) + align256(beam_bytes(g, max_slots)) + align256(ls_bytes(g, max_slots));
     return b;
 }
 
@@ -211,6 +215,7 @@ pusch_status pusch_create(pusch_handle **out, const pusch_cell_cfg *cfg, int max
     if ((e = cudaMemset(h->kernel_err, 0, 16)) != cudaSuccess) goto cuda_error;
     if ((e = cudaMalloc(&h->freq, freq_bytes(g, max_slots))) != cudaSuccess) goto cuda_error;
     if ((e = cudaMalloc((void **)&h->beam, beam_bytes(g, max_slots))) != cudaSuccess) goto cuda_error;
+    if ((e = cudaMalloc((void **)&h->ls, ls_bytes(g, max_slots))) != cudaSuccess) goto cuda_error;
     if ((e = cudaMalloc((void **)&h->status_sink, 4 * sizeof(uint32_t))) != cudaSuccess) goto cuda_error;
     *out = h;
     return ok();
@@ -227,6 +232,7 @@ pusch_status pusch_destroy(pusch_handle *h) {
     cudaFree(h->kernel_err);
     cudaFree(h->freq);
     cudaFree(h->beam);
+    cudaFree(h->ls);
     cudaFree(h->status_sink);
     cudaFree(h->h_time);
     cudaFree(h->h_pilots);
@@ -313,10 +319,12 @@ pusch_status pusch_slot(pusch_handle *h, int n_slots, const void *time_in, const
     if (ev) cudaEventRecord(ev[2], s);
     uint32_t *stat = status ? status : h->status_sink;
     if ((st = reset_status(stat, s)) != PUSCH_OK) return st;
-    cudaError_t e = pusch::launch_mmse_fused(h->geo, n_slots, h->beam, (const float2 *)pilots, (float2 *)x_hat, bits,
-                                             stat, s);
-    if (e != cudaSuccess) return cuda_fail(e, "fused estimation + detection launch");
+    cudaError_t e = pusch::launch_ls_pilots(h->geo, n_slots, h->beam, (const float2 *)pilots, h->ls, s);
+    if (e != cudaSuccess) return cuda_fail(e, "LS pilot table launch");
     if (ev) cudaEventRecord(ev[3], s);
+    e = pusch::launch_mmse_fused(h->geo, n_slots, h->beam, h->ls, (float2 *)x_hat, bits, stat, s);
+    if (e != cudaSuccess) return cuda_fail(e, "fused estimation + detection launch");
+    if (ev) cudaEventRecord(ev[4], s);
     return ok();
 }
 

@@ -49,7 +49,57 @@ chest_ls_kernel(ChestArgs g, long long total, const float2 *__restrict__ beam, c
     }
 }
 
+// LS estimate at every pilot subcarrier of every layer (the element-wise division alone):
+// ls[slot][l][k][b] for the layer's k-th pilot q = port[l] + k * comb (k < kmax; zero past n_sc).
+__global__ void __launch_bounds__(256)
+ls_pilots_kernel(ChestArgs g, int kmax, long long total, const float2 *__restrict__ beam,
+                 const float2 *__restrict__ pilots, float2 *__restrict__ ls) {
+    const long long per_l = (long long)kmax * g.n_beams;
+    const long long per_slot = per_l * g.n_layers;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long slot = idx / per_slot;
+        long long rem = idx - slot * per_slot;
+        const int l = (int)(rem / per_l);
+        rem -= (long long)l * per_l;
+        const int k = (int)(rem / g.n_beams);
+        const int b = (int)(rem - (long long)k * g.n_beams);
+        const int q = g.port[l] + k * g.comb;
+        float2 v = make_float2(0.f, 0.f);
+        if (q < g.n_sc) {
+            const float2 *y0 = beam + (slot * g.n_sym + g.dmrs0) * (long long)g.n_sc * g.n_beams;
+            const float2 *y1 = beam + (slot * g.n_sym + g.dmrs1) * (long long)g.n_sc * g.n_beams;
+            const float2 *p0 = pilots + (slot * g.n_layers + l) * 2LL * g.n_sc;
+            v = ls_value(__ldg(&y0[(long long)q * g.n_beams + b]), __ldg(&y1[(long long)q * g.n_beams + b]),
+                         pilot_inverse(__ldg(&p0[q])), pilot_inverse(__ldg(&p0[g.n_sc + q])));
+        }
+        ls[idx] = v;
+    }
+}
+
 }  // namespace
+
+int ls_pilots_per_layer(const Geometry &g) { return (g.n_sc + g.comb - 1) / g.comb; }
+
+cudaError_t launch_ls_pilots(const Geometry &g, int n_slots, const float2 *beam, const float2 *pilots, float2 *ls,
+                             cudaStream_t st) {
+    ChestArgs a;
+    a.n_sc = g.n_sc;
+    a.n_beams = g.n_beams;
+    a.n_layers = g.n_layers;
+    a.comb = g.comb;
+    a.n_sym = g.n_sym;
+    a.dmrs0 = g.dmrs0;
+    a.dmrs1 = g.dmrs1;
+    for (int l = 0; l < 32; ++l) a.port[l] = g.port[l];
+    const int kmax = ls_pilots_per_layer(g);
+    const long long total = (long long)n_slots * g.n_layers * kmax * g.n_beams;
+    if (total == 0) return cudaSuccess;
+    long long blocks = (total + 255) / 256;
+    if (blocks > 152LL * 32) blocks = 152LL * 32;
+    ls_pilots_kernel<<<(unsigned)blocks, 256, 0, st>>>(a, kmax, total, beam, pilots, ls);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_chest_ls(const Geometry &g, int n_slots, const float2 *beam, const float2 *pilots, float2 *H,
                             cudaStream_t st) {

@@ -63,9 +63,13 @@ cudaError_t launch_chest_ls(const Geometry &g, int n_slots, const float2 *beam, 
                             cudaStream_t st);
 cudaError_t launch_mmse(const Geometry &g, int n_slots, const float2 *H, const float2 *beam, float2 *x_hat,
                         uint8_t *bits, uint32_t *status, cudaStream_t st);
-// Estimation fused into detection: the estimate is formed from the DMRS symbols of `beam` and the pilots
-// inside the detection kernel and never written to memory.
-cudaError_t launch_mmse_fused(const Geometry &g, int n_slots, const float2 *beam, const float2 *pilots,
+// LS values at the pilot subcarriers: ls[slot][l][k][b] for pilot q = port[l] + k * comb, k < kmax.
+int ls_pilots_per_layer(const Geometry &g);
+cudaError_t launch_ls_pilots(const Geometry &g, int n_slots, const float2 *beam, const float2 *pilots, float2 *ls,
+                             cudaStream_t st);
+// Estimation fused into detection: the estimate is interpolated from the LS pilot table inside the
+// detection kernel and never written to memory.
+cudaError_t launch_mmse_fused(const Geometry &g, int n_slots, const float2 *beam, const float2 *ls,
                               float2 *x_hat, uint8_t *bits, uint32_t *status, cudaStream_t st);
 
 // Mixed form: the tcgen05 beamforming GEMM. err_word (device, one uint32) gets bit 0 set if a bounded

@@ -5,12 +5,12 @@
 // warp detects 32/NL subcarriers at once; lane i of a group owns layer i.
 //   1. The estimate H of the warp's subcarriers is staged in shared memory (rows padded to an even stride):
 //      copied from the caller's buffer with cp.async, or - in the fused variant used by pusch_slot -
-//      formed right here from the DMRS symbols and the pilots (LS division + interpolation, the same
-//      arithmetic as the estimation kernel), so that the estimate never travels to HBM. In the fused
-//      variant the per-row pilot parameters are computed once per (subcarrier, layer), then the DMRS rows
-//      are read with coalesced loads.
-//   2. Lane i forms row i of G from 16-byte shared loads, then r_d = H^H y_d for every data symbol d,
-//      reading y_d with broadcast global loads (all lanes of a group read the same address).
+//      interpolated right here from the table of LS values at the pilot subcarriers (the same arithmetic
+//      as the estimation kernel), so that the full estimate never travels to HBM. The per-row pilot
+//      brackets are computed once per (subcarrier, layer), then the LS rows are read with coalesced loads.
+//   0. The data-symbol vectors y_d of the warp's subcarriers are copied to shared memory with cp.async
+//      first, so that their latency overlaps steps 1-2a.
+//   2. Lane i forms row i of G from 16-byte shared loads, then r_d = H^H y_d for every data symbol d.
 //   3. Right-looking Cholesky of G in registers: the pivot and column entries are broadcast by warp
 //      shuffles. L is written to shared memory over the (now dead) H tile.
 //   4. Forward and back solves for all data symbols together, one shuffle per unknown and symbol, L read
@@ -23,11 +23,11 @@
 namespace pusch {
 namespace {
 
-constexpr int kMmseWarps = 4;
+constexpr int kMmseWarps = 2;
 constexpr unsigned kFull = 0xffffffffu;
 
 struct MmseArgs {
-    int n_sc, n_beams, n_layers, n_sym, n_data, qam_bits, comb, dmrs0, dmrs1;
+    int n_sc, n_beams, n_layers, n_sym, n_data, qam_bits, comb, dmrs0, dmrs1, kmax;
     float load;  // sigma^2 + extra loading
     int data_sym[16];
     int port[32];
@@ -64,26 +64,28 @@ __host__ __device__ __forceinline__ int htile(int nb) {
     return (m + 1) & ~1;
 }
 
-// Pilot parameters of one (subcarrier, layer) row of the fused estimate.
+// Interpolation parameters of one (subcarrier, layer) row of the fused estimate.
 struct RowParam {
-    long long y0, y1;     // element offsets of the subcarrier's slot DMRS symbols in the beam grid
-    float2 q0lo, q1lo;    // 1 / pilot at lo on the two DMRS symbols
-    float2 q0hi, q1hi;    // 1 / pilot at hi
-    int lo, hi;           // neighbouring pilot subcarriers (lo == hi: hold)
+    long long lo, hi;     // element offsets of the LS rows of the neighbouring pilots (lo == hi: hold)
     float w;              // interpolation weight
     int valid;            // 0: row is padding (layer >= n_layers or subcarrier out of range)
 };
 
 template <int NL, bool FUSED>
-__host__ __device__ __forceinline__ size_t warp_smem_bytes(int nb) {
-    return (size_t)(32 / NL) * (htile<NL>(nb) * sizeof(float2) + (FUSED ? NL * sizeof(RowParam) : 0));
+__host__ __device__ __forceinline__ size_t warp_smem_bytes(int nb, int nd) {
+    return (size_t)(32 / NL) *
+           ((htile<NL>(nb) + (size_t)nd * row_stride(nb)) * sizeof(float2) + (FUSED ? NL * sizeof(RowParam) : 0));
+}
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
 }
 
 // Register cap: five 4-warp CTAs per SM up to 8 layers, four for 16 layers (no spills), none for 32.
 template <int NL, int ND, bool FUSED>
 __global__ void __launch_bounds__(kMmseWarps * 32, NL <= 8 ? 5 : (NL == 16 ? 4 : 1))
 mmse_kernel(MmseArgs g, long long total_sc, const float2 *__restrict__ H, const float2 *__restrict__ beam,
-            const float2 *__restrict__ pilots, float2 *__restrict__ xhat, uint8_t *__restrict__ bits,
+            const float2 *__restrict__ ls, float2 *__restrict__ xhat, uint8_t *__restrict__ bits,
             uint32_t *__restrict__ status) {
     constexpr int SPW = 32 / NL;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -94,9 +96,10 @@ mmse_kernel(MmseArgs g, long long total_sc, const float2 *__restrict__ H, const 
     const int nd = ND > 0 ? ND : g.n_data;
     const int hs = row_stride(nb), ht = htile<NL>(nb);
 
-    unsigned char *wbase = smem_raw + (size_t)warp * warp_smem_bytes<NL, FUSED>(nb);
+    unsigned char *wbase = smem_raw + (size_t)warp * warp_smem_bytes<NL, FUSED>(nb, nd);
     float2 *Ht = reinterpret_cast<float2 *>(wbase);  // [SPW][ht]
-    RowParam *rp = reinterpret_cast<RowParam *>(wbase + (size_t)SPW * ht * sizeof(float2));  // [SPW*NL]
+    float2 *Yt = Ht + SPW * ht;                      // [SPW][nd][hs]
+    RowParam *rp = reinterpret_cast<RowParam *>(Yt + (size_t)SPW * nd * hs);  // [SPW*NL]
 
     const long long sc0 = ((long long)blockIdx.x * kMmseWarps + warp) * SPW;  // first (slot*n_sc + a) of warp
     if (sc0 >= total_sc) return;                                              // whole warp idle
@@ -105,11 +108,36 @@ mmse_kernel(MmseArgs g, long long total_sc, const float2 *__restrict__ H, const 
     const long long slot = my_sc / n_sc;
     const int a = (int)(my_sc - slot * n_sc);
 
-    // ---- 0. the 12 data-symbol rows of y this group reads in step 2b are pulled towards L2 now
-    if (valid && i < nd) {
-        const char *yrow = reinterpret_cast<const char *>(
-            beam + ((slot * g.n_sym + g.data_sym[i]) * (long long)n_sc + a) * nb);
-        for (int off = 0; off < nb * 8; off += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(yrow + off));
+    // ---- 0. the data-symbol rows y_d of the warp's subcarriers -> shared memory, asynchronously (cp.async,
+    //         16-byte pieces when the beam count is even); waited for just before step 2b.
+    {
+        const bool wide = (nb & 1) == 0;
+        const int cpr = wide ? nb >> 1 : nb;  // pieces per row
+        int row = lane / cpr, c = lane - (lane / cpr) * cpr;
+        const int step_r = 32 / cpr, step_c = 32 - (32 / cpr) * cpr;
+        for (; row < SPW * nd;) {
+            const int gg = row / nd, d = row - gg * nd;
+            const long long sc = sc0 + gg;
+            float2 *dst = Yt + (gg * nd + d) * hs + (wide ? 2 * c : c);
+            if (sc < total_sc) {
+                const long long sl = sc / n_sc, aa = sc - sl * n_sc;
+                const float2 *src = beam + ((sl * g.n_sym + g.data_sym[d]) * n_sc + aa) * nb + (wide ? 2 * c : c);
+                if (wide)
+                    cp_async16(dst, src);
+                else
+                    cp_async8(dst, src);
+            } else {
+                dst[0] = make_float2(0.f, 0.f);
+                if (wide) dst[1] = make_float2(0.f, 0.f);
+            }
+            row += step_r;
+            c += step_c;
+            if (c >= cpr) {
+                c -= cpr;
+                ++row;
+            }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
     }
 
     // ---- 1. channel estimate rows -> shared memory. Element e of the warp's [SPW*NL][nb] tile is handled
@@ -132,25 +160,20 @@ mmse_kernel(MmseArgs g, long long total_sc, const float2 *__restrict__ H, const 
                 ++r;
             }
         }
-        cp_async_wait_all();
+        cp_async_wait_all();  // the H tile (and the earlier y group)
     } else {
         {   // row parameters: lane = row (SPW*NL == 32)
             RowParam q;
             q.valid = (valid && i < nl) ? 1 : 0;
             q.lo = q.hi = 0;
             q.w = 0.f;
-            q.y0 = (slot * g.n_sym + g.dmrs0) * (long long)n_sc * nb;
-            q.y1 = (slot * g.n_sym + g.dmrs1) * (long long)n_sc * nb;
-            q.q0lo = q.q1lo = q.q0hi = q.q1hi = make_float2(1.f, 0.f);
             if (q.valid) {
-                pilot_bracket(a, g.port[i], g.comb, n_sc, q.lo, q.hi);
-                const float2 *p0 = pilots + (slot * nl + i) * 2LL * n_sc;
-                const float2 *p1 = p0 + n_sc;
-                q.q0lo = pilot_inverse(__ldg(&p0[q.lo]));
-                q.q1lo = pilot_inverse(__ldg(&p1[q.lo]));
-                q.q0hi = pilot_inverse(__ldg(&p0[q.hi]));
-                q.q1hi = pilot_inverse(__ldg(&p1[q.hi]));
-                q.w = interp_weight(a, q.lo, q.hi);
+                int lo, hi;
+                pilot_bracket(a, g.port[i], g.comb, n_sc, lo, hi);
+                const long long base = (slot * nl + i) * (long long)g.kmax * nb;
+                q.lo = base + (long long)((lo - g.port[i]) / g.comb) * nb;
+                q.hi = base + (long long)((hi - g.port[i]) / g.comb) * nb;
+                q.w = interp_weight(a, lo, hi);
             }
             rp[lane] = q;
         }
@@ -162,15 +185,8 @@ mmse_kernel(MmseArgs g, long long total_sc, const float2 *__restrict__ H, const 
             const RowParam &q = rp[r];
             float2 h = make_float2(0.f, 0.f);
             if (q.valid) {
-                const float2 *y0 = beam + q.y0;
-                const float2 *y1 = beam + q.y1;
-                h = ls_value(__ldg(&y0[(long long)q.lo * nb + b]), __ldg(&y1[(long long)q.lo * nb + b]), q.q0lo,
-                             q.q1lo);
-                if (q.hi != q.lo) {
-                    const float2 hh = ls_value(__ldg(&y0[(long long)q.hi * nb + b]),
-                                               __ldg(&y1[(long long)q.hi * nb + b]), q.q0hi, q.q1hi);
-                    h = interp(h, hh, q.w);
-                }
+                h = __ldg(&ls[q.lo + b]);
+                if (q.hi != q.lo) h = interp(h, __ldg(&ls[q.hi + b]), q.w);
             }
             Ht[gg * ht + l * hs + b] = h;
             r += step_r;
@@ -210,36 +226,32 @@ mmse_kernel(MmseArgs g, long long total_sc, const float2 *__restrict__ H, const 
     for (int j = 0; j < NL; ++j)
         if (j == i) G[j] = (i < nl) ? make_float2(G[j].x + g.load, 0.f) : make_float2(1.f, 0.f);
 
-    // ---- 2b. right-hand sides r_d = H^H y_d; y_d read with broadcast loads (same address in a group)
+    // ---- 2b. right-hand sides r_d = H^H y_d (y_d from the shared tile; a group reads one address)
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncwarp();
     constexpr int NR = ND > 0 ? ND : 14;
     float2 acc[NR];
 #pragma unroll
     for (int d = 0; d < NR; ++d) acc[d] = make_float2(0.f, 0.f);
     {
-        const long long sl = valid ? slot : 0;
-        const int aa = valid ? a : 0;
-        const float2 *yb = beam + (sl * g.n_sym * (long long)n_sc + aa) * nb;  // symbol s adds s*n_sc*nb
-        const long long sym_stride = (long long)n_sc * nb;
-        // 16-byte loads of y need an even beam count (16-byte aligned rows); odd counts take the scalar tail
-        const int nb2 = (nb & 1) ? 0 : nb;
-#pragma unroll 2
-        for (b = 0; b + 1 < nb2; b += 2) {
+        const float2 *yt = Yt + grp * nd * hs;
+        for (b = 0; b + 1 < nb; b += 2) {
             const float4 hv = *reinterpret_cast<const float4 *>(hr + b);
             const float2 h0 = make_float2(hv.x, hv.y), h1 = make_float2(hv.z, hv.w);
 #pragma unroll
             for (int d = 0; d < NR; ++d) {
                 if (ND > 0 || d < nd) {
-                    const float4 yv = __ldg(reinterpret_cast<const float4 *>(yb + g.data_sym[d] * sym_stride + b));
+                    const float4 yv = *reinterpret_cast<const float4 *>(yt + d * hs + b);
                     cfmac(acc[d], h0, make_float2(yv.x, yv.y));
                     cfmac(acc[d], h1, make_float2(yv.z, yv.w));
                 }
             }
         }
-        for (; b < nb; ++b) {
+        if (b < nb) {
             const float2 h0 = hr[b];
 #pragma unroll
             for (int d = 0; d < NR; ++d)
-                if (ND > 0 || d < nd) cfmac(acc[d], h0, __ldg(yb + g.data_sym[d] * sym_stride + b));
+                if (ND > 0 || d < nd) cfmac(acc[d], h0, yt[d * hs + b]);
         }
     }
     __syncwarp();  // the H tile is reused for L below
@@ -337,7 +349,7 @@ template <int NL, int ND, bool FUSED>
 cudaError_t launch_nl(const MmseArgs &a, long long total_sc, const float2 *H, const float2 *beam,
                       const float2 *pilots, float2 *xhat, uint8_t *bits, uint32_t *status, cudaStream_t st) {
     constexpr int SPW = 32 / NL;
-    const size_t smem = (size_t)kMmseWarps * warp_smem_bytes<NL, FUSED>(a.n_beams);
+    const size_t smem = (size_t)kMmseWarps * warp_smem_bytes<NL, FUSED>(a.n_beams, ND > 0 ? ND : a.n_data);
     const long long per_cta = (long long)kMmseWarps * SPW;
     const long long grid = (total_sc + per_cta - 1) / per_cta;
     if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
@@ -371,6 +383,7 @@ cudaError_t launch_any(const Geometry &g, int n_slots, const float2 *H, const fl
     a.dmrs0 = g.dmrs0;
     a.dmrs1 = g.dmrs1;
     a.load = g.noise_var + g.loading;
+    a.kmax = ls_pilots_per_layer(g);
     for (int d = 0; d < 16; ++d) a.data_sym[d] = g.data_sym[d];
     for (int l = 0; l < 32; ++l) a.port[l] = g.port[l];
     if (g.n_data > 14) return cudaErrorInvalidValue;
@@ -391,9 +404,9 @@ cudaError_t launch_mmse(const Geometry &g, int n_slots, const float2 *H, const f
     return launch_any<false>(g, n_slots, H, beam, nullptr, x_hat, bits, status, st);
 }
 
-cudaError_t launch_mmse_fused(const Geometry &g, int n_slots, const float2 *beam, const float2 *pilots,
+cudaError_t launch_mmse_fused(const Geometry &g, int n_slots, const float2 *beam, const float2 *ls,
                               float2 *x_hat, uint8_t *bits, uint32_t *status, cudaStream_t st) {
-    return launch_any<true>(g, n_slots, nullptr, beam, pilots, x_hat, bits, status, st);
+    return launch_any<true>(g, n_slots, nullptr, beam, ls, x_hat, bits, status, st);
 }
 
 }  // namespace pusch

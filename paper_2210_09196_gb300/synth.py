@@ -206,3 +206,145 @@ def make_slot(cfg: CellConfig, slot_index: int = 0, seed: int | None = None) -> 
 
 def make_slots(cfg: CellConfig, n: int, first: int = 0, seed: int | None = None) -> list[Slot]:
     return [make_slot(cfg, first + i, seed) for i in range(n)]
+
+
+# ------------------------------------------------------------------------------------------------------------
+# Ragged multi-cell batches: several cells (antennas 32 or 64, FFT 2048 or 4096), each with users on seeded
+# random contiguous PRB ranges, 1-4 layers, QPSK or 16-QAM and their own SNR. A cell's DMRS comb has N_B/2
+# ports; overlapping users get disjoint contiguous port ranges (see _draw_users).
+
+@dataclass
+class RaggedCell:
+    n_rx: int
+    n_fft: int
+    n_sc: int
+    n_beams: int
+    noise_var: float
+    comb: int = 1                 # DMRS comb size = number of ports of the cell (N_B / 2)
+
+
+@dataclass
+class RaggedUser:
+    cell: int
+    sc_start: int
+    sc_count: int
+    n_layers: int
+    port0: int
+    qam_bits: int
+    snr_db: float
+
+
+@dataclass
+class RaggedSlot:
+    cells: list
+    users: list
+    time_in: list = field(repr=False)       # per cell [14, n_rx, n_fft, 2] float16
+    W: list = field(repr=False)             # per cell [n_rx, n_beams] complex64
+    pilots: list = field(repr=False)        # per user [n_layers, 2, sc_count] complex64 (zero off its comb)
+    x: list = field(repr=False)             # per user [n_layers, 12, sc_count] complex128 (truth)
+    bits: list = field(repr=False)          # per user [n_layers, 12, sc_count] uint8 packed (truth)
+
+    def time_as_complex128(self, c: int) -> np.ndarray:
+        t = self.time_in[c]
+        return t[..., 0].astype(np.float64) + 1j * t[..., 1].astype(np.float64)
+
+
+RAGGED_SEED = 3
+
+
+def _draw_users(rng, cells, n_users, max_tries=10000):
+    """Users are drawn one at a time. A cell's comb (port count) is N_B/2; a user takes the lowest contiguous
+    ports that no user overlapping its range already uses. The user is redrawn while its range would make
+    more than N_B/2 layers overlap, no such ports exist, or its range misses a pilot of one of its ports."""
+    cell_of = [int(rng.integers(0, len(cells))) for _ in range(n_users)]
+    out = []
+    placed = [[] for _ in cells]  # (a0, a1, p0, L)
+    for c in cell_of:
+        cell = cells[c]
+        cap = cell.n_beams // 2
+        cell.comb = cap
+        n_prb_max = cell.n_sc // 12
+        for _ in range(max_tries):
+            n_prb = int(rng.integers(1, n_prb_max + 1))
+            a0 = 12 * int(rng.integers(0, n_prb_max - n_prb + 1))
+            a1 = a0 + 12 * n_prb
+            L = int(rng.integers(1, 5))
+            used = np.zeros(cap, dtype=bool)
+            load = np.zeros(a1 - a0, dtype=np.int64)
+            for (b0, b1, q0, K) in placed[c]:
+                lo, hi = max(a0, b0), min(a1, b1)
+                if lo < hi:
+                    used[q0:q0 + K] = True
+                    load[lo - a0:hi - a0] += K
+            if L > cap or load.max(initial=0) + L > cap:
+                continue
+            p0 = next((p for p in range(cap - L + 1) if not used[p:p + L].any()), None)
+            if p0 is None:
+                continue
+            a = np.arange(a0, a1)
+            if not all(np.any(a % cap == p) for p in range(p0, p0 + L)):
+                continue
+            placed[c].append((a0, a1, p0, L))
+            out.append(RaggedUser(cell=c, sc_start=a0, sc_count=a1 - a0, n_layers=L, port0=p0,
+                                  qam_bits=int(rng.choice([2, 4])), snr_db=float(rng.uniform(5.0, 25.0))))
+            break
+        else:
+            raise RuntimeError("could not draw a valid user")
+    return out
+
+
+def make_ragged_slot(n_cells: int = 8, n_users: int = 64, slot_index: int = 0, seed: int = RAGGED_SEED,
+                     cell_shapes=None) -> RaggedSlot:
+    """One slot of a ragged multi-cell batch (the noise variance of every cell is 10^-2.5; a user's SNR sets
+    its channel power)."""
+    rng = np.random.default_rng([seed, slot_index])
+    cells = []
+    for c in range(n_cells):
+        if cell_shapes is not None:
+            n_rx, n_fft = cell_shapes[c % len(cell_shapes)]
+        else:
+            n_rx, n_fft = int(rng.choice([32, 64])), int(rng.choice([2048, 4096]))
+        n_sc = 12 * int(np.floor(0.8 * n_fft / 12))
+        cells.append(RaggedCell(n_rx=n_rx, n_fft=n_fft, n_sc=n_sc, n_beams=n_rx // 2, noise_var=10 ** -2.5))
+    users = _draw_users(rng, cells, n_users)
+
+    time_in, Ws = [], []
+    X = [np.zeros((N_SYM, c.n_rx, c.n_sc), dtype=np.complex128) for c in cells]
+    pilots, xs, bitss = [], [], []
+    for u in users:
+        cell = cells[u.cell]
+        ccfg = CellConfig("u", n_rx=cell.n_rx, n_fft=cell.n_fft, n_sc=cell.n_sc, n_beams=cell.n_beams,
+                          n_layers=u.n_layers, qam_bits=u.qam_bits, snr_db=u.snr_db, channel="pdp", beam="dft",
+                          in_fp16=True)
+        Hant = _channel(ccfg, rng)[u.sc_start:u.sc_start + u.sc_count]            # [n, R, L]
+        gain = np.sqrt(10.0 ** (u.snr_db / 10.0) * cell.noise_var)
+        Hant = Hant * gain
+        a = np.arange(u.sc_start, u.sc_start + u.sc_count)
+        pb = rng.integers(0, 2, size=(u.n_layers, 2, u.sc_count, 2))
+        pil = qam_map(pb, 2)
+        ports = u.port0 + np.arange(u.n_layers)
+        mask = (a[None, :] % cell.comb) == ports[:, None]
+        pil = (pil * mask[:, None, :]).astype(np.complex64)
+        bits = rng.integers(0, 2, size=(u.n_layers, len(DATA_SYMBOLS), u.sc_count, u.qam_bits)).astype(np.uint8)
+        x = qam_map(bits, u.qam_bits)
+        t = np.zeros((u.n_layers, N_SYM, u.sc_count), dtype=np.complex128)
+        for j, s in enumerate(DMRS_SYMBOLS):
+            t[:, s, :] = pil[:, j, :].astype(np.complex128)
+        for j, s in enumerate(DATA_SYMBOLS):
+            t[:, s, :] = x[:, j, :]
+        X[u.cell][:, :, u.sc_start:u.sc_start + u.sc_count] += np.matmul(
+            Hant, np.ascontiguousarray(t.transpose(2, 0, 1))).transpose(2, 1, 0)
+        pilots.append(pil)
+        xs.append(x)
+        bitss.append(pack_bits(bits))
+    for c, cell in enumerate(cells):
+        Xc = X[c] + (rng.standard_normal(X[c].shape) + 1j * rng.standard_normal(X[c].shape)) * np.sqrt(
+            cell.noise_var / 2.0)
+        spec = np.zeros((N_SYM, cell.n_rx, cell.n_fft), dtype=np.complex128)
+        spec[:, :, active_bins(cell.n_sc, cell.n_fft)] = Xc
+        tm = np.fft.ifft(spec, axis=-1)
+        time_in.append(np.stack([tm.real, tm.imag], axis=-1).astype(np.float16))
+        r = np.arange(cell.n_rx)[:, None]
+        b = np.arange(cell.n_beams)[None, :]
+        Ws.append((np.exp(-2j * np.pi * r * b / cell.n_rx) / np.sqrt(cell.n_rx)).astype(np.complex64))
+    return RaggedSlot(cells=cells, users=users, time_in=time_in, W=Ws, pilots=pilots, x=xs, bits=bitss)

@@ -70,7 +70,7 @@ def test_invalid_configs_are_rejected_on_the_host(B, bad, code):
 def test_workspace_size(B):
     cfg = _good()
     n = B.pusch_workspace_size(cfg, 2)
-    per_slot = 14 * 16 * 300 * 8 + 14 * 300 * 16 * 8  # FFT output + beamformed grid
+    per_slot = 14 * 16 * 300 * 8 + 14 * 300 * 16 * 8 + 4 * 75 * 16 * 8  # FFT out + beams + LS pilot table
     assert n >= 2 * per_slot and n < 2 * per_slot + 64 * 1024
 
 

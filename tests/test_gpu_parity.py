@@ -159,7 +159,7 @@ def test_profile_hooks_time_pusch_slot(orc, small_slots):
     for _ in range(3):
         rx.slot(*args)
     ms, n = B.pusch_profile_read(rx.h)
-    assert n == 2 and all(v > 0 for v in ms.values()) and set(ms) == {"fft", "beamform", "detect"}
+    assert n == 2 and all(v > 0 for v in ms.values()) and set(ms) == {"fft", "beamform", "ls", "detect"}
     ms, n = B.pusch_profile_read(rx.h)
     assert n == 0 and all(v == 0 for v in ms.values())
     rx.close()
