@@ -162,6 +162,51 @@ pusch_status pusch_slot_host(pusch_handle *h, int n_slots, const void *time_in_h
                              const void *pilots_host, void *x_hat_host, uint8_t *bits_host, uint32_t *status_host,
                              void *stream);
 
+/* ------------------------------------------------------------------------------------------------------
+ * Ragged multi-cell batches: several cells of different sizes, each with users on their own contiguous
+ * subcarrier ranges (PRB allocations) and layer counts, processed by one CUDA graph launch.
+ *
+ * Per cell, cells[c] gives n_rx, n_fft, n_sc, n_beams, comb, noise_var, loading (its n_layers, port and
+ * qam_bits are not used); in_fp16, form, n_sym and dmrs_sym must be equal for all cells.
+ * Users overlap freely: at every subcarrier, all layers of all users whose range covers it are detected
+ * jointly (MU-MIMO, Eq. 2 with N_L = those layers). A user's layer l transmits its pilots on the
+ * subcarriers a of its range with a % comb == port0 + l; its estimate is interpolated between those pilots
+ * only (held constant outside the first/last one).
+ *
+ * Buffers (device, caller-owned) are the per-cell / per-user arrays concatenated in cell / user order:
+ *   time_in : per cell [n_sym][n_rx][n_fft] c16 (or c64)      W      : per cell [n_rx][n_beams] c64
+ *   pilots  : per user [n_layers][2][sc_count] c64 (index 0 = sc_start)
+ *   x_hat   : per user [n_layers][n_sym-2][sc_count] c64      bits   : same shape, uint8
+ * pusch_batch_sizes returns the element counts of the five buffers.
+ * status words as for pusch_mmse_detect; status[2] holds the smallest failing cell * 65536 + subcarrier.
+ */
+typedef struct {
+    int cell;        /* index of the user's cell                                              */
+    int sc_start;    /* first subcarrier of its contiguous allocation                         */
+    int sc_count;    /* number of subcarriers                                                  */
+    int n_layers;    /* layers of the user, 1 .. 32                                            */
+    int port0;       /* its layers use DMRS ports port0 .. port0 + n_layers - 1 (< comb)       */
+    int qam_bits;    /* 2 = QPSK, 4 = 16-QAM                                                    */
+} pusch_user_desc;
+
+typedef struct pusch_batch pusch_batch;   /* opaque: descriptor tables, workspace, captured graph */
+
+/* Validates the cells and users (ranges inside the cell, ports inside the comb, at least one pilot of
+ * every port inside its user's range, at most min(32, n_beams) layers overlapping anywhere), builds the
+ * constant-user-set segments and the device descriptor tables, and allocates the workspace. */
+pusch_status pusch_batch_create(pusch_batch **b, const pusch_cell_cfg *cells, int n_cells,
+                                const pusch_user_desc *users, int n_users);
+pusch_status pusch_batch_destroy(pusch_batch *b);
+
+/* sizes[0..4] = elements of time_in (complex samples), W, pilots, x_hat (complex), bits. */
+pusch_status pusch_batch_sizes(const pusch_batch *b, size_t sizes[5]);
+
+/* Runs the whole chain for the batch on `stream`. The first call (and any call with different buffer
+ * pointers) captures the chain into a CUDA graph on an internal stream; later calls replay it with
+ * cudaGraphLaunch on `stream`. */
+pusch_status pusch_batch_run(pusch_batch *b, const void *time_in, const void *W, const void *pilots, void *x_hat,
+                             uint8_t *bits, uint32_t *status, void *stream);
+
 /*
  * pusch_slot for callers that cannot allocate device memory.
  * The paper has no counterpart of this entry point; it exists for integration. Some callers must not call

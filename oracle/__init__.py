@@ -50,6 +50,7 @@ def lib():
             "orc_cholesky": (I, [P, I, P]),
             "orc_chol_solve": (None, [P, I, P, P]),
             "orc_mmse": (I, [P, P, I, I, I, P, I, D, D, P, I, P]),
+            "orc_mmse_active": (I, [P, P, P, I, I, I, P, I, D, D, P]),
             "orc_demap": (None, [P, LL, I, I, P]),
             "orc_op_counts": (None, [I, I, I, I, I, I, P]),
             "orc_slot": (I, [P, I, I, I, I, P, I, P, I, P, P, I, I, D, D, P, P]),
@@ -171,6 +172,18 @@ def mmse(H, beam, noise_var: float, loading: float = 0.0, sc_list=None, data_sym
         sl = _i32(sc_list)
         fails = lib().orc_mmse(_p(H), _p(beam), n_sc, B, L, _p(ds), ds.size, noise_var, loading, _p(sl), sl.size,
                                _p(xhat))
+    return xhat, int(fails)
+
+
+def mmse_active(H, beam, active, noise_var: float, loading: float = 0.0, data_sym=None):
+    """H [N_SC, L, B], beam [S, N_SC, B], active [N_SC, L] (bool) -> (xhat [L, n_data, N_SC], n_failed);
+    entries of layers inactive at a subcarrier are zero."""
+    H, beam = _c128(H), _c128(beam)
+    act = np.ascontiguousarray(active, dtype=np.uint8)
+    n_sc, L, B = H.shape
+    ds = data_symbols(beam.shape[0]) if data_sym is None else _i32(data_sym)
+    xhat = np.zeros((L, ds.size, n_sc), dtype=np.complex128)
+    fails = lib().orc_mmse_active(_p(H), _p(beam), _p(act), n_sc, B, L, _p(ds), ds.size, noise_var, loading, _p(xhat))
     return xhat, int(fails)
 
 

@@ -18,6 +18,8 @@
  *   orc_cholesky    Section V-C: Cholesky-Crout, L computed column by column, G = L L^H.
  *   orc_mmse        Eq. 2 via Section II's Cholesky + two triangular solves, per data symbol and
  *                   subcarrier (the paper's accounting in Table I).
+ *   orc_mmse_active Eq. 2 at each subcarrier over the layers active there (users sharing a subcarrier
+ *                   are detected jointly).
  *   orc_demap       Gray hard decisions of 3GPP TS 38.211 5.1.3/5.1.4 (QPSK/16-QAM).
  *   orc_op_counts   Table I complex-MAC model.
  *
@@ -281,6 +283,56 @@ int orc_mmse(const cplx *H, const cplx *beam, int n_sc, int n_beams, int n_layer
             for (int l = 0; l < nl; ++l) xhat[((size_t)l * n_data + d) * n_sc + a] = x[l];
         }
     }
+    free(G);
+    free(L);
+    free(r);
+    free(x);
+    return fails;
+}
+
+/*
+ * MU-MIMO form of Eq. 2: at every subcarrier a, the layers l with active[a][l] != 0 (all users covering a)
+ * are detected jointly, G = H_A^H H_A + (noise_var + loading) I over those layers only, formed and
+ * factored anew for each data symbol. xhat[l][d][a] is written for the active layers only.
+ * Returns the number of (subcarrier, symbol) pairs whose factorisation failed.
+ */
+int orc_mmse_active(const cplx *H, const cplx *beam, const uint8_t *active, int n_sc, int n_beams, int n_layers,
+                    const int *data_sym, int n_data, double noise_var, double loading, cplx *xhat)
+{
+    int *idx = malloc(sizeof(int) * (size_t)n_layers);
+    cplx *Hs = malloc(sizeof(cplx) * (size_t)n_layers * n_beams);
+    cplx *G = malloc(sizeof(cplx) * (size_t)n_layers * n_layers);
+    cplx *L = malloc(sizeof(cplx) * (size_t)n_layers * n_layers);
+    cplx *r = malloc(sizeof(cplx) * (size_t)n_layers);
+    cplx *x = malloc(sizeof(cplx) * (size_t)n_layers);
+    int fails = 0;
+    for (int a = 0; a < n_sc; ++a) {
+        int m = 0;
+        for (int l = 0; l < n_layers; ++l)
+            if (active[(size_t)a * n_layers + l]) idx[m++] = l;
+        if (m == 0) continue;
+        for (int j = 0; j < m; ++j)
+            for (int b = 0; b < n_beams; ++b)
+                Hs[(size_t)j * n_beams + b] = H[((size_t)a * n_layers + idx[j]) * n_beams + b];
+        for (int d = 0; d < n_data; ++d) {
+            const cplx *y = beam + ((size_t)data_sym[d] * n_sc + a) * n_beams;
+            orc_gram(Hs, m, n_beams, noise_var + loading, G);
+            if (orc_cholesky(G, m, L) != 0) {
+                ++fails;
+                for (int j = 0; j < m; ++j) xhat[((size_t)idx[j] * n_data + d) * n_sc + a] = 0;
+                continue;
+            }
+            for (int i = 0; i < m; ++i) {
+                cplx acc = 0;
+                for (int b = 0; b < n_beams; ++b) acc += conj(Hs[(size_t)i * n_beams + b]) * y[b];
+                r[i] = acc;
+            }
+            orc_chol_solve(L, m, r, x);
+            for (int j = 0; j < m; ++j) xhat[((size_t)idx[j] * n_data + d) * n_sc + a] = x[j];
+        }
+    }
+    free(idx);
+    free(Hs);
     free(G);
     free(L);
     free(r);

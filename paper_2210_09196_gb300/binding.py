@@ -34,6 +34,7 @@ EXPORTS = (
     "pusch_create", "pusch_destroy", "pusch_workspace_size", "pusch_sc_pitch", "pusch_ofdm_fft", "pusch_beamform",
     "pusch_chest_ls", "pusch_mmse_detect", "pusch_slot", "pusch_slot_host", "pusch_last_error", "pusch_version",
     "pusch_slot_noalloc", "pusch_profile_start", "pusch_profile_read",
+    "pusch_batch_create", "pusch_batch_destroy", "pusch_batch_sizes", "pusch_batch_run",
 )
 
 
@@ -50,6 +51,11 @@ class pusch_cell_cfg(ctypes.Structure):
         ("qam_bits", ctypes.c_int), ("in_fp16", ctypes.c_int), ("form", ctypes.c_int), ("n_sym", ctypes.c_int),
         ("dmrs_sym", ctypes.c_int * 2), ("noise_var", ctypes.c_float), ("loading", ctypes.c_float),
     ]
+
+
+class pusch_user_desc(ctypes.Structure):
+    _fields_ = [("cell", ctypes.c_int), ("sc_start", ctypes.c_int), ("sc_count", ctypes.c_int),
+                ("n_layers", ctypes.c_int), ("port0", ctypes.c_int), ("qam_bits", ctypes.c_int)]
 
 
 def make_cfg(*, n_rx, n_fft, n_sc, n_beams, n_layers, comb=None, ports=None, qam_bits=2, in_fp16=False,
@@ -90,6 +96,11 @@ def lib():
             "pusch_slot_noalloc": (I, [ctypes.POINTER(pusch_cell_cfg), I, P, P, P, P, P, P, P]),
             "pusch_profile_start": (I, [P, I]),
             "pusch_profile_read": (I, [P, ctypes.POINTER(ctypes.c_float), I, ctypes.POINTER(I)]),
+            "pusch_batch_create": (I, [ctypes.POINTER(P), ctypes.POINTER(pusch_cell_cfg), I,
+                                       ctypes.POINTER(pusch_user_desc), I]),
+            "pusch_batch_destroy": (I, [P]),
+            "pusch_batch_sizes": (I, [P, ctypes.POINTER(ctypes.c_size_t)]),
+            "pusch_batch_run": (I, [P, P, P, P, P, P, P, P]),
             "pusch_last_error": (ctypes.c_char_p, []),
             "pusch_version": (ctypes.c_char_p, []),
         }
@@ -201,3 +212,27 @@ def pusch_profile_read(h) -> tuple[dict, int]:
     n = ctypes.c_int()
     _check(lib().pusch_profile_read(h, ms, len(SLOT_STAGES), ctypes.byref(n)), "pusch_profile_read")
     return dict(zip(SLOT_STAGES, list(ms))), n.value
+
+
+def pusch_batch_create(cells, users) -> int:
+    """cells: sequence of pusch_cell_cfg; users: sequence of pusch_user_desc."""
+    ca = (pusch_cell_cfg * len(cells))(*cells)
+    ua = (pusch_user_desc * len(users))(*users)
+    b = ctypes.c_void_p()
+    _check(lib().pusch_batch_create(ctypes.byref(b), ca, len(cells), ua, len(users)), "pusch_batch_create")
+    return b.value
+
+
+def pusch_batch_destroy(b) -> None:
+    _check(lib().pusch_batch_destroy(b), "pusch_batch_destroy")
+
+
+def pusch_batch_sizes(b) -> list:
+    out = (ctypes.c_size_t * 5)()
+    _check(lib().pusch_batch_sizes(b, out), "pusch_batch_sizes")
+    return list(out)
+
+
+def pusch_batch_run(b, time_in, W, pilots, x_hat, bits, status=None, stream=None) -> None:
+    _check(lib().pusch_batch_run(b, _ptr(time_in), _ptr(W), _ptr(pilots), _ptr(x_hat), _ptr(bits), _ptr(status),
+                                 _stream(stream)), "pusch_batch_run")

@@ -19,6 +19,7 @@
 // because the estimate is constant over the slot. Layers beyond n_layers (up to NL) are padded with
 // identity rows and produce nothing.
 #include "chest_common.cuh"
+#include "detect_core.cuh"
 
 namespace pusch {
 namespace {
@@ -32,54 +33,6 @@ struct MmseArgs {
     int data_sym[16];
     int port[32];
 };
-
-__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
-}
-
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
-}
-
-__device__ __forceinline__ float2 shfl2(float2 v, int src) {
-    return make_float2(__shfl_sync(kFull, v.x, src), __shfl_sync(kFull, v.y, src));
-}
-
-__device__ __forceinline__ uint8_t demap(float2 x, int q) {
-    const float thr = 0.63245553203367586640f;  // 2 / sqrt(10), rounded to float
-    uint8_t v = (uint8_t)(x.x < 0.f) | (uint8_t)((x.y < 0.f) << 1);
-    if (q == 4) v |= (uint8_t)((fabsf(x.x) > thr) << 2) | (uint8_t)((fabsf(x.y) > thr) << 3);
-    return v;
-}
-
-// Shared memory per subcarrier, in float2 units: the H tile (NL rows of an even stride >= nb + 1), which
-// later holds L ([NL][NL + 1]); in the fused variant also NL row-parameter records.
-__host__ __device__ __forceinline__ int row_stride(int nb) { return (nb + 3) & ~1; }
-template <int NL>
-__host__ __device__ __forceinline__ int htile(int nb) {
-    const int a = NL * row_stride(nb), b = NL * (NL + 1) + NL / 2;  // L tile + 1/L[k][k] (NL floats)
-    const int m = a > b ? a : b;
-    return (m + 1) & ~1;
-}
-
-// Interpolation parameters of one (subcarrier, layer) row of the fused estimate.
-struct RowParam {
-    long long lo, hi;     // element offsets of the LS rows of the neighbouring pilots (lo == hi: hold)
-    float w;              // interpolation weight
-    int valid;            // 0: row is padding (layer >= n_layers or subcarrier out of range)
-};
-
-template <int NL, bool FUSED>
-__host__ __device__ __forceinline__ size_t warp_smem_bytes(int nb, int nd) {
-    return (size_t)(32 / NL) *
-           ((htile<NL>(nb) + (size_t)nd * row_stride(nb)) * sizeof(float2) + (FUSED ? NL * sizeof(RowParam) : 0));
-}
-
-__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
-}
 
 // Register cap: five 4-warp CTAs per SM up to 8 layers, four for 16 layers (no spills), none for 32.
 template <int NL, int ND, bool FUSED>
@@ -201,134 +154,16 @@ mmse_kernel(MmseArgs g, long long total_sc, const float2 *__restrict__ H, const 
 
     const float2 *hr = Ht + grp * ht + i * hs;  // own row
     const float2 *hg = Ht + grp * ht;           // the group's rows
-
-    // ---- 2a. Gram row i: G[j] = sum_b conj(H[i][b]) H[j][b]
-    float2 G[NL];
-#pragma unroll
-    for (int j = 0; j < NL; ++j) G[j] = make_float2(0.f, 0.f);
-    int b = 0;
-    for (; b + 1 < nb; b += 2) {
-        const float4 hv = *reinterpret_cast<const float4 *>(hr + b);
-        const float2 h0 = make_float2(hv.x, hv.y), h1 = make_float2(hv.z, hv.w);
-#pragma unroll
-        for (int j = 0; j < NL; ++j) {
-            const float4 gv = *reinterpret_cast<const float4 *>(hg + j * hs + b);
-            cfmac(G[j], h0, make_float2(gv.x, gv.y));
-            cfmac(G[j], h1, make_float2(gv.z, gv.w));
-        }
-    }
-    if (b < nb) {
-        const float2 h0 = hr[b];
-#pragma unroll
-        for (int j = 0; j < NL; ++j) cfmac(G[j], h0, hg[j * hs + b]);
-    }
-#pragma unroll
-    for (int j = 0; j < NL; ++j)
-        if (j == i) G[j] = (i < nl) ? make_float2(G[j].x + g.load, 0.f) : make_float2(1.f, 0.f);
-
-    // ---- 2b. right-hand sides r_d = H^H y_d (y_d from the shared tile; a group reads one address)
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-    __syncwarp();
     constexpr int NR = ND > 0 ? ND : 14;
     float2 acc[NR];
-#pragma unroll
-    for (int d = 0; d < NR; ++d) acc[d] = make_float2(0.f, 0.f);
-    {
-        const float2 *yt = Yt + grp * nd * hs;
-        for (b = 0; b + 1 < nb; b += 2) {
-            const float4 hv = *reinterpret_cast<const float4 *>(hr + b);
-            const float2 h0 = make_float2(hv.x, hv.y), h1 = make_float2(hv.z, hv.w);
-#pragma unroll
-            for (int d = 0; d < NR; ++d) {
-                if (ND > 0 || d < nd) {
-                    const float4 yv = *reinterpret_cast<const float4 *>(yt + d * hs + b);
-                    cfmac(acc[d], h0, make_float2(yv.x, yv.y));
-                    cfmac(acc[d], h1, make_float2(yv.z, yv.w));
-                }
-            }
-        }
-        if (b < nb) {
-            const float2 h0 = hr[b];
-#pragma unroll
-            for (int d = 0; d < NR; ++d)
-                if (ND > 0 || d < nd) cfmac(acc[d], h0, yt[d * hs + b]);
-        }
-    }
-    __syncwarp();  // the H tile is reused for L below
-
-    // ---- 3. Cholesky, right-looking, row i of L replaces row i of G; then L -> shared memory
-    bool bad = false;
-    float dinv = 1.f;
-#pragma unroll
-    for (int j = 0; j < NL; ++j) {
-        float dj = __shfl_sync(kFull, G[j].x, src0 + j);
-        if (!(dj > 0.f) || !isfinite(dj)) {
-            bad = true;
-            dj = 1.f;
-        }
-        const float ljj = sqrtf(dj);
-        const float inv = 1.f / ljj;
-        if (i > j) G[j] = cscale(G[j], inv);
-        else if (i == j) G[j] = make_float2(ljj, 0.f);
-        else G[j] = make_float2(0.f, 0.f);
-        if (i == j) dinv = inv;
-#pragma unroll
-        for (int k = j + 1; k < NL; ++k) {
-            const float2 lkj = shfl2(G[j], src0 + k);
-            if (i >= k) {
-                // G[i][k] -= L[i][j] conj(L[k][j])
-                G[k].x -= G[j].x * lkj.x + G[j].y * lkj.y;
-                G[k].y -= G[j].y * lkj.x - G[j].x * lkj.y;
-            }
-        }
-    }
-    float2 *lt = Ht + grp * ht;  // [NL][NL + 1]
-#pragma unroll
-    for (int k = 0; k < NL; ++k) lt[i * (NL + 1) + k] = G[k];
-    __syncwarp();
-
+    const bool bad = detect_group<NL, ND, NR>(hr, hg, Yt + grp * nd * hs, Ht + grp * ht, hs, nb, nd, nl, g.load, i,
+                                              src0, acc);
     if (valid && bad && i == 0) {
         atomicAdd(&status[1], 1u);
         atomicMin(&status[2], (unsigned)my_sc);
         atomicOr(&status[0], (unsigned)PUSCH_STATUS_PIVOT);
     }
 
-    // ---- 4. forward L z = r, then back L^H x = z, for all data symbols, in unit-diagonal form:
-    //         with D = diag(L), u = D z solves (L D^-1) u = r and x solves (D^-1 L^H) x = D^-1 z, so each step
-    //         broadcasts an unknown that is already final (no scaling before the shuffle). Lane i's unknown is
-    //         final at step i and not updated afterwards. dv[k] = 1 / L[k][k] sits after L in shared memory.
-    float *dv = reinterpret_cast<float *>(lt + NL * (NL + 1));
-    dv[i] = dinv;
-    __syncwarp();
-    const float2 *lrow = lt + i * (NL + 1);  // L[i][k]
-#pragma unroll
-    for (int k = 0; k < NL; ++k) {
-        const float2 m = cscale(lrow[k], dv[k]);  // L[i][k] / L[k][k]
-#pragma unroll
-        for (int d = 0; d < NR; ++d) {
-            if (ND > 0 || d < nd) {
-                const float2 uk = shfl2(acc[d], src0 + k);
-                if (i > k) cfms(acc[d], m, uk);
-            }
-        }
-    }
-#pragma unroll
-    for (int d = 0; d < NR; ++d) acc[d] = cscale(acc[d], dinv * dinv);  // z_i / L[i][i]
-#pragma unroll
-    for (int k = NL - 1; k >= 0; --k) {
-        const float2 lki = cscale(lt[k * (NL + 1) + i], dinv);  // L[k][i] / L[i][i]
-#pragma unroll
-        for (int d = 0; d < NR; ++d) {
-            if (ND > 0 || d < nd) {
-                const float2 xk = shfl2(acc[d], src0 + k);
-                if (i < k) {
-                    // acc -= conj(L[k][i] / L[i][i]) x_k
-                    acc[d].x -= lki.x * xk.x + lki.y * xk.y;
-                    acc[d].y -= lki.x * xk.y - lki.y * xk.x;
-                }
-            }
-        }
-    }
     bool nonfinite = false;
     if (valid && i < nl) {
         const long long o0 = (slot * nl + i) * (long long)nd * n_sc + a;
@@ -337,7 +172,7 @@ mmse_kernel(MmseArgs g, long long total_sc, const float2 *__restrict__ H, const 
             if (ND > 0 || d < nd) {
                 const float2 x = acc[d];
                 xhat[o0 + (long long)d * n_sc] = x;
-                bits[o0 + (long long)d * n_sc] = demap(x, g.qam_bits);
+                bits[o0 + (long long)d * n_sc] = det_demap(x, g.qam_bits);
                 if (!isfinite(x.x) || !isfinite(x.y)) nonfinite = true;
             }
         }

@@ -123,3 +123,58 @@ class Receiver:
         x, b, st = out_host
         B.pusch_slot_host(self.h, time_in_host.shape[0], time_in_host, W, pilots_host, x, b, st, stream)
         return x, b, st
+
+
+class RaggedReceiver:
+    """One pusch_batch for a generated ragged multi-cell slot (synth.RaggedSlot) and its packed buffers."""
+
+    def __init__(self, rs, form: int = B.PUSCH_FORM_MIXED, device="cuda"):
+        self.cells = []
+        for c in rs.cells:
+            cfg = B.make_cfg(n_rx=c.n_rx, n_fft=c.n_fft, n_sc=c.n_sc, n_beams=c.n_beams, n_layers=1, comb=c.comb,
+                             ports=[0], in_fp16=True, form=form, noise_var=c.noise_var)
+            self.cells.append(cfg)
+        self.users = [B.pusch_user_desc(u.cell, u.sc_start, u.sc_count, u.n_layers, u.port0, u.qam_bits)
+                      for u in rs.users]
+        self.h = B.pusch_batch_create(self.cells, self.users)
+        self.sizes = B.pusch_batch_sizes(self.h)
+        self.device = torch.device(device)
+        self.n_data = 12
+
+    def close(self):
+        if self.h:
+            B.pusch_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def pack(self, rs):
+        """Concatenated device buffers (time_in, W, pilots) of a ragged slot."""
+        t = torch.from_numpy(np.concatenate([x.reshape(-1, 2) for x in rs.time_in])).to(self.device)
+        w = torch.from_numpy(np.concatenate([x.reshape(-1) for x in rs.W])).to(self.device)
+        p = torch.from_numpy(np.concatenate([x.reshape(-1) for x in rs.pilots])).to(self.device)
+        assert t.shape[0] == self.sizes[0] and w.numel() == self.sizes[1] and p.numel() == self.sizes[2]
+        return t, w, p
+
+    def outputs(self):
+        x = torch.empty(self.sizes[3], dtype=torch.complex64, device=self.device)
+        b = torch.empty(self.sizes[4], dtype=torch.uint8, device=self.device)
+        s = torch.zeros(4, dtype=torch.int32, device=self.device)
+        return x, b, s
+
+    def run(self, t, w, p, out, stream=None):
+        B.pusch_batch_run(self.h, t, w, p, *out, stream=stream)
+        return out
+
+    def split(self, flat, rs):
+        """Per-user [n_layers, 12, sc_count] views of a packed output."""
+        res, o = [], 0
+        for u in rs.users:
+            n = u.n_layers * self.n_data * u.sc_count
+            res.append(flat[o:o + n].reshape(u.n_layers, self.n_data, u.sc_count))
+            o += n
+        return res

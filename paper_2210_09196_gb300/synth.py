@@ -257,12 +257,13 @@ def _draw_users(rng, cells, n_users, max_tries=10000):
     ports that no user overlapping its range already uses. The user is redrawn while its range would make
     more than N_B/2 layers overlap, no such ports exist, or its range misses a pilot of one of its ports."""
     cell_of = [int(rng.integers(0, len(cells))) for _ in range(n_users)]
+    for cell in cells:
+        cell.comb = cell.n_beams // 2
     out = []
     placed = [[] for _ in cells]  # (a0, a1, p0, L)
     for c in cell_of:
         cell = cells[c]
-        cap = cell.n_beams // 2
-        cell.comb = cap
+        cap = cell.comb
         n_prb_max = cell.n_sc // 12
         for _ in range(max_tries):
             n_prb = int(rng.integers(1, n_prb_max + 1))
@@ -294,9 +295,9 @@ def _draw_users(rng, cells, n_users, max_tries=10000):
 
 
 def make_ragged_slot(n_cells: int = 8, n_users: int = 64, slot_index: int = 0, seed: int = RAGGED_SEED,
-                     cell_shapes=None) -> RaggedSlot:
+                     cell_shapes=None, users=None) -> RaggedSlot:
     """One slot of a ragged multi-cell batch (the noise variance of every cell is 10^-2.5; a user's SNR sets
-    its channel power)."""
+    its channel power). `users` (a list of RaggedUser) replaces the random user draw."""
     rng = np.random.default_rng([seed, slot_index])
     cells = []
     for c in range(n_cells):
@@ -306,7 +307,11 @@ def make_ragged_slot(n_cells: int = 8, n_users: int = 64, slot_index: int = 0, s
             n_rx, n_fft = int(rng.choice([32, 64])), int(rng.choice([2048, 4096]))
         n_sc = 12 * int(np.floor(0.8 * n_fft / 12))
         cells.append(RaggedCell(n_rx=n_rx, n_fft=n_fft, n_sc=n_sc, n_beams=n_rx // 2, noise_var=10 ** -2.5))
-    users = _draw_users(rng, cells, n_users)
+    if users is None:
+        users = _draw_users(rng, cells, n_users)
+    else:
+        for c in cells:
+            c.comb = c.n_beams // 2
 
     time_in, Ws = [], []
     X = [np.zeros((N_SYM, c.n_rx, c.n_sc), dtype=np.complex128) for c in cells]

@@ -384,3 +384,29 @@ def test_slot_deploy_pdp_decodes_well_at_30db(orc):
     _, bits, fails = orc.run_slot(s)
     assert fails == 0
     assert np.mean(bits != s.bits) < 0.02
+
+
+# ------------------------------------------------------------------------------------------ MU-MIMO
+
+
+def test_mmse_active_all_layers_equals_plain_mmse(orc):
+    n_sc, L, B = 6, 3, 5
+    H, beam = crandn(n_sc, L, B), crandn(14, n_sc, B)
+    x1, _ = orc.mmse_active(H, beam, np.ones((n_sc, L), bool), 0.3)
+    x2, _ = orc.mmse(H, beam, 0.3)
+    assert np.array_equal(x1, x2)
+
+
+def test_mmse_active_detects_only_the_layers_present(orc):
+    """A layer absent at a subcarrier neither receives an output nor enters the Gram there (Eq. 2 over the
+    users that share the subcarrier)."""
+    n_sc, L, B = 5, 4, 6
+    H, beam = crandn(n_sc, L, B), crandn(14, n_sc, B)
+    act = np.ones((n_sc, L), bool)
+    act[1, 2] = act[3, 0] = act[3, 3] = False
+    x, _ = orc.mmse_active(H, beam, act, 0.2)
+    for a in range(n_sc):
+        keep = np.flatnonzero(act[a])
+        xr, _ = orc.mmse(H[a:a + 1][:, keep], beam[:, a:a + 1], 0.2)
+        assert rel(x[keep][:, :, a], xr[:, :, 0]) < 1e-14
+        assert np.all(x[~act[a]][:, :, a] == 0)
