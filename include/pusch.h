@@ -163,6 +163,47 @@ pusch_status pusch_slot_host(pusch_handle *h, int n_slots, const void *time_in_h
                              void *stream);
 
 /* ------------------------------------------------------------------------------------------------------
+ * Learned channel-estimate denoiser (an addition to the paper's LS estimator, which stays the fallback).
+ * A 4-layer CNN of 3x3 same-padded convolutions 2 -> 32 -> 32 -> 32 -> 2 with ReLU after the first three and
+ * the input added to the output, run on grids [n][2 channels (re, im)][2 DMRS symbols][w subcarriers].
+ * Parameters (pusch_cnn_param_count() = 19682) are packed per layer as W[co][ci][3][3] then b[co]; weights
+ * and activations are bfloat16, arithmetic and gradients FP32. All pointers are device pointers.
+ */
+int pusch_cnn_param_count(void);
+
+/* y [n][2][2][w] (FP32) = CNN(x); acts receives the post-ReLU activations [3][n][32][2][w] (bf16), needed
+ * by pusch_cnn_backward. n <= 65535. */
+pusch_status pusch_cnn_forward(int n, int w, const void *x_bf16, const void *params_bf16, float *y, void *acts_bf16,
+                               void *stream);
+
+/* grad (FP32, param_count values, overwritten) = d/dparams of mean((y - target)^2) for the forward pass
+ * that produced y and acts; *loss (if not NULL) = that mean. work: 2 * n * 32 * 2 * w floats of scratch;
+ * wflip: param_count bf16 values of scratch. */
+pusch_status pusch_cnn_backward(int n, int w, const void *x_bf16, const void *acts_bf16, const void *params_bf16,
+                                const float *y, const float *target, float *grad, float *loss, float *work,
+                                void *wflip_bf16, void *stream);
+
+/* One Adam step (step >= 1) on the FP32 master parameters; params_bf16 receives their bfloat16 copy. */
+pusch_status pusch_cnn_adam(int step, float lr, float beta1, float beta2, float eps, float *params, void *params_bf16,
+                            const float *grad, float *m, float *v, void *stream);
+
+/* The denoiser's input: for every (slot, layer l, beam b), grid index (slot * n_layers + l) * n_beams + b,
+ * the LS estimate of each DMRS symbol separately (y_j / p_j at the layer's pilots, linearly interpolated
+ * as in pusch_chest_ls), divided by its RMS over the grid: grid [grids][2][2][n_sc] bf16, scale [grids]. */
+pusch_status pusch_ls_grid(pusch_handle *h, int n_slots, const void *beam, const void *pilots, void *grid_bf16,
+                           float *scale, void *stream);
+
+/* Channel estimation with the denoiser: H_hat (layout of pusch_chest_ls) receives, per (slot, layer, beam),
+ * the CNN estimate (mean of its two DMRS rows, rescaled) when its pilot residual - the mean over the
+ * layer's pilots and both DMRS symbols of |y / p - estimate|^2 - is at most kappa * sigma^2, and the plain
+ * LS estimate of pusch_chest_ls otherwise (fallback). resid [grids] (optional) receives residual / sigma^2,
+ * fallback [grids] (optional) 1 where the LS estimate was kept. The first call allocates the handle's CNN
+ * workspace for max_slots (max_slots * n_layers * n_beams <= 65535 grids). */
+pusch_status pusch_chest_cnn(pusch_handle *h, int n_slots, const void *beam, const void *pilots,
+                             const void *params_bf16, float kappa, void *H_hat, float *resid, uint8_t *fallback,
+                             void *stream);
+
+/* ------------------------------------------------------------------------------------------------------
  * Ragged multi-cell batches: several cells of different sizes, each with users on their own contiguous
  * subcarrier ranges (PRB allocations) and layer counts, processed by one CUDA graph launch.
  *

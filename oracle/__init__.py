@@ -52,6 +52,10 @@ def lib():
             "orc_mmse": (I, [P, P, I, I, I, P, I, D, D, P, I, P]),
             "orc_mmse_active": (I, [P, P, P, I, I, I, P, I, D, D, P]),
             "orc_demap": (None, [P, LL, I, I, P]),
+            "orc_cnn_param_count": (I, []),
+            "orc_round_bf16": (D, [D]),
+            "orc_cnn_forward": (None, [P, P, I, I, I, P, P]),
+            "orc_cnn_loss_grad": (D, [P, P, P, I, I, I, P]),
             "orc_op_counts": (None, [I, I, I, I, I, I, P]),
             "orc_slot": (I, [P, I, I, I, I, P, I, P, I, P, P, I, I, D, D, P, P]),
         }
@@ -221,3 +225,37 @@ def run_slot(s, loading: float = 0.0):
     """Convenience: run the chain on a generated slot object (paper_2210_09196_gb300.synth.Slot)."""
     return slot(s.time_as_complex128(), s.W, s.pilots, s.ports, s.cfg.comb, s.cfg.n_sc, s.cfg.qam_bits,
                 s.noise_var, loading)
+
+
+# ---------------------------------------------------------------------------------------- denoiser CNN
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def cnn_param_count() -> int:
+    return int(lib().orc_cnn_param_count())
+
+
+def round_bf16(v) -> np.ndarray:
+    f = np.vectorize(lambda t: lib().orc_round_bf16(float(t)))
+    return f(np.asarray(v, dtype=np.float64))
+
+
+def cnn_forward(params, x, bf16: bool = False):
+    """params (packed), x [n, 2, 2, w] -> (y [n, 2, 2, w], activations [3, n, 32, 2, w])."""
+    params, x = _f64(params), _f64(x)
+    n, _, _, w = x.shape
+    y = np.empty_like(x)
+    acts = np.empty((3, n, 32, 2, w))
+    lib().orc_cnn_forward(_p(params), _p(x), n, w, 1 if bf16 else 0, _p(y), _p(acts))
+    return y, acts
+
+
+def cnn_loss_grad(params, x, target, bf16: bool = False):
+    """(mean squared error, d loss / d params)."""
+    params, x, target = _f64(params), _f64(x), _f64(target)
+    n, _, _, w = x.shape
+    g = np.empty_like(params)
+    loss = lib().orc_cnn_loss_grad(_p(params), _p(x), _p(target), n, w, 1 if bf16 else 0, _p(g))
+    return float(loss), g

@@ -442,3 +442,183 @@ done:
     free(count);
     return rc;
 }
+
+/* ------------------------------------------------------ learned denoiser (CNN) ---- */
+
+/*
+ * The channel-estimate denoiser: four 3x3 same-padded convolutions 2 -> 32 -> 32 -> 32 -> 2 with ReLU after
+ * the first three and the input added to the output (residual). Tensors are [n][c][2][w] (n grids, c
+ * channels, the 2 DMRS symbols as rows, w subcarriers); zero padding outside the grid.
+ *   conv:  out[n][co][h][x] = b[co] + sum_{ci, dh, dx} W[co][ci][dh][dx] in[n][ci][h + dh - 1][x + dx - 1]
+ * Parameters are packed layer by layer as W (co, ci, 3, 3) then b (co).
+ * bf16 != 0 rounds weights, biases, the input and every stored activation to bfloat16 (round to nearest
+ * even), at the points where a bfloat16 implementation stores them; arithmetic stays double.
+ */
+static const int CNN_CH[5] = {2, 32, 32, 32, 2};
+
+int orc_cnn_param_count(void)
+{
+    int n = 0;
+    for (int k = 0; k < 4; ++k) n += CNN_CH[k + 1] * CNN_CH[k] * 9 + CNN_CH[k + 1];
+    return n;
+}
+
+double orc_round_bf16(double v)
+{
+    float f = (float)v;
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    if ((u & 0x7f800000u) == 0x7f800000u) return v; /* inf / nan unchanged */
+    uint32_t lsb = (u >> 16) & 1u;
+    u += 0x7fffu + lsb;
+    u &= 0xffff0000u;
+    memcpy(&f, &u, 4);
+    return (double)f;
+}
+
+static void cnn_conv(const double *in, int n, int cin, int w, const double *W, const double *b, int cout,
+                     double *out)
+{
+    for (int s = 0; s < n; ++s)
+        for (int co = 0; co < cout; ++co)
+            for (int h = 0; h < 2; ++h)
+                for (int x = 0; x < w; ++x) {
+                    double acc = b[co];
+                    for (int ci = 0; ci < cin; ++ci)
+                        for (int dh = 0; dh < 3; ++dh) {
+                            int hh = h + dh - 1;
+                            if (hh < 0 || hh > 1) continue;
+                            for (int dx = 0; dx < 3; ++dx) {
+                                int xx = x + dx - 1;
+                                if (xx < 0 || xx >= w) continue;
+                                acc += W[((co * cin + ci) * 3 + dh) * 3 + dx] *
+                                       in[(((size_t)s * cin + ci) * 2 + hh) * w + xx];
+                            }
+                        }
+                    out[(((size_t)s * cout + co) * 2 + h) * w + x] = acc;
+                }
+}
+
+/* Forward pass. acts (optional) receives the post-ReLU activations of layers 1..3 ([n][32][2][w] each). */
+void orc_cnn_forward(const double *params, const double *x, int n, int w, int bf16, double *y, double *acts)
+{
+    size_t big = (size_t)n * 32 * 2 * w;
+    double *p = malloc(sizeof(double) * (size_t)orc_cnn_param_count());
+    double *a = malloc(sizeof(double) * big), *z = malloc(sizeof(double) * big);
+    double *x0 = malloc(sizeof(double) * (size_t)n * 2 * 2 * w);
+    int np = orc_cnn_param_count();
+    for (int i = 0; i < np; ++i) p[i] = bf16 ? orc_round_bf16(params[i]) : params[i];
+    for (size_t i = 0; i < (size_t)n * 4 * w; ++i) x0[i] = bf16 ? orc_round_bf16(x[i]) : x[i];
+    /* in -> z (pre-activation) -> a (post-activation, next input); buffers swapped by copying */
+    double *cur = malloc(sizeof(double) * big);
+    memcpy(cur, x0, sizeof(double) * (size_t)n * 4 * w);
+    int off = 0;
+    for (int k = 0; k < 4; ++k) {
+        int cin = CNN_CH[k], cout = CNN_CH[k + 1];
+        const double *W = p + off, *b = p + off + cout * cin * 9;
+        off += cout * cin * 9 + cout;
+        cnn_conv(cur, n, cin, w, W, b, cout, z);
+        size_t m = (size_t)n * cout * 2 * w;
+        if (k < 3) {
+            for (size_t i = 0; i < m; ++i) {
+                double v = z[i] > 0 ? z[i] : 0.0;
+                a[i] = bf16 ? orc_round_bf16(v) : v;
+            }
+            if (acts) memcpy(acts + (size_t)k * big, a, sizeof(double) * m);
+            memcpy(cur, a, sizeof(double) * m);
+        } else {
+            for (size_t i = 0; i < m; ++i) y[i] = z[i] + x0[i];
+        }
+    }
+    free(cur);
+    free(p);
+    free(a);
+    free(z);
+    free(x0);
+}
+
+/*
+ * Loss and gradient: L = mean over all output elements of (y - target)^2. grad (same packing as params)
+ * receives dL/dparams. Returns L. Same bf16 convention as orc_cnn_forward (the backward pass itself is
+ * exact in double, using the rounded forward activations).
+ */
+double orc_cnn_loss_grad(const double *params, const double *x, const double *target, int n, int w, int bf16,
+                         double *grad)
+{
+    int np = orc_cnn_param_count();
+    size_t big = (size_t)n * 32 * 2 * w, small = (size_t)n * 2 * 2 * w;
+    double *acts = malloc(sizeof(double) * 3 * big);
+    double *y = malloc(sizeof(double) * small);
+    double *p = malloc(sizeof(double) * (size_t)np);
+    double *x0 = malloc(sizeof(double) * small);
+    double *g = malloc(sizeof(double) * big), *gin = malloc(sizeof(double) * big);
+    for (int i = 0; i < np; ++i) p[i] = bf16 ? orc_round_bf16(params[i]) : params[i];
+    for (size_t i = 0; i < small; ++i) x0[i] = bf16 ? orc_round_bf16(x[i]) : x[i];
+    orc_cnn_forward(params, x, n, w, bf16, y, acts);
+    double loss = 0;
+    for (size_t i = 0; i < small; ++i) {
+        double d = y[i] - target[i];
+        loss += d * d;
+        g[i] = 2.0 * d / (double)small;
+    }
+    loss /= (double)small;
+    int offs[4];
+    int off = 0;
+    for (int k = 0; k < 4; ++k) {
+        offs[k] = off;
+        off += CNN_CH[k + 1] * CNN_CH[k] * 9 + CNN_CH[k + 1];
+    }
+    for (int i = 0; i < np; ++i) grad[i] = 0;
+    for (int k = 3; k >= 0; --k) {
+        int cin = CNN_CH[k], cout = CNN_CH[k + 1];
+        const double *in = k == 0 ? x0 : acts + (size_t)(k - 1) * big;
+        const double *W = p + offs[k];
+        double *dW = grad + offs[k], *db = grad + offs[k] + cout * cin * 9;
+        for (int s = 0; s < n; ++s)
+            for (int co = 0; co < cout; ++co)
+                for (int h = 0; h < 2; ++h)
+                    for (int x = 0; x < w; ++x) {
+                        double go = g[(((size_t)s * cout + co) * 2 + h) * w + x];
+                        db[co] += go;
+                        for (int ci = 0; ci < cin; ++ci)
+                            for (int dh = 0; dh < 3; ++dh) {
+                                int hh = h + dh - 1;
+                                if (hh < 0 || hh > 1) continue;
+                                for (int dx = 0; dx < 3; ++dx) {
+                                    int xx = x + dx - 1;
+                                    if (xx < 0 || xx >= w) continue;
+                                    dW[((co * cin + ci) * 3 + dh) * 3 + dx] +=
+                                        go * in[(((size_t)s * cin + ci) * 2 + hh) * w + xx];
+                                }
+                            }
+                    }
+        if (k == 0) break;
+        /* gradient w.r.t. this layer's input, masked by the ReLU of the previous layer */
+        for (size_t i = 0; i < (size_t)n * cin * 2 * w; ++i) gin[i] = 0;
+        for (int s = 0; s < n; ++s)
+            for (int co = 0; co < cout; ++co)
+                for (int h = 0; h < 2; ++h)
+                    for (int x = 0; x < w; ++x) {
+                        double go = g[(((size_t)s * cout + co) * 2 + h) * w + x];
+                        for (int ci = 0; ci < cin; ++ci)
+                            for (int dh = 0; dh < 3; ++dh) {
+                                int hh = h + dh - 1;
+                                if (hh < 0 || hh > 1) continue;
+                                for (int dx = 0; dx < 3; ++dx) {
+                                    int xx = x + dx - 1;
+                                    if (xx < 0 || xx >= w) continue;
+                                    gin[(((size_t)s * cin + ci) * 2 + hh) * w + xx] +=
+                                        go * W[((co * cin + ci) * 3 + dh) * 3 + dx];
+                                }
+                            }
+                    }
+        for (size_t i = 0; i < (size_t)n * cin * 2 * w; ++i) g[i] = in[i] > 0 ? gin[i] : 0.0;
+    }
+    free(acts);
+    free(y);
+    free(p);
+    free(x0);
+    free(g);
+    free(gin);
+    return loss;
+}

@@ -35,6 +35,8 @@ EXPORTS = (
     "pusch_chest_ls", "pusch_mmse_detect", "pusch_slot", "pusch_slot_host", "pusch_last_error", "pusch_version",
     "pusch_slot_noalloc", "pusch_profile_start", "pusch_profile_read",
     "pusch_batch_create", "pusch_batch_destroy", "pusch_batch_sizes", "pusch_batch_run",
+    "pusch_cnn_param_count", "pusch_cnn_forward", "pusch_cnn_backward", "pusch_cnn_adam", "pusch_ls_grid",
+    "pusch_chest_cnn",
 )
 
 
@@ -101,6 +103,13 @@ def lib():
             "pusch_batch_destroy": (I, [P]),
             "pusch_batch_sizes": (I, [P, ctypes.POINTER(ctypes.c_size_t)]),
             "pusch_batch_run": (I, [P, P, P, P, P, P, P, P]),
+            "pusch_cnn_param_count": (I, []),
+            "pusch_cnn_forward": (I, [I, I, P, P, P, P, P]),
+            "pusch_cnn_backward": (I, [I, I, P, P, P, P, P, P, P, P, P, P]),
+            "pusch_cnn_adam": (I, [I, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, P, P, P, P, P,
+                                   P]),
+            "pusch_ls_grid": (I, [P, I, P, P, P, P, P]),
+            "pusch_chest_cnn": (I, [P, I, P, P, P, ctypes.c_float, P, P, P, P]),
             "pusch_last_error": (ctypes.c_char_p, []),
             "pusch_version": (ctypes.c_char_p, []),
         }
@@ -236,3 +245,33 @@ def pusch_batch_sizes(b) -> list:
 def pusch_batch_run(b, time_in, W, pilots, x_hat, bits, status=None, stream=None) -> None:
     _check(lib().pusch_batch_run(b, _ptr(time_in), _ptr(W), _ptr(pilots), _ptr(x_hat), _ptr(bits), _ptr(status),
                                  _stream(stream)), "pusch_batch_run")
+
+
+def pusch_cnn_param_count() -> int:
+    return lib().pusch_cnn_param_count()
+
+
+def pusch_cnn_forward(n, w, x, params_bf16, y, acts, stream=None) -> None:
+    _check(lib().pusch_cnn_forward(n, w, _ptr(x), _ptr(params_bf16), _ptr(y), _ptr(acts), _stream(stream)),
+           "pusch_cnn_forward")
+
+
+def pusch_cnn_backward(n, w, x, acts, params_bf16, y, target, grad, loss, work, wflip, stream=None) -> None:
+    _check(lib().pusch_cnn_backward(n, w, _ptr(x), _ptr(acts), _ptr(params_bf16), _ptr(y), _ptr(target), _ptr(grad),
+                                    _ptr(loss), _ptr(work), _ptr(wflip), _stream(stream)), "pusch_cnn_backward")
+
+
+def pusch_cnn_adam(step, lr, beta1, beta2, eps, params, params_bf16, grad, m, v, stream=None) -> None:
+    _check(lib().pusch_cnn_adam(step, lr, beta1, beta2, eps, _ptr(params), _ptr(params_bf16), _ptr(grad), _ptr(m),
+                                _ptr(v), _stream(stream)), "pusch_cnn_adam")
+
+
+def pusch_ls_grid(h, n_slots, beam, pilots, grid, scale, stream=None) -> None:
+    _check(lib().pusch_ls_grid(h, n_slots, _ptr(beam), _ptr(pilots), _ptr(grid), _ptr(scale), _stream(stream)),
+           "pusch_ls_grid")
+
+
+def pusch_chest_cnn(h, n_slots, beam, pilots, params_bf16, kappa, H_hat, resid=None, fallback=None,
+                    stream=None) -> None:
+    _check(lib().pusch_chest_cnn(h, n_slots, _ptr(beam), _ptr(pilots), _ptr(params_bf16), kappa, _ptr(H_hat),
+                                 _ptr(resid), _ptr(fallback), _stream(stream)), "pusch_chest_cnn")

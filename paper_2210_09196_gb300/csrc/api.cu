@@ -5,32 +5,9 @@
 #include <string.h>
 
 #include <new>
-#include <vector>
 
 #include "internal.cuh"
 
-struct pusch_handle {
-    pusch_cell_cfg cfg;
-    pusch::Geometry geo;
-    int max_slots = 0;
-    int device = 0;
-    float2 *twiddle = nullptr;      // exp(-2 pi i q / n_fft), q < n_fft
-    uint32_t *kernel_err = nullptr;   // bounded-wait expiry flags of the tensor-core kernel
-    void *freq = nullptr;           // workspace: FFT output
-    float2 *beam = nullptr;         // workspace: beamformed grid
-    float2 *ls = nullptr;           // workspace: LS values at the pilot subcarriers
-    uint32_t *status_sink = nullptr;  // status words used when the caller passes NULL
-    // staging for pusch_slot_host (allocated on first use)
-    void *h_time = nullptr;
-    float2 *h_pilots = nullptr;
-    float2 *h_xhat = nullptr;
-    uint8_t *h_bits = nullptr;
-    uint32_t *h_status = nullptr;
-    // per-stage timing of pusch_slot (pusch_profile_start / pusch_profile_read)
-    std::vector<cudaEvent_t> prof_events;  // [max_calls][kSlotStages + 1]
-    int prof_max_calls = 0;
-    int prof_calls = 0;
-};
 
 namespace {
 

@@ -5,6 +5,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cuda_bf16.h>
+
+#include <vector>
+
 #include "../../include/pusch.h"
 
 namespace pusch {
@@ -78,4 +82,47 @@ cudaError_t launch_beamform_tc(const Geometry &g, int n_slots, const __half *fre
                                uint32_t *err_word, cudaStream_t st);
 bool bf_tc_supported(const Geometry &g);
 
+// Learned channel-estimate denoiser (cnn.cu). Parameters packed per layer as W[co][ci][3][3], b[co].
+int cnn_param_count();
+cudaError_t cnn_forward(int n, int w, const __nv_bfloat16 *x, const __nv_bfloat16 *P, float *y, __nv_bfloat16 *acts,
+                        cudaStream_t st);
+cudaError_t cnn_backward(int n, int w, const __nv_bfloat16 *x, const __nv_bfloat16 *acts, const __nv_bfloat16 *P,
+                         const float *y, const float *target, float *grad, float *loss, float *work,
+                         __nv_bfloat16 *wflip, cudaStream_t st);
+cudaError_t cnn_adam(int step, float lr, float b1, float b2, float eps, float *p, __nv_bfloat16 *pb, const float *g,
+                     float *m, float *v, cudaStream_t st);
+cudaError_t launch_ls_grid(const Geometry &g, int n_slots, const float2 *beam, const float2 *pilots,
+                           __nv_bfloat16 *grid, float *scale, cudaStream_t st);
+cudaError_t launch_cnn_to_h(const Geometry &g, int n_slots, float kappa, const float *y, const float *scale,
+                            const float2 *beam, const float2 *pilots, float2 *H, float *resid, uint8_t *fallback,
+                            cudaStream_t st);
+
 }  // namespace pusch
+
+struct pusch_handle {
+    pusch_cell_cfg cfg;
+    pusch::Geometry geo;
+    int max_slots = 0;
+    int device = 0;
+    float2 *twiddle = nullptr;      // exp(-2 pi i q / n_fft), q < n_fft
+    uint32_t *kernel_err = nullptr;   // bounded-wait expiry flags of the tensor-core kernel
+    void *freq = nullptr;           // workspace: FFT output
+    float2 *beam = nullptr;         // workspace: beamformed grid
+    float2 *ls = nullptr;           // workspace: LS values at the pilot subcarriers
+    uint32_t *status_sink = nullptr;  // status words used when the caller passes NULL
+    // staging for pusch_slot_host (allocated on first use)
+    void *h_time = nullptr;
+    float2 *h_pilots = nullptr;
+    float2 *h_xhat = nullptr;
+    uint8_t *h_bits = nullptr;
+    uint32_t *h_status = nullptr;
+    // per-stage timing of pusch_slot (pusch_profile_start / pusch_profile_read)
+    std::vector<cudaEvent_t> prof_events;  // [max_calls][kSlotStages + 1]
+    int prof_max_calls = 0;
+    int prof_calls = 0;
+    // learned-estimator workspace (pusch_chest_cnn; allocated on first use, sized for max_slots)
+    void *cnn_grid = nullptr;       // [grids][2][2][n_sc] bf16
+    float *cnn_scale = nullptr;     // [grids]
+    void *cnn_acts = nullptr;       // [3][grids][32][2][n_sc] bf16
+    float *cnn_y = nullptr;         // [grids][2][2][n_sc]
+};
