@@ -194,11 +194,13 @@ pusch_status pusch_ls_grid(pusch_handle *h, int n_slots, const void *beam, const
                            float *scale, void *stream);
 
 /* Channel estimation with the denoiser: H_hat (layout of pusch_chest_ls) receives, per (slot, layer, beam),
- * the CNN estimate (mean of its two DMRS rows, rescaled) when its pilot residual - the mean over the
- * layer's pilots and both DMRS symbols of |y / p - estimate|^2 - is at most kappa * sigma^2, and the plain
- * LS estimate of pusch_chest_ls otherwise (fallback). resid [grids] (optional) receives residual / sigma^2,
- * fallback [grids] (optional) 1 where the LS estimate was kept. The first call allocates the handle's CNN
- * workspace for max_slots (max_slots * n_layers * n_beams <= 65535 grids). */
+ * the CNN estimate (mean of its two DMRS rows, rescaled), or the plain LS estimate of pusch_chest_ls when
+ * the CNN explains the layer's pilots worse than plain interpolation would (fallback). On the pilots q of
+ * both DMRS symbols, with LS_j[q] = y_j[q] / p_j[q]: r_cnn = mean |LS_j[q] - estimate_j[q]|^2 and
+ * r_ref = max(sigma^2, mean |LS_j[q] - (LS_j[q - comb] + LS_j[q + comb]) / 2|^2) (leave-one-out
+ * interpolation over the inner pilots); fallback when r_cnn > kappa * r_ref. resid [grids] (optional)
+ * receives r_cnn / r_ref, fallback [grids] (optional) 1 where the LS estimate was kept. The first call
+ * allocates the handle's CNN workspace for max_slots (max_slots * n_layers * n_beams <= 65535 grids). */
 pusch_status pusch_chest_cnn(pusch_handle *h, int n_slots, const void *beam, const void *pilots,
                              const void *params_bf16, float kappa, void *H_hat, float *resid, uint8_t *fallback,
                              void *stream);

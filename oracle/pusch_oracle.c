@@ -449,12 +449,15 @@ done:
  * The channel-estimate denoiser: four 3x3 same-padded convolutions 2 -> 32 -> 32 -> 32 -> 2 with ReLU after
  * the first three and the input added to the output (residual). Tensors are [n][c][2][w] (n grids, c
  * channels, the 2 DMRS symbols as rows, w subcarriers); zero padding outside the grid.
- *   conv:  out[n][co][h][x] = b[co] + sum_{ci, dh, dx} W[co][ci][dh][dx] in[n][ci][h + dh - 1][x + dx - 1]
+ *   conv:  out[n][co][h][x] = b[co] + sum_{ci, dh, dx} W[co][ci][dh][dx] in[n][ci][h + dh - 1][x + (dx - 1) d]
+ * with the kernel dilated along the subcarriers by d = 1, 8, 16, 1 for the four layers (receptive field of
+ * +-26 subcarriers, several pilot spacings of a comb of 8 or 16).
  * Parameters are packed layer by layer as W (co, ci, 3, 3) then b (co).
  * bf16 != 0 rounds weights, biases, the input and every stored activation to bfloat16 (round to nearest
  * even), at the points where a bfloat16 implementation stores them; arithmetic stays double.
  */
 static const int CNN_CH[5] = {2, 32, 32, 32, 2};
+static const int CNN_DIL[4] = {1, 8, 16, 1};
 
 int orc_cnn_param_count(void)
 {
@@ -476,7 +479,7 @@ double orc_round_bf16(double v)
     return (double)f;
 }
 
-static void cnn_conv(const double *in, int n, int cin, int w, const double *W, const double *b, int cout,
+static void cnn_conv(const double *in, int n, int cin, int w, const double *W, const double *b, int cout, int dil,
                      double *out)
 {
     for (int s = 0; s < n; ++s)
@@ -489,7 +492,7 @@ static void cnn_conv(const double *in, int n, int cin, int w, const double *W, c
                             int hh = h + dh - 1;
                             if (hh < 0 || hh > 1) continue;
                             for (int dx = 0; dx < 3; ++dx) {
-                                int xx = x + dx - 1;
+                                int xx = x + (dx - 1) * dil;
                                 if (xx < 0 || xx >= w) continue;
                                 acc += W[((co * cin + ci) * 3 + dh) * 3 + dx] *
                                        in[(((size_t)s * cin + ci) * 2 + hh) * w + xx];
@@ -517,7 +520,7 @@ void orc_cnn_forward(const double *params, const double *x, int n, int w, int bf
         int cin = CNN_CH[k], cout = CNN_CH[k + 1];
         const double *W = p + off, *b = p + off + cout * cin * 9;
         off += cout * cin * 9 + cout;
-        cnn_conv(cur, n, cin, w, W, b, cout, z);
+        cnn_conv(cur, n, cin, w, W, b, cout, CNN_DIL[k], z);
         size_t m = (size_t)n * cout * 2 * w;
         if (k < 3) {
             for (size_t i = 0; i < m; ++i) {
@@ -585,7 +588,7 @@ double orc_cnn_loss_grad(const double *params, const double *x, const double *ta
                                 int hh = h + dh - 1;
                                 if (hh < 0 || hh > 1) continue;
                                 for (int dx = 0; dx < 3; ++dx) {
-                                    int xx = x + dx - 1;
+                                    int xx = x + (dx - 1) * CNN_DIL[k];
                                     if (xx < 0 || xx >= w) continue;
                                     dW[((co * cin + ci) * 3 + dh) * 3 + dx] +=
                                         go * in[(((size_t)s * cin + ci) * 2 + hh) * w + xx];
@@ -605,7 +608,7 @@ double orc_cnn_loss_grad(const double *params, const double *x, const double *ta
                                 int hh = h + dh - 1;
                                 if (hh < 0 || hh > 1) continue;
                                 for (int dx = 0; dx < 3; ++dx) {
-                                    int xx = x + dx - 1;
+                                    int xx = x + (dx - 1) * CNN_DIL[k];
                                     if (xx < 0 || xx >= w) continue;
                                     gin[(((size_t)s * cin + ci) * 2 + hh) * w + xx] +=
                                         go * W[((co * cin + ci) * 3 + dh) * 3 + dx];

@@ -1,5 +1,6 @@
 // Learned channel-estimate denoiser: four 3x3 same-padded convolutions 2 -> 32 -> 32 -> 32 -> 2, ReLU after
-// the first three, the input added to the output. Grids are [n][c][2][w]: n grids (one per slot, layer and
+// the first three, the input added to the output; the kernels are dilated along the subcarriers by 1, 8, 16, 1
+// (receptive field +-26 subcarriers, several pilot spacings). Grids are [n][c][2][w]: n grids (one per slot, layer and
 // beam), c channels (re, im of the estimate at the input and output), the two DMRS symbols as rows and w
 // subcarriers. Weights and activations are stored as bfloat16, arithmetic and gradients are FP32, the
 // optimiser keeps FP32 master weights. Parameters are packed per layer as W[co][ci][3][3] then b[co].
@@ -18,6 +19,8 @@ namespace {
 
 constexpr int kConvThreads = 128;
 constexpr int kCh[5] = {2, 32, 32, 32, 2};
+constexpr int kDil[4] = {1, 8, 16, 1};   // kernel dilation along the subcarriers, per layer
+constexpr int kMaxDil = 16;
 
 __device__ __forceinline__ float ldv(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
 __device__ __forceinline__ float ldv(const float *p) { return *p; }
@@ -31,30 +34,31 @@ struct ConvGeom {
     static constexpr int CGS = kConvThreads / COG;     // column groups
     static constexpr int WPT = COUT >= 8 ? 4 : 1;      // output columns per thread (tiles of 128 columns)
     static constexpr int TW = CGS * WPT;               // tile width
-    static constexpr size_t SMEM = (size_t)(COUT * CIN * 9 + CIN * 2 * (TW + 2)) * sizeof(float);
+    static size_t smem(int dil) { return (size_t)(COUT * CIN * 9 + CIN * 2 * (TW + 2 * dil)) * sizeof(float); }
 };
 
-// out[s][co][h][x] = b[co] + sum_{ci, kh, kw} W[co][ci][kh][kw] in[s][ci][h + kh - 1][x + kw - 1]
+// out[s][co][h][x] = b[co] + sum_{ci, kh, kw} W[co][ci][kh][kw] in[s][ci][h + kh - 1][x + (kw - 1) dil]
 //   kOutReluBf16: out (bf16) = relu(.)
 //   kOutResidF32: out (f32)  = . + aux[s][co][h][x]          (aux: the CNN input, bf16)
 //   kOutMaskF32 : out (f32)  = aux[s][co][h][x] > 0 ? . : 0   (aux: an activation, bf16; b is NULL)
 template <int CIN, int COUT, typename TIn, int MODE>
 __global__ void __launch_bounds__(kConvThreads)
 conv3x3_kernel(const TIn *__restrict__ in, const __nv_bfloat16 *__restrict__ W, const __nv_bfloat16 *__restrict__ b,
-               void *__restrict__ out, const __nv_bfloat16 *__restrict__ aux, int w) {
+               void *__restrict__ out, const __nv_bfloat16 *__restrict__ aux, int w, int dil) {
     using G = ConvGeom<CIN, COUT>;
     constexpr int CPT = G::CPT, COG = G::COG, TW = G::TW, kWPT = G::WPT;
     extern __shared__ float sm[];
+    const int TP = TW + 2 * dil;         // tile with halo
     float *sW = sm;                      // [COUT][CIN][9]
-    float *sX = sm + COUT * CIN * 9;     // [CIN][2][TW + 2]
+    float *sX = sm + COUT * CIN * 9;     // [CIN][2][TP], column c <-> x = x0 + c - dil
     const long long s = blockIdx.y;
     const int x0 = blockIdx.x * TW;
     for (int i = threadIdx.x; i < COUT * CIN * 9; i += kConvThreads) sW[i] = __bfloat162float(W[i]);
-    for (int i = threadIdx.x; i < CIN * 2 * (TW + 2); i += kConvThreads) {
-        const int ci = i / (2 * (TW + 2));
-        const int rem = i - ci * 2 * (TW + 2);
-        const int h = rem / (TW + 2);
-        const int xx = rem - h * (TW + 2) + x0 - 1;
+    for (int i = threadIdx.x; i < CIN * 2 * TP; i += kConvThreads) {
+        const int ci = i / (2 * TP);
+        const int rem = i - ci * 2 * TP;
+        const int h = rem / TP;
+        const int xx = rem - h * TP + x0 - dil;
         sX[i] = (xx >= 0 && xx < w) ? ldv(in + ((s * CIN + ci) * 2 + h) * (long long)w + xx) : 0.f;
     }
     __syncthreads();
@@ -69,11 +73,13 @@ conv3x3_kernel(const TIn *__restrict__ in, const __nv_bfloat16 *__restrict__ W, 
         for (int j = 0; j < kWPT; ++j) acc[0][j][c] = acc[1][j][c] = bv;
     }
     for (int ci = 0; ci < CIN; ++ci) {
-        float xv[2][kWPT + 2];
+        float xv[2][3][kWPT];  // [row][tap][column]
 #pragma unroll
         for (int h = 0; h < 2; ++h)
 #pragma unroll
-            for (int j = 0; j < kWPT + 2; ++j) xv[h][j] = sX[(ci * 2 + h) * (TW + 2) + xl + j];
+            for (int kw = 0; kw < 3; ++kw)
+#pragma unroll
+                for (int j = 0; j < kWPT; ++j) xv[h][kw][j] = sX[(ci * 2 + h) * TP + xl + j + kw * dil];
 #pragma unroll
         for (int c = 0; c < CPT; ++c) {
             const float *wp = sW + ((co0 + c) * CIN + ci) * 9;
@@ -85,8 +91,8 @@ conv3x3_kernel(const TIn *__restrict__ in, const __nv_bfloat16 *__restrict__ W, 
 #pragma unroll
                 for (int kw = 0; kw < 3; ++kw) {
                     // output row 0 reads input rows 0 (kh = 1) and 1 (kh = 2); row 1 reads 0 (kh = 0) and 1 (kh = 1)
-                    acc[0][j][c] = fmaf(wv[3 + kw], xv[0][j + kw], fmaf(wv[6 + kw], xv[1][j + kw], acc[0][j][c]));
-                    acc[1][j][c] = fmaf(wv[0 + kw], xv[0][j + kw], fmaf(wv[3 + kw], xv[1][j + kw], acc[1][j][c]));
+                    acc[0][j][c] = fmaf(wv[3 + kw], xv[0][kw][j], fmaf(wv[6 + kw], xv[1][kw][j], acc[0][j][c]));
+                    acc[1][j][c] = fmaf(wv[0 + kw], xv[0][kw][j], fmaf(wv[3 + kw], xv[1][kw][j], acc[1][j][c]));
                 }
         }
     }
@@ -113,20 +119,21 @@ conv3x3_kernel(const TIn *__restrict__ in, const __nv_bfloat16 *__restrict__ W, 
 
 template <int CIN, int COUT, typename TIn, int MODE>
 cudaError_t launch_conv(const TIn *in, const __nv_bfloat16 *W, const __nv_bfloat16 *b, void *out,
-                        const __nv_bfloat16 *aux, int n, int w, cudaStream_t st) {
+                        const __nv_bfloat16 *aux, int n, int w, int dil, cudaStream_t st) {
     using G = ConvGeom<CIN, COUT>;
     auto k = conv3x3_kernel<CIN, COUT, TIn, MODE>;
-    if (G::SMEM > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
+    const size_t smem = G::smem(dil);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem(kMaxDil));
         if (e != cudaSuccess) return e;
     }
     if (n > 65535) return cudaErrorInvalidConfiguration;
     dim3 grid((w + G::TW - 1) / G::TW, n);
-    k<<<grid, kConvThreads, G::SMEM, st>>>(in, W, b, out, aux, w);
+    k<<<grid, kConvThreads, smem, st>>>(in, W, b, out, aux, w, dil);
     return cudaGetLastError();
 }
 
-// dW[co][ci][kh][kw] += sum_{s, h, x} g[s][co][h][x] in[s][ci][h + kh - 1][x + kw - 1];  db[co] += sum g.
+// dW[co][ci][kh][kw] += sum_{s, h, x} g[s][co][h][x] in[s][ci][h + kh - 1][x + (kw - 1) dil];  db[co] += sum g.
 // Persistent CTAs over (grid, 64-column tile) pairs; thread t owns input channel ci = t % CIN and COPT
 // consecutive output channels, accumulating 9 taps each in registers; one atomic add per weight per CTA.
 constexpr int kWgThreads = 256;
@@ -135,12 +142,12 @@ constexpr int kWgTW = 64;
 template <int CIN, int COUT, typename TIn>
 __global__ void __launch_bounds__(kWgThreads)
 conv3x3_wgrad_kernel(const float *__restrict__ g, const TIn *__restrict__ in, float *__restrict__ dW,
-                     float *__restrict__ db, int n, int w) {
+                     float *__restrict__ db, int n, int w, int dil) {
     constexpr int PAIRS = COUT * CIN;
     constexpr int COPT = PAIRS >= 4 * kWgThreads ? 4 : 1;
     constexpr int ACTIVE = PAIRS / COPT;
     __shared__ float sG[COUT][2][kWgTW];
-    __shared__ float sI[CIN][2][kWgTW + 2];
+    __shared__ float sI[CIN][2][kWgTW + 2 * kMaxDil];  // column c <-> x = x0 + c - dil
     const int t = threadIdx.x;
     const bool act = t < ACTIVE;
     const int ci = t % CIN;
@@ -163,10 +170,11 @@ conv3x3_wgrad_kernel(const float *__restrict__ g, const TIn *__restrict__ in, fl
             const int co = i / (2 * kWgTW), rem = i - co * 2 * kWgTW, h = rem / kWgTW, x = rem - h * kWgTW + x0;
             sG[co][h][rem - h * kWgTW] = x < w ? g[((s * COUT + co) * 2 + h) * (long long)w + x] : 0.f;
         }
-        for (int i = t; i < CIN * 2 * (kWgTW + 2); i += kWgThreads) {
-            const int c = i / (2 * (kWgTW + 2)), rem = i - c * 2 * (kWgTW + 2), h = rem / (kWgTW + 2);
-            const int x = rem - h * (kWgTW + 2) + x0 - 1;
-            sI[c][h][rem - h * (kWgTW + 2)] = (x >= 0 && x < w) ? ldv(in + ((s * CIN + c) * 2 + h) * (long long)w + x) : 0.f;
+        const int TP = kWgTW + 2 * dil;
+        for (int i = t; i < CIN * 2 * TP; i += kWgThreads) {
+            const int c = i / (2 * TP), rem = i - c * 2 * TP, h = rem / TP;
+            const int x = rem - h * TP + x0 - dil;
+            sI[c][h][rem - h * TP] = (x >= 0 && x < w) ? ldv(in + ((s * CIN + c) * 2 + h) * (long long)w + x) : 0.f;
         }
         __syncthreads();
         if (act) {
@@ -175,7 +183,7 @@ conv3x3_wgrad_kernel(const float *__restrict__ g, const TIn *__restrict__ in, fl
 #pragma unroll
                 for (int h = 0; h < 2; ++h)
 #pragma unroll
-                    for (int kw = 0; kw < 3; ++kw) iv[h][kw] = sI[ci][h][x + kw];
+                    for (int kw = 0; kw < 3; ++kw) iv[h][kw] = sI[ci][h][x + kw * dil];
 #pragma unroll
                 for (int c = 0; c < COPT; ++c) {
                     const int co = cq * COPT + c;
@@ -205,7 +213,7 @@ conv3x3_wgrad_kernel(const float *__restrict__ g, const TIn *__restrict__ in, fl
 }
 
 template <int CIN, int COUT, typename TIn>
-cudaError_t launch_wgrad(const float *g, const TIn *in, float *dW, float *db, int n, int w, cudaStream_t st) {
+cudaError_t launch_wgrad(const float *g, const TIn *in, float *dW, float *db, int n, int w, int dil, cudaStream_t st) {
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -213,7 +221,7 @@ cudaError_t launch_wgrad(const float *g, const TIn *in, float *dW, float *db, in
     long long grid = 2LL * sms;
     if (grid > tiles) grid = tiles;
     if (grid < 1) return cudaSuccess;
-    conv3x3_wgrad_kernel<CIN, COUT, TIn><<<(unsigned)grid, kWgThreads, 0, st>>>(g, in, dW, db, n, w);
+    conv3x3_wgrad_kernel<CIN, COUT, TIn><<<(unsigned)grid, kWgThreads, 0, st>>>(g, in, dW, db, n, w, dil);
     return cudaGetLastError();
 }
 
@@ -272,16 +280,17 @@ cudaError_t cnn_forward(int n, int w, const __nv_bfloat16 *x, const __nv_bfloat1
     const __nv_bfloat16 *W0 = P + param_offset(0), *W1 = P + param_offset(1), *W2 = P + param_offset(2),
                         *W3 = P + param_offset(3);
     cudaError_t e;
-    if ((e = launch_conv<2, 32, __nv_bfloat16, kOutReluBf16>(x, W0, W0 + 32 * 2 * 9, acts, nullptr, n, w, st)) !=
-        cudaSuccess)
+    if ((e = launch_conv<2, 32, __nv_bfloat16, kOutReluBf16>(x, W0, W0 + 32 * 2 * 9, acts, nullptr, n, w, kDil[0],
+                                                             st)) != cudaSuccess)
         return e;
     if ((e = launch_conv<32, 32, __nv_bfloat16, kOutReluBf16>(acts, W1, W1 + 32 * 32 * 9, acts + big, nullptr, n, w,
-                                                              st)) != cudaSuccess)
+                                                              kDil[1], st)) != cudaSuccess)
         return e;
     if ((e = launch_conv<32, 32, __nv_bfloat16, kOutReluBf16>(acts + big, W2, W2 + 32 * 32 * 9, acts + 2 * big,
-                                                              nullptr, n, w, st)) != cudaSuccess)
+                                                              nullptr, n, w, kDil[2], st)) != cudaSuccess)
         return e;
-    return launch_conv<32, 2, __nv_bfloat16, kOutResidF32>(acts + 2 * big, W3, W3 + 2 * 32 * 9, y, x, n, w, st);
+    return launch_conv<32, 2, __nv_bfloat16, kOutResidF32>(acts + 2 * big, W3, W3 + 2 * 32 * 9, y, x, n, w, kDil[3],
+                                                           st);
 }
 
 // Backward pass: grad (zeroed here) = d mean((y - target)^2) / d params; *loss = that mean (if loss != NULL).
@@ -307,24 +316,27 @@ cudaError_t cnn_backward(int n, int w, const __nv_bfloat16 *x, const __nv_bfloat
     float *G3 = grad + param_offset(3), *G2 = grad + param_offset(2), *G1 = grad + param_offset(1),
           *G0 = grad + param_offset(0);
     // layer 4 (32 -> 2): weights from a3, input gradient into a3's channels, masked by a3 > 0
-    if ((e = launch_wgrad<32, 2, __nv_bfloat16>(ga, acts + 2 * big, G3, G3 + 2 * 32 * 9, n, w, st)) != cudaSuccess)
+    if ((e = launch_wgrad<32, 2, __nv_bfloat16>(ga, acts + 2 * big, G3, G3 + 2 * 32 * 9, n, w, kDil[3], st)) !=
+        cudaSuccess)
         return e;
     if ((e = launch_conv<2, 32, float, kOutMaskF32>(ga, wflip + param_offset(3), nullptr, gb, acts + 2 * big, n, w,
-                                                    st)) != cudaSuccess)
+                                                    kDil[3], st)) != cudaSuccess)
         return e;
     // layer 3 (32 -> 32)
-    if ((e = launch_wgrad<32, 32, __nv_bfloat16>(gb, acts + big, G2, G2 + 32 * 32 * 9, n, w, st)) != cudaSuccess)
-        return e;
-    if ((e = launch_conv<32, 32, float, kOutMaskF32>(gb, wflip + param_offset(2), nullptr, ga, acts + big, n, w, st)) !=
+    if ((e = launch_wgrad<32, 32, __nv_bfloat16>(gb, acts + big, G2, G2 + 32 * 32 * 9, n, w, kDil[2], st)) !=
         cudaSuccess)
+        return e;
+    if ((e = launch_conv<32, 32, float, kOutMaskF32>(gb, wflip + param_offset(2), nullptr, ga, acts + big, n, w,
+                                                     kDil[2], st)) != cudaSuccess)
         return e;
     // layer 2 (32 -> 32)
-    if ((e = launch_wgrad<32, 32, __nv_bfloat16>(ga, acts, G1, G1 + 32 * 32 * 9, n, w, st)) != cudaSuccess) return e;
-    if ((e = launch_conv<32, 32, float, kOutMaskF32>(ga, wflip + param_offset(1), nullptr, gb, acts, n, w, st)) !=
-        cudaSuccess)
+    if ((e = launch_wgrad<32, 32, __nv_bfloat16>(ga, acts, G1, G1 + 32 * 32 * 9, n, w, kDil[1], st)) != cudaSuccess)
+        return e;
+    if ((e = launch_conv<32, 32, float, kOutMaskF32>(ga, wflip + param_offset(1), nullptr, gb, acts, n, w, kDil[1],
+                                                     st)) != cudaSuccess)
         return e;
     // layer 1 (2 -> 32): weights only
-    return launch_wgrad<2, 32, __nv_bfloat16>(gb, x, G0, G0 + 32 * 2 * 9, n, w, st);
+    return launch_wgrad<2, 32, __nv_bfloat16>(gb, x, G0, G0 + 32 * 2 * 9, n, w, kDil[0], st);
 }
 
 cudaError_t cnn_adam(int step, float lr, float b1, float b2, float eps, float *p, __nv_bfloat16 *pb, const float *g,
@@ -405,10 +417,13 @@ ls_grid_kernel(GridArgs g, const float2 *__restrict__ beam, const float2 *__rest
     }
 }
 
-// Denoised estimate of grid gi: H = scale * (y_row0 + y_row1) / 2. The pilot residual
-// r = mean over the layer's pilots and both DMRS symbols of |y_j[q] / p_j[q] - scale * y_row_j[q]|^2 is
-// compared with kappa * sigma^2: at or below, the grid's estimate replaces the plain LS estimate in H_hat;
-// above, the plain LS estimate already in H_hat is kept (fallback). resid[gi] = r / sigma^2.
+// Denoised estimate of grid gi: H = scale * (y_row0 + y_row1) / 2.
+// Fallback test on the layer's pilots q (both DMRS symbols j, LS_j[q] = y_j[q] / p_j[q]):
+//   r_cnn = mean |LS_j[q] - scale * y_row_j[q]|^2                 (how well the estimate explains the pilots)
+//   r_ref = mean |LS_j[q] - (LS_j[q - comb] + LS_j[q + comb]) / 2|^2 over the inner pilots
+//           (how well plain linear interpolation predicts a pilot from its neighbours), floored at sigma^2.
+// r_cnn <= kappa * r_ref: the CNN estimate replaces the plain LS estimate in H_hat; otherwise the plain LS
+// estimate already written there is kept (fallback). resid[gi] = r_cnn / r_ref.
 __global__ void __launch_bounds__(256)
 cnn_to_h_kernel(GridArgs g, float noise_var, float kappa, const float *__restrict__ y, const float *__restrict__ scale,
                 const float2 *__restrict__ beam, const float2 *__restrict__ pilots, float2 *__restrict__ H,
@@ -427,20 +442,30 @@ cnn_to_h_kernel(GridArgs g, float noise_var, float kappa, const float *__restric
     const float sc = scale[gi];
     const int port = g.port[l];
     const int npil = (g.n_sc - 1 - port) / g.comb + 1;
-    float rs = 0.f;
+    auto ls = [&](const float2 *yy, const float2 *pp, int q) {
+        return cmul(__ldg(&yy[(long long)q * g.n_beams]), pilot_inverse(__ldg(&pp[q])));
+    };
+    float rc = 0.f, rr = 0.f;
     for (int k = threadIdx.x; k < npil; k += blockDim.x) {
         const int q = port + k * g.comb;
-        const float2 l0 = cmul(__ldg(&y0[(long long)q * g.n_beams]), pilot_inverse(__ldg(&p0[q])));
-        const float2 l1 = cmul(__ldg(&y1[(long long)q * g.n_beams]), pilot_inverse(__ldg(&p1[q])));
+        const float2 l0 = ls(y0, p0, q), l1 = ls(y1, p1, q);
         const float d0x = l0.x - sc * yo[0 * g.n_sc + q], d0y = l0.y - sc * yo[2 * g.n_sc + q];
         const float d1x = l1.x - sc * yo[1 * g.n_sc + q], d1y = l1.y - sc * yo[3 * g.n_sc + q];
-        rs += d0x * d0x + d0y * d0y + d1x * d1x + d1y * d1y;
+        rc += d0x * d0x + d0y * d0y + d1x * d1x + d1y * d1y;
+        if (k > 0 && k + 1 < npil) {
+            const float2 a0 = ls(y0, p0, q - g.comb), b0 = ls(y0, p0, q + g.comb);
+            const float2 a1 = ls(y1, p1, q - g.comb), b1 = ls(y1, p1, q + g.comb);
+            const float e0x = l0.x - 0.5f * (a0.x + b0.x), e0y = l0.y - 0.5f * (a0.y + b0.y);
+            const float e1x = l1.x - 0.5f * (a1.x + b1.x), e1y = l1.y - 0.5f * (a1.y + b1.y);
+            rr += e0x * e0x + e0y * e0y + e1x * e1x + e1y * e1y;
+        }
     }
-    const float r = block_sum(rs, red) / (2.f * npil);
-    const float nv = noise_var > 0.f ? noise_var : 1e-30f;
-    const bool use_cnn = r <= kappa * nv;
+    const float r_cnn = block_sum(rc, red) / (2.f * npil);
+    const float r_loo = npil > 2 ? block_sum(rr, red) / (2.f * (npil - 2)) : 0.f;
+    const float r_ref = fmaxf(r_loo, noise_var > 0.f ? noise_var : 1e-30f);
+    const bool use_cnn = r_cnn <= kappa * r_ref;
     if (threadIdx.x == 0) {
-        if (resid) resid[gi] = r / nv;
+        if (resid) resid[gi] = r_cnn / r_ref;
         if (fallback) fallback[gi] = use_cnn ? 0 : 1;
     }
     if (!use_cnn) return;

@@ -53,6 +53,7 @@ class CellConfig:
     delay_spread_s: float = 300e-9
     n_taps: int = 16
     tap_spacing_s: float = 60e-9
+    doppler_hz: float = 0.0  # > 0: each tap fades over the slot (sum of 16 sinusoids, Clarke/Jakes spectrum)
     seed: int = 0
 
     @property
@@ -72,7 +73,11 @@ DEPLOY = CellConfig("deploy-64rx-4096fft-32beam-16ue", n_rx=64, n_fft=4096, n_sc
 MASSIVE = CellConfig("massive-256rx-4096fft-64beam-32ue", n_rx=256, n_fft=4096, n_sc=3276, n_beams=64,
                      n_layers=32, qam_bits=4, snr_db=25.0, channel="pdp", beam="dft", in_fp16=True, seed=5)
 
-PRESETS = {"small": SMALL_FP32, "deploy": DEPLOY, "massive": MASSIVE}
+# Evaluation cell of the learned estimator (the deployment cell with a fading channel): 300 ns delay
+# spread, 200 Hz maximum Doppler; the SNR is swept by the caller.
+DENOISE_EVAL = DEPLOY.with_(name="denoise-64rx-4096fft-32beam-16ue-doppler", doppler_hz=200.0, seed=4)
+
+PRESETS = {"small": SMALL_FP32, "deploy": DEPLOY, "massive": MASSIVE, "denoise": DENOISE_EVAL}
 
 
 def active_bins(n_sc: int, n_fft: int) -> np.ndarray:
@@ -135,6 +140,32 @@ def _channel(cfg: CellConfig, rng: np.random.Generator) -> np.ndarray:
     raise ValueError(f"unknown channel model {cfg.channel}")
 
 
+_SYM_S = 1.0 / _SCS_HZ * (1 + 0.0703125)  # OFDM symbol duration with the normal cyclic prefix
+
+
+def _channel_per_symbol(cfg: CellConfig, rng: np.random.Generator):
+    """Time-varying PDP channel: list of 14 arrays Hant_s [N_SC, R, L]. Tap i of (r, l) is
+    sqrt(p_i / M) sum_m exp(j (2 pi f_d cos(alpha_m) t + phi_m)) with uniformly random alpha, phi (M = 16)."""
+    R, L, n_sc = cfg.n_rx, cfg.n_layers, cfg.n_sc
+    ts = 1.0 / (cfg.n_fft * _SCS_HZ)
+    i = np.arange(cfg.n_taps)
+    delays = np.round(i * cfg.tap_spacing_s / ts)
+    power = np.exp(-i * cfg.tap_spacing_s / cfg.delay_spread_s)
+    power = power / power.sum()
+    M = 16
+    alpha = rng.uniform(0, 2 * np.pi, (R, L, cfg.n_taps, M))
+    phi = rng.uniform(0, 2 * np.pi, (R, L, cfg.n_taps, M))
+    k = (np.arange(n_sc) - n_sc // 2)[:, None]
+    F = np.exp(-2j * np.pi * k * delays[None, :] / cfg.n_fft)                   # [N_SC, taps]
+    out = []
+    for s in range(N_SYM):
+        t = s * _SYM_S
+        taps = np.exp(1j * (2 * np.pi * cfg.doppler_hz * np.cos(alpha) * t + phi)).sum(-1) / np.sqrt(M)
+        taps = taps * np.sqrt(power)                                              # [R, L, taps]
+        out.append(np.matmul(F, taps.reshape(R * L, -1).T).reshape(n_sc, R, L))
+    return out
+
+
 @dataclass
 class Slot:
     cfg: CellConfig
@@ -165,7 +196,12 @@ def make_slot(cfg: CellConfig, slot_index: int = 0, seed: int | None = None) -> 
     comb = cfg.comb
     ports = np.arange(L, dtype=np.int32) % comb
 
-    Hant = _channel(cfg, rng)                                            # [N_SC, R, L]
+    if cfg.doppler_hz > 0 and cfg.channel == "pdp":
+        Hsym = _channel_per_symbol(cfg, rng)                             # 14 x [N_SC, R, L]
+        Hant = Hsym[DMRS_SYMBOLS[0]]
+    else:
+        Hant = _channel(cfg, rng)                                        # [N_SC, R, L]
+        Hsym = None
     W = beam_matrix(cfg)
     noise_var = float(10.0 ** (-cfg.snr_db / 10.0))
 
@@ -187,7 +223,10 @@ def make_slot(cfg: CellConfig, slot_index: int = 0, seed: int | None = None) -> 
     for j, s in enumerate(DATA_SYMBOLS):
         t[:, s, :] = x[:, j, :]
 
-    X = np.matmul(Hant, np.ascontiguousarray(t.transpose(2, 0, 1))).transpose(2, 1, 0)   # [S, R, N_SC]
+    if Hsym is None:
+        X = np.matmul(Hant, np.ascontiguousarray(t.transpose(2, 0, 1))).transpose(2, 1, 0)   # [S, R, N_SC]
+    else:
+        X = np.stack([np.einsum("arl,la->ra", Hsym[s], t[:, s, :]) for s in range(N_SYM)])
     noise = (rng.standard_normal(X.shape) + 1j * rng.standard_normal(X.shape)) * np.sqrt(noise_var / 2.0)
     X = X + noise
 

@@ -109,3 +109,24 @@ def test_gradients_match_finite_differences(orc, bf16):
         lb, gb = orc.cnn_loss_grad(p, x, t, bf16=True)
         assert abs(lb - loss) < 0.05 * loss
         assert np.linalg.norm(gb - g) < 0.1 * np.linalg.norm(g)
+
+
+def test_dilation_shifts_by_the_layer_dilation(orc):
+    """A single right-hand tap in layer 2 (dilation 8) or layer 3 (dilation 16) moves the signal by 8 or 16
+    subcarriers; layers 1 and 4 use dilation 1."""
+    o = offsets()
+    for layer, d in ((1, 8), (2, 16)):
+        p = np.zeros(orc.cnn_param_count())
+        for k in range(3):
+            W = p[o[k][0]:o[k][1]].reshape(CH[k + 1], CH[k], 3, 3)
+            if k == layer:
+                W[0, 0, 1, 2] = 1.0            # in[x + d]
+            else:
+                W[0, 0, 1, 1] = 1.0
+        W4 = p[o[3][0]:o[3][1]].reshape(2, 32, 3, 3)
+        W4[0, 0, 1, 1] = 1.0
+        x = np.abs(RNG.standard_normal((1, 2, 2, 40)))
+        y, _ = orc.cnn_forward(p, x)
+        want = np.zeros_like(x[0, 0])
+        want[:, :40 - d] = x[0, 0][:, d:]
+        assert np.allclose(y[0, 0] - x[0, 0], want, atol=1e-14)
