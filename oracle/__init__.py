@@ -58,6 +58,11 @@ def lib():
             "orc_cnn_loss_grad": (D, [P, P, P, I, I, I, P]),
             "orc_op_counts": (None, [I, I, I, I, I, I, P]),
             "orc_slot": (I, [P, I, I, I, I, P, I, P, I, P, P, I, I, D, D, P, P]),
+            "orc_e4m3_round": (D, [D]),
+            "orc_e4m3_round_array": (None, [P, LL, P]),
+            "orc_e4m3_block_exp": (I, [D]),
+            "orc_e4m3_quant_rows": (None, [P, LL, I, P, P]),
+            "orc_beamform_fp8": (None, [P, P, P, I, I, I, I, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -259,3 +264,40 @@ def cnn_loss_grad(params, x, target, bf16: bool = False):
     g = np.empty_like(params)
     loss = lib().orc_cnn_loss_grad(_p(params), _p(x), _p(target), n, w, 1 if bf16 else 0, _p(g))
     return float(loss), g
+
+
+# ------------------------------------------------------------------------------------ FP8 E4M3 form
+
+def e4m3_round(v) -> np.ndarray:
+    """Nearest E4M3 value (ties to even, saturating at +-448) of every element."""
+    x = _f64(v)
+    y = np.empty_like(x)
+    lib().orc_e4m3_round_array(_p(x), x.size, _p(y))
+    return y
+
+
+def e4m3_block_exp(amax: float) -> int:
+    return int(lib().orc_e4m3_block_exp(float(amax)))
+
+
+def e4m3_quant_rows(x):
+    """x complex [..., n] -> (codes complex [..., n] (E4M3 values, scale not applied), exps int [..., n_blk])."""
+    x = _c128(x)
+    n = x.shape[-1]
+    rows = x.size // n if n else 0
+    codes = np.empty_like(x)
+    exps = np.empty(x.shape[:-1] + ((n + 127) // 128,), dtype=np.int32)
+    lib().orc_e4m3_quant_rows(_p(x), rows, n, _p(codes), _p(exps))
+    return codes, exps
+
+
+def beamform_fp8(codes, exps, W) -> np.ndarray:
+    """codes [n_sym, n_rx, n_sc] (E4M3 values), exps [n_sym, n_rx, ceil(n_sc/128)], W [n_rx, n_beams]
+    -> beam [n_sym, n_sc, n_beams] of the FP8 form's block-scaled product."""
+    codes, exps, W = _c128(codes), _i32(exps), _c128(W)
+    n_sym, n_rx, n_sc = codes.shape
+    n_beams = W.shape[1]
+    assert exps.shape == (n_sym, n_rx, (n_sc + 127) // 128) and W.shape[0] == n_rx
+    beam = np.empty((n_sym, n_sc, n_beams), dtype=np.complex128)
+    lib().orc_beamform_fp8(_p(codes), _p(exps), _p(W), n_sym, n_rx, n_sc, n_beams, _p(beam))
+    return beam

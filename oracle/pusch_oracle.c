@@ -22,6 +22,9 @@
  *                   are detected jointly).
  *   orc_demap       Gray hard decisions of 3GPP TS 38.211 5.1.3/5.1.4 (QPSK/16-QAM).
  *   orc_op_counts   Table I complex-MAC model.
+ *   orc_e4m3_*,     the FP8 precision form of the beamforming step (not in the paper; the form this
+ *   orc_beamform_fp8  project adds): E4M3 rounding, power-of-two block scales, and the block-scaled
+ *                   product y = W^H x with its exact power-of-two alignment.
  *
  * Layouts (complex values interleaved re,im; C99 double complex):
  *   time  [n_sym][n_rx][n_fft]     freq [n_sym][n_rx][n_sc]     beam [n_sym][n_sc][n_beams]
@@ -624,4 +627,132 @@ double orc_cnn_loss_grad(const double *params, const double *x, const double *ta
     free(g);
     free(gin);
     return loss;
+}
+
+/* ------------------------------------------------------------------ FP8 E4M3 form ---- */
+/*
+ * The FP8 form of the beamforming product (Section II "MMM with known coefficients" in a reduced-precision
+ * storage format this project adds; the paper has no FP8). Values are stored as E4M3 codes times
+ * power-of-two block scales. E4M3: sign, 4 exponent bits (bias 7), 3 mantissa bits, no infinities;
+ * normal values (1 + m/8) 2^(e-7) for e = 1..15 (m <= 6 when e = 15, so the largest is 448), subnormal
+ * values (m/8) 2^-6.
+ */
+
+/* Nearest E4M3 value, ties to the even mantissa; magnitudes of 448 and above give +-448 (saturation);
+ * NaN stays NaN. */
+double orc_e4m3_round(double v)
+{
+    if (isnan(v)) return v;
+    double a = fabs(v);
+    if (a >= 448.0) return copysign(448.0, v);
+    int ex;
+    frexp(a, &ex);              /* a in [2^(ex-1), 2^ex) */
+    int p = ex - 1;             /* binade of a */
+    if (p < -6) p = -6;         /* the subnormals share the spacing of the lowest normal binade */
+    double q = ldexp(1.0, p - 3);            /* spacing of the 3-bit mantissa grid */
+    return copysign(nearbyint(a / q) * q, v);  /* default rounding mode: nearest, ties to even */
+}
+
+void orc_e4m3_round_array(const double *x, long long n, double *y)
+{
+    for (long long i = 0; i < n; ++i) y[i] = orc_e4m3_round(x[i]);
+}
+
+/* Exponent of the power-of-two block scale: the smallest integer e >= -126 with amax <= 448 * 2^e;
+ * 128 for a non-finite amax. */
+int orc_e4m3_block_exp(double amax)
+{
+    if (!isfinite(amax)) return 128;
+    int e = -126;
+    while (amax > 448.0 * ldexp(1.0, e)) ++e;
+    return e;
+}
+
+/* Block quantisation of rows of complex samples: each block of 128 consecutive entries of a row gets
+ * e = orc_e4m3_block_exp(largest |Re|, |Im| of the block) and every component becomes
+ * orc_e4m3_round(value / 2^e). codes [rows][n] (the E4M3 values, scale not applied), exps
+ * [rows][ceil(n / 128)]; a block with a non-finite component gets e = 128 and NaN codes. */
+void orc_e4m3_quant_rows(const cplx *x, long long rows, int n, cplx *codes, int *exps)
+{
+    int n_blk = (n + 127) / 128;
+    for (long long r = 0; r < rows; ++r)
+        for (int j = 0; j < n_blk; ++j) {
+            double amax = 0.0;
+            int bad = 0;
+            for (int a = 128 * j; a < n && a < 128 * j + 128; ++a) {
+                double re = fabs(creal(x[r * n + a])), im = fabs(cimag(x[r * n + a]));
+                if (!isfinite(re) || !isfinite(im)) bad = 1;
+                if (re > amax) amax = re;
+                if (im > amax) amax = im;
+            }
+            int e = bad ? 128 : orc_e4m3_block_exp(amax);
+            exps[r * n_blk + j] = e;
+            for (int a = 128 * j; a < n && a < 128 * j + 128; ++a) {
+                cplx v = x[r * n + a];
+                codes[r * n + a] = bad ? NAN : orc_e4m3_round(ldexp(creal(v), -e)) + I * orc_e4m3_round(ldexp(cimag(v), -e));
+            }
+        }
+}
+
+/* FP8-form beamforming. codes [n_sym][n_rx][n_sc] (E4M3 values) with block exponents exps
+ * [n_sym][n_rx][ceil(n_sc / 128)] are the samples; W [n_rx][n_beams] is quantised here with one block
+ * exponent per (beam, 128 antennas): ew = orc_e4m3_block_exp(largest |Re|, |Im| of the block),
+ * cw = E4M3(W / 2^ew). The product aligns the block scales by powers of two:
+ *   the samples of subcarrier block j are brought to E = max over antennas of exps[s][r][j]:
+ *       xq = E4M3(code * 2^(exps - E)), sample = xq 2^E;
+ *   the weights of beam b are brought to E_b = max over its blocks of ew:
+ *       wq = E4M3(cw * 2^(ew - E_b)), weight = wq 2^E_b;
+ *   beam[s][a][b] = sum_r conj(weight[r][b]) sample[s][r][a].
+ * The alignment changes no value unless a shifted code falls below the smallest normal E4M3 (2^-6).
+ * A block exponent of 128 (non-finite block) makes the affected outputs NaN. */
+void orc_beamform_fp8(const cplx *codes, const int *exps, const cplx *W, int n_sym, int n_rx, int n_sc, int n_beams,
+                      cplx *beam)
+{
+    int n_blk = (n_sc + 127) / 128, n_kb = (n_rx + 127) / 128;
+    cplx *wv = malloc(sizeof(cplx) * (size_t)n_rx * n_beams);
+    double *wscale = malloc(sizeof(double) * (size_t)n_beams);
+    int *ew = malloc(sizeof(int) * (size_t)n_kb);
+    for (int b = 0; b < n_beams; ++b) {
+        int eb = -126, bad = 0;
+        for (int kb = 0; kb < n_kb; ++kb) {
+            double amax = 0.0;
+            for (int r = 128 * kb; r < n_rx && r < 128 * kb + 128; ++r) {
+                double re = fabs(creal(W[r * n_beams + b])), im = fabs(cimag(W[r * n_beams + b]));
+                if (!isfinite(re) || !isfinite(im)) bad = 1;
+                if (re > amax) amax = re;
+                if (im > amax) amax = im;
+            }
+            ew[kb] = orc_e4m3_block_exp(amax);
+            if (ew[kb] > eb) eb = ew[kb];
+        }
+        wscale[b] = bad ? NAN : ldexp(1.0, eb);
+        for (int r = 0; r < n_rx; ++r) {
+            cplx w = W[r * n_beams + b];
+            int e = ew[r / 128];
+            double cr = orc_e4m3_round(ldexp(creal(w), -e)), ci = orc_e4m3_round(ldexp(cimag(w), -e));
+            wv[r * n_beams + b] = orc_e4m3_round(ldexp(cr, e - eb)) + I * orc_e4m3_round(ldexp(ci, e - eb));
+        }
+    }
+    for (int s = 0; s < n_sym; ++s)
+        for (int j = 0; j < n_blk; ++j) {
+            int E = -126;
+            for (int r = 0; r < n_rx; ++r) {
+                int e = exps[((long long)s * n_rx + r) * n_blk + j];
+                if (e > E) E = e;
+            }
+            for (int a = 128 * j; a < n_sc && a < 128 * j + 128; ++a)
+                for (int b = 0; b < n_beams; ++b) {
+                    cplx acc = 0;
+                    for (int r = 0; r < n_rx; ++r) {
+                        int e = exps[((long long)s * n_rx + r) * n_blk + j];
+                        cplx c = codes[((long long)s * n_rx + r) * n_sc + a];
+                        cplx xq = orc_e4m3_round(ldexp(creal(c), e - E)) + I * orc_e4m3_round(ldexp(cimag(c), e - E));
+                        acc += conj(wv[r * n_beams + b]) * xq;
+                    }
+                    beam[((long long)s * n_sc + a) * n_beams + b] = E >= 128 ? NAN : acc * ldexp(1.0, E) * wscale[b];
+                }
+        }
+    free(wv);
+    free(wscale);
+    free(ew);
 }

@@ -1,0 +1,129 @@
+"""Pins of the oracle's FP8 (E4M3) form of the beamforming product: the rounding against the format's own bit
+definition and a library cast, the power-of-two block scale against its definition, the block quantiser's
+error bound, and the block-scaled product against plain products of exactly known operands."""
+import numpy as np
+import pytest
+
+RNG = np.random.default_rng(8)
+
+
+def e4m3_decode(code: int) -> float:
+    """Value of an E4M3 bit pattern from the format definition (sign, 4-bit exponent bias 7, 3-bit mantissa;
+    S.1111.111 is NaN)."""
+    s = -1.0 if code & 0x80 else 1.0
+    e = (code >> 3) & 0xF
+    m = code & 0x7
+    if e == 0xF and m == 0x7:
+        return float("nan")
+    if e == 0:
+        return s * (m / 8.0) * 2.0 ** -6
+    return s * (1.0 + m / 8.0) * 2.0 ** (e - 7)
+
+
+FINITE = sorted({e4m3_decode(c) for c in range(256) if not np.isnan(e4m3_decode(c))})
+
+
+def test_every_code_is_a_fixed_point_and_448_is_the_largest(orc):
+    vals = np.array(FINITE)
+    assert len(vals) == 253                 # 2 * 126 nonzero finite magnitudes + one zero (+0 == -0)
+    assert np.array_equal(orc.e4m3_round(vals), vals)
+    assert vals.max() == 448.0 and vals.min() == -448.0
+    assert min(v for v in FINITE if v > 0) == 2.0 ** -9
+
+
+def test_midpoints_round_to_even_mantissa(orc):
+    pos = [v for v in FINITE if v >= 0]
+    codes = {e4m3_decode(c): c for c in range(128) if not np.isnan(e4m3_decode(c))}
+    for lo, hi in zip(pos[:-1], pos[1:]):
+        mid = 0.5 * (lo + hi)
+        want = lo if codes[lo] % 2 == 0 else hi
+        assert orc.e4m3_round([mid])[0] == want, (lo, hi)
+        assert orc.e4m3_round([-mid])[0] == -want
+        # just off the midpoint the nearer value wins
+        assert orc.e4m3_round([np.nextafter(mid, 0)])[0] == lo
+        assert orc.e4m3_round([np.nextafter(mid, 1e9)])[0] == hi
+
+
+def test_saturation_and_nan(orc):
+    out = orc.e4m3_round([449.0, 464.0, 465.0, 1e30, -1e30, np.inf, np.nan])
+    assert list(out[:6]) == [448.0, 448.0, 448.0, 448.0, -448.0, 448.0]
+    assert np.isnan(out[6])
+
+
+def test_rounding_matches_library_cast(orc):
+    torch = pytest.importorskip("torch")
+    if not hasattr(torch, "float8_e4m3fn"):
+        pytest.skip("no float8 dtype")
+    v = RNG.uniform(-1, 1, 20000) * 2.0 ** RNG.integers(-12, 9, 20000)
+    v = np.clip(v, -448, 448).astype(np.float32).astype(np.float64)
+    ref = torch.from_numpy(v).to(torch.float8_e4m3fn).to(torch.float64).numpy()
+    assert np.array_equal(orc.e4m3_round(v), ref)
+
+
+def test_block_exponent_definition(orc):
+    assert orc.e4m3_block_exp(448.0) == 0
+    assert orc.e4m3_block_exp(448.0 * (1 + 2.0 ** -40)) == 1
+    assert orc.e4m3_block_exp(224.0) == -1
+    assert orc.e4m3_block_exp(448.0 * 2.0 ** -20) == -20
+    assert orc.e4m3_block_exp(0.0) == -126 and orc.e4m3_block_exp(1e-300) == -126
+    assert orc.e4m3_block_exp(np.inf) == 128 and orc.e4m3_block_exp(np.nan) == 128
+    for a in RNG.uniform(0, 1, 200) * 10.0 ** RNG.integers(-20, 20, 200):
+        e = orc.e4m3_block_exp(a)
+        assert a <= 448.0 * 2.0 ** e and (e == -126 or a > 448.0 * 2.0 ** (e - 1))
+
+
+def test_row_quantisation_error_bound_and_range(orc):
+    x = (RNG.standard_normal((5, 300)) + 1j * RNG.standard_normal((5, 300))) * 10.0 ** RNG.integers(-3, 3, (5, 1))
+    x[2, 128:256] = 0.0                                          # an all-zero block
+    codes, exps = orc.e4m3_quant_rows(x)
+    assert exps.shape == (5, 3)
+    assert np.all(exps[2, 1] == -126) and np.all(codes[2, 128:256] == 0)
+    for r in range(5):
+        for j in range(3):
+            blk = slice(128 * j, min(300, 128 * j + 128))
+            v, c, e = x[r, blk], codes[r, blk], exps[r, j]
+            comp_v = np.r_[v.real, v.imag]
+            comp_c = np.r_[c.real, c.imag]
+            if np.all(comp_v == 0):
+                continue
+            assert 224.0 < np.abs(comp_v).max() / 2.0 ** e <= 448.0
+            assert np.abs(comp_c).max() <= 448.0
+            err = np.abs(comp_c * 2.0 ** e - comp_v)
+            # half a unit in the last place: 2^-4 relative for normal codes, 2^-10 * 2^e absolute below 2^-6
+            bound = np.maximum(2.0 ** -4 * np.abs(comp_v), 2.0 ** -10 * 2.0 ** e)
+            assert np.all(err <= bound * (1 + 1e-12))
+
+
+def test_nonfinite_block_is_marked(orc):
+    x = np.ones((1, 200), complex)
+    x[0, 150] = np.nan
+    codes, exps = orc.e4m3_quant_rows(x)
+    assert exps[0, 0] == orc.e4m3_block_exp(1.0) == -8 and exps[0, 1] == 128
+    assert np.all(np.isnan(codes[0, 128:]))
+
+
+def test_fp8_product_is_the_plain_product_when_alignment_is_exact(orc):
+    """Codes that are E4M3 values on a coarse grid survive every alignment shift exactly, so the block-scaled
+    product must equal the plain W^H x of the dequantised operands (brute force, in the test)."""
+    n_sym, n_rx, n_sc, n_beams = 2, 20, 260, 3
+    codes = (RNG.integers(-7, 8, (n_sym, n_rx, n_sc)) + 1j * RNG.integers(-7, 8, (n_sym, n_rx, n_sc))) * 16.0
+    exps = RNG.integers(-3, 3, (n_sym, n_rx, 3)).astype(np.int32)
+    # W with entries k/8 (k < 8) in one block: block max 7/8 -> exponent -9, codes k * 64 exactly
+    W = (RNG.integers(-7, 8, (n_rx, n_beams)) + 1j * RNG.integers(-7, 8, (n_rx, n_beams))) / 8.0
+    W[0, :] = 7.0 / 8.0                                          # every beam's block max is exactly 7/8
+    beam = orc.beamform_fp8(codes, exps, W)
+    X = codes * 2.0 ** np.repeat(exps, 128, axis=2)[:, :, :n_sc]
+    want = np.einsum("rb,sra->sab", W.conj(), X)
+    assert np.allclose(beam, want, rtol=0, atol=1e-12)
+
+
+def test_fp8_product_rounds_a_shift_into_the_subnormal_range(orc):
+    """Hand case: two antennas, one subcarrier, W = [1, 1]^T. Antenna 1's block exponent is 8 below antenna
+    0's, so its code 1.125 becomes 1.125 * 2^-8 = 2.25 * 2^-9, which E4M3 rounds to 2 * 2^-9."""
+    codes = np.array([[[2.0], [1.125]]], complex)                # [sym][rx][sc]
+    exps = np.array([[[0], [-8]]], np.int32)
+    W = np.array([[1.0], [1.0]], complex)                        # block max 1 -> exponent -8, code 256
+    beam = orc.beamform_fp8(codes, exps, W)
+    assert beam[0, 0, 0] == pytest.approx(2.0 + 2.0 * 2.0 ** -9, abs=0)
+    exps_nan = np.array([[[0], [128]]], np.int32)
+    assert np.isnan(orc.beamform_fp8(codes, exps_nan, W)[0, 0, 0])
