@@ -733,6 +733,7 @@ void orc_beamform_fp8(const cplx *codes, const int *exps, const cplx *W, int n_s
             wv[r * n_beams + b] = orc_e4m3_round(ldexp(cr, e - eb)) + I * orc_e4m3_round(ldexp(ci, e - eb));
         }
     }
+    cplx *xq = malloc(sizeof(cplx) * (size_t)n_rx);
     for (int s = 0; s < n_sym; ++s)
         for (int j = 0; j < n_blk; ++j) {
             int E = -126;
@@ -740,18 +741,20 @@ void orc_beamform_fp8(const cplx *codes, const int *exps, const cplx *W, int n_s
                 int e = exps[((long long)s * n_rx + r) * n_blk + j];
                 if (e > E) E = e;
             }
-            for (int a = 128 * j; a < n_sc && a < 128 * j + 128; ++a)
+            for (int a = 128 * j; a < n_sc && a < 128 * j + 128; ++a) {
+                for (int r = 0; r < n_rx; ++r) {      /* the aligned samples of subcarrier a */
+                    int e = exps[((long long)s * n_rx + r) * n_blk + j];
+                    cplx c = codes[((long long)s * n_rx + r) * n_sc + a];
+                    xq[r] = orc_e4m3_round(ldexp(creal(c), e - E)) + I * orc_e4m3_round(ldexp(cimag(c), e - E));
+                }
                 for (int b = 0; b < n_beams; ++b) {
                     cplx acc = 0;
-                    for (int r = 0; r < n_rx; ++r) {
-                        int e = exps[((long long)s * n_rx + r) * n_blk + j];
-                        cplx c = codes[((long long)s * n_rx + r) * n_sc + a];
-                        cplx xq = orc_e4m3_round(ldexp(creal(c), e - E)) + I * orc_e4m3_round(ldexp(cimag(c), e - E));
-                        acc += conj(wv[r * n_beams + b]) * xq;
-                    }
+                    for (int r = 0; r < n_rx; ++r) acc += conj(wv[r * n_beams + b]) * xq[r];
                     beam[((long long)s * n_sc + a) * n_beams + b] = E >= 128 ? NAN : acc * ldexp(1.0, E) * wscale[b];
                 }
+            }
         }
+    free(xq);
     free(wv);
     free(wscale);
     free(ew);
