@@ -23,6 +23,8 @@
  *   - No C++ exception crosses this interface.
  *
  * Supported shapes: n_fft a power of two in [64, 4096]; 1 <= n_sc <= n_fft; 1 <= n_beams <= 64;
+ * mixed form: n_rx a multiple of 8 and n_beams a multiple of 8; FP8 form: n_rx a multiple of 16 up to 512
+ * and n_beams a multiple of 8;
  * 1 <= n_layers <= 32 and n_layers <= n_beams; 1 <= comb <= n_sc; n_sym = 14 with two distinct DMRS
  * symbols; 1 <= n_rx <= 1024; qam_bits 2 (QPSK) or 4 (16-QAM).
  */
@@ -48,9 +50,13 @@ typedef enum {
 /* Arithmetic form of the chain. */
 typedef enum {
     PUSCH_FORM_FP32 = 0,   /* plain: FFT and beamforming in FP32, intermediates stored as c64           */
-    PUSCH_FORM_MIXED = 1   /* FFT in FP32 registers with its output stored as FP16; beamforming on the
-                              tcgen05 tensor cores with FP16 operands and FP32 accumulation. Channel
-                              estimation and detection stay FP32 in both forms.                          */
+    PUSCH_FORM_MIXED = 1,  /* FFT in FP32 registers with its output stored as FP16; beamforming on the
+                              tcgen05 tensor cores with FP16 operands and FP32 accumulation.              */
+    PUSCH_FORM_FP8 = 2     /* FFT output stored as FP8 E4M3 with one power-of-two scale per 128
+                              subcarriers of each (symbol, antenna) row; W quantised to E4M3 with one
+                              power-of-two scale per (beam, 128 antennas); beamforming on the tcgen05
+                              tensor cores (kind::f8f6f4) with FP32 accumulation. Channel estimation and
+                              detection stay FP32 in every form.                                        */
 } pusch_form;
 
 /* Device status words written by the detection kernels (uint32_t status[4]):
@@ -92,9 +98,14 @@ pusch_status pusch_destroy(pusch_handle *h);
 /* Bytes of device workspace pusch_create allocates for (cfg, max_slots). */
 pusch_status pusch_workspace_size(const pusch_cell_cfg *cfg, int max_slots, size_t *bytes);
 
-/* Number of c16 elements between the re and im planes of one mixed-form FFT output row
- * (n_sc rounded up to a multiple of 8, so that every row starts on a 16-byte boundary). */
+/* Number of elements between the re and im planes of one FFT output row of the mixed form (c16 planes:
+ * n_sc rounded up to a multiple of 8) or of the FP8 form (byte planes: n_sc rounded up to a multiple of
+ * 16), so that every plane starts on a 16-byte boundary. */
 int pusch_sc_pitch(const pusch_cell_cfg *cfg);
+
+/* Bytes of the FFT output buffer (freq_out of pusch_ofdm_fft, freq_in of pusch_beamform) for n_slots slots
+ * of cfg's form; 0 for an invalid cfg or n_slots < 0. */
+size_t pusch_freq_bytes(const pusch_cell_cfg *cfg, int n_slots);
 
 /*
  * OFDM demodulation (Section II; Table I "OFDM dem."): for every slot, symbol s and antenna r,
@@ -103,14 +114,23 @@ int pusch_sc_pitch(const pusch_cell_cfg *cfg);
  * freq_out: FP32 form  -> [n_sym][n_rx][n_sc] c64.
  *           mixed form -> [n_sym][n_rx][2][pitch] binary16: plane 0 = re, plane 1 = im of bins 0..n_sc-1
  *                         (pitch = pusch_sc_pitch(cfg); elements n_sc..pitch-1 are written as 0).
+ *           FP8 form   -> E4M3 codes [n_slots][n_sym][n_rx][2][pitch] (planes as above, pads 0) and, at
+ *                         byte offset ceil256(n_slots * n_sym * n_rx * 2 * pitch), float block scales
+ *                         [n_slots][n_sym][n_blk][n_rx], n_blk = ceil(n_sc / 128): block j of a row holds
+ *                         subcarriers 128 j .. 128 j + 127 as code * scale, where scale = 2^e with e the
+ *                         smallest integer (>= -126) for which the block's largest |re| or |im| is at most
+ *                         448 * 2^e, and code = E4M3(value / scale) rounded to nearest even; a block
+ *                         holding a non-finite value gets scale NaN. This leading-n_slots layout is the
+ *                         one exception to the per-slot convention; the size is pusch_freq_bytes.
  */
 pusch_status pusch_ofdm_fft(pusch_handle *h, int n_slots, const void *time_in, void *freq_out, void *stream);
 
 /*
  * Beamforming (Section II, Table I "BF": a matrix-matrix product with known coefficients):
  *     Y[s][a][b] = sum_r conj(W[r][b]) X[s][r][a]      (y = W^H x per subcarrier and symbol)
- * freq_in : the layout pusch_ofdm_fft writes for cfg.form.
- * W       : [n_rx][n_beams] c64.
+ * freq_in : the layout pusch_ofdm_fft writes for cfg.form (and the same n_slots).
+ * W       : [n_rx][n_beams] c64. The mixed form rounds it to FP16; the FP8 form quantises it to E4M3 with
+ *           one power-of-two scale per (beam, block of 128 antennas), chosen like the sample scales.
  * beam_out: [n_sym][n_sc][n_beams] c64 (all symbols, DMRS included).
  */
 pusch_status pusch_beamform(pusch_handle *h, int n_slots, const void *freq_in, const void *W, void *beam_out,

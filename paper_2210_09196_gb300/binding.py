@@ -25,13 +25,15 @@ PUSCH_ERR_UNSUPPORTED = -5
 
 PUSCH_FORM_FP32 = 0
 PUSCH_FORM_MIXED = 1
+PUSCH_FORM_FP8 = 2
 
 PUSCH_STATUS_PIVOT = 0x1
 PUSCH_STATUS_NONFINITE = 0x2
 
 # every symbol include/pusch.h declares
 EXPORTS = (
-    "pusch_create", "pusch_destroy", "pusch_workspace_size", "pusch_sc_pitch", "pusch_ofdm_fft", "pusch_beamform",
+    "pusch_create", "pusch_destroy", "pusch_workspace_size", "pusch_sc_pitch", "pusch_freq_bytes", "pusch_ofdm_fft",
+    "pusch_beamform",
     "pusch_chest_ls", "pusch_mmse_detect", "pusch_slot", "pusch_slot_host", "pusch_last_error", "pusch_version",
     "pusch_slot_noalloc", "pusch_profile_start", "pusch_profile_read",
     "pusch_batch_create", "pusch_batch_destroy", "pusch_batch_sizes", "pusch_batch_run",
@@ -89,6 +91,7 @@ def lib():
             "pusch_destroy": (I, [P]),
             "pusch_workspace_size": (I, [ctypes.POINTER(pusch_cell_cfg), I, ctypes.POINTER(ctypes.c_size_t)]),
             "pusch_sc_pitch": (I, [ctypes.POINTER(pusch_cell_cfg)]),
+            "pusch_freq_bytes": (ctypes.c_size_t, [ctypes.POINTER(pusch_cell_cfg), I]),
             "pusch_ofdm_fft": (I, [P, I, P, P, P]),
             "pusch_beamform": (I, [P, I, P, P, P, P]),
             "pusch_chest_ls": (I, [P, I, P, P, P, P]),
@@ -153,6 +156,10 @@ def pusch_last_error() -> str:
 
 def pusch_sc_pitch(cfg: pusch_cell_cfg) -> int:
     return lib().pusch_sc_pitch(ctypes.byref(cfg))
+
+
+def pusch_freq_bytes(cfg: pusch_cell_cfg, n_slots: int) -> int:
+    return int(lib().pusch_freq_bytes(ctypes.byref(cfg), int(n_slots)))
 
 
 def pusch_workspace_size(cfg: pusch_cell_cfg, max_slots: int) -> int:

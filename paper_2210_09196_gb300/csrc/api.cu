@@ -50,7 +50,8 @@ pusch_status validate_cfg(const pusch_cell_cfg *c) {
             return fail(PUSCH_ERR_ARG, "port[%d]=%d out of [0, comb)", l, c->port[l]);
     if (c->qam_bits != 2 && c->qam_bits != 4) return fail(PUSCH_ERR_ARG, "qam_bits=%d: 2 or 4", c->qam_bits);
     if (c->in_fp16 != 0 && c->in_fp16 != 1) return fail(PUSCH_ERR_ARG, "in_fp16 must be 0 or 1");
-    if (c->form != PUSCH_FORM_FP32 && c->form != PUSCH_FORM_MIXED) return fail(PUSCH_ERR_ARG, "unknown form %d", c->form);
+    if (c->form != PUSCH_FORM_FP32 && c->form != PUSCH_FORM_MIXED && c->form != PUSCH_FORM_FP8)
+        return fail(PUSCH_ERR_ARG, "unknown form %d", c->form);
     if (c->n_sym < 3 || c->n_sym > 16) return fail(PUSCH_ERR_ARG, "n_sym=%d out of [3, 16]", c->n_sym);
     if (c->dmrs_sym[0] < 0 || c->dmrs_sym[0] >= c->n_sym || c->dmrs_sym[1] < 0 || c->dmrs_sym[1] >= c->n_sym ||
         c->dmrs_sym[0] == c->dmrs_sym[1])
@@ -61,15 +62,19 @@ pusch_status validate_cfg(const pusch_cell_cfg *c) {
         pusch::Geometry g = pusch::make_geometry(*c);
         if (!pusch::bf_tc_supported(g))
             return fail(PUSCH_ERR_UNSUPPORTED,
-                        "mixed form needs n_beams a multiple of 8 and n_rx in {8,16,...,128} (multiple of 8)");
+                        "mixed form needs n_beams a multiple of 8 and n_rx a multiple of 8 whose W operand fits "
+                        "in shared memory");
+    }
+    if (c->form == PUSCH_FORM_FP8) {
+        pusch::Geometry g = pusch::make_geometry(*c);
+        if (!pusch::bf_fp8_supported(g))
+            return fail(PUSCH_ERR_UNSUPPORTED, "FP8 form needs n_beams a multiple of 8 and n_rx a multiple of 16 "
+                                               "up to 512");
     }
     return PUSCH_OK;
 }
 
-size_t freq_bytes(const pusch::Geometry &g, int n_slots) {
-    const size_t rows = (size_t)n_slots * g.n_sym * g.n_rx;
-    return g.form == PUSCH_FORM_MIXED ? rows * 2 * g.sc_pitch * sizeof(__half) : rows * g.n_sc * sizeof(float2);
-}
+size_t freq_bytes(const pusch::Geometry &g, int n_slots) { return pusch::freq_bytes_of(g, n_slots); }
 size_t beam_bytes(const pusch::Geometry &g, int n_slots) {
     return (size_t)n_slots * g.n_sym * g.n_sc * g.n_beams * sizeof(float2);
 }
@@ -137,7 +142,7 @@ Geometry make_geometry(const pusch_cell_cfg &c) {
     g.dmrs1 = c.dmrs_sym[1];
     g.noise_var = c.noise_var;
     g.loading = c.loading;
-    g.sc_pitch = (c.n_sc + 7) & ~7;
+    g.sc_pitch = c.form == PUSCH_FORM_FP8 ? (c.n_sc + 15) & ~15 : (c.n_sc + 7) & ~7;
     for (int l = 0; l < 32; ++l) g.port[l] = l < c.n_layers ? c.port[l] : 0;
     int nd = 0;
     for (int s = 0; s < c.n_sym; ++s)
@@ -154,7 +159,15 @@ const char *pusch_last_error(void) { return g_err; }
 
 const char *pusch_version(void) { return "pusch-gb300 0.1 (sm_103a)"; }
 
-int pusch_sc_pitch(const pusch_cell_cfg *cfg) { return cfg ? (cfg->n_sc + 7) & ~7 : 0; }
+int pusch_sc_pitch(const pusch_cell_cfg *cfg) {
+    if (!cfg) return 0;
+    return cfg->form == PUSCH_FORM_FP8 ? (cfg->n_sc + 15) & ~15 : (cfg->n_sc + 7) & ~7;
+}
+
+size_t pusch_freq_bytes(const pusch_cell_cfg *cfg, int n_slots) {
+    if (validate_cfg(cfg) != PUSCH_OK || n_slots < 0) return 0;
+    return pusch::freq_bytes_of(pusch::make_geometry(*cfg), n_slots);
+}
 
 pusch_status pusch_workspace_size(const pusch_cell_cfg *cfg, int max_slots, size_t *bytes) {
     pusch_status st = validate_cfg(cfg);
@@ -238,14 +251,8 @@ pusch_status pusch_beamform(pusch_handle *h, int n_slots, const void *freq_in, c
     if (n_slots == 0) return ok();
     if (!freq_in || !W || !beam_out) return fail(PUSCH_ERR_ARG, "pusch_beamform: NULL buffer");
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e;
-    if (h->geo.form == PUSCH_FORM_MIXED) {
-        e = pusch::launch_beamform_tc(h->geo, n_slots, (const __half *)freq_in, (const float2 *)W, (float2 *)beam_out,
-                                      h->kernel_err, s);
-    } else {
-        e = pusch::launch_beamform_fp32(h->geo, n_slots, (const float2 *)freq_in, (const float2 *)W,
-                                        (float2 *)beam_out, s);
-    }
+    cudaError_t e = pusch::launch_beamform(h->geo, n_slots, freq_in, (const float2 *)W, (float2 *)beam_out,
+                                           h->kernel_err, s);
     if (e != cudaSuccess) return cuda_fail(e, "beamforming launch");
     return ok();
 }

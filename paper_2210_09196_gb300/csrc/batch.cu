@@ -321,12 +321,7 @@ pusch_status enqueue(pusch_batch *b, const void *time_in, const void *W, const v
     for (size_t c = 0; c < b->cells.size(); ++c) {
         const Geometry &g = b->geo[c];
         const float2 *w = static_cast<const float2 *>(W) + b->w_off[c];
-        if (g.form == PUSCH_FORM_MIXED)
-            e = pusch::launch_beamform_tc(g, 1, reinterpret_cast<const __half *>(b->freq + b->f_off[c]), w,
-                                          b->beam + b->beam_off[c], b->kernel_err, s);
-        else
-            e = pusch::launch_beamform_fp32(g, 1, reinterpret_cast<const float2 *>(b->freq + b->f_off[c]), w,
-                                            b->beam + b->beam_off[c], s);
+        e = pusch::launch_beamform(g, 1, b->freq + b->f_off[c], w, b->beam + b->beam_off[c], b->kernel_err, s);
         if (e != cudaSuccess) return bcuda(e, "batch beamforming launch");
     }
     if (b->n_jobs > 0) {
@@ -427,8 +422,7 @@ pusch_status pusch_batch_create(pusch_batch **out, const pusch_cell_cfg *cells, 
         t += (long long)g.n_sym * g.n_rx * g.n_fft;
         w += (long long)g.n_rx * g.n_beams;
         bm += (long long)g.n_sym * g.n_sc * g.n_beams;
-        f += up256(g.form == PUSCH_FORM_MIXED ? (size_t)g.n_sym * g.n_rx * 2 * g.sc_pitch * sizeof(__half)
-                                              : (size_t)g.n_sym * g.n_rx * g.n_sc * sizeof(float2));
+        f += up256(pusch::freq_bytes_of(g, 1));
     }
     b->sizes[0] = (size_t)t;
     b->sizes[1] = (size_t)w;

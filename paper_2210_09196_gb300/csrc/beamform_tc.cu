@@ -1,30 +1,51 @@
-// Beamforming, mixed form, on the 5th-generation tensor cores (tcgen05 + TMEM, operands staged by TMA).
+// Beamforming on the 5th-generation tensor cores (tcgen05 + TMEM, operands staged by TMA): the mixed form
+// (FP16 operands) and the FP8 form (E4M3 operands with power-of-two block scales), FP32 accumulation.
 //
 // The per-symbol product Y = W^H X of Section II (Table I "BF") is computed as a real GEMM with the
 // complex values embedded:  D[a][2b + c] = sum_k A[a][k] B[2b + c][k],  k = 2r + ri, where
-//   A[a][2r + 0] = Re X[r][a],  A[a][2r + 1] = Im X[r][a]                        (the FFT output, FP16)
+//   A[a][2r + 0] = Re X[r][a],  A[a][2r + 1] = Im X[r][a]                        (the FFT output)
 //   B[2b][2r] = Re W[r][b],  B[2b][2r+1] = Im W[r][b],  B[2b+1][2r] = -Im W[r][b],  B[2b+1][2r+1] = Re W[r][b]
-// so that D[a][2b] = Re y_b and D[a][2b + 1] = Im y_b, i.e. each accumulator row is the c64 output row of
+// so that D[a][2b] = Re y_b and D[a][2b + 1] = Im y_b: each accumulator row is the c64 output row of
 // subcarrier a. The MMA's M dimension is the subcarrier axis (tiles of 128), N = 2 N_B, K = 2 N_R.
 //
-// A is the mixed-form FFT output [rows][2 N_R][pitch] binary16 (subcarriers contiguous): an MN-major
-// operand. TMA copies two 64-subcarrier x K boxes per tile with 128-byte swizzling into shared memory;
-// B is built once per CTA from W (complex64) in the no-swizzle K-major core-matrix layout. One thread
-// issues K/16 tcgen05.mma (kind::f16, FP32 accumulate) into TMEM; the four warps read their 32 TMEM lanes
-// back with tcgen05.ld and store the rows. CTAs are persistent over tiles with a 2-stage TMA ring.
-// Every wait is bounded (%globaltimer); on expiry the CTA records a timeout, drains and exits.
+// A is the FFT output [rows][2 N_R][pitch] (subcarriers contiguous): an MN-major operand, copied by TMA
+// in K chunks with 128-byte swizzling into a ring of shared-memory stages. B is built once per CTA from W
+// in the no-swizzle K-major core-matrix layout and stays resident.
+//
+// Warp roles (persistent CTAs, one per SM):
+//   warp 0      TMA producer: streams the (tile, K chunk) sequence into the stage ring;
+//   warp 1      owns the TMEM allocation; one lane issues the MMAs of each chunk into one of two TMEM
+//               accumulators and commits the chunk's stage back to the producer;
+//   warps 2-5   epilogue: tcgen05.ld of the finished accumulator (one 32-lane quarter per warp), scaling
+//               (FP8 form), stores of the c64 rows; the other accumulator is being filled meanwhile;
+//   warps 6-9   FP8 form only: align each landed chunk to the tile's common scale (below).
+//
+// FP8 form. The FFT stores each (symbol, antenna) row as E4M3 codes with one power-of-two scale 2^e per
+// 128 subcarriers; W is quantised in the kernel with one power-of-two scale per (beam, 128 antennas).
+// Because the M tile is the 128-subcarrier block, a tile's samples carry one exponent e_r per antenna.
+// The rescale warps shift every antenna's codes to the tile's largest exponent E (code * 2^(e_r - E),
+// re-rounded to E4M3, which is exact unless the shifted value leaves the normal range) and W's blocks are
+// likewise shifted to each beam's largest exponent E_b when B is built, so one accumulator holds
+// D * 2^-(E + E_b) and the epilogue multiplies by 2^E * 2^E_b. A non-finite scale (a non-finite sample in
+// the block) makes the tile's output NaN, so detection reports it.
+//
+// Every wait is bounded (%globaltimer, 2 s); on expiry the CTA records a timeout in err_word bit 0, all
+// roles leave their loops, in-flight copies and MMAs are drained (bounded) and TMEM is freed.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_fp8.h>
+#include <float.h>
 
 #include "internal.cuh"
 
 namespace pusch {
 namespace {
 
-constexpr int kTcThreads = 128;
 constexpr int kTileM = 128;
-constexpr int kStages = 2;
+constexpr int kMaxStages = 8;
+constexpr int kSmemLimit = 227 * 1024;
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s
+constexpr int kMaxRxFp8 = 512;   // W block exponents are kept for up to 4 blocks of 128 antennas
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -42,6 +63,10 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -54,11 +79,27 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait on an mbarrier phase; false when the deadline passed first.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t deadline) {
-    while (!mbar_try_wait(bar, parity))
-        if (globaltimer() > deadline) return false;
+// Bounded wait on an mbarrier phase. Gives up when the deadline passes (sets *abort and the error bit) or
+// when another role has already aborted; returns false then.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort, uint32_t *err) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t deadline = globaltimer() + kWaitNs;
+    while (!mbar_try_wait(bar, parity)) {
+        if (*abort) return false;
+        if (globaltimer() > deadline) {
+            *abort = 1;
+            if (err) atomicOr(err, 1u);
+            return false;
+        }
+    }
     return true;
+}
+
+// Wait used while draining after an abort: bounded, ignores the abort flag.
+__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity) {
+    const uint64_t deadline = globaltimer() + kWaitNs;
+    while (!mbar_try_wait(bar, parity))
+        if (globaltimer() > deadline) return;
 }
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
@@ -68,6 +109,18 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
         : "memory");
 }
+
+// Tensor store shared -> global (bulk async-group of the issuing thread); rows past the tensor's extent
+// are clipped by the copy engine.
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, uint32_t src, int x, int y, int z) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(src), "r"(x), "r"(y), "r"(z)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // tcgen05 shared-memory matrix descriptor: start >> 4 [0,14), LBO >> 4 [16,30), SBO >> 4 [32,46),
 // version 1 at [46,48), base offset 0, layout type at [61,64) (0 = no swizzle, 2 = 128-byte swizzle).
@@ -80,18 +133,27 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
     return d;
 }
 
-// Instruction descriptor, kind::f16: D = F32, A = B = F16, A MN-major, B K-major, N >> 3 at [17,23),
-// M >> 4 at [24,29).
-__host__ __device__ constexpr uint32_t instr_desc_f16(int M, int N) {
+// Instruction descriptor: D = F32 (bit 4), A and B format code 0 (F16 for kind::f16, E4M3 for
+// kind::f8f6f4), A MN-major (bit 15), B K-major, N >> 3 at [17,23), M >> 4 at [24,29).
+__host__ __device__ constexpr uint32_t instr_desc(int M, int N) {
     return (1u << 4) | (1u << 15) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+template <bool FP8>
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    if constexpr (FP8) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc));
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc));
+    }
 }
 
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
@@ -111,148 +173,457 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+// Exponent of a power-of-two block scale as stored by the FFT (an exact power of two, or NaN for a
+// non-finite block): e in [-126, 127], or 128 for NaN/inf.
+__device__ __forceinline__ int scale_exp(float s) { return (int)((__float_as_uint(s) >> 23) & 0xFFu) - 127; }
+
+// 2^e as a float for e in [-126, 127]; NaN for e = 128.
+__device__ __forceinline__ float exp2_int(int e) {
+    return e >= 128 ? __uint_as_float(0x7FC00000u) : __uint_as_float((uint32_t)(e + 127) << 23);
+}
+
+// E4M3 helpers (cuda_fp8.h conversions: round to nearest even, saturating to +-448).
+__device__ __forceinline__ float2 e4m3x2_to_float2(uint16_t v) {
+    const __half2_raw h = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)v, __NV_E4M3);
+    return __half22float2(*reinterpret_cast<const __half2 *>(&h));
+}
+__device__ __forceinline__ uint16_t float2_to_e4m3x2(float2 v) {
+    return (uint16_t)__nv_cvt_float2_to_fp8x2(v, __NV_SATFINITE, __NV_E4M3);
+}
+
+// Smallest e with amax <= 448 * 2^e (the power-of-two E4M3 block scale), clamped below at -126;
+// 128 for a non-finite amax. Read from the float's bits: amax = 1.m * 2^(E - 127).
+__device__ __forceinline__ int block_exp(float amax) {
+    if (!(amax <= FLT_MAX)) return 128;
+    const uint32_t u = __float_as_uint(amax);
+    const int eb = (int)(u >> 23);
+    if (eb == 0) return -126;                      // zero or subnormal
+    const int e = eb - 127 - 8 + ((u & 0x7FFFFFu) > 0x600000u ? 1 : 0);   // 448 = 1.75 * 2^8
+    return e < -126 ? -126 : e;
+}
+
 struct TcArgs {
-    int n_rx, n_beams, n_sc, n_mtiles, tmem_cols;
+    int n_rx, n_beams, n_sc, n_mtiles, n_blk;
+    int K, N, chunk_rows, n_chunks, n_stages, tmem_cols;
+    uint32_t stage_bytes, b_bytes;
+    int stage_out;             // 1: the epilogue writes through shared memory and TMA tensor stores
     long long total_tiles;
 };
 
-__global__ void __launch_bounds__(kTcThreads, 2)
-beamform_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g, const float2 *__restrict__ W,
-                   float2 *__restrict__ beam, uint32_t *__restrict__ err) {
-    extern __shared__ uint8_t smem_raw[];
-    const int K = 2 * g.n_rx;
-    const int N = 2 * g.n_beams;
-    const uint32_t a_bytes = (uint32_t)kTileM * K * 2;
-    const uint32_t b_sbo = (uint32_t)K * 16;  // bytes between 8-row groups of B
+struct TcShared {
+    uint64_t full[kMaxStages], ready[kMaxStages], empty[kMaxStages];
+    uint64_t tfull[2], tempty[2], drain;
+    uint32_t tmem_base;
+    int abort;
+    int ew[64 * 4];            // FP8: W block exponents [beam][128-antenna block]
+    int wexp[64];              // FP8: E_b, the largest block exponent of beam b
+    float wsc[64];             // FP8: 2^E_b
+    uint8_t shift[4][kMaxRxFp8];  // FP8: per rescale warp, the shift E - e_r of each antenna of its tile
+};
 
+template <bool FP8>
+__global__ void __launch_bounds__(FP8 ? 320 : 192, 1)
+beamform_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap omap, TcArgs g,
+                   const float2 *__restrict__ W, const float *__restrict__ scales, float2 *__restrict__ beam,
+                   uint32_t *__restrict__ err) {
+    constexpr int kThreads = FP8 ? 320 : 192;
+    constexpr int kKStep = FP8 ? 32 : 16;       // K per MMA instruction (32 bytes of K)
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ TcShared sh;
+
+    const int K = g.K, N = g.N;
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t *gbase = smem_raw + (base - raw);
     const uint32_t sA = base;
-    const uint32_t sB = base + kStages * a_bytes;
-    uint8_t *gB = gbase + kStages * a_bytes;
-    const uint32_t sBar = sB + (uint32_t)N * K * 2;
-    uint64_t *gBar = reinterpret_cast<uint64_t *>(gB + (size_t)N * K * 2);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(gBar + kStages + 1);
-    __shared__ int s_abort;
+    const uint32_t sB = base + (uint32_t)g.n_stages * g.stage_bytes;
+    uint8_t *gB = gbase + (size_t)g.n_stages * g.stage_bytes;
+    // output staging (stage_out): per epilogue warp, 32 rows x N floats as N/16 boxes of 32 x 16 floats with
+    // 64-byte swizzling (16-byte chunk c of row r at r * 64 + ((c ^ ((r >> 1) & 3)) << 4)), 2 KB each
+    const uint32_t out_off = (uint32_t)g.n_stages * g.stage_bytes + ((g.b_bytes + 1023u) & ~1023u);
+    const uint32_t b_sbo = FP8 ? (uint32_t)K * 8 : (uint32_t)K * 16;  // bytes between 8-row groups of B
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    volatile int *abort = &sh.abort;
 
-    // ---- B operand from W: element (n, k) at (n/8)*SBO + (k/8)*128 + (n%8)*16 + (k%8)*2
-    for (int idx = tid; idx < g.n_rx * g.n_beams; idx += kTcThreads) {
-        const int r = idx / g.n_beams, b = idx - r * g.n_beams;
-        const float2 w = __ldg(&W[idx]);
-        const __half wr = __float2half_rn(w.x), wi = __float2half_rn(w.y), nwi = __float2half_rn(-w.y);
-        auto put = [&](int n, int k, __half v) {
-            *reinterpret_cast<__half *>(gB + (n >> 3) * b_sbo + (k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2) = v;
-        };
-        put(2 * b, 2 * r, wr);
-        put(2 * b, 2 * r + 1, wi);
-        put(2 * b + 1, 2 * r, nwi);
-        put(2 * b + 1, 2 * r + 1, wr);
+    // ---------------------------------------------------------------- B operand (resident) from W
+    // W is read in coalesced batches of kBatch loads per thread in flight (the build is latency-bound
+    // otherwise: every CTA does it before its first MMA).
+    constexpr int kBatch = 8;
+    const int total = g.n_rx * g.n_beams;
+    if constexpr (!FP8) {
+        // element (n, k) at (n/8)*SBO + (k/8)*128 + (n%8)*16 + (k%8)*2
+        for (int base0 = 0; base0 < total; base0 += kThreads * kBatch) {
+            float2 w[kBatch];
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                const int idx = base0 + u * kThreads + tid;
+                w[u] = idx < total ? __ldg(&W[idx]) : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                const int idx = base0 + u * kThreads + tid;
+                if (idx >= total) continue;
+                const int r = idx / g.n_beams, b = idx - r * g.n_beams;
+                const __half wr = __float2half_rn(w[u].x), wi = __float2half_rn(w[u].y),
+                             nwi = __float2half_rn(-w[u].y);
+                auto put = [&](int n, int k, __half v) {
+                    *reinterpret_cast<__half *>(gB + (n >> 3) * b_sbo + (k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2) = v;
+                };
+                put(2 * b, 2 * r, wr);
+                put(2 * b, 2 * r + 1, wi);
+                put(2 * b + 1, 2 * r, nwi);
+                put(2 * b + 1, 2 * r + 1, wr);
+            }
+        }
+    } else {
+        // pass 1: largest |Re|, |Im| per (beam, 128-antenna block) by shared atomics on the bit patterns
+        // (non-negative floats order like their bits); a non-finite component records +inf
+        const int n_kb = (g.n_rx + 127) / 128;
+        uint32_t *wmax = reinterpret_cast<uint32_t *>(sh.ew);
+        for (int i2 = tid; i2 < 64 * 4; i2 += kThreads) wmax[i2] = 0u;
+        __syncthreads();
+        for (int base0 = 0; base0 < total; base0 += kThreads * kBatch) {
+            float2 w[kBatch];
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                const int idx = base0 + u * kThreads + tid;
+                w[u] = idx < total ? __ldg(&W[idx]) : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                const int idx = base0 + u * kThreads + tid;
+                if (idx >= total) continue;
+                const int r = idx / g.n_beams, b = idx - r * g.n_beams;
+                const float ax = fabsf(w[u].x), ay = fabsf(w[u].y);
+                const bool bad = !(ax <= FLT_MAX) || !(ay <= FLT_MAX);
+                atomicMax(&wmax[b * 4 + (r >> 7)], bad ? 0x7F800000u : __float_as_uint(fmaxf(ax, ay)));
+            }
+        }
+        __syncthreads();
+        for (int i2 = tid; i2 < g.n_beams * 4; i2 += kThreads)
+            sh.ew[i2] = (i2 & 3) < n_kb ? block_exp(__uint_as_float(wmax[i2])) : -126;
+        __syncthreads();
+        for (int b = tid; b < g.n_beams; b += kThreads) {
+            int e = -126;
+            for (int kb = 0; kb < n_kb; ++kb) e = max(e, sh.ew[b * 4 + kb]);
+            sh.wexp[b] = e;
+            sh.wsc[b] = exp2_int(e);
+        }
+        __syncthreads();
+        // pass 2: element (n, k) at (n/8)*SBO + (k/16)*128 + (n%8)*16 + (k%16)
+        for (int base0 = 0; base0 < total; base0 += kThreads * kBatch) {
+            float2 w[kBatch];
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                const int idx = base0 + u * kThreads + tid;
+                w[u] = idx < total ? __ldg(&W[idx]) : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                const int idx = base0 + u * kThreads + tid;
+                if (idx >= total) continue;
+                const int r = idx / g.n_beams, b = idx - r * g.n_beams;
+                const int eb = sh.wexp[b], e_blk = sh.ew[b * 4 + (r >> 7)];
+                const int d = eb - e_blk;                     // shift of this block to the beam exponent
+                uint8_t qr, qi;
+                if (eb >= 128) {
+                    qr = qi = 0;                              // the beam's scale is NaN; codes unused
+                } else {
+                    const float inv = exp2_int(-e_blk);      // 2^-e_blk, e_blk in [-126, 120]
+                    const float2 c = e4m3x2_to_float2(float2_to_e4m3x2(make_float2(w[u].x * inv, w[u].y * inv)));
+                    const float sh2 = exp2_int(d > 40 ? -40 : -d);
+                    const uint16_t q = float2_to_e4m3x2(make_float2(c.x * sh2, c.y * sh2));
+                    qr = (uint8_t)(q & 0xFFu);
+                    qi = (uint8_t)(q >> 8);
+                }
+                auto put = [&](int n, int k, uint8_t v) {
+                    gB[(n >> 3) * b_sbo + (k >> 4) * 128 + (n & 7) * 16 + (k & 15)] = v;
+                };
+                put(2 * b, 2 * r, qr);
+                put(2 * b, 2 * r + 1, qi);
+                put(2 * b + 1, 2 * r, (uint8_t)(qi ^ 0x80u));   // -Im W: sign flip of the code
+                put(2 * b + 1, 2 * r + 1, qr);
+            }
+        }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 
     if (tid == 0) {
-        for (int s = 0; s <= kStages; ++s) mbar_init(sBar + 8 * s, 1);
+        for (int s = 0; s < g.n_stages; ++s) {
+            mbar_init(smem_u32(&sh.full[s]), 1);
+            mbar_init(smem_u32(&sh.ready[s]), 4);
+            mbar_init(smem_u32(&sh.empty[s]), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&sh.tfull[b]), 1);
+            mbar_init(smem_u32(&sh.tempty[b]), 4);
+        }
+        mbar_init(smem_u32(&sh.drain), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        s_abort = 0;
+        sh.abort = 0;
     }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh.tmem_base)),
                      "r"(g.tmem_cols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
-    const uint32_t tmem = *tmem_slot;
-    const uint32_t mma_bar = sBar + 8 * kStages;
-    const uint32_t idesc = instr_desc_f16(kTileM, N);
+    const uint32_t tmem = sh.tmem_base;
 
     const long long n_my =
         g.total_tiles > blockIdx.x ? (g.total_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
-    auto issue = [&](int s, long long i) {
-        const long long t = blockIdx.x + i * gridDim.x;
-        const long long row = t / g.n_mtiles;
-        const int mt = (int)(t - row * g.n_mtiles);
-        const uint32_t dst = sA + s * a_bytes;
-        mbar_expect_tx(sBar + 8 * s, a_bytes);
-        tma_load_2d(dst, &tmap, mt * kTileM, (int)(row * K), sBar + 8 * s);
-        tma_load_2d(dst + (uint32_t)K * 128, &tmap, mt * kTileM + 64, (int)(row * K), sBar + 8 * s);
-    };
-    if (tid == 0)
-        for (int s = 0; s < kStages && s < n_my; ++s) issue(s, s);
+    const int NS = g.n_stages;
 
-    long long issued = n_my < kStages ? n_my : kStages;
-    long long i = 0;
-    for (; i < n_my; ++i) {
-        const int s = (int)(i % kStages);
-        const uint32_t ph = (uint32_t)((i / kStages) & 1);
-        const uint64_t deadline = globaltimer() + kWaitNs;
-        int bad = 0;
-        if (tid == 0) {
-            if (mbar_wait(sBar + 8 * s, ph, deadline)) {
-                fence_after_sync();
-                const uint32_t a0 = sA + s * a_bytes;
-                for (int ks = 0; ks < K / 16; ++ks) {
-                    const uint64_t ad = smem_desc(a0 + ks * 2048, (uint32_t)K * 128, 1024, 2);
-                    const uint64_t bd = smem_desc(sB + ks * 256, 128, b_sbo, 0);
-                    mma_f16(tmem, ad, bd, idesc, ks > 0 ? 1u : 0u);
+    if (warp == 0) {
+        // ------------------------------------------------------------------ TMA producer
+        if (lane == 0) {
+            long long gch = 0;
+            bool ok = true;
+            for (long long i = 0; i < n_my && ok; ++i) {
+                const long long t = blockIdx.x + i * gridDim.x;
+                const long long row = t / g.n_mtiles;
+                const int mt = (int)(t - row * g.n_mtiles);
+                for (int c = 0; c < g.n_chunks; ++c, ++gch) {
+                    const int s = (int)(gch % NS);
+                    const uint32_t ph = (uint32_t)((gch / NS) & 1);
+                    if (!mbar_wait(smem_u32(&sh.empty[s]), ph ^ 1u, abort, err)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t bar = smem_u32(&sh.full[s]);
+                    const uint32_t dst = sA + (uint32_t)s * g.stage_bytes;
+                    const int y = (int)(row * K) + c * g.chunk_rows;
+                    mbar_expect_tx(bar, g.stage_bytes);
+                    if constexpr (FP8) {
+                        tma_load_2d(dst, &tmap, mt * kTileM, y, bar);
+                    } else {
+                        tma_load_2d(dst, &tmap, mt * kTileM, y, bar);
+                        tma_load_2d(dst + (uint32_t)g.chunk_rows * 128, &tmap, mt * kTileM + 64, y, bar);
+                    }
                 }
-                mma_commit(mma_bar);
-            } else {
-                bad = 1;
+            }
+            if (*abort) {
+                // drain: the latest copy issued into each stage (bounded)
+                for (long long j = gch - 1; j >= 0 && j >= gch - NS; --j)
+                    mbar_drain(smem_u32(&sh.full[(int)(j % NS)]), (uint32_t)((j / NS) & 1));
             }
         }
-        if (!bad && !mbar_wait(mma_bar, (uint32_t)(i & 1), deadline)) bad = 1;
-        if (__syncthreads_or(bad)) {
-            if (tid == 0) {
-                s_abort = 1;
-                atomicOr(err, 1u);
+    } else if (warp == 1) {
+        // ------------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = instr_desc(kTileM, N);
+            const uint32_t a_lbo = (uint32_t)g.chunk_rows * 128;   // FP16: between the two 64-subcarrier halves
+            long long gch = 0;
+            bool ok = true;
+            for (long long i = 0; i < n_my && ok; ++i) {
+                const int buf = (int)(i & 1);
+                const uint32_t use = (uint32_t)((i >> 1) & 1);
+                if (!mbar_wait(smem_u32(&sh.tempty[buf]), use ^ 1u, abort, err)) break;
+                fence_after_sync();
+                const uint32_t d = tmem + (uint32_t)(buf * N);
+                for (int c = 0; c < g.n_chunks; ++c, ++gch) {
+                    const int s = (int)(gch % NS);
+                    const uint32_t ph = (uint32_t)((gch / NS) & 1);
+                    if (!mbar_wait(smem_u32(&sh.full[s]), ph, abort, err)) {
+                        ok = false;
+                        break;
+                    }
+                    if constexpr (FP8) {
+                        if (!mbar_wait(smem_u32(&sh.ready[s]), ph, abort, err)) {
+                            ok = false;
+                            break;
+                        }
+                    }
+                    fence_after_sync();
+                    const int rows_here = min(g.chunk_rows, K - c * g.chunk_rows);
+                    const uint32_t a0 = sA + (uint32_t)s * g.stage_bytes;
+                    const int kb0 = c * (g.chunk_rows / kKStep);
+                    for (int ks = 0; ks < rows_here / kKStep; ++ks) {
+                        const uint64_t ad = smem_desc(a0 + (uint32_t)ks * (kKStep * 128), a_lbo, 1024, 2);
+                        const uint64_t bd = smem_desc(sB + (uint32_t)(kb0 + ks) * 256, 128, b_sbo, 0);
+                        mma<FP8>(d, ad, bd, idesc, (c > 0 || ks > 0) ? 1u : 0u);
+                    }
+                    mma_commit(smem_u32(&sh.empty[s]));
+                }
+                if (!ok) break;
+                mma_commit(smem_u32(&sh.tfull[buf]));
             }
-            break;
+            // every MMA issued by this thread has completed once the drain barrier flips (bounded)
+            mma_commit(smem_u32(&sh.drain));
+            mbar_drain(smem_u32(&sh.drain), 0);
         }
-        fence_after_sync();
-        if (tid == 0 && i + kStages < n_my) {
-            issue(s, i + kStages);
-            ++issued;
-        }
-        const long long t = blockIdx.x + i * gridDim.x;
-        const long long row = t / g.n_mtiles;
-        const int mt = (int)(t - row * g.n_mtiles);
-        const int a = mt * kTileM + warp * 32 + lane;
-        float *dst = reinterpret_cast<float *>(beam + (row * g.n_sc + a) * (long long)g.n_beams);
-        for (int c0 = 0; c0 < N; c0 += 32) {
-            uint32_t r[32];
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
-            const int ncol = N - c0 < 32 ? N - c0 : 32;  // N is a multiple of 16: 16 or 32 columns here
-            if (a < g.n_sc) {
+    } else if (warp < 6) {
+        // ------------------------------------------------------------------ epilogue
+        const int q = warp & 3;                         // TMEM lane quarter this warp may access
+        for (long long i = 0; i < n_my; ++i) {
+            const int buf = (int)(i & 1);
+            const long long t = blockIdx.x + i * gridDim.x;
+            const long long row = t / g.n_mtiles;
+            const int mt = (int)(t - row * g.n_mtiles);
+            float p2e = 1.f;
+            if constexpr (FP8) {
+                const float *sc = scales + ((size_t)row * g.n_blk + mt) * g.n_rx;
+                int e = -126;
+                for (int r = lane; r < g.n_rx; r += 32) e = max(e, scale_exp(__ldg(&sc[r])));
 #pragma unroll
-                for (int j = 0; j < 32; j += 4)
-                    if (j < ncol)
-                        *reinterpret_cast<float4 *>(dst + c0 + j) =
-                            make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]), __uint_as_float(r[j + 2]),
-                                        __uint_as_float(r[j + 3]));
+                for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xFFFFFFFFu, e, o));
+                p2e = exp2_int(e);
+            }
+            const bool okw = mbar_wait(smem_u32(&sh.tfull[buf]), (uint32_t)((i >> 1) & 1), abort, err);
+            if (!__all_sync(0xFFFFFFFFu, okw)) break;     // warp-uniform: tcgen05.ld is warp-collective
+            fence_after_sync();
+            const int a = mt * kTileM + q * 32 + lane;
+            float *dst = reinterpret_cast<float *>(beam + (row * g.n_sc + a) * (long long)g.n_beams);
+            const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * N);
+            const uint32_t stg = base + out_off + (uint32_t)(warp - 2) * (uint32_t)(128 * N);
+            uint8_t *gstg = gbase + out_off + (size_t)(warp - 2) * (128 * N);
+            if (g.stage_out) {
+                if (lane == 0) bulk_wait_read0();          // the previous tile's stores have read the staging
+                __syncwarp();
+            }
+            for (int c0 = 0; c0 < N; c0 += 32) {
+                uint32_t r[32];
+                const int ncol = N - c0 < 32 ? N - c0 : 32;   // N is a multiple of 16
+                if (ncol == 32) tmem_ld32(tbase + (uint32_t)c0, r);
+                else tmem_ld16(tbase + (uint32_t)c0, r);
+#pragma unroll
+                for (int j = 0; j < 32; j += 4) {
+                    if (j < ncol) {
+                        float4 v = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                                               __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
+                        if constexpr (FP8) {
+                            const float s0 = p2e * sh.wsc[(c0 + j) >> 1], s1 = p2e * sh.wsc[(c0 + j + 2) >> 1];
+                            v.x *= s0;
+                            v.y *= s0;
+                            v.z *= s1;
+                            v.w *= s1;
+                        }
+                        if (g.stage_out) {
+                            const int col = c0 + j, box = col >> 4, ch = (col >> 2) & 3;
+                            *reinterpret_cast<float4 *>(gstg + box * 2048 + lane * 64 + ((ch ^ ((lane >> 1) & 3)) << 4)) = v;
+                        } else if (a < g.n_sc) {
+                            *reinterpret_cast<float4 *>(dst + c0 + j) = v;
+                        }
+                    }
+                }
+            }
+            if (g.stage_out) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                const int y0 = mt * kTileM + q * 32;       // rows past n_sc are clipped; a wholly past box is skipped
+                if (lane == 0 && y0 < g.n_sc) {
+                    for (int box = 0; box < N / 16; ++box)
+                        tma_store_3d(&omap, stg + (uint32_t)box * 2048u, box * 16, y0, (int)row);
+                    bulk_commit();
+                }
+            }
+            fence_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&sh.tempty[buf]));
+        }
+        if (g.stage_out && lane == 0) bulk_wait0();        // stores complete before the CTA's shared memory goes
+    } else if constexpr (FP8) {
+        // ------------------------------------------------------------------ FP8: align chunks to the tile scale
+        // Each of the four warps derives the tile exponent E itself (no cross-warp barrier, so an abort in
+        // one warp cannot strand the others) and shifts the K rows u = 32 w + lane (mod 128) of each chunk.
+        const int w4 = warp - 6;
+        long long gch = 0;
+        bool ok = true;
+        for (long long i = 0; i < n_my && ok; ++i) {
+            const long long t = blockIdx.x + i * gridDim.x;
+            const long long row = t / g.n_mtiles;
+            const int mt = (int)(t - row * g.n_mtiles);
+            const float *sc = scales + ((size_t)row * g.n_blk + mt) * g.n_rx;
+            int E = -126;
+            for (int r = lane; r < g.n_rx; r += 32) E = max(E, scale_exp(__ldg(&sc[r])));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) E = max(E, __shfl_xor_sync(0xFFFFFFFFu, E, o));
+            __syncwarp();                                    // this warp's previous tile no longer reads shift[]
+            for (int r = lane; r < g.n_rx; r += 32) {
+                const int d = E - scale_exp(__ldg(&sc[r]));
+                sh.shift[w4][r] = (uint8_t)(d > 19 ? 19 : d);
+            }
+            __syncwarp();
+            for (int c = 0; c < g.n_chunks; ++c, ++gch) {
+                const int s = (int)(gch % NS);
+                const uint32_t ph = (uint32_t)((gch / NS) & 1);
+                const bool okw = mbar_wait(smem_u32(&sh.full[s]), ph, abort, err);
+                if (!__all_sync(0xFFFFFFFFu, okw)) {
+                    ok = false;
+                    break;
+                }
+                uint8_t *stage = gbase + (size_t)s * g.stage_bytes;
+                const int k0 = c * g.chunk_rows;
+                const int rows_here = min(g.chunk_rows, K - k0);
+                // A K row (one antenna's re or im plane over the tile's 128 subcarriers) is 128 contiguous
+                // bytes of the swizzled stage and takes one factor 2^-d, so the swizzle does not matter here.
+                // code * 2^-d is exact in binary16 whenever E4M3 can represent it (4 significant bits,
+                // >= 2^-13); smaller values round to E4M3 zero either way; d >= 19 leaves only zeros.
+                for (int u0 = w4 * 32 + lane; u0 < rows_here * 8; u0 += 128 * 4) {
+                    uint4 v[4];
+                    int dd[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int u = u0 + 128 * q;
+                        dd[q] = u < rows_here * 8 ? sh.shift[w4][(k0 + (u >> 3)) >> 1] : 0;
+                        if (dd[q] != 0) v[q] = *reinterpret_cast<const uint4 *>(stage + (size_t)(u >> 3) * 128 + (u & 7) * 16);
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        if (dd[q] == 0) continue;
+                        const int u = u0 + 128 * q;
+                        uint4 o = make_uint4(0u, 0u, 0u, 0u);
+                        if (dd[q] < 19) {
+                            // 2^-d in binary16: normal for d <= 14, subnormal 2^(10 - 24 + (24 - d)) beyond
+                            const unsigned short hb = dd[q] <= 14 ? (unsigned short)((15 - dd[q]) << 10)
+                                                                  : (unsigned short)(1u << (24 - dd[q]));
+                            __half2_raw fr;
+                            fr.x = hb;
+                            fr.y = hb;
+                            const __half2 f2 = *reinterpret_cast<const __half2 *>(&fr);
+                            uint32_t w[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w[j] & 0xFFFFu), __NV_E4M3);
+                                __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w[j] >> 16), __NV_E4M3);
+                                const __half2 l2 = __hmul2(*reinterpret_cast<const __half2 *>(&lo), f2);
+                                const __half2 h2 = __hmul2(*reinterpret_cast<const __half2 *>(&hi), f2);
+                                w[j] = (uint32_t)__nv_cvt_halfraw2_to_fp8x2(*reinterpret_cast<const __half2_raw *>(&l2),
+                                                                            __NV_SATFINITE, __NV_E4M3) |
+                                       ((uint32_t)__nv_cvt_halfraw2_to_fp8x2(*reinterpret_cast<const __half2_raw *>(&h2),
+                                                                             __NV_SATFINITE, __NV_E4M3) << 16);
+                            }
+                            o = make_uint4(w[0], w[1], w[2], w[3]);
+                        }
+                        *reinterpret_cast<uint4 *>(stage + (size_t)(u >> 3) * 128 + (u & 7) * 16) = o;
+                    }
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&sh.ready[s]));
             }
         }
-        fence_before_sync();
-        __syncthreads();
     }
 
-    if (s_abort && tid == 0) {
-        // drain the TMA loads still in flight for this CTA (bounded), so no copy lands after exit
-        const uint64_t d2 = globaltimer() + kWaitNs;
-        for (long long j = i; j < issued; ++j)
-            mbar_wait(sBar + 8 * (int)(j % kStages), (uint32_t)((j / kStages) & 1), d2);
-        mbar_wait(mma_bar, (uint32_t)(i & 1), d2);
-    }
     fence_before_sync();
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 1) {
         fence_after_sync();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(g.tmem_cols));
     }
@@ -271,56 +642,136 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-size_t tc_smem_bytes(const Geometry &g) {
-    const size_t K = 2 * (size_t)g.n_rx, N = 2 * (size_t)g.n_beams;
-    return 1024 + kStages * (size_t)kTileM * K * 2 + N * K * 2 + 8 * (kStages + 1) + 16;
+// Launch plan for a geometry: chunk size and stage count so that B, the ring and the static shared state
+// fit in 227 KB with at least 3 stages (2 for the largest B).
+struct Plan {
+    bool ok;
+    int chunk_rows, n_chunks, n_stages, tmem_cols, stage_out;
+    uint32_t stage_bytes, b_bytes;
+    size_t smem;
+};
+
+// Launch plan for a geometry: chunk size, stage count and whether the output is staged for TMA stores, so
+// that B, the output staging, the ring and the static shared state fit in 227 KB. Preference: staged
+// output with >= 3 stages, then direct stores with >= 3 stages, halving the chunk down to 64 rows (2 stages
+// are accepted at 64 rows).
+Plan make_plan(const Geometry &g, bool fp8) {
+    Plan p{};
+    const int elem = fp8 ? 1 : 2;
+    const int K = 2 * g.n_rx, N = 2 * g.n_beams;
+    p.b_bytes = (uint32_t)((size_t)N * K * elem);
+    const size_t fixed = 1024 + sizeof(TcShared) + 256 + (((size_t)p.b_bytes + 1023) & ~(size_t)1023);
+    int cols = 32;
+    while (cols < 2 * N) cols *= 2;
+    p.tmem_cols = cols;
+    for (int staged = 1; staged >= 0; --staged) {
+        const size_t out_b = staged ? (size_t)512 * N : 0;
+        for (int rows = fp8 ? 256 : 128; rows >= 64; rows >>= 1) {
+            const int cr = K < rows ? K : rows;
+            const uint32_t sb = (uint32_t)kTileM * elem * cr;
+            const long long avail = (long long)kSmemLimit - (long long)(fixed + out_b);
+            int ns = avail > 0 ? (int)(avail / sb) : 0;
+            if (ns > kMaxStages) ns = kMaxStages;
+            if (ns >= 3 || (!staged && rows == 64 && ns >= 2)) {
+                p.chunk_rows = cr;
+                p.stage_bytes = sb;
+                p.n_stages = ns;
+                p.stage_out = staged;
+                p.n_chunks = (K + cr - 1) / cr;
+                p.smem = 1024 + (size_t)ns * sb + (((size_t)p.b_bytes + 1023) & ~(size_t)1023) + out_b;
+                p.ok = cols <= 256;
+                return p;
+            }
+        }
+    }
+    return p;
 }
 
-}  // namespace
-
-bool bf_tc_supported(const Geometry &g) {
-    return g.n_rx % 8 == 0 && g.n_rx >= 8 && g.n_rx <= 128 && g.n_beams % 8 == 0 && g.n_beams >= 8 &&
-           g.n_beams <= 64 && tc_smem_bytes(g) <= 227 * 1024;
+bool shape_ok(const Geometry &g, bool fp8) {
+    if (g.n_beams % 8 != 0 || g.n_beams < 8 || g.n_beams > 64) return false;
+    if (fp8) {
+        if (g.n_rx % 16 != 0 || g.n_rx < 16 || g.n_rx > kMaxRxFp8) return false;
+    } else {
+        if (g.n_rx % 8 != 0 || g.n_rx < 8 || g.n_rx > 1024) return false;
+    }
+    return make_plan(g, fp8).ok;
 }
 
-cudaError_t launch_beamform_tc(const Geometry &g, int n_slots, const __half *freq16, const float2 *W, float2 *beam,
-                               uint32_t *err_word, cudaStream_t st) {
+template <bool FP8>
+cudaError_t launch_tc(const Geometry &g, int n_slots, const void *freq, const float *scales, const float2 *W,
+                      float2 *beam, uint32_t *err_word, cudaStream_t st) {
     if (n_slots == 0) return cudaSuccess;
-    if (!bf_tc_supported(g)) return cudaErrorNotSupported;
-    if (reinterpret_cast<uintptr_t>(freq16) % 16 != 0 || reinterpret_cast<uintptr_t>(beam) % 16 != 0)
+    if (!shape_ok(g, FP8)) return cudaErrorNotSupported;
+    if (reinterpret_cast<uintptr_t>(freq) % 16 != 0 || reinterpret_cast<uintptr_t>(beam) % 16 != 0)
         return cudaErrorMisalignedAddress;
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
+    const Plan p = make_plan(g, FP8);
     const int K = 2 * g.n_rx;
     const long long rows = (long long)n_slots * g.n_sym;
+    const int elem = FP8 ? 1 : 2;
     CUtensorMap map;
     cuuint64_t dims[2] = {(cuuint64_t)g.sc_pitch, (cuuint64_t)(rows * K)};
-    cuuint64_t strides[1] = {(cuuint64_t)g.sc_pitch * 2};
-    cuuint32_t box[2] = {64, (cuuint32_t)K};
+    cuuint64_t strides[1] = {(cuuint64_t)g.sc_pitch * elem};
+    cuuint32_t box[2] = {(cuuint32_t)(FP8 ? 128 : 64), (cuuint32_t)p.chunk_rows};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<__half *>(freq16), dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r = enc(&map, FP8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
+                     const_cast<void *>(freq), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    // output as floats [rows][n_sc][2 n_beams]: boxes of 16 floats x 32 subcarriers, 64-byte swizzle
+    CUtensorMap omap;
+    {
+        cuuint64_t od[3] = {(cuuint64_t)(2 * g.n_beams), (cuuint64_t)g.n_sc, (cuuint64_t)rows};
+        cuuint64_t os[2] = {(cuuint64_t)g.n_beams * 8, (cuuint64_t)g.n_sc * g.n_beams * 8};
+        cuuint32_t ob[3] = {16, 32, 1};
+        cuuint32_t oe[3] = {1, 1, 1};
+        r = enc(&omap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, beam, od, os, ob, oe, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    }
     TcArgs a;
     a.n_rx = g.n_rx;
     a.n_beams = g.n_beams;
     a.n_sc = g.n_sc;
     a.n_mtiles = (g.n_sc + kTileM - 1) / kTileM;
+    a.n_blk = a.n_mtiles;
+    a.K = K;
+    a.N = 2 * g.n_beams;
+    a.chunk_rows = p.chunk_rows;
+    a.n_chunks = p.n_chunks;
+    a.n_stages = p.n_stages;
+    a.tmem_cols = p.tmem_cols;
+    a.stage_bytes = p.stage_bytes;
+    a.b_bytes = p.b_bytes;
+    a.stage_out = p.stage_out;
     a.total_tiles = rows * a.n_mtiles;
-    int cols = 32;
-    while (cols < 2 * g.n_beams) cols *= 2;
-    a.tmem_cols = cols;
-    const size_t smem = tc_smem_bytes(g);
-    cudaError_t e = cudaFuncSetAttribute(beamform_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = beamform_tc_kernel<FP8>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    long long grid = 2LL * sms;
+    long long grid = sms;
     if (grid > a.total_tiles) grid = a.total_tiles;
-    beamform_tc_kernel<<<(unsigned)grid, kTcThreads, smem, st>>>(map, a, W, beam, err_word);
+    kern<<<(unsigned)grid, FP8 ? 320 : 192, p.smem, st>>>(map, omap, a, W, scales, beam, err_word);
     return cudaGetLastError();
+}
+
+}  // namespace
+
+bool bf_tc_supported(const Geometry &g) { return shape_ok(g, false); }
+bool bf_fp8_supported(const Geometry &g) { return shape_ok(g, true); }
+
+cudaError_t launch_beamform_tc(const Geometry &g, int n_slots, const __half *freq16, const float2 *W, float2 *beam,
+                               uint32_t *err_word, cudaStream_t st) {
+    return launch_tc<false>(g, n_slots, freq16, nullptr, W, beam, err_word, st);
+}
+
+cudaError_t launch_beamform_fp8(const Geometry &g, int n_slots, const uint8_t *freq8, const float *scales,
+                                const float2 *W, float2 *beam, uint32_t *err_word, cudaStream_t st) {
+    if (reinterpret_cast<uintptr_t>(scales) % 16 != 0) return cudaErrorMisalignedAddress;
+    return launch_tc<true>(g, n_slots, freq8, scales, W, beam, err_word, st);
 }
 
 }  // namespace pusch

@@ -1,413 +1,19 @@
-// OFDM demodulation: batched forward FFTs of N_F = 64..4096 points with active-bin extraction
-// (Section II: one FFT per antenna and OFDM symbol; Table I "OFDM dem.").
-//
-// Design (GB300): one FFT per group of T = N/E threads, each thread holding E = 8 or 16 complex values in
-// registers. The transform is a Stockham auto-sort sequence of radix-16/8/4 passes, so that
-//   * pass 1 reads its butterfly inputs (element t + T*e) from the shared-memory copy of the input row,
-//   * the last pass leaves bin t + T*e in register e, written to global memory in natural order,
-//   * the passes in between exchange through shared memory padded by one slot per 16 (conflict-free).
-// 4096 = 16*16*16 therefore costs one global read, two shared-memory exchanges and one global write.
-// CTAs are persistent: the input rows arrive by bulk (TMA) copies into a 2-3 stage ring issued ahead of
-// the transform, so HBM reads overlap the arithmetic. Twiddles come from a table exp(-2 pi i q / N)
-// (computed in double precision).
-#include "internal.cuh"
+// OFDM demodulation (Section II; Table I "OFDM dem."): dispatch of the batched FFT kernels of
+// fft_impl.cuh on the cell's arithmetic form.
+#include "fft_impl.cuh"
 
 namespace pusch {
-namespace {
-
-constexpr float kC8 = 0.70710678118654752440f;   // cos(pi/4)
-constexpr float kC16 = 0.92387953251128675613f;  // cos(pi/8)
-constexpr float kS16 = 0.38268343236508977173f;  // sin(pi/8)
-
-// x * exp(-2 pi i q / 16) for a compile-time q in [0, 16)
-template <int Q>
-__device__ __forceinline__ float2 rot16(float2 x) {
-    constexpr int q = Q & 15;
-    if constexpr (q == 0) return x;
-    else if constexpr (q == 4) return make_float2(x.y, -x.x);
-    else if constexpr (q == 8) return make_float2(-x.x, -x.y);
-    else if constexpr (q == 12) return make_float2(-x.y, x.x);
-    else {
-        constexpr float c[16] = {1.f, kC16, kC8, kS16, 0.f, -kS16, -kC8, -kC16,
-                                 -1.f, -kC16, -kC8, -kS16, 0.f, kS16, kC8, kC16};
-        constexpr float s[16] = {0.f, kS16, kC8, kC16, 1.f, kC16, kC8, kS16,
-                                 0.f, -kS16, -kC8, -kC16, -1.f, -kC16, -kC8, -kS16};
-        // multiply by (c - i s)
-        return make_float2(x.x * c[q] + x.y * s[q], x.y * c[q] - x.x * s[q]);
-    }
-}
-
-__device__ __forceinline__ void dft2(float2 &a, float2 &b) {
-    float2 t = a;
-    a = cadd(t, b);
-    b = csub(t, b);
-}
-
-// forward 4-point DFT in place
-__device__ __forceinline__ void dft4(float2 &x0, float2 &x1, float2 &x2, float2 &x3) {
-    float2 a = cadd(x0, x2), b = csub(x0, x2), c = cadd(x1, x3), d = csub(x1, x3);
-    x0 = cadd(a, c);
-    x2 = csub(a, c);
-    x1 = make_float2(b.x + d.y, b.y - d.x);  // b - i d
-    x3 = make_float2(b.x - d.y, b.y + d.x);  // b + i d
-}
-
-// Forward R-point DFT of x[0..R) in natural order, R in {2, 4, 8, 16}.
-// R = 8 and 16 are split as R = 4 * (R/4): n = (R/4)*n1 + n2, k = k1 + 4*k2.
-template <int R>
-__device__ __forceinline__ void dft(float2 (&x)[R]) {
-    if constexpr (R == 2) {
-        dft2(x[0], x[1]);
-    } else if constexpr (R == 4) {
-        dft4(x[0], x[1], x[2], x[3]);
-    } else if constexpr (R == 8) {
-        // inner DFT-4 over n1 for n2 = 0, 1 (stride-2 samples)
-        dft4(x[0], x[2], x[4], x[6]);
-        dft4(x[1], x[3], x[5], x[7]);
-        float2 a1 = rot16<2>(x[3]), a2 = rot16<4>(x[5]), a3 = rot16<6>(x[7]);
-        float2 y[8];
-        y[0] = cadd(x[0], x[1]); y[4] = csub(x[0], x[1]);
-        y[1] = cadd(x[2], a1);   y[5] = csub(x[2], a1);
-        y[2] = cadd(x[4], a2);   y[6] = csub(x[4], a2);
-        y[3] = cadd(x[6], a3);   y[7] = csub(x[6], a3);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) x[i] = y[i];
-    } else if constexpr (R == 16) {
-        // A[n2][k1] = DFT4_{n1}(x[4 n1 + n2]) stored back at x[4 k1 + n2]
-        dft4(x[0], x[4], x[8], x[12]);
-        dft4(x[1], x[5], x[9], x[13]);
-        dft4(x[2], x[6], x[10], x[14]);
-        dft4(x[3], x[7], x[11], x[15]);
-        // twiddle A[n2][k1] by w16^(n2 k1)
-        x[5] = rot16<1>(x[5]);  x[9] = rot16<2>(x[9]);   x[13] = rot16<3>(x[13]);
-        x[6] = rot16<2>(x[6]);  x[10] = rot16<4>(x[10]); x[14] = rot16<6>(x[14]);
-        x[7] = rot16<3>(x[7]);  x[11] = rot16<6>(x[11]); x[15] = rot16<9>(x[15]);
-        // out[k1 + 4 k2] = DFT4_{n2}(A[n2][k1]); A[.][k1] sits at x[4 k1 .. 4 k1 + 3]
-        dft4(x[0], x[1], x[2], x[3]);
-        dft4(x[4], x[5], x[6], x[7]);
-        dft4(x[8], x[9], x[10], x[11]);
-        dft4(x[12], x[13], x[14], x[15]);
-        float2 y[16];
-#pragma unroll
-        for (int k1 = 0; k1 < 4; ++k1)
-#pragma unroll
-            for (int k2 = 0; k2 < 4; ++k2) y[k1 + 4 * k2] = x[4 * k1 + k2];
-#pragma unroll
-        for (int i = 0; i < 16; ++i) x[i] = y[i];
-    }
-}
-
-__device__ __forceinline__ int pad16(int p) { return p + (p >> 4); }
-
-// One Stockham radix-R pass over the E register values of thread t (Ls = product of earlier radices).
-// Butterfly j = t + u*T takes inputs j + m*N/R (register u + m*E/R) and twiddles input m by
-// exp(-2 pi i (j mod Ls) m / (Ls R)).
-template <int N, int E, int R, int LS>
-__device__ __forceinline__ void fft_pass(float2 (&v)[E], const float2 *__restrict__ tw, int t) {
-    constexpr int T = N / E;
-    constexpr int NB = E / R;
-#pragma unroll
-    for (int u = 0; u < NB; ++u) {
-        const int j = t + u * T;
-        const int k = j & (LS - 1);
-        float2 x[R];
-#pragma unroll
-        for (int m = 0; m < R; ++m) x[m] = v[u + m * NB];
-        if constexpr (LS > 1) {
-            // w^m, m < R, from the table entries w^1..w^4 and at most two more products (<= 3 roundings)
-            constexpr int S = N / (LS * R);
-            float2 w[R];
-            w[0] = make_float2(1.f, 0.f);
-#pragma unroll
-            for (int m = 1; m < R && m <= 4; ++m) w[m] = __ldg(&tw[(k * m) * S]);
-            if constexpr (R > 5) {
-                const float2 w8 = cmul(w[4], w[4]);
-                const float2 w12 = cmul(w8, w[4]);
-#pragma unroll
-                for (int m = 5; m < R; ++m) {
-                    const int a4 = m >> 2, b = m & 3;
-                    const float2 base = a4 == 1 ? w[4] : (a4 == 2 ? w8 : w12);
-                    w[m] = b == 0 ? base : cmul(base, w[b]);
-                }
-            }
-#pragma unroll
-            for (int m = 1; m < R; ++m) x[m] = cmul(x[m], w[m]);
-        }
-        dft<R>(x);
-#pragma unroll
-        for (int m = 0; m < R; ++m) v[u + m * NB] = x[m];
-    }
-}
-
-// Stockham output placement of a non-final pass, then gather of the next pass's inputs t + T*e.
-template <int N, int E, int R, int LS>
-__device__ __forceinline__ void fft_exchange(float2 (&v)[E], float2 *sm, int t) {
-    constexpr int T = N / E;
-    constexpr int NB = E / R;
-    __syncthreads();
-#pragma unroll
-    for (int u = 0; u < NB; ++u) {
-        const int j = t + u * T;
-        const int k = j & (LS - 1);
-        const int base = (j - k) * R + k;
-#pragma unroll
-        for (int m = 0; m < R; ++m) sm[pad16(base + m * LS)] = v[u + m * NB];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int e = 0; e < E; ++e) v[e] = sm[pad16(t + T * e)];
-}
-
-template <int N, int E, int LS, int R, int... Rest>
-__device__ __forceinline__ void fft_run(float2 (&v)[E], float2 *sm, const float2 *__restrict__ tw, int t) {
-    fft_pass<N, E, R, LS>(v, tw, t);
-    if constexpr (sizeof...(Rest) > 0) {
-        fft_exchange<N, E, R, LS>(v, sm, t);
-        fft_run<N, E, LS * R, Rest...>(v, sm, tw, t);
-    }
-}
-
-template <int N> struct Plan;
-template <> struct Plan<4096> { static constexpr int E = 16; };
-template <> struct Plan<2048> { static constexpr int E = 16; };
-template <> struct Plan<1024> { static constexpr int E = 16; };
-template <> struct Plan<512> { static constexpr int E = 8; };
-template <> struct Plan<256> { static constexpr int E = 16; };
-template <> struct Plan<128> { static constexpr int E = 16; };
-template <> struct Plan<64> { static constexpr int E = 8; };
-
-template <int N>
-__device__ __forceinline__ void fft_full(float2 (&v)[Plan<N>::E], float2 *sm, const float2 *__restrict__ tw, int t) {
-    constexpr int E = Plan<N>::E;
-    if constexpr (N == 4096) fft_run<N, E, 1, 16, 16, 16>(v, sm, tw, t);
-    else if constexpr (N == 2048) fft_run<N, E, 1, 16, 16, 8>(v, sm, tw, t);
-    else if constexpr (N == 1024) fft_run<N, E, 1, 16, 16, 4>(v, sm, tw, t);
-    else if constexpr (N == 512) fft_run<N, E, 1, 8, 8, 8>(v, sm, tw, t);
-    else if constexpr (N == 256) fft_run<N, E, 1, 16, 16>(v, sm, tw, t);
-    else if constexpr (N == 128) fft_run<N, E, 1, 16, 8>(v, sm, tw, t);
-    else if constexpr (N == 64) fft_run<N, E, 1, 8, 8>(v, sm, tw, t);
-}
-
-__device__ __forceinline__ float2 to_f2(float2 v) { return v; }
-__device__ __forceinline__ float2 to_f2(__half2 v) { return __half22float2(v); }
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ uint64_t globaltimer() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait (2 s of %globaltimer); false on expiry.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    const uint64_t deadline = globaltimer() + 2000000000ull;
-    while (!mbar_try_wait(bar, parity))
-        if (globaltimer() > deadline) return false;
-    return true;
-}
-
-// One bulk (TMA, non-tensor) copy global -> shared completing on an mbarrier: 16-byte aligned, size % 16 == 0.
-__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "l"(src), "r"(bytes), "r"(bar)
-                 : "memory");
-}
-
-constexpr int kFftThreads = 256;
-
-template <int N>
-constexpr int ffts_per_cta() {
-    return (kFftThreads / (N / Plan<N>::E)) > 0 ? kFftThreads / (N / Plan<N>::E) : 1;
-}
-
-template <typename TIn>
-constexpr int fft_stages() { return 2; }
-
-template <int N, typename TIn>
-constexpr size_t fft_smem_bytes() {
-    return (size_t)fft_stages<TIn>() * ffts_per_cta<N>() * N * sizeof(TIn)        // input ring
-           + (size_t)ffts_per_cta<N>() * (N + N / 16) * sizeof(float2)             // exchange buffer
-           + 8 * fft_stages<TIn>() + 16;                                           // mbarriers
-}
-
-// Persistent batched FFT. rows = n_slots * n_sym * n_rx transforms; each CTA iterates over blocks of F
-// consecutive rows (one contiguous span of F*N input samples). The spans arrive by bulk copies into a
-// ring of STAGES shared-memory buffers issued STAGES-1 blocks ahead, so HBM reads overlap the passes.
-// out16 = false: c64 [rows][n_sc]; out16 = true: binary16 [rows][2][pitch] (re plane, im plane; pads
-// zeroed), staged through shared memory for 16-byte stores.
-// Three 256-thread CTAs per SM (registers capped at 85; the 2-stage ring keeps shared memory at ~67 KB
-// per CTA for FP16 input): 24 warps hide the exchange barriers while one row per CTA streams in.
-template <int N, typename TIn, bool OUT16>
-__global__ void __launch_bounds__(kFftThreads, 3)
-fft_kernel(const TIn *__restrict__ in, void *__restrict__ out, const float2 *__restrict__ tw, long long rows,
-           int n_sc, int pitch, uint32_t *__restrict__ err) {
-    constexpr int E = Plan<N>::E;
-    constexpr int T = N / E;
-    constexpr int F = ffts_per_cta<N>();
-    constexpr int STAGES = fft_stages<TIn>();
-    constexpr uint32_t kSpan = (uint32_t)F * N * sizeof(TIn);
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    TIn *ring = reinterpret_cast<TIn *>(smem_raw);
-    float2 *xbuf = reinterpret_cast<float2 *>(smem_raw + (size_t)STAGES * kSpan);
-    const uint32_t bar0 = smem_u32(smem_raw + (size_t)STAGES * kSpan + (size_t)F * (N + N / 16) * sizeof(float2));
-    __shared__ int s_abort;
-
-    const int f = threadIdx.x / T;
-    const int t = threadIdx.x - f * T;
-    float2 *sm = xbuf + f * (N + N / 16);
-    const long long n_blocks = (rows + F - 1) / F;
-    const long long n_my = n_blocks > blockIdx.x ? (n_blocks - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
-
-    auto issue = [&](long long it) {
-        const long long blk = blockIdx.x + it * gridDim.x;
-        const long long r0 = blk * F;
-        const long long nr = rows - r0 < F ? rows - r0 : F;
-        const int s = (int)(it % STAGES);
-        bulk_load(smem_u32(ring) + s * kSpan, in + r0 * N, (uint32_t)(nr * N * sizeof(TIn)), bar0 + 8 * s);
-    };
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) mbar_init(bar0 + 8 * s, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        s_abort = 0;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0)
-        for (long long it = 0; it < STAGES - 1 && it < n_my; ++it) issue(it);
-
-    const int h = n_sc >> 1;
-    long long it = 0;
-    for (; it < n_my; ++it) {
-        const int s = (int)(it % STAGES);
-        const bool ok = mbar_wait(bar0 + 8 * s, (uint32_t)((it / STAGES) & 1));
-        if (__syncthreads_or(!ok)) {
-            if (threadIdx.x == 0) {
-                s_abort = 1;
-                if (err) atomicOr(err, 2u);
-            }
-            break;
-        }
-        // the ring slot consumed by the previous block is free (all threads passed a barrier since)
-        if (threadIdx.x == 0 && it + STAGES - 1 < n_my) issue(it + STAGES - 1);
-
-        const long long row = (blockIdx.x + it * gridDim.x) * F + f;
-        const bool valid = row < rows;
-        const TIn *src = ring + (size_t)s * F * N + (size_t)f * N;
-        float2 v[E];
-#pragma unroll
-        for (int e = 0; e < E; ++e) v[e] = to_f2(src[t + T * e]);
-        fft_full<N>(v, sm, tw, t);
-
-        if constexpr (!OUT16) {
-            if (valid) {
-                float2 *dst = static_cast<float2 *>(out) + row * n_sc;
-#pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    int a = t + T * e + h;
-                    if (a >= N) a -= N;
-                    if (a < n_sc) dst[a] = v[e];
-                }
-            }
-        } else {
-            // stage the two planes of this FFT in its exchange buffer (free after the last pass), then
-            // write them with 16-byte stores
-            __syncthreads();
-            __half *pl = reinterpret_cast<__half *>(sm);
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                int a = t + T * e + h;
-                if (a >= N) a -= N;
-                if (a < n_sc) {
-                    pl[a] = __float2half_rn(v[e].x);
-                    pl[pitch + a] = __float2half_rn(v[e].y);
-                }
-            }
-            for (int a = n_sc + t; a < pitch; a += T) {
-                pl[a] = __float2half_rn(0.f);
-                pl[pitch + a] = __float2half_rn(0.f);
-            }
-            __syncthreads();
-            if (valid) {
-                const uint4 *srcv = reinterpret_cast<const uint4 *>(pl);
-                uint4 *dstv = reinterpret_cast<uint4 *>(static_cast<__half *>(out) + row * 2 * (long long)pitch);
-                for (int c = t; c < pitch / 4; c += T) dstv[c] = srcv[c];  // 2 * pitch halves = pitch / 4 x 16 B
-            }
-        }
-    }
-    if (s_abort && threadIdx.x == 0) {
-        // drain the copies still in flight (bounded) before the CTA exits
-        for (long long j = it; j < it + STAGES - 1 && j < n_my; ++j)
-            mbar_wait(bar0 + 8 * (int)(j % STAGES), (uint32_t)((j / STAGES) & 1));
-    }
-}
-
-template <int N, typename TIn, bool OUT16>
-cudaError_t launch_n(long long rows, const void *in, void *out, const float2 *tw, int n_sc, int pitch, uint32_t *err,
-                     cudaStream_t st) {
-    constexpr int F = ffts_per_cta<N>();
-    constexpr size_t smem = fft_smem_bytes<N, TIn>();
-    static_assert(smem <= 227 * 1024, "FFT shared memory");
-    auto k = fft_kernel<N, TIn, OUT16>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 152, per_sm = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kFftThreads, smem);
-    if (per_sm < 1) per_sm = 1;
-    const long long blocks = (rows + F - 1) / F;
-    long long grid = (long long)sms * per_sm;
-    if (grid > blocks) grid = blocks;
-    k<<<(unsigned)grid, kFftThreads, smem, st>>>(static_cast<const TIn *>(in), out, tw, rows, n_sc, pitch, err);
-    return cudaGetLastError();
-}
-
-template <int N>
-cudaError_t launch_typed(const Geometry &g, long long rows, const void *in, void *out, const float2 *tw, uint32_t *err,
-                         cudaStream_t st) {
-    const bool out16 = g.form == PUSCH_FORM_MIXED;
-    if (g.in_fp16) {
-        return out16 ? launch_n<N, __half2, true>(rows, in, out, tw, g.n_sc, g.sc_pitch, err, st)
-                     : launch_n<N, __half2, false>(rows, in, out, tw, g.n_sc, g.sc_pitch, err, st);
-    }
-    return out16 ? launch_n<N, float2, true>(rows, in, out, tw, g.n_sc, g.sc_pitch, err, st)
-                 : launch_n<N, float2, false>(rows, in, out, tw, g.n_sc, g.sc_pitch, err, st);
-}
-
-}  // namespace
 
 cudaError_t launch_fft(const Geometry &g, int n_slots, const void *time_in, void *freq_out, const float2 *twiddle,
                        uint32_t *err, cudaStream_t st) {
     if (reinterpret_cast<uintptr_t>(time_in) % 16 != 0) return cudaErrorMisalignedAddress;
     const long long rows = (long long)n_slots * g.n_sym * g.n_rx;
     if (rows == 0) return cudaSuccess;
-    switch (g.n_fft) {
-        case 4096: return launch_typed<4096>(g, rows, time_in, freq_out, twiddle, err, st);
-        case 2048: return launch_typed<2048>(g, rows, time_in, freq_out, twiddle, err, st);
-        case 1024: return launch_typed<1024>(g, rows, time_in, freq_out, twiddle, err, st);
-        case 512: return launch_typed<512>(g, rows, time_in, freq_out, twiddle, err, st);
-        case 256: return launch_typed<256>(g, rows, time_in, freq_out, twiddle, err, st);
-        case 128: return launch_typed<128>(g, rows, time_in, freq_out, twiddle, err, st);
-        case 64: return launch_typed<64>(g, rows, time_in, freq_out, twiddle, err, st);
-        default: return cudaErrorInvalidValue;
-    }
+    if (rows > 0x7fffffffLL) return cudaErrorInvalidValue;   // row indices are 32-bit in the epilogues
+    if (g.form == PUSCH_FORM_MIXED) return launch_fft_f16(g, rows, time_in, freq_out, twiddle, nullptr, err, st);
+    if (g.form == PUSCH_FORM_FP8)
+        return launch_fft_e4m3(g, rows, time_in, freq_out, twiddle, fp8_scales(g, n_slots, freq_out), err, st);
+    return launch_fft_c64(g, rows, time_in, freq_out, twiddle, nullptr, err, st);
 }
 
 }  // namespace pusch

@@ -45,13 +45,31 @@ struct Geometry {
     int n_rx, n_fft, n_sc, n_beams, n_layers, comb, qam_bits, in_fp16, form, n_sym;
     int dmrs0, dmrs1;
     int n_data;
-    int sc_pitch;                 // mixed-form FFT output row pitch (elements)
+    int sc_pitch;                 // mixed / FP8 FFT output: elements between the re and im planes of a row
     float noise_var, loading;
     int port[32];
     int data_sym[16];             // data symbol indices in increasing order
 };
 
 Geometry make_geometry(const pusch_cell_cfg &c);
+
+// Bytes of the FFT output (pusch_ofdm_fft's freq_out) for n_slots slots of a geometry. FP8 form: the E4M3
+// planes [rows][2][sc_pitch] followed, at fp8_scale_offset, by the float block scales
+// [n_slots * n_sym][n_blk][n_rx], n_blk = ceil(n_sc / 128).
+inline size_t fp8_scale_offset(const Geometry &g, int n_slots) {
+    const size_t planes = (size_t)n_slots * g.n_sym * g.n_rx * 2 * g.sc_pitch;
+    return (planes + 255) & ~(size_t)255;
+}
+inline float *fp8_scales(const Geometry &g, int n_slots, void *freq) {
+    return reinterpret_cast<float *>(static_cast<uint8_t *>(freq) + fp8_scale_offset(g, n_slots));
+}
+inline size_t freq_bytes_of(const Geometry &g, int n_slots) {
+    const size_t rows = (size_t)n_slots * g.n_sym * g.n_rx;
+    if (g.form == PUSCH_FORM_MIXED) return rows * 2 * g.sc_pitch * sizeof(__half);
+    if (g.form == PUSCH_FORM_FP8)
+        return fp8_scale_offset(g, n_slots) + (size_t)n_slots * g.n_sym * ((g.n_sc + 127) / 128) * g.n_rx * 4;
+    return rows * g.n_sc * sizeof(float2);
+}
 
 // Sets the thread's pusch_last_error() message.
 void set_last_error(const char *msg);
@@ -81,6 +99,20 @@ cudaError_t launch_mmse_fused(const Geometry &g, int n_slots, const float2 *beam
 cudaError_t launch_beamform_tc(const Geometry &g, int n_slots, const __half *freq16, const float2 *W, float2 *beam,
                                uint32_t *err_word, cudaStream_t st);
 bool bf_tc_supported(const Geometry &g);
+// FP8 form: E4M3 codes with power-of-two block scales (layout of freq_bytes_of), same kernel family.
+cudaError_t launch_beamform_fp8(const Geometry &g, int n_slots, const uint8_t *freq8, const float *scales,
+                                const float2 *W, float2 *beam, uint32_t *err_word, cudaStream_t st);
+bool bf_fp8_supported(const Geometry &g);
+// Beamforming of the FFT output in the geometry's form (FP32 SIMT, FP16 or FP8 tensor cores).
+inline cudaError_t launch_beamform(const Geometry &g, int n_slots, const void *freq, const float2 *W, float2 *beam,
+                                   uint32_t *err_word, cudaStream_t st) {
+    if (g.form == PUSCH_FORM_MIXED)
+        return launch_beamform_tc(g, n_slots, static_cast<const __half *>(freq), W, beam, err_word, st);
+    if (g.form == PUSCH_FORM_FP8)
+        return launch_beamform_fp8(g, n_slots, static_cast<const uint8_t *>(freq),
+                                   fp8_scales(g, n_slots, const_cast<void *>(freq)), W, beam, err_word, st);
+    return launch_beamform_fp32(g, n_slots, static_cast<const float2 *>(freq), W, beam, st);
+}
 
 // Learned channel-estimate denoiser (cnn.cu). Parameters packed per layer as W[co][ci][3][3], b[co].
 int cnn_param_count();

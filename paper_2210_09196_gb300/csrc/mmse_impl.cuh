@@ -1,0 +1,226 @@
+// MMSE MIMO detection (Eq. 2), computed as in Section II: Gram G = H^H H + sigma^2 I, Cholesky
+// G = L L^H (Section V-C), forward solve L z = H^H y, back solve L^H x = z; then Gray hard decisions.
+//
+// GB300 mapping: a group of NL lanes owns one subcarrier (NL = layer class 2..32, a power of two), so a
+// warp detects 32/NL subcarriers at once; lane i of a group owns layer i.
+//   1. The estimate H of the warp's subcarriers is staged in shared memory (rows padded to an even stride):
+//      copied from the caller's buffer with cp.async, or - in the fused variant used by pusch_slot -
+//      interpolated right here from the table of LS values at the pilot subcarriers (the same arithmetic
+//      as the estimation kernel), so that the full estimate never travels to HBM. The per-row pilot
+//      brackets are computed once per (subcarrier, layer), then the LS rows are read with coalesced loads.
+//   0. The data-symbol vectors y_d of the warp's subcarriers are copied to shared memory with cp.async
+//      first, so that their latency overlaps steps 1-2a.
+//   2. Lane i forms row i of G from 16-byte shared loads, then r_d = H^H y_d for every data symbol d.
+//   3. Right-looking Cholesky of G in registers: the pivot and column entries are broadcast by warp
+//      shuffles. L is written to shared memory over the (now dead) H tile.
+//   4. Forward and back solves for all data symbols together, one shuffle per unknown and symbol, L read
+//      from shared memory (row i for the forward solve, column i for the back solve).
+// G and L are formed once per subcarrier, which gives the same result as forming them per data symbol
+// because the estimate is constant over the slot. Layers beyond n_layers (up to NL) are padded with
+// identity rows and produce nothing.
+#pragma once
+
+#include "chest_common.cuh"
+#include "detect_core.cuh"
+
+namespace pusch {
+namespace mmse_detail {
+
+constexpr int kMmseWarps = 2;
+constexpr unsigned kFull = 0xffffffffu;
+
+struct MmseArgs {
+    int n_sc, n_beams, n_layers, n_sym, n_data, qam_bits, comb, dmrs0, dmrs1, kmax;
+    float load;  // sigma^2 + extra loading
+    int data_sym[16];
+    int port[32];
+};
+
+// Register cap: five 4-warp CTAs per SM up to 8 layers, four for 16 layers (no spills), none for 32.
+template <int NL, int ND, bool FUSED>
+__global__ void __launch_bounds__(kMmseWarps * 32, NL <= 8 ? 5 : (NL == 16 ? 4 : 1))
+mmse_kernel(MmseArgs g, long long total_sc, const float2 *__restrict__ H, const float2 *__restrict__ beam,
+            const float2 *__restrict__ ls, float2 *__restrict__ xhat, uint8_t *__restrict__ bits,
+            uint32_t *__restrict__ status) {
+    constexpr int SPW = 32 / NL;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int grp = lane / NL, i = lane - grp * NL;
+    const int src0 = grp * NL;
+    const int nl = g.n_layers, nb = g.n_beams, n_sc = g.n_sc;
+    const int nd = ND > 0 ? ND : g.n_data;
+    const int hs = row_stride(nb), ht = htile<NL>(nb);
+
+    unsigned char *wbase = smem_raw + (size_t)warp * warp_smem_bytes<NL, FUSED>(nb, nd);
+    float2 *Ht = reinterpret_cast<float2 *>(wbase);  // [SPW][ht]
+    float2 *Yt = Ht + SPW * ht;                      // [SPW][nd][hs]
+    RowParam *rp = reinterpret_cast<RowParam *>(Yt + (size_t)SPW * nd * hs);  // [SPW*NL]
+
+    const long long sc0 = ((long long)blockIdx.x * kMmseWarps + warp) * SPW;  // first (slot*n_sc + a) of warp
+    if (sc0 >= total_sc) return;                                              // whole warp idle
+    const long long my_sc = sc0 + grp;
+    const bool valid = my_sc < total_sc;
+    const long long slot = my_sc / n_sc;
+    const int a = (int)(my_sc - slot * n_sc);
+
+    // ---- 0. the data-symbol rows y_d of the warp's subcarriers -> shared memory, asynchronously (cp.async,
+    //         16-byte pieces when the beam count is even); waited for just before step 2b.
+    {
+        const bool wide = (nb & 1) == 0;
+        const int cpr = wide ? nb >> 1 : nb;  // pieces per row
+        int row = lane / cpr, c = lane - (lane / cpr) * cpr;
+        const int step_r = 32 / cpr, step_c = 32 - (32 / cpr) * cpr;
+        for (; row < SPW * nd;) {
+            const int gg = row / nd, d = row - gg * nd;
+            const long long sc = sc0 + gg;
+            float2 *dst = Yt + (gg * nd + d) * hs + (wide ? 2 * c : c);
+            if (sc < total_sc) {
+                const long long sl = sc / n_sc, aa = sc - sl * n_sc;
+                const float2 *src = beam + ((sl * g.n_sym + g.data_sym[d]) * n_sc + aa) * nb + (wide ? 2 * c : c);
+                if (wide)
+                    cp_async16(dst, src);
+                else
+                    cp_async8(dst, src);
+            } else {
+                dst[0] = make_float2(0.f, 0.f);
+                if (wide) dst[1] = make_float2(0.f, 0.f);
+            }
+            row += step_r;
+            c += step_c;
+            if (c >= cpr) {
+                c -= cpr;
+                ++row;
+            }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+
+    // ---- 1. channel estimate rows -> shared memory. Element e of the warp's [SPW*NL][nb] tile is handled
+    //         by lane e % 32; (row, b) advance incrementally (no division in the loop).
+    const int rows = SPW * NL;
+    if constexpr (!FUSED) {
+        int r = lane / nb, b = lane - (lane / nb) * nb;
+        const int step_r = 32 / nb, step_b = 32 - (32 / nb) * nb;
+        for (; r < rows;) {
+            const int gg = r / NL, l = r - gg * NL;  // NL is a power of two
+            float2 *dst = Ht + gg * ht + l * hs + b;
+            if (l < nl && sc0 + gg < total_sc)
+                cp_async8(dst, H + ((sc0 + gg) * nl + l) * (long long)nb + b);
+            else
+                *dst = make_float2(0.f, 0.f);
+            r += step_r;
+            b += step_b;
+            if (b >= nb) {
+                b -= nb;
+                ++r;
+            }
+        }
+        cp_async_wait_all();  // the H tile (and the earlier y group)
+    } else {
+        {   // row parameters: lane = row (SPW*NL == 32)
+            RowParam q;
+            q.valid = (valid && i < nl) ? 1 : 0;
+            q.lo = q.hi = 0;
+            q.w = 0.f;
+            if (q.valid) {
+                int lo, hi;
+                pilot_bracket(a, g.port[i], g.comb, n_sc, lo, hi);
+                const long long base = (slot * nl + i) * (long long)g.kmax * nb;
+                q.lo = base + (long long)((lo - g.port[i]) / g.comb) * nb;
+                q.hi = base + (long long)((hi - g.port[i]) / g.comb) * nb;
+                q.w = interp_weight(a, lo, hi);
+            }
+            rp[lane] = q;
+        }
+        __syncwarp();
+        int r = lane / nb, b = lane - (lane / nb) * nb;
+        const int step_r = 32 / nb, step_b = 32 - (32 / nb) * nb;
+        for (; r < rows;) {
+            const int gg = r / NL, l = r - gg * NL;
+            const RowParam &q = rp[r];
+            float2 h = make_float2(0.f, 0.f);
+            if (q.valid) {
+                h = __ldg(&ls[q.lo + b]);
+                if (q.hi != q.lo) h = interp(h, __ldg(&ls[q.hi + b]), q.w);
+            }
+            Ht[gg * ht + l * hs + b] = h;
+            r += step_r;
+            b += step_b;
+            if (b >= nb) {
+                b -= nb;
+                ++r;
+            }
+        }
+    }
+    __syncwarp();
+
+    const float2 *hr = Ht + grp * ht + i * hs;  // own row
+    const float2 *hg = Ht + grp * ht;           // the group's rows
+    constexpr int NR = ND > 0 ? ND : 14;
+    float2 acc[NR];
+    const bool bad = detect_group<NL, ND, NR>(hr, hg, Yt + grp * nd * hs, Ht + grp * ht, hs, nb, nd, nl, g.load, i,
+                                              src0, acc);
+    if (valid && bad && i == 0) {
+        atomicAdd(&status[1], 1u);
+        atomicMin(&status[2], (unsigned)my_sc);
+        atomicOr(&status[0], (unsigned)PUSCH_STATUS_PIVOT);
+    }
+
+    bool nonfinite = false;
+    if (valid && i < nl) {
+        const long long o0 = (slot * nl + i) * (long long)nd * n_sc + a;
+#pragma unroll
+        for (int d = 0; d < NR; ++d) {
+            if (ND > 0 || d < nd) {
+                const float2 x = acc[d];
+                xhat[o0 + (long long)d * n_sc] = x;
+                bits[o0 + (long long)d * n_sc] = det_demap(x, g.qam_bits);
+                if (!isfinite(x.x) || !isfinite(x.y)) nonfinite = true;
+            }
+        }
+    }
+    if (__any_sync(kFull, nonfinite) && lane == 0) atomicOr(&status[0], (unsigned)PUSCH_STATUS_NONFINITE);
+}
+
+template <int NL, int ND, bool FUSED>
+cudaError_t launch_nl(const MmseArgs &a, long long total_sc, const float2 *H, const float2 *beam,
+                      const float2 *pilots, float2 *xhat, uint8_t *bits, uint32_t *status, cudaStream_t st) {
+    constexpr int SPW = 32 / NL;
+    const size_t smem = (size_t)kMmseWarps * warp_smem_bytes<NL, FUSED>(a.n_beams, ND > 0 ? ND : a.n_data);
+    const long long per_cta = (long long)kMmseWarps * SPW;
+    const long long grid = (total_sc + per_cta - 1) / per_cta;
+    if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    auto k = mmse_kernel<NL, ND, FUSED>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k<<<(unsigned)grid, kMmseWarps * 32, smem, st>>>(a, total_sc, H, beam, pilots, xhat, bits, status);
+    return cudaGetLastError();
+}
+
+template <int NL, bool FUSED>
+cudaError_t launch_nd(const MmseArgs &a, long long total_sc, const float2 *H, const float2 *beam,
+                      const float2 *pilots, float2 *xhat, uint8_t *bits, uint32_t *status, cudaStream_t st) {
+    if (a.n_data == 12) return launch_nl<NL, 12, FUSED>(a, total_sc, H, beam, pilots, xhat, bits, status, st);
+    return launch_nl<NL, 0, FUSED>(a, total_sc, H, beam, pilots, xhat, bits, status, st);
+}
+
+}  // namespace mmse_detail
+
+// Launch of one layer class (separate translation units, compiled in parallel): NL = 2, 4 or 8 in
+// mmse_small.cu, 16 in mmse_nl16.cu, 32 in mmse_nl32.cu (the fused variant in mmse_nl32f.cu).
+cudaError_t mmse_launch_class(int nl_class, bool fused, const mmse_detail::MmseArgs &a, long long total_sc,
+                              const float2 *H, const float2 *beam, const float2 *pilots, float2 *xhat, uint8_t *bits,
+                              uint32_t *status, cudaStream_t st);
+cudaError_t mmse_launch_class16(bool fused, const mmse_detail::MmseArgs &a, long long total_sc, const float2 *H,
+                                const float2 *beam, const float2 *pilots, float2 *xhat, uint8_t *bits,
+                                uint32_t *status, cudaStream_t st);
+cudaError_t mmse_launch_class32(bool fused, const mmse_detail::MmseArgs &a, long long total_sc, const float2 *H,
+                                const float2 *beam, const float2 *pilots, float2 *xhat, uint8_t *bits,
+                                uint32_t *status, cudaStream_t st);
+cudaError_t mmse_launch_class32_fused(const mmse_detail::MmseArgs &a, long long total_sc, const float2 *beam,
+                                      const float2 *pilots, float2 *xhat, uint8_t *bits, uint32_t *status,
+                                      cudaStream_t st);
+
+}  // namespace pusch

@@ -82,11 +82,9 @@ extern "C" pusch_status pusch_slot_noalloc(const pusch_cell_cfg *cfg, int n_slot
     if (!time_in || !W || !pilots || !x_hat || !bits) return na_fail(PUSCH_ERR_ARG, "pusch_slot_noalloc: NULL buffer");
 
     const pusch::Geometry g = pusch::make_geometry(*cfg);
-    const size_t rows = (size_t)n_slots * g.n_sym * g.n_rx;
     const size_t tw_b = up256((size_t)g.n_fft * sizeof(float2));
     const size_t words_b = 256;  // status sink (16 B) + tensor-core timeout word (16 B)
-    const size_t freq_b = up256(g.form == PUSCH_FORM_MIXED ? rows * 2 * g.sc_pitch * sizeof(__half)
-                                                           : rows * g.n_sc * sizeof(float2));
+    const size_t freq_b = up256(pusch::freq_bytes_of(g, n_slots));
     const size_t beam_b = up256((size_t)n_slots * g.n_sym * g.n_sc * g.n_beams * sizeof(float2));
     const size_t H_b = up256((size_t)n_slots * g.n_sc * g.n_layers * g.n_beams * sizeof(float2));
     const size_t need = tw_b + words_b + freq_b + beam_b + H_b;
@@ -116,12 +114,7 @@ extern "C" pusch_status pusch_slot_noalloc(const pusch_cell_cfg *cfg, int n_slot
     if (e != cudaSuccess) return na_fail(PUSCH_ERR_CUDA, "pusch_slot_noalloc set-up launch", e);
     if ((e = pusch::launch_fft(g, n_slots, time_in, freq, tw, tc_err, s)) != cudaSuccess)
         return na_fail(PUSCH_ERR_CUDA, "pusch_slot_noalloc fft launch", e);
-    if (g.form == PUSCH_FORM_MIXED)
-        e = pusch::launch_beamform_tc(g, n_slots, static_cast<const __half *>(freq), static_cast<const float2 *>(W),
-                                      beam, tc_err, s);
-    else
-        e = pusch::launch_beamform_fp32(g, n_slots, static_cast<const float2 *>(freq), static_cast<const float2 *>(W),
-                                        beam, s);
+    e = pusch::launch_beamform(g, n_slots, freq, static_cast<const float2 *>(W), beam, tc_err, s);
     if (e != cudaSuccess) return na_fail(PUSCH_ERR_CUDA, "pusch_slot_noalloc beamforming launch", e);
     if ((e = pusch::launch_chest_ls(g, n_slots, beam, static_cast<const float2 *>(pilots), H, s)) != cudaSuccess)
         return na_fail(PUSCH_ERR_CUDA, "pusch_slot_noalloc channel estimation launch", e);

@@ -63,6 +63,8 @@ class Receiver:
     # --- buffer factories (layouts of include/pusch.h, leading [n_slots])
     def freq_buffer(self, n):
         c = self.cfg
+        if c.form == B.PUSCH_FORM_FP8:   # E4M3 planes + block scales, one byte buffer (include/pusch.h)
+            return torch.empty(B.pusch_freq_bytes(c, n), dtype=torch.uint8, device=self.device)
         if c.form == B.PUSCH_FORM_MIXED:
             return torch.empty((n, c.n_sym, c.n_rx, 2, self.pitch), dtype=torch.float16, device=self.device)
         return torch.empty((n, c.n_sym, c.n_rx, c.n_sc), dtype=torch.complex64, device=self.device)
@@ -95,8 +97,17 @@ class Receiver:
         B.pusch_ofdm_fft(self.h, n, time_in, freq, stream)
         return freq
 
+    def freq_slots(self, freq) -> int:
+        """Slots held by an FFT output buffer (the FP8 form's byte buffer carries no slot dimension)."""
+        if self.cfg.form != B.PUSCH_FORM_FP8:
+            return freq.shape[0]
+        for n in range(self.max_slots + 1):
+            if B.pusch_freq_bytes(self.cfg, n) == freq.numel():
+                return n
+        raise ValueError("buffer size matches no slot count of this cell's FP8 layout")
+
     def beamform(self, freq, W, beam=None, stream=None):
-        n = freq.shape[0]
+        n = self.freq_slots(freq)
         beam = self.beam_buffer(n) if beam is None else beam
         B.pusch_beamform(self.h, n, freq, W, beam, stream)
         return beam

@@ -43,7 +43,9 @@ MIXED_SHAPES = [
     dict(n_rx=16, n_fft=512, n_sc=300, n_beams=16, n_layers=4, qam_bits=2),
     dict(n_rx=32, n_fft=1024, n_sc=1000, n_beams=24, n_layers=8, qam_bits=4),
     dict(n_rx=64, n_fft=4096, n_sc=3276, n_beams=32, n_layers=16, qam_bits=4),
+    dict(n_rx=72, n_fft=1024, n_sc=900, n_beams=16, n_layers=8, qam_bits=4),       # partial last K chunk
     dict(n_rx=128, n_fft=2048, n_sc=1638, n_beams=64, n_layers=32, qam_bits=4),
+    dict(n_rx=256, n_fft=4096, n_sc=3276, n_beams=64, n_layers=32, qam_bits=4),    # K = 512 in 8 chunks
 ]
 
 
