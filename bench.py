@@ -33,7 +33,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--slots", type=int, default=16)
-    ap.add_argument("--form", default="auto", choices=["auto", "mixed", "fp32"])
+    ap.add_argument("--form", default="auto", choices=["auto", "mixed", "fp32", "fp8"])
+    ap.add_argument("--workload", default="deploy", choices=["deploy", "massive"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-ragged", action="store_true")
@@ -123,9 +124,9 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------------------- workload
-def workload(n_slots):
+def workload(n_slots, name="deploy"):
     from paper_2210_09196_gb300 import synth
-    cell = synth.DEPLOY
+    cell = synth.DEPLOY if name == "deploy" else synth.MASSIVE
     slots = synth.make_slots(cell, n_slots)
     return cell, slots
 
@@ -209,7 +210,7 @@ def run_ours(args, rank, world, local):
     from paper_2210_09196_gb300 import host
 
     torch.cuda.set_device(local)
-    cell, slots = workload(args.slots)
+    cell, slots = workload(args.slots, args.workload)
     form = args.form
     if form == "auto":
         cfg_m = host.cfg_for(cell, B.PUSCH_FORM_MIXED)
@@ -224,7 +225,8 @@ def run_ours(args, rank, world, local):
     W = host.beam_tensor(slots[0].W)
 
     def make_rx(f):
-        return host.Receiver(host.cfg_for(cell, B.PUSCH_FORM_MIXED if f == "mixed" else B.PUSCH_FORM_FP32), n)
+        code = {"mixed": B.PUSCH_FORM_MIXED, "fp8": B.PUSCH_FORM_FP8, "fp32": B.PUSCH_FORM_FP32}[f]
+        return host.Receiver(host.cfg_for(cell, code), n)
 
     def timed(rx, steps, warmup):
         """Time `steps` calls of pusch_slot; the handle records per-stage events inside the timed region."""
@@ -260,7 +262,7 @@ def run_ours(args, rank, world, local):
 
     # plain FP32 form beside it (same steps)
     fp32 = None
-    if form == "mixed":
+    if form in ("mixed", "fp8"):
         rx32 = make_rx("fp32")
         t32, st32, _ = timed(rx32, args.steps, args.warmup)
         t32 = max_over_ranks(t32, world)
@@ -331,8 +333,8 @@ def run_ours(args, rank, world, local):
     out = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 4), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "fp16+f32" if form == "mixed" else "f32",
-        "data": "synthetic (seeded generator: 16-tap exponential PDP channel, 16-QAM, 30 dB)",
+        "scaling": "weak", "vs_baseline": None, "dtype": {"mixed": "fp16+f32", "fp8": "e4m3+f32", "fp32": "f32"}[form],
+        "data": f"synthetic (seeded generator: 16-tap exponential PDP channel, 16-QAM, {cell.snr_db:g} dB)",
         "config": {"workload": cell.name, "form": form, "slots_per_step": n, "n_rx": cell.n_rx,
                    "n_fft": cell.n_fft, "n_sc": cell.n_sc, "n_beams": cell.n_beams, "n_layers": cell.n_layers,
                    "time_input": "complex fp16",
@@ -475,7 +477,7 @@ def cpu_baseline(slots, budget_s):
     dt = time.perf_counter() - t0
     done = len(outs)
     return ({"value": round(done / dt, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
-             "sample": f"{done} whole deployment slots through the FP64 C oracle (single thread), {dt:.1f} s"},
+             "sample": f"{done} whole slots of {slots[0].cfg.name} through the FP64 C oracle (single thread), {dt:.1f} s"},
             outs)
 
 

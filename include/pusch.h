@@ -184,8 +184,10 @@ pusch_status pusch_slot_host(pusch_handle *h, int n_slots, const void *time_in_h
 
 /* ------------------------------------------------------------------------------------------------------
  * Learned channel-estimate denoiser (an addition to the paper's LS estimator, which stays the fallback).
- * A 4-layer CNN of 3x3 same-padded convolutions 2 -> 32 -> 32 -> 32 -> 2 with ReLU after the first three and
- * the input added to the output, run on grids [n][2 channels (re, im)][2 DMRS symbols][w subcarriers].
+ * A 4-layer CNN of 3x3 zero-padded ("same") convolutions 2 -> 32 -> 32 -> 32 -> 2, dilated along the
+ * subcarrier axis by 1, 8, 16 and 1 (tap offsets d * {-1, 0, 1}; the 2-row DMRS axis is not dilated), with
+ * ReLU after the first three and the input added to the output, run on grids
+ * [n][2 channels (re, im)][2 DMRS symbols][w subcarriers].
  * Parameters (pusch_cnn_param_count() = 19682) are packed per layer as W[co][ci][3][3] then b[co]; weights
  * and activations are bfloat16, arithmetic and gradients FP32. All pointers are device pointers.
  */
