@@ -359,7 +359,8 @@ def run_ours(args, rank, world, local):
 
 def run_ragged(world, reps=50):
     """Ragged multi-cell slot (8 cells of 32/64 antennas and 2048/4096-point FFTs, 64 users on random PRB
-    ranges with 1-4 layers) through pusch_batch_run: one graph launch per slot, L2 flushed before each."""
+    ranges with 1-4 layers) through pusch_batch_run: one graph launch per slot, L2 flushed before each;
+    timed with the default launch shapes and again after pusch_batch_autotune."""
     import torch
     from paper_2210_09196_gb300 import binding as B
     from paper_2210_09196_gb300 import host, synth
@@ -369,22 +370,32 @@ def run_ragged(world, reps=50):
     out = rx.outputs()
     flush = torch.empty(256 * 2**20, dtype=torch.uint8, device="cuda")
     st = torch.cuda.current_stream()
-    for _ in range(5):
-        rx.run(t, w, p, out, st)
-    torch.cuda.synchronize()
-    total = 0.0
-    for _ in range(reps):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(st)
-        rx.run(t, w, p, out, st)
-        e1.record(st)
+
+    def timed():
+        for _ in range(5):
+            rx.run(t, w, p, out, st)
         torch.cuda.synchronize()
-        total += e0.elapsed_time(e1)
-    ms = max_over_ranks(total / reps, world)
+        total = 0.0
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            rx.run(t, w, p, out, st)
+            e1.record(st)
+            torch.cuda.synchronize()
+            total += e0.elapsed_time(e1)
+        return max_over_ranks(total / reps, world)
+
+    ms_default = timed()
+    t0 = time.perf_counter()
+    n_timed = rx.autotune(t, w, p, out, cache_path=None, stream=st)
+    tune_s = time.perf_counter() - t0
+    ms = timed()
     res = {"value": round(world * 1e3 / ms, 1), "unit": "slots/s", "ms_per_slot": round(ms, 4), "cells": len(rs.cells),
            "users": len(rs.users), "layers": sum(u.n_layers for u in rs.users), "form": "mixed",
            "launch": "one CUDA graph per slot", "l2": "flushed before every slot",
+           "default_shapes_ms_per_slot": round(ms_default, 4),
+           "autotune": {"keys_timed": n_timed, "seconds": round(tune_s, 2), "choice": rx.tuning()},
            "device_status": [int(v) & 0xffffffff for v in out[2].cpu().numpy()]}
     rx.close()
     return res

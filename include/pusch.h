@@ -272,6 +272,27 @@ pusch_status pusch_batch_sizes(const pusch_batch *b, size_t sizes[5]);
 pusch_status pusch_batch_run(pusch_batch *b, const void *time_in, const void *W, const void *pilots, void *x_hat,
                              uint8_t *bits, uint32_t *status, void *stream);
 
+/* Autotuning of the batch's launch shapes (arguments as pusch_batch_run; the buffers must hold a valid
+ * slot, whose outputs are overwritten). For each key not found in the cache file it times the candidates on
+ * `stream` (synchronising it) and keeps the fastest:
+ *   "bf form=F n_rx=R n_beams=B n_sc=S"   tensor-core GEMM: K rows per pipeline stage, staged TMA-store
+ *                                         output or direct stores (every shape that fits shared memory);
+ *   "det form=F class=NL nbmax=B n_data=D" detector of a layer class: 1, 2 or 4 warps per CTA x CTAs per SM
+ *                                         (occupancy limit, 1 or 2);
+ *   "graph form=F n_cells=C"              parallel graph branches for the cells' chains: 1, 2, 4 or 8.
+ * cache_path may be NULL (nothing read or written); otherwise its lines "<key> | <choice>" are read and the
+ * newly timed keys appended. *n_timed (if not NULL) receives the number of keys that were timed. The next
+ * pusch_batch_run re-captures its graph with the chosen shapes. Shapes change the order of floating-point
+ * accumulation only. */
+pusch_status pusch_batch_autotune(pusch_batch *b, const void *time_in, const void *W, const void *pilots,
+                                  void *x_hat, uint8_t *bits, uint32_t *status, const char *cache_path, void *stream,
+                                  int *n_timed);
+
+/* The batch's current launch shapes: out[0] = graph branches; out[1 + 2c], out[2 + 2c] = warps per CTA and
+ * CTA-per-SM cap of layer class c (NL = 2 << c, 0 = occupancy limit); then per cell (chunk rows, staged)
+ * of the tensor-core GEMM (0 = chosen by the kernel), as far as n_out allows (n_out >= 11). */
+pusch_status pusch_batch_tuning(const pusch_batch *b, int *out, int n_out);
+
 /*
  * pusch_slot for callers that cannot allocate device memory.
  * The paper has no counterpart of this entry point; it exists for integration. Some callers must not call

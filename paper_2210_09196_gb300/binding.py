@@ -36,7 +36,8 @@ EXPORTS = (
     "pusch_beamform",
     "pusch_chest_ls", "pusch_mmse_detect", "pusch_slot", "pusch_slot_host", "pusch_last_error", "pusch_version",
     "pusch_slot_noalloc", "pusch_profile_start", "pusch_profile_read",
-    "pusch_batch_create", "pusch_batch_destroy", "pusch_batch_sizes", "pusch_batch_run",
+    "pusch_batch_create", "pusch_batch_destroy", "pusch_batch_sizes", "pusch_batch_run", "pusch_batch_autotune",
+    "pusch_batch_tuning",
     "pusch_cnn_param_count", "pusch_cnn_forward", "pusch_cnn_backward", "pusch_cnn_adam", "pusch_ls_grid",
     "pusch_chest_cnn",
 )
@@ -106,6 +107,8 @@ def lib():
             "pusch_batch_destroy": (I, [P]),
             "pusch_batch_sizes": (I, [P, ctypes.POINTER(ctypes.c_size_t)]),
             "pusch_batch_run": (I, [P, P, P, P, P, P, P, P]),
+            "pusch_batch_autotune": (I, [P, P, P, P, P, P, P, ctypes.c_char_p, P, ctypes.POINTER(I)]),
+            "pusch_batch_tuning": (I, [P, ctypes.POINTER(I), I]),
             "pusch_cnn_param_count": (I, []),
             "pusch_cnn_forward": (I, [I, I, P, P, P, P, P]),
             "pusch_cnn_backward": (I, [I, I, P, P, P, P, P, P, P, P, P, P]),
@@ -252,6 +255,25 @@ def pusch_batch_sizes(b) -> list:
 def pusch_batch_run(b, time_in, W, pilots, x_hat, bits, status=None, stream=None) -> None:
     _check(lib().pusch_batch_run(b, _ptr(time_in), _ptr(W), _ptr(pilots), _ptr(x_hat), _ptr(bits), _ptr(status),
                                  _stream(stream)), "pusch_batch_run")
+
+
+def pusch_batch_autotune(b, time_in, W, pilots, x_hat, bits, status=None, cache_path=None, stream=None) -> int:
+    """Returns the number of keys that were timed (0 when every choice came from the cache)."""
+    n = ctypes.c_int(0)
+    path = None if cache_path is None else str(cache_path).encode()
+    _check(lib().pusch_batch_autotune(b, _ptr(time_in), _ptr(W), _ptr(pilots), _ptr(x_hat), _ptr(bits), _ptr(status),
+                                      path, _stream(stream), ctypes.byref(n)), "pusch_batch_autotune")
+    return n.value
+
+
+def pusch_batch_tuning(b, n_cells: int) -> dict:
+    n = 11 + 2 * n_cells
+    arr = (ctypes.c_int * n)()
+    _check(lib().pusch_batch_tuning(b, arr, n), "pusch_batch_tuning")
+    v = list(arr)
+    return {"branches": v[0],
+            "detector": {2 << c: {"warps": v[1 + 2 * c], "ctas_per_sm": v[2 + 2 * c]} for c in range(5)},
+            "beamform": [{"chunk_rows": v[11 + 2 * c], "staged": v[12 + 2 * c]} for c in range(n_cells)]}
 
 
 def pusch_cnn_param_count() -> int:

@@ -8,13 +8,20 @@
 // subcarrier) the work items (segment, first subcarrier of a group).
 // Device side, captured into one graph: per cell the FFT and beamforming kernels of the single-cell path;
 // one LS-at-pilots kernel over every (user, layer); one persistent detector per layer class whose warps pull
-// work items from an atomic counter (no waits), with the detection core of the single-cell path.
+// work items from an atomic counter (no waits), with the detection core of the single-cell path. The cells'
+// FFT/beamforming chains and the layer classes' detectors run on parallel graph branches.
+//
+// Autotuning (pusch_batch_autotune): the launch shapes are timed on the batch's own buffers and the fastest
+// kept: per distinct cell shape (form, N_R, N_B, N_SC) the tensor-core GEMM's K rows per stage and output
+// path, per layer class the detector's warps per CTA and CTAs per SM, and the number of graph branches.
+// Choices are written to / read from a text cache, one line per key.
 #include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
 #include <map>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "chest_common.cuh"
@@ -25,7 +32,8 @@ namespace {
 using pusch::Geometry;
 
 constexpr int kClasses = 5;        // NL = 2, 4, 8, 16, 32
-constexpr int kDetWarps = 2;
+constexpr int kDetMaxWarps = 4;    // detector CTAs have 1, 2 or 4 warps (a tuned launch shape)
+constexpr int kMaxBranches = 8;
 constexpr int kMaxData = 14;
 
 struct SegLayer {                  // one layer of a segment
@@ -99,7 +107,7 @@ __host__ __device__ __forceinline__ size_t batch_warp_smem(int nbmax, int nd) {
 // Persistent detector for one layer class. Each warp takes work items (segment, first subcarrier of a group
 // of 32/NL subcarriers) from *counter until the list is exhausted.
 template <int NL, int ND>
-__global__ void __launch_bounds__(kDetWarps * 32)
+__global__ void __launch_bounds__(kDetMaxWarps * 32)
 batch_detect_kernel(DetArgs g, int nbmax, const Segment *__restrict__ segs, const SegLayer *__restrict__ layers,
                     const int2 *__restrict__ items, int n_items, int *__restrict__ counter,
                     const float2 *__restrict__ beam, const float2 *__restrict__ ls, float2 *__restrict__ xhat,
@@ -212,33 +220,42 @@ batch_detect_kernel(DetArgs g, int nbmax, const Segment *__restrict__ segs, cons
 template <int NL, int ND>
 cudaError_t launch_detect_nl(const DetArgs &g, int nbmax, const Segment *segs, const SegLayer *layers,
                              const int2 *items, int n_items, int *counter, const float2 *beam, const float2 *ls,
-                             float2 *xhat, uint8_t *bits, uint32_t *status, cudaStream_t st) {
+                             float2 *xhat, uint8_t *bits, uint32_t *status, int warps, int ctas_per_sm,
+                             cudaStream_t st) {
     const int nd = ND > 0 ? ND : g.n_data;
-    const size_t smem = (size_t)kDetWarps * batch_warp_smem<NL>(nbmax, nd);
+    const size_t per_warp = batch_warp_smem<NL>(nbmax, nd);
+    const size_t limit = 227 * 1024;                  // dynamic shared memory a CTA may opt in to
+    const int fit = (int)std::min<size_t>(kDetMaxWarps, limit / per_warp);
+    if (fit < 1) return cudaErrorInvalidValue;
+    if (warps > fit) warps = fit;                     // a shape that does not fit runs with fewer warps
+    const size_t smem = (size_t)warps * per_warp;
     auto k = batch_detect_kernel<NL, ND>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)((size_t)fit * per_warp));
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 152, per_sm = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kDetWarps * 32, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, warps * 32, smem);
     if (per_sm < 1) per_sm = 1;
+    if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
     long long grid = (long long)sms * per_sm;
-    const long long need = ((long long)n_items + kDetWarps - 1) / kDetWarps;
+    const long long need = ((long long)n_items + warps - 1) / warps;
     if (grid > need) grid = need;
-    k<<<(unsigned)grid, kDetWarps * 32, smem, st>>>(g, nbmax, segs, layers, items, n_items, counter, beam, ls, xhat,
-                                                    bits, status);
+    k<<<(unsigned)grid, warps * 32, smem, st>>>(g, nbmax, segs, layers, items, n_items, counter, beam, ls, xhat, bits,
+                                                status);
     return cudaGetLastError();
 }
 
 template <int NL>
 cudaError_t launch_detect(const DetArgs &g, int nbmax, const Segment *segs, const SegLayer *layers,
                           const int2 *items, int n_items, int *counter, const float2 *beam, const float2 *ls,
-                          float2 *xhat, uint8_t *bits, uint32_t *status, cudaStream_t st) {
+                          float2 *xhat, uint8_t *bits, uint32_t *status, int warps, int ctas_per_sm,
+                          cudaStream_t st) {
     if (g.n_data == 12)
         return launch_detect_nl<NL, 12>(g, nbmax, segs, layers, items, n_items, counter, beam, ls, xhat, bits, status,
-                                        st);
-    return launch_detect_nl<NL, 0>(g, nbmax, segs, layers, items, n_items, counter, beam, ls, xhat, bits, status, st);
+                                        warps, ctas_per_sm, st);
+    return launch_detect_nl<NL, 0>(g, nbmax, segs, layers, items, n_items, counter, beam, ls, xhat, bits, status,
+                                   warps, ctas_per_sm, st);
 }
 
 size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -269,6 +286,13 @@ struct pusch_batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     const void *key[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    // launch shapes (defaults until pusch_batch_autotune chooses)
+    std::vector<pusch::TcTune> bf_tune;                      // per cell
+    int det_warps[kClasses] = {2, 2, 2, 2, 2};
+    int det_ctas[kClasses] = {0, 0, 0, 0, 0};                // CTAs per SM cap, 0 = occupancy limit
+    int branches = 4;                                         // parallel graph branches
+    cudaStream_t fork[kMaxBranches] = {};
+    cudaEvent_t ev[2 + kMaxBranches + kClasses] = {};        // fork, LS done, branch joins, detector joins
 };
 
 namespace {
@@ -304,45 +328,149 @@ int class_of(int nl) {
     return c;
 }
 
-// Records the chain on stream s (used under stream capture).
+// Records the chain on stream s (used under stream capture; also run directly by the autotuner). With
+// branches > 1 the cells' FFT/beamforming chains are spread over that many forked streams and the layer
+// classes' detectors over the forked streams, joined back into s by events.
 pusch_status enqueue(pusch_batch *b, const void *time_in, const void *W, const void *pilots, void *x_hat,
-                     uint8_t *bits, uint32_t *status, cudaStream_t s) {
+                     uint8_t *bits, uint32_t *status, cudaStream_t s, int only_class = -1) {
     cudaError_t e;
+    const int nbr = std::max(1, std::min(b->branches, kMaxBranches));
+    auto fail_e = [&](const char *what) { return bcuda(e, what); };
     batch_reset_kernel<<<1, 32, 0, s>>>(b->d_counters, status);
-    if ((e = cudaGetLastError()) != cudaSuccess) return bcuda(e, "batch reset launch");
-    const size_t tsz = b->cells[0].in_fp16 ? 4 : 8;
-    for (size_t c = 0; c < b->cells.size(); ++c) {
-        const Geometry &g = b->geo[c];
-        const void *tin = static_cast<const unsigned char *>(time_in) + (size_t)b->t_off[c] * tsz;
-        if ((e = pusch::launch_fft(g, 1, tin, b->freq + b->f_off[c], b->twiddle[g.n_fft], b->kernel_err, s)) !=
-            cudaSuccess)
-            return bcuda(e, "batch FFT launch");
-    }
-    for (size_t c = 0; c < b->cells.size(); ++c) {
-        const Geometry &g = b->geo[c];
-        const float2 *w = static_cast<const float2 *>(W) + b->w_off[c];
-        e = pusch::launch_beamform(g, 1, b->freq + b->f_off[c], w, b->beam + b->beam_off[c], b->kernel_err, s);
-        if (e != cudaSuccess) return bcuda(e, "batch beamforming launch");
-    }
-    if (b->n_jobs > 0) {
-        batch_ls_kernel<<<b->n_jobs, 256, 0, s>>>(b->d_jobs, b->det, b->beam, static_cast<const float2 *>(pilots),
-                                                  b->ls);
-        if ((e = cudaGetLastError()) != cudaSuccess) return bcuda(e, "batch LS launch");
+    if ((e = cudaGetLastError()) != cudaSuccess) return fail_e("batch reset launch");
+    if (only_class < 0) {
+        const size_t tsz = b->cells[0].in_fp16 ? 4 : 8;
+        if (nbr > 1) {
+            if ((e = cudaEventRecord(b->ev[0], s)) != cudaSuccess) return fail_e("fork record");
+            for (int k = 0; k < nbr; ++k)
+                if ((e = cudaStreamWaitEvent(b->fork[k], b->ev[0], 0)) != cudaSuccess) return fail_e("fork wait");
+        }
+        for (size_t c = 0; c < b->cells.size(); ++c) {
+            const Geometry &g = b->geo[c];
+            cudaStream_t sc = nbr > 1 ? b->fork[c % nbr] : s;
+            const void *tin = static_cast<const unsigned char *>(time_in) + (size_t)b->t_off[c] * tsz;
+            if ((e = pusch::launch_fft(g, 1, tin, b->freq + b->f_off[c], b->twiddle[g.n_fft], b->kernel_err, sc)) !=
+                cudaSuccess)
+                return fail_e("batch FFT launch");
+            const float2 *w = static_cast<const float2 *>(W) + b->w_off[c];
+            e = pusch::launch_beamform(g, 1, b->freq + b->f_off[c], w, b->beam + b->beam_off[c], b->kernel_err, sc,
+                                       &b->bf_tune[c]);
+            if (e != cudaSuccess) return fail_e("batch beamforming launch");
+        }
+        if (nbr > 1)
+            for (int k = 0; k < nbr; ++k) {
+                if ((e = cudaEventRecord(b->ev[2 + k], b->fork[k])) != cudaSuccess) return fail_e("join record");
+                if ((e = cudaStreamWaitEvent(s, b->ev[2 + k], 0)) != cudaSuccess) return fail_e("join wait");
+            }
+        if (b->n_jobs > 0) {
+            batch_ls_kernel<<<b->n_jobs, 256, 0, s>>>(b->d_jobs, b->det, b->beam, static_cast<const float2 *>(pilots),
+                                                      b->ls);
+            if ((e = cudaGetLastError()) != cudaSuccess) return fail_e("batch LS launch");
+        }
     }
     float2 *xh = static_cast<float2 *>(x_hat);
+    int used = 0;
+    const bool fan = nbr > 1 && only_class < 0;
+    if (fan && (e = cudaEventRecord(b->ev[1], s)) != cudaSuccess) return fail_e("detector fork record");
     for (int c = 0; c < kClasses; ++c) {
-        if (b->n_items[c] == 0) continue;
-        int *ctr = b->d_counters + c;
-        switch (c) {
-            case 0: e = launch_detect<2>(b->det, b->nbmax, b->d_segs, b->d_layers, b->d_items[c], b->n_items[c], ctr, b->beam, b->ls, xh, bits, status, s); break;
-            case 1: e = launch_detect<4>(b->det, b->nbmax, b->d_segs, b->d_layers, b->d_items[c], b->n_items[c], ctr, b->beam, b->ls, xh, bits, status, s); break;
-            case 2: e = launch_detect<8>(b->det, b->nbmax, b->d_segs, b->d_layers, b->d_items[c], b->n_items[c], ctr, b->beam, b->ls, xh, bits, status, s); break;
-            case 3: e = launch_detect<16>(b->det, b->nbmax, b->d_segs, b->d_layers, b->d_items[c], b->n_items[c], ctr, b->beam, b->ls, xh, bits, status, s); break;
-            default: e = launch_detect<32>(b->det, b->nbmax, b->d_segs, b->d_layers, b->d_items[c], b->n_items[c], ctr, b->beam, b->ls, xh, bits, status, s); break;
+        if (b->n_items[c] == 0 || (only_class >= 0 && c != only_class)) continue;
+        cudaStream_t sd = s;
+        if (fan) {
+            sd = b->fork[used % nbr];
+            if ((e = cudaStreamWaitEvent(sd, b->ev[1], 0)) != cudaSuccess) return fail_e("detector fork wait");
         }
-        if (e != cudaSuccess) return bcuda(e, "batch detection launch");
+        int *ctr = b->d_counters + c;
+        const int wps = b->det_warps[c], cps = b->det_ctas[c];
+        switch (c) {
+            case 0: e = launch_detect<2>(b->det, b->nbmax, b->d_segs, b->d_layers, b->d_items[c], b->n_items[c], ctr, b->beam, b->ls, xh, bits, status, wps, cps, sd); break;
+            case 1: e = launch_detect<4>(b->det, b->nbmax, b->d_segs, b->d_layers, b->d_items[c], b->n_items[c], ctr, b->beam, b->ls, xh, bits, status, wps, cps, sd); break;
+            case 2: e = launch_detect<8>(b->det, b->nbmax, b->d_segs, b->d_layers, b->d_items[c], b->n_items[c], ctr, b->beam, b->ls, xh, bits, status, wps, cps, sd); break;
+            case 3: e = launch_detect<16>(b->det, b->nbmax, b->d_segs, b->d_layers, b->d_items[c], b->n_items[c], ctr, b->beam, b->ls, xh, bits, status, wps, cps, sd); break;
+            default: e = launch_detect<32>(b->det, b->nbmax, b->d_segs, b->d_layers, b->d_items[c], b->n_items[c], ctr, b->beam, b->ls, xh, bits, status, wps, cps, sd); break;
+        }
+        if (e != cudaSuccess) return fail_e("batch detection launch");
+        if (fan) {
+            if ((e = cudaEventRecord(b->ev[2 + kMaxBranches + c], sd)) != cudaSuccess) return fail_e("detector join record");
+            if ((e = cudaStreamWaitEvent(s, b->ev[2 + kMaxBranches + c], 0)) != cudaSuccess) return fail_e("detector join wait");
+        }
+        ++used;
     }
     return PUSCH_OK;
+}
+
+void drop_graph(pusch_batch *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    memset(b->key, 0, sizeof b->key);
+}
+
+// ---------------------------------------------------------------------------------------- autotuning
+
+std::string bf_key(const Geometry &g) {
+    char buf[128];
+    snprintf(buf, sizeof buf, "bf form=%d n_rx=%d n_beams=%d n_sc=%d", g.form, g.n_rx, g.n_beams, g.n_sc);
+    return buf;
+}
+std::string det_key(const pusch_batch *b, int c) {
+    char buf[128];
+    snprintf(buf, sizeof buf, "det form=%d class=%d nbmax=%d n_data=%d", b->geo[0].form, 2 << c, b->nbmax,
+             b->det.n_data);
+    return buf;
+}
+std::string graph_key(const pusch_batch *b) {
+    char buf[128];
+    snprintf(buf, sizeof buf, "graph form=%d n_cells=%d", b->geo[0].form, (int)b->cells.size());
+    return buf;
+}
+
+// Cache file: one "<key> | <value>" line per tuned item; later lines override earlier ones.
+std::map<std::string, std::string> read_cache(const char *path) {
+    std::map<std::string, std::string> m;
+    if (!path) return m;
+    FILE *f = fopen(path, "r");
+    if (!f) return m;
+    char line[512];
+    while (fgets(line, sizeof line, f)) {
+        std::string l(line);
+        while (!l.empty() && (l.back() == '\n' || l.back() == '\r')) l.pop_back();
+        const size_t bar = l.find(" | ");
+        if (l.empty() || l[0] == '#' || bar == std::string::npos) continue;
+        m[l.substr(0, bar)] = l.substr(bar + 3);
+    }
+    fclose(f);
+    return m;
+}
+
+int value_of(const std::string &v, const char *name, int dflt) {
+    const std::string pat = std::string(name) + "=";
+    const size_t p = v.find(pat);
+    if (p == std::string::npos) return dflt;
+    return atoi(v.c_str() + p + pat.size());
+}
+
+// Mean milliseconds of `reps` runs of f on stream s (after one warm-up run).
+template <typename F>
+float time_ms(cudaStream_t s, int reps, F &&f, cudaError_t *err) {
+    cudaEvent_t e0, e1;
+    *err = cudaEventCreate(&e0);
+    if (*err != cudaSuccess) return 0.f;
+    if ((*err = cudaEventCreate(&e1)) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return 0.f;
+    }
+    f();
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < reps; ++r) f();
+    cudaEventRecord(e1, s);
+    *err = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (*err == cudaSuccess) *err = cudaEventElapsedTime(&ms, e0, e1);
+    if (*err == cudaSuccess) *err = cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return ms / reps;
 }
 
 }  // namespace
@@ -355,6 +483,10 @@ pusch_status pusch_batch_destroy(pusch_batch *b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->cap) cudaStreamDestroy(b->cap);
+    for (int k = 0; k < kMaxBranches; ++k)
+        if (b->fork[k]) cudaStreamDestroy(b->fork[k]);
+    for (auto &ev : b->ev)
+        if (ev) cudaEventDestroy(ev);
     for (auto &kv : b->twiddle) cudaFree(kv.second);
     cudaFree(b->freq);
     cudaFree(b->beam);
@@ -569,6 +701,12 @@ pusch_status pusch_batch_create(pusch_batch **out, const pusch_cell_cfg *cells, 
         b->twiddle[N] = d;
     }
     if ((e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking)) != cudaSuccess) goto cuda_error;
+    for (int k = 0; k < kMaxBranches; ++k)
+        if ((e = cudaStreamCreateWithFlags(&b->fork[k], cudaStreamNonBlocking)) != cudaSuccess) goto cuda_error;
+    for (auto &ev : b->ev)
+        if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) goto cuda_error;
+    b->bf_tune.assign(n_cells, pusch::TcTune{});
+    b->branches = std::min(4, n_cells);
     (void)c0;
     *out = b;
     pusch::set_last_error("");
@@ -592,14 +730,7 @@ pusch_status pusch_batch_run(pusch_batch *b, const void *time_in, const void *W,
     const void *key[6] = {time_in, W, pilots, x_hat, bits, stat};
     cudaError_t e;
     if (!b->exec || memcmp(key, b->key, sizeof key) != 0) {
-        if (b->exec) {
-            cudaGraphExecDestroy(b->exec);
-            b->exec = nullptr;
-        }
-        if (b->graph) {
-            cudaGraphDestroy(b->graph);
-            b->graph = nullptr;
-        }
+        drop_graph(b);
         if ((e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
             return bcuda(e, "graph capture begin");
         pusch_status st = enqueue(b, time_in, W, pilots, x_hat, bits, stat, b->cap);
@@ -616,6 +747,149 @@ pusch_status pusch_batch_run(pusch_batch *b, const void *time_in, const void *W,
     }
     if ((e = cudaGraphLaunch(b->exec, (cudaStream_t)stream)) != cudaSuccess) return bcuda(e, "graph launch");
     pusch::set_last_error("");
+    return PUSCH_OK;
+}
+
+pusch_status pusch_batch_autotune(pusch_batch *b, const void *time_in, const void *W, const void *pilots,
+                                  void *x_hat, uint8_t *bits, uint32_t *status, const char *cache_path, void *stream,
+                                  int *n_timed) {
+    if (!b) return bfail(PUSCH_ERR_ARG, "batch is NULL");
+    if (!time_in || !W || !pilots || !x_hat || !bits) return bfail(PUSCH_ERR_ARG, "pusch_batch_autotune: NULL buffer");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint32_t *stat = status ? status : b->status_sink;
+    std::map<std::string, std::string> cache = read_cache(cache_path);
+    std::vector<std::string> lines;
+    int timed = 0;
+    cudaError_t e = cudaSuccess;
+    const int reps = 10;
+    char buf[256];
+    drop_graph(b);
+    // one uncaptured pass: FFT output, beams and the LS table the candidates below read
+    pusch_status st = enqueue(b, time_in, W, pilots, x_hat, bits, stat, s);
+    if (st != PUSCH_OK) return st;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return bcuda(e, "autotune first pass");
+
+    // 1. tensor-core GEMM shape per distinct cell shape
+    std::map<std::string, pusch::TcTune> bf_choice;
+    for (size_t c = 0; c < b->cells.size(); ++c) {
+        const Geometry &g = b->geo[c];
+        if (g.form == PUSCH_FORM_FP32) continue;
+        const std::string k = bf_key(g);
+        if (!bf_choice.count(k)) {
+            pusch::TcTune best;
+            auto it = cache.find(k);
+            if (it != cache.end()) {
+                best.chunk_rows = value_of(it->second, "chunk", 0);
+                best.staged = value_of(it->second, "staged", 0);
+            } else {
+                pusch::TcTune cand[8];
+                const int n = pusch::bf_tc_candidates(g, cand, 8);
+                float best_ms = 1e30f;
+                const float2 *w = static_cast<const float2 *>(W) + b->w_off[c];
+                for (int i = 0; i < n; ++i) {
+                    const float ms = time_ms(s, reps, [&] {
+                        pusch::launch_beamform(g, 1, b->freq + b->f_off[c], w, b->beam + b->beam_off[c],
+                                               b->kernel_err, s, &cand[i]);
+                    }, &e);
+                    if (e != cudaSuccess) return bcuda(e, "autotune beamforming");
+                    if (ms < best_ms) {
+                        best_ms = ms;
+                        best = cand[i];
+                    }
+                }
+                ++timed;
+                snprintf(buf, sizeof buf, "%s | chunk=%d staged=%d ms=%.5f", k.c_str(), best.chunk_rows, best.staged,
+                         best_ms);
+                lines.push_back(buf);
+            }
+            bf_choice[k] = best;
+        }
+        b->bf_tune[c] = bf_choice[k];
+    }
+
+    // 2. detector shape per layer class (the LS table from the first pass stays valid)
+    const int warps_c[3] = {1, 2, 4}, ctas_c[3] = {0, 1, 2};
+    for (int c = 0; c < kClasses; ++c) {
+        if (b->n_items[c] == 0) continue;
+        const std::string k = det_key(b, c);
+        auto it = cache.find(k);
+        if (it != cache.end()) {
+            b->det_warps[c] = value_of(it->second, "warps", 2);
+            b->det_ctas[c] = value_of(it->second, "ctas", 0);
+            continue;
+        }
+        float best_ms = 1e30f;
+        int bw = 2, bc = 0;
+        for (int wi = 0; wi < 3; ++wi)
+            for (int ci = 0; ci < 3; ++ci) {
+                b->det_warps[c] = warps_c[wi];
+                b->det_ctas[c] = ctas_c[ci];
+                const float ms = time_ms(s, reps, [&] { enqueue(b, time_in, W, pilots, x_hat, bits, stat, s, c); }, &e);
+                if (e != cudaSuccess) return bcuda(e, "autotune detection");
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    bw = warps_c[wi];
+                    bc = ctas_c[ci];
+                }
+            }
+        b->det_warps[c] = bw;
+        b->det_ctas[c] = bc;
+        ++timed;
+        snprintf(buf, sizeof buf, "%s | warps=%d ctas=%d ms=%.5f", k.c_str(), bw, bc, best_ms);
+        lines.push_back(buf);
+    }
+
+    // 3. graph branches, timed as whole captured graphs
+    {
+        const std::string k = graph_key(b);
+        auto it = cache.find(k);
+        if (it != cache.end()) {
+            b->branches = std::max(1, std::min(kMaxBranches, value_of(it->second, "branches", 4)));
+        } else {
+            float best_ms = 1e30f;
+            int best_k = 1;
+            for (int nbr = 1; nbr <= kMaxBranches && nbr <= (int)b->cells.size(); nbr *= 2) {
+                b->branches = nbr;
+                drop_graph(b);
+                st = pusch_batch_run(b, time_in, W, pilots, x_hat, bits, status, stream);
+                if (st != PUSCH_OK) return st;
+                const float ms = time_ms(s, reps, [&] { cudaGraphLaunch(b->exec, s); }, &e);
+                if (e != cudaSuccess) return bcuda(e, "autotune graph");
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best_k = nbr;
+                }
+            }
+            b->branches = best_k;
+            ++timed;
+            snprintf(buf, sizeof buf, "%s | branches=%d ms=%.5f", k.c_str(), best_k, best_ms);
+            lines.push_back(buf);
+        }
+    }
+    drop_graph(b);
+    if (cache_path && !lines.empty()) {
+        FILE *f = fopen(cache_path, "a");
+        if (!f) return bfail(PUSCH_ERR_ARG, "cannot append to the autotune cache file");
+        for (const auto &l : lines) fprintf(f, "%s\n", l.c_str());
+        fclose(f);
+    }
+    if (n_timed) *n_timed = timed;
+    pusch::set_last_error("");
+    return PUSCH_OK;
+}
+
+pusch_status pusch_batch_tuning(const pusch_batch *b, int *out, int n_out) {
+    if (!b || !out || n_out < 1 + 2 * kClasses) return bfail(PUSCH_ERR_ARG, "pusch_batch_tuning: bad arguments");
+    out[0] = b->branches;
+    for (int c = 0; c < kClasses; ++c) {
+        out[1 + 2 * c] = b->det_warps[c];
+        out[2 + 2 * c] = b->det_ctas[c];
+    }
+    int k = 1 + 2 * kClasses;
+    for (size_t c = 0; c < b->cells.size() && k + 1 < n_out; ++c, k += 2) {
+        out[k] = b->bf_tune[c].chunk_rows;
+        out[k + 1] = b->bf_tune[c].staged;
+    }
     return PUSCH_OK;
 }
 

@@ -652,10 +652,10 @@ struct Plan {
 };
 
 // Launch plan for a geometry: chunk size, stage count and whether the output is staged for TMA stores, so
-// that B, the output staging, the ring and the static shared state fit in 227 KB. Preference: staged
-// output with >= 3 stages, then direct stores with >= 3 stages, halving the chunk down to 64 rows (2 stages
-// are accepted at 64 rows).
-Plan make_plan(const Geometry &g, bool fp8) {
+// that B, the output staging, the ring and the static shared state fit in 227 KB. Without a tuning:
+// staged output with >= 3 stages, then direct stores with >= 3 stages, halving the chunk down to 64 rows
+// (2 stages are accepted at 64 rows). A tuning (chunk rows, staged) is taken when it fits with >= 2 stages.
+Plan plan_for(const Geometry &g, bool fp8, int rows, int staged) {
     Plan p{};
     const int elem = fp8 ? 1 : 2;
     const int K = 2 * g.n_rx, N = 2 * g.n_beams;
@@ -664,27 +664,33 @@ Plan make_plan(const Geometry &g, bool fp8) {
     int cols = 32;
     while (cols < 2 * N) cols *= 2;
     p.tmem_cols = cols;
-    for (int staged = 1; staged >= 0; --staged) {
-        const size_t out_b = staged ? (size_t)512 * N : 0;
-        for (int rows = fp8 ? 256 : 128; rows >= 64; rows >>= 1) {
-            const int cr = K < rows ? K : rows;
-            const uint32_t sb = (uint32_t)kTileM * elem * cr;
-            const long long avail = (long long)kSmemLimit - (long long)(fixed + out_b);
-            int ns = avail > 0 ? (int)(avail / sb) : 0;
-            if (ns > kMaxStages) ns = kMaxStages;
-            if (ns >= 3 || (!staged && rows == 64 && ns >= 2)) {
-                p.chunk_rows = cr;
-                p.stage_bytes = sb;
-                p.n_stages = ns;
-                p.stage_out = staged;
-                p.n_chunks = (K + cr - 1) / cr;
-                p.smem = 1024 + (size_t)ns * sb + (((size_t)p.b_bytes + 1023) & ~(size_t)1023) + out_b;
-                p.ok = cols <= 256;
-                return p;
-            }
-        }
-    }
+    const size_t out_b = staged ? (size_t)512 * N : 0;
+    const int cr = K < rows ? K : rows;
+    const uint32_t sb = (uint32_t)kTileM * elem * cr;
+    const long long avail = (long long)kSmemLimit - (long long)(fixed + out_b);
+    int ns = avail > 0 ? (int)(avail / sb) : 0;
+    if (ns > kMaxStages) ns = kMaxStages;
+    p.chunk_rows = cr;
+    p.stage_bytes = sb;
+    p.n_stages = ns;
+    p.stage_out = staged;
+    p.n_chunks = (K + cr - 1) / cr;
+    p.smem = 1024 + (size_t)ns * sb + (((size_t)p.b_bytes + 1023) & ~(size_t)1023) + out_b;
+    p.ok = cols <= 256 && ns >= 2;
     return p;
+}
+
+Plan make_plan(const Geometry &g, bool fp8, const TcTune *tune = nullptr) {
+    if (tune && tune->chunk_rows > 0) {
+        const Plan p = plan_for(g, fp8, tune->chunk_rows, tune->staged ? 1 : 0);
+        if (p.ok) return p;
+    }
+    for (int staged = 1; staged >= 0; --staged)
+        for (int rows = fp8 ? 256 : 128; rows >= 64; rows >>= 1) {
+            const Plan p = plan_for(g, fp8, rows, staged);
+            if (p.ok && (p.n_stages >= 3 || (!staged && rows == 64))) return p;
+        }
+    return Plan{};
 }
 
 bool shape_ok(const Geometry &g, bool fp8) {
@@ -699,14 +705,14 @@ bool shape_ok(const Geometry &g, bool fp8) {
 
 template <bool FP8>
 cudaError_t launch_tc(const Geometry &g, int n_slots, const void *freq, const float *scales, const float2 *W,
-                      float2 *beam, uint32_t *err_word, cudaStream_t st) {
+                      float2 *beam, uint32_t *err_word, cudaStream_t st, const TcTune *tune) {
     if (n_slots == 0) return cudaSuccess;
     if (!shape_ok(g, FP8)) return cudaErrorNotSupported;
     if (reinterpret_cast<uintptr_t>(freq) % 16 != 0 || reinterpret_cast<uintptr_t>(beam) % 16 != 0)
         return cudaErrorMisalignedAddress;
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
-    const Plan p = make_plan(g, FP8);
+    const Plan p = make_plan(g, FP8, tune);
     const int K = 2 * g.n_rx;
     const long long rows = (long long)n_slots * g.n_sym;
     const int elem = FP8 ? 1 : 2;
@@ -763,15 +769,33 @@ cudaError_t launch_tc(const Geometry &g, int n_slots, const void *freq, const fl
 bool bf_tc_supported(const Geometry &g) { return shape_ok(g, false); }
 bool bf_fp8_supported(const Geometry &g) { return shape_ok(g, true); }
 
+int bf_tc_candidates(const Geometry &g, TcTune *out, int max_out) {
+    const bool fp8 = g.form == PUSCH_FORM_FP8;
+    if (g.form == PUSCH_FORM_FP32 || !shape_ok(g, fp8)) return 0;
+    int n = 0, last_cr = -1, last_st = -1;
+    for (int staged = 1; staged >= 0; --staged)
+        for (int rows = fp8 ? 256 : 128; rows >= 64; rows >>= 1) {
+            const Plan p = plan_for(g, fp8, rows, staged);
+            if (!p.ok || (p.chunk_rows == last_cr && staged == last_st) || n >= max_out) continue;
+            out[n].chunk_rows = p.chunk_rows;
+            out[n].staged = staged;
+            last_cr = p.chunk_rows;
+            last_st = staged;
+            ++n;
+        }
+    return n;
+}
+
 cudaError_t launch_beamform_tc(const Geometry &g, int n_slots, const __half *freq16, const float2 *W, float2 *beam,
-                               uint32_t *err_word, cudaStream_t st) {
-    return launch_tc<false>(g, n_slots, freq16, nullptr, W, beam, err_word, st);
+                               uint32_t *err_word, cudaStream_t st, const TcTune *tune) {
+    return launch_tc<false>(g, n_slots, freq16, nullptr, W, beam, err_word, st, tune);
 }
 
 cudaError_t launch_beamform_fp8(const Geometry &g, int n_slots, const uint8_t *freq8, const float *scales,
-                                const float2 *W, float2 *beam, uint32_t *err_word, cudaStream_t st) {
+                                const float2 *W, float2 *beam, uint32_t *err_word, cudaStream_t st,
+                                const TcTune *tune) {
     if (reinterpret_cast<uintptr_t>(scales) % 16 != 0) return cudaErrorMisalignedAddress;
-    return launch_tc<true>(g, n_slots, freq8, scales, W, beam, err_word, st);
+    return launch_tc<true>(g, n_slots, freq8, scales, W, beam, err_word, st, tune);
 }
 
 }  // namespace pusch

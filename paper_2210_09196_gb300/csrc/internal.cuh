@@ -94,23 +94,34 @@ cudaError_t launch_ls_pilots(const Geometry &g, int n_slots, const float2 *beam,
 cudaError_t launch_mmse_fused(const Geometry &g, int n_slots, const float2 *beam, const float2 *ls,
                               float2 *x_hat, uint8_t *bits, uint32_t *status, cudaStream_t st);
 
+// Launch shape of the tensor-core beamforming kernel: K rows per pipeline stage and whether the epilogue
+// writes through shared memory and TMA stores. chunk_rows = 0 lets the kernel choose from its shared-memory
+// budget; a shape that does not fit falls back to that choice.
+struct TcTune {
+    int chunk_rows = 0;
+    int staged = 0;
+};
+// The feasible shapes for g's form (tensor-core forms only); returns how many were written (<= max_out).
+int bf_tc_candidates(const Geometry &g, TcTune *out, int max_out);
+
 // Mixed form: the tcgen05 beamforming GEMM. err_word (device, one uint32) gets bit 0 set if a bounded
 // wait of the kernel expired.
 cudaError_t launch_beamform_tc(const Geometry &g, int n_slots, const __half *freq16, const float2 *W, float2 *beam,
-                               uint32_t *err_word, cudaStream_t st);
+                               uint32_t *err_word, cudaStream_t st, const TcTune *tune = nullptr);
 bool bf_tc_supported(const Geometry &g);
 // FP8 form: E4M3 codes with power-of-two block scales (layout of freq_bytes_of), same kernel family.
 cudaError_t launch_beamform_fp8(const Geometry &g, int n_slots, const uint8_t *freq8, const float *scales,
-                                const float2 *W, float2 *beam, uint32_t *err_word, cudaStream_t st);
+                                const float2 *W, float2 *beam, uint32_t *err_word, cudaStream_t st,
+                                const TcTune *tune = nullptr);
 bool bf_fp8_supported(const Geometry &g);
 // Beamforming of the FFT output in the geometry's form (FP32 SIMT, FP16 or FP8 tensor cores).
 inline cudaError_t launch_beamform(const Geometry &g, int n_slots, const void *freq, const float2 *W, float2 *beam,
-                                   uint32_t *err_word, cudaStream_t st) {
+                                   uint32_t *err_word, cudaStream_t st, const TcTune *tune = nullptr) {
     if (g.form == PUSCH_FORM_MIXED)
-        return launch_beamform_tc(g, n_slots, static_cast<const __half *>(freq), W, beam, err_word, st);
+        return launch_beamform_tc(g, n_slots, static_cast<const __half *>(freq), W, beam, err_word, st, tune);
     if (g.form == PUSCH_FORM_FP8)
         return launch_beamform_fp8(g, n_slots, static_cast<const uint8_t *>(freq),
-                                   fp8_scales(g, n_slots, const_cast<void *>(freq)), W, beam, err_word, st);
+                                   fp8_scales(g, n_slots, const_cast<void *>(freq)), W, beam, err_word, st, tune);
     return launch_beamform_fp32(g, n_slots, static_cast<const float2 *>(freq), W, beam, st);
 }
 

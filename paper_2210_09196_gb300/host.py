@@ -181,6 +181,13 @@ class RaggedReceiver:
         B.pusch_batch_run(self.h, t, w, p, *out, stream=stream)
         return out
 
+    def autotune(self, t, w, p, out, cache_path=None, stream=None) -> int:
+        """Times the batch's launch shapes on these buffers (or loads them from cache_path)."""
+        return B.pusch_batch_autotune(self.h, t, w, p, *out, cache_path=cache_path, stream=stream)
+
+    def tuning(self) -> dict:
+        return B.pusch_batch_tuning(self.h, len(self.cells))
+
     def split(self, flat, rs):
         """Per-user [n_layers, 12, sc_count] views of a packed output."""
         res, o = [], 0

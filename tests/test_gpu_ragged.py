@@ -154,3 +154,32 @@ def test_ragged_invalid_descriptors_rejected():
         with pytest.raises(B.PuschError) as ei:
             make(users)
         assert ei.value.code == B.PUSCH_ERR_ARG
+
+
+def test_ragged_autotune_keeps_results_and_reuses_its_cache(orc, ragged, ragged_ref, tmp_path):
+    """The autotuner times launch shapes on the batch's own buffers, writes its choices, and a second batch
+    with the same shapes takes every choice from the cache; results stay within the oracle's bar."""
+    rs0 = ragged[0]
+    cache = tmp_path / "pusch_tune.txt"
+    rx = host.RaggedReceiver(rs0, B.PUSCH_FORM_MIXED)
+    out = rx.outputs()
+    t, w, p = rx.pack(rs0)
+    n_timed = rx.autotune(t, w, p, out, cache_path=cache)
+    assert n_timed >= 3 and cache.exists()
+    lines = [l for l in cache.read_text().splitlines() if l.strip()]
+    assert len(lines) == n_timed and any(l.startswith("graph ") for l in lines)
+    tun = rx.tuning()
+    assert tun["branches"] in (1, 2, 4, 8)
+    rx.run(t, w, p, out)
+    torch.cuda.synchronize()
+    assert list(out[2].cpu().numpy()) == [0, 0, -1, 0]
+    check_users(rs0, rx.split(out[0], rs0), rx.split(out[1], rs0), ragged_ref[0], -40.0)
+    rx2 = host.RaggedReceiver(rs0, B.PUSCH_FORM_MIXED)
+    out2 = rx2.outputs()
+    assert rx2.autotune(t, w, p, out2, cache_path=cache) == 0
+    assert rx2.tuning() == tun
+    rx2.run(t, w, p, out2)
+    torch.cuda.synchronize()
+    assert torch.equal(out2[0], out[0])
+    rx.close()
+    rx2.close()
