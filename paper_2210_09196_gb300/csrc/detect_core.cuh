@@ -69,54 +69,83 @@ __device__ __forceinline__ bool detect_group(const float2 *__restrict__ hr, cons
                                              const float2 *__restrict__ yt, float2 *lt, int hs, int nb, int nd,
                                              int nl, float load, int i, int src0, float2 (&acc)[NR]) {
     constexpr unsigned kFull = kDetFull;
-    // ---- 2a. Gram row i: G[j] = sum_b conj(H[i][b]) H[j][b]
+    // ---- 2a. Gram row i: G[j] = sum_b conj(H[i][b]) H[j][b], with packed FP32x2 FMAs: P[j] = sum_b Re(h_b) H[j][b]
+    //         and Q[j] = sum_b Im(h_b) H[j][b] (h_b = H[i][b]), then G[j] = P[j] - i Q[j].
     float2 G[NL];
+    {
+        float2 P[NL], Q[NL];
 #pragma unroll
-    for (int j = 0; j < NL; ++j) G[j] = make_float2(0.f, 0.f);
-    int b = 0;
-    for (; b + 1 < nb; b += 2) {
-        const float4 hv = *reinterpret_cast<const float4 *>(hr + b);
-        const float2 h0 = make_float2(hv.x, hv.y), h1 = make_float2(hv.z, hv.w);
+        for (int j = 0; j < NL; ++j) P[j] = Q[j] = make_float2(0.f, 0.f);
+        int b = 0;
+        for (; b + 1 < nb; b += 2) {
+            const float4 hv = *reinterpret_cast<const float4 *>(hr + b);
+            const float2 hx0 = make_float2(hv.x, hv.x), hy0 = make_float2(hv.y, hv.y);
+            const float2 hx1 = make_float2(hv.z, hv.z), hy1 = make_float2(hv.w, hv.w);
 #pragma unroll
-        for (int j = 0; j < NL; ++j) {
-            const float4 gv = *reinterpret_cast<const float4 *>(hg + j * hs + b);
-            cfmac(G[j], h0, make_float2(gv.x, gv.y));
-            cfmac(G[j], h1, make_float2(gv.z, gv.w));
+            for (int j = 0; j < NL; ++j) {
+                const float4 gv = *reinterpret_cast<const float4 *>(hg + j * hs + b);
+                const float2 g0 = make_float2(gv.x, gv.y), g1 = make_float2(gv.z, gv.w);
+                P[j] = __ffma2_rn(hx0, g0, P[j]);
+                Q[j] = __ffma2_rn(hy0, g0, Q[j]);
+                P[j] = __ffma2_rn(hx1, g1, P[j]);
+                Q[j] = __ffma2_rn(hy1, g1, Q[j]);
+            }
         }
-    }
-    if (b < nb) {
-        const float2 h0 = hr[b];
+        if (b < nb) {
+            const float2 h0 = hr[b];
+            const float2 hx0 = make_float2(h0.x, h0.x), hy0 = make_float2(h0.y, h0.y);
 #pragma unroll
-        for (int j = 0; j < NL; ++j) cfmac(G[j], h0, hg[j * hs + b]);
+            for (int j = 0; j < NL; ++j) {
+                const float2 g0 = hg[j * hs + b];
+                P[j] = __ffma2_rn(hx0, g0, P[j]);
+                Q[j] = __ffma2_rn(hy0, g0, Q[j]);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < NL; ++j) G[j] = make_float2(P[j].x + Q[j].y, P[j].y - Q[j].x);
     }
 #pragma unroll
     for (int j = 0; j < NL; ++j)
         if (j == i) G[j] = (i < nl) ? make_float2(G[j].x + load, 0.f) : make_float2(1.f, 0.f);
 
-    // ---- 2b. right-hand sides r_d = H^H y_d (y_d from the shared tile; a group reads one address)
+    // ---- 2b. right-hand sides r_d = H^H y_d (y_d from the shared tile; a group reads one address), packed the
+    //         same way: P[d] = sum_b Re(h_b) y_d[b], Q[d] = sum_b Im(h_b) y_d[b], r_d[i] = P[d] - i Q[d].
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncwarp();
-#pragma unroll
-    for (int d = 0; d < NR; ++d) acc[d] = make_float2(0.f, 0.f);
     {
-        for (b = 0; b + 1 < nb; b += 2) {
+        float2 Q[NR];
+#pragma unroll
+        for (int d = 0; d < NR; ++d) acc[d] = Q[d] = make_float2(0.f, 0.f);
+        int b = 0;
+        for (; b + 1 < nb; b += 2) {
             const float4 hv = *reinterpret_cast<const float4 *>(hr + b);
-            const float2 h0 = make_float2(hv.x, hv.y), h1 = make_float2(hv.z, hv.w);
+            const float2 hx0 = make_float2(hv.x, hv.x), hy0 = make_float2(hv.y, hv.y);
+            const float2 hx1 = make_float2(hv.z, hv.z), hy1 = make_float2(hv.w, hv.w);
 #pragma unroll
             for (int d = 0; d < NR; ++d) {
                 if (ND > 0 || d < nd) {
                     const float4 yv = *reinterpret_cast<const float4 *>(yt + d * hs + b);
-                    cfmac(acc[d], h0, make_float2(yv.x, yv.y));
-                    cfmac(acc[d], h1, make_float2(yv.z, yv.w));
+                    const float2 y0 = make_float2(yv.x, yv.y), y1 = make_float2(yv.z, yv.w);
+                    acc[d] = __ffma2_rn(hx0, y0, acc[d]);
+                    Q[d] = __ffma2_rn(hy0, y0, Q[d]);
+                    acc[d] = __ffma2_rn(hx1, y1, acc[d]);
+                    Q[d] = __ffma2_rn(hy1, y1, Q[d]);
                 }
             }
         }
         if (b < nb) {
             const float2 h0 = hr[b];
+            const float2 hx0 = make_float2(h0.x, h0.x), hy0 = make_float2(h0.y, h0.y);
 #pragma unroll
             for (int d = 0; d < NR; ++d)
-                if (ND > 0 || d < nd) cfmac(acc[d], h0, yt[d * hs + b]);
+                if (ND > 0 || d < nd) {
+                    const float2 y0 = yt[d * hs + b];
+                    acc[d] = __ffma2_rn(hx0, y0, acc[d]);
+                    Q[d] = __ffma2_rn(hy0, y0, Q[d]);
+                }
         }
+#pragma unroll
+        for (int d = 0; d < NR; ++d) acc[d] = make_float2(acc[d].x + Q[d].y, acc[d].y - Q[d].x);
     }
     __syncwarp();  // the H tile is reused for L below
 
@@ -158,7 +187,9 @@ __device__ __forceinline__ bool detect_group(const float2 *__restrict__ hr, cons
     dv[i] = dinv;
     __syncwarp();
     const float2 *lrow = lt + i * (NL + 1);  // L[i][k]
-#pragma unroll
+    // the k loops stay rolled: their bodies (NR shuffled updates) are large, and unrolling them all made the
+    // kernel miss in the instruction cache
+#pragma unroll 1
     for (int k = 0; k < NL; ++k) {
         const float2 m = cscale(lrow[k], dv[k]);  // L[i][k] / L[k][k]
 #pragma unroll
@@ -171,7 +202,7 @@ __device__ __forceinline__ bool detect_group(const float2 *__restrict__ hr, cons
     }
 #pragma unroll
     for (int d = 0; d < NR; ++d) acc[d] = cscale(acc[d], dinv * dinv);  // z_i / L[i][i]
-#pragma unroll
+#pragma unroll 1
     for (int k = NL - 1; k >= 0; --k) {
         const float2 lki = cscale(lt[k * (NL + 1) + i], dinv);  // L[k][i] / L[i][i]
 #pragma unroll

@@ -36,9 +36,10 @@ struct MmseArgs {
     int port[32];
 };
 
-// Register cap: five 4-warp CTAs per SM up to 8 layers, four for 16 layers (no spills), none for 32.
+// Register cap: five CTAs per SM up to 8 layers, seven for 16 layers (128 registers: the shared-memory
+// limit is also seven), none for 32.
 template <int NL, int ND, bool FUSED>
-__global__ void __launch_bounds__(kMmseWarps * 32, NL <= 8 ? 5 : (NL == 16 ? 4 : 1))
+__global__ void __launch_bounds__(kMmseWarps * 32, NL <= 8 ? 5 : (NL == 16 ? 7 : 1))
 mmse_kernel(MmseArgs g, long long total_sc, const float2 *__restrict__ H, const float2 *__restrict__ beam,
             const float2 *__restrict__ ls, float2 *__restrict__ xhat, uint8_t *__restrict__ bits,
             uint32_t *__restrict__ status) {
