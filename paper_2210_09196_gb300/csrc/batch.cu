@@ -176,16 +176,33 @@ batch_detect_kernel(DetArgs g, int nbmax, const Segment *__restrict__ segs, cons
             rp[lane] = q;
         }
         __syncwarp();
-        for (int idx = lane; idx < SPW * NL * nb; idx += 32) {
-            const int r = idx / nb, b = idx - r * nb;
-            const int gg = r / NL, l = r - gg * NL;
-            const BRow &q = rp[r];
-            float2 h = make_float2(0.f, 0.f);
-            if (q.valid) {
-                h = __ldg(&ls[q.lo + b]);
-                if (q.hi != q.lo) h = pusch::interp(h, __ldg(&ls[q.hi + b]), q.w);
+        // kB elements per lane at a time: their LS-table loads are all issued before any is used
+        constexpr int kB = 8;
+        for (int idx0 = lane; idx0 < SPW * NL * nb; idx0 += 32 * kB) {
+            float2 lo[kB], hi[kB];
+            float w[kB];
+            int off[kB];
+#pragma unroll
+            for (int u = 0; u < kB; ++u) {
+                const int idx = idx0 + 32 * u;
+                off[u] = -1;
+                lo[u] = hi[u] = make_float2(0.f, 0.f);
+                w[u] = 0.f;
+                if (idx < SPW * NL * nb) {
+                    const int r = idx / nb, b = idx - r * nb;
+                    const int gg = r / NL, l = r - gg * NL;
+                    off[u] = gg * ht + l * hs + b;
+                    const BRow &q = rp[r];
+                    if (q.valid) {
+                        lo[u] = __ldg(&ls[q.lo + b]);
+                        hi[u] = q.hi != q.lo ? __ldg(&ls[q.hi + b]) : lo[u];
+                        w[u] = q.w;
+                    }
+                }
             }
-            Ht[gg * ht + l * hs + b] = h;
+#pragma unroll
+            for (int u = 0; u < kB; ++u)
+                if (off[u] >= 0) Ht[off[u]] = pusch::interp(lo[u], hi[u], w[u]);
         }
         __syncwarp();
 

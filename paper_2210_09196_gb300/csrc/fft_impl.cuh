@@ -44,19 +44,25 @@ __device__ __forceinline__ float2 rot16(float2 x) {
     }
 }
 
+// Complex add / subtract as one packed FP32x2 instruction each (the subtraction as b * (-1) + a, which is
+// exact in the product and rounds once, like a - b).
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 psub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+
 __device__ __forceinline__ void dft2(float2 &a, float2 &b) {
     float2 t = a;
-    a = cadd(t, b);
-    b = csub(t, b);
+    a = padd(t, b);
+    b = psub(t, b);
 }
 
 // forward 4-point DFT in place
 __device__ __forceinline__ void dft4(float2 &x0, float2 &x1, float2 &x2, float2 &x3) {
-    float2 a = cadd(x0, x2), b = csub(x0, x2), c = cadd(x1, x3), d = csub(x1, x3);
-    x0 = cadd(a, c);
-    x2 = csub(a, c);
-    x1 = make_float2(b.x + d.y, b.y - d.x);  // b - i d
-    x3 = make_float2(b.x - d.y, b.y + d.x);  // b + i d
+    const float2 a = padd(x0, x2), b = psub(x0, x2), c = padd(x1, x3), d = psub(x1, x3);
+    x0 = padd(a, c);
+    x2 = psub(a, c);
+    const float2 id = make_float2(d.y, -d.x);  // -i d
+    x1 = padd(b, id);                          // b - i d
+    x3 = psub(b, id);                          // b + i d
 }
 
 // Forward R-point DFT of x[0..R) in natural order, R in {2, 4, 8, 16}.
@@ -73,10 +79,10 @@ __device__ __forceinline__ void dft(float2 (&x)[R]) {
         dft4(x[1], x[3], x[5], x[7]);
         float2 a1 = rot16<2>(x[3]), a2 = rot16<4>(x[5]), a3 = rot16<6>(x[7]);
         float2 y[8];
-        y[0] = cadd(x[0], x[1]); y[4] = csub(x[0], x[1]);
-        y[1] = cadd(x[2], a1);   y[5] = csub(x[2], a1);
-        y[2] = cadd(x[4], a2);   y[6] = csub(x[4], a2);
-        y[3] = cadd(x[6], a3);   y[7] = csub(x[6], a3);
+        y[0] = padd(x[0], x[1]); y[4] = psub(x[0], x[1]);
+        y[1] = padd(x[2], a1);   y[5] = psub(x[2], a1);
+        y[2] = padd(x[4], a2);   y[6] = psub(x[4], a2);
+        y[3] = padd(x[6], a3);   y[7] = psub(x[6], a3);
 #pragma unroll
         for (int i = 0; i < 8; ++i) x[i] = y[i];
     } else if constexpr (R == 16) {

@@ -134,23 +134,40 @@ mmse_kernel(MmseArgs g, long long total_sc, const float2 *__restrict__ H, const 
             rp[lane] = q;
         }
         __syncwarp();
+        // kB elements per lane at a time: all their LS-table loads are issued before any is used, so each
+        // lane waits for about rows * nb / (32 kB) round trips to L2 instead of one per element
+        constexpr int kB = 8;
         int r = lane / nb, b = lane - (lane / nb) * nb;
         const int step_r = 32 / nb, step_b = 32 - (32 / nb) * nb;
-        for (; r < rows;) {
-            const int gg = r / NL, l = r - gg * NL;
-            const RowParam &q = rp[r];
-            float2 h = make_float2(0.f, 0.f);
-            if (q.valid) {
-                h = __ldg(&ls[q.lo + b]);
-                if (q.hi != q.lo) h = interp(h, __ldg(&ls[q.hi + b]), q.w);
+        while (r < rows) {
+            float2 lo[kB], hi[kB];
+            float w[kB];
+            int off[kB];
+#pragma unroll
+            for (int u = 0; u < kB; ++u) {
+                off[u] = -1;
+                lo[u] = hi[u] = make_float2(0.f, 0.f);
+                w[u] = 0.f;
+                if (r < rows) {
+                    const int gg = r / NL, l = r - gg * NL;
+                    off[u] = gg * ht + l * hs + b;
+                    const RowParam &q = rp[r];
+                    if (q.valid) {
+                        lo[u] = __ldg(&ls[q.lo + b]);
+                        hi[u] = q.hi != q.lo ? __ldg(&ls[q.hi + b]) : lo[u];
+                        w[u] = q.w;
+                    }
+                }
+                r += step_r;
+                b += step_b;
+                if (b >= nb) {
+                    b -= nb;
+                    ++r;
+                }
             }
-            Ht[gg * ht + l * hs + b] = h;
-            r += step_r;
-            b += step_b;
-            if (b >= nb) {
-                b -= nb;
-                ++r;
-            }
+#pragma unroll
+            for (int u = 0; u < kB; ++u)
+                if (off[u] >= 0) Ht[off[u]] = interp(lo[u], hi[u], w[u]);
         }
     }
     __syncwarp();
