@@ -33,7 +33,6 @@
 // roles leave their loops, in-flight copies and MMAs are drained (bounded) and TMEM is freed.
 #include <cuda.h>
 #include <cudaTypedefs.h>
-#include <cuda_fp8.h>
 #include <float.h>
 
 #include "internal.cuh"
@@ -195,13 +194,26 @@ __device__ __forceinline__ float exp2_int(int e) {
     return e >= 128 ? __uint_as_float(0x7FC00000u) : __uint_as_float((uint32_t)(e + 127) << 23);
 }
 
-// E4M3 helpers (cuda_fp8.h conversions: round to nearest even, saturating to +-448).
+// E4M3 conversions (PTX cvt: round to nearest even, saturating to +-448). A pair's low byte / low half is
+// the first element.
+__device__ __forceinline__ uint32_t h2_from_e4m3x2(uint16_t v) {          // two codes -> f16x2 (exact)
+    uint32_t r;
+    asm("cvt.rn.f16x2.e4m3x2 %0, %1;" : "=r"(r) : "h"(v));
+    return r;
+}
+__device__ __forceinline__ uint16_t e4m3x2_from_h2(uint32_t v) {          // f16x2 -> two codes
+    uint16_t r;
+    asm("cvt.rn.satfinite.e4m3x2.f16x2 %0, %1;" : "=h"(r) : "r"(v));
+    return r;
+}
 __device__ __forceinline__ float2 e4m3x2_to_float2(uint16_t v) {
-    const __half2_raw h = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)v, __NV_E4M3);
+    const uint32_t h = h2_from_e4m3x2(v);
     return __half22float2(*reinterpret_cast<const __half2 *>(&h));
 }
 __device__ __forceinline__ uint16_t float2_to_e4m3x2(float2 v) {
-    return (uint16_t)__nv_cvt_float2_to_fp8x2(v, __NV_SATFINITE, __NV_E4M3);
+    uint16_t r;
+    asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(r) : "f"(v.y), "f"(v.x));
+    return r;
 }
 
 // Smallest e with amax <= 448 * 2^e (the power-of-two E4M3 block scale), clamped below at -126;
@@ -575,43 +587,39 @@ beamform_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_consta
                 // bytes of the swizzled stage and takes one factor 2^-d, so the swizzle does not matter here.
                 // code * 2^-d is exact in binary16 whenever E4M3 can represent it (4 significant bits,
                 // >= 2^-13); smaller values round to E4M3 zero either way; d >= 19 leaves only zeros.
+                // Every unit takes the same path (a warp covers four rows with different shifts, and a
+                // branch on the shift diverged): 2^-0 = 1 leaves a code unchanged, and a shift of 19 or more
+                // (2^-19 is a binary16 subnormal) rounds every code to zero.
                 for (int u0 = w4 * 32 + lane; u0 < rows_here * 8; u0 += 128 * 4) {
                     uint4 v[4];
-                    int dd[4];
+                    __half2 f2[4];
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         const int u = u0 + 128 * q;
-                        dd[q] = u < rows_here * 8 ? sh.shift[w4][(k0 + (u >> 3)) >> 1] : 0;
-                        if (dd[q] != 0) v[q] = *reinterpret_cast<const uint4 *>(stage + (size_t)(u >> 3) * 128 + (u & 7) * 16);
+                        const int d = u < rows_here * 8 ? sh.shift[w4][(k0 + (u >> 3)) >> 1] : 0;
+                        // 2^-d in binary16: normal for d <= 14, subnormal 2^-24 * 2^(24 - d) beyond
+                        __half2_raw fr;
+                        fr.x = fr.y = d <= 14 ? (unsigned short)((15 - d) << 10) : (unsigned short)(1u << (24 - d));
+                        f2[q] = *reinterpret_cast<const __half2 *>(&fr);
+                        if (u < rows_here * 8)
+                            v[q] = *reinterpret_cast<const uint4 *>(stage + (size_t)(u >> 3) * 128 + (u & 7) * 16);
                     }
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        if (dd[q] == 0) continue;
                         const int u = u0 + 128 * q;
-                        uint4 o = make_uint4(0u, 0u, 0u, 0u);
-                        if (dd[q] < 19) {
-                            // 2^-d in binary16: normal for d <= 14, subnormal 2^(10 - 24 + (24 - d)) beyond
-                            const unsigned short hb = dd[q] <= 14 ? (unsigned short)((15 - dd[q]) << 10)
-                                                                  : (unsigned short)(1u << (24 - dd[q]));
-                            __half2_raw fr;
-                            fr.x = hb;
-                            fr.y = hb;
-                            const __half2 f2 = *reinterpret_cast<const __half2 *>(&fr);
-                            uint32_t w[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
+                        if (u >= rows_here * 8) continue;
+                        uint32_t w[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
 #pragma unroll
-                            for (int j = 0; j < 4; ++j) {
-                                __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w[j] & 0xFFFFu), __NV_E4M3);
-                                __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w[j] >> 16), __NV_E4M3);
-                                const __half2 l2 = __hmul2(*reinterpret_cast<const __half2 *>(&lo), f2);
-                                const __half2 h2 = __hmul2(*reinterpret_cast<const __half2 *>(&hi), f2);
-                                w[j] = (uint32_t)__nv_cvt_halfraw2_to_fp8x2(*reinterpret_cast<const __half2_raw *>(&l2),
-                                                                            __NV_SATFINITE, __NV_E4M3) |
-                                       ((uint32_t)__nv_cvt_halfraw2_to_fp8x2(*reinterpret_cast<const __half2_raw *>(&h2),
-                                                                             __NV_SATFINITE, __NV_E4M3) << 16);
-                            }
-                            o = make_uint4(w[0], w[1], w[2], w[3]);
+                        for (int j = 0; j < 4; ++j) {
+                            const uint32_t lo = h2_from_e4m3x2((uint16_t)(w[j] & 0xFFFFu));
+                            const uint32_t hi = h2_from_e4m3x2((uint16_t)(w[j] >> 16));
+                            const __half2 l2 = __hmul2(*reinterpret_cast<const __half2 *>(&lo), f2[q]);
+                            const __half2 h2 = __hmul2(*reinterpret_cast<const __half2 *>(&hi), f2[q]);
+                            w[j] = (uint32_t)e4m3x2_from_h2(*reinterpret_cast<const uint32_t *>(&l2)) |
+                                   ((uint32_t)e4m3x2_from_h2(*reinterpret_cast<const uint32_t *>(&h2)) << 16);
                         }
-                        *reinterpret_cast<uint4 *>(stage + (size_t)(u >> 3) * 128 + (u & 7) * 16) = o;
+                        *reinterpret_cast<uint4 *>(stage + (size_t)(u >> 3) * 128 + (u & 7) * 16) =
+                            make_uint4(w[0], w[1], w[2], w[3]);
                     }
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");

@@ -12,7 +12,6 @@
 // (computed in double precision).
 #pragma once
 
-#include <cuda_fp8.h>
 #include <float.h>
 
 #include "internal.cuh"
@@ -261,6 +260,13 @@ constexpr size_t fft_smem_bytes() {
            + 8 * fft_stages<TIn>() + 16;                                           // mbarriers
 }
 
+// Two floats to two E4M3 codes, round to nearest even, saturating to +-448: the low byte holds lo.
+__device__ __forceinline__ uint32_t e4m3x2_of(float lo, float hi) {
+    uint16_t r;
+    asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+
 // Smallest e with amax <= 448 * 2^e (power-of-two E4M3 block scale), clamped below at -126; 128 when
 // amax is not finite. From the float's bits: amax = 1.m * 2^(E - 127) and 448 = 1.75 * 2^8.
 __device__ __forceinline__ int e4m3_block_exp(float amax) {
@@ -390,58 +396,100 @@ fft_kernel(const TIn *__restrict__ in, void *__restrict__ out, const float2 *__r
             const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
             const long long row0 = (blockIdx.x + it * gridDim.x) * F;
             constexpr int kWarps = kFftThreads / 32;
-            const int n_jobs = F * n_blk;                          // (FFT of this CTA, 128-subcarrier block)
-            // four jobs per warp at a time, so that their reductions overlap
-            for (int p0 = warp; p0 < n_jobs; p0 += 4 * kWarps) {
-                float2 q[4][4];
-                float m[4];
-                bool bad[4];
+            // one (FFT, 128-subcarrier block) job per warp at a time: block maximum, exponent, codes
+            auto quantise = [&](const float2 *sb, unsigned rw32, unsigned srow, unsigned ant, int blk) {
+                float2 q[4];
+                float m = 0.f;
+                bool bad = false;
 #pragma unroll
-                for (int g4 = 0; g4 < 4; ++g4) {
-                    const int p = p0 + g4 * kWarps;
-                    const int ff = p / n_blk, blk = p - ff * n_blk;
-                    const bool live = p < n_jobs && row0 + ff < rows;   // warp-uniform
-                    const float2 *sb = xbuf + ff * (N + N / 16);
-                    m[g4] = 0.f;
-                    bad[g4] = false;
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const int a = blk * 128 + lane + 32 * j;      // consecutive lanes, consecutive banks
-                        q[g4][j] = live && a < n_sc ? sb[a] : make_float2(0.f, 0.f);
-                        const float ax = fabsf(q[g4][j].x), ay = fabsf(q[g4][j].y);
-                        bad[g4] |= !(ax <= FLT_MAX) || !(ay <= FLT_MAX);
-                        m[g4] = fmaxf(m[g4], fmaxf(ax, ay));
-                    }
+                for (int j = 0; j < 4; ++j) {
+                    const int a = blk * 128 + lane + 32 * j;          // consecutive lanes, consecutive banks
+                    q[j] = a < n_sc ? sb[a] : make_float2(0.f, 0.f);
+                    const float ax = fabsf(q[j].x), ay = fabsf(q[j].y);
+                    bad |= !(ax <= FLT_MAX) || !(ay <= FLT_MAX);
+                    m = fmaxf(m, fmaxf(ax, ay));
                 }
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1)
+                for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+                const bool anybad = __any_sync(0xFFFFFFFFu, bad);
+                const int ex = anybad ? 128 : e4m3_block_exp(m);
+                if (lane == 0)
+                    scales[((size_t)srow * n_blk + blk) * n_rx + ant] =
+                        anybad ? __uint_as_float(0x7FC00000u) : __uint_as_float((uint32_t)(ex + 127) << 23);
+                const float inv = anybad ? 1.f : __uint_as_float((uint32_t)(127 - ex) << 23);   // 2^-e
+                const float2 inv2 = make_float2(inv, inv);
+                uint8_t *o8 = static_cast<uint8_t *>(out) + (size_t)rw32 * 2 * pitch;
 #pragma unroll
-                    for (int g4 = 0; g4 < 4; ++g4) m[g4] = fmaxf(m[g4], __shfl_xor_sync(0xFFFFFFFFu, m[g4], o));
-#pragma unroll
-                for (int g4 = 0; g4 < 4; ++g4) {
-                    const int p = p0 + g4 * kWarps;
-                    const int ff = p / n_blk, blk = p - ff * n_blk;
-                    const bool anybad = __any_sync(0xFFFFFFFFu, bad[g4]);
-                    if (p >= n_jobs || row0 + ff >= rows) continue;          // warp-uniform
-                    const unsigned rw32 = (unsigned)(row0 + ff);             // rows < 2^31 (host check)
+                for (int j = 0; j < 4; ++j) {
+                    const int a = blk * 128 + lane + 32 * j;
+                    if (a < pitch) {
+                        // one conversion per complex value: low byte = re code, high byte = im code
+                        const float2 sv = __fmul2_rn(q[j], inv2);
+                        const uint32_t c = e4m3x2_of(sv.x, sv.y);
+                        o8[a] = (uint8_t)(c & 0xFFu);
+                        o8[pitch + a] = (uint8_t)(c >> 8);
+                    }
+                }
+            };
+            if constexpr (F == 1) {
+                // one FFT per CTA: a warp's blocks warp, warp + 8, ... (at most 4 for 4096 points) are
+                // processed together so that their loads, reductions and stores overlap
+                if (row0 < rows) {
+                    const unsigned rw32 = (unsigned)row0;                // rows < 2^31 (host check)
                     const unsigned srow = rw32 / (unsigned)n_rx, ant = rw32 - srow * (unsigned)n_rx;
-                    const int ex = anybad ? 128 : e4m3_block_exp(m[g4]);
-                    if (lane == 0)
-                        scales[((size_t)srow * n_blk + blk) * n_rx + ant] =
-                            anybad ? __uint_as_float(0x7FC00000u) : __uint_as_float((uint32_t)(ex + 127) << 23);
-                    const float inv = anybad ? 1.f : __uint_as_float((uint32_t)(127 - ex) << 23);   // 2^-e
                     uint8_t *o8 = static_cast<uint8_t *>(out) + (size_t)rw32 * 2 * pitch;
+                    constexpr int kJ = (N / 128 + kWarps - 1) / kWarps > 0 ? (N / 128 + kWarps - 1) / kWarps : 1;
+                    float2 q[kJ][4];
+                    float m[kJ];
+                    bool bad[kJ];
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const int a = blk * 128 + lane + 32 * j;
-                        if (a < pitch) {
-                            // one conversion per complex value: low byte = re code, high byte = im code
-                            const uint32_t c = __nv_cvt_float2_to_fp8x2(
-                                make_float2(q[g4][j].x * inv, q[g4][j].y * inv), __NV_SATFINITE, __NV_E4M3);
-                            o8[a] = (uint8_t)(c & 0xFFu);
-                            o8[pitch + a] = (uint8_t)(c >> 8);
+                    for (int g4 = 0; g4 < kJ; ++g4) {
+                        const int blk = warp + g4 * kWarps;
+                        m[g4] = 0.f;
+                        bad[g4] = false;
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const int a = blk * 128 + lane + 32 * j;
+                            q[g4][j] = (blk < n_blk && a < n_sc) ? xbuf[a] : make_float2(0.f, 0.f);
+                            const float ax = fabsf(q[g4][j].x), ay = fabsf(q[g4][j].y);
+                            bad[g4] |= !(ax <= FLT_MAX) || !(ay <= FLT_MAX);
+                            m[g4] = fmaxf(m[g4], fmaxf(ax, ay));
                         }
                     }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                        for (int g4 = 0; g4 < kJ; ++g4) m[g4] = fmaxf(m[g4], __shfl_xor_sync(0xFFFFFFFFu, m[g4], o));
+#pragma unroll
+                    for (int g4 = 0; g4 < kJ; ++g4) {
+                        const int blk = warp + g4 * kWarps;
+                        const bool anybad = __any_sync(0xFFFFFFFFu, bad[g4]);
+                        if (blk >= n_blk) continue;                      // warp-uniform
+                        const int ex = anybad ? 128 : e4m3_block_exp(m[g4]);
+                        if (lane == 0)
+                            scales[((size_t)srow * n_blk + blk) * n_rx + ant] =
+                                anybad ? __uint_as_float(0x7FC00000u) : __uint_as_float((uint32_t)(ex + 127) << 23);
+                        const float inv = anybad ? 1.f : __uint_as_float((uint32_t)(127 - ex) << 23);   // 2^-e
+                        const float2 inv2 = make_float2(inv, inv);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const int a = blk * 128 + lane + 32 * j;
+                            if (a < pitch) {
+                                const float2 sv = __fmul2_rn(q[g4][j], inv2);
+                                const uint32_t c = e4m3x2_of(sv.x, sv.y);    // low byte re, high byte im
+                                o8[a] = (uint8_t)(c & 0xFFu);
+                                o8[pitch + a] = (uint8_t)(c >> 8);
+                            }
+                        }
+                    }
+                }
+            } else {
+                for (int p = warp; p < F * n_blk; p += kWarps) {
+                    const int ff = p / n_blk, blk = p - ff * n_blk;
+                    if (row0 + ff >= rows) continue;                     // warp-uniform
+                    const unsigned rw32 = (unsigned)(row0 + ff);
+                    const unsigned srow = rw32 / (unsigned)n_rx, ant = rw32 - srow * (unsigned)n_rx;
+                    quantise(xbuf + ff * (N + N / 16), rw32, srow, ant, blk);
                 }
             }
         }
