@@ -58,6 +58,7 @@ def lib():
             "orc_cnn_loss_grad": (D, [P, P, P, I, I, I, P]),
             "orc_op_counts": (None, [I, I, I, I, I, I, P]),
             "orc_slot": (I, [P, I, I, I, I, P, I, P, I, P, P, I, I, D, D, P, P]),
+            "orc_noise_est": (D, [P, I, I, I, P, I, P, P, I]),
             "orc_e4m3_round": (D, [D]),
             "orc_e4m3_round_array": (None, [P, LL, P]),
             "orc_e4m3_block_exp": (I, [D]),
@@ -137,6 +138,17 @@ def chest_ls(beam, pilots, ports, comb: int, sc_start=None, sc_count=None, dmrs=
     if rc != 0:
         raise ValueError(f"orc_chest_ls: layer {-rc - 1} has no pilot in its range")
     return H
+
+
+def noise_est(beam, pilots, ports, comb: int, dmrs=DMRS_SYMBOLS) -> float:
+    """beam [S, N_SC, B], pilots [L, 2, N_SC] -> sigma2_hat (Section II NE; see orc_noise_est)."""
+    beam, pilots = _c128(beam), _c128(pilots)
+    S, n_sc, B = beam.shape
+    L = pilots.shape[0]
+    v = lib().orc_noise_est(_p(beam), S, n_sc, B, _p(_i32(dmrs)), L, _p(pilots), _p(_i32(ports)), comb)
+    if v < 0:
+        raise ValueError("orc_noise_est: no pilot subcarrier")
+    return float(v)
 
 
 def gram(Hs, load: float) -> np.ndarray:

@@ -22,6 +22,7 @@
  *                   are detected jointly).
  *   orc_demap       Gray hard decisions of 3GPP TS 38.211 5.1.3/5.1.4 (QPSK/16-QAM).
  *   orc_op_counts   Table I complex-MAC model.
+ *   orc_noise_est   Section II "NE": noise variance from the pilot residual y - H_hat p.
  *   orc_e4m3_*,     the FP8 precision form of the beamforming step (not in the paper; the form this
  *   orc_beamform_fp8  project adds): E4M3 rounding, power-of-two block scales, and the block-scaled
  *                   product y = W^H x with its exact power-of-two alignment.
@@ -185,6 +186,51 @@ int orc_chest_ls(const cplx *beam, int n_sym, int n_sc, int n_beams, const int *
         }
     }
     return 0;
+}
+
+/* Noise-variance estimate, Section II "NE": the autocorrelation (mean squared magnitude) of the difference
+ * between the received pilot symbols and the output expected from the estimated channel and the pilots.
+ * At every subcarrier q that carries a pilot of some layer (q % comb == port[l]) and each DMRS symbol j:
+ *     e_j[q] = y_j[q] - sum over the layers l with a pilot at q of H_hat[q][l] p_{l,j}[q]    (all beams)
+ * with H_hat from orc_chest_ls (over the whole band), and
+ *     sigma2_hat = 2 * mean |e_j[q][b]|^2 over (j, q, b).
+ * The factor 2 undoes the two-symbol average: at its own pilot H_hat = (LS_0 + LS_1) / 2, so
+ * e_j = p_j (LS_j - LS_{1-j}) / 2 and E|e_j|^2 = sigma^2 / 2 for unit-modulus pilots and a channel that does
+ * not change between the DMRS symbols (distinct ports: one layer per pilot subcarrier). Returns -1 when no
+ * subcarrier carries a pilot. */
+double orc_noise_est(const cplx *beam, int n_sym, int n_sc, int n_beams, const int *dmrs_sym, int n_layers,
+                     const cplx *pilots, const int *port, int comb)
+{
+    cplx *H = malloc(sizeof(cplx) * (size_t)n_sc * n_layers * n_beams);
+    int *st = malloc(sizeof(int) * (size_t)n_layers), *ct = malloc(sizeof(int) * (size_t)n_layers);
+    for (int l = 0; l < n_layers; ++l) {
+        st[l] = 0;
+        ct[l] = n_sc;
+    }
+    double sum = 0.0;
+    long long count = 0;
+    if (orc_chest_ls(beam, n_sym, n_sc, n_beams, dmrs_sym, n_layers, pilots, port, comb, st, ct, H) == 0) {
+        for (int q = 0; q < n_sc; ++q) {
+            int any = 0;
+            for (int l = 0; l < n_layers; ++l) any |= (q % comb == port[l]);
+            if (!any) continue;
+            for (int j = 0; j < 2; ++j) {
+                const cplx *y = beam + (size_t)dmrs_sym[j] * n_sc * n_beams;
+                for (int b = 0; b < n_beams; ++b) {
+                    cplx e = y[(size_t)q * n_beams + b];
+                    for (int l = 0; l < n_layers; ++l)
+                        if (q % comb == port[l])
+                            e -= H[((size_t)q * n_layers + l) * n_beams + b] * pilots[((size_t)l * 2 + j) * n_sc + q];
+                    sum += creal(e) * creal(e) + cimag(e) * cimag(e);
+                    ++count;
+                }
+            }
+        }
+    }
+    free(H);
+    free(st);
+    free(ct);
+    return count ? 2.0 * sum / (double)count : -1.0;
 }
 
 /* --------------------------------------------------------------- MMSE ---- */
