@@ -81,9 +81,14 @@ typedef struct {
     int form;          /* pusch_form                                                             */
     int n_sym;         /* OFDM symbols per slot, 14                                              */
     int dmrs_sym[2];   /* the two DMRS (pilot) symbols, e.g. {2, 11}                             */
-    float noise_var;   /* sigma^2 of Eq. 2                                                       */
+    float noise_var;   /* sigma^2 of Eq. 2, or PUSCH_NOISE_ESTIMATE: estimated per slot from the pilots  */
     float loading;     /* extra diagonal loading added to sigma^2 (0 = the plain Eq. 2)          */
 } pusch_cell_cfg;
+
+/* noise_var value that makes the chain estimate sigma^2 per slot (pusch_noise_estimate) instead of using a
+ * given value: pusch_slot estimates after the LS stage; pusch_mmse_detect uses the estimates of the handle's
+ * last pusch_noise_estimate call. Not accepted by pusch_batch_create. */
+#define PUSCH_NOISE_ESTIMATE (-1.0f)
 
 typedef struct pusch_handle pusch_handle;   /* opaque: owns the twiddle table and workspace   */
 
@@ -148,6 +153,20 @@ pusch_status pusch_beamform(pusch_handle *h, int n_slots, const void *freq_in, c
  */
 pusch_status pusch_chest_ls(pusch_handle *h, int n_slots, const void *beam, const void *pilots, void *H_hat,
                             void *stream);
+
+/*
+ * Noise-variance estimation (Section II "NE": the autocorrelation of the difference between the received pilot
+ * symbols and the output expected from the estimated channel and the pilots). Per slot, over the pilot
+ * subcarriers q of every layer l, both DMRS symbols j and all beams b, with LS[q] = 1/2 sum_j y_j[q] / p_j[q]
+ * (the channel estimate at the layer's own pilot):
+ *     sigma2[slot] = 2 * mean |y_j[q][b] - LS[q][b] p_{l,j}[q]|^2
+ * The factor 2 undoes the two-symbol mean (E|.|^2 = sigma^2 / 2 for unit-modulus pilots and a channel that is
+ * constant between the DMRS symbols). The sum runs in a fixed order (no float atomics): reruns are
+ * bit-identical. beam, pilots: as pusch_chest_ls. sigma2: [n_slots] floats (device; may be NULL). The
+ * estimates are also kept in the handle for pusch_mmse_detect in PUSCH_NOISE_ESTIMATE mode.
+ */
+pusch_status pusch_noise_estimate(pusch_handle *h, int n_slots, const void *beam, const void *pilots, float *sigma2,
+                                  void *stream);
 
 /*
  * MMSE detection (Eq. 2 with Section II's Cholesky + two triangular solves), per subcarrier a:

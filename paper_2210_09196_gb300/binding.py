@@ -27,6 +27,8 @@ PUSCH_FORM_FP32 = 0
 PUSCH_FORM_MIXED = 1
 PUSCH_FORM_FP8 = 2
 
+PUSCH_NOISE_ESTIMATE = -1.0
+
 PUSCH_STATUS_PIVOT = 0x1
 PUSCH_STATUS_NONFINITE = 0x2
 
@@ -34,7 +36,8 @@ PUSCH_STATUS_NONFINITE = 0x2
 EXPORTS = (
     "pusch_create", "pusch_destroy", "pusch_workspace_size", "pusch_sc_pitch", "pusch_freq_bytes", "pusch_ofdm_fft",
     "pusch_beamform",
-    "pusch_chest_ls", "pusch_mmse_detect", "pusch_slot", "pusch_slot_host", "pusch_last_error", "pusch_version",
+    "pusch_chest_ls", "pusch_noise_estimate", "pusch_mmse_detect", "pusch_slot", "pusch_slot_host",
+    "pusch_last_error", "pusch_version",
     "pusch_slot_noalloc", "pusch_profile_start", "pusch_profile_read",
     "pusch_batch_create", "pusch_batch_destroy", "pusch_batch_sizes", "pusch_batch_run", "pusch_batch_autotune",
     "pusch_batch_tuning",
@@ -96,6 +99,7 @@ def lib():
             "pusch_ofdm_fft": (I, [P, I, P, P, P]),
             "pusch_beamform": (I, [P, I, P, P, P, P]),
             "pusch_chest_ls": (I, [P, I, P, P, P, P]),
+            "pusch_noise_estimate": (I, [P, I, P, P, P, P]),
             "pusch_mmse_detect": (I, [P, I, P, P, P, P, P, P]),
             "pusch_slot": (I, [P, I, P, P, P, P, P, P, P]),
             "pusch_slot_host": (I, [P, I, P, P, P, P, P, P, P]),
@@ -193,6 +197,11 @@ def pusch_beamform(h, n_slots, freq_in, W, beam_out, stream=None) -> None:
 def pusch_chest_ls(h, n_slots, beam, pilots, H_hat, stream=None) -> None:
     _check(lib().pusch_chest_ls(h, n_slots, _ptr(beam), _ptr(pilots), _ptr(H_hat), _stream(stream)),
            "pusch_chest_ls")
+
+
+def pusch_noise_estimate(h, n_slots, beam, pilots, sigma2=None, stream=None) -> None:
+    _check(lib().pusch_noise_estimate(h, n_slots, _ptr(beam), _ptr(pilots), _ptr(sigma2), _stream(stream)),
+           "pusch_noise_estimate")
 
 
 def pusch_mmse_detect(h, n_slots, H_hat, beam, x_hat, bits, status=None, stream=None) -> None:

@@ -56,7 +56,8 @@ pusch_status validate_cfg(const pusch_cell_cfg *c) {
     if (c->dmrs_sym[0] < 0 || c->dmrs_sym[0] >= c->n_sym || c->dmrs_sym[1] < 0 || c->dmrs_sym[1] >= c->n_sym ||
         c->dmrs_sym[0] == c->dmrs_sym[1])
         return fail(PUSCH_ERR_ARG, "dmrs_sym must be two distinct symbols of the slot");
-    if (!(c->noise_var >= 0.f) || !isfinite(c->noise_var)) return fail(PUSCH_ERR_ARG, "noise_var must be >= 0");
+    if (c->noise_var != PUSCH_NOISE_ESTIMATE && (!(c->noise_var >= 0.f) || !isfinite(c->noise_var)))
+        return fail(PUSCH_ERR_ARG, "noise_var must be >= 0 or PUSCH_NOISE_ESTIMATE");
     if (!(c->loading >= 0.f) || !isfinite(c->loading)) return fail(PUSCH_ERR_ARG, "loading must be >= 0");
     if (c->form == PUSCH_FORM_MIXED) {
         pusch::Geometry g = pusch::make_geometry(*c);
@@ -207,6 +208,11 @@ pusch_status pusch_create(pusch_handle **out, const pusch_cell_cfg *cfg, int max
     if ((e = cudaMalloc((void **)&h->beam, beam_bytes(g, max_slots))) != cudaSuccess) goto cuda_error;
     if ((e = cudaMalloc((void **)&h->ls, ls_bytes(g, max_slots))) != cudaSuccess) goto cuda_error;
     if ((e = cudaMalloc((void **)&h->status_sink, 4 * sizeof(uint32_t))) != cudaSuccess) goto cuda_error;
+    if ((e = cudaMalloc((void **)&h->ne_partial, (size_t)max_slots * pusch::kNoiseParts * sizeof(float2))) !=
+        cudaSuccess)
+        goto cuda_error;
+    if ((e = cudaMalloc((void **)&h->sigma2, (size_t)max_slots * sizeof(float))) != cudaSuccess) goto cuda_error;
+    if ((e = cudaMemset(h->sigma2, 0, (size_t)max_slots * sizeof(float))) != cudaSuccess) goto cuda_error;
     *out = h;
     return ok();
 cuda_error:
@@ -224,6 +230,8 @@ pusch_status pusch_destroy(pusch_handle *h) {
     cudaFree(h->beam);
     cudaFree(h->ls);
     cudaFree(h->status_sink);
+    cudaFree(h->ne_partial);
+    cudaFree(h->sigma2);
     cudaFree(h->h_time);
     cudaFree(h->h_pilots);
     cudaFree(h->h_xhat);
@@ -269,6 +277,22 @@ pusch_status pusch_chest_ls(pusch_handle *h, int n_slots, const void *beam, cons
     return ok();
 }
 
+pusch_status pusch_noise_estimate(pusch_handle *h, int n_slots, const void *beam, const void *pilots, float *sigma2,
+                                  void *stream) {
+    pusch_status st = check_handle(h, n_slots);
+    if (st != PUSCH_OK) return st;
+    if (n_slots == 0) return ok();
+    if (!beam || !pilots) return fail(PUSCH_ERR_ARG, "pusch_noise_estimate: NULL buffer");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = pusch::launch_noise_est(h->geo, n_slots, (const float2 *)beam, (const float2 *)pilots,
+                                            h->ne_partial, h->sigma2, s);
+    if (e != cudaSuccess) return cuda_fail(e, "noise estimation launch");
+    if (sigma2 && (e = cudaMemcpyAsync(sigma2, h->sigma2, (size_t)n_slots * sizeof(float), cudaMemcpyDeviceToDevice,
+                                       s)) != cudaSuccess)
+        return cuda_fail(e, "noise estimate copy");
+    return ok();
+}
+
 pusch_status pusch_mmse_detect(pusch_handle *h, int n_slots, const void *H_hat, const void *beam, void *x_hat,
                                uint8_t *bits, uint32_t *status, void *stream) {
     pusch_status st = check_handle(h, n_slots);
@@ -281,8 +305,9 @@ pusch_status pusch_mmse_detect(pusch_handle *h, int n_slots, const void *H_hat, 
     uint32_t *stat = status ? status : h->status_sink;
     if ((st = reset_status(stat, s)) != PUSCH_OK) return st;
     if (n_slots == 0) return ok();
+    const float *sg2 = h->cfg.noise_var == PUSCH_NOISE_ESTIMATE ? h->sigma2 : nullptr;
     cudaError_t e = pusch::launch_mmse(h->geo, n_slots, (const float2 *)H_hat, (const float2 *)beam, (float2 *)x_hat,
-                                       bits, stat, s);
+                                       bits, stat, s, sg2);
     if (e != cudaSuccess) return cuda_fail(e, "detection launch");
     return ok();
 }
@@ -305,8 +330,13 @@ pusch_status pusch_slot(pusch_handle *h, int n_slots, const void *time_in, const
     if ((st = reset_status(stat, s)) != PUSCH_OK) return st;
     cudaError_t e = pusch::launch_ls_pilots(h->geo, n_slots, h->beam, (const float2 *)pilots, h->ls, s);
     if (e != cudaSuccess) return cuda_fail(e, "LS pilot table launch");
+    const bool est = h->cfg.noise_var == PUSCH_NOISE_ESTIMATE;
+    if (est && (e = pusch::launch_noise_est(h->geo, n_slots, h->beam, (const float2 *)pilots, h->ne_partial,
+                                            h->sigma2, s)) != cudaSuccess)
+        return cuda_fail(e, "noise estimation launch");
     if (ev) cudaEventRecord(ev[3], s);
-    e = pusch::launch_mmse_fused(h->geo, n_slots, h->beam, h->ls, (float2 *)x_hat, bits, stat, s);
+    e = pusch::launch_mmse_fused(h->geo, n_slots, h->beam, h->ls, (float2 *)x_hat, bits, stat, s,
+                                 est ? h->sigma2 : nullptr);
     if (e != cudaSuccess) return cuda_fail(e, "fused estimation + detection launch");
     if (ev) cudaEventRecord(ev[4], s);
     return ok();

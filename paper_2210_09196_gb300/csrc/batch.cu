@@ -533,6 +533,8 @@ pusch_status pusch_batch_create(pusch_batch **out, const pusch_cell_cfg *cells, 
         size_t ws;
         pusch_status st = pusch_workspace_size(&cc, 1, &ws);
         if (st != PUSCH_OK) return st;
+        if (cells[c].noise_var == PUSCH_NOISE_ESTIMATE)
+            return bfail(PUSCH_ERR_UNSUPPORTED, "cell %d: the batch takes a given noise variance per cell", c);
         if (cells[c].in_fp16 != cells[0].in_fp16 || cells[c].form != cells[0].form ||
             cells[c].n_sym != cells[0].n_sym || cells[c].dmrs_sym[0] != cells[0].dmrs_sym[0] ||
             cells[c].dmrs_sym[1] != cells[0].dmrs_sym[1])

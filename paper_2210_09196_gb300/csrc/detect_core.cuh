@@ -64,10 +64,13 @@ __device__ __forceinline__ uint8_t det_demap(float2 x, int q) {
 }
 
 // Returns true when a pivot was not a positive finite number (the factorisation continued with 1).
+// load: sigma^2 + extra loading, or, when sigma2 is not NULL, sigma2[slot] + load (the per-slot noise estimate;
+// read only where the diagonal is loaded, so nothing extra stays live across the Gram loop).
 template <int NL, int ND, int NR>
 __device__ __forceinline__ bool detect_group(const float2 *__restrict__ hr, const float2 *__restrict__ hg,
                                              const float2 *__restrict__ yt, float2 *lt, int hs, int nb, int nd,
-                                             int nl, float load, int i, int src0, float2 (&acc)[NR]) {
+                                             int nl, float load, int i, int src0, float2 (&acc)[NR],
+                                             const float *__restrict__ sigma2 = nullptr, long long slot = 0) {
     constexpr unsigned kFull = kDetFull;
     // ---- 2a. Gram row i: G[j] = sum_b conj(H[i][b]) H[j][b], with packed FP32x2 FMAs: P[j] = sum_b Re(h_b) H[j][b]
     //         and Q[j] = sum_b Im(h_b) H[j][b] (h_b = H[i][b]), then G[j] = P[j] - i Q[j].
@@ -104,6 +107,7 @@ __device__ __forceinline__ bool detect_group(const float2 *__restrict__ hr, cons
 #pragma unroll
         for (int j = 0; j < NL; ++j) G[j] = make_float2(P[j].x + Q[j].y, P[j].y - Q[j].x);
     }
+    if (sigma2) load += __ldg(&sigma2[slot]);
 #pragma unroll
     for (int j = 0; j < NL; ++j)
         if (j == i) G[j] = (i < nl) ? make_float2(G[j].x + load, 0.f) : make_float2(1.f, 0.f);

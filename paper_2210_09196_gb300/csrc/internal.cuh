@@ -83,16 +83,23 @@ cudaError_t launch_beamform_fp32(const Geometry &g, int n_slots, const float2 *f
                                  cudaStream_t st);
 cudaError_t launch_chest_ls(const Geometry &g, int n_slots, const float2 *beam, const float2 *pilots, float2 *H,
                             cudaStream_t st);
+// sigma2 (optional, device, one float per slot): per-slot noise variance replacing g.noise_var.
 cudaError_t launch_mmse(const Geometry &g, int n_slots, const float2 *H, const float2 *beam, float2 *x_hat,
-                        uint8_t *bits, uint32_t *status, cudaStream_t st);
+                        uint8_t *bits, uint32_t *status, cudaStream_t st, const float *sigma2 = nullptr);
 // LS values at the pilot subcarriers: ls[slot][l][k][b] for pilot q = port[l] + k * comb, k < kmax.
 int ls_pilots_per_layer(const Geometry &g);
 cudaError_t launch_ls_pilots(const Geometry &g, int n_slots, const float2 *beam, const float2 *pilots, float2 *ls,
                              cudaStream_t st);
+// Noise-variance estimate per slot from the pilot residuals (Section II "NE"): partial needs
+// n_slots * kNoiseParts float2 of scratch; sigma2 receives one float per slot.
+constexpr int kNoiseParts = 64;
+cudaError_t launch_noise_est(const Geometry &g, int n_slots, const float2 *beam, const float2 *pilots,
+                             float2 *partial, float *sigma2, cudaStream_t st);
 // Estimation fused into detection: the estimate is interpolated from the LS pilot table inside the
 // detection kernel and never written to memory.
 cudaError_t launch_mmse_fused(const Geometry &g, int n_slots, const float2 *beam, const float2 *ls,
-                              float2 *x_hat, uint8_t *bits, uint32_t *status, cudaStream_t st);
+                              float2 *x_hat, uint8_t *bits, uint32_t *status, cudaStream_t st,
+                              const float *sigma2 = nullptr);
 
 // Launch shape of the tensor-core beamforming kernel: K rows per pipeline stage and whether the epilogue
 // writes through shared memory and TMA stores. chunk_rows = 0 lets the kernel choose from its shared-memory
@@ -153,6 +160,8 @@ struct pusch_handle {
     float2 *beam = nullptr;         // workspace: beamformed grid
     float2 *ls = nullptr;           // workspace: LS values at the pilot subcarriers
     uint32_t *status_sink = nullptr;  // status words used when the caller passes NULL
+    float2 *ne_partial = nullptr;     // noise estimation: per (slot, part) partial sums
+    float *sigma2 = nullptr;          // noise estimation: per-slot estimate (read by the detector in estimate mode)
     // staging for pusch_slot_host (allocated on first use)
     void *h_time = nullptr;
     float2 *h_pilots = nullptr;

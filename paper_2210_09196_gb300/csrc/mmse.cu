@@ -9,7 +9,7 @@ using mmse_detail::MmseArgs;
 
 template <bool FUSED>
 cudaError_t launch_any(const Geometry &g, int n_slots, const float2 *H, const float2 *beam, const float2 *pilots,
-                       float2 *x_hat, uint8_t *bits, uint32_t *status, cudaStream_t st) {
+                       float2 *x_hat, uint8_t *bits, uint32_t *status, cudaStream_t st, const float *sigma2) {
     MmseArgs a;
     a.n_sc = g.n_sc;
     a.n_beams = g.n_beams;
@@ -21,6 +21,8 @@ cudaError_t launch_any(const Geometry &g, int n_slots, const float2 *H, const fl
     a.dmrs0 = g.dmrs0;
     a.dmrs1 = g.dmrs1;
     a.load = g.noise_var + g.loading;
+    a.loading = g.loading;
+    a.sigma2 = sigma2;
     a.kmax = ls_pilots_per_layer(g);
     for (int d = 0; d < 16; ++d) a.data_sym[d] = g.data_sym[d];
     for (int l = 0; l < 32; ++l) a.port[l] = g.port[l];
@@ -37,13 +39,13 @@ cudaError_t launch_any(const Geometry &g, int n_slots, const float2 *H, const fl
 }  // namespace
 
 cudaError_t launch_mmse(const Geometry &g, int n_slots, const float2 *H, const float2 *beam, float2 *x_hat,
-                        uint8_t *bits, uint32_t *status, cudaStream_t st) {
-    return launch_any<false>(g, n_slots, H, beam, nullptr, x_hat, bits, status, st);
+                        uint8_t *bits, uint32_t *status, cudaStream_t st, const float *sigma2) {
+    return launch_any<false>(g, n_slots, H, beam, nullptr, x_hat, bits, status, st, sigma2);
 }
 
 cudaError_t launch_mmse_fused(const Geometry &g, int n_slots, const float2 *beam, const float2 *ls,
-                              float2 *x_hat, uint8_t *bits, uint32_t *status, cudaStream_t st) {
-    return launch_any<true>(g, n_slots, nullptr, beam, ls, x_hat, bits, status, st);
+                              float2 *x_hat, uint8_t *bits, uint32_t *status, cudaStream_t st, const float *sigma2) {
+    return launch_any<true>(g, n_slots, nullptr, beam, ls, x_hat, bits, status, st, sigma2);
 }
 
 }  // namespace pusch

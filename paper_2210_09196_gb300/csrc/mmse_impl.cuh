@@ -31,7 +31,9 @@ constexpr unsigned kFull = 0xffffffffu;
 
 struct MmseArgs {
     int n_sc, n_beams, n_layers, n_sym, n_data, qam_bits, comb, dmrs0, dmrs1, kmax;
-    float load;  // sigma^2 + extra loading
+    float load;  // sigma^2 + extra loading (sigma2 == nullptr)
+    float loading;             // extra loading alone
+    const float *sigma2;       // per-slot noise variance (device) or nullptr
     int data_sym[16];
     int port[32];
 };
@@ -176,8 +178,9 @@ mmse_kernel(MmseArgs g, long long total_sc, const float2 *__restrict__ H, const 
     const float2 *hg = Ht + grp * ht;           // the group's rows
     constexpr int NR = ND > 0 ? ND : 14;
     float2 acc[NR];
-    const bool bad = detect_group<NL, ND, NR>(hr, hg, Yt + grp * nd * hs, Ht + grp * ht, hs, nb, nd, nl, g.load, i,
-                                              src0, acc);
+    const bool bad = detect_group<NL, ND, NR>(hr, hg, Yt + grp * nd * hs, Ht + grp * ht, hs, nb, nd, nl,
+                                              g.sigma2 ? g.loading : g.load, i, src0, acc, g.sigma2,
+                                              valid ? slot : 0);
     if (valid && bad && i == 0) {
         atomicAdd(&status[1], 1u);
         atomicMin(&status[2], (unsigned)my_sc);

@@ -87,7 +87,9 @@ extern "C" pusch_status pusch_slot_noalloc(const pusch_cell_cfg *cfg, int n_slot
     const size_t freq_b = up256(pusch::freq_bytes_of(g, n_slots));
     const size_t beam_b = up256((size_t)n_slots * g.n_sym * g.n_sc * g.n_beams * sizeof(float2));
     const size_t H_b = up256((size_t)n_slots * g.n_sc * g.n_layers * g.n_beams * sizeof(float2));
-    const size_t need = tw_b + words_b + freq_b + beam_b + H_b;
+    const bool est = cfg->noise_var == PUSCH_NOISE_ESTIMATE;
+    const size_t ne_b = est ? up256((size_t)n_slots * (pusch::kNoiseParts * sizeof(float2) + sizeof(float))) : 0;
+    const size_t need = tw_b + words_b + freq_b + beam_b + H_b + ne_b;
     if (need > (size_t)PUSCH_NOALLOC_SCRATCH_BYTES) {
         char buf[512];
         snprintf(buf, sizeof buf,
@@ -105,6 +107,8 @@ extern "C" pusch_status pusch_slot_noalloc(const pusch_cell_cfg *cfg, int n_slot
     void *freq = base + tw_b + words_b;
     float2 *beam = reinterpret_cast<float2 *>(base + tw_b + words_b + freq_b);
     float2 *H = reinterpret_cast<float2 *>(base + tw_b + words_b + freq_b + beam_b);
+    float2 *ne_partial = reinterpret_cast<float2 *>(base + tw_b + words_b + freq_b + beam_b + H_b);
+    float *sigma2 = reinterpret_cast<float *>(ne_partial + (size_t)n_slots * pusch::kNoiseParts);
     uint32_t *stat = status ? status : sink;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
 
@@ -118,7 +122,11 @@ extern "C" pusch_status pusch_slot_noalloc(const pusch_cell_cfg *cfg, int n_slot
     if (e != cudaSuccess) return na_fail(PUSCH_ERR_CUDA, "pusch_slot_noalloc beamforming launch", e);
     if ((e = pusch::launch_chest_ls(g, n_slots, beam, static_cast<const float2 *>(pilots), H, s)) != cudaSuccess)
         return na_fail(PUSCH_ERR_CUDA, "pusch_slot_noalloc channel estimation launch", e);
-    if ((e = pusch::launch_mmse(g, n_slots, H, beam, static_cast<float2 *>(x_hat), bits, stat, s)) != cudaSuccess)
+    if (est && (e = pusch::launch_noise_est(g, n_slots, beam, static_cast<const float2 *>(pilots), ne_partial, sigma2,
+                                            s)) != cudaSuccess)
+        return na_fail(PUSCH_ERR_CUDA, "pusch_slot_noalloc noise estimation launch", e);
+    if ((e = pusch::launch_mmse(g, n_slots, H, beam, static_cast<float2 *>(x_hat), bits, stat, s,
+                                est ? sigma2 : nullptr)) != cudaSuccess)
         return na_fail(PUSCH_ERR_CUDA, "pusch_slot_noalloc detection launch", e);
     pusch::set_last_error("");
     return PUSCH_OK;

@@ -118,6 +118,12 @@ class Receiver:
         B.pusch_chest_ls(self.h, n, beam, pilots, H, stream)
         return H
 
+    def noise_estimate(self, beam, pilots, stream=None):
+        n = beam.shape[0]
+        out = torch.empty(n, dtype=torch.float32, device=self.device)
+        B.pusch_noise_estimate(self.h, n, beam, pilots, out, stream)
+        return out
+
     def mmse_detect(self, H, beam, stream=None):
         n = H.shape[0]
         x, b, st = self.xhat_buffer(n), self.bits_buffer(n), self.status_buffer()

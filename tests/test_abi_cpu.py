@@ -52,7 +52,7 @@ def _good(**kw):
 @pytest.mark.parametrize("bad,code", [
     (dict(n_fft=500), -5), (dict(n_fft=8192), -5), (dict(n_sc=0), -1), (dict(n_sc=600), -1),
     (dict(n_beams=65), -5), (dict(n_layers=17), -1), (dict(n_layers=33, n_beams=64), -1),
-    (dict(qam_bits=3), -1), (dict(noise_var=-1.0), -1), (dict(noise_var=float("nan")), -1),
+    (dict(qam_bits=3), -1), (dict(noise_var=-0.5), -1), (dict(noise_var=float("nan")), -1),
     (dict(comb=0), -1), (dict(ports=[0, 1, 2, 4]), -1), (dict(dmrs_sym=(2, 2)), -1), (dict(dmrs_sym=(2, 14)), -1),
     (dict(n_sym=2), -1), (dict(form=7), -1), (dict(n_rx=0), -5),
 ])
@@ -65,6 +65,12 @@ def test_invalid_configs_are_rejected_on_the_host(B, bad, code):
     h = ctypes.c_void_p(123)
     assert B.lib().pusch_create(ctypes.byref(h), ctypes.byref(cfg), 1) == code
     assert h.value is None
+
+
+def test_noise_estimate_mode_is_accepted(B):
+    cfg = _good(noise_var=B.PUSCH_NOISE_ESTIMATE)
+    out = ctypes.c_size_t()
+    assert B.lib().pusch_workspace_size(ctypes.byref(cfg), 1, ctypes.byref(out)) == 0
 
 
 def test_workspace_size(B):
