@@ -93,9 +93,15 @@ size_t xhat_count(const pusch::Geometry &g, int n_slots) {
 }
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+size_t H_bytes(const pusch::Geometry &g, int n_slots) {
+    return (size_t)n_slots * g.n_sc * g.n_layers * g.n_beams * sizeof(float2);
+}
+
 size_t workspace_bytes(const pusch::Geometry &g, int max_slots) {
     size_t b = align256(g.n_fft * sizeof(float2));
     b += align256(freq_bytes(g, max_slots)) + align256(beam_bytes(g, max_slots)) + align256(ls_bytes(g, max_slots));
+    b += align256(H_bytes(g, max_slots));
+    b += align256((size_t)max_slots * pusch::kNoiseParts * sizeof(float2)) + align256((size_t)max_slots * sizeof(float));
     return b;
 }
 
@@ -207,6 +213,7 @@ pusch_status pusch_create(pusch_handle **out, const pusch_cell_cfg *cfg, int max
     if ((e = cudaMalloc(&h->freq, freq_bytes(g, max_slots))) != cudaSuccess) goto cuda_error;
     if ((e = cudaMalloc((void **)&h->beam, beam_bytes(g, max_slots))) != cudaSuccess) goto cuda_error;
     if ((e = cudaMalloc((void **)&h->ls, ls_bytes(g, max_slots))) != cudaSuccess) goto cuda_error;
+    if ((e = cudaMalloc((void **)&h->H, H_bytes(g, max_slots))) != cudaSuccess) goto cuda_error;
     if ((e = cudaMalloc((void **)&h->status_sink, 4 * sizeof(uint32_t))) != cudaSuccess) goto cuda_error;
     if ((e = cudaMalloc((void **)&h->ne_partial, (size_t)max_slots * pusch::kNoiseParts * sizeof(float2))) !=
         cudaSuccess)
@@ -229,6 +236,7 @@ pusch_status pusch_destroy(pusch_handle *h) {
     cudaFree(h->freq);
     cudaFree(h->beam);
     cudaFree(h->ls);
+    cudaFree(h->H);
     cudaFree(h->status_sink);
     cudaFree(h->ne_partial);
     cudaFree(h->sigma2);
@@ -271,8 +279,9 @@ pusch_status pusch_chest_ls(pusch_handle *h, int n_slots, const void *beam, cons
     if (st != PUSCH_OK) return st;
     if (n_slots == 0) return ok();
     if (!beam || !pilots || !H_hat) return fail(PUSCH_ERR_ARG, "pusch_chest_ls: NULL buffer");
-    cudaError_t e = pusch::launch_chest_ls(h->geo, n_slots, (const float2 *)beam, (const float2 *)pilots,
-                                           (float2 *)H_hat, (cudaStream_t)stream);
+    cudaError_t e = pusch::launch_ls_pilots(h->geo, n_slots, (const float2 *)beam, (const float2 *)pilots, h->ls,
+                                            (cudaStream_t)stream);
+    if (e == cudaSuccess) e = pusch::launch_chest_interp(h->geo, n_slots, h->ls, (float2 *)H_hat, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "channel estimation launch");
     return ok();
 }
@@ -334,10 +343,11 @@ pusch_status pusch_slot(pusch_handle *h, int n_slots, const void *time_in, const
     if (est && (e = pusch::launch_noise_est(h->geo, n_slots, h->beam, (const float2 *)pilots, h->ne_partial,
                                             h->sigma2, s)) != cudaSuccess)
         return cuda_fail(e, "noise estimation launch");
+    if ((e = pusch::launch_chest_interp(h->geo, n_slots, h->ls, h->H, s)) != cudaSuccess)
+        return cuda_fail(e, "estimate interpolation launch");
     if (ev) cudaEventRecord(ev[3], s);
-    e = pusch::launch_mmse_fused(h->geo, n_slots, h->beam, h->ls, (float2 *)x_hat, bits, stat, s,
-                                 est ? h->sigma2 : nullptr);
-    if (e != cudaSuccess) return cuda_fail(e, "fused estimation + detection launch");
+    e = pusch::launch_mmse(h->geo, n_slots, h->H, h->beam, (float2 *)x_hat, bits, stat, s, est ? h->sigma2 : nullptr);
+    if (e != cudaSuccess) return cuda_fail(e, "detection launch");
     if (ev) cudaEventRecord(ev[4], s);
     return ok();
 }

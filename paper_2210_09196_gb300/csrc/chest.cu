@@ -1,11 +1,13 @@
 // LS channel estimation on the DMRS symbols (Section II: block-type pilots filling whole OFDM symbols;
 // the estimate is an element-wise division of the received pilot REs by the known pilots, Table I "CHE"),
-// followed by linear interpolation between each layer's comb of pilot subcarriers.
+// followed by linear interpolation between each layer's comb of pilot subcarriers; and the noise-variance
+// estimate from the pilot residuals (Section II "NE").
 //
-// One thread per output element (slot, subcarrier a, layer l, beam b), beam fastest, so that the
-// [n_sc][n_layers][n_beams] estimate the detector reads is written with fully coalesced stores. The two
-// pilot REs a thread needs are re-derived per thread (they are read from L1/L2; the DMRS rows are a
-// small fraction of the slot).
+// Two passes: the LS values at every layer's pilot subcarriers (a small table, L2-resident), then the full
+// estimate, one thread per output element (slot, subcarrier a, layer l, beam b), beam fastest, so that the
+// [n_sc][n_layers][n_beams] estimate the detector reads is written with fully coalesced stores.
+#include <algorithm>
+
 #include "chest_common.cuh"
 
 namespace pusch {
@@ -16,65 +18,77 @@ struct ChestArgs {
     int port[32];
 };
 
-__global__ void __launch_bounds__(256)
-chest_ls_kernel(ChestArgs g, long long total, const float2 *__restrict__ beam, const float2 *__restrict__ pilots,
-                float2 *__restrict__ H) {
-    const long long per_sc = (long long)g.n_layers * g.n_beams;
-    const long long per_slot = per_sc * g.n_sc;
-    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const long long slot = idx / per_slot;
-        long long rem = idx - slot * per_slot;
-        const int a = (int)(rem / per_sc);
-        rem -= (long long)a * per_sc;
-        const int l = (int)(rem / g.n_beams);
-        const int b = (int)(rem - (long long)l * g.n_beams);
+// The estimate H[slot][a][l][b] from the LS pilot table: linear interpolation between the layer's neighbouring
+// pilot subcarriers, held outside the first/last. CTA (subcarrier run, slot) covers kRun consecutive
+// subcarriers; thread t owns (layer l, beam unit u) = (t / units, t % units) for the whole run, so the pilot
+// bracket is found once (one division) and then advanced, and consecutive threads write consecutive 16-byte
+// (or 8-byte) units of a subcarrier's [n_layers][n_beams] block. T = float4 (beam pairs) or float2.
+constexpr int kRun = 16;
 
-        int lo, hi;
-        pilot_bracket(a, g.port[l], g.comb, g.n_sc, lo, hi);
-        const float2 *y0 = beam + (slot * g.n_sym + g.dmrs0) * (long long)g.n_sc * g.n_beams;
-        const float2 *y1 = beam + (slot * g.n_sym + g.dmrs1) * (long long)g.n_sc * g.n_beams;
-        const float2 *p0 = pilots + (slot * g.n_layers + l) * 2LL * g.n_sc;
-        const float2 *p1 = p0 + g.n_sc;
-        const float2 h_lo = ls_value(__ldg(&y0[(long long)lo * g.n_beams + b]), __ldg(&y1[(long long)lo * g.n_beams + b]),
-                                     pilot_inverse(__ldg(&p0[lo])), pilot_inverse(__ldg(&p1[lo])));
-        float2 h = h_lo;
-        if (hi != lo) {
-            const float2 h_hi =
-                ls_value(__ldg(&y0[(long long)hi * g.n_beams + b]), __ldg(&y1[(long long)hi * g.n_beams + b]),
-                         pilot_inverse(__ldg(&p0[hi])), pilot_inverse(__ldg(&p1[hi])));
-            h = interp(h_lo, h_hi, interp_weight(a, lo, hi));
+__device__ __forceinline__ float4 lerp_unit(float4 lo, float4 hi, float w) {
+    const float2 h0 = interp(make_float2(lo.x, lo.y), make_float2(hi.x, hi.y), w);
+    const float2 h1 = interp(make_float2(lo.z, lo.w), make_float2(hi.z, hi.w), w);
+    return make_float4(h0.x, h0.y, h1.x, h1.y);
+}
+__device__ __forceinline__ float2 lerp_unit(float2 lo, float2 hi, float w) { return interp(lo, hi, w); }
+
+template <typename T>
+__global__ void __launch_bounds__(1024)
+chest_interp_kernel(ChestArgs g, int kmax, int units, int layers_per_cta, const T *__restrict__ ls,
+                    T *__restrict__ H) {
+    const int t = threadIdx.x;
+    const int l = blockIdx.z * layers_per_cta + t / units, u = t - (t / units) * units;
+    if (l >= g.n_layers) return;
+    const long long slot = blockIdx.y;
+    const int a0 = blockIdx.x * kRun;
+    const int port = g.port[l], comb = g.comb;
+    const int first = port, last = port + ((g.n_sc - 1 - port) / comb) * comb;
+    int lo = a0 <= first ? first : port + ((min(a0, last) - port) / comb) * comb;   // pilot at or below a0
+    const T *tab = ls + ((slot * g.n_layers + l) * (long long)kmax) * units + u;
+    T *out = H + ((slot * g.n_sc + a0) * g.n_layers + l) * (long long)units + u;
+    const long long stride = (long long)g.n_layers * units;
+    for (int r = 0; r < kRun; ++r, out += stride) {
+        const int a = a0 + r;
+        if (a >= g.n_sc) break;
+        int plo, phi;
+        if (a <= first) {
+            plo = phi = first;
+        } else if (a >= last) {
+            plo = phi = last;
+        } else {
+            while (lo + comb <= a) lo += comb;
+            plo = lo;
+            phi = lo == a ? lo : lo + comb;
         }
-        H[idx] = h;
+        const T vlo = __ldg(&tab[(long long)((plo - port) / comb) * units]);
+        const T vhi = __ldg(&tab[(long long)((phi - port) / comb) * units]);
+        *out = lerp_unit(vlo, vhi, interp_weight(a, plo, phi));
     }
 }
 
 // LS estimate at every pilot subcarrier of every layer (the element-wise division alone):
 // ls[slot][l][k][b] for the layer's k-th pilot q = port[l] + k * comb (k < kmax; zero past n_sc).
 __global__ void __launch_bounds__(256)
-ls_pilots_kernel(ChestArgs g, int kmax, long long total, const float2 *__restrict__ beam,
-                 const float2 *__restrict__ pilots, float2 *__restrict__ ls) {
-    const long long per_l = (long long)kmax * g.n_beams;
-    const long long per_slot = per_l * g.n_layers;
-    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const long long slot = idx / per_slot;
-        long long rem = idx - slot * per_slot;
-        const int l = (int)(rem / per_l);
-        rem -= (long long)l * per_l;
-        const int k = (int)(rem / g.n_beams);
-        const int b = (int)(rem - (long long)k * g.n_beams);
-        const int q = g.port[l] + k * g.comb;
-        float2 v = make_float2(0.f, 0.f);
-        if (q < g.n_sc) {
-            const float2 *y0 = beam + (slot * g.n_sym + g.dmrs0) * (long long)g.n_sc * g.n_beams;
-            const float2 *y1 = beam + (slot * g.n_sym + g.dmrs1) * (long long)g.n_sc * g.n_beams;
-            const float2 *p0 = pilots + (slot * g.n_layers + l) * 2LL * g.n_sc;
-            v = ls_value(__ldg(&y0[(long long)q * g.n_beams + b]), __ldg(&y1[(long long)q * g.n_beams + b]),
-                         pilot_inverse(__ldg(&p0[q])), pilot_inverse(__ldg(&p0[g.n_sc + q])));
-        }
-        ls[idx] = v;
+ls_pilots_kernel(ChestArgs g, int kmax, const float2 *__restrict__ beam, const float2 *__restrict__ pilots,
+                 float2 *__restrict__ ls) {
+    // grid.y = slot * n_layers + l, grid.x: chunks of the layer's kmax * n_beams (pilot, beam) elements
+    const long long sl = blockIdx.y;
+    const long long slot = sl / g.n_layers;
+    const int l = (int)(sl - slot * g.n_layers);
+    const int per_l = kmax * g.n_beams;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= per_l) return;
+    const int k = idx / g.n_beams, b = idx - k * g.n_beams;
+    const int q = g.port[l] + k * g.comb;
+    float2 v = make_float2(0.f, 0.f);
+    if (q < g.n_sc) {
+        const float2 *y0 = beam + (slot * g.n_sym + g.dmrs0) * (long long)g.n_sc * g.n_beams;
+        const float2 *y1 = beam + (slot * g.n_sym + g.dmrs1) * (long long)g.n_sc * g.n_beams;
+        const float2 *p0 = pilots + sl * 2LL * g.n_sc;
+        v = ls_value(__ldg(&y0[(long long)q * g.n_beams + b]), __ldg(&y1[(long long)q * g.n_beams + b]),
+                     pilot_inverse(__ldg(&p0[q])), pilot_inverse(__ldg(&p0[g.n_sc + q])));
     }
+    ls[sl * per_l + idx] = v;
 }
 
 // Noise-variance estimate (Section II "NE"), pass 1: CTA (part, slot) sums the squared pilot residuals
@@ -86,15 +100,15 @@ ne_partial_kernel(ChestArgs g, int kmax, const float2 *__restrict__ beam, const 
                   float2 *__restrict__ partial) {
     __shared__ float2 red[8];
     const long long slot = blockIdx.y;
-    const long long per_slot = (long long)g.n_layers * kmax * g.n_beams;
+    const int per_l = kmax * g.n_beams;                     // < 2^31: n_sc <= 4096, n_beams <= 64
+    const int per_slot = g.n_layers * per_l;
     const float2 *y0 = beam + (slot * g.n_sym + g.dmrs0) * (long long)g.n_sc * g.n_beams;
     const float2 *y1 = beam + (slot * g.n_sym + g.dmrs1) * (long long)g.n_sc * g.n_beams;
     float sum = 0.f, cnt = 0.f;
-    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < per_slot;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const int l = (int)(idx / ((long long)kmax * g.n_beams));
-        const long long rem = idx - (long long)l * kmax * g.n_beams;
-        const int k = (int)(rem / g.n_beams), b = (int)(rem - (long long)k * g.n_beams);
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < per_slot; idx += gridDim.x * blockDim.x) {
+        const int l = idx / per_l;
+        const int rem = idx - l * per_l;
+        const int k = rem / g.n_beams, b = rem - k * g.n_beams;
         const int q = g.port[l] + k * g.comb;
         if (q >= g.n_sc) continue;
         const float2 *p0 = pilots + (slot * g.n_layers + l) * 2LL * g.n_sc;
@@ -170,16 +184,15 @@ cudaError_t launch_ls_pilots(const Geometry &g, int n_slots, const float2 *beam,
     a.dmrs1 = g.dmrs1;
     for (int l = 0; l < 32; ++l) a.port[l] = g.port[l];
     const int kmax = ls_pilots_per_layer(g);
-    const long long total = (long long)n_slots * g.n_layers * kmax * g.n_beams;
-    if (total == 0) return cudaSuccess;
-    long long blocks = (total + 255) / 256;
-    if (blocks > 152LL * 32) blocks = 152LL * 32;
-    ls_pilots_kernel<<<(unsigned)blocks, 256, 0, st>>>(a, kmax, total, beam, pilots, ls);
+    const long long rows = (long long)n_slots * g.n_layers;
+    if (rows == 0) return cudaSuccess;
+    if (rows > 65535) return cudaErrorInvalidValue;   // grid.y; n_slots * n_layers per call
+    const int per_l = kmax * g.n_beams;
+    ls_pilots_kernel<<<dim3((unsigned)((per_l + 255) / 256), (unsigned)rows), 256, 0, st>>>(a, kmax, beam, pilots, ls);
     return cudaGetLastError();
 }
 
-cudaError_t launch_chest_ls(const Geometry &g, int n_slots, const float2 *beam, const float2 *pilots, float2 *H,
-                            cudaStream_t st) {
+cudaError_t launch_chest_interp(const Geometry &g, int n_slots, const float2 *ls, float2 *H, cudaStream_t st) {
     ChestArgs a;
     a.n_sc = g.n_sc;
     a.n_beams = g.n_beams;
@@ -189,12 +202,27 @@ cudaError_t launch_chest_ls(const Geometry &g, int n_slots, const float2 *beam, 
     a.dmrs0 = g.dmrs0;
     a.dmrs1 = g.dmrs1;
     for (int l = 0; l < 32; ++l) a.port[l] = g.port[l];
-    const long long total = (long long)n_slots * g.n_sc * g.n_layers * g.n_beams;
-    if (total == 0) return cudaSuccess;
-    long long blocks = (total + 255) / 256;
-    if (blocks > 152LL * 64) blocks = 152LL * 64;
-    chest_ls_kernel<<<(unsigned)blocks, 256, 0, st>>>(a, total, beam, pilots, H);
+    if ((long long)n_slots * g.n_sc == 0) return cudaSuccess;
+    if (n_slots > 65535) return cudaErrorInvalidValue;                 // grid.y
+    const int kmax = ls_pilots_per_layer(g);
+    const bool pairs = (g.n_beams & 1) == 0;
+    const int units = pairs ? g.n_beams / 2 : g.n_beams;
+    const int lpc = std::min(g.n_layers, 1024 / units);                  // layers per CTA (units <= 64)
+    const dim3 grid((unsigned)((g.n_sc + kRun - 1) / kRun), (unsigned)n_slots, (unsigned)((g.n_layers + lpc - 1) / lpc));
+    const int threads = lpc * units;
+    if (pairs)
+        chest_interp_kernel<float4><<<grid, threads, 0, st>>>(a, kmax, units, lpc, reinterpret_cast<const float4 *>(ls),
+                                                              reinterpret_cast<float4 *>(H));
+    else
+        chest_interp_kernel<float2><<<grid, threads, 0, st>>>(a, kmax, units, lpc, ls, H);
     return cudaGetLastError();
+}
+
+cudaError_t launch_chest_ls(const Geometry &g, int n_slots, const float2 *beam, const float2 *pilots, float2 *H,
+                            float2 *ls_scratch, cudaStream_t st) {
+    cudaError_t e = launch_ls_pilots(g, n_slots, beam, pilots, ls_scratch, st);
+    if (e != cudaSuccess) return e;
+    return launch_chest_interp(g, n_slots, ls_scratch, H, st);
 }
 
 }  // namespace pusch

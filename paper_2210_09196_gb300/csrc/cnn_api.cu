@@ -100,7 +100,8 @@ pusch_status pusch_chest_cnn(pusch_handle *h, int n_slots, const void *beam, con
     }
     cudaStream_t s = (cudaStream_t)stream;
     const int grids = n_slots * g.n_layers * g.n_beams;
-    if ((e = pusch::launch_chest_ls(g, n_slots, (const float2 *)beam, (const float2 *)pilots, (float2 *)H_hat, s)) !=
+    if ((e = pusch::launch_chest_ls(g, n_slots, (const float2 *)beam, (const float2 *)pilots, (float2 *)H_hat, h->ls,
+                                    s)) !=
         cudaSuccess)
         return cfail(PUSCH_ERR_CUDA, "plain LS launch", e);
     if ((e = pusch::launch_ls_grid(g, n_slots, (const float2 *)beam, (const float2 *)pilots,

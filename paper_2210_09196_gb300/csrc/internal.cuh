@@ -81,8 +81,10 @@ cudaError_t launch_fft(const Geometry &g, int n_slots, const void *time_in, void
                        uint32_t *err, cudaStream_t st);
 cudaError_t launch_beamform_fp32(const Geometry &g, int n_slots, const float2 *freq, const float2 *W, float2 *beam,
                                  cudaStream_t st);
+// The full LS estimate (pilot table into ls_scratch, then interpolation); ls_scratch holds
+// n_slots * n_layers * ls_pilots_per_layer(g) * n_beams float2.
 cudaError_t launch_chest_ls(const Geometry &g, int n_slots, const float2 *beam, const float2 *pilots, float2 *H,
-                            cudaStream_t st);
+                            float2 *ls_scratch, cudaStream_t st);
 // sigma2 (optional, device, one float per slot): per-slot noise variance replacing g.noise_var.
 cudaError_t launch_mmse(const Geometry &g, int n_slots, const float2 *H, const float2 *beam, float2 *x_hat,
                         uint8_t *bits, uint32_t *status, cudaStream_t st, const float *sigma2 = nullptr);
@@ -90,6 +92,8 @@ cudaError_t launch_mmse(const Geometry &g, int n_slots, const float2 *H, const f
 int ls_pilots_per_layer(const Geometry &g);
 cudaError_t launch_ls_pilots(const Geometry &g, int n_slots, const float2 *beam, const float2 *pilots, float2 *ls,
                              cudaStream_t st);
+// The full estimate H [slots][n_sc][n_layers][n_beams] interpolated from the LS pilot table.
+cudaError_t launch_chest_interp(const Geometry &g, int n_slots, const float2 *ls, float2 *H, cudaStream_t st);
 // Noise-variance estimate per slot from the pilot residuals (Section II "NE"): partial needs
 // n_slots * kNoiseParts float2 of scratch; sigma2 receives one float per slot.
 constexpr int kNoiseParts = 64;
@@ -159,6 +163,7 @@ struct pusch_handle {
     void *freq = nullptr;           // workspace: FFT output
     float2 *beam = nullptr;         // workspace: beamformed grid
     float2 *ls = nullptr;           // workspace: LS values at the pilot subcarriers
+    float2 *H = nullptr;            // workspace: the interpolated estimate (pusch_slot)
     uint32_t *status_sink = nullptr;  // status words used when the caller passes NULL
     float2 *ne_partial = nullptr;     // noise estimation: per (slot, part) partial sums
     float *sigma2 = nullptr;          // noise estimation: per-slot estimate (read by the detector in estimate mode)

@@ -87,9 +87,10 @@ extern "C" pusch_status pusch_slot_noalloc(const pusch_cell_cfg *cfg, int n_slot
     const size_t freq_b = up256(pusch::freq_bytes_of(g, n_slots));
     const size_t beam_b = up256((size_t)n_slots * g.n_sym * g.n_sc * g.n_beams * sizeof(float2));
     const size_t H_b = up256((size_t)n_slots * g.n_sc * g.n_layers * g.n_beams * sizeof(float2));
+    const size_t ls_b = up256((size_t)n_slots * g.n_layers * pusch::ls_pilots_per_layer(g) * g.n_beams * sizeof(float2));
     const bool est = cfg->noise_var == PUSCH_NOISE_ESTIMATE;
     const size_t ne_b = est ? up256((size_t)n_slots * (pusch::kNoiseParts * sizeof(float2) + sizeof(float))) : 0;
-    const size_t need = tw_b + words_b + freq_b + beam_b + H_b + ne_b;
+    const size_t need = tw_b + words_b + freq_b + beam_b + H_b + ls_b + ne_b;
     if (need > (size_t)PUSCH_NOALLOC_SCRATCH_BYTES) {
         char buf[512];
         snprintf(buf, sizeof buf,
@@ -107,7 +108,8 @@ extern "C" pusch_status pusch_slot_noalloc(const pusch_cell_cfg *cfg, int n_slot
     void *freq = base + tw_b + words_b;
     float2 *beam = reinterpret_cast<float2 *>(base + tw_b + words_b + freq_b);
     float2 *H = reinterpret_cast<float2 *>(base + tw_b + words_b + freq_b + beam_b);
-    float2 *ne_partial = reinterpret_cast<float2 *>(base + tw_b + words_b + freq_b + beam_b + H_b);
+    float2 *lsw = reinterpret_cast<float2 *>(base + tw_b + words_b + freq_b + beam_b + H_b);
+    float2 *ne_partial = reinterpret_cast<float2 *>(base + tw_b + words_b + freq_b + beam_b + H_b + ls_b);
     float *sigma2 = reinterpret_cast<float *>(ne_partial + (size_t)n_slots * pusch::kNoiseParts);
     uint32_t *stat = status ? status : sink;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -120,7 +122,7 @@ extern "C" pusch_status pusch_slot_noalloc(const pusch_cell_cfg *cfg, int n_slot
         return na_fail(PUSCH_ERR_CUDA, "pusch_slot_noalloc fft launch", e);
     e = pusch::launch_beamform(g, n_slots, freq, static_cast<const float2 *>(W), beam, tc_err, s);
     if (e != cudaSuccess) return na_fail(PUSCH_ERR_CUDA, "pusch_slot_noalloc beamforming launch", e);
-    if ((e = pusch::launch_chest_ls(g, n_slots, beam, static_cast<const float2 *>(pilots), H, s)) != cudaSuccess)
+    if ((e = pusch::launch_chest_ls(g, n_slots, beam, static_cast<const float2 *>(pilots), H, lsw, s)) != cudaSuccess)
         return na_fail(PUSCH_ERR_CUDA, "pusch_slot_noalloc channel estimation launch", e);
     if (est && (e = pusch::launch_noise_est(g, n_slots, beam, static_cast<const float2 *>(pilots), ne_partial, sigma2,
                                             s)) != cudaSuccess)

@@ -76,7 +76,8 @@ def test_noise_estimate_mode_is_accepted(B):
 def test_workspace_size(B):
     cfg = _good()
     n = B.pusch_workspace_size(cfg, 2)
-    per_slot = 14 * 16 * 300 * 8 + 14 * 300 * 16 * 8 + 4 * 75 * 16 * 8  # FFT out + beams + LS pilot table
+    # FFT out + beams + LS pilot table + interpolated estimate
+    per_slot = 14 * 16 * 300 * 8 + 14 * 300 * 16 * 8 + 4 * 75 * 16 * 8 + 300 * 4 * 16 * 8
     assert n >= 2 * per_slot and n < 2 * per_slot + 64 * 1024
 
 
