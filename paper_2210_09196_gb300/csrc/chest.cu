@@ -36,34 +36,34 @@ template <typename T>
 __global__ void __launch_bounds__(1024)
 chest_interp_kernel(ChestArgs g, int kmax, int units, int layers_per_cta, const T *__restrict__ ls,
                     T *__restrict__ H) {
+    __shared__ int s_klo[kRun][32], s_khi[kRun][32];
+    __shared__ float s_w[kRun][32];
     const int t = threadIdx.x;
-    const int l = blockIdx.z * layers_per_cta + t / units, u = t - (t / units) * units;
-    if (l >= g.n_layers) return;
+    const int l_base = blockIdx.z * layers_per_cta;
+    const int n_l = min(layers_per_cta, g.n_layers - l_base);
     const long long slot = blockIdx.y;
     const int a0 = blockIdx.x * kRun;
-    const int port = g.port[l], comb = g.comb;
-    const int first = port, last = port + ((g.n_sc - 1 - port) / comb) * comb;
-    int lo = a0 <= first ? first : port + ((min(a0, last) - port) / comb) * comb;   // pilot at or below a0
+    // 1. the run's (subcarrier, layer) brackets: table indices of the neighbouring pilots and the weight
+    for (int e = t; e < kRun * n_l; e += blockDim.x) {
+        const int r = e / n_l, ll = e - r * n_l, l = l_base + ll;
+        const int a = min(a0 + r, g.n_sc - 1);
+        int lo, hi;
+        pilot_bracket(a, g.port[l], g.comb, g.n_sc, lo, hi);
+        s_klo[r][ll] = (lo - g.port[l]) / g.comb;
+        s_khi[r][ll] = (hi - g.port[l]) / g.comb;
+        s_w[r][ll] = interp_weight(a, lo, hi);
+    }
+    __syncthreads();
+    // 2. thread (layer, unit) writes its unit of every subcarrier of the run
+    const int ll = t / units, u = t - ll * units;
+    if (ll >= n_l) return;
+    const int l = l_base + ll;
     const T *tab = ls + ((slot * g.n_layers + l) * (long long)kmax) * units + u;
     T *out = H + ((slot * g.n_sc + a0) * g.n_layers + l) * (long long)units + u;
     const long long stride = (long long)g.n_layers * units;
-    for (int r = 0; r < kRun; ++r, out += stride) {
-        const int a = a0 + r;
-        if (a >= g.n_sc) break;
-        int plo, phi;
-        if (a <= first) {
-            plo = phi = first;
-        } else if (a >= last) {
-            plo = phi = last;
-        } else {
-            while (lo + comb <= a) lo += comb;
-            plo = lo;
-            phi = lo == a ? lo : lo + comb;
-        }
-        const T vlo = __ldg(&tab[(long long)((plo - port) / comb) * units]);
-        const T vhi = __ldg(&tab[(long long)((phi - port) / comb) * units]);
-        *out = lerp_unit(vlo, vhi, interp_weight(a, plo, phi));
-    }
+    const int rn = min(kRun, g.n_sc - a0);
+    for (int r = 0; r < rn; ++r, out += stride)
+        *out = lerp_unit(__ldg(&tab[s_klo[r][ll] * units]), __ldg(&tab[s_khi[r][ll] * units]), s_w[r][ll]);
 }
 
 // LS estimate at every pilot subcarrier of every layer (the element-wise division alone):
