@@ -102,19 +102,29 @@ mmse_kernel(MmseArgs g, long long total_sc, const float2 *__restrict__ H, const 
     //         by lane e % 32; (row, b) advance incrementally (no division in the loop).
     const int rows = SPW * NL;
     if constexpr (!FUSED) {
-        int r = lane / nb, b = lane - (lane / nb) * nb;
-        const int step_r = 32 / nb, step_b = 32 - (32 / nb) * nb;
+        // 16-byte pieces (two beams) when the beam count is even, 8-byte pieces otherwise
+        const bool wide = (nb & 1) == 0;
+        const int cpr = wide ? nb >> 1 : nb;  // pieces per row
+        int r = lane / cpr, c = lane - (lane / cpr) * cpr;
+        const int step_r = 32 / cpr, step_c = 32 - (32 / cpr) * cpr;
         for (; r < rows;) {
             const int gg = r / NL, l = r - gg * NL;  // NL is a power of two
+            const int b = wide ? 2 * c : c;
             float2 *dst = Ht + gg * ht + l * hs + b;
-            if (l < nl && sc0 + gg < total_sc)
-                cp_async8(dst, H + ((sc0 + gg) * nl + l) * (long long)nb + b);
-            else
-                *dst = make_float2(0.f, 0.f);
+            if (l < nl && sc0 + gg < total_sc) {
+                const float2 *src = H + ((sc0 + gg) * nl + l) * (long long)nb + b;
+                if (wide)
+                    cp_async16(dst, src);
+                else
+                    cp_async8(dst, src);
+            } else {
+                dst[0] = make_float2(0.f, 0.f);
+                if (wide) dst[1] = make_float2(0.f, 0.f);
+            }
             r += step_r;
-            b += step_b;
-            if (b >= nb) {
-                b -= nb;
+            c += step_c;
+            if (c >= cpr) {
+                c -= cpr;
                 ++r;
             }
         }
