@@ -59,6 +59,8 @@ def lib():
             "orc_op_counts": (None, [I, I, I, I, I, I, P]),
             "orc_slot": (I, [P, I, I, I, I, P, I, P, I, P, P, I, I, D, D, P, P]),
             "orc_noise_est": (D, [P, I, I, I, P, I, P, P, I]),
+            "orc_chest_ls_sym": (I, [P, I, I, I, P, I, P, P, I, I, P]),
+            "orc_mmse_tv": (I, [P, P, P, I, I, I, P, P, I, D, D, I, P]),
             "orc_e4m3_round": (D, [D]),
             "orc_e4m3_round_array": (None, [P, LL, P]),
             "orc_e4m3_block_exp": (I, [D]),
@@ -193,6 +195,31 @@ def mmse(H, beam, noise_var: float, loading: float = 0.0, sc_list=None, data_sym
         sl = _i32(sc_list)
         fails = lib().orc_mmse(_p(H), _p(beam), n_sc, B, L, _p(ds), ds.size, noise_var, loading, _p(sl), sl.size,
                                _p(xhat))
+    return xhat, int(fails)
+
+
+def chest_ls_sym(beam, pilots, ports, comb: int, j: int, dmrs=DMRS_SYMBOLS) -> np.ndarray:
+    """The estimate of DMRS symbol j alone: beam [S, N_SC, B], pilots [L, 2, N_SC] -> H [N_SC, L, B]."""
+    beam, pilots = _c128(beam), _c128(pilots)
+    S, n_sc, B = beam.shape
+    L = pilots.shape[0]
+    H = np.zeros((n_sc, L, B), dtype=np.complex128)
+    rc = lib().orc_chest_ls_sym(_p(beam), S, n_sc, B, _p(_i32(dmrs)), L, _p(pilots), _p(_i32(ports)), comb, int(j),
+                                _p(H))
+    if rc != 0:
+        raise ValueError(f"orc_chest_ls_sym: layer {-rc - 1} has no pilot")
+    return H
+
+
+def mmse_tv(H0, H1, beam, noise_var: float, K: int, loading: float = 0.0, dmrs=DMRS_SYMBOLS, data_sym=None):
+    """Eq. 2 with the estimate interpolated in time between the DMRS symbols and factorised every K data
+    symbols -> (xhat [L, n_data, N_SC], n_failed)."""
+    H0, H1, beam = _c128(H0), _c128(H1), _c128(beam)
+    n_sc, L, B = H0.shape
+    ds = data_symbols(beam.shape[0], dmrs) if data_sym is None else _i32(data_sym)
+    xhat = np.zeros((L, ds.size, n_sc), dtype=np.complex128)
+    fails = lib().orc_mmse_tv(_p(H0), _p(H1), _p(beam), n_sc, B, L, _p(_i32(dmrs)), _p(ds), ds.size, noise_var,
+                              loading, int(K), _p(xhat))
     return xhat, int(fails)
 
 

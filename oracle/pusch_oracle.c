@@ -23,6 +23,8 @@
  *   orc_demap       Gray hard decisions of 3GPP TS 38.211 5.1.3/5.1.4 (QPSK/16-QAM).
  *   orc_op_counts   Table I complex-MAC model.
  *   orc_noise_est   Section II "NE": noise variance from the pilot residual y - H_hat p.
+ *   orc_chest_ls_sym, orc_mmse_tv  the estimate of one DMRS symbol, and Eq. 2 with the estimate interpolated
+ *                   in time and factorised every K data symbols (Section VI's schedule).
  *   orc_e4m3_*,     the FP8 precision form of the beamforming step (not in the paper; the form this
  *   orc_beamform_fp8  project adds): E4M3 rounding, power-of-two block scales, and the block-scaled
  *                   product y = W^H x with its exact power-of-two alignment.
@@ -145,11 +147,13 @@ void orc_beamform(const cplx *freq, const cplx *W, int n_sym, int n_rx, int n_sc
  * Subcarriers outside the range are left untouched.
  * Returns 0, or -(l+1) when layer l has no pilot in its range.
  */
-int orc_chest_ls(const cplx *beam, int n_sym, int n_sc, int n_beams, const int *dmrs_sym,
-                 int n_layers, const cplx *pilots, const int *port, int comb,
-                 const int *sc_start, const int *sc_count, cplx *H)
+/* LS estimate with DMRS-symbol weights wj[2]: at a pilot q, sum_j wj[j] y_j[q] / p_j[q], then frequency
+ * interpolation. wj = {1/2, 1/2} is the two-symbol mean (orc_chest_ls); {1, 0} and {0, 1} are the estimates of
+ * one DMRS symbol alone (orc_chest_ls_sym). */
+static int chest_ls_weighted(const cplx *beam, int n_sc, int n_beams, const int *dmrs_sym, int n_layers,
+                             const cplx *pilots, const int *port, int comb, const int *sc_start, const int *sc_count,
+                             const double *wj, cplx *H)
 {
-    (void)n_sym;
     for (int l = 0; l < n_layers; ++l) {
         int a0 = sc_start[l], a1 = sc_start[l] + sc_count[l];
         int first = -1, last = -1;
@@ -176,8 +180,8 @@ int orc_chest_ls(const cplx *beam, int n_sym, int n_sc, int n_beams, const int *
                 for (int j = 0; j < 2; ++j) {
                     const cplx *y = beam + (size_t)dmrs_sym[j] * n_sc * n_beams;
                     const cplx *p = pilots + ((size_t)l * 2 + j) * n_sc;
-                    ls_lo += 0.5 * y[(size_t)lo * n_beams + b] / p[lo];
-                    ls_hi += 0.5 * y[(size_t)hi * n_beams + b] / p[hi];
+                    ls_lo += wj[j] * y[(size_t)lo * n_beams + b] / p[lo];
+                    ls_hi += wj[j] * y[(size_t)hi * n_beams + b] / p[hi];
                 }
                 cplx h = ls_lo;
                 if (hi != lo) h = ls_lo + ((double)(a - lo) / (double)(hi - lo)) * (ls_hi - ls_lo);
@@ -186,6 +190,32 @@ int orc_chest_ls(const cplx *beam, int n_sym, int n_sc, int n_beams, const int *
         }
     }
     return 0;
+}
+
+int orc_chest_ls(const cplx *beam, int n_sym, int n_sc, int n_beams, const int *dmrs_sym,
+                 int n_layers, const cplx *pilots, const int *port, int comb,
+                 const int *sc_start, const int *sc_count, cplx *H)
+{
+    (void)n_sym;
+    const double w[2] = {0.5, 0.5};
+    return chest_ls_weighted(beam, n_sc, n_beams, dmrs_sym, n_layers, pilots, port, comb, sc_start, sc_count, w, H);
+}
+
+/* The LS estimate of DMRS symbol j (0 or 1) alone: y_j[q] / p_j[q] at the pilots, frequency interpolation. */
+int orc_chest_ls_sym(const cplx *beam, int n_sym, int n_sc, int n_beams, const int *dmrs_sym, int n_layers,
+                     const cplx *pilots, const int *port, int comb, int j, cplx *H)
+{
+    (void)n_sym;
+    const double w[2] = {j == 0 ? 1.0 : 0.0, j == 0 ? 0.0 : 1.0};
+    int *st = malloc(sizeof(int) * (size_t)n_layers), *ct = malloc(sizeof(int) * (size_t)n_layers);
+    for (int l = 0; l < n_layers; ++l) {
+        st[l] = 0;
+        ct[l] = n_sc;
+    }
+    int rc = chest_ls_weighted(beam, n_sc, n_beams, dmrs_sym, n_layers, pilots, port, comb, st, ct, w, H);
+    free(st);
+    free(ct);
+    return rc;
 }
 
 /* Noise-variance estimate, Section II "NE": the autocorrelation (mean squared magnitude) of the difference
@@ -336,6 +366,41 @@ int orc_mmse(const cplx *H, const cplx *beam, int n_sc, int n_beams, int n_layer
     free(L);
     free(r);
     free(x);
+    return fails;
+}
+
+/*
+ * Eq. 2 with a time-varying estimate and the factorisation scheduled every K data symbols (Section VI: one
+ * Cholesky per data symbol in Table I's accounting, or every 4 data symbols). H0, H1: the estimates of the two
+ * DMRS symbols s0 = dmrs_sym[0], s1 = dmrs_sym[1] alone (orc_chest_ls_sym). Data symbol s has the estimate
+ * H(s) = H0 + (s - s0) / (s1 - s0) (H1 - H0) (linear in time, extrapolated outside [s0, s1]). The data symbols,
+ * in increasing order, are taken in groups of K (the last group may be shorter); a group uses H at the mean
+ * time of its symbols for all of them, one Gram and one factorisation per subcarrier. K = 1: per data symbol.
+ * xhat [n_layers][n_data][n_sc] as orc_mmse; returns the number of failed factorisations.
+ */
+int orc_mmse_tv(const cplx *H0, const cplx *H1, const cplx *beam, int n_sc, int n_beams, int n_layers,
+                const int *dmrs_sym, const int *data_sym, int n_data, double noise_var, double loading, int K,
+                cplx *xhat)
+{
+    size_t nh = (size_t)n_sc * n_layers * n_beams;
+    cplx *Hg = malloc(sizeof(cplx) * nh);
+    cplx *xg = malloc(sizeof(cplx) * (size_t)n_layers * K * n_sc);
+    int fails = 0;
+    double span = (double)(dmrs_sym[1] - dmrs_sym[0]);
+    for (int g0 = 0; g0 < n_data; g0 += K) {
+        int ng = n_data - g0 < K ? n_data - g0 : K;
+        double t = 0.0;
+        for (int d = g0; d < g0 + ng; ++d) t += (double)(data_sym[d] - dmrs_sym[0]) / span;
+        t /= ng;
+        for (size_t e = 0; e < nh; ++e) Hg[e] = H0[e] + t * (H1[e] - H0[e]);
+        fails += orc_mmse(Hg, beam, n_sc, n_beams, n_layers, data_sym + g0, ng, noise_var, loading, NULL, 0, xg);
+        for (int l = 0; l < n_layers; ++l)
+            for (int d = 0; d < ng; ++d)
+                for (int a = 0; a < n_sc; ++a)
+                    xhat[((size_t)l * n_data + g0 + d) * n_sc + a] = xg[((size_t)l * ng + d) * n_sc + a];
+    }
+    free(Hg);
+    free(xg);
     return fails;
 }
 
