@@ -83,6 +83,13 @@ typedef struct {
     int dmrs_sym[2];   /* the two DMRS (pilot) symbols, e.g. {2, 11}                             */
     float noise_var;   /* sigma^2 of Eq. 2, or PUSCH_NOISE_ESTIMATE: estimated per slot from the pilots  */
     float loading;     /* extra diagonal loading added to sigma^2 (0 = the plain Eq. 2)          */
+    int chol_every;    /* 0: one estimate per slot (mean of the two DMRS symbols), one factorisation per
+                          subcarrier. K in [1, n_sym - 2] (pusch_slot only): the estimate of each DMRS
+                          symbol is kept apart and interpolated linearly in time, the data symbols are
+                          taken in increasing order in groups of K, and each group is detected with the
+                          estimate at its mean symbol time and one factorisation per subcarrier (K = 1:
+                          one per data symbol, Section VI's schedule; K = n_sym - 2 gives the 0 result
+                          up to rounding)                                                          */
 } pusch_cell_cfg;
 
 /* noise_var value that makes the chain estimate sigma^2 per slot (pusch_noise_estimate) instead of using a

@@ -58,6 +58,7 @@ class pusch_cell_cfg(ctypes.Structure):
         ("n_layers", ctypes.c_int), ("comb", ctypes.c_int), ("port", ctypes.c_int * 32),
         ("qam_bits", ctypes.c_int), ("in_fp16", ctypes.c_int), ("form", ctypes.c_int), ("n_sym", ctypes.c_int),
         ("dmrs_sym", ctypes.c_int * 2), ("noise_var", ctypes.c_float), ("loading", ctypes.c_float),
+        ("chol_every", ctypes.c_int),
     ]
 
 
@@ -67,7 +68,8 @@ class pusch_user_desc(ctypes.Structure):
 
 
 def make_cfg(*, n_rx, n_fft, n_sc, n_beams, n_layers, comb=None, ports=None, qam_bits=2, in_fp16=False,
-             form=PUSCH_FORM_FP32, noise_var=0.0, loading=0.0, n_sym=14, dmrs_sym=(2, 11)) -> pusch_cell_cfg:
+             form=PUSCH_FORM_FP32, noise_var=0.0, loading=0.0, n_sym=14, dmrs_sym=(2, 11),
+             chol_every=0) -> pusch_cell_cfg:
     c = pusch_cell_cfg()
     c.n_rx, c.n_fft, c.n_sc, c.n_beams, c.n_layers = n_rx, n_fft, n_sc, n_beams, n_layers
     c.comb = n_layers if comb is None else comb
@@ -77,6 +79,7 @@ def make_cfg(*, n_rx, n_fft, n_sc, n_beams, n_layers, comb=None, ports=None, qam
     c.qam_bits, c.in_fp16, c.form, c.n_sym = qam_bits, int(bool(in_fp16)), int(form), n_sym
     c.dmrs_sym[0], c.dmrs_sym[1] = dmrs_sym
     c.noise_var, c.loading = float(noise_var), float(loading)
+    c.chol_every = int(chol_every)
     return c
 
 

@@ -59,6 +59,8 @@ pusch_status validate_cfg(const pusch_cell_cfg *c) {
     if (c->noise_var != PUSCH_NOISE_ESTIMATE && (!(c->noise_var >= 0.f) || !isfinite(c->noise_var)))
         return fail(PUSCH_ERR_ARG, "noise_var must be >= 0 or PUSCH_NOISE_ESTIMATE");
     if (!(c->loading >= 0.f) || !isfinite(c->loading)) return fail(PUSCH_ERR_ARG, "loading must be >= 0");
+    if (c->chol_every < 0 || c->chol_every > c->n_sym - 2)
+        return fail(PUSCH_ERR_ARG, "chol_every=%d out of [0, n_sym - 2]", c->chol_every);
     if (c->form == PUSCH_FORM_MIXED) {
         pusch::Geometry g = pusch::make_geometry(*c);
         if (!pusch::bf_tc_supported(g))
@@ -80,7 +82,9 @@ size_t beam_bytes(const pusch::Geometry &g, int n_slots) {
     return (size_t)n_slots * g.n_sym * g.n_sc * g.n_beams * sizeof(float2);
 }
 size_t ls_bytes(const pusch::Geometry &g, int n_slots) {
-    return (size_t)n_slots * g.n_layers * pusch::ls_pilots_per_layer(g) * g.n_beams * sizeof(float2);
+    // one table (the two-symbol mean), or one per DMRS symbol when the estimate varies in time
+    return (g.chol_every > 0 ? 2 : 1) * (size_t)n_slots * g.n_layers * pusch::ls_pilots_per_layer(g) * g.n_beams *
+           sizeof(float2);
 }
 size_t time_bytes(const pusch::Geometry &g, int n_slots) {
     return (size_t)n_slots * g.n_sym * g.n_rx * g.n_fft * (g.in_fp16 ? 4 : 8);
@@ -94,7 +98,7 @@ size_t xhat_count(const pusch::Geometry &g, int n_slots) {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 size_t H_bytes(const pusch::Geometry &g, int n_slots) {
-    return (size_t)n_slots * g.n_sc * g.n_layers * g.n_beams * sizeof(float2);
+    return (size_t)g.n_groups * n_slots * g.n_sc * g.n_layers * g.n_beams * sizeof(float2);
 }
 
 size_t workspace_bytes(const pusch::Geometry &g, int max_slots) {
@@ -149,12 +153,23 @@ Geometry make_geometry(const pusch_cell_cfg &c) {
     g.dmrs1 = c.dmrs_sym[1];
     g.noise_var = c.noise_var;
     g.loading = c.loading;
+    g.chol_every = c.chol_every;
     g.sc_pitch = c.form == PUSCH_FORM_FP8 ? (c.n_sc + 15) & ~15 : (c.n_sc + 7) & ~7;
     for (int l = 0; l < 32; ++l) g.port[l] = l < c.n_layers ? c.port[l] : 0;
     int nd = 0;
     for (int s = 0; s < c.n_sym; ++s)
         if (s != g.dmrs0 && s != g.dmrs1 && nd < 16) g.data_sym[nd++] = s;
     g.n_data = nd;
+    // detection groups: one (the two-symbol mean) or groups of chol_every data symbols at their mean time
+    const int K = c.chol_every > 0 ? c.chol_every : (nd > 0 ? nd : 1);
+    g.n_groups = c.chol_every > 0 ? (nd + K - 1) / K : 1;
+    for (int q = 0; q < g.n_groups && q < 16; ++q) {
+        double t = 0.0;
+        int cnt = 0;
+        for (int d = q * K; d < nd && d < (q + 1) * K; ++d, ++cnt)
+            t += (double)(g.data_sym[d] - g.dmrs0) / (double)(g.dmrs1 - g.dmrs0);
+        g.group_t[q] = cnt ? (float)(t / cnt) : 0.5f;
+    }
     return g;
 }
 
@@ -337,16 +352,27 @@ pusch_status pusch_slot(pusch_handle *h, int n_slots, const void *time_in, const
     if (ev) cudaEventRecord(ev[2], s);
     uint32_t *stat = status ? status : h->status_sink;
     if ((st = reset_status(stat, s)) != PUSCH_OK) return st;
-    cudaError_t e = pusch::launch_ls_pilots(h->geo, n_slots, h->beam, (const float2 *)pilots, h->ls, s);
-    if (e != cudaSuccess) return cuda_fail(e, "LS pilot table launch");
     const bool est = h->cfg.noise_var == PUSCH_NOISE_ESTIMATE;
+    const bool tv = h->geo.chol_every > 0;
+    cudaError_t e = cudaSuccess;
+    // the two-symbol-mean table: the estimate itself, or the noise estimator's reference when the estimate
+    // varies in time
+    if ((!tv || est) &&
+        (e = pusch::launch_ls_pilots(h->geo, n_slots, h->beam, (const float2 *)pilots, h->ls, s)) != cudaSuccess)
+        return cuda_fail(e, "LS pilot table launch");
     if (est && (e = pusch::launch_noise_est(h->geo, n_slots, h->beam, (const float2 *)pilots, h->ne_partial,
                                             h->sigma2, s)) != cudaSuccess)
         return cuda_fail(e, "noise estimation launch");
-    if ((e = pusch::launch_chest_interp(h->geo, n_slots, h->ls, h->H, s)) != cudaSuccess)
+    if (tv) {   // per-DMRS-symbol tables and one estimate per detection group
+        if ((e = pusch::launch_chest_time(h->geo, n_slots, h->beam, (const float2 *)pilots, h->H, h->ls, s)) !=
+            cudaSuccess)
+            return cuda_fail(e, "time-varying estimate launch");
+    } else if ((e = pusch::launch_chest_interp(h->geo, n_slots, h->ls, h->H, s)) != cudaSuccess) {
         return cuda_fail(e, "estimate interpolation launch");
+    }
     if (ev) cudaEventRecord(ev[3], s);
-    e = pusch::launch_mmse(h->geo, n_slots, h->H, h->beam, (float2 *)x_hat, bits, stat, s, est ? h->sigma2 : nullptr);
+    e = pusch::launch_mmse(h->geo, n_slots, h->H, h->beam, (float2 *)x_hat, bits, stat, s, est ? h->sigma2 : nullptr,
+                           tv);
     if (e != cudaSuccess) return cuda_fail(e, "detection launch");
     if (ev) cudaEventRecord(ev[4], s);
     return ok();

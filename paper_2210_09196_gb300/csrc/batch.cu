@@ -533,6 +533,8 @@ pusch_status pusch_batch_create(pusch_batch **out, const pusch_cell_cfg *cells, 
         size_t ws;
         pusch_status st = pusch_workspace_size(&cc, 1, &ws);
         if (st != PUSCH_OK) return st;
+        if (cells[c].chol_every != 0)
+            return bfail(PUSCH_ERR_UNSUPPORTED, "cell %d: the batch detects with one estimate per slot (chol_every 0)", c);
         if (cells[c].noise_var == PUSCH_NOISE_ESTIMATE)
             return bfail(PUSCH_ERR_UNSUPPORTED, "cell %d: the batch takes a given noise variance per cell", c);
         if (cells[c].in_fp16 != cells[0].in_fp16 || cells[c].form != cells[0].form ||

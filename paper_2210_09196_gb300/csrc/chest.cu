@@ -15,8 +15,25 @@ namespace {
 
 struct ChestArgs {
     int n_sc, n_beams, n_layers, comb, n_sym, dmrs0, dmrs1;
+    int n_groups;                  // estimates interpolated in time: one per detection group
+    float group_t[16];
     int port[32];
 };
+
+ChestArgs chest_args(const Geometry &g) {
+    ChestArgs a;
+    a.n_sc = g.n_sc;
+    a.n_beams = g.n_beams;
+    a.n_layers = g.n_layers;
+    a.comb = g.comb;
+    a.n_sym = g.n_sym;
+    a.dmrs0 = g.dmrs0;
+    a.dmrs1 = g.dmrs1;
+    a.n_groups = g.n_groups;
+    for (int q = 0; q < 16; ++q) a.group_t[q] = g.group_t[q];
+    for (int l = 0; l < 32; ++l) a.port[l] = g.port[l];
+    return a;
+}
 
 // The estimate H[slot][a][l][b] from the LS pilot table: linear interpolation between the layer's neighbouring
 // pilot subcarriers, held outside the first/last. CTA (subcarrier run, slot) covers kRun consecutive
@@ -32,10 +49,13 @@ __device__ __forceinline__ float4 lerp_unit(float4 lo, float4 hi, float w) {
 }
 __device__ __forceinline__ float2 lerp_unit(float2 lo, float2 hi, float w) { return interp(lo, hi, w); }
 
-template <typename T>
+// TV (time-varying mode): tab holds the two DMRS symbols' tables back to back (second at tab_stride units);
+// each unit's two frequency-interpolated values f0, f1 give the estimate of group q at its mean time,
+// f0 + t_q (f1 - f0), written to H + q * h_stride.
+template <typename T, bool TV>
 __global__ void __launch_bounds__(1024)
 chest_interp_kernel(ChestArgs g, int kmax, int units, int layers_per_cta, const T *__restrict__ ls,
-                    T *__restrict__ H) {
+                    long long tab_stride, T *__restrict__ H, long long h_stride) {
     __shared__ int s_klo[kRun][32], s_khi[kRun][32];
     __shared__ float s_w[kRun][32];
     const int t = threadIdx.x;
@@ -62,14 +82,22 @@ chest_interp_kernel(ChestArgs g, int kmax, int units, int layers_per_cta, const 
     T *out = H + ((slot * g.n_sc + a0) * g.n_layers + l) * (long long)units + u;
     const long long stride = (long long)g.n_layers * units;
     const int rn = min(kRun, g.n_sc - a0);
-    for (int r = 0; r < rn; ++r, out += stride)
-        *out = lerp_unit(__ldg(&tab[s_klo[r][ll] * units]), __ldg(&tab[s_khi[r][ll] * units]), s_w[r][ll]);
+    for (int r = 0; r < rn; ++r, out += stride) {
+        const T f0 = lerp_unit(__ldg(&tab[s_klo[r][ll] * units]), __ldg(&tab[s_khi[r][ll] * units]), s_w[r][ll]);
+        if constexpr (!TV) {
+            *out = f0;
+        } else {
+            const T *tab1 = tab + tab_stride;
+            const T f1 = lerp_unit(__ldg(&tab1[s_klo[r][ll] * units]), __ldg(&tab1[s_khi[r][ll] * units]), s_w[r][ll]);
+            for (int q = 0; q < g.n_groups; ++q) out[q * h_stride] = lerp_unit(f0, f1, g.group_t[q]);
+        }
+    }
 }
 
 // LS estimate at every pilot subcarrier of every layer (the element-wise division alone):
 // ls[slot][l][k][b] for the layer's k-th pilot q = port[l] + k * comb (k < kmax; zero past n_sc).
 __global__ void __launch_bounds__(256)
-ls_pilots_kernel(ChestArgs g, int kmax, const float2 *__restrict__ beam, const float2 *__restrict__ pilots,
+ls_pilots_kernel(ChestArgs g, int kmax, int sym, const float2 *__restrict__ beam, const float2 *__restrict__ pilots,
                  float2 *__restrict__ ls) {
     // grid.y = slot * n_layers + l, grid.x: chunks of the layer's kmax * n_beams (pilot, beam) elements
     const long long sl = blockIdx.y;
@@ -85,8 +113,12 @@ ls_pilots_kernel(ChestArgs g, int kmax, const float2 *__restrict__ beam, const f
         const float2 *y0 = beam + (slot * g.n_sym + g.dmrs0) * (long long)g.n_sc * g.n_beams;
         const float2 *y1 = beam + (slot * g.n_sym + g.dmrs1) * (long long)g.n_sc * g.n_beams;
         const float2 *p0 = pilots + sl * 2LL * g.n_sc;
-        v = ls_value(__ldg(&y0[(long long)q * g.n_beams + b]), __ldg(&y1[(long long)q * g.n_beams + b]),
-                     pilot_inverse(__ldg(&p0[q])), pilot_inverse(__ldg(&p0[g.n_sc + q])));
+        if (sym < 0)   // the mean of the two DMRS symbols
+            v = ls_value(__ldg(&y0[(long long)q * g.n_beams + b]), __ldg(&y1[(long long)q * g.n_beams + b]),
+                         pilot_inverse(__ldg(&p0[q])), pilot_inverse(__ldg(&p0[g.n_sc + q])));
+        else           // one DMRS symbol alone
+            v = cmul(__ldg(&(sym == 0 ? y0 : y1)[(long long)q * g.n_beams + b]),
+                     pilot_inverse(__ldg(&p0[(sym == 0 ? 0 : g.n_sc) + q])));
     }
     ls[sl * per_l + idx] = v;
 }
@@ -155,15 +187,7 @@ cudaError_t launch_noise_est(const Geometry &g, int n_slots, const float2 *beam,
                              float2 *partial, float *sigma2, cudaStream_t st) {
     if (n_slots == 0) return cudaSuccess;
     if (n_slots > 65535) return cudaErrorInvalidValue;
-    ChestArgs a;
-    a.n_sc = g.n_sc;
-    a.n_beams = g.n_beams;
-    a.n_layers = g.n_layers;
-    a.comb = g.comb;
-    a.n_sym = g.n_sym;
-    a.dmrs0 = g.dmrs0;
-    a.dmrs1 = g.dmrs1;
-    for (int l = 0; l < 32; ++l) a.port[l] = g.port[l];
+    const ChestArgs a = chest_args(g);
     ne_partial_kernel<<<dim3(kNoiseParts, (unsigned)n_slots), 256, 0, st>>>(a, ls_pilots_per_layer(g), beam, pilots,
                                                                              partial);
     cudaError_t e = cudaGetLastError();
@@ -173,35 +197,25 @@ cudaError_t launch_noise_est(const Geometry &g, int n_slots, const float2 *beam,
 }
 
 cudaError_t launch_ls_pilots(const Geometry &g, int n_slots, const float2 *beam, const float2 *pilots, float2 *ls,
-                             cudaStream_t st) {
-    ChestArgs a;
-    a.n_sc = g.n_sc;
-    a.n_beams = g.n_beams;
-    a.n_layers = g.n_layers;
-    a.comb = g.comb;
-    a.n_sym = g.n_sym;
-    a.dmrs0 = g.dmrs0;
-    a.dmrs1 = g.dmrs1;
-    for (int l = 0; l < 32; ++l) a.port[l] = g.port[l];
+                             cudaStream_t st, int sym) {
+    const ChestArgs a = chest_args(g);
     const int kmax = ls_pilots_per_layer(g);
     const long long rows = (long long)n_slots * g.n_layers;
     if (rows == 0) return cudaSuccess;
     if (rows > 65535) return cudaErrorInvalidValue;   // grid.y; n_slots * n_layers per call
     const int per_l = kmax * g.n_beams;
-    ls_pilots_kernel<<<dim3((unsigned)((per_l + 255) / 256), (unsigned)rows), 256, 0, st>>>(a, kmax, beam, pilots, ls);
+    ls_pilots_kernel<<<dim3((unsigned)((per_l + 255) / 256), (unsigned)rows), 256, 0, st>>>(a, kmax, sym, beam, pilots,
+                                                                                           ls);
     return cudaGetLastError();
 }
 
-cudaError_t launch_chest_interp(const Geometry &g, int n_slots, const float2 *ls, float2 *H, cudaStream_t st) {
-    ChestArgs a;
-    a.n_sc = g.n_sc;
-    a.n_beams = g.n_beams;
-    a.n_layers = g.n_layers;
-    a.comb = g.comb;
-    a.n_sym = g.n_sym;
-    a.dmrs0 = g.dmrs0;
-    a.dmrs1 = g.dmrs1;
-    for (int l = 0; l < 32; ++l) a.port[l] = g.port[l];
+size_t ls_table_elems(const Geometry &g, int n_slots) {
+    return (size_t)n_slots * g.n_layers * ls_pilots_per_layer(g) * g.n_beams;
+}
+
+cudaError_t launch_chest_interp(const Geometry &g, int n_slots, const float2 *ls, float2 *H, cudaStream_t st,
+                                bool time_groups) {
+    const ChestArgs a = chest_args(g);
     if ((long long)n_slots * g.n_sc == 0) return cudaSuccess;
     if (n_slots > 65535) return cudaErrorInvalidValue;                 // grid.y
     const int kmax = ls_pilots_per_layer(g);
@@ -210,11 +224,18 @@ cudaError_t launch_chest_interp(const Geometry &g, int n_slots, const float2 *ls
     const int lpc = std::min(g.n_layers, 1024 / units);                  // layers per CTA (units <= 64)
     const dim3 grid((unsigned)((g.n_sc + kRun - 1) / kRun), (unsigned)n_slots, (unsigned)((g.n_layers + lpc - 1) / lpc));
     const int threads = lpc * units;
-    if (pairs)
-        chest_interp_kernel<float4><<<grid, threads, 0, st>>>(a, kmax, units, lpc, reinterpret_cast<const float4 *>(ls),
-                                                              reinterpret_cast<float4 *>(H));
-    else
-        chest_interp_kernel<float2><<<grid, threads, 0, st>>>(a, kmax, units, lpc, ls, H);
+    // table and estimate strides in units (the second DMRS symbol's table; the next group's estimate)
+    const long long tab_u = (long long)ls_table_elems(g, n_slots) / (pairs ? 2 : 1);
+    const long long h_u = (long long)n_slots * g.n_sc * g.n_layers * units;
+    if (pairs) {
+        const float4 *l4 = reinterpret_cast<const float4 *>(ls);
+        float4 *h4 = reinterpret_cast<float4 *>(H);
+        if (time_groups) chest_interp_kernel<float4, true><<<grid, threads, 0, st>>>(a, kmax, units, lpc, l4, tab_u, h4, h_u);
+        else chest_interp_kernel<float4, false><<<grid, threads, 0, st>>>(a, kmax, units, lpc, l4, tab_u, h4, h_u);
+    } else {
+        if (time_groups) chest_interp_kernel<float2, true><<<grid, threads, 0, st>>>(a, kmax, units, lpc, ls, tab_u, H, h_u);
+        else chest_interp_kernel<float2, false><<<grid, threads, 0, st>>>(a, kmax, units, lpc, ls, tab_u, H, h_u);
+    }
     return cudaGetLastError();
 }
 
@@ -223,6 +244,15 @@ cudaError_t launch_chest_ls(const Geometry &g, int n_slots, const float2 *beam, 
     cudaError_t e = launch_ls_pilots(g, n_slots, beam, pilots, ls_scratch, st);
     if (e != cudaSuccess) return e;
     return launch_chest_interp(g, n_slots, ls_scratch, H, st);
+}
+
+cudaError_t launch_chest_time(const Geometry &g, int n_slots, const float2 *beam, const float2 *pilots, float2 *H,
+                              float2 *ls_scratch, cudaStream_t st) {
+    cudaError_t e = launch_ls_pilots(g, n_slots, beam, pilots, ls_scratch, st, 0);
+    if (e != cudaSuccess) return e;
+    if ((e = launch_ls_pilots(g, n_slots, beam, pilots, ls_scratch + ls_table_elems(g, n_slots), st, 1)) != cudaSuccess)
+        return e;
+    return launch_chest_interp(g, n_slots, ls_scratch, H, st, true);
 }
 
 }  // namespace pusch

@@ -24,7 +24,7 @@ __device__ __forceinline__ void cp_async_wait_all() {
 }
 
 // Shared memory per subcarrier, in float2 units: the H tile (NL rows of an even stride >= nb + 1), which
-// later holds L ([NL][NL + 1]); in the fused variant also NL row-parameter records.
+// later holds L ([NL][NL + 1]).
 __host__ __device__ __forceinline__ int row_stride(int nb) { return (nb + 3) & ~1; }
 template <int NL>
 __host__ __device__ __forceinline__ int htile(int nb) {
@@ -33,17 +33,10 @@ __host__ __device__ __forceinline__ int htile(int nb) {
     return (m + 1) & ~1;
 }
 
-// Interpolation parameters of one (subcarrier, layer) row of the fused estimate.
-struct RowParam {
-    long long lo, hi;     // element offsets of the LS rows of the neighbouring pilots (lo == hi: hold)
-    float w;              // interpolation weight
-    int valid;            // 0: row is padding (layer >= n_layers or subcarrier out of range)
-};
-
-template <int NL, bool FUSED>
+// Shared memory of one warp of the single-cell detector: per subcarrier the H tile and the data-symbol rows.
+template <int NL>
 __host__ __device__ __forceinline__ size_t warp_smem_bytes(int nb, int nd) {
-    return (size_t)(32 / NL) *
-           ((htile<NL>(nb) + (size_t)nd * row_stride(nb)) * sizeof(float2) + (FUSED ? NL * sizeof(RowParam) : 0));
+    return (size_t)(32 / NL) * ((htile<NL>(nb) + (size_t)nd * row_stride(nb)) * sizeof(float2));
 }
 
 __device__ __forceinline__ void cp_async16(void *dst, const void *src) {

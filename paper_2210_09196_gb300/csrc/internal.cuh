@@ -49,6 +49,9 @@ struct Geometry {
     float noise_var, loading;
     int port[32];
     int data_sym[16];             // data symbol indices in increasing order
+    int chol_every;               // 0, or the data-symbol group size (pusch_cell_cfg.chol_every)
+    int n_groups;                 // detection groups (1 when chol_every == 0)
+    float group_t[16];            // per group: mean (s - dmrs0) / (dmrs1 - dmrs0) of its data symbols
 };
 
 Geometry make_geometry(const pusch_cell_cfg &c);
@@ -85,26 +88,31 @@ cudaError_t launch_beamform_fp32(const Geometry &g, int n_slots, const float2 *f
 // n_slots * n_layers * ls_pilots_per_layer(g) * n_beams float2.
 cudaError_t launch_chest_ls(const Geometry &g, int n_slots, const float2 *beam, const float2 *pilots, float2 *H,
                             float2 *ls_scratch, cudaStream_t st);
+// Time-varying estimates of the detection groups (chol_every > 0): ls_scratch holds two tables.
+cudaError_t launch_chest_time(const Geometry &g, int n_slots, const float2 *beam, const float2 *pilots, float2 *H,
+                              float2 *ls_scratch, cudaStream_t st);
 // sigma2 (optional, device, one float per slot): per-slot noise variance replacing g.noise_var.
+// time_groups: H holds g.n_groups estimates (launch_chest_time) and each group of g.chol_every data symbols
+// is detected with its own.
 cudaError_t launch_mmse(const Geometry &g, int n_slots, const float2 *H, const float2 *beam, float2 *x_hat,
-                        uint8_t *bits, uint32_t *status, cudaStream_t st, const float *sigma2 = nullptr);
+                        uint8_t *bits, uint32_t *status, cudaStream_t st, const float *sigma2 = nullptr,
+                        bool time_groups = false);
 // LS values at the pilot subcarriers: ls[slot][l][k][b] for pilot q = port[l] + k * comb, k < kmax.
 int ls_pilots_per_layer(const Geometry &g);
+// sym = -1: the mean of the two DMRS symbols; 0 / 1: that DMRS symbol alone.
 cudaError_t launch_ls_pilots(const Geometry &g, int n_slots, const float2 *beam, const float2 *pilots, float2 *ls,
-                             cudaStream_t st);
+                             cudaStream_t st, int sym = -1);
+size_t ls_table_elems(const Geometry &g, int n_slots);
 // The full estimate H [slots][n_sc][n_layers][n_beams] interpolated from the LS pilot table.
-cudaError_t launch_chest_interp(const Geometry &g, int n_slots, const float2 *ls, float2 *H, cudaStream_t st);
+// time_groups: ls holds the two DMRS symbols' tables back to back and H receives g.n_groups estimates
+// (group q at g.group_t[q]), each n_slots * n_sc * n_layers * n_beams values.
+cudaError_t launch_chest_interp(const Geometry &g, int n_slots, const float2 *ls, float2 *H, cudaStream_t st,
+                                bool time_groups = false);
 // Noise-variance estimate per slot from the pilot residuals (Section II "NE"): partial needs
 // n_slots * kNoiseParts float2 of scratch; sigma2 receives one float per slot.
 constexpr int kNoiseParts = 64;
 cudaError_t launch_noise_est(const Geometry &g, int n_slots, const float2 *beam, const float2 *pilots,
                              float2 *partial, float *sigma2, cudaStream_t st);
-// Estimation fused into detection: the estimate is interpolated from the LS pilot table inside the
-// detection kernel and never written to memory.
-cudaError_t launch_mmse_fused(const Geometry &g, int n_slots, const float2 *beam, const float2 *ls,
-                              float2 *x_hat, uint8_t *bits, uint32_t *status, cudaStream_t st,
-                              const float *sigma2 = nullptr);
-
 // Launch shape of the tensor-core beamforming kernel: K rows per pipeline stage and whether the epilogue
 // writes through shared memory and TMA stores. chunk_rows = 0 lets the kernel choose from its shared-memory
 // budget; a shape that does not fit falls back to that choice.

@@ -3,21 +3,20 @@
 //
 // GB300 mapping: a group of NL lanes owns one subcarrier (NL = layer class 2..32, a power of two), so a
 // warp detects 32/NL subcarriers at once; lane i of a group owns layer i.
-//   1. The estimate H of the warp's subcarriers is staged in shared memory (rows padded to an even stride):
-//      copied from the caller's buffer with cp.async, or - in the fused variant used by pusch_slot -
-//      interpolated right here from the table of LS values at the pilot subcarriers (the same arithmetic
-//      as the estimation kernel), so that the full estimate never travels to HBM. The per-row pilot
-//      brackets are computed once per (subcarrier, layer), then the LS rows are read with coalesced loads.
 //   0. The data-symbol vectors y_d of the warp's subcarriers are copied to shared memory with cp.async
-//      first, so that their latency overlaps steps 1-2a.
+//      first, so that their latency overlaps step 1.
+//   1. The estimate rows of the warp's subcarriers are copied to shared memory with 16-byte cp.async pieces
+//      (rows padded to an even stride).
 //   2. Lane i forms row i of G from 16-byte shared loads, then r_d = H^H y_d for every data symbol d.
 //   3. Right-looking Cholesky of G in registers: the pivot and column entries are broadcast by warp
 //      shuffles. L is written to shared memory over the (now dead) H tile.
 //   4. Forward and back solves for all data symbols together, one shuffle per unknown and symbol, L read
 //      from shared memory (row i for the forward solve, column i for the back solve).
-// G and L are formed once per subcarrier, which gives the same result as forming them per data symbol
-// because the estimate is constant over the slot. Layers beyond n_layers (up to NL) are padded with
-// identity rows and produce nothing.
+// With one estimate per slot, G and L are formed once per subcarrier, which gives the same result as forming
+// them per data symbol. With an estimate that varies in time (chol_every = K > 0) the data symbols are taken
+// in groups of K: steps 1-4 run per group with that group's estimate (Section VI's schedule: K = 1 is one
+// factorisation per data symbol). Layers beyond n_layers (up to NL) are padded with identity rows and produce
+// nothing.
 #pragma once
 
 #include "chest_common.cuh"
@@ -30,21 +29,21 @@ constexpr int kMmseWarps = 2;
 constexpr unsigned kFull = 0xffffffffu;
 
 struct MmseArgs {
-    int n_sc, n_beams, n_layers, n_sym, n_data, qam_bits, comb, dmrs0, dmrs1, kmax;
+    int n_sc, n_beams, n_layers, n_sym, n_data, qam_bits;
     float load;  // sigma^2 + extra loading (sigma2 == nullptr)
     float loading;             // extra loading alone
     const float *sigma2;       // per-slot noise variance (device) or nullptr
+    int n_groups, group_k;     // detection groups of group_k data symbols, each with its own estimate
+    long long h_group_stride;  // elements between the groups' estimates
     int data_sym[16];
-    int port[32];
 };
 
 // Register cap: five CTAs per SM up to 8 layers, seven for 16 layers (128 registers: the shared-memory
 // limit is also seven), none for 32.
-template <int NL, int ND, bool FUSED>
+template <int NL, int ND>
 __global__ void __launch_bounds__(kMmseWarps * 32, NL <= 8 ? 5 : (NL == 16 ? 7 : 1))
 mmse_kernel(MmseArgs g, long long total_sc, const float2 *__restrict__ H, const float2 *__restrict__ beam,
-            const float2 *__restrict__ ls, float2 *__restrict__ xhat, uint8_t *__restrict__ bits,
-            uint32_t *__restrict__ status) {
+            float2 *__restrict__ xhat, uint8_t *__restrict__ bits, uint32_t *__restrict__ status) {
     constexpr int SPW = 32 / NL;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -54,10 +53,9 @@ mmse_kernel(MmseArgs g, long long total_sc, const float2 *__restrict__ H, const 
     const int nd = ND > 0 ? ND : g.n_data;
     const int hs = row_stride(nb), ht = htile<NL>(nb);
 
-    unsigned char *wbase = smem_raw + (size_t)warp * warp_smem_bytes<NL, FUSED>(nb, nd);
+    unsigned char *wbase = smem_raw + (size_t)warp * warp_smem_bytes<NL>(nb, nd);
     float2 *Ht = reinterpret_cast<float2 *>(wbase);  // [SPW][ht]
     float2 *Yt = Ht + SPW * ht;                      // [SPW][nd][hs]
-    RowParam *rp = reinterpret_cast<RowParam *>(Yt + (size_t)SPW * nd * hs);  // [SPW*NL]
 
     const long long sc0 = ((long long)blockIdx.x * kMmseWarps + warp) * SPW;  // first (slot*n_sc + a) of warp
     if (sc0 >= total_sc) return;                                              // whole warp idle
@@ -101,8 +99,9 @@ mmse_kernel(MmseArgs g, long long total_sc, const float2 *__restrict__ H, const 
     // ---- 1. channel estimate rows -> shared memory. Element e of the warp's [SPW*NL][nb] tile is handled
     //         by lane e % 32; (row, b) advance incrementally (no division in the loop).
     const int rows = SPW * NL;
-    if constexpr (!FUSED) {
-        // 16-byte pieces (two beams) when the beam count is even, 8-byte pieces otherwise
+    // the estimate rows of group q (H + q * h_group_stride) -> the H tile; 16-byte pieces (two beams) when the
+    // beam count is even, 8-byte pieces otherwise
+    auto stage_H = [&](const float2 *Hq) {
         const bool wide = (nb & 1) == 0;
         const int cpr = wide ? nb >> 1 : nb;  // pieces per row
         int r = lane / cpr, c = lane - (lane / cpr) * cpr;
@@ -112,7 +111,7 @@ mmse_kernel(MmseArgs g, long long total_sc, const float2 *__restrict__ H, const 
             const int b = wide ? 2 * c : c;
             float2 *dst = Ht + gg * ht + l * hs + b;
             if (l < nl && sc0 + gg < total_sc) {
-                const float2 *src = H + ((sc0 + gg) * nl + l) * (long long)nb + b;
+                const float2 *src = Hq + ((sc0 + gg) * nl + l) * (long long)nb + b;
                 if (wide)
                     cp_async16(dst, src);
                 else
@@ -129,129 +128,82 @@ mmse_kernel(MmseArgs g, long long total_sc, const float2 *__restrict__ H, const 
             }
         }
         cp_async_wait_all();  // the H tile (and the earlier y group)
-    } else {
-        {   // row parameters: lane = row (SPW*NL == 32)
-            RowParam q;
-            q.valid = (valid && i < nl) ? 1 : 0;
-            q.lo = q.hi = 0;
-            q.w = 0.f;
-            if (q.valid) {
-                int lo, hi;
-                pilot_bracket(a, g.port[i], g.comb, n_sc, lo, hi);
-                const long long base = (slot * nl + i) * (long long)g.kmax * nb;
-                q.lo = base + (long long)((lo - g.port[i]) / g.comb) * nb;
-                q.hi = base + (long long)((hi - g.port[i]) / g.comb) * nb;
-                q.w = interp_weight(a, lo, hi);
-            }
-            rp[lane] = q;
-        }
-        __syncwarp();
-        // kB elements per lane at a time: all their LS-table loads are issued before any is used, so each
-        // lane waits for about rows * nb / (32 kB) round trips to L2 instead of one per element
-        constexpr int kB = 8;
-        int r = lane / nb, b = lane - (lane / nb) * nb;
-        const int step_r = 32 / nb, step_b = 32 - (32 / nb) * nb;
-        while (r < rows) {
-            float2 lo[kB], hi[kB];
-            float w[kB];
-            int off[kB];
-#pragma unroll
-            for (int u = 0; u < kB; ++u) {
-                off[u] = -1;
-                lo[u] = hi[u] = make_float2(0.f, 0.f);
-                w[u] = 0.f;
-                if (r < rows) {
-                    const int gg = r / NL, l = r - gg * NL;
-                    off[u] = gg * ht + l * hs + b;
-                    const RowParam &q = rp[r];
-                    if (q.valid) {
-                        lo[u] = __ldg(&ls[q.lo + b]);
-                        hi[u] = q.hi != q.lo ? __ldg(&ls[q.hi + b]) : lo[u];
-                        w[u] = q.w;
-                    }
-                }
-                r += step_r;
-                b += step_b;
-                if (b >= nb) {
-                    b -= nb;
-                    ++r;
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < kB; ++u)
-                if (off[u] >= 0) Ht[off[u]] = interp(lo[u], hi[u], w[u]);
-        }
-    }
+    };
+    stage_H(H);
     __syncwarp();
 
     const float2 *hr = Ht + grp * ht + i * hs;  // own row
     const float2 *hg = Ht + grp * ht;           // the group's rows
     constexpr int NR = ND > 0 ? ND : 14;
     float2 acc[NR];
-    const bool bad = detect_group<NL, ND, NR>(hr, hg, Yt + grp * nd * hs, Ht + grp * ht, hs, nb, nd, nl,
-                                              g.sigma2 ? g.loading : g.load, i, src0, acc, g.sigma2,
-                                              valid ? slot : 0);
+    bool bad = false, nonfinite = false;
+    // detection groups: one (all data symbols, one estimate) unless the estimate varies in time; group q holds
+    // data symbols [q K, q K + K) and its own estimate (the H tile is restaged: L of the previous group is dead)
+    for (int q = 0; q < g.n_groups; ++q) {
+        const int d0 = q * g.group_k;
+        const int ndq = ND > 0 ? ND : min(g.group_k, nd - d0);
+        if (q > 0) {
+            __syncwarp();
+            stage_H(H + q * g.h_group_stride);
+            __syncwarp();
+        }
+        bad |= detect_group<NL, ND, NR>(hr, hg, Yt + (grp * nd + d0) * hs, Ht + grp * ht, hs, nb, ndq, nl,
+                                        g.sigma2 ? g.loading : g.load, i, src0, acc, g.sigma2, valid ? slot : 0);
+        if (valid && i < nl) {
+            const long long o0 = (slot * nl + i) * (long long)nd * n_sc + a;
+#pragma unroll
+            for (int d = 0; d < NR; ++d) {
+                if (ND > 0 || d < ndq) {
+                    const float2 x = acc[d];
+                    xhat[o0 + (long long)(d0 + d) * n_sc] = x;
+                    bits[o0 + (long long)(d0 + d) * n_sc] = det_demap(x, g.qam_bits);
+                    if (!isfinite(x.x) || !isfinite(x.y)) nonfinite = true;
+                }
+            }
+        }
+    }
     if (valid && bad && i == 0) {
         atomicAdd(&status[1], 1u);
         atomicMin(&status[2], (unsigned)my_sc);
         atomicOr(&status[0], (unsigned)PUSCH_STATUS_PIVOT);
     }
-
-    bool nonfinite = false;
-    if (valid && i < nl) {
-        const long long o0 = (slot * nl + i) * (long long)nd * n_sc + a;
-#pragma unroll
-        for (int d = 0; d < NR; ++d) {
-            if (ND > 0 || d < nd) {
-                const float2 x = acc[d];
-                xhat[o0 + (long long)d * n_sc] = x;
-                bits[o0 + (long long)d * n_sc] = det_demap(x, g.qam_bits);
-                if (!isfinite(x.x) || !isfinite(x.y)) nonfinite = true;
-            }
-        }
-    }
     if (__any_sync(kFull, nonfinite) && lane == 0) atomicOr(&status[0], (unsigned)PUSCH_STATUS_NONFINITE);
 }
 
-template <int NL, int ND, bool FUSED>
-cudaError_t launch_nl(const MmseArgs &a, long long total_sc, const float2 *H, const float2 *beam,
-                      const float2 *pilots, float2 *xhat, uint8_t *bits, uint32_t *status, cudaStream_t st) {
+template <int NL, int ND>
+cudaError_t launch_nl(const MmseArgs &a, long long total_sc, const float2 *H, const float2 *beam, float2 *xhat,
+                      uint8_t *bits, uint32_t *status, cudaStream_t st) {
     constexpr int SPW = 32 / NL;
-    const size_t smem = (size_t)kMmseWarps * warp_smem_bytes<NL, FUSED>(a.n_beams, ND > 0 ? ND : a.n_data);
+    const size_t smem = (size_t)kMmseWarps * warp_smem_bytes<NL>(a.n_beams, ND > 0 ? ND : a.n_data);
     const long long per_cta = (long long)kMmseWarps * SPW;
     const long long grid = (total_sc + per_cta - 1) / per_cta;
     if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    auto k = mmse_kernel<NL, ND, FUSED>;
+    auto k = mmse_kernel<NL, ND>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k<<<(unsigned)grid, kMmseWarps * 32, smem, st>>>(a, total_sc, H, beam, pilots, xhat, bits, status);
+    k<<<(unsigned)grid, kMmseWarps * 32, smem, st>>>(a, total_sc, H, beam, xhat, bits, status);
     return cudaGetLastError();
 }
 
-template <int NL, bool FUSED>
-cudaError_t launch_nd(const MmseArgs &a, long long total_sc, const float2 *H, const float2 *beam,
-                      const float2 *pilots, float2 *xhat, uint8_t *bits, uint32_t *status, cudaStream_t st) {
-    if (a.n_data == 12) return launch_nl<NL, 12, FUSED>(a, total_sc, H, beam, pilots, xhat, bits, status, st);
-    return launch_nl<NL, 0, FUSED>(a, total_sc, H, beam, pilots, xhat, bits, status, st);
+// The 12-data-symbol instantiation serves one group of 12; everything else runs with a run-time count.
+template <int NL>
+cudaError_t launch_nd(const MmseArgs &a, long long total_sc, const float2 *H, const float2 *beam, float2 *xhat,
+                      uint8_t *bits, uint32_t *status, cudaStream_t st) {
+    if (a.n_data == 12 && a.n_groups == 1) return launch_nl<NL, 12>(a, total_sc, H, beam, xhat, bits, status, st);
+    return launch_nl<NL, 0>(a, total_sc, H, beam, xhat, bits, status, st);
 }
 
 }  // namespace mmse_detail
 
 // Launch of one layer class (separate translation units, compiled in parallel): NL = 2, 4 or 8 in
-// mmse_small.cu, 16 in mmse_nl16.cu, 32 in mmse_nl32.cu (the fused variant in mmse_nl32f.cu).
-cudaError_t mmse_launch_class(int nl_class, bool fused, const mmse_detail::MmseArgs &a, long long total_sc,
-                              const float2 *H, const float2 *beam, const float2 *pilots, float2 *xhat, uint8_t *bits,
-                              uint32_t *status, cudaStream_t st);
-cudaError_t mmse_launch_class16(bool fused, const mmse_detail::MmseArgs &a, long long total_sc, const float2 *H,
-                                const float2 *beam, const float2 *pilots, float2 *xhat, uint8_t *bits,
-                                uint32_t *status, cudaStream_t st);
-cudaError_t mmse_launch_class32(bool fused, const mmse_detail::MmseArgs &a, long long total_sc, const float2 *H,
-                                const float2 *beam, const float2 *pilots, float2 *xhat, uint8_t *bits,
-                                uint32_t *status, cudaStream_t st);
-cudaError_t mmse_launch_class32_fused(const mmse_detail::MmseArgs &a, long long total_sc, const float2 *beam,
-                                      const float2 *pilots, float2 *xhat, uint8_t *bits, uint32_t *status,
-                                      cudaStream_t st);
+// mmse_small.cu, 16 in mmse_nl16.cu, 32 in mmse_nl32.cu.
+cudaError_t mmse_launch_class(int nl_class, const mmse_detail::MmseArgs &a, long long total_sc, const float2 *H,
+                              const float2 *beam, float2 *xhat, uint8_t *bits, uint32_t *status, cudaStream_t st);
+cudaError_t mmse_launch_class16(const mmse_detail::MmseArgs &a, long long total_sc, const float2 *H,
+                                const float2 *beam, float2 *xhat, uint8_t *bits, uint32_t *status, cudaStream_t st);
+cudaError_t mmse_launch_class32(const mmse_detail::MmseArgs &a, long long total_sc, const float2 *H,
+                                const float2 *beam, float2 *xhat, uint8_t *bits, uint32_t *status, cudaStream_t st);
 
 }  // namespace pusch

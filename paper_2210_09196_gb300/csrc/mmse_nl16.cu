@@ -3,12 +3,9 @@
 
 namespace pusch {
 
-cudaError_t mmse_launch_class16(bool fused, const mmse_detail::MmseArgs &a, long long total_sc, const float2 *H,
-                                const float2 *beam, const float2 *pilots, float2 *xhat, uint8_t *bits,
-                                uint32_t *status, cudaStream_t st) {
-    using namespace mmse_detail;
-    return fused ? launch_nd<16, true>(a, total_sc, H, beam, pilots, xhat, bits, status, st)
-                 : launch_nd<16, false>(a, total_sc, H, beam, pilots, xhat, bits, status, st);
+cudaError_t mmse_launch_class16(const mmse_detail::MmseArgs &a, long long total_sc, const float2 *H,
+                                const float2 *beam, float2 *xhat, uint8_t *bits, uint32_t *status, cudaStream_t st) {
+    return mmse_detail::launch_nd<16>(a, total_sc, H, beam, xhat, bits, status, st);
 }
 
 }  // namespace pusch

@@ -81,6 +81,8 @@ extern "C" pusch_status pusch_slot_noalloc(const pusch_cell_cfg *cfg, int n_slot
     if (n_slots == 0) return PUSCH_OK;
     if (!time_in || !W || !pilots || !x_hat || !bits) return na_fail(PUSCH_ERR_ARG, "pusch_slot_noalloc: NULL buffer");
 
+    if (cfg->chol_every != 0)
+        return na_fail(PUSCH_ERR_UNSUPPORTED, "pusch_slot_noalloc: chol_every > 0 needs a handle (pusch_slot)");
     const pusch::Geometry g = pusch::make_geometry(*cfg);
     const size_t tw_b = up256((size_t)g.n_fft * sizeof(float2));
     const size_t words_b = 256;  // status sink (16 B) + tensor-core timeout word (16 B)

@@ -10,12 +10,12 @@ from . import binding as B
 
 
 def cfg_for(cell, form: int = B.PUSCH_FORM_FP32, noise_var: float | None = None, loading: float = 0.0,
-            ports=None) -> B.pusch_cell_cfg:
+            ports=None, chol_every: int = 0) -> B.pusch_cell_cfg:
     """pusch_cell_cfg for a generator CellConfig (paper_2210_09196_gb300.synth)."""
     nv = float(10.0 ** (-cell.snr_db / 10.0)) if noise_var is None else float(noise_var)
     return B.make_cfg(n_rx=cell.n_rx, n_fft=cell.n_fft, n_sc=cell.n_sc, n_beams=cell.n_beams,
                       n_layers=cell.n_layers, comb=cell.comb, ports=ports, qam_bits=cell.qam_bits,
-                      in_fp16=cell.in_fp16, form=form, noise_var=nv, loading=loading)
+                      in_fp16=cell.in_fp16, form=form, noise_var=nv, loading=loading, chol_every=chol_every)
 
 
 def time_tensor(slots, device="cuda", pin=False) -> torch.Tensor:

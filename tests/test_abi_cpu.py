@@ -54,7 +54,8 @@ def _good(**kw):
     (dict(n_beams=65), -5), (dict(n_layers=17), -1), (dict(n_layers=33, n_beams=64), -1),
     (dict(qam_bits=3), -1), (dict(noise_var=-0.5), -1), (dict(noise_var=float("nan")), -1),
     (dict(comb=0), -1), (dict(ports=[0, 1, 2, 4]), -1), (dict(dmrs_sym=(2, 2)), -1), (dict(dmrs_sym=(2, 14)), -1),
-    (dict(n_sym=2), -1), (dict(form=7), -1), (dict(n_rx=0), -5),
+    (dict(n_sym=2), -1), (dict(form=7), -1), (dict(n_rx=0), -5), (dict(chol_every=-1), -1),
+    (dict(chol_every=13), -1),
 ])
 def test_invalid_configs_are_rejected_on_the_host(B, bad, code):
     cfg = _good(**bad)
@@ -79,6 +80,14 @@ def test_workspace_size(B):
     # FFT out + beams + LS pilot table + interpolated estimate
     per_slot = 14 * 16 * 300 * 8 + 14 * 300 * 16 * 8 + 4 * 75 * 16 * 8 + 300 * 4 * 16 * 8
     assert n >= 2 * per_slot and n < 2 * per_slot + 64 * 1024
+
+
+def test_workspace_size_of_the_time_varying_estimate(B):
+    """chol_every = 4 over 12 data symbols: two LS tables (one per DMRS symbol) and three estimates."""
+    n0 = B.pusch_workspace_size(_good(), 2)
+    n4 = B.pusch_workspace_size(_good(chol_every=4), 2)
+    assert n4 - n0 >= 2 * (4 * 75 * 16 * 8 + 2 * 300 * 4 * 16 * 8)
+    assert n4 - n0 < 2 * (4 * 75 * 16 * 8 + 2 * 300 * 4 * 16 * 8) + 64 * 1024
 
 
 def test_null_handle_and_bad_batch_rejected(B):
