@@ -19,7 +19,8 @@ cudaError_t launch_mmse(const Geometry &g, int n_slots, const float2 *H, const f
     a.n_groups = time_groups ? g.n_groups : 1;
     a.group_k = time_groups ? g.chol_every : g.n_data;
     a.h_group_stride = (long long)n_slots * g.n_sc * g.n_layers * g.n_beams;
-    for (int d = 0; d < 16; ++d) a.data_sym[d] = g.data_sym[d];
+    a.dmrs_lo = g.dmrs0 < g.dmrs1 ? g.dmrs0 : g.dmrs1;
+    a.dmrs_hi = g.dmrs0 < g.dmrs1 ? g.dmrs1 : g.dmrs0;
     if (g.n_data > 14) return cudaErrorInvalidValue;
     const long long total_sc = (long long)n_slots * g.n_sc;
     if (total_sc == 0) return cudaSuccess;

@@ -35,12 +35,58 @@ struct MmseArgs {
     const float *sigma2;       // per-slot noise variance (device) or nullptr
     int n_groups, group_k;     // detection groups of group_k data symbols, each with its own estimate
     long long h_group_stride;  // elements between the groups' estimates
-    int data_sym[16];
+    int dmrs_lo, dmrs_hi;      // the two DMRS symbols, dmrs_lo < dmrs_hi
 };
+
+// Symbol index of data symbol d: the data symbols are all other symbols of the slot in increasing order.
+// (Computed rather than read from a parameter table: a run-time index into a kernel parameter array would
+// copy the whole parameter block to local memory.)
+__device__ __forceinline__ int data_symbol(const MmseArgs &g, int d) {
+    int s = d;
+    if (s >= g.dmrs_lo) ++s;
+    if (s >= g.dmrs_hi) ++s;
+    return s;
+}
+
+// The estimate rows of the warp's SPW subcarriers (from Hq, one group's estimate) -> the warp's H tile, rows
+// padded to stride hs; 16-byte cp.async pieces (two beams) when the beam count is even, 8-byte pieces
+// otherwise; rows of absent layers and subcarriers are zeroed. Waits for all of the lane's copies.
+template <int NL>
+__device__ __forceinline__ void stage_H(float2 *Ht, const float2 *__restrict__ Hq, long long sc0, long long total_sc,
+                                        int nl, int nb, int hs, int ht, int lane) {
+    constexpr int SPW = 32 / NL;
+    const int rows = SPW * NL;
+    const bool wide = (nb & 1) == 0;
+    const int cpr = wide ? nb >> 1 : nb;  // pieces per row
+    int r = lane / cpr, c = lane - (lane / cpr) * cpr;
+    const int step_r = 32 / cpr, step_c = 32 - (32 / cpr) * cpr;
+    for (; r < rows;) {
+        const int gg = r / NL, l = r - gg * NL;  // NL is a power of two
+        const int b = wide ? 2 * c : c;
+        float2 *dst = Ht + gg * ht + l * hs + b;
+        if (l < nl && sc0 + gg < total_sc) {
+            const float2 *src = Hq + ((sc0 + gg) * nl + l) * (long long)nb + b;
+            if (wide)
+                cp_async16(dst, src);
+            else
+                cp_async8(dst, src);
+        } else {
+            dst[0] = make_float2(0.f, 0.f);
+            if (wide) dst[1] = make_float2(0.f, 0.f);
+        }
+        r += step_r;
+        c += step_c;
+        if (c >= cpr) {
+            c -= cpr;
+            ++r;
+        }
+    }
+    cp_async_wait_all();  // the H tile (and the earlier y group)
+}
 
 // Register cap: five CTAs per SM up to 8 layers, seven for 16 layers (128 registers: the shared-memory
 // limit is also seven), none for 32.
-template <int NL, int ND>
+template <int NL, int ND, bool GROUPS>
 __global__ void __launch_bounds__(kMmseWarps * 32, NL <= 8 ? 5 : (NL == 16 ? 7 : 1))
 mmse_kernel(MmseArgs g, long long total_sc, const float2 *__restrict__ H, const float2 *__restrict__ beam,
             float2 *__restrict__ xhat, uint8_t *__restrict__ bits, uint32_t *__restrict__ status) {
@@ -77,7 +123,7 @@ mmse_kernel(MmseArgs g, long long total_sc, const float2 *__restrict__ H, const 
             float2 *dst = Yt + (gg * nd + d) * hs + (wide ? 2 * c : c);
             if (sc < total_sc) {
                 const long long sl = sc / n_sc, aa = sc - sl * n_sc;
-                const float2 *src = beam + ((sl * g.n_sym + g.data_sym[d]) * n_sc + aa) * nb + (wide ? 2 * c : c);
+                const float2 *src = beam + ((sl * g.n_sym + data_symbol(g, d)) * n_sc + aa) * nb + (wide ? 2 * c : c);
                 if (wide)
                     cp_async16(dst, src);
                 else
@@ -96,41 +142,7 @@ mmse_kernel(MmseArgs g, long long total_sc, const float2 *__restrict__ H, const 
         asm volatile("cp.async.commit_group;" ::: "memory");
     }
 
-    // ---- 1. channel estimate rows -> shared memory. Element e of the warp's [SPW*NL][nb] tile is handled
-    //         by lane e % 32; (row, b) advance incrementally (no division in the loop).
-    const int rows = SPW * NL;
-    // the estimate rows of group q (H + q * h_group_stride) -> the H tile; 16-byte pieces (two beams) when the
-    // beam count is even, 8-byte pieces otherwise
-    auto stage_H = [&](const float2 *Hq) {
-        const bool wide = (nb & 1) == 0;
-        const int cpr = wide ? nb >> 1 : nb;  // pieces per row
-        int r = lane / cpr, c = lane - (lane / cpr) * cpr;
-        const int step_r = 32 / cpr, step_c = 32 - (32 / cpr) * cpr;
-        for (; r < rows;) {
-            const int gg = r / NL, l = r - gg * NL;  // NL is a power of two
-            const int b = wide ? 2 * c : c;
-            float2 *dst = Ht + gg * ht + l * hs + b;
-            if (l < nl && sc0 + gg < total_sc) {
-                const float2 *src = Hq + ((sc0 + gg) * nl + l) * (long long)nb + b;
-                if (wide)
-                    cp_async16(dst, src);
-                else
-                    cp_async8(dst, src);
-            } else {
-                dst[0] = make_float2(0.f, 0.f);
-                if (wide) dst[1] = make_float2(0.f, 0.f);
-            }
-            r += step_r;
-            c += step_c;
-            if (c >= cpr) {
-                c -= cpr;
-                ++r;
-            }
-        }
-        cp_async_wait_all();  // the H tile (and the earlier y group)
-    };
-    stage_H(H);
-    __syncwarp();
+    // ---- 1. channel estimate rows -> shared memory (stage_H, per detection group, in the loop below).
 
     const float2 *hr = Ht + grp * ht + i * hs;  // own row
     const float2 *hg = Ht + grp * ht;           // the group's rows
@@ -139,14 +151,15 @@ mmse_kernel(MmseArgs g, long long total_sc, const float2 *__restrict__ H, const 
     bool bad = false, nonfinite = false;
     // detection groups: one (all data symbols, one estimate) unless the estimate varies in time; group q holds
     // data symbols [q K, q K + K) and its own estimate (the H tile is restaged: L of the previous group is dead)
-    for (int q = 0; q < g.n_groups; ++q) {
-        const int d0 = q * g.group_k;
-        const int ndq = ND > 0 ? ND : min(g.group_k, nd - d0);
-        if (q > 0) {
-            __syncwarp();
-            stage_H(H + q * g.h_group_stride);
-            __syncwarp();
-        }
+    // (GROUPS = false: one group of all data symbols, no loop -- the loop costs registers at the cap)
+    const int n_groups = GROUPS ? g.n_groups : 1;
+    for (int q = 0; q < n_groups; ++q) {
+        const int d0 = GROUPS ? q * g.group_k : 0;
+        const int ndq = ND > 0 ? ND : (GROUPS ? min(g.group_k, nd - d0) : nd);
+        // one call site, so that the staging code is inlined
+        if (q > 0) __syncwarp();
+        stage_H<NL>(Ht, GROUPS ? H + q * g.h_group_stride : H, sc0, total_sc, nl, nb, hs, ht, lane);
+        __syncwarp();
         bad |= detect_group<NL, ND, NR>(hr, hg, Yt + (grp * nd + d0) * hs, Ht + grp * ht, hs, nb, ndq, nl,
                                         g.sigma2 ? g.loading : g.load, i, src0, acc, g.sigma2, valid ? slot : 0);
         if (valid && i < nl) {
@@ -170,7 +183,7 @@ mmse_kernel(MmseArgs g, long long total_sc, const float2 *__restrict__ H, const 
     if (__any_sync(kFull, nonfinite) && lane == 0) atomicOr(&status[0], (unsigned)PUSCH_STATUS_NONFINITE);
 }
 
-template <int NL, int ND>
+template <int NL, int ND, bool GROUPS>
 cudaError_t launch_nl(const MmseArgs &a, long long total_sc, const float2 *H, const float2 *beam, float2 *xhat,
                       uint8_t *bits, uint32_t *status, cudaStream_t st) {
     constexpr int SPW = 32 / NL;
@@ -178,7 +191,7 @@ cudaError_t launch_nl(const MmseArgs &a, long long total_sc, const float2 *H, co
     const long long per_cta = (long long)kMmseWarps * SPW;
     const long long grid = (total_sc + per_cta - 1) / per_cta;
     if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    auto k = mmse_kernel<NL, ND>;
+    auto k = mmse_kernel<NL, ND, GROUPS>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -187,12 +200,14 @@ cudaError_t launch_nl(const MmseArgs &a, long long total_sc, const float2 *H, co
     return cudaGetLastError();
 }
 
-// The 12-data-symbol instantiation serves one group of 12; everything else runs with a run-time count.
+// The 12-data-symbol instantiation serves one group of 12, the run-time count any other single group, and the
+// group loop the estimate that varies in time.
 template <int NL>
 cudaError_t launch_nd(const MmseArgs &a, long long total_sc, const float2 *H, const float2 *beam, float2 *xhat,
                       uint8_t *bits, uint32_t *status, cudaStream_t st) {
-    if (a.n_data == 12 && a.n_groups == 1) return launch_nl<NL, 12>(a, total_sc, H, beam, xhat, bits, status, st);
-    return launch_nl<NL, 0>(a, total_sc, H, beam, xhat, bits, status, st);
+    if (a.n_groups > 1) return launch_nl<NL, 0, true>(a, total_sc, H, beam, xhat, bits, status, st);
+    if (a.n_data == 12) return launch_nl<NL, 12, false>(a, total_sc, H, beam, xhat, bits, status, st);
+    return launch_nl<NL, 0, false>(a, total_sc, H, beam, xhat, bits, status, st);
 }
 
 }  // namespace mmse_detail
