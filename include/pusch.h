@@ -190,18 +190,35 @@ pusch_status pusch_mmse_detect(pusch_handle *h, int n_slots, const void *H_hat, 
 
 /*
  * The whole chain for n_slots slots (Fig. 1): OFDM FFT -> beamforming -> LS division at the pilot
- * subcarriers -> interpolation + MMSE detection. The FFT output, the beamformed grid and the table of LS
- * values at the pilot subcarriers live in the handle's workspace (n_slots <= max_slots); the interpolated
- * estimate is formed inside the detection kernel and never stored, with the same arithmetic as
- * pusch_chest_ls (so the result equals pusch_chest_ls + pusch_mmse_detect). Four kernels plus a
- * one-thread status reset. time_in, W, pilots, x_hat, bits, status: as in the stage entry points.
+ * subcarriers -> interpolated estimate (-> noise estimate when noise_var is PUSCH_NOISE_ESTIMATE) -> MMSE
+ * detection. The FFT output, the beamformed grid, the LS table and the estimate live in the handle's
+ * workspace (n_slots <= max_slots), with the arithmetic of the stage entry points (the result equals
+ * pusch_chest_ls + pusch_mmse_detect on the pusch_beamform output). With chol_every = K > 0 the estimate
+ * varies in time and the detector factorises once per group of K data symbols (pusch_cell_cfg).
+ * time_in, W, pilots, x_hat, bits, status: as in the stage entry points. Kernels: a one-thread status reset,
+ * then per run FFT, beamforming, LS table (+ noise estimate), estimate, detection; see pusch_set_pipeline.
  */
 pusch_status pusch_slot(pusch_handle *h, int n_slots, const void *time_in, const void *W, const void *pilots,
                         void *x_hat, uint8_t *bits, uint32_t *status, void *stream);
 
 /*
+ * Pipelining of pusch_slot and pusch_slot_host (a GPU scheduling choice; no counterpart in the paper).
+ * n_chunks = 1 (the default): the batch runs as one pass of the kernels on the caller's stream.
+ * n_chunks in [2, 16]: the batch runs as min(n_chunks, n_slots) passes over contiguous runs of slots (sizes
+ * differing by at most one), issued alternately on two streams owned by the handle; they start after the
+ * work already queued on the caller's stream and the caller's stream waits for them (events), so the call is
+ * still ordered on `stream`. Runs on the two streams overlap on the GPU (one run's FFT beside the other's
+ * detector; in pusch_slot_host one run's copies beside another's kernels). Results are bit-identical for
+ * every n_chunks: each slot's arithmetic does not depend on the batch it is in. Each run uses the workspace
+ * slice of its own slots. Returns PUSCH_ERR_ARG for n_chunks out of range, PUSCH_ERR_CUDA if the streams
+ * cannot be created (the setting is then unchanged).
+ */
+pusch_status pusch_set_pipeline(pusch_handle *h, int n_chunks);
+
+/*
  * pusch_slot on HOST buffers: copies time_in and pilots host->device into handle-owned staging buffers,
- * runs the chain, copies x_hat, bits and status device->host, all on `stream`, then waits for the stream.
+ * runs the chain, copies x_hat, bits and status device->host, then waits for `stream`. Without pipelining
+ * everything runs on `stream`; with it each run's copies go on that run's stream (pusch_set_pipeline).
  * W is a DEVICE pointer (it is fixed per cell). Host buffers should be page-locked for full speed.
  */
 pusch_status pusch_slot_host(pusch_handle *h, int n_slots, const void *time_in_host, const void *W,
@@ -346,11 +363,13 @@ pusch_status pusch_slot_noalloc(const pusch_cell_cfg *cfg, int n_slots, const vo
 
 /*
  * Per-stage device timing of pusch_slot (measurement aid; no counterpart in the paper).
- * pusch_profile_start arms timing for the next max_calls calls of pusch_slot on this handle: each call
- * records CUDA events on its stream before the FFT, after the FFT, after beamforming, after the LS pilot
- * table and after the detector. pusch_profile_read waits for the last recorded event, writes the summed
- * milliseconds of the four stages (FFT, beamforming, LS pilot table, detection) to stage_ms[0..3]
- * (n_stages >= 4) and the number of timed calls to *n_calls, and disarms timing.
+ * pusch_profile_start arms timing for the next max_calls calls of pusch_slot / pusch_slot_host on this
+ * handle (at the pipelining set when it is called): each run of the chain records CUDA events on its own
+ * stream before the FFT, after the FFT, after beamforming, after the estimate (LS table, noise estimate,
+ * interpolation) and after the detector. pusch_profile_read waits for the recorded events, writes the
+ * milliseconds of the four stages summed over all timed runs (FFT, beamforming, estimate, detection) to
+ * stage_ms[0..3] (n_stages >= 4) and the number of timed calls to *n_calls, and disarms timing. With
+ * pipelining a stage's time is that of its kernels while they share the GPU with the other stream's.
  */
 pusch_status pusch_profile_start(pusch_handle *h, int max_calls);
 pusch_status pusch_profile_read(pusch_handle *h, float *stage_ms, int n_stages, int *n_calls);

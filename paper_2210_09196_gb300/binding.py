@@ -37,7 +37,7 @@ EXPORTS = (
     "pusch_create", "pusch_destroy", "pusch_workspace_size", "pusch_sc_pitch", "pusch_freq_bytes", "pusch_ofdm_fft",
     "pusch_beamform",
     "pusch_chest_ls", "pusch_noise_estimate", "pusch_mmse_detect", "pusch_slot", "pusch_slot_host",
-    "pusch_last_error", "pusch_version",
+    "pusch_set_pipeline", "pusch_last_error", "pusch_version",
     "pusch_slot_noalloc", "pusch_profile_start", "pusch_profile_read",
     "pusch_batch_create", "pusch_batch_destroy", "pusch_batch_sizes", "pusch_batch_run", "pusch_batch_autotune",
     "pusch_batch_tuning",
@@ -108,6 +108,7 @@ def lib():
             "pusch_slot_host": (I, [P, I, P, P, P, P, P, P, P]),
             "pusch_slot_noalloc": (I, [ctypes.POINTER(pusch_cell_cfg), I, P, P, P, P, P, P, P]),
             "pusch_profile_start": (I, [P, I]),
+            "pusch_set_pipeline": (I, [P, I]),
             "pusch_profile_read": (I, [P, ctypes.POINTER(ctypes.c_float), I, ctypes.POINTER(I)]),
             "pusch_batch_create": (I, [ctypes.POINTER(P), ctypes.POINTER(pusch_cell_cfg), I,
                                        ctypes.POINTER(pusch_user_desc), I]),
@@ -231,6 +232,10 @@ def pusch_slot_noalloc(cfg: pusch_cell_cfg, n_slots, time_in, W, pilots, x_hat, 
 
 
 SLOT_STAGES = ("fft", "beamform", "ls", "detect")
+
+
+def pusch_set_pipeline(h, n_chunks: int) -> None:
+    _check(lib().pusch_set_pipeline(h, n_chunks), "pusch_set_pipeline")
 
 
 def pusch_profile_start(h, max_calls: int) -> None:

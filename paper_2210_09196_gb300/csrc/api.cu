@@ -101,9 +101,18 @@ size_t H_bytes(const pusch::Geometry &g, int n_slots) {
     return (size_t)g.n_groups * n_slots * g.n_sc * g.n_layers * g.n_beams * sizeof(float2);
 }
 
+constexpr int kMaxChunks = 16;  // pusch_set_pipeline limit
+
+// The FFT output of a chunk run is a self-contained buffer of the chunk's slots (the FP8 form keeps its
+// scales after its own planes), so chunk c starts after the 256-byte-aligned buffers of the chunks before it.
+// Slack over one buffer of all slots: at most 2 x 256 bytes of alignment per chunk.
+size_t freq_ws_bytes(const pusch::Geometry &g, int max_slots) {
+    return align256(freq_bytes(g, max_slots)) + 2 * 256 * kMaxChunks;
+}
+
 size_t workspace_bytes(const pusch::Geometry &g, int max_slots) {
     size_t b = align256(g.n_fft * sizeof(float2));
-    b += align256(freq_bytes(g, max_slots)) + align256(beam_bytes(g, max_slots)) + align256(ls_bytes(g, max_slots));
+    b += freq_ws_bytes(g, max_slots) + align256(beam_bytes(g, max_slots)) + align256(ls_bytes(g, max_slots));
     b += align256(H_bytes(g, max_slots));
     b += align256((size_t)max_slots * pusch::kNoiseParts * sizeof(float2)) + align256((size_t)max_slots * sizeof(float));
     return b;
@@ -225,7 +234,7 @@ pusch_status pusch_create(pusch_handle **out, const pusch_cell_cfg *cfg, int max
         goto cuda_error;
     if ((e = cudaMalloc((void **)&h->kernel_err, 16)) != cudaSuccess) goto cuda_error;
     if ((e = cudaMemset(h->kernel_err, 0, 16)) != cudaSuccess) goto cuda_error;
-    if ((e = cudaMalloc(&h->freq, freq_bytes(g, max_slots))) != cudaSuccess) goto cuda_error;
+    if ((e = cudaMalloc(&h->freq, freq_ws_bytes(g, max_slots))) != cudaSuccess) goto cuda_error;
     if ((e = cudaMalloc((void **)&h->beam, beam_bytes(g, max_slots))) != cudaSuccess) goto cuda_error;
     if ((e = cudaMalloc((void **)&h->ls, ls_bytes(g, max_slots))) != cudaSuccess) goto cuda_error;
     if ((e = cudaMalloc((void **)&h->H, H_bytes(g, max_slots))) != cudaSuccess) goto cuda_error;
@@ -246,6 +255,11 @@ pusch_status pusch_destroy(pusch_handle *h) {
     if (!h) return ok();
     cudaDeviceSynchronize();
     for (cudaEvent_t ev : h->prof_events) cudaEventDestroy(ev);
+    for (int j = 0; j < 2; ++j) {
+        if (h->pipe[j]) cudaStreamDestroy(h->pipe[j]);
+        if (h->ev_join[j]) cudaEventDestroy(h->ev_join[j]);
+    }
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     cudaFree(h->twiddle);
     cudaFree(h->kernel_err);
     cudaFree(h->freq);
@@ -336,45 +350,176 @@ pusch_status pusch_mmse_detect(pusch_handle *h, int n_slots, const void *H_hat, 
     return ok();
 }
 
+}  // extern "C"
+
+namespace {
+
+// Chunk c of a batch of n slots split into k contiguous runs whose sizes differ by at most one.
+void chunk_of(int n, int k, int c, int &s0, int &nc) {
+    const int q = n / k, r = n % k;
+    s0 = c * q + (c < r ? c : r);
+    nc = q + (c < r ? 1 : 0);
+}
+
+// Profiling records for one call of `runs` chunk runs (nullptr: not timed).
+cudaEvent_t *take_records(pusch_handle *h, int runs) {
+    if (h->prof_records + runs > h->prof_max_records) return nullptr;
+    cudaEvent_t *ev = &h->prof_events[(size_t)h->prof_records * (kSlotStages + 1)];
+    h->prof_records += runs;
+    ++h->prof_calls;
+    return ev;
+}
+
+// The chain over slots [s0, s0 + n) of a call, on stream s, in the handle's workspace slice of those slots
+// (freq_off: byte offset of the chunk's FFT output buffer). ev: kSlotStages + 1 events or nullptr.
+pusch_status run_chain(pusch_handle *h, int s0, int n, size_t freq_off, const void *time_in, const void *W,
+                       const void *pilots, void *x_hat, uint8_t *bits, uint32_t *stat, cudaStream_t s,
+                       cudaEvent_t *ev) {
+    const pusch::Geometry &g = h->geo;
+    const char *tin = (const char *)time_in + time_bytes(g, s0);
+    const float2 *pil = (const float2 *)((const char *)pilots + pilot_bytes(g, s0));
+    float2 *xh = (float2 *)x_hat + xhat_count(g, s0);
+    uint8_t *bt = bits + xhat_count(g, s0);
+    void *freq = (char *)h->freq + freq_off;
+    float2 *beam = h->beam + beam_bytes(g, s0) / sizeof(float2);
+    float2 *ls = h->ls + ls_bytes(g, s0) / sizeof(float2);
+    float2 *H = h->H + H_bytes(g, s0) / sizeof(float2);
+    float2 *ne_partial = h->ne_partial + (size_t)s0 * pusch::kNoiseParts;
+    float *sigma2 = h->sigma2 + s0;
+    cudaError_t e;
+    if (ev) cudaEventRecord(ev[0], s);
+    if ((e = pusch::launch_fft(g, n, tin, freq, h->twiddle, h->kernel_err, s)) != cudaSuccess)
+        return cuda_fail(e, "fft launch");
+    if (ev) cudaEventRecord(ev[1], s);
+    if ((e = pusch::launch_beamform(g, n, freq, (const float2 *)W, beam, h->kernel_err, s)) != cudaSuccess)
+        return cuda_fail(e, "beamforming launch");
+    if (ev) cudaEventRecord(ev[2], s);
+    const bool est = h->cfg.noise_var == PUSCH_NOISE_ESTIMATE;
+    const bool tv = g.chol_every > 0;
+    // the two-symbol-mean table: the estimate itself, or the noise estimator's reference when the estimate
+    // varies in time
+    if ((!tv || est) && (e = pusch::launch_ls_pilots(g, n, beam, pil, ls, s)) != cudaSuccess)
+        return cuda_fail(e, "LS pilot table launch");
+    if (est && (e = pusch::launch_noise_est(g, n, beam, pil, ne_partial, sigma2, s)) != cudaSuccess)
+        return cuda_fail(e, "noise estimation launch");
+    if (tv) {  // per-DMRS-symbol tables and one estimate per detection group
+        if ((e = pusch::launch_chest_time(g, n, beam, pil, H, ls, s)) != cudaSuccess)
+            return cuda_fail(e, "time-varying estimate launch");
+    } else if ((e = pusch::launch_chest_interp(g, n, ls, H, s)) != cudaSuccess) {
+        return cuda_fail(e, "estimate interpolation launch");
+    }
+    if (ev) cudaEventRecord(ev[3], s);
+    if ((e = pusch::launch_mmse(g, n, H, beam, xh, bt, stat, s, est ? sigma2 : nullptr, tv)) != cudaSuccess)
+        return cuda_fail(e, "detection launch");
+    if (ev) cudaEventRecord(ev[4], s);
+    return PUSCH_OK;
+}
+
+// Fork: the pipeline streams wait for everything issued so far on s.
+pusch_status pipe_fork(pusch_handle *h, cudaStream_t s) {
+    cudaError_t e = cudaEventRecord(h->ev_fork, s);
+    for (int j = 0; j < 2 && e == cudaSuccess; ++j) e = cudaStreamWaitEvent(h->pipe[j], h->ev_fork, 0);
+    return e == cudaSuccess ? PUSCH_OK : cuda_fail(e, "pipeline fork");
+}
+
+// Join: s waits for everything issued on the pipeline streams.
+pusch_status pipe_join(pusch_handle *h, cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+    for (int j = 0; j < 2 && e == cudaSuccess; ++j) {
+        e = cudaEventRecord(h->ev_join[j], h->pipe[j]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->ev_join[j], 0);
+    }
+    return e == cudaSuccess ? PUSCH_OK : cuda_fail(e, "pipeline join");
+}
+
+// Copies of one chunk for pusch_slot_host: `in` = host->device inputs before the chain, else outputs back.
+pusch_status chunk_copies(pusch_handle *h, bool in, int s0, int n, const void *time_host, const void *pil_host,
+                          void *xhat_host, uint8_t *bits_host, cudaStream_t s) {
+    const pusch::Geometry &g = h->geo;
+    cudaError_t e;
+    if (in) {
+        e = cudaMemcpyAsync((char *)h->h_time + time_bytes(g, s0), (const char *)time_host + time_bytes(g, s0),
+                            time_bytes(g, n), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync((char *)h->h_pilots + pilot_bytes(g, s0), (const char *)pil_host + pilot_bytes(g, s0),
+                                pilot_bytes(g, n), cudaMemcpyHostToDevice, s);
+        return e == cudaSuccess ? PUSCH_OK : cuda_fail(e, "input copy");
+    }
+    const size_t x0 = xhat_count(g, s0), nx = xhat_count(g, n);
+    e = cudaMemcpyAsync((float2 *)xhat_host + x0, h->h_xhat + x0, nx * sizeof(float2), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(bits_host + x0, h->h_bits + x0, nx, cudaMemcpyDeviceToHost, s);
+    return e == cudaSuccess ? PUSCH_OK : cuda_fail(e, "output copy");
+}
+
+// pusch_slot / pusch_slot_host body: the status reset on s, then the chain, as one run on s or as chunk runs
+// alternating over the two pipeline streams. With host buffers (time_host != nullptr) each run is bracketed
+// by its own input and output copies on its stream, so copies of one chunk overlap the kernels of another.
+pusch_status slot_batch(pusch_handle *h, int n_slots, const void *time_in, const void *W, const void *pilots,
+                        void *x_hat, uint8_t *bits, uint32_t *stat, cudaStream_t s, const void *time_host,
+                        const void *pil_host, void *xhat_host, uint8_t *bits_host) {
+    pusch_status st;
+    if ((st = reset_status(stat, s)) != PUSCH_OK) return st;
+    const int k = h->pipeline < n_slots ? h->pipeline : n_slots;
+    cudaEvent_t *ev = h->prof_events.empty() ? nullptr : take_records(h, k);
+    if (k > 1 && (st = pipe_fork(h, s)) != PUSCH_OK) return st;
+    size_t freq_off = 0;
+    for (int c = 0; c < k; ++c) {
+        int s0, nc;
+        chunk_of(n_slots, k, c, s0, nc);
+        cudaStream_t cs = k > 1 ? h->pipe[c & 1] : s;
+        if (time_host && (st = chunk_copies(h, true, s0, nc, time_host, pil_host, nullptr, nullptr, cs)) != PUSCH_OK)
+            return st;
+        st = run_chain(h, s0, nc, freq_off, time_in, W, pilots, x_hat, bits, stat, cs,
+                       ev ? ev + (size_t)c * (kSlotStages + 1) : nullptr);
+        if (st != PUSCH_OK) return st;
+        if (time_host && (st = chunk_copies(h, false, s0, nc, nullptr, nullptr, xhat_host, bits_host, cs)) != PUSCH_OK)
+            return st;
+        freq_off += align256(freq_bytes(h->geo, nc));
+    }
+    if (k > 1 && (st = pipe_join(h, s)) != PUSCH_OK) return st;
+    return PUSCH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 pusch_status pusch_slot(pusch_handle *h, int n_slots, const void *time_in, const void *W, const void *pilots,
                         void *x_hat, uint8_t *bits, uint32_t *status, void *stream) {
     pusch_status st = check_handle(h, n_slots);
     if (st != PUSCH_OK) return st;
     if (n_slots == 0) return ok();
     if (!time_in || !W || !pilots || !x_hat || !bits) return fail(PUSCH_ERR_ARG, "pusch_slot: NULL buffer");
-    cudaStream_t s = (cudaStream_t)stream;
-    cudaEvent_t *ev = nullptr;
-    if (h->prof_calls < h->prof_max_calls) ev = &h->prof_events[(size_t)h->prof_calls++ * (kSlotStages + 1)];
-    if (ev) cudaEventRecord(ev[0], s);
-    if ((st = pusch_ofdm_fft(h, n_slots, time_in, h->freq, stream)) != PUSCH_OK) return st;
-    if (ev) cudaEventRecord(ev[1], s);
-    if ((st = pusch_beamform(h, n_slots, h->freq, W, h->beam, stream)) != PUSCH_OK) return st;
-    if (ev) cudaEventRecord(ev[2], s);
     uint32_t *stat = status ? status : h->status_sink;
-    if ((st = reset_status(stat, s)) != PUSCH_OK) return st;
-    const bool est = h->cfg.noise_var == PUSCH_NOISE_ESTIMATE;
-    const bool tv = h->geo.chol_every > 0;
-    cudaError_t e = cudaSuccess;
-    // the two-symbol-mean table: the estimate itself, or the noise estimator's reference when the estimate
-    // varies in time
-    if ((!tv || est) &&
-        (e = pusch::launch_ls_pilots(h->geo, n_slots, h->beam, (const float2 *)pilots, h->ls, s)) != cudaSuccess)
-        return cuda_fail(e, "LS pilot table launch");
-    if (est && (e = pusch::launch_noise_est(h->geo, n_slots, h->beam, (const float2 *)pilots, h->ne_partial,
-                                            h->sigma2, s)) != cudaSuccess)
-        return cuda_fail(e, "noise estimation launch");
-    if (tv) {   // per-DMRS-symbol tables and one estimate per detection group
-        if ((e = pusch::launch_chest_time(h->geo, n_slots, h->beam, (const float2 *)pilots, h->H, h->ls, s)) !=
-            cudaSuccess)
-            return cuda_fail(e, "time-varying estimate launch");
-    } else if ((e = pusch::launch_chest_interp(h->geo, n_slots, h->ls, h->H, s)) != cudaSuccess) {
-        return cuda_fail(e, "estimate interpolation launch");
+    st = slot_batch(h, n_slots, time_in, W, pilots, x_hat, bits, stat, (cudaStream_t)stream, nullptr, nullptr, nullptr,
+                    nullptr);
+    return st == PUSCH_OK ? ok() : st;
+}
+
+pusch_status pusch_set_pipeline(pusch_handle *h, int n_chunks) {
+    if (!h) return fail(PUSCH_ERR_ARG, "handle is NULL");
+    if (n_chunks < 1 || n_chunks > kMaxChunks) return fail(PUSCH_ERR_ARG, "n_chunks=%d out of [1, %d]", n_chunks,
+                                                             kMaxChunks);
+    if (n_chunks > 1 && !h->ev_fork) {
+        cudaError_t e = cudaSuccess;
+        for (int j = 0; j < 2 && e == cudaSuccess; ++j) {
+            e = cudaStreamCreateWithFlags(&h->pipe[j], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join[j], cudaEventDisableTiming);
+        }
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            for (int j = 0; j < 2; ++j) {
+                if (h->pipe[j]) cudaStreamDestroy(h->pipe[j]);
+                if (h->ev_join[j]) cudaEventDestroy(h->ev_join[j]);
+                h->pipe[j] = nullptr;
+                h->ev_join[j] = nullptr;
+            }
+            if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+            h->ev_fork = nullptr;
+            return cuda_fail(e, "pipeline streams");
+        }
     }
-    if (ev) cudaEventRecord(ev[3], s);
-    e = pusch::launch_mmse(h->geo, n_slots, h->H, h->beam, (float2 *)x_hat, bits, stat, s, est ? h->sigma2 : nullptr,
-                           tv);
-    if (e != cudaSuccess) return cuda_fail(e, "detection launch");
-    if (ev) cudaEventRecord(ev[4], s);
+    h->pipeline = n_chunks;
     return ok();
 }
 
@@ -382,16 +527,17 @@ pusch_status pusch_profile_start(pusch_handle *h, int max_calls) {
     if (!h) return fail(PUSCH_ERR_ARG, "handle is NULL");
     if (max_calls < 0 || max_calls > 1000000) return fail(PUSCH_ERR_ARG, "max_calls out of [0, 1e6]");
     for (cudaEvent_t ev : h->prof_events) cudaEventDestroy(ev);
-    h->prof_events.assign((size_t)max_calls * (kSlotStages + 1), nullptr);
+    const int records = max_calls * h->pipeline;
+    h->prof_events.assign((size_t)records * (kSlotStages + 1), nullptr);
     for (auto &ev : h->prof_events) {
         cudaError_t e = cudaEventCreate(&ev);
         if (e != cudaSuccess) {
-            h->prof_max_calls = h->prof_calls = 0;
+            h->prof_max_records = h->prof_records = h->prof_calls = 0;
             return cuda_fail(e, "profiling event");
         }
     }
-    h->prof_max_calls = max_calls;
-    h->prof_calls = 0;
+    h->prof_max_records = records;
+    h->prof_records = h->prof_calls = 0;
     return ok();
 }
 
@@ -399,24 +545,21 @@ pusch_status pusch_profile_read(pusch_handle *h, float *stage_ms, int n_stages, 
     if (!h) return fail(PUSCH_ERR_ARG, "handle is NULL");
     if (!stage_ms || n_stages < kSlotStages) return fail(PUSCH_ERR_ARG, "stage_ms must hold %d values", kSlotStages);
     for (int k = 0; k < kSlotStages; ++k) stage_ms[k] = 0.f;
-    const int calls = h->prof_calls;
-    if (calls > 0) {
-        cudaError_t e = cudaEventSynchronize(h->prof_events[(size_t)calls * (kSlotStages + 1) - 1]);
+    for (int r = 0; r < h->prof_records; ++r) {
+        cudaEvent_t *ev = &h->prof_events[(size_t)r * (kSlotStages + 1)];
+        cudaError_t e = cudaEventSynchronize(ev[kSlotStages]);
         if (e != cudaSuccess) return cuda_fail(e, "profiling synchronize");
-    }
-    for (int c = 0; c < calls; ++c) {
-        cudaEvent_t *ev = &h->prof_events[(size_t)c * (kSlotStages + 1)];
         for (int k = 0; k < kSlotStages; ++k) {
             float ms = 0.f;
-            cudaError_t e = cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+            e = cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
             if (e != cudaSuccess) return cuda_fail(e, "profiling elapsed time");
             stage_ms[k] += ms;
         }
     }
-    if (n_calls) *n_calls = calls;
+    if (n_calls) *n_calls = h->prof_calls;
     for (cudaEvent_t ev : h->prof_events) cudaEventDestroy(ev);
     h->prof_events.clear();
-    h->prof_max_calls = h->prof_calls = 0;
+    h->prof_max_records = h->prof_records = h->prof_calls = 0;
     return ok();
 }
 
@@ -442,19 +585,9 @@ pusch_status pusch_slot_host(pusch_handle *h, int n_slots, const void *time_in_h
             return cuda_fail(e, "staging");
     }
     cudaStream_t s = (cudaStream_t)stream;
-    if ((e = cudaMemcpyAsync(h->h_time, time_in_host, time_bytes(g, n_slots), cudaMemcpyHostToDevice, s)) !=
-        cudaSuccess)
-        return cuda_fail(e, "input copy");
-    if ((e = cudaMemcpyAsync(h->h_pilots, pilots_host, pilot_bytes(g, n_slots), cudaMemcpyHostToDevice, s)) !=
-        cudaSuccess)
-        return cuda_fail(e, "pilot copy");
-    st = pusch_slot(h, n_slots, h->h_time, W, h->h_pilots, h->h_xhat, h->h_bits, h->h_status, stream);
+    st = slot_batch(h, n_slots, h->h_time, W, h->h_pilots, h->h_xhat, h->h_bits, h->h_status, s, time_in_host,
+                    pilots_host, x_hat_host, bits_host);
     if (st != PUSCH_OK) return st;
-    const size_t nx = xhat_count(g, n_slots);
-    if ((e = cudaMemcpyAsync(x_hat_host, h->h_xhat, nx * sizeof(float2), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
-        return cuda_fail(e, "output copy");
-    if ((e = cudaMemcpyAsync(bits_host, h->h_bits, nx, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
-        return cuda_fail(e, "output copy");
     if (status_host &&
         (e = cudaMemcpyAsync(status_host, h->h_status, 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s)) !=
             cudaSuccess)

@@ -181,9 +181,17 @@ struct pusch_handle {
     float2 *h_xhat = nullptr;
     uint8_t *h_bits = nullptr;
     uint32_t *h_status = nullptr;
-    // per-stage timing of pusch_slot (pusch_profile_start / pusch_profile_read)
-    std::vector<cudaEvent_t> prof_events;  // [max_calls][kSlotStages + 1]
-    int prof_max_calls = 0;
+    // pipelined pusch_slot (pusch_set_pipeline): the batch runs as `pipeline` chunks of slots alternating over
+    // two streams, forked from and joined to the caller's stream by events
+    int pipeline = 1;
+    cudaStream_t pipe[2] = {nullptr, nullptr};
+    cudaEvent_t ev_fork = nullptr;
+    cudaEvent_t ev_join[2] = {nullptr, nullptr};
+    // per-stage timing of pusch_slot (pusch_profile_start / pusch_profile_read): one record of
+    // kSlotStages + 1 events per chunk run
+    std::vector<cudaEvent_t> prof_events;  // [max_records][kSlotStages + 1]
+    int prof_max_records = 0;
+    int prof_records = 0;
     int prof_calls = 0;
     // learned-estimator workspace (pusch_chest_cnn; allocated on first use, sized for max_slots)
     void *cnn_grid = nullptr;       // [grids][2][2][n_sc] bf16

@@ -118,6 +118,10 @@ class Receiver:
         B.pusch_chest_ls(self.h, n, beam, pilots, H, stream)
         return H
 
+    def set_pipeline(self, n_chunks: int):
+        """Run pusch_slot / pusch_slot_host batches as n_chunks runs over two streams (1 = one run)."""
+        B.pusch_set_pipeline(self.h, n_chunks)
+
     def noise_estimate(self, beam, pilots, stream=None):
         n = beam.shape[0]
         out = torch.empty(n, dtype=torch.float32, device=self.device)

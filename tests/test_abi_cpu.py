@@ -95,5 +95,6 @@ def test_null_handle_and_bad_batch_rejected(B):
     assert L.pusch_ofdm_fft(None, 1, 1, 1, None) == B.PUSCH_ERR_ARG
     assert L.pusch_slot(None, 1, 1, 1, 1, 1, 1, None, None) == B.PUSCH_ERR_ARG
     assert L.pusch_destroy(None) == B.PUSCH_OK
+    assert L.pusch_set_pipeline(None, 2) == B.PUSCH_ERR_ARG
     with pytest.raises(B.PuschError):
         B.pusch_ofdm_fft(None, 1, 1, 1, stream=0)
