@@ -33,16 +33,32 @@ __host__ __device__ __forceinline__ int htile(int nb) {
     return (m + 1) & ~1;
 }
 
+// Row stride of the data-symbol rows in the single-cell detector: at least NL for the 16-layer class, whose
+// solve transposes the right-hand sides through those rows (detect_group, RHS_LANES).
+template <int NL>
+__host__ __device__ __forceinline__ int y_stride(int nb) {
+    const int hs = row_stride(nb);
+    return NL == 16 && hs < NL ? NL : hs;
+}
+
 // Shared memory of one warp of the single-cell detector: per subcarrier the H tile and the data-symbol rows.
 template <int NL>
 __host__ __device__ __forceinline__ size_t warp_smem_bytes(int nb, int nd) {
-    return (size_t)(32 / NL) * ((htile<NL>(nb) + (size_t)nd * row_stride(nb)) * sizeof(float2));
+    return (size_t)(32 / NL) * ((htile<NL>(nb) + (size_t)nd * y_stride<NL>(nb)) * sizeof(float2));
 }
 
 __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
 }
 
+
+// Shared-memory load kept in program order (volatile): the fully unrolled solves would otherwise hoist their
+// L loads far ahead of use and run out of registers.
+__device__ __forceinline__ float2 lds_ordered(const float2 *p) {
+    float2 v;
+    asm volatile("ld.volatile.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(smem_addr(p)));
+    return v;
+}
 
 __device__ __forceinline__ float2 det_shfl2(float2 v, int src) {
     return make_float2(__shfl_sync(kDetFull, v.x, src), __shfl_sync(kDetFull, v.y, src));
@@ -59,11 +75,15 @@ __device__ __forceinline__ uint8_t det_demap(float2 x, int q) {
 // Returns true when a pivot was not a positive finite number (the factorisation continued with 1).
 // load: sigma^2 + extra loading, or, when sigma2 is not NULL, sigma2[slot] + load (the per-slot noise estimate;
 // read only where the diagonal is loaded, so nothing extra stays live across the Gram loop).
-template <int NL, int ND, int NR>
+// RHS_LANES (16-layer class): the solves run with one data symbol per lane instead of one layer per lane
+// (below); the data-symbol rows yt then have stride ys >= NL and are overwritten.
+template <int NL, int ND, int NR, bool RHS_LANES = false>
 __device__ __forceinline__ bool detect_group(const float2 *__restrict__ hr, const float2 *__restrict__ hg,
-                                             const float2 *__restrict__ yt, float2 *lt, int hs, int nb, int nd,
+                                             float2 *yt, float2 *lt, int hs, int nb, int nd,
                                              int nl, float load, int i, int src0, float2 (&acc)[NR],
-                                             const float *__restrict__ sigma2 = nullptr, long long slot = 0) {
+                                             const float *__restrict__ sigma2 = nullptr, long long slot = 0,
+                                             int ys = 0) {
+    if (ys == 0) ys = hs;
     constexpr unsigned kFull = kDetFull;
     // ---- 2a. Gram row i: G[j] = sum_b conj(H[i][b]) H[j][b], with packed FP32x2 FMAs: P[j] = sum_b Re(h_b) H[j][b]
     //         and Q[j] = sum_b Im(h_b) H[j][b] (h_b = H[i][b]), then G[j] = P[j] - i Q[j].
@@ -121,7 +141,7 @@ __device__ __forceinline__ bool detect_group(const float2 *__restrict__ hr, cons
 #pragma unroll
             for (int d = 0; d < NR; ++d) {
                 if (ND > 0 || d < nd) {
-                    const float4 yv = *reinterpret_cast<const float4 *>(yt + d * hs + b);
+                    const float4 yv = *reinterpret_cast<const float4 *>(yt + d * ys + b);
                     const float2 y0 = make_float2(yv.x, yv.y), y1 = make_float2(yv.z, yv.w);
                     acc[d] = __ffma2_rn(hx0, y0, acc[d]);
                     Q[d] = __ffma2_rn(hy0, y0, Q[d]);
@@ -136,7 +156,7 @@ __device__ __forceinline__ bool detect_group(const float2 *__restrict__ hr, cons
 #pragma unroll
             for (int d = 0; d < NR; ++d)
                 if (ND > 0 || d < nd) {
-                    const float2 y0 = yt[d * hs + b];
+                    const float2 y0 = yt[d * ys + b];
                     acc[d] = __ffma2_rn(hx0, y0, acc[d]);
                     Q[d] = __ffma2_rn(hy0, y0, Q[d]);
                 }
@@ -175,6 +195,55 @@ __device__ __forceinline__ bool detect_group(const float2 *__restrict__ hr, cons
 #pragma unroll
     for (int k = 0; k < NL; ++k) lt[i * (NL + 1) + k] = G[k];
     __syncwarp();
+
+    if constexpr (RHS_LANES) {
+        // ---- 4'. one data symbol per lane: r_d[i] (lane i) -> the group's dead y rows T[d][i] -> lane d holds
+        //          r_d[0..NL); forward z_k = (r_k - sum_{j<k} L[k][j] z_j) / L[k][k] and back
+        //          x_k = (z_k - sum_{j>k} conj(L[j][k]) x_j) / L[k][k] in registers, every L entry a broadcast
+        //          shared load (no shuffles, no idle upper-triangle lanes); then x back to lane i = layer.
+        //          Lanes d >= nd solve a copy of symbol 0 and discard it.
+        float *dv = reinterpret_cast<float *>(lt + NL * (NL + 1));
+        dv[i] = dinv;
+#pragma unroll
+        for (int d = 0; d < NR; ++d)
+            if (ND > 0 || d < nd) yt[d * ys + i] = acc[d];
+        __syncwarp();
+        const int dl = i < nd ? i : 0;
+        float2 u[NL];
+#pragma unroll
+        for (int k = 0; k < NL; k += 2) {
+            const float4 v = *reinterpret_cast<const float4 *>(yt + dl * ys + k);
+            u[k] = make_float2(v.x, v.y);
+            u[k + 1] = make_float2(v.z, v.w);
+        }
+#pragma unroll
+        for (int k = 0; k < NL; ++k) {
+#pragma unroll
+            for (int j = 0; j < k; ++j) cfms(u[k], lds_ordered(lt + k * (NL + 1) + j), u[j]);
+            u[k] = cscale(u[k], dv[k]);
+        }
+#pragma unroll
+        for (int k = NL - 1; k >= 0; --k) {
+#pragma unroll
+            for (int j = k + 1; j < NL; ++j) {
+                const float2 l = lds_ordered(lt + j * (NL + 1) + k);  // u_k -= conj(L[j][k]) x_j
+                u[k].x -= l.x * u[j].x + l.y * u[j].y;
+                u[k].y -= l.x * u[j].y - l.y * u[j].x;
+            }
+            u[k] = cscale(u[k], dv[k]);
+        }
+        __syncwarp();  // every lane has read its row of T
+        if (i < nd) {
+#pragma unroll
+            for (int k = 0; k < NL; k += 2)
+                *reinterpret_cast<float4 *>(yt + i * ys + k) = make_float4(u[k].x, u[k].y, u[k + 1].x, u[k + 1].y);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int d = 0; d < NR; ++d)
+            if (ND > 0 || d < nd) acc[d] = yt[d * ys + i];
+        return bad;
+    }
 
     // ---- 4. forward L z = r, then back L^H x = z, for all data symbols, in unit-diagonal form:
     //         with D = diag(L), u = D z solves (L D^-1) u = r and x solves (D^-1 L^H) x = D^-1 z, so each step

@@ -97,11 +97,11 @@ mmse_kernel(MmseArgs g, long long total_sc, const float2 *__restrict__ H, const 
     const int src0 = grp * NL;
     const int nl = g.n_layers, nb = g.n_beams, n_sc = g.n_sc;
     const int nd = ND > 0 ? ND : g.n_data;
-    const int hs = row_stride(nb), ht = htile<NL>(nb);
+    const int hs = row_stride(nb), ht = htile<NL>(nb), ys = y_stride<NL>(nb);
 
     unsigned char *wbase = smem_raw + (size_t)warp * warp_smem_bytes<NL>(nb, nd);
     float2 *Ht = reinterpret_cast<float2 *>(wbase);  // [SPW][ht]
-    float2 *Yt = Ht + SPW * ht;                      // [SPW][nd][hs]
+    float2 *Yt = Ht + SPW * ht;                      // [SPW][nd][ys]
 
     const long long sc0 = ((long long)blockIdx.x * kMmseWarps + warp) * SPW;  // first (slot*n_sc + a) of warp
     if (sc0 >= total_sc) return;                                              // whole warp idle
@@ -120,7 +120,7 @@ mmse_kernel(MmseArgs g, long long total_sc, const float2 *__restrict__ H, const 
         for (; row < SPW * nd;) {
             const int gg = row / nd, d = row - gg * nd;
             const long long sc = sc0 + gg;
-            float2 *dst = Yt + (gg * nd + d) * hs + (wide ? 2 * c : c);
+            float2 *dst = Yt + (gg * nd + d) * ys + (wide ? 2 * c : c);
             if (sc < total_sc) {
                 const long long sl = sc / n_sc, aa = sc - sl * n_sc;
                 const float2 *src = beam + ((sl * g.n_sym + data_symbol(g, d)) * n_sc + aa) * nb + (wide ? 2 * c : c);
@@ -160,8 +160,9 @@ mmse_kernel(MmseArgs g, long long total_sc, const float2 *__restrict__ H, const 
         if (q > 0) __syncwarp();
         stage_H<NL>(Ht, GROUPS ? H + q * g.h_group_stride : H, sc0, total_sc, nl, nb, hs, ht, lane);
         __syncwarp();
-        bad |= detect_group<NL, ND, NR>(hr, hg, Yt + (grp * nd + d0) * hs, Ht + grp * ht, hs, nb, ndq, nl,
-                                        g.sigma2 ? g.loading : g.load, i, src0, acc, g.sigma2, valid ? slot : 0);
+        bad |= detect_group<NL, ND, NR, NL == 16>(hr, hg, Yt + (grp * nd + d0) * ys, Ht + grp * ht, hs, nb, ndq, nl,
+                                                  g.sigma2 ? g.loading : g.load, i, src0, acc, g.sigma2,
+                                                  valid ? slot : 0, ys);
         if (valid && i < nl) {
             const long long o0 = (slot * nl + i) * (long long)nd * n_sc + a;
 #pragma unroll
