@@ -30,7 +30,9 @@ template <int NL>
 __host__ __device__ __forceinline__ int htile(int nb) {
     const int a = NL * row_stride(nb), b = NL * (NL + 1) + NL / 2;  // L tile + 1/L[k][k] (NL floats)
     const int m = a > b ? a : b;
-    return (m + 1) & ~1;
+    // the next subcarrier's tile starts 16 bytes further into the 128-byte bank cycle, so that the groups of a
+    // warp reading the same element of their own tiles (broadcast 16-byte loads) hit different banks
+    return m + ((2 - m) & 15);
 }
 
 // Row stride of the data-symbol rows in the single-cell detector: at least NL for the 16-layer class, whose
@@ -52,14 +54,6 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
 }
 
 
-// Shared-memory load kept in program order (volatile): the fully unrolled solves would otherwise hoist their
-// L loads far ahead of use and run out of registers.
-__device__ __forceinline__ float2 lds_ordered(const float2 *p) {
-    float2 v;
-    asm volatile("ld.volatile.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(smem_addr(p)));
-    return v;
-}
-
 __device__ __forceinline__ float2 det_shfl2(float2 v, int src) {
     return make_float2(__shfl_sync(kDetFull, v.x, src), __shfl_sync(kDetFull, v.y, src));
 }
@@ -75,6 +69,111 @@ __device__ __forceinline__ uint8_t det_demap(float2 x, int q) {
 // Returns true when a pivot was not a positive finite number (the factorisation continued with 1).
 // load: sigma^2 + extra loading, or, when sigma2 is not NULL, sigma2[slot] + load (the per-slot noise estimate;
 // read only where the diagonal is loaded, so nothing extra stays live across the Gram loop).
+// Shared-memory load kept in program order (volatile): the fully unrolled factorisation and solves would
+// otherwise hoist their L loads far ahead of use and run out of registers.
+__device__ __forceinline__ float4 lds4_ordered(const float4 *p) {
+    float4 v;
+    asm volatile("ld.volatile.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(smem_addr(p)));
+    return v;
+}
+
+// Steps 3-4 for the 16-layer class (lane i holds row i of G; r_d[i] in acc[d]):
+//   * r_d[i] goes to the group's (dead) data-symbol rows T[d][i] (stride ys >= NL);
+//   * Crout Cholesky, column j at step j: s_i = G[i][j] - sum_{k<j} L[i][k] conj(L[j][k]) in lane i, the pivot
+//     s_j broadcast by one shuffle, L[i][j] = s_i / sqrt(s_j); lane i keeps its row of L in registers and
+//     publishes each entry to shared memory as (-Re, -Re, Im, Im) (packed lower triangle, rows in order), so
+//     that every complex multiply-add below is one broadcast 16-byte load and two packed FMAs;
+//   * lane d solves data symbol d: forward z_k = (r_k - sum_{j<k} L[k][j] z_j) / L[k][k], back
+//     x_k = (z_k - sum_{j>k} conj(L[j][k]) x_j) / L[k][k], in registers; lanes d >= nd solve a copy of symbol 0;
+//   * x_d[i] returns to lane i through T.
+// Uses the H tile (lt) for L: 120 float4 + NL floats.
+template <int NL, int ND, int NR>
+__device__ __forceinline__ bool factor_solve_rhs_lanes(float2 (&G)[NL], float2 *yt, float2 *lt, int ys, int nd,
+                                                       int i, int src0, float2 (&acc)[NR]) {
+    constexpr unsigned kFull = kDetFull;
+#pragma unroll
+    for (int d = 0; d < NR; ++d)
+        if (ND > 0 || d < nd) yt[d * ys + i] = acc[d];
+    float4 *L4 = reinterpret_cast<float4 *>(lt);                 // L[k][j], j < k, at k (k - 1) / 2 + j
+    float *dv = reinterpret_cast<float *>(L4 + NL * (NL - 1) / 2);  // 1 / L[k][k]
+    bool bad = false;
+    float dinv = 1.f;
+    {
+        float2 Lrot[NL];  // (-Im, Re) of lane i's L entries
+#pragma unroll
+        for (int j = 0; j < NL; ++j) {
+            float2 sj = G[j];
+#pragma unroll
+            for (int k = 0; k < j; ++k) {
+                const float4 b = lds4_ordered(L4 + j * (j - 1) / 2 + k);  // L[j][k], broadcast
+                sj = __ffma2_rn(make_float2(b.x, b.y), G[k], sj);          // G[k] holds L[i][k] by now
+                sj = __ffma2_rn(make_float2(b.z, b.w), Lrot[k], sj);
+            }
+            float dj = __shfl_sync(kFull, sj.x, src0 + j);
+            if (!(dj > 0.f) || !isfinite(dj)) {
+                bad = true;
+                dj = 1.f;
+            }
+            const float inv = rsqrtf(dj);
+            if (i > j) G[j] = cscale(sj, inv);
+            else if (i == j) G[j] = make_float2(dj * inv, 0.f);
+            else G[j] = make_float2(0.f, 0.f);
+            if (i == j) dinv = inv;
+            Lrot[j] = make_float2(-G[j].y, G[j].x);
+            if (i > j) L4[i * (i - 1) / 2 + j] = make_float4(-G[j].x, -G[j].x, G[j].y, G[j].y);
+            __syncwarp();
+        }
+    }
+    dv[i] = dinv;
+    __syncwarp();
+
+    const int dl = i < nd ? i : 0;
+    float2 u[NL], w[NL];
+#pragma unroll
+    for (int k = 0; k < NL; k += 2) {
+        const float4 v = *reinterpret_cast<const float4 *>(yt + dl * ys + k);
+        u[k] = make_float2(v.x, v.y);
+        u[k + 1] = make_float2(v.z, v.w);
+    }
+    // forward: u_k += (-Re L) u_j + (Im L) (Im u_j, -Re u_j) = u_k - L[k][j] u_j
+#pragma unroll
+    for (int k = 0; k < NL; ++k) {
+#pragma unroll
+        for (int j = 0; j < k; ++j) {
+            const float4 b = lds4_ordered(L4 + k * (k - 1) / 2 + j);
+            u[k] = __ffma2_rn(make_float2(b.x, b.y), u[j], u[k]);
+            u[k] = __ffma2_rn(make_float2(b.z, b.w), w[j], u[k]);
+        }
+        u[k] = cscale(u[k], dv[k]);
+        w[k] = make_float2(u[k].y, -u[k].x);
+    }
+    // back: u_k += (-Re L) x_j + (Im L) (-Im x_j, Re x_j) = u_k - conj(L[j][k]) x_j
+#pragma unroll
+    for (int k = NL - 1; k >= 0; --k) {
+#pragma unroll
+        for (int j = k + 1; j < NL; ++j) {
+            const float4 b = lds4_ordered(L4 + j * (j - 1) / 2 + k);
+            u[k] = __ffma2_rn(make_float2(b.x, b.y), u[j], u[k]);
+            u[k] = __ffma2_rn(make_float2(b.z, b.w), w[j], u[k]);
+        }
+        u[k] = cscale(u[k], dv[k]);
+        w[k] = make_float2(-u[k].y, u[k].x);
+    }
+    __syncwarp();  // every lane has read its row of T
+    if (i < nd) {
+#pragma unroll
+        for (int k = 0; k < NL; k += 2)
+            *reinterpret_cast<float4 *>(yt + i * ys + k) = make_float4(u[k].x, u[k].y, u[k + 1].x, u[k + 1].y);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int d = 0; d < NR; ++d)
+        if (ND > 0 || d < nd) acc[d] = yt[d * ys + i];
+    return bad;
+}
+
 // RHS_LANES (16-layer class): the solves run with one data symbol per lane instead of one layer per lane
 // (below); the data-symbol rows yt then have stride ys >= NL and are overwritten.
 template <int NL, int ND, int NR, bool RHS_LANES = false>
@@ -166,6 +265,8 @@ __device__ __forceinline__ bool detect_group(const float2 *__restrict__ hr, cons
     }
     __syncwarp();  // the H tile is reused for L below
 
+    if constexpr (RHS_LANES) return factor_solve_rhs_lanes<NL, ND, NR>(G, yt, lt, ys, nd, i, src0, acc);
+
     // ---- 3. Cholesky, right-looking, row i of L replaces row i of G; then L -> shared memory
     bool bad = false;
     float dinv = 1.f;
@@ -195,55 +296,6 @@ __device__ __forceinline__ bool detect_group(const float2 *__restrict__ hr, cons
 #pragma unroll
     for (int k = 0; k < NL; ++k) lt[i * (NL + 1) + k] = G[k];
     __syncwarp();
-
-    if constexpr (RHS_LANES) {
-        // ---- 4'. one data symbol per lane: r_d[i] (lane i) -> the group's dead y rows T[d][i] -> lane d holds
-        //          r_d[0..NL); forward z_k = (r_k - sum_{j<k} L[k][j] z_j) / L[k][k] and back
-        //          x_k = (z_k - sum_{j>k} conj(L[j][k]) x_j) / L[k][k] in registers, every L entry a broadcast
-        //          shared load (no shuffles, no idle upper-triangle lanes); then x back to lane i = layer.
-        //          Lanes d >= nd solve a copy of symbol 0 and discard it.
-        float *dv = reinterpret_cast<float *>(lt + NL * (NL + 1));
-        dv[i] = dinv;
-#pragma unroll
-        for (int d = 0; d < NR; ++d)
-            if (ND > 0 || d < nd) yt[d * ys + i] = acc[d];
-        __syncwarp();
-        const int dl = i < nd ? i : 0;
-        float2 u[NL];
-#pragma unroll
-        for (int k = 0; k < NL; k += 2) {
-            const float4 v = *reinterpret_cast<const float4 *>(yt + dl * ys + k);
-            u[k] = make_float2(v.x, v.y);
-            u[k + 1] = make_float2(v.z, v.w);
-        }
-#pragma unroll
-        for (int k = 0; k < NL; ++k) {
-#pragma unroll
-            for (int j = 0; j < k; ++j) cfms(u[k], lds_ordered(lt + k * (NL + 1) + j), u[j]);
-            u[k] = cscale(u[k], dv[k]);
-        }
-#pragma unroll
-        for (int k = NL - 1; k >= 0; --k) {
-#pragma unroll
-            for (int j = k + 1; j < NL; ++j) {
-                const float2 l = lds_ordered(lt + j * (NL + 1) + k);  // u_k -= conj(L[j][k]) x_j
-                u[k].x -= l.x * u[j].x + l.y * u[j].y;
-                u[k].y -= l.x * u[j].y - l.y * u[j].x;
-            }
-            u[k] = cscale(u[k], dv[k]);
-        }
-        __syncwarp();  // every lane has read its row of T
-        if (i < nd) {
-#pragma unroll
-            for (int k = 0; k < NL; k += 2)
-                *reinterpret_cast<float4 *>(yt + i * ys + k) = make_float4(u[k].x, u[k].y, u[k + 1].x, u[k + 1].y);
-        }
-        __syncwarp();
-#pragma unroll
-        for (int d = 0; d < NR; ++d)
-            if (ND > 0 || d < nd) acc[d] = yt[d * ys + i];
-        return bad;
-    }
 
     // ---- 4. forward L z = r, then back L^H x = z, for all data symbols, in unit-diagonal form:
     //         with D = diag(L), u = D z solves (L D^-1) u = r and x solves (D^-1 L^H) x = D^-1 z, so each step
