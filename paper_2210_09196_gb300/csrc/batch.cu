@@ -59,8 +59,17 @@ struct LsJob {                     // LS values at the pilots of one (user, laye
 
 struct DetArgs {
     int n_sym, n_data, dmrs0, dmrs1;
-    int data_sym[16];
+    int dmrs_lo, dmrs_hi;  // the two DMRS symbols in increasing order
 };
+
+// Symbol index of data symbol d (all non-DMRS symbols in increasing order), computed: a run-time index into
+// a kernel parameter array would copy the parameter block to local memory.
+__device__ __forceinline__ int data_symbol(const DetArgs &g, int d) {
+    int s = d;
+    if (s >= g.dmrs_lo) ++s;
+    if (s >= g.dmrs_hi) ++s;
+    return s;
+}
 
 // ------------------------------------------------------------------------------------------------ kernels
 
@@ -146,7 +155,7 @@ batch_detect_kernel(DetArgs g, int nbmax, const Segment *__restrict__ segs, cons
                 const int aa = it.y + gg;
                 float2 *dst = Yt + (gg * nd + d) * hs + b;
                 if (aa < sg.a0 + sg.n)
-                    pusch::cp_async8(dst, beam + sg.beam_off + ((long long)g.data_sym[d] * sg.n_sc + aa) * nb + b);
+                    pusch::cp_async8(dst, beam + sg.beam_off + ((long long)data_symbol(g, d) * sg.n_sc + aa) * nb + b);
                 else
                     *dst = make_float2(0.f, 0.f);
             }
@@ -560,7 +569,8 @@ pusch_status pusch_batch_create(pusch_batch **out, const pusch_cell_cfg *cells, 
     b->det.n_data = g0.n_data;
     b->det.dmrs0 = g0.dmrs0;
     b->det.dmrs1 = g0.dmrs1;
-    for (int d = 0; d < 16; ++d) b->det.data_sym[d] = g0.data_sym[d];
+    b->det.dmrs_lo = g0.dmrs0 < g0.dmrs1 ? g0.dmrs0 : g0.dmrs1;
+    b->det.dmrs_hi = g0.dmrs0 < g0.dmrs1 ? g0.dmrs1 : g0.dmrs0;
     const int nd = g0.n_data;
 
     // ---- per-cell offsets
