@@ -44,6 +44,9 @@ def lib():
             "orc_dft": (None, [P, I, P]),
             "orc_fft": (I, [P, I, P]),
             "orc_ofdm_demod": (I, [P, I, I, I, I, P, I, P]),
+            "orc_cp_len": (I, [I, I]),
+            "orc_slot_len": (ctypes.c_longlong, [I, I]),
+            "orc_ofdm_demod_cp": (I, [P, I, I, I, I, I, P]),
             "orc_beamform": (None, [P, P, I, I, I, I, P]),
             "orc_chest_ls": (I, [P, I, I, I, P, I, P, P, I, P, P, P]),
             "orc_gram": (None, [P, I, I, D, P]),
@@ -100,6 +103,28 @@ def fft(x) -> np.ndarray:
     if lib().orc_fft(_p(x), x.size, _p(X)) != 0:
         raise ValueError("orc_fft needs a power-of-two length")
     return X
+
+
+def cp_len(n_fft: int, sym: int) -> int:
+    """Normal cyclic-prefix length (samples) of symbol sym of a 30 kHz slot."""
+    return int(lib().orc_cp_len(n_fft, sym))
+
+
+def slot_len(n_sym: int, n_fft: int) -> int:
+    return int(lib().orc_slot_len(n_sym, n_fft))
+
+
+def ofdm_demod_cp(stream, n_sym: int, n_fft: int, n_sc: int, shift: bool = False) -> np.ndarray:
+    """stream [R, slot_len] (cyclic prefixes included) -> freq [S, R, N_SC]."""
+    stream = _c128(stream)
+    R = stream.shape[0]
+    if stream.shape[1] != slot_len(n_sym, n_fft):
+        raise ValueError("stream length is not the slot length")
+    freq = np.zeros((n_sym, R, n_sc), dtype=np.complex128)
+    rc = lib().orc_ofdm_demod_cp(_p(stream), n_sym, R, n_fft, n_sc, int(bool(shift)), _p(freq))
+    if rc != 0:
+        raise ValueError(f"orc_ofdm_demod_cp failed ({rc})")
+    return freq
 
 
 def ofdm_demod(time, n_sc: int, pairs=None) -> np.ndarray:

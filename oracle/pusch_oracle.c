@@ -10,6 +10,8 @@
  *   orc_dft         Section II "OFDM demodulation ... via a FFT": the DFT definition itself.
  *   orc_fft         textbook recursive radix-2 decimation-in-time FFT (pinned against orc_dft).
  *   orc_ofdm_demod  Section II: one FFT per antenna and OFDM symbol, keep the N_SC active bins.
+ *   orc_cp_len, orc_slot_len, orc_ofdm_demod_cp  the same on a slot with NR normal cyclic prefixes and the
+ *                   optional 7.5 kHz shift (TS 38.211 5.3.1, 5.4; not in the paper, which starts after them).
  *   orc_beamform    Section II: "a MMM with known coefficients", y = W^H x per subcarrier and symbol.
  *   orc_chest_ls    Section II: LS estimate = element-wise division of the received pilot REs by the
  *                   pilots (block-type pilots on whole OFDM symbols), averaged over the two DMRS
@@ -113,6 +115,58 @@ int orc_ofdm_demod(const cplx *time, int n_sym, int n_rx, int n_fft, int n_sc,
         cplx *f = freq + ((size_t)s * n_rx + r) * n_sc;
         for (int a = 0; a < n_sc; ++a) f[a] = X[active_bin(a, n_sc, n_fft)];
     }
+    free(X);
+    return rc;
+}
+
+/* Cyclic-prefix length in samples of symbol `sym` of a 14-symbol slot at 30 kHz subcarrier spacing with normal
+ * cyclic prefix (TS 38.211 5.3.1, mu = 1): 144 kappa 2^-mu T_c, plus 16 kappa T_c on the first symbol of every
+ * half subframe (symbol 0 of each slot), kappa = 64. One sample of an n_fft = 4096 transform lasts 16 T_c, so
+ * that is 288 and 352 samples, scaled by n_fft / 4096 (an integer for n_fft >= 128). */
+int orc_cp_len(int n_fft, int sym)
+{
+    return (sym == 0 ? 352 : 288) * n_fft / 4096;
+}
+
+/* Samples of one antenna's slot with cyclic prefixes: sum over the symbols of cp + n_fft. */
+long long orc_slot_len(int n_sym, int n_fft)
+{
+    long long t = 0;
+    for (int s = 0; s < n_sym; ++s) t += orc_cp_len(n_fft, s) + n_fft;
+    return t;
+}
+
+/* OFDM demodulation of a slot given as one sample stream per antenna, stream [n_rx][slot_len]: symbol s starts
+ * after the earlier symbols (each cp + n_fft samples) and its cp_s prefix samples are dropped. With shift != 0 the
+ * transmitter moved the spectrum up by 7.5 kHz, a quarter of the 30 kHz spacing, with the phase reference at the
+ * start of each symbol's useful part (TS 38.211 5.4): sample n of the useful part is multiplied by
+ * exp(-2 pi i n / (4 n_fft)) before the FFT. Then as orc_ofdm_demod: freq [n_sym][n_rx][n_sc]. */
+int orc_ofdm_demod_cp(const cplx *stream, int n_sym, int n_rx, int n_fft, int n_sc, int shift, cplx *freq)
+{
+    if (n_sc > n_fft || n_sc < 0 || n_fft < 128) return -1;
+    const long long slot_len = orc_slot_len(n_sym, n_fft);
+    cplx *x = malloc(sizeof(cplx) * (size_t)n_fft);
+    cplx *X = malloc(sizeof(cplx) * (size_t)n_fft);
+    if (!x || !X) {
+        free(x);
+        free(X);
+        return -2;
+    }
+    int rc = 0;
+    long long start = 0;
+    for (int s = 0; s < n_sym && rc == 0; ++s) {
+        start += orc_cp_len(n_fft, s);
+        for (int r = 0; r < n_rx && rc == 0; ++r) {
+            const cplx *u = stream + (size_t)r * slot_len + start;
+            for (int n = 0; n < n_fft; ++n)
+                x[n] = shift ? u[n] * cexp(-2.0 * I * ORC_PI * (double)n / (4.0 * (double)n_fft)) : u[n];
+            rc = orc_fft(x, n_fft, X);
+            cplx *f = freq + ((size_t)s * n_rx + r) * n_sc;
+            for (int a = 0; a < n_sc; ++a) f[a] = X[active_bin(a, n_sc, n_fft)];
+        }
+        start += n_fft;
+    }
+    free(x);
     free(X);
     return rc;
 }
