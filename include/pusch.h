@@ -90,6 +90,15 @@ typedef struct {
                           estimate at its mean symbol time and one factorisation per subcarrier (K = 1:
                           one per data symbol, Section VI's schedule; K = n_sym - 2 gives the 0 result
                           up to rounding)                                                          */
+    int cp;            /* 0: time samples [n_sym][n_rx][n_fft] per slot (prefixes already removed).
+                          1: NR normal cyclic prefixes (TS 38.211 5.3.1, 30 kHz): per slot one stream per
+                          antenna, [n_rx][slot_len] with slot_len = n_sym * n_fft + cp0 + (n_sym - 1) * cp1,
+                          cp0 = 352 * n_fft / 4096 (symbol 0), cp1 = 288 * n_fft / 4096 (other symbols);
+                          symbol s's useful part starts at s * (n_fft + cp1) + cp0. Needs n_fft >= 512.  */
+    int shift_7p5khz;  /* 1: the transmitter shifted the spectrum up by 7.5 kHz (a quarter of the 30 kHz
+                          spacing) with the phase reference at the start of each useful part (TS 38.211
+                          5.4): sample n of the useful part is multiplied by exp(-2 pi i n / (4 n_fft))
+                          before the FFT. 0: no shift.                                               */
 } pusch_cell_cfg;
 
 /* noise_var value that makes the chain estimate sigma^2 per slot (pusch_noise_estimate) instead of using a

@@ -59,6 +59,8 @@ class pusch_cell_cfg(ctypes.Structure):
         ("qam_bits", ctypes.c_int), ("in_fp16", ctypes.c_int), ("form", ctypes.c_int), ("n_sym", ctypes.c_int),
         ("dmrs_sym", ctypes.c_int * 2), ("noise_var", ctypes.c_float), ("loading", ctypes.c_float),
         ("chol_every", ctypes.c_int),
+        ("cp", ctypes.c_int),
+        ("shift_7p5khz", ctypes.c_int),
     ]
 
 
@@ -69,7 +71,7 @@ class pusch_user_desc(ctypes.Structure):
 
 def make_cfg(*, n_rx, n_fft, n_sc, n_beams, n_layers, comb=None, ports=None, qam_bits=2, in_fp16=False,
              form=PUSCH_FORM_FP32, noise_var=0.0, loading=0.0, n_sym=14, dmrs_sym=(2, 11),
-             chol_every=0) -> pusch_cell_cfg:
+             chol_every=0, cp=False, shift_7p5khz=False) -> pusch_cell_cfg:
     c = pusch_cell_cfg()
     c.n_rx, c.n_fft, c.n_sc, c.n_beams, c.n_layers = n_rx, n_fft, n_sc, n_beams, n_layers
     c.comb = n_layers if comb is None else comb
@@ -80,6 +82,7 @@ def make_cfg(*, n_rx, n_fft, n_sc, n_beams, n_layers, comb=None, ports=None, qam
     c.dmrs_sym[0], c.dmrs_sym[1] = dmrs_sym
     c.noise_var, c.loading = float(noise_var), float(loading)
     c.chol_every = int(chol_every)
+    c.cp, c.shift_7p5khz = int(bool(cp)), int(bool(shift_7p5khz))
     return c
 
 
@@ -136,10 +139,14 @@ def lib():
 
 
 def _ptr(x):
+    """Address of a buffer: None, a raw address (int), or a tensor, which must be contiguous (the C ABI takes
+    dense row-major buffers)."""
     if x is None:
         return None
     if isinstance(x, int):
         return x
+    if hasattr(x, "is_contiguous") and not x.is_contiguous():
+        raise ValueError("buffers passed to libpusch must be contiguous tensors")
     return x.data_ptr()
 
 

@@ -61,6 +61,10 @@ pusch_status validate_cfg(const pusch_cell_cfg *c) {
     if (!(c->loading >= 0.f) || !isfinite(c->loading)) return fail(PUSCH_ERR_ARG, "loading must be >= 0");
     if (c->chol_every < 0 || c->chol_every > c->n_sym - 2)
         return fail(PUSCH_ERR_ARG, "chol_every=%d out of [0, n_sym - 2]", c->chol_every);
+    if ((c->cp != 0 && c->cp != 1) || (c->shift_7p5khz != 0 && c->shift_7p5khz != 1))
+        return fail(PUSCH_ERR_ARG, "cp and shift_7p5khz must be 0 or 1");
+    if (c->cp && c->n_fft < 512)
+        return fail(PUSCH_ERR_UNSUPPORTED, "cyclic prefixes need n_fft >= 512 (n_fft=%d)", c->n_fft);
     if (c->form == PUSCH_FORM_MIXED) {
         pusch::Geometry g = pusch::make_geometry(*c);
         if (!pusch::bf_tc_supported(g))
@@ -87,7 +91,7 @@ size_t ls_bytes(const pusch::Geometry &g, int n_slots) {
            sizeof(float2);
 }
 size_t time_bytes(const pusch::Geometry &g, int n_slots) {
-    return (size_t)n_slots * g.n_sym * g.n_rx * g.n_fft * (g.in_fp16 ? 4 : 8);
+    return (size_t)n_slots * pusch::time_elems_per_slot(g) * (g.in_fp16 ? 4 : 8);
 }
 size_t pilot_bytes(const pusch::Geometry &g, int n_slots) {
     return (size_t)n_slots * g.n_layers * 2 * g.n_sc * sizeof(float2);
@@ -111,7 +115,7 @@ size_t freq_ws_bytes(const pusch::Geometry &g, int max_slots) {
 }
 
 size_t workspace_bytes(const pusch::Geometry &g, int max_slots) {
-    size_t b = align256(g.n_fft * sizeof(float2));
+    size_t b = align256(pusch::fft_twiddle_count(g.n_fft) * sizeof(float2));
     b += freq_ws_bytes(g, max_slots) + align256(beam_bytes(g, max_slots)) + align256(ls_bytes(g, max_slots));
     b += align256(H_bytes(g, max_slots));
     b += align256((size_t)max_slots * pusch::kNoiseParts * sizeof(float2)) + align256((size_t)max_slots * sizeof(float));
@@ -163,6 +167,11 @@ Geometry make_geometry(const pusch_cell_cfg &c) {
     g.noise_var = c.noise_var;
     g.loading = c.loading;
     g.chol_every = c.chol_every;
+    g.cp = c.cp;
+    g.cp0 = c.cp ? 352 * c.n_fft / 4096 : 0;
+    g.cp1 = c.cp ? 288 * c.n_fft / 4096 : 0;
+    g.slot_len = (long long)c.n_sym * c.n_fft + (c.cp ? g.cp0 + (long long)(c.n_sym - 1) * g.cp1 : 0);
+    g.shift = c.shift_7p5khz;
     g.sc_pitch = c.form == PUSCH_FORM_FP8 ? (c.n_sc + 15) & ~15 : (c.n_sc + 7) & ~7;
     for (int l = 0; l < 32; ++l) g.port[l] = l < c.n_layers ? c.port[l] : 0;
     int nd = 0;
@@ -224,13 +233,9 @@ pusch_status pusch_create(pusch_handle **out, const pusch_cell_cfg *cfg, int max
     const pusch::Geometry &g = h->geo;
 
     cudaError_t e;
-    std::vector<float2> tw(g.n_fft);
-    for (int q = 0; q < g.n_fft; ++q) {
-        const double ang = -2.0 * 3.14159265358979323846 * (double)q / (double)g.n_fft;
-        tw[q] = make_float2((float)cos(ang), (float)sin(ang));
-    }
-    if ((e = cudaMalloc(&h->twiddle, g.n_fft * sizeof(float2))) != cudaSuccess) goto cuda_error;
-    if ((e = cudaMemcpy(h->twiddle, tw.data(), g.n_fft * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess)
+    const std::vector<float2> tw = pusch::fft_twiddle_table(g.n_fft);
+    if ((e = cudaMalloc(&h->twiddle, tw.size() * sizeof(float2))) != cudaSuccess) goto cuda_error;
+    if ((e = cudaMemcpy(h->twiddle, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess)
         goto cuda_error;
     if ((e = cudaMalloc((void **)&h->kernel_err, 16)) != cudaSuccess) goto cuda_error;
     if ((e = cudaMemset(h->kernel_err, 0, 16)) != cudaSuccess) goto cuda_error;

@@ -582,7 +582,7 @@ pusch_status pusch_batch_create(pusch_batch **out, const pusch_cell_cfg *cells, 
         b->w_off.push_back(w);
         b->beam_off.push_back(bm);
         b->f_off.push_back(f);
-        t += (long long)g.n_sym * g.n_rx * g.n_fft;
+        t += pusch::time_elems_per_slot(g);
         w += (long long)g.n_rx * g.n_beams;
         bm += (long long)g.n_sym * g.n_sc * g.n_beams;
         f += up256(pusch::freq_bytes_of(g, 1));
@@ -722,11 +722,7 @@ pusch_status pusch_batch_create(pusch_batch **out, const pusch_cell_cfg *cells, 
     for (int c = 0; c < n_cells; ++c) {
         const int N = b->geo[c].n_fft;
         if (b->twiddle.count(N)) continue;
-        std::vector<float2> tw(N);
-        for (int q = 0; q < N; ++q) {
-            const double ang = -2.0 * 3.14159265358979323846 * (double)q / (double)N;
-            tw[q] = make_float2((float)cos(ang), (float)sin(ang));
-        }
+        const std::vector<float2> tw = pusch::fft_twiddle_table(N);
         float2 *d = nullptr;
         if ((e = upload(&d, tw)) != cudaSuccess) goto cuda_error;
         b->twiddle[N] = d;

@@ -235,12 +235,36 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     return true;
 }
 
-// One bulk (TMA, non-tensor) copy global -> shared completing on an mbarrier: 16-byte aligned, size % 16 == 0.
-__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+// Bulk (TMA, non-tensor) copies global -> shared completing on an mbarrier: 16-byte aligned, size % 16 == 0.
+// bulk_expect announces the bytes of all copies of one phase, bulk_copy issues one of them.
+__device__ __forceinline__ void bulk_expect(uint32_t bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
                  "l"(src), "r"(bytes), "r"(bar)
                  : "memory");
+}
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    bulk_expect(bar, bytes);
+    bulk_copy(dst, src, bytes, bar);
+}
+
+// Where the input rows are. cp == 0: row r (= (slot * n_sym + sym) * n_rx + rx) at r * N. cp == 1: one stream
+// of slot_len samples per (slot, antenna) with NR normal cyclic prefixes; the useful part of symbol s starts at
+// s * (N + cp1) + cp0. shift == 1: sample n of the useful part is multiplied by exp(-2 pi i n / (4 N)) (table
+// entries N + n) to undo the 7.5 kHz shift.
+struct FftIn {
+    int cp, cp0, cp1, shift, n_sym, n_rx;
+    long long slot_len;
+};
+__device__ __forceinline__ long long fft_row_offset(const FftIn &fi, int N, long long row) {
+    if (!fi.cp) return row * N;
+    const long long sr = row / fi.n_rx;
+    const int rx = (int)(row - sr * fi.n_rx);
+    const long long slot = sr / fi.n_sym;
+    const int sym = (int)(sr - slot * fi.n_sym);
+    return (slot * fi.n_rx + rx) * fi.slot_len + (long long)sym * (N + fi.cp1) + fi.cp0;
 }
 
 constexpr int kFftThreads = 256;
@@ -292,7 +316,8 @@ __device__ __forceinline__ int e4m3_block_exp(float amax) {
 template <int N, typename TIn, int OUT>
 __global__ void __launch_bounds__(kFftThreads, 3)
 fft_kernel(const TIn *__restrict__ in, void *__restrict__ out, const float2 *__restrict__ tw, long long rows,
-           int n_sc, int pitch, float *__restrict__ scales, int n_rx, int n_blk, uint32_t *__restrict__ err) {
+           int n_sc, int pitch, float *__restrict__ scales, int n_rx, int n_blk, uint32_t *__restrict__ err,
+           FftIn fi) {
     constexpr int E = Plan<N>::E;
     constexpr int T = N / E;
     constexpr int F = ffts_per_cta<N>();
@@ -315,7 +340,14 @@ fft_kernel(const TIn *__restrict__ in, void *__restrict__ out, const float2 *__r
         const long long r0 = blk * F;
         const long long nr = rows - r0 < F ? rows - r0 : F;
         const int s = (int)(it % STAGES);
-        bulk_load(smem_u32(ring) + s * kSpan, in + r0 * N, (uint32_t)(nr * N * sizeof(TIn)), bar0 + 8 * s);
+        if (!fi.cp) {  // the block's rows are one contiguous span
+            bulk_load(smem_u32(ring) + s * kSpan, in + r0 * N, (uint32_t)(nr * N * sizeof(TIn)), bar0 + 8 * s);
+        } else {       // one copy per row, out of the antennas' streams
+            bulk_expect(bar0 + 8 * s, (uint32_t)(nr * N * sizeof(TIn)));
+            for (int f = 0; f < (int)nr; ++f)
+                bulk_copy(smem_u32(ring) + s * kSpan + (uint32_t)(f * N * sizeof(TIn)), in + fft_row_offset(fi, N, r0 + f),
+                          (uint32_t)(N * sizeof(TIn)), bar0 + 8 * s);
+        }
     };
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) mbar_init(bar0 + 8 * s, 1);
@@ -347,6 +379,10 @@ fft_kernel(const TIn *__restrict__ in, void *__restrict__ out, const float2 *__r
         float2 v[E];
 #pragma unroll
         for (int e = 0; e < E; ++e) v[e] = to_f2(src[t + T * e]);
+        if (fi.shift) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) v[e] = cmul(v[e], __ldg(&tw[N + t + T * e]));
+        }
         fft_full<N>(v, sm, tw, t);
 
         if constexpr (OUT == kOutC64) {
@@ -503,7 +539,7 @@ fft_kernel(const TIn *__restrict__ in, void *__restrict__ out, const float2 *__r
 
 template <int N, typename TIn, int OUT>
 cudaError_t launch_n(long long rows, const void *in, void *out, const float2 *tw, int n_sc, int pitch, float *scales,
-                     int n_rx, int n_blk, uint32_t *err, cudaStream_t st) {
+                     int n_rx, int n_blk, uint32_t *err, const FftIn &fi, cudaStream_t st) {
     constexpr int F = ffts_per_cta<N>();
     constexpr size_t smem = fft_smem_bytes<N, TIn>();
     static_assert(smem <= 227 * 1024, "FFT shared memory");
@@ -519,7 +555,7 @@ cudaError_t launch_n(long long rows, const void *in, void *out, const float2 *tw
     long long grid = (long long)sms * per_sm;
     if (grid > blocks) grid = blocks;
     k<<<(unsigned)grid, kFftThreads, smem, st>>>(static_cast<const TIn *>(in), out, tw, rows, n_sc, pitch, scales,
-                                                  n_rx, n_blk, err);
+                                                  n_rx, n_blk, err, fi);
     return cudaGetLastError();
 }
 
@@ -528,14 +564,22 @@ template <typename TIn, int OUT>
 cudaError_t launch_out(const Geometry &g, long long rows, const void *in, void *out, const float2 *tw, float *scales,
                        uint32_t *err, cudaStream_t st) {
     const int n_blk = (g.n_sc + 127) / 128;
+    FftIn fi;
+    fi.cp = g.cp;
+    fi.cp0 = g.cp0;
+    fi.cp1 = g.cp1;
+    fi.shift = g.shift;
+    fi.n_sym = g.n_sym;
+    fi.n_rx = g.n_rx;
+    fi.slot_len = g.slot_len;
     switch (g.n_fft) {
-        case 4096: return launch_n<4096, TIn, OUT>(rows, in, out, tw, g.n_sc, g.sc_pitch, scales, g.n_rx, n_blk, err, st);
-        case 2048: return launch_n<2048, TIn, OUT>(rows, in, out, tw, g.n_sc, g.sc_pitch, scales, g.n_rx, n_blk, err, st);
-        case 1024: return launch_n<1024, TIn, OUT>(rows, in, out, tw, g.n_sc, g.sc_pitch, scales, g.n_rx, n_blk, err, st);
-        case 512: return launch_n<512, TIn, OUT>(rows, in, out, tw, g.n_sc, g.sc_pitch, scales, g.n_rx, n_blk, err, st);
-        case 256: return launch_n<256, TIn, OUT>(rows, in, out, tw, g.n_sc, g.sc_pitch, scales, g.n_rx, n_blk, err, st);
-        case 128: return launch_n<128, TIn, OUT>(rows, in, out, tw, g.n_sc, g.sc_pitch, scales, g.n_rx, n_blk, err, st);
-        case 64: return launch_n<64, TIn, OUT>(rows, in, out, tw, g.n_sc, g.sc_pitch, scales, g.n_rx, n_blk, err, st);
+        case 4096: return launch_n<4096, TIn, OUT>(rows, in, out, tw, g.n_sc, g.sc_pitch, scales, g.n_rx, n_blk, err, fi, st);
+        case 2048: return launch_n<2048, TIn, OUT>(rows, in, out, tw, g.n_sc, g.sc_pitch, scales, g.n_rx, n_blk, err, fi, st);
+        case 1024: return launch_n<1024, TIn, OUT>(rows, in, out, tw, g.n_sc, g.sc_pitch, scales, g.n_rx, n_blk, err, fi, st);
+        case 512: return launch_n<512, TIn, OUT>(rows, in, out, tw, g.n_sc, g.sc_pitch, scales, g.n_rx, n_blk, err, fi, st);
+        case 256: return launch_n<256, TIn, OUT>(rows, in, out, tw, g.n_sc, g.sc_pitch, scales, g.n_rx, n_blk, err, fi, st);
+        case 128: return launch_n<128, TIn, OUT>(rows, in, out, tw, g.n_sc, g.sc_pitch, scales, g.n_rx, n_blk, err, fi, st);
+        case 64: return launch_n<64, TIn, OUT>(rows, in, out, tw, g.n_sc, g.sc_pitch, scales, g.n_rx, n_blk, err, fi, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -3,6 +3,7 @@
 
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 #include <cuda_bf16.h>
@@ -52,7 +53,28 @@ struct Geometry {
     int chol_every;               // 0, or the data-symbol group size (pusch_cell_cfg.chol_every)
     int n_groups;                 // detection groups (1 when chol_every == 0)
     float group_t[16];            // per group: mean (s - dmrs0) / (dmrs1 - dmrs0) of its data symbols
+    int cp;                       // 1: time input is one stream per antenna with NR normal cyclic prefixes
+    int cp0, cp1;                 // prefix samples of symbol 0 and of the other symbols (cp == 1)
+    long long slot_len;           // samples of one antenna's slot (cp == 1)
+    int shift;                    // 1: undo the 7.5 kHz shift before the FFT
 };
+
+// Complex time samples of one slot's input.
+inline long long time_elems_per_slot(const Geometry &g) {
+    return g.cp ? (long long)g.n_rx * g.slot_len : (long long)g.n_sym * g.n_rx * g.n_fft;
+}
+
+// FFT twiddle table entries: exp(-2 pi i q / n_fft) for q < n_fft, then exp(-2 pi i q / (4 n_fft)) for
+// q < n_fft (the derotation of the 7.5 kHz shift).
+inline int fft_twiddle_count(int n_fft) { return 2 * n_fft; }
+inline std::vector<float2> fft_twiddle_table(int n_fft) {
+    std::vector<float2> tw(2 * n_fft);
+    for (int q = 0; q < 2 * n_fft; ++q) {
+        const double ang = -2.0 * 3.14159265358979323846 * (double)(q % n_fft) / (double)(q < n_fft ? n_fft : 4 * n_fft);
+        tw[q] = make_float2((float)cos(ang), (float)sin(ang));
+    }
+    return tw;
+}
 
 Geometry make_geometry(const pusch_cell_cfg &c);
 
@@ -166,7 +188,7 @@ struct pusch_handle {
     pusch::Geometry geo;
     int max_slots = 0;
     int device = 0;
-    float2 *twiddle = nullptr;      // exp(-2 pi i q / n_fft), q < n_fft
+    float2 *twiddle = nullptr;      // FFT twiddle table (fft_twiddle_table)
     uint32_t *kernel_err = nullptr;   // bounded-wait expiry flags of the tensor-core kernel
     void *freq = nullptr;           // workspace: FFT output
     float2 *beam = nullptr;         // workspace: beamformed grid

@@ -32,12 +32,13 @@ pusch_status na_fail(pusch_status st, const char *msg, cudaError_t e = cudaSucce
     return st;
 }
 
-// exp(-2 pi i q / n), computed in double precision and rounded once to float.
+// The FFT twiddle table (pusch::fft_twiddle_table): exp(-2 pi i q / n), then exp(-2 pi i q / (4 n)), q < n,
+// computed in double precision and rounded once to float.
 __global__ void noalloc_twiddle_kernel(float2 *tw, int n) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q < n) {
+    if (q < 2 * n) {
         double s, c;
-        sincospi(-2.0 * (double)q / (double)n, &s, &c);
+        sincospi(-2.0 * (double)(q % n) / (double)(q < n ? n : 4 * n), &s, &c);
         tw[q] = make_float2((float)c, (float)s);
     }
 }
@@ -84,7 +85,7 @@ extern "C" pusch_status pusch_slot_noalloc(const pusch_cell_cfg *cfg, int n_slot
     if (cfg->chol_every != 0)
         return na_fail(PUSCH_ERR_UNSUPPORTED, "pusch_slot_noalloc: chol_every > 0 needs a handle (pusch_slot)");
     const pusch::Geometry g = pusch::make_geometry(*cfg);
-    const size_t tw_b = up256((size_t)g.n_fft * sizeof(float2));
+    const size_t tw_b = up256((size_t)pusch::fft_twiddle_count(g.n_fft) * sizeof(float2));
     const size_t words_b = 256;  // status sink (16 B) + tensor-core timeout word (16 B)
     const size_t freq_b = up256(pusch::freq_bytes_of(g, n_slots));
     const size_t beam_b = up256((size_t)n_slots * g.n_sym * g.n_sc * g.n_beams * sizeof(float2));
@@ -116,7 +117,7 @@ extern "C" pusch_status pusch_slot_noalloc(const pusch_cell_cfg *cfg, int n_slot
     uint32_t *stat = status ? status : sink;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
 
-    noalloc_twiddle_kernel<<<(g.n_fft + 255) / 256, 256, 0, s>>>(tw, g.n_fft);
+    noalloc_twiddle_kernel<<<(2 * g.n_fft + 255) / 256, 256, 0, s>>>(tw, g.n_fft);
     noalloc_status_kernel<<<1, 1, 0, s>>>(stat, tc_err);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return na_fail(PUSCH_ERR_CUDA, "pusch_slot_noalloc set-up launch", e);

@@ -15,7 +15,8 @@ def cfg_for(cell, form: int = B.PUSCH_FORM_FP32, noise_var: float | None = None,
     nv = float(10.0 ** (-cell.snr_db / 10.0)) if noise_var is None else float(noise_var)
     return B.make_cfg(n_rx=cell.n_rx, n_fft=cell.n_fft, n_sc=cell.n_sc, n_beams=cell.n_beams,
                       n_layers=cell.n_layers, comb=cell.comb, ports=ports, qam_bits=cell.qam_bits,
-                      in_fp16=cell.in_fp16, form=form, noise_var=nv, loading=loading, chol_every=chol_every)
+                      in_fp16=cell.in_fp16, form=form, noise_var=nv, loading=loading, chol_every=chol_every,
+                      cp=getattr(cell, "cp", False), shift_7p5khz=getattr(cell, "shift_7p5khz", False))
 
 
 def time_tensor(slots, device="cuda", pin=False) -> torch.Tensor:

@@ -55,6 +55,8 @@ class CellConfig:
     tap_spacing_s: float = 60e-9
     doppler_hz: float = 0.0  # > 0: each tap fades over the slot (sum of 16 sinusoids, Clarke/Jakes spectrum)
     seed: int = 0
+    cp: bool = False         # time input as one stream per antenna with NR normal cyclic prefixes
+    shift_7p5khz: bool = False  # spectrum shifted up by 7.5 kHz (a quarter subcarrier) before transmission
 
     @property
     def comb(self) -> int:
@@ -169,7 +171,8 @@ def _channel_per_symbol(cfg: CellConfig, rng: np.random.Generator):
 @dataclass
 class Slot:
     cfg: CellConfig
-    time_in: np.ndarray      # [S, N_R, N_F] complex64, or [S, N_R, N_F, 2] float16 when cfg.in_fp16
+    time_in: np.ndarray      # [S, N_R, N_F] complex64, or [S, N_R, N_F, 2] float16 when cfg.in_fp16; with cfg.cp
+                             # one stream per antenna, [N_R, slot_len] (or [N_R, slot_len, 2])
     W: np.ndarray            # [N_R, N_B] complex64
     pilots: np.ndarray       # [N_L, 2, N_SC] complex64 (zero off the layer's comb)
     ports: np.ndarray        # [N_L] int32 comb offsets
@@ -233,6 +236,8 @@ def make_slot(cfg: CellConfig, slot_index: int = 0, seed: int | None = None) -> 
     spec = np.zeros((N_SYM, R, N), dtype=np.complex128)
     spec[:, :, active_bins(n_sc, N)] = X
     time = np.fft.ifft(spec, axis=-1)
+    if cfg.cp or cfg.shift_7p5khz:
+        time = _waveform(time, cfg.cp, cfg.shift_7p5khz)
     if cfg.in_fp16:
         time_in = np.stack([time.real, time.imag], axis=-1).astype(np.float16)
     else:
@@ -241,6 +246,28 @@ def make_slot(cfg: CellConfig, slot_index: int = 0, seed: int | None = None) -> 
     H_beam = np.matmul(W.astype(np.complex128).conj().T, Hant).transpose(0, 2, 1)   # [N_SC, L, B]
     return Slot(cfg=cfg, time_in=time_in, W=W, pilots=pilots, ports=ports, noise_var=noise_var,
                 H_beam=H_beam, x=x, bits=pack_bits(bits))
+
+
+def cp_lengths(n_fft: int) -> tuple[int, int]:
+    """NR normal cyclic prefix at 30 kHz (TS 38.211 5.3.1): samples of symbol 0 and of the other symbols."""
+    return 352 * n_fft // 4096, 288 * n_fft // 4096
+
+
+def _waveform(time: np.ndarray, cp: bool, shift: bool) -> np.ndarray:
+    """[S, R, N] periodic symbols -> the transmitted samples: with cp, [R, slot_len] streams where each symbol is
+    preceded by its cyclic prefix; with shift, every sample multiplied by exp(2 pi i n' / (4 N)), n' counted from
+    the start of its symbol's useful part (negative inside the prefix), as the 7.5 kHz shift of TS 38.211 5.4."""
+    S, R, N = time.shape
+    cp0, cp1 = cp_lengths(N) if cp else (0, 0)
+    parts = []
+    for s in range(S):
+        c = cp0 if s == 0 else cp1
+        n = np.arange(-c, N)
+        x = time[s][:, n % N]
+        if shift:
+            x = x * np.exp(2j * np.pi * n / (4 * N))
+        parts.append(x)
+    return np.ascontiguousarray(np.concatenate(parts, axis=1) if cp else np.stack(parts))
 
 
 def make_slots(cfg: CellConfig, n: int, first: int = 0, seed: int | None = None) -> list[Slot]:

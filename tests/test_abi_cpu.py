@@ -68,6 +68,16 @@ def test_invalid_configs_are_rejected_on_the_host(B, bad, code):
     assert h.value is None
 
 
+def test_prefix_needs_512_points(B):
+    out = ctypes.c_size_t()
+    cfg = _good(n_fft=256, n_sc=200, cp=True)
+    assert B.lib().pusch_workspace_size(ctypes.byref(cfg), 1, ctypes.byref(out)) == B.PUSCH_ERR_UNSUPPORTED
+    cfg = _good(cp=True, shift_7p5khz=True)
+    assert B.lib().pusch_workspace_size(ctypes.byref(cfg), 1, ctypes.byref(out)) == 0
+    cfg.cp = 2
+    assert B.lib().pusch_workspace_size(ctypes.byref(cfg), 1, ctypes.byref(out)) == B.PUSCH_ERR_ARG
+
+
 def test_noise_estimate_mode_is_accepted(B):
     cfg = _good(noise_var=B.PUSCH_NOISE_ESTIMATE)
     out = ctypes.c_size_t()
@@ -98,3 +108,12 @@ def test_null_handle_and_bad_batch_rejected(B):
     assert L.pusch_set_pipeline(None, 2) == B.PUSCH_ERR_ARG
     with pytest.raises(B.PuschError):
         B.pusch_ofdm_fft(None, 1, 1, 1, stream=0)
+
+
+def test_binding_rejects_non_contiguous_buffers(B):
+    torch = pytest.importorskip("torch")
+    t = torch.zeros((4, 6), dtype=torch.complex64).t()
+    with pytest.raises(ValueError):
+        B._ptr(t)
+    c = t.contiguous()
+    assert B._ptr(c) == c.data_ptr()
