@@ -45,6 +45,10 @@ def lib():
             "orc_fft": (I, [P, I, P]),
             "orc_ofdm_demod": (I, [P, I, I, I, I, P, I, P]),
             "orc_cp_len": (I, [I, I]),
+            "orc_gold": (I, [ctypes.c_uint32, I, P]),
+            "orc_dmrs_cinit": (ctypes.c_uint32, [I, I, I, I]),
+            "orc_dmrs_type1_pilots": (I, [I, I, I, P, I, P, I, P]),
+            "orc_chest_ls_type1": (I, [P, I, I, I, P, I, P, P, P]),
             "orc_slot_len": (ctypes.c_longlong, [I, I]),
             "orc_ofdm_demod_cp": (I, [P, I, I, I, I, I, P]),
             "orc_beamform": (None, [P, P, I, I, I, I, P]),
@@ -103,6 +107,39 @@ def fft(x) -> np.ndarray:
     if lib().orc_fft(_p(x), x.size, _p(X)) != 0:
         raise ValueError("orc_fft needs a power-of-two length")
     return X
+
+
+def gold(c_init: int, n: int) -> np.ndarray:
+    """c(0..n) of the TS 38.211 5.2.1 sequence for c_init, as uint8 bits."""
+    c = np.zeros(n, dtype=np.uint8)
+    if lib().orc_gold(int(c_init), n, _p(c)) != 0:
+        raise ValueError("orc_gold failed")
+    return c
+
+
+def dmrs_cinit(n_id: int, n_scid: int, slot: int, sym: int) -> int:
+    return int(lib().orc_dmrs_cinit(n_id, n_scid, slot, sym))
+
+
+def dmrs_type1_pilots(n_id: int, n_scid: int, slot: int, ports, n_sc: int, dmrs=DMRS_SYMBOLS) -> np.ndarray:
+    """[L, 2, n_sc] type-1 DMRS values of the layers' ports (0..3) on the two DMRS symbols."""
+    ports = _i32(ports)
+    out = np.zeros((ports.size, 2, n_sc), dtype=np.complex128)
+    if lib().orc_dmrs_type1_pilots(n_id, n_scid, slot, _p(_i32(dmrs)), ports.size, _p(ports), n_sc, _p(out)) != 0:
+        raise ValueError("orc_dmrs_type1_pilots failed")
+    return out
+
+
+def chest_ls_type1(beam, pilots, ports, dmrs=DMRS_SYMBOLS) -> np.ndarray:
+    """beam [S, N_SC, B], pilots [L, 2, N_SC] (type 1) -> H [N_SC, L, B]."""
+    beam, pilots = _c128(beam), _c128(pilots)
+    S, n_sc, B = beam.shape
+    L = pilots.shape[0]
+    H = np.zeros((n_sc, L, B), dtype=np.complex128)
+    rc = lib().orc_chest_ls_type1(_p(beam), S, n_sc, B, _p(_i32(dmrs)), L, _p(_i32(ports)), _p(pilots), _p(H))
+    if rc != 0:
+        raise ValueError(f"orc_chest_ls_type1 failed ({rc})")
+    return H
 
 
 def cp_len(n_fft: int, sym: int) -> int:

@@ -10,6 +10,9 @@
  *   orc_dft         Section II "OFDM demodulation ... via a FFT": the DFT definition itself.
  *   orc_fft         textbook recursive radix-2 decimation-in-time FFT (pinned against orc_dft).
  *   orc_ofdm_demod  Section II: one FFT per antenna and OFDM symbol, keep the N_SC active bins.
+ *   orc_gold, orc_dmrs_cinit, orc_dmrs_type1_pilots, orc_chest_ls_type1  3GPP type-1 DMRS (TS 38.211 5.2.1,
+ *                   6.4.1.1): Gold sequence, pilot mapping with frequency OCC, and the LS estimate with OCC
+ *                   despreading over each CDM pair (the paper's element-wise division, then the pair mean).
  *   orc_cp_len, orc_slot_len, orc_ofdm_demod_cp  the same on a slot with NR normal cyclic prefixes and the
  *                   optional 7.5 kHz shift (TS 38.211 5.3.1, 5.4; not in the paper, which starts after them).
  *   orc_beamform    Section II: "a MMM with known coefficients", y = W^H x per subcarrier and symbol.
@@ -169,6 +172,124 @@ int orc_ofdm_demod_cp(const cplx *stream, int n_sym, int n_rx, int n_fft, int n_
     free(x);
     free(X);
     return rc;
+}
+
+/* ------------------------------------------------- 3GPP DMRS (type 1) ---- */
+
+/* Pseudo-random sequence of TS 38.211 5.2.1: c(n) = x1(n + 1600) + x2(n + 1600) mod 2 with
+ * x1(n + 31) = x1(n + 3) + x1(n), x2(n + 31) = x2(n + 3) + x2(n + 2) + x2(n + 1) + x2(n) (mod 2),
+ * x1(0) = 1, x1(1..30) = 0, and x2(i) = bit i of c_init. Bit by bit, as defined. */
+int orc_gold(uint32_t c_init, int len, uint8_t *c)
+{
+    const int total = 1600 + len + 31;
+    uint8_t *x1 = calloc((size_t)total, 1), *x2 = calloc((size_t)total, 1);
+    if (!x1 || !x2) {
+        free(x1);
+        free(x2);
+        return -2;
+    }
+    x1[0] = 1;
+    for (int i = 0; i < 31; ++i) x2[i] = (uint8_t)((c_init >> i) & 1u);
+    for (int n = 0; n + 31 < total; ++n) {
+        x1[n + 31] = x1[n + 3] ^ x1[n];
+        x2[n + 31] = x2[n + 3] ^ x2[n + 2] ^ x2[n + 1] ^ x2[n];
+    }
+    for (int n = 0; n < len; ++n) c[n] = x1[n + 1600] ^ x2[n + 1600];
+    free(x1);
+    free(x2);
+    return 0;
+}
+
+/* c_init of the PUSCH DMRS with transform precoding disabled (TS 38.211 6.4.1.1.1.1):
+ * (2^17 (14 slot + sym + 1)(2 N_ID + 1) + 2 N_ID + n_SCID) mod 2^31, slot = slot number in the frame. */
+uint32_t orc_dmrs_cinit(int n_id, int n_scid, int slot, int sym)
+{
+    const unsigned long long v = (1ull << 17) * (14ull * (unsigned)slot + (unsigned)sym + 1ull) *
+                                     (2ull * (unsigned)n_id + 1ull) + 2ull * (unsigned)n_id + (unsigned)n_scid;
+    return (uint32_t)(v % (1ull << 31));
+}
+
+/* Type-1 single-symbol DMRS (TS 38.211 6.4.1.1.3): antenna port 1000 + p, p in {0, 1, 2, 3}, uses CDM group
+ * Delta = p / 2 on subcarriers k = 4n + 2k' + Delta (k' in {0, 1}) with the value w_f(k') r(2n + k'),
+ * w_f = (+1, +1) for p = 0, 2 and (+1, -1) for p = 1, 3, and r(m) = ((1 - 2c(2m)) + i (1 - 2c(2m + 1))) / sqrt 2
+ * from the c_init of its OFDM symbol; zero on the other subcarriers. Subcarrier k counts from the first
+ * subcarrier of the band. pilots [n_layers][2][n_sc] for the two DMRS symbols dmrs_sym[0..1]. */
+int orc_dmrs_type1_pilots(int n_id, int n_scid, int slot, const int *dmrs_sym, int n_layers, const int *ports,
+                          int n_sc, cplx *pilots)
+{
+    uint8_t *c = malloc((size_t)n_sc + 2);
+    if (!c) return -2;
+    const double a = 1.0 / sqrt(2.0);
+    for (int j = 0; j < 2; ++j) {
+        int rc = orc_gold(orc_dmrs_cinit(n_id, n_scid, slot, dmrs_sym[j]), n_sc + 2, c);
+        if (rc) {
+            free(c);
+            return rc;
+        }
+        for (int l = 0; l < n_layers; ++l) {
+            const int p = ports[l], delta = p / 2;
+            cplx *out = pilots + ((size_t)l * 2 + j) * n_sc;
+            for (int k = 0; k < n_sc; ++k) out[k] = 0;
+            for (int k = delta; k < n_sc; k += 2) {
+                const int kp = ((k - delta) / 2) % 2, m = (k - delta) / 2;  /* k = 4n + 2k' + Delta, m = 2n + k' */
+                const double w = (p % 2 == 1 && kp == 1) ? -1.0 : 1.0;
+                out[k] = w * a * ((1.0 - 2.0 * c[2 * m]) + I * (1.0 - 2.0 * c[2 * m + 1]));
+            }
+        }
+    }
+    free(c);
+    return 0;
+}
+
+/* LS estimate with type-1 DMRS: for layer l (port p, CDM group Delta = p / 2) and every pair of its group's
+ * subcarriers k0 = 4n + Delta, k1 = k0 + 2 inside the band, the despread value 1/2 (y(k0) / p(k0) + y(k1) / p(k1))
+ * of each DMRS symbol (the OCC w_f is inside the pilot values, so the other port of the group cancels where the
+ * channel is equal on k0 and k1), averaged over the two DMRS symbols and placed at the pair centre k0 + 1; then
+ * linear interpolation between the centres and the value held outside the first and last. H [n_sc][n_layers][n_beams]. */
+int orc_chest_ls_type1(const cplx *beam, int n_sym, int n_sc, int n_beams, const int *dmrs_sym, int n_layers,
+                       const int *ports, const cplx *pilots, cplx *H)
+{
+    (void)n_sym;
+    for (int l = 0; l < n_layers; ++l) {
+        const int delta = ports[l] / 2;
+        const int n_pairs = (n_sc - delta - 2) >= 0 ? (n_sc - delta - 2) / 4 + 1 : 0;
+        if (n_pairs < 1) return -(l + 1);
+        cplx *ls = malloc(sizeof(cplx) * (size_t)n_pairs * n_beams);
+        if (!ls) return -2;
+        for (int n = 0; n < n_pairs; ++n) {
+            const int k0 = 4 * n + delta, k1 = k0 + 2;
+            for (int b = 0; b < n_beams; ++b) {
+                cplx v = 0;
+                for (int j = 0; j < 2; ++j) {
+                    const cplx *y = beam + (size_t)dmrs_sym[j] * n_sc * n_beams;
+                    const cplx *p = pilots + ((size_t)l * 2 + j) * n_sc;
+                    v += 0.5 * (y[(size_t)k0 * n_beams + b] / p[k0] + y[(size_t)k1 * n_beams + b] / p[k1]);
+                }
+                ls[(size_t)n * n_beams + b] = 0.5 * v;
+            }
+        }
+        const int first = delta + 1, last = 4 * (n_pairs - 1) + delta + 1;
+        for (int a = 0; a < n_sc; ++a) {
+            int lo, hi;
+            if (a <= first) {
+                lo = hi = 0;
+            } else if (a >= last) {
+                lo = hi = n_pairs - 1;
+            } else {
+                lo = (a - first) / 4;
+                hi = lo + 1;
+            }
+            const int c_lo = first + 4 * lo;
+            for (int b = 0; b < n_beams; ++b) {
+                cplx h = ls[(size_t)lo * n_beams + b];
+                if (hi != lo)
+                    h += ((double)(a - c_lo) / 4.0) * (ls[(size_t)hi * n_beams + b] - ls[(size_t)lo * n_beams + b]);
+                H[((size_t)a * n_layers + l) * n_beams + b] = h;
+            }
+        }
+        free(ls);
+    }
+    return 0;
 }
 
 /* ---------------------------------------------------------- beamforming ---- */
