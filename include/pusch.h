@@ -99,6 +99,15 @@ typedef struct {
                           spacing) with the phase reference at the start of each useful part (TS 38.211
                           5.4): sample n of the useful part is multiplied by exp(-2 pi i n / (4 n_fft))
                           before the FFT. 0: no shift.                                               */
+    int dmrs_type;     /* 0: the comb pilot model above (layer l on subcarriers a % comb == port[l]).
+                          1: 3GPP type-1 single-symbol DMRS (TS 38.211 6.4.1.1.3): port[l] in {0..3}
+                          (antenna ports 1000..1003, distinct), n_layers <= 4, n_sc % 4 == 0; port p
+                          sends w_f(k') r(2n + k') on subcarriers 4n + 2k' + p / 2 (w_f = (+1, -1) for odd
+                          p), so two ports share each comb-2 CDM group. pilots holds those values
+                          (pusch_dmrs_type1_pilots). The LS estimate despreads each pair of a group,
+                          1/2 (y(k0) / p(k0) + y(k0 + 2) / p(k0 + 2)), placed at k0 + 1, then interpolates
+                          between the pair centres as above. comb is ignored. Not with
+                          PUSCH_NOISE_ESTIMATE, the ragged batch or the learned estimator.            */
 } pusch_cell_cfg;
 
 /* noise_var value that makes the chain estimate sigma^2 per slot (pusch_noise_estimate) instead of using a
@@ -209,6 +218,18 @@ pusch_status pusch_mmse_detect(pusch_handle *h, int n_slots, const void *H_hat, 
  */
 pusch_status pusch_slot(pusch_handle *h, int n_slots, const void *time_in, const void *W, const void *pilots,
                         void *x_hat, uint8_t *bits, uint32_t *status, void *stream);
+
+/*
+ * 3GPP type-1 DMRS values for dmrs_type = 1 (TS 38.211 5.2.1, 6.4.1.1; not in the paper, whose pilots are a
+ * block-type model): for slot i (slot number slot_numbers[i] within the frame, host array, 0..159) and DMRS
+ * symbol l = cfg->dmrs_sym[j], the Gold sequence c(n) of c_init = (2^17 (14 slot + l + 1)(2 n_id + 1) + 2 n_id
+ * + n_scid) mod 2^31 gives r(m) = ((1 - 2c(2m)) + i (1 - 2c(2m + 1))) / sqrt 2, and layer l's port p gets
+ * w_f(k') r(2n + k') on subcarriers k = 4n + 2k' + p / 2 (subcarrier 0 = the band's first), zero elsewhere.
+ * pilots: DEVICE [n_slots][n_layers][2][n_sc] c64, written on `stream`. n_id in [0, 65535], n_scid in {0, 1}.
+ * PUSCH_ERR_ARG for a cfg that is not dmrs_type 1 or arguments out of range.
+ */
+pusch_status pusch_dmrs_type1_pilots(const pusch_cell_cfg *cfg, int n_slots, const int *slot_numbers, int n_id,
+                                     int n_scid, void *pilots, void *stream);
 
 /*
  * Pipelining of pusch_slot and pusch_slot_host (a GPU scheduling choice; no counterpart in the paper).

@@ -49,6 +49,7 @@ def lib():
             "orc_dmrs_cinit": (ctypes.c_uint32, [I, I, I, I]),
             "orc_dmrs_type1_pilots": (I, [I, I, I, P, I, P, I, P]),
             "orc_chest_ls_type1": (I, [P, I, I, I, P, I, P, P, P]),
+            "orc_chest_ls_type1_sym": (I, [P, I, I, I, P, I, P, P, I, P]),
             "orc_slot_len": (ctypes.c_longlong, [I, I]),
             "orc_ofdm_demod_cp": (I, [P, I, I, I, I, I, P]),
             "orc_beamform": (None, [P, P, I, I, I, I, P]),
@@ -139,6 +140,19 @@ def chest_ls_type1(beam, pilots, ports, dmrs=DMRS_SYMBOLS) -> np.ndarray:
     rc = lib().orc_chest_ls_type1(_p(beam), S, n_sc, B, _p(_i32(dmrs)), L, _p(_i32(ports)), _p(pilots), _p(H))
     if rc != 0:
         raise ValueError(f"orc_chest_ls_type1 failed ({rc})")
+    return H
+
+
+def chest_ls_type1_sym(beam, pilots, ports, j: int, dmrs=DMRS_SYMBOLS) -> np.ndarray:
+    """The type-1 estimate of DMRS symbol j alone: [N_SC, L, B]."""
+    beam, pilots = _c128(beam), _c128(pilots)
+    S, n_sc, B = beam.shape
+    L = pilots.shape[0]
+    H = np.zeros((n_sc, L, B), dtype=np.complex128)
+    rc = lib().orc_chest_ls_type1_sym(_p(beam), S, n_sc, B, _p(_i32(dmrs)), L, _p(_i32(ports)), _p(pilots), int(j),
+                                      _p(H))
+    if rc != 0:
+        raise ValueError(f"orc_chest_ls_type1_sym failed ({rc})")
     return H
 
 

@@ -246,10 +246,30 @@ int orc_dmrs_type1_pilots(int n_id, int n_scid, int slot, const int *dmrs_sym, i
  * of each DMRS symbol (the OCC w_f is inside the pilot values, so the other port of the group cancels where the
  * channel is equal on k0 and k1), averaged over the two DMRS symbols and placed at the pair centre k0 + 1; then
  * linear interpolation between the centres and the value held outside the first and last. H [n_sc][n_layers][n_beams]. */
+static int chest_ls_type1_weighted(const cplx *beam, int n_sc, int n_beams, const int *dmrs_sym, int n_layers,
+                                   const int *ports, const cplx *pilots, const double *wj, cplx *H);
+
 int orc_chest_ls_type1(const cplx *beam, int n_sym, int n_sc, int n_beams, const int *dmrs_sym, int n_layers,
                        const int *ports, const cplx *pilots, cplx *H)
 {
     (void)n_sym;
+    const double w[2] = {0.5, 0.5};
+    return chest_ls_type1_weighted(beam, n_sc, n_beams, dmrs_sym, n_layers, ports, pilots, w, H);
+}
+
+/* The same estimate from DMRS symbol j alone (the despread pairs of that symbol, interpolated). */
+int orc_chest_ls_type1_sym(const cplx *beam, int n_sym, int n_sc, int n_beams, const int *dmrs_sym, int n_layers,
+                           const int *ports, const cplx *pilots, int j, cplx *H)
+{
+    (void)n_sym;
+    const double w[2] = {j == 0 ? 1.0 : 0.0, j == 0 ? 0.0 : 1.0};
+    return chest_ls_type1_weighted(beam, n_sc, n_beams, dmrs_sym, n_layers, ports, pilots, w, H);
+}
+
+/* Despread pairs weighted by wj over the DMRS symbols, then interpolation between the pair centres. */
+static int chest_ls_type1_weighted(const cplx *beam, int n_sc, int n_beams, const int *dmrs_sym, int n_layers,
+                                   const int *ports, const cplx *pilots, const double *wj, cplx *H)
+{
     for (int l = 0; l < n_layers; ++l) {
         const int delta = ports[l] / 2;
         const int n_pairs = (n_sc - delta - 2) >= 0 ? (n_sc - delta - 2) / 4 + 1 : 0;
@@ -263,9 +283,9 @@ int orc_chest_ls_type1(const cplx *beam, int n_sym, int n_sc, int n_beams, const
                 for (int j = 0; j < 2; ++j) {
                     const cplx *y = beam + (size_t)dmrs_sym[j] * n_sc * n_beams;
                     const cplx *p = pilots + ((size_t)l * 2 + j) * n_sc;
-                    v += 0.5 * (y[(size_t)k0 * n_beams + b] / p[k0] + y[(size_t)k1 * n_beams + b] / p[k1]);
+                    v += wj[j] * 0.5 * (y[(size_t)k0 * n_beams + b] / p[k0] + y[(size_t)k1 * n_beams + b] / p[k1]);
                 }
-                ls[(size_t)n * n_beams + b] = 0.5 * v;
+                ls[(size_t)n * n_beams + b] = v;
             }
         }
         const int first = delta + 1, last = 4 * (n_pairs - 1) + delta + 1;

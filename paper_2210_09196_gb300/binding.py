@@ -37,7 +37,7 @@ EXPORTS = (
     "pusch_create", "pusch_destroy", "pusch_workspace_size", "pusch_sc_pitch", "pusch_freq_bytes", "pusch_ofdm_fft",
     "pusch_beamform",
     "pusch_chest_ls", "pusch_noise_estimate", "pusch_mmse_detect", "pusch_slot", "pusch_slot_host",
-    "pusch_set_pipeline", "pusch_last_error", "pusch_version",
+    "pusch_set_pipeline", "pusch_dmrs_type1_pilots", "pusch_last_error", "pusch_version",
     "pusch_slot_noalloc", "pusch_profile_start", "pusch_profile_read",
     "pusch_batch_create", "pusch_batch_destroy", "pusch_batch_sizes", "pusch_batch_run", "pusch_batch_autotune",
     "pusch_batch_tuning",
@@ -61,6 +61,7 @@ class pusch_cell_cfg(ctypes.Structure):
         ("chol_every", ctypes.c_int),
         ("cp", ctypes.c_int),
         ("shift_7p5khz", ctypes.c_int),
+        ("dmrs_type", ctypes.c_int),
     ]
 
 
@@ -71,7 +72,7 @@ class pusch_user_desc(ctypes.Structure):
 
 def make_cfg(*, n_rx, n_fft, n_sc, n_beams, n_layers, comb=None, ports=None, qam_bits=2, in_fp16=False,
              form=PUSCH_FORM_FP32, noise_var=0.0, loading=0.0, n_sym=14, dmrs_sym=(2, 11),
-             chol_every=0, cp=False, shift_7p5khz=False) -> pusch_cell_cfg:
+             chol_every=0, cp=False, shift_7p5khz=False, dmrs_type=0) -> pusch_cell_cfg:
     c = pusch_cell_cfg()
     c.n_rx, c.n_fft, c.n_sc, c.n_beams, c.n_layers = n_rx, n_fft, n_sc, n_beams, n_layers
     c.comb = n_layers if comb is None else comb
@@ -83,6 +84,7 @@ def make_cfg(*, n_rx, n_fft, n_sc, n_beams, n_layers, comb=None, ports=None, qam
     c.noise_var, c.loading = float(noise_var), float(loading)
     c.chol_every = int(chol_every)
     c.cp, c.shift_7p5khz = int(bool(cp)), int(bool(shift_7p5khz))
+    c.dmrs_type = int(dmrs_type)
     return c
 
 
@@ -112,6 +114,7 @@ def lib():
             "pusch_slot_noalloc": (I, [ctypes.POINTER(pusch_cell_cfg), I, P, P, P, P, P, P, P]),
             "pusch_profile_start": (I, [P, I]),
             "pusch_set_pipeline": (I, [P, I]),
+            "pusch_dmrs_type1_pilots": (I, [P, I, P, I, I, P, P]),
             "pusch_profile_read": (I, [P, ctypes.POINTER(ctypes.c_float), I, ctypes.POINTER(I)]),
             "pusch_batch_create": (I, [ctypes.POINTER(P), ctypes.POINTER(pusch_cell_cfg), I,
                                        ctypes.POINTER(pusch_user_desc), I]),
@@ -239,6 +242,12 @@ def pusch_slot_noalloc(cfg: pusch_cell_cfg, n_slots, time_in, W, pilots, x_hat, 
 
 
 SLOT_STAGES = ("fft", "beamform", "ls", "detect")
+
+
+def pusch_dmrs_type1_pilots(cfg, n_slots, slot_numbers, n_id, n_scid, pilots, stream=None) -> None:
+    sl = (ctypes.c_int * max(1, n_slots))(*[int(v) for v in slot_numbers])
+    _check(lib().pusch_dmrs_type1_pilots(ctypes.byref(cfg), n_slots, sl, n_id, n_scid, _ptr(pilots), _stream(stream)),
+           "pusch_dmrs_type1_pilots")
 
 
 def pusch_set_pipeline(h, n_chunks: int) -> None:

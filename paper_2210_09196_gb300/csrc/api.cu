@@ -44,10 +44,24 @@ pusch_status validate_cfg(const pusch_cell_cfg *c) {
         return fail(PUSCH_ERR_UNSUPPORTED, "n_beams=%d out of [1, 64]", c->n_beams);
     if (c->n_layers < 1 || c->n_layers > 32 || c->n_layers > c->n_beams)
         return fail(PUSCH_ERR_ARG, "n_layers=%d out of [1, min(32, n_beams)]", c->n_layers);
-    if (c->comb < 1 || c->comb > c->n_sc) return fail(PUSCH_ERR_ARG, "comb=%d out of [1, n_sc]", c->comb);
-    for (int l = 0; l < c->n_layers; ++l)
-        if (c->port[l] < 0 || c->port[l] >= c->comb)
-            return fail(PUSCH_ERR_ARG, "port[%d]=%d out of [0, comb)", l, c->port[l]);
+    if (c->dmrs_type == 0 && (c->comb < 1 || c->comb > c->n_sc))
+        return fail(PUSCH_ERR_ARG, "comb=%d out of [1, n_sc]", c->comb);
+    if (c->dmrs_type != 0 && c->dmrs_type != 1) return fail(PUSCH_ERR_ARG, "dmrs_type must be 0 or 1");
+    if (c->dmrs_type == 0) {
+        for (int l = 0; l < c->n_layers; ++l)
+            if (c->port[l] < 0 || c->port[l] >= c->comb)
+                return fail(PUSCH_ERR_ARG, "port[%d]=%d out of [0, comb)", l, c->port[l]);
+    } else {
+        if (c->n_layers > 4) return fail(PUSCH_ERR_ARG, "type-1 DMRS carries at most 4 ports (n_layers=%d)", c->n_layers);
+        if (c->n_sc % 4 != 0) return fail(PUSCH_ERR_ARG, "type-1 DMRS needs n_sc %% 4 == 0 (n_sc=%d)", c->n_sc);
+        for (int l = 0; l < c->n_layers; ++l) {
+            if (c->port[l] < 0 || c->port[l] > 3) return fail(PUSCH_ERR_ARG, "port[%d]=%d out of [0, 3]", l, c->port[l]);
+            for (int m = 0; m < l; ++m)
+                if (c->port[m] == c->port[l]) return fail(PUSCH_ERR_ARG, "ports must be distinct");
+        }
+        if (c->noise_var == PUSCH_NOISE_ESTIMATE)
+            return fail(PUSCH_ERR_UNSUPPORTED, "noise estimation is not available with type-1 DMRS");
+    }
     if (c->qam_bits != 2 && c->qam_bits != 4) return fail(PUSCH_ERR_ARG, "qam_bits=%d: 2 or 4", c->qam_bits);
     if (c->in_fp16 != 0 && c->in_fp16 != 1) return fail(PUSCH_ERR_ARG, "in_fp16 must be 0 or 1");
     if (c->form != PUSCH_FORM_FP32 && c->form != PUSCH_FORM_MIXED && c->form != PUSCH_FORM_FP8)
@@ -174,6 +188,11 @@ Geometry make_geometry(const pusch_cell_cfg &c) {
     g.shift = c.shift_7p5khz;
     g.sc_pitch = c.form == PUSCH_FORM_FP8 ? (c.n_sc + 15) & ~15 : (c.n_sc + 7) & ~7;
     for (int l = 0; l < 32; ++l) g.port[l] = l < c.n_layers ? c.port[l] : 0;
+    g.dmrs_type = c.dmrs_type;
+    if (c.dmrs_type == 1) {  // the estimate lives at the CDM pair centres: spacing 4, offset 1 + CDM group
+        g.comb = 4;
+        for (int l = 0; l < c.n_layers; ++l) g.port[l] = 1 + c.port[l] / 2;
+    }
     int nd = 0;
     for (int s = 0; s < c.n_sym; ++s)
         if (s != g.dmrs0 && s != g.dmrs1 && nd < 16) g.data_sym[nd++] = s;

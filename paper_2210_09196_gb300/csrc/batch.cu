@@ -542,6 +542,8 @@ pusch_status pusch_batch_create(pusch_batch **out, const pusch_cell_cfg *cells, 
         size_t ws;
         pusch_status st = pusch_workspace_size(&cc, 1, &ws);
         if (st != PUSCH_OK) return st;
+        if (cells[c].dmrs_type != 0)
+            return bfail(PUSCH_ERR_UNSUPPORTED, "cell %d: the batch uses the comb pilot model (dmrs_type 0)", c);
         if (cells[c].chol_every != 0)
             return bfail(PUSCH_ERR_UNSUPPORTED, "cell %d: the batch detects with one estimate per slot (chol_every 0)", c);
         if (cells[c].noise_var == PUSCH_NOISE_ESTIMATE)

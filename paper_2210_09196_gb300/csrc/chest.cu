@@ -15,6 +15,7 @@ namespace {
 
 struct ChestArgs {
     int n_sc, n_beams, n_layers, comb, n_sym, dmrs0, dmrs1;
+    int dmrs_type;                 // 1: type-1 DMRS, the table entries are OCC-despread CDM pairs
     int n_groups;                  // estimates interpolated in time: one per detection group
     float group_t[16];
     int port[32];
@@ -29,6 +30,7 @@ ChestArgs chest_args(const Geometry &g) {
     a.n_sym = g.n_sym;
     a.dmrs0 = g.dmrs0;
     a.dmrs1 = g.dmrs1;
+    a.dmrs_type = g.dmrs_type;
     a.n_groups = g.n_groups;
     for (int q = 0; q < 16; ++q) a.group_t[q] = g.group_t[q];
     for (int l = 0; l < 32; ++l) a.port[l] = g.port[l];
@@ -113,7 +115,19 @@ ls_pilots_kernel(ChestArgs g, int kmax, int sym, const float2 *__restrict__ beam
         const float2 *y0 = beam + (slot * g.n_sym + g.dmrs0) * (long long)g.n_sc * g.n_beams;
         const float2 *y1 = beam + (slot * g.n_sym + g.dmrs1) * (long long)g.n_sc * g.n_beams;
         const float2 *p0 = pilots + sl * 2LL * g.n_sc;
-        if (sym < 0)   // the mean of the two DMRS symbols
+        if (g.dmrs_type == 1) {
+            // type-1 DMRS: q is the centre of the CDM pair q - 1, q + 1 (both inside the band: n_sc % 4 == 0);
+            // 1/2 (y(q-1) / p(q-1) + y(q+1) / p(q+1)) despreads the OCC, per DMRS symbol
+            auto pair = [&](const float2 *y, int j) {
+                const float2 *p = p0 + (long long)j * g.n_sc;
+                return ls_value(__ldg(&y[(long long)(q - 1) * g.n_beams + b]), __ldg(&y[(long long)(q + 1) * g.n_beams + b]),
+                                pilot_inverse(__ldg(&p[q - 1])), pilot_inverse(__ldg(&p[q + 1])));
+            };
+            if (sym < 0)
+                v = cscale(cadd(pair(y0, 0), pair(y1, 1)), 0.5f);
+            else
+                v = sym == 0 ? pair(y0, 0) : pair(y1, 1);
+        } else if (sym < 0)   // the mean of the two DMRS symbols
             v = ls_value(__ldg(&y0[(long long)q * g.n_beams + b]), __ldg(&y1[(long long)q * g.n_beams + b]),
                          pilot_inverse(__ldg(&p0[q])), pilot_inverse(__ldg(&p0[g.n_sc + q])));
         else           // one DMRS symbol alone

@@ -72,6 +72,7 @@ pusch_status pusch_ls_grid(pusch_handle *h, int n_slots, const void *beam, const
     if (n_slots < 0 || n_slots > h->max_slots) return cfail(PUSCH_ERR_ARG, "n_slots out of [0, max_slots]");
     if (n_slots == 0) return PUSCH_OK;
     if (!beam || !pilots || !grid || !scale) return cfail(PUSCH_ERR_ARG, "pusch_ls_grid: NULL buffer");
+    if (h->geo.dmrs_type != 0) return cfail(PUSCH_ERR_UNSUPPORTED, "the learned estimator uses the comb pilot model");
     cudaError_t e = pusch::launch_ls_grid(h->geo, n_slots, (const float2 *)beam, (const float2 *)pilots,
                                           (__nv_bfloat16 *)grid, scale, (cudaStream_t)stream);
     if (e != cudaSuccess) return cfail(PUSCH_ERR_CUDA, "LS grid launch", e);
@@ -86,6 +87,7 @@ pusch_status pusch_chest_cnn(pusch_handle *h, int n_slots, const void *beam, con
     if (n_slots == 0) return PUSCH_OK;
     if (!beam || !pilots || !params || !H_hat) return cfail(PUSCH_ERR_ARG, "pusch_chest_cnn: NULL buffer");
     if (!(kappa > 0.f)) return cfail(PUSCH_ERR_ARG, "kappa must be > 0");
+    if (h->geo.dmrs_type != 0) return cfail(PUSCH_ERR_UNSUPPORTED, "the learned estimator uses the comb pilot model");
     const pusch::Geometry &g = h->geo;
     const long long grids_max = (long long)h->max_slots * g.n_layers * g.n_beams;
     if (grids_max > 65535) return cfail(PUSCH_ERR_UNSUPPORTED, "max_slots * n_layers * n_beams exceeds 65535 grids");

@@ -57,6 +57,7 @@ struct Geometry {
     int cp0, cp1;                 // prefix samples of symbol 0 and of the other symbols (cp == 1)
     long long slot_len;           // samples of one antenna's slot (cp == 1)
     int shift;                    // 1: undo the 7.5 kHz shift before the FFT
+    int dmrs_type;                // 1: 3GPP type-1 DMRS; comb / port then give the CDM pair centres (4, 1 + group)
 };
 
 // Complex time samples of one slot's input.

@@ -16,7 +16,8 @@ def cfg_for(cell, form: int = B.PUSCH_FORM_FP32, noise_var: float | None = None,
     return B.make_cfg(n_rx=cell.n_rx, n_fft=cell.n_fft, n_sc=cell.n_sc, n_beams=cell.n_beams,
                       n_layers=cell.n_layers, comb=cell.comb, ports=ports, qam_bits=cell.qam_bits,
                       in_fp16=cell.in_fp16, form=form, noise_var=nv, loading=loading, chol_every=chol_every,
-                      cp=getattr(cell, "cp", False), shift_7p5khz=getattr(cell, "shift_7p5khz", False))
+                      cp=getattr(cell, "cp", False), shift_7p5khz=getattr(cell, "shift_7p5khz", False),
+                      dmrs_type=1 if getattr(cell, "dmrs", "comb") == "type1" else 0)
 
 
 def time_tensor(slots, device="cuda", pin=False) -> torch.Tensor:

@@ -55,6 +55,10 @@ class CellConfig:
     tap_spacing_s: float = 60e-9
     doppler_hz: float = 0.0  # > 0: each tap fades over the slot (sum of 16 sinusoids, Clarke/Jakes spectrum)
     seed: int = 0
+    dmrs: str = "comb"       # "comb": layer l's QPSK pilots on subcarriers a % n_layers == l (seeded draws);
+                             # "type1": 3GPP type-1 DMRS, ports 0..3 (n_layers <= 4), Gold sequence of (n_id, n_scid)
+    n_id: int = 0
+    n_scid: int = 0
     cp: bool = False         # time input as one stream per antenna with NR normal cyclic prefixes
     shift_7p5khz: bool = False  # spectrum shifted up by 7.5 kHz (a quarter subcarrier) before transmission
 
@@ -208,12 +212,16 @@ def make_slot(cfg: CellConfig, slot_index: int = 0, seed: int | None = None) -> 
     W = beam_matrix(cfg)
     noise_var = float(10.0 ** (-cfg.snr_db / 10.0))
 
-    # DMRS: QPSK on each layer's comb, zero elsewhere.
+    # DMRS: QPSK on each layer's comb, zero elsewhere (or the 3GPP type-1 sequence of the slot).
     pb = rng.integers(0, 2, size=(L, 2, n_sc, 2))
     pil = qam_map(pb, 2)
     a = np.arange(n_sc)
     mask = (a[None, :] % comb) == ports[:, None]                          # [L, N_SC]
     pil = pil * mask[:, None, :]
+    if cfg.dmrs == "type1":
+        if L > 4:
+            raise ValueError("type-1 DMRS carries at most 4 ports")
+        pil = dmrs_type1(cfg.n_id, cfg.n_scid, slot_index % 20, ports, n_sc)
     pilots = pil.astype(np.complex64)
 
     bits = rng.integers(0, 2, size=(L, len(DATA_SYMBOLS), n_sc, q)).astype(np.uint8)
@@ -246,6 +254,38 @@ def make_slot(cfg: CellConfig, slot_index: int = 0, seed: int | None = None) -> 
     H_beam = np.matmul(W.astype(np.complex128).conj().T, Hant).transpose(0, 2, 1)   # [N_SC, L, B]
     return Slot(cfg=cfg, time_in=time_in, W=W, pilots=pilots, ports=ports, noise_var=noise_var,
                 H_beam=H_beam, x=x, bits=pack_bits(bits))
+
+
+def gold_bits(c_init: int, n: int) -> np.ndarray:
+    """c(0..n) of the length-31 Gold sequence of TS 38.211 5.2.1 (the transmitter's copy of the definition)."""
+    total = 1600 + n + 31
+    x1 = [0] * total
+    x2 = [0] * total
+    x1[0] = 1
+    for i in range(31):
+        x2[i] = (c_init >> i) & 1
+    for k in range(total - 31):
+        x1[k + 31] = x1[k + 3] ^ x1[k]
+        x2[k + 31] = x2[k + 3] ^ x2[k + 2] ^ x2[k + 1] ^ x2[k]
+    return np.array([x1[k + 1600] ^ x2[k + 1600] for k in range(n)], dtype=np.uint8)
+
+
+def dmrs_type1(n_id: int, n_scid: int, slot: int, ports, n_sc: int, dmrs=DMRS_SYMBOLS) -> np.ndarray:
+    """Transmitted type-1 DMRS [L, 2, n_sc] (TS 38.211 6.4.1.1): port p on subcarriers k = 4n + 2k' + p // 2 with
+    w_f(k') r(2n + k'), w_f = (1, -1) for odd p, r(m) = ((1 - 2c(2m)) + i (1 - 2c(2m + 1))) / sqrt 2 from
+    c_init = (2^17 (14 slot + l + 1)(2 n_id + 1) + 2 n_id + n_scid) mod 2^31 of DMRS symbol l."""
+    ports = list(ports)
+    out = np.zeros((len(ports), 2, n_sc), dtype=np.complex128)
+    for j, sym in enumerate(dmrs):
+        c_init = ((1 << 17) * (14 * slot + sym + 1) * (2 * n_id + 1) + 2 * n_id + n_scid) % (1 << 31)
+        c = gold_bits(c_init, n_sc + 2).astype(np.float64)
+        for li, p in enumerate(ports):
+            delta = p // 2
+            k = np.arange(delta, n_sc, 2)
+            m = (k - delta) // 2
+            w = np.where((p % 2 == 1) & (m % 2 == 1), -1.0, 1.0)
+            out[li, j, k] = w * ((1 - 2 * c[2 * m]) + 1j * (1 - 2 * c[2 * m + 1])) / np.sqrt(2)
+    return out
 
 
 def cp_lengths(n_fft: int) -> tuple[int, int]:

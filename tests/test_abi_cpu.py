@@ -78,6 +78,30 @@ def test_prefix_needs_512_points(B):
     assert B.lib().pusch_workspace_size(ctypes.byref(cfg), 1, ctypes.byref(out)) == B.PUSCH_ERR_ARG
 
 
+@pytest.mark.parametrize("bad,code", [
+    (dict(n_layers=5, n_beams=16), -1), (dict(ports=[0, 1, 1, 2]), -1), (dict(ports=[0, 1, 2, 4]), -1),
+    (dict(n_sc=302), -1), (dict(noise_var=-1.0), -5),
+])
+def test_type1_dmrs_rules(B, bad, code):
+    kw = dict(dmrs_type=1, ports=[0, 1, 2, 3])
+    kw.update(bad)
+    cfg = _good(**kw)
+    out = ctypes.c_size_t()
+    assert B.lib().pusch_workspace_size(ctypes.byref(cfg), 1, ctypes.byref(out)) == code
+
+
+def test_type1_pilot_generator_arguments(B):
+    ok = _good(dmrs_type=1, ports=[0, 1, 2, 3])
+    comb = _good()
+    sl = (ctypes.c_int * 1)(0)
+    assert B.lib().pusch_dmrs_type1_pilots(ctypes.byref(comb), 1, sl, 0, 0, 16, None) == B.PUSCH_ERR_ARG
+    assert B.lib().pusch_dmrs_type1_pilots(ctypes.byref(ok), 1, sl, 70000, 0, 16, None) == B.PUSCH_ERR_ARG
+    assert B.lib().pusch_dmrs_type1_pilots(ctypes.byref(ok), 1, sl, 0, 2, 16, None) == B.PUSCH_ERR_ARG
+    sl[0] = 160
+    assert B.lib().pusch_dmrs_type1_pilots(ctypes.byref(ok), 1, sl, 0, 0, 16, None) == B.PUSCH_ERR_ARG
+    assert B.lib().pusch_dmrs_type1_pilots(ctypes.byref(ok), 0, None, 0, 0, None, None) == B.PUSCH_OK
+
+
 def test_noise_estimate_mode_is_accepted(B):
     cfg = _good(noise_var=B.PUSCH_NOISE_ESTIMATE)
     out = ctypes.c_size_t()

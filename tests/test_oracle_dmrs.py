@@ -124,3 +124,20 @@ def test_ls_leakage_of_the_other_port_in_a_group(orc):
         c = 4 * n + 1
         assert np.allclose(H[c, 0], A[0] + c * S[0] - S[1], atol=1e-12)
         assert np.allclose(H[c, 1], A[1] + c * S[1] - S[0], atol=1e-12)
+
+
+def test_single_symbol_estimates_average_to_the_mean(orc):
+    n_sc, B = 48, 2
+    P = orc.dmrs_type1_pilots(1, 0, 4, [0, 1, 3], n_sc)
+    beam = RNG.standard_normal((14, n_sc, B)) + 1j * RNG.standard_normal((14, n_sc, B))
+    h0 = orc.chest_ls_type1_sym(beam, P, [0, 1, 3], 0)
+    h1 = orc.chest_ls_type1_sym(beam, P, [0, 1, 3], 1)
+    assert np.allclose(0.5 * (h0 + h1), orc.chest_ls_type1(beam, P, [0, 1, 3]), atol=1e-13)
+
+
+def test_generator_transmits_the_same_pilots(orc):
+    """The signal generator's own copy of the definition (the transmitter) agrees with the oracle exactly."""
+    from paper_2210_09196_gb300 import synth
+    for n_id, n_scid, slot in ((0, 0, 0), (517, 1, 13), (65535, 0, 19)):
+        assert np.array_equal(synth.dmrs_type1(n_id, n_scid, slot, [0, 1, 2, 3], 132),
+                              orc.dmrs_type1_pilots(n_id, n_scid, slot, [0, 1, 2, 3], 132))
