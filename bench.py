@@ -169,7 +169,7 @@ KERNELS = {"fft": ("fft_kernel", "fft_impl.cuh"),
            "beamform": {"mixed": ("beamform_tc_kernel", "beamform_tc.cu"), "fp8": ("beamform_tc_kernel", "beamform_tc.cu"),
                         "fp32": ("beamform_fp32_kernel", "beamform.cu")},
            "ls": ("ls_pilots_kernel", "chest.cu"),
-           "detect": ("mmse_kernel", "mmse_impl.cuh")}
+           "detect": ("mmse_kernel", "mmse_impl.cuh+detect_core.cuh")}
 
 
 def kernel_of(stage, form):
@@ -179,14 +179,18 @@ def kernel_of(stage, form):
 
 def measured_traffic(kernel, src, n_slots):
     """DRAM bytes per launch from the committed ncu summary, scaled to n_slots; None when the kernel's
-    source changed since the capture (its SHA-256 is stored beside the counters)."""
+    source changed since the capture (the SHA-256 of its source files, in order, is stored beside the
+    counters)."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             t = json.load(f)
         e = t[kernel]
-        with open(os.path.join(ROOT, "paper_2210_09196_gb300", "csrc", src), "rb") as f:
-            sha = hashlib.sha256(f.read()).hexdigest()
+        h = hashlib.sha256()
+        for part in src.split("+"):          # every source file the kernel is compiled from
+            with open(os.path.join(ROOT, "paper_2210_09196_gb300", "csrc", part), "rb") as f:
+                h.update(f.read())
+        sha = h.hexdigest()
         if sha != e["source_sha256"]:
             return None
         return int(e["dram_bytes"] / e["slots"] * n_slots)
