@@ -35,12 +35,13 @@ __host__ __device__ __forceinline__ int htile(int nb) {
     return m + ((2 - m) & 15);
 }
 
-// Row stride of the data-symbol rows in the single-cell detector: at least NL for the 16-layer class, whose
+// Row stride of the data-symbol rows in the single-cell detector: at least NL for the 16- and 32-layer classes,
+// whose
 // solve transposes the right-hand sides through those rows (detect_group, RHS_LANES).
 template <int NL>
 __host__ __device__ __forceinline__ int y_stride(int nb) {
     const int hs = row_stride(nb);
-    return NL == 16 && hs < NL ? NL : hs;
+    return NL >= 16 && hs < NL ? NL : hs;
 }
 
 // Shared memory of one warp of the single-cell detector: per subcarrier the H tile and the data-symbol rows.

@@ -160,7 +160,7 @@ mmse_kernel(MmseArgs g, long long total_sc, const float2 *__restrict__ H, const 
         if (q > 0) __syncwarp();
         stage_H<NL>(Ht, GROUPS ? H + q * g.h_group_stride : H, sc0, total_sc, nl, nb, hs, ht, lane);
         __syncwarp();
-        bad |= detect_group<NL, ND, NR, NL == 16>(hr, hg, Yt + (grp * nd + d0) * ys, Ht + grp * ht, hs, nb, ndq, nl,
+        bad |= detect_group<NL, ND, NR, (NL >= 16)>(hr, hg, Yt + (grp * nd + d0) * ys, Ht + grp * ht, hs, nb, ndq, nl,
                                                   g.sigma2 ? g.loading : g.load, i, src0, acc, g.sigma2,
                                                   valid ? slot : 0, ys);
         if (valid && i < nl) {
