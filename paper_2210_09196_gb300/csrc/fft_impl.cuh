@@ -313,7 +313,9 @@ __device__ __forceinline__ int e4m3_block_exp(float amax) {
 // non-finite value). Each warp quantises one (FFT, block): 4 subcarriers per lane.
 // Three 256-thread CTAs per SM (registers capped at 85; the 2-stage ring keeps shared memory at ~67 KB
 // per CTA for FP16 input): 24 warps hide the exchange barriers while one row per CTA streams in.
-template <int N, typename TIn, int OUT>
+// OPT: the input options (prefixed streams, shift) are compiled in; without them the kernel is the plain
+// contiguous-row transform.
+template <int N, typename TIn, int OUT, bool OPT>
 __global__ void __launch_bounds__(kFftThreads, 3)
 fft_kernel(const TIn *__restrict__ in, void *__restrict__ out, const float2 *__restrict__ tw, long long rows,
            int n_sc, int pitch, float *__restrict__ scales, int n_rx, int n_blk, uint32_t *__restrict__ err,
@@ -340,7 +342,7 @@ fft_kernel(const TIn *__restrict__ in, void *__restrict__ out, const float2 *__r
         const long long r0 = blk * F;
         const long long nr = rows - r0 < F ? rows - r0 : F;
         const int s = (int)(it % STAGES);
-        if (!fi.cp) {  // the block's rows are one contiguous span
+        if (!OPT || !fi.cp) {  // the block's rows are one contiguous span
             bulk_load(smem_u32(ring) + s * kSpan, in + r0 * N, (uint32_t)(nr * N * sizeof(TIn)), bar0 + 8 * s);
         } else {       // one copy per row, out of the antennas' streams
             bulk_expect(bar0 + 8 * s, (uint32_t)(nr * N * sizeof(TIn)));
@@ -379,7 +381,7 @@ fft_kernel(const TIn *__restrict__ in, void *__restrict__ out, const float2 *__r
         float2 v[E];
 #pragma unroll
         for (int e = 0; e < E; ++e) v[e] = to_f2(src[t + T * e]);
-        if (fi.shift) {
+        if (OPT && fi.shift) {
 #pragma unroll
             for (int e = 0; e < E; ++e) v[e] = cmul(v[e], __ldg(&tw[N + t + T * e]));
         }
@@ -543,7 +545,7 @@ cudaError_t launch_n(long long rows, const void *in, void *out, const float2 *tw
     constexpr int F = ffts_per_cta<N>();
     constexpr size_t smem = fft_smem_bytes<N, TIn>();
     static_assert(smem <= 227 * 1024, "FFT shared memory");
-    auto k = fft_kernel<N, TIn, OUT>;
+    auto k = (fi.cp || fi.shift) ? fft_kernel<N, TIn, OUT, true> : fft_kernel<N, TIn, OUT, false>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 152, per_sm = 1;
