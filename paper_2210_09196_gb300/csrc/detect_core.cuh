@@ -105,13 +105,18 @@ __device__ __forceinline__ bool factor_solve_rhs_lanes(float2 (&G)[NL], float2 *
         float2 Lrot[NL];  // (-Im, Re) of lane i's L entries
 #pragma unroll
         for (int j = 0; j < NL; ++j) {
-            float2 sj = G[j];
+            // two partial sums (even and odd k) halve the dependent FMA chain where the registers allow (the
+            // 16-layer class is at its 128-register cap and spills with them)
+            constexpr bool kSplit = NL >= 32;
+            float2 sj = G[j], sj1 = make_float2(0.f, 0.f);
 #pragma unroll
             for (int k = 0; k < j; ++k) {
                 const float4 b = lds4_ordered(L4 + j * (j - 1) / 2 + k);  // L[j][k], broadcast
-                sj = __ffma2_rn(make_float2(b.x, b.y), G[k], sj);          // G[k] holds L[i][k] by now
-                sj = __ffma2_rn(make_float2(b.z, b.w), Lrot[k], sj);
+                float2 &acc2 = (kSplit && (k & 1)) ? sj1 : sj;
+                acc2 = __ffma2_rn(make_float2(b.x, b.y), G[k], acc2);      // G[k] holds L[i][k] by now
+                acc2 = __ffma2_rn(make_float2(b.z, b.w), Lrot[k], acc2);
             }
+            sj = __fadd2_rn(sj, sj1);
             float dj = __shfl_sync(kFull, sj.x, src0 + j);
             if (!(dj > 0.f) || !isfinite(dj)) {
                 bad = true;
@@ -131,6 +136,7 @@ __device__ __forceinline__ bool factor_solve_rhs_lanes(float2 (&G)[NL], float2 *
     __syncwarp();
 
     const int dl = i < nd ? i : 0;
+    constexpr bool kSplitSolve = NL >= 32;  // as in the factorisation
     float2 u[NL], w[NL];
 #pragma unroll
     for (int k = 0; k < NL; k += 2) {
@@ -141,25 +147,29 @@ __device__ __forceinline__ bool factor_solve_rhs_lanes(float2 (&G)[NL], float2 *
     // forward: u_k += (-Re L) u_j + (Im L) (Im u_j, -Re u_j) = u_k - L[k][j] u_j
 #pragma unroll
     for (int k = 0; k < NL; ++k) {
+        float2 u1 = make_float2(0.f, 0.f);  // odd-j partial sum (shorter dependent chain)
 #pragma unroll
         for (int j = 0; j < k; ++j) {
             const float4 b = lds4_ordered(L4 + k * (k - 1) / 2 + j);
-            u[k] = __ffma2_rn(make_float2(b.x, b.y), u[j], u[k]);
-            u[k] = __ffma2_rn(make_float2(b.z, b.w), w[j], u[k]);
+            float2 &acc2 = (kSplitSolve && (j & 1)) ? u1 : u[k];
+            acc2 = __ffma2_rn(make_float2(b.x, b.y), u[j], acc2);
+            acc2 = __ffma2_rn(make_float2(b.z, b.w), w[j], acc2);
         }
-        u[k] = cscale(u[k], dv[k]);
+        u[k] = cscale(__fadd2_rn(u[k], u1), dv[k]);
         w[k] = make_float2(u[k].y, -u[k].x);
     }
     // back: u_k += (-Re L) x_j + (Im L) (-Im x_j, Re x_j) = u_k - conj(L[j][k]) x_j
 #pragma unroll
     for (int k = NL - 1; k >= 0; --k) {
+        float2 u1 = make_float2(0.f, 0.f);
 #pragma unroll
         for (int j = k + 1; j < NL; ++j) {
             const float4 b = lds4_ordered(L4 + j * (j - 1) / 2 + k);
-            u[k] = __ffma2_rn(make_float2(b.x, b.y), u[j], u[k]);
-            u[k] = __ffma2_rn(make_float2(b.z, b.w), w[j], u[k]);
+            float2 &acc2 = (kSplitSolve && (j & 1)) ? u1 : u[k];
+            acc2 = __ffma2_rn(make_float2(b.x, b.y), u[j], acc2);
+            acc2 = __ffma2_rn(make_float2(b.z, b.w), w[j], acc2);
         }
-        u[k] = cscale(u[k], dv[k]);
+        u[k] = cscale(__fadd2_rn(u[k], u1), dv[k]);
         w[k] = make_float2(-u[k].y, u[k].x);
     }
     __syncwarp();  // every lane has read its row of T
