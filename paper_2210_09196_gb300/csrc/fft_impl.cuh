@@ -398,28 +398,24 @@ fft_kernel(const TIn *__restrict__ in, void *__restrict__ out, const float2 *__r
                 }
             }
         } else if constexpr (OUT == kOutF16) {
-            // stage the two planes of this FFT in its exchange buffer (free after the last pass), then
-            // write them with 16-byte stores
-            __syncthreads();
-            __half *pl = reinterpret_cast<__half *>(sm);
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                int a = t + T * e + h;
-                if (a >= N) a -= N;
-                if (a < n_sc) {
-                    pl[a] = __float2half_rn(v[e].x);
-                    pl[pitch + a] = __float2half_rn(v[e].y);
-                }
-            }
-            for (int a = n_sc + t; a < pitch; a += T) {
-                pl[a] = __float2half_rn(0.f);
-                pl[pitch + a] = __float2half_rn(0.f);
-            }
-            __syncthreads();
+            // direct 2-byte stores of the two planes: consecutive threads hold consecutive bins, so each warp
+            // writes 64 contiguous bytes of each plane per register (no staging, no barrier)
             if (valid) {
-                const uint4 *srcv = reinterpret_cast<const uint4 *>(pl);
-                uint4 *dstv = reinterpret_cast<uint4 *>(static_cast<__half *>(out) + row * 2 * (long long)pitch);
-                for (int c = t; c < pitch / 4; c += T) dstv[c] = srcv[c];  // 2 * pitch halves = pitch / 4 x 16 B
+                __half *o = static_cast<__half *>(out) + row * 2 * (long long)pitch;
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    int a = t + T * e + h;
+                    if (a >= N) a -= N;
+                    if (a < n_sc) {
+                        const __half2 hv = __floats2half2_rn(v[e].x, v[e].y);
+                        o[a] = __low2half(hv);
+                        o[pitch + a] = __high2half(hv);
+                    }
+                }
+                for (int a = n_sc + t; a < pitch; a += T) {
+                    o[a] = __float2half_rn(0.f);
+                    o[pitch + a] = __float2half_rn(0.f);
+                }
             }
         } else {
             // stage this FFT's active bins (FP32) in its exchange buffer, then quantise block by block
