@@ -107,6 +107,14 @@ SHAPES = [
     dict(n_rx=40, n_fft=1024, n_sc=601, n_beams=24, n_layers=7, qam_bits=4),
     dict(n_rx=64, n_fft=2048, n_sc=1638, n_beams=40, n_layers=16, qam_bits=4),
     dict(n_rx=70, n_fft=4096, n_sc=3276, n_beams=64, n_layers=32, qam_bits=4),
+    # the 16- and 32-lane classes with padded lanes (identity rows), odd beam counts (8-byte staging) and
+    # beam counts whose row stride is below the lane count (the data-symbol rows padded to it). Square or
+    # nearly square H is avoided: its Gram matrices reach condition numbers near 1e4, where a plain FP32
+    # Cholesky (LAPACK) is itself 2e-5 from the FP64 result; these shapes stay below 2e-6 there.
+    dict(n_rx=12, n_fft=256, n_sc=200, n_beams=12, n_layers=9, qam_bits=2),
+    dict(n_rx=24, n_fft=512, n_sc=300, n_beams=15, n_layers=12, qam_bits=4),
+    dict(n_rx=20, n_fft=512, n_sc=333, n_beams=20, n_layers=17, qam_bits=4),
+    dict(n_rx=48, n_fft=1024, n_sc=720, n_beams=33, n_layers=25, qam_bits=2),
 ]
 
 
