@@ -274,8 +274,13 @@ constexpr int ffts_per_cta() {
     return (kFftThreads / (N / Plan<N>::E)) > 0 ? kFftThreads / (N / Plan<N>::E) : 1;
 }
 
+// One ring stage: the next row's copy is issued as soon as every thread has loaded the current row into
+// registers, so it still overlaps the transform, and the smaller footprint fits one more CTA per SM
+// (FP16 input: 4 x 51 KB; c64 input: 3 x 67 KB).
 template <typename TIn>
-constexpr int fft_stages() { return 2; }
+constexpr int fft_stages() { return 1; }
+template <typename TIn>
+constexpr int fft_min_ctas() { return sizeof(TIn) == 4 ? 4 : 3; }
 
 template <int N, typename TIn>
 constexpr size_t fft_smem_bytes() {
@@ -311,12 +316,12 @@ __device__ __forceinline__ int e4m3_block_exp(float amax) {
 // for which the block's largest |re|, |im| is at most 448 * 2^e; codes = round-to-nearest-even E4M3 of
 // value * 2^-e. Scales go to scales[(row / n_rx) * n_blk + blk][row % n_rx] (NaN for a block holding a
 // non-finite value). Each warp quantises one (FFT, block): 4 subcarriers per lane.
-// Three 256-thread CTAs per SM (registers capped at 85; the 2-stage ring keeps shared memory at ~67 KB
-// per CTA for FP16 input): 24 warps hide the exchange barriers while one row per CTA streams in.
+// Four 256-thread CTAs per SM for FP16 input (registers capped at 64, 51 KB of shared memory each), three for
+// c64 input: 32 (24) warps hide the exchange barriers while the next row per CTA streams in.
 // OPT: the input options (prefixed streams, shift) are compiled in; without them the kernel is the plain
 // contiguous-row transform.
 template <int N, typename TIn, int OUT, bool OPT>
-__global__ void __launch_bounds__(kFftThreads, 3)
+__global__ void __launch_bounds__(kFftThreads, fft_min_ctas<TIn>())
 fft_kernel(const TIn *__restrict__ in, void *__restrict__ out, const float2 *__restrict__ tw, long long rows,
            int n_sc, int pitch, float *__restrict__ scales, int n_rx, int n_blk, uint32_t *__restrict__ err,
            FftIn fi) {
@@ -358,7 +363,7 @@ fft_kernel(const TIn *__restrict__ in, void *__restrict__ out, const float2 *__r
     }
     __syncthreads();
     if (threadIdx.x == 0)
-        for (long long it = 0; it < STAGES - 1 && it < n_my; ++it) issue(it);
+        for (long long it = 0; it < (STAGES > 1 ? STAGES - 1 : 1) && it < n_my; ++it) issue(it);
 
     const int h = n_sc >> 1;
     long long it = 0;
@@ -373,7 +378,7 @@ fft_kernel(const TIn *__restrict__ in, void *__restrict__ out, const float2 *__r
             break;
         }
         // the ring slot consumed by the previous block is free (all threads passed a barrier since)
-        if (threadIdx.x == 0 && it + STAGES - 1 < n_my) issue(it + STAGES - 1);
+        if (STAGES > 1 && threadIdx.x == 0 && it + STAGES - 1 < n_my) issue(it + STAGES - 1);
 
         const long long row = (blockIdx.x + it * gridDim.x) * F + f;
         const bool valid = row < rows;
@@ -381,6 +386,11 @@ fft_kernel(const TIn *__restrict__ in, void *__restrict__ out, const float2 *__r
         float2 v[E];
 #pragma unroll
         for (int e = 0; e < E; ++e) v[e] = to_f2(src[t + T * e]);
+        if constexpr (STAGES == 1) {
+            // every thread holds its row in registers: the single ring slot takes the next block's copy
+            __syncthreads();
+            if (threadIdx.x == 0 && it + 1 < n_my) issue(it + 1);
+        }
         if (OPT && fi.shift) {
 #pragma unroll
             for (int e = 0; e < E; ++e) v[e] = cmul(v[e], __ldg(&tw[N + t + T * e]));
@@ -530,7 +540,7 @@ fft_kernel(const TIn *__restrict__ in, void *__restrict__ out, const float2 *__r
     }
     if (s_abort && threadIdx.x == 0) {
         // drain the copies still in flight (bounded) before the CTA exits
-        for (long long j = it; j < it + STAGES - 1 && j < n_my; ++j)
+        for (long long j = it; j < it + (STAGES > 1 ? STAGES - 1 : 1) && j < n_my; ++j)
             mbar_wait(bar0 + 8 * (int)(j % STAGES), (uint32_t)((j / STAGES) & 1));
     }
 }
