@@ -109,7 +109,7 @@ struct BRow {                      // interpolation parameters of one (subcarrie
 
 template <int NL>
 __host__ __device__ __forceinline__ size_t batch_warp_smem(int nbmax, int nd) {
-    return (size_t)(32 / NL) * ((pusch::htile<NL>(nbmax) + (size_t)nd * pusch::row_stride(nbmax)) * sizeof(float2) +
+    return (size_t)(32 / NL) * ((pusch::htile<NL>(nbmax) + (size_t)nd * pusch::y_stride<NL>(nbmax)) * sizeof(float2) +
                                 NL * sizeof(BRow));
 }
 
@@ -129,11 +129,10 @@ batch_detect_kernel(DetArgs g, int nbmax, const Segment *__restrict__ segs, cons
     const int src0 = grp * NL;
     const int nd = ND > 0 ? ND : g.n_data;
     const int ht = pusch::htile<NL>(nbmax);
-    const int hsm = pusch::row_stride(nbmax);
     unsigned char *wbase = smem_raw + (size_t)warp * batch_warp_smem<NL>(nbmax, nd);
     float2 *Ht = reinterpret_cast<float2 *>(wbase);
     float2 *Yt = Ht + SPW * ht;
-    BRow *rp = reinterpret_cast<BRow *>(Yt + (size_t)SPW * nd * hsm);
+    BRow *rp = reinterpret_cast<BRow *>(Yt + (size_t)SPW * nd * pusch::y_stride<NL>(nbmax));
 
     for (;;) {
         int item = 0;
@@ -142,7 +141,7 @@ batch_detect_kernel(DetArgs g, int nbmax, const Segment *__restrict__ segs, cons
         if (item >= n_items) break;
         const int2 it = items[item];
         const Segment sg = segs[it.x];
-        const int nb = sg.nb, nl = sg.nl, hs = pusch::row_stride(nb);
+        const int nb = sg.nb, nl = sg.nl, hs = pusch::row_stride(nb), ys = pusch::y_stride<NL>(nb);
         const int a = it.y + grp;
         const bool valid = a < sg.a0 + sg.n;
 
@@ -153,7 +152,7 @@ batch_detect_kernel(DetArgs g, int nbmax, const Segment *__restrict__ segs, cons
                 const int rem = idx - gg * nd * nb;
                 const int d = rem / nb, b = rem - d * nb;
                 const int aa = it.y + gg;
-                float2 *dst = Yt + (gg * nd + d) * hs + b;
+                float2 *dst = Yt + (gg * nd + d) * ys + b;
                 if (aa < sg.a0 + sg.n)
                     pusch::cp_async8(dst, beam + sg.beam_off + ((long long)data_symbol(g, d) * sg.n_sc + aa) * nb + b);
                 else
@@ -217,8 +216,10 @@ batch_detect_kernel(DetArgs g, int nbmax, const Segment *__restrict__ segs, cons
 
         // 2-4. Gram, right-hand sides, Cholesky, solves
         float2 acc[NR];
-        const bool bad = pusch::detect_group<NL, ND, NR>(Ht + grp * ht + i * hs, Ht + grp * ht, Yt + grp * nd * hs,
-                                                         Ht + grp * ht, hs, nb, nd, nl, sg.load, i, src0, acc);
+        // the 16- and 32-lane classes take the Crout factorisation and one-data-symbol-per-lane solves
+        const bool bad = pusch::detect_group<NL, ND, NR, (NL >= 16)>(Ht + grp * ht + i * hs, Ht + grp * ht,
+                                                                     Yt + grp * nd * ys, Ht + grp * ht, hs, nb, nd, nl,
+                                                                     sg.load, i, src0, acc, nullptr, 0, ys);
         if (valid && bad && i == 0) {
             atomicAdd(&status[1], 1u);
             atomicMin(&status[2], (unsigned)(sg.cell * 65536 + a));
