@@ -47,15 +47,22 @@ def parse():
 
 
 # ----------------------------------------------------------------------------------------- distributed
-def dist_init(n_gpus):
+def dist_init(n_gpus, backend=None):
+    """Ranks from the torchrun environment; one process per GPU over NCCL, or gloo without a GPU (the host-side
+    logic is exercised that way on CPU). Replicas only: no collective touches the data path."""
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
         import torch
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if backend is None:
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group("gloo")
     return rank, world, local
 
 
@@ -70,9 +77,14 @@ def max_over_ranks(x, world):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, seconds):
+    """Units all ranks processed per second of the slowest rank (weak scaling: every rank does the same work)."""
+    return units_per_rank * world / seconds
 
 
 # ------------------------------------------------------------------------------------------------ clocks
@@ -274,7 +286,7 @@ def run_ours(args, rank, world, local):
     total_ms, stages, outs = timed(rx, args.steps, args.warmup)
     clocks = sampler.stop()
     t_max = max_over_ranks(total_ms, world)
-    value = n * args.steps * world / (t_max / 1e3)
+    value = whole_job_rate(n * args.steps, world, t_max / 1e3)
     stat = outs[2].cpu().numpy()
 
     # the same form with one pass per call: stage times of kernels that do not share the GPU (context for the
@@ -294,7 +306,7 @@ def run_ours(args, rank, world, local):
         rx32 = make_rx("fp32")
         t32, st32, _ = timed(rx32, args.steps, args.warmup)
         t32 = max_over_ranks(t32, world)
-        fp32 = {"value": n * args.steps * world / (t32 / 1e3), "ms_per_step": t32 / args.steps,
+        fp32 = {"value": whole_job_rate(n * args.steps, world, t32 / 1e3), "ms_per_step": t32 / args.steps,
                 "stage_ms": st32}
         rx32.close()
 
@@ -331,7 +343,7 @@ def run_ours(args, rank, world, local):
         dt = max_over_ranks(time.perf_counter() - t0, world)
         h2d = t_h.numel() * t_h.element_size() + p_h.numel() * p_h.element_size()
         d2h = sum(t.numel() * t.element_size() for t in out_h)
-        e2e = {"value": n * e_steps * world / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+        e2e = {"value": whole_job_rate(n * e_steps, world, dt), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "steps": e_steps,
                "pipeline": f"{min(k_e2e, n)} chunk runs per call over two streams (fastest of "
                            f"{sorted(tune)} over 8 untimed calls each)"}
@@ -593,11 +605,11 @@ def reference_step(oracle, s, frac, rng):
 
 
 def run_reference(args, rank, world):
+    if rank != 0:          # the reference arm runs on rank 0 only; the other ranks exit without work
+        return None
     import numpy as np
     import oracle
     oracle.build()
-    if rank != 0:
-        return None
     from paper_2210_09196_gb300 import synth
     cell = synth.DEPLOY
     s = synth.make_slot(cell, 0)
