@@ -487,21 +487,25 @@ pusch_status slot_batch(pusch_handle *h, int n_slots, const void *time_in, const
     cudaEvent_t *ev = h->prof_events.empty() ? nullptr : take_records(h, k);
     if (k > 1 && (st = pipe_fork(h, s)) != PUSCH_OK) return st;
     size_t freq_off = 0;
-    for (int c = 0; c < k; ++c) {
+    for (int c = 0; c < k && st == PUSCH_OK; ++c) {
         int s0, nc;
         chunk_of(n_slots, k, c, s0, nc);
         cudaStream_t cs = k > 1 ? h->pipe[c & 1] : s;
-        if (time_host && (st = chunk_copies(h, true, s0, nc, time_host, pil_host, nullptr, nullptr, cs)) != PUSCH_OK)
-            return st;
-        st = run_chain(h, s0, nc, freq_off, time_in, W, pilots, x_hat, bits, stat, cs,
-                       ev ? ev + (size_t)c * (kSlotStages + 1) : nullptr);
-        if (st != PUSCH_OK) return st;
-        if (time_host && (st = chunk_copies(h, false, s0, nc, nullptr, nullptr, xhat_host, bits_host, cs)) != PUSCH_OK)
-            return st;
+        if (time_host) st = chunk_copies(h, true, s0, nc, time_host, pil_host, nullptr, nullptr, cs);
+        if (st == PUSCH_OK)
+            st = run_chain(h, s0, nc, freq_off, time_in, W, pilots, x_hat, bits, stat, cs,
+                           ev ? ev + (size_t)c * (kSlotStages + 1) : nullptr);
+        if (st == PUSCH_OK && time_host)
+            st = chunk_copies(h, false, s0, nc, nullptr, nullptr, xhat_host, bits_host, cs);
         freq_off += align256(freq_bytes(h->geo, nc));
     }
-    if (k > 1 && (st = pipe_join(h, s)) != PUSCH_OK) return st;
-    return PUSCH_OK;
+    // joined on every path once forked: whatever reached the pipeline streams stays ordered before the caller's
+    // later work (the first error is the one reported)
+    if (k > 1) {
+        const pusch_status sj = pipe_join(h, s);
+        if (st == PUSCH_OK) st = sj;
+    }
+    return st;
 }
 
 }  // namespace
