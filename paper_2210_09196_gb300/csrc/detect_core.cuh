@@ -80,7 +80,7 @@ __device__ __forceinline__ float4 lds4_ordered(const float4 *p) {
     return v;
 }
 
-// Steps 3-4 for the 16-layer class (lane i holds row i of G; r_d[i] in acc[d]):
+// Steps 3-4 for the 16- and 32-layer classes (lane i holds row i of G; r_d[i] in acc[d]):
 //   * r_d[i] goes to the group's (dead) data-symbol rows T[d][i] (stride ys >= NL);
 //   * Crout Cholesky, column j at step j: s_i = G[i][j] - sum_{k<j} L[i][k] conj(L[j][k]) in lane i, the pivot
 //     s_j broadcast by one shuffle, L[i][j] = s_i / sqrt(s_j); lane i keeps its row of L in registers and
@@ -185,7 +185,7 @@ __device__ __forceinline__ bool factor_solve_rhs_lanes(float2 (&G)[NL], float2 *
     return bad;
 }
 
-// RHS_LANES (16-layer class): the solves run with one data symbol per lane instead of one layer per lane
+// RHS_LANES (16- and 32-layer classes): the solves run with one data symbol per lane instead of one layer per lane
 // (below); the data-symbol rows yt then have stride ys >= NL and are overwritten.
 template <int NL, int ND, int NR, bool RHS_LANES = false>
 __device__ __forceinline__ bool detect_group(const float2 *__restrict__ hr, const float2 *__restrict__ hg,
