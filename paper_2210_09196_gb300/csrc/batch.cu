@@ -216,8 +216,7 @@ batch_detect_kernel(DetArgs g, int nbmax, const Segment *__restrict__ segs, cons
 
         // 2-4. Gram, right-hand sides, Cholesky, solves
         float2 acc[NR];
-        // the 16- and 32-lane classes take the Crout factorisation and one-data-symbol-per-lane solves
-        const bool bad = pusch::detect_group<NL, ND, NR, (NL >= 16)>(Ht + grp * ht + i * hs, Ht + grp * ht,
+        const bool bad = pusch::detect_group<NL, ND, NR>(Ht + grp * ht + i * hs, Ht + grp * ht,
                                                                      Yt + grp * nd * ys, Ht + grp * ht, hs, nb, nd, nl,
                                                                      sg.load, i, src0, acc, nullptr, 0, ys);
         if (valid && bad && i == 0) {

@@ -2,9 +2,9 @@
 // shared by the single-cell detector and the ragged multi-cell detector.
 //
 // A group of NL lanes owns one subcarrier; lane i owns layer i. Inputs in shared memory: the group's
-// estimate rows H[l][b] (stride hs, rows >= nl zero) and its data-symbol vectors y_d[b] (stride hs).
-// Output: x_i for every data symbol in registers. The L tile ([NL][NL + 1] complex + NL floats) may alias
-// the H rows: it is written only after the last read of H.
+// estimate rows H[l][b] (stride hs, rows >= nl zero) and its data-symbol vectors y_d[b] (stride ys >= NL).
+// Output: x_i for every data symbol in registers. The packed L (NL(NL-1)/2 broadcast-ready float4 entries +
+// NL floats 1/L[k][k]) aliases the H rows: it is written only after the last read of H.
 #pragma once
 
 #include "internal.cuh"
@@ -24,7 +24,7 @@ __device__ __forceinline__ void cp_async_wait_all() {
 }
 
 // Shared memory per subcarrier, in float2 units: the H tile (NL rows of an even stride >= nb + 1), which
-// later holds L ([NL][NL + 1]).
+// later holds the packed L (at most NL(NL + 1) + NL/2 float2, the second term of the maximum below).
 __host__ __device__ __forceinline__ int row_stride(int nb) { return (nb + 3) & ~1; }
 template <int NL>
 __host__ __device__ __forceinline__ int htile(int nb) {
@@ -35,9 +35,9 @@ __host__ __device__ __forceinline__ int htile(int nb) {
     return m + ((2 - m) & 15);
 }
 
-// Row stride of the data-symbol rows in the single-cell detector: at least NL for the 16- and 32-layer classes,
-// whose
-// solve transposes the right-hand sides through those rows (detect_group, RHS_LANES).
+// Row stride of the data-symbol rows: at least NL, because the solves transpose the right-hand sides through
+// those rows (below NL only for the 16- and 32-lane classes with few beams; the smaller classes always have
+// row_stride(nb) >= NL).
 template <int NL>
 __host__ __device__ __forceinline__ int y_stride(int nb) {
     const int hs = row_stride(nb);
@@ -54,10 +54,6 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
 }
 
-
-__device__ __forceinline__ float2 det_shfl2(float2 v, int src) {
-    return make_float2(__shfl_sync(kDetFull, v.x, src), __shfl_sync(kDetFull, v.y, src));
-}
 
 // Gray hard decisions (3GPP TS 38.211 5.1.3 / 5.1.4), ties to bit 0.
 __device__ __forceinline__ uint8_t det_demap(float2 x, int q) {
@@ -80,14 +76,15 @@ __device__ __forceinline__ float4 lds4_ordered(const float4 *p) {
     return v;
 }
 
-// Steps 3-4 for the 16- and 32-layer classes (lane i holds row i of G; r_d[i] in acc[d]):
+// Steps 3-4 (lane i holds row i of G; r_d[i] in acc[d]):
 //   * r_d[i] goes to the group's (dead) data-symbol rows T[d][i] (stride ys >= NL);
 //   * Crout Cholesky, column j at step j: s_i = G[i][j] - sum_{k<j} L[i][k] conj(L[j][k]) in lane i, the pivot
 //     s_j broadcast by one shuffle, L[i][j] = s_i / sqrt(s_j); lane i keeps its row of L in registers and
 //     publishes each entry to shared memory as (-Re, -Re, Im, Im) (packed lower triangle, rows in order), so
 //     that every complex multiply-add below is one broadcast 16-byte load and two packed FMAs;
-//   * lane d solves data symbol d: forward z_k = (r_k - sum_{j<k} L[k][j] z_j) / L[k][k], back
-//     x_k = (z_k - sum_{j>k} conj(L[j][k]) x_j) / L[k][k], in registers; lanes d >= nd solve a copy of symbol 0;
+//   * lane i solves data symbols i, i + NL, ...: forward z_k = (r_k - sum_{j<k} L[k][j] z_j) / L[k][k], back
+//     x_k = (z_k - sum_{j>k} conj(L[j][k]) x_j) / L[k][k], in registers (a lane past the last symbol solves a
+//     copy of symbol 0 and discards it); the results are written back only after every lane has read;
 //   * x_d[i] returns to lane i through T.
 // Uses the H tile (lt) for L: 120 float4 + NL floats.
 template <int NL, int ND, int NR>
@@ -135,48 +132,62 @@ __device__ __forceinline__ bool factor_solve_rhs_lanes(float2 (&G)[NL], float2 *
     dv[i] = dinv;
     __syncwarp();
 
-    const int dl = i < nd ? i : 0;
+    // right-hand sides per lane: lane i solves data symbols i, i + NL, ... (one for 16 and 32 lanes; the
+    // small classes take several); a lane past the last symbol solves a copy of symbol 0 and discards it
+    constexpr int RPL = (NR + NL - 1) / NL;
     constexpr bool kSplitSolve = NL >= 32;  // as in the factorisation
-    float2 u[NL], w[NL];
+    float2 X[RPL][NL];
 #pragma unroll
-    for (int k = 0; k < NL; k += 2) {
-        const float4 v = *reinterpret_cast<const float4 *>(yt + dl * ys + k);
-        u[k] = make_float2(v.x, v.y);
-        u[k + 1] = make_float2(v.z, v.w);
-    }
-    // forward: u_k += (-Re L) u_j + (Im L) (Im u_j, -Re u_j) = u_k - L[k][j] u_j
+    for (int r = 0; r < RPL; ++r) {
+        const int d = i + NL * r;
+        const int dl = d < nd ? d : 0;
+        float2 u[NL], w[NL];
 #pragma unroll
-    for (int k = 0; k < NL; ++k) {
-        float2 u1 = make_float2(0.f, 0.f);  // odd-j partial sum (shorter dependent chain)
-#pragma unroll
-        for (int j = 0; j < k; ++j) {
-            const float4 b = lds4_ordered(L4 + k * (k - 1) / 2 + j);
-            float2 &acc2 = (kSplitSolve && (j & 1)) ? u1 : u[k];
-            acc2 = __ffma2_rn(make_float2(b.x, b.y), u[j], acc2);
-            acc2 = __ffma2_rn(make_float2(b.z, b.w), w[j], acc2);
+        for (int k = 0; k < NL; k += 2) {
+            const float4 v = *reinterpret_cast<const float4 *>(yt + dl * ys + k);
+            u[k] = make_float2(v.x, v.y);
+            u[k + 1] = make_float2(v.z, v.w);
         }
-        u[k] = cscale(__fadd2_rn(u[k], u1), dv[k]);
-        w[k] = make_float2(u[k].y, -u[k].x);
-    }
-    // back: u_k += (-Re L) x_j + (Im L) (-Im x_j, Re x_j) = u_k - conj(L[j][k]) x_j
+        // forward: u_k += (-Re L) u_j + (Im L) (Im u_j, -Re u_j) = u_k - L[k][j] u_j
 #pragma unroll
-    for (int k = NL - 1; k >= 0; --k) {
-        float2 u1 = make_float2(0.f, 0.f);
+        for (int k = 0; k < NL; ++k) {
+            float2 u1 = make_float2(0.f, 0.f);  // odd-j partial sum (shorter dependent chain)
 #pragma unroll
-        for (int j = k + 1; j < NL; ++j) {
-            const float4 b = lds4_ordered(L4 + j * (j - 1) / 2 + k);
-            float2 &acc2 = (kSplitSolve && (j & 1)) ? u1 : u[k];
-            acc2 = __ffma2_rn(make_float2(b.x, b.y), u[j], acc2);
-            acc2 = __ffma2_rn(make_float2(b.z, b.w), w[j], acc2);
+            for (int j = 0; j < k; ++j) {
+                const float4 b = lds4_ordered(L4 + k * (k - 1) / 2 + j);
+                float2 &acc2 = (kSplitSolve && (j & 1)) ? u1 : u[k];
+                acc2 = __ffma2_rn(make_float2(b.x, b.y), u[j], acc2);
+                acc2 = __ffma2_rn(make_float2(b.z, b.w), w[j], acc2);
+            }
+            u[k] = cscale(__fadd2_rn(u[k], u1), dv[k]);
+            w[k] = make_float2(u[k].y, -u[k].x);
         }
-        u[k] = cscale(__fadd2_rn(u[k], u1), dv[k]);
-        w[k] = make_float2(-u[k].y, u[k].x);
-    }
-    __syncwarp();  // every lane has read its row of T
-    if (i < nd) {
+        // back: u_k += (-Re L) x_j + (Im L) (-Im x_j, Re x_j) = u_k - conj(L[j][k]) x_j
 #pragma unroll
-        for (int k = 0; k < NL; k += 2)
-            *reinterpret_cast<float4 *>(yt + i * ys + k) = make_float4(u[k].x, u[k].y, u[k + 1].x, u[k + 1].y);
+        for (int k = NL - 1; k >= 0; --k) {
+            float2 u1 = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int j = k + 1; j < NL; ++j) {
+                const float4 b = lds4_ordered(L4 + j * (j - 1) / 2 + k);
+                float2 &acc2 = (kSplitSolve && (j & 1)) ? u1 : u[k];
+                acc2 = __ffma2_rn(make_float2(b.x, b.y), u[j], acc2);
+                acc2 = __ffma2_rn(make_float2(b.z, b.w), w[j], acc2);
+            }
+            u[k] = cscale(__fadd2_rn(u[k], u1), dv[k]);
+            w[k] = make_float2(-u[k].y, u[k].x);
+        }
+#pragma unroll
+        for (int k = 0; k < NL; ++k) X[r][k] = u[k];
+    }
+    __syncwarp();  // every lane has read its rows of T
+#pragma unroll
+    for (int r = 0; r < RPL; ++r) {
+        const int d = i + NL * r;
+        if (d < nd) {
+#pragma unroll
+            for (int k = 0; k < NL; k += 2)
+                *reinterpret_cast<float4 *>(yt + d * ys + k) = make_float4(X[r][k].x, X[r][k].y, X[r][k + 1].x, X[r][k + 1].y);
+        }
     }
     __syncwarp();
 #pragma unroll
@@ -185,16 +196,14 @@ __device__ __forceinline__ bool factor_solve_rhs_lanes(float2 (&G)[NL], float2 *
     return bad;
 }
 
-// RHS_LANES (16- and 32-layer classes): the solves run with one data symbol per lane instead of one layer per lane
-// (below); the data-symbol rows yt then have stride ys >= NL and are overwritten.
-template <int NL, int ND, int NR, bool RHS_LANES = false>
+// Steps 2-4 for one subcarrier per lane group; the data-symbol rows yt (stride ys >= NL) are overwritten.
+template <int NL, int ND, int NR>
 __device__ __forceinline__ bool detect_group(const float2 *__restrict__ hr, const float2 *__restrict__ hg,
                                              float2 *yt, float2 *lt, int hs, int nb, int nd,
                                              int nl, float load, int i, int src0, float2 (&acc)[NR],
                                              const float *__restrict__ sigma2 = nullptr, long long slot = 0,
                                              int ys = 0) {
     if (ys == 0) ys = hs;
-    constexpr unsigned kFull = kDetFull;
     // ---- 2a. Gram row i: G[j] = sum_b conj(H[i][b]) H[j][b], with packed FP32x2 FMAs: P[j] = sum_b Re(h_b) H[j][b]
     //         and Q[j] = sum_b Im(h_b) H[j][b] (h_b = H[i][b]), then G[j] = P[j] - i Q[j].
     float2 G[NL];
@@ -276,77 +285,7 @@ __device__ __forceinline__ bool detect_group(const float2 *__restrict__ hr, cons
     }
     __syncwarp();  // the H tile is reused for L below
 
-    if constexpr (RHS_LANES) return factor_solve_rhs_lanes<NL, ND, NR>(G, yt, lt, ys, nd, i, src0, acc);
-
-    // ---- 3. Cholesky, right-looking, row i of L replaces row i of G; then L -> shared memory
-    bool bad = false;
-    float dinv = 1.f;
-#pragma unroll
-    for (int j = 0; j < NL; ++j) {
-        float dj = __shfl_sync(kFull, G[j].x, src0 + j);
-        if (!(dj > 0.f) || !isfinite(dj)) {
-            bad = true;
-            dj = 1.f;
-        }
-        const float ljj = sqrtf(dj);
-        const float inv = 1.f / ljj;
-        if (i > j) G[j] = cscale(G[j], inv);
-        else if (i == j) G[j] = make_float2(ljj, 0.f);
-        else G[j] = make_float2(0.f, 0.f);
-        if (i == j) dinv = inv;
-#pragma unroll
-        for (int k = j + 1; k < NL; ++k) {
-            const float2 lkj = det_shfl2(G[j], src0 + k);
-            if (i >= k) {
-                // G[i][k] -= L[i][j] conj(L[k][j])
-                G[k].x -= G[j].x * lkj.x + G[j].y * lkj.y;
-                G[k].y -= G[j].y * lkj.x - G[j].x * lkj.y;
-            }
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < NL; ++k) lt[i * (NL + 1) + k] = G[k];
-    __syncwarp();
-
-    // ---- 4. forward L z = r, then back L^H x = z, for all data symbols, in unit-diagonal form:
-    //         with D = diag(L), u = D z solves (L D^-1) u = r and x solves (D^-1 L^H) x = D^-1 z, so each step
-    //         broadcasts an unknown that is already final (no scaling before the shuffle). Lane i's unknown is
-    //         final at step i and not updated afterwards. dv[k] = 1 / L[k][k] sits after L in shared memory.
-    float *dv = reinterpret_cast<float *>(lt + NL * (NL + 1));
-    dv[i] = dinv;
-    __syncwarp();
-    const float2 *lrow = lt + i * (NL + 1);  // L[i][k]
-    // the k loops stay rolled: their bodies (NR shuffled updates) are large, and unrolling them all made the
-    // kernel miss in the instruction cache
-#pragma unroll 1
-    for (int k = 0; k < NL; ++k) {
-        const float2 m = cscale(lrow[k], dv[k]);  // L[i][k] / L[k][k]
-#pragma unroll
-        for (int d = 0; d < NR; ++d) {
-            if (ND > 0 || d < nd) {
-                const float2 uk = det_shfl2(acc[d], src0 + k);
-                if (i > k) cfms(acc[d], m, uk);
-            }
-        }
-    }
-#pragma unroll
-    for (int d = 0; d < NR; ++d) acc[d] = cscale(acc[d], dinv * dinv);  // z_i / L[i][i]
-#pragma unroll 1
-    for (int k = NL - 1; k >= 0; --k) {
-        const float2 lki = cscale(lt[k * (NL + 1) + i], dinv);  // L[k][i] / L[i][i]
-#pragma unroll
-        for (int d = 0; d < NR; ++d) {
-            if (ND > 0 || d < nd) {
-                const float2 xk = det_shfl2(acc[d], src0 + k);
-                if (i < k) {
-                    // acc -= conj(L[k][i] / L[i][i]) x_k
-                    acc[d].x -= lki.x * xk.x + lki.y * xk.y;
-                    acc[d].y -= lki.x * xk.y - lki.y * xk.x;
-                }
-            }
-        }
-    }
-    return bad;
+    return factor_solve_rhs_lanes<NL, ND, NR>(G, yt, lt, ys, nd, i, src0, acc);
 }
 
 }  // namespace pusch

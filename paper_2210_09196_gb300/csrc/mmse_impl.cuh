@@ -8,10 +8,11 @@
 //   1. The estimate rows of the warp's subcarriers are copied to shared memory with 16-byte cp.async pieces
 //      (rows padded to an even stride).
 //   2. Lane i forms row i of G from 16-byte shared loads, then r_d = H^H y_d for every data symbol d.
-//   3. Right-looking Cholesky of G in registers: the pivot and column entries are broadcast by warp
-//      shuffles. L is written to shared memory over the (now dead) H tile.
-//   4. Forward and back solves for all data symbols together, one shuffle per unknown and symbol, L read
-//      from shared memory (row i for the forward solve, column i for the back solve).
+//   3. The r_d go to shared memory (over the group's data-symbol rows); Crout Cholesky of G column by column:
+//      lane i keeps row i of L in registers, the pivot by one shuffle, and publishes every entry over the (now
+//      dead) H tile as a broadcast-ready (-Re, -Re, Im, Im) float4.
+//   4. Lane i solves the forward and back systems of data symbols i, i + NL, ... with packed FMAs, one
+//      broadcast 16-byte load per complex multiply-add; x returns to lane i (= layer i) through shared memory.
 // With one estimate per slot, G and L are formed once per subcarrier, which gives the same result as forming
 // them per data symbol. With an estimate that varies in time (chol_every = K > 0) the data symbols are taken
 // in groups of K: steps 1-4 run per group with that group's estimate (Section VI's schedule: K = 1 is one
@@ -160,7 +161,7 @@ mmse_kernel(MmseArgs g, long long total_sc, const float2 *__restrict__ H, const 
         if (q > 0) __syncwarp();
         stage_H<NL>(Ht, GROUPS ? H + q * g.h_group_stride : H, sc0, total_sc, nl, nb, hs, ht, lane);
         __syncwarp();
-        bad |= detect_group<NL, ND, NR, (NL >= 16)>(hr, hg, Yt + (grp * nd + d0) * ys, Ht + grp * ht, hs, nb, ndq, nl,
+        bad |= detect_group<NL, ND, NR>(hr, hg, Yt + (grp * nd + d0) * ys, Ht + grp * ht, hs, nb, ndq, nl,
                                                   g.sigma2 ? g.loading : g.load, i, src0, acc, g.sigma2,
                                                   valid ? slot : 0, ys);
         if (valid && i < nl) {
