@@ -94,7 +94,8 @@ typedef struct {
                           1: NR normal cyclic prefixes (TS 38.211 5.3.1, 30 kHz): per slot one stream per
                           antenna, [n_rx][slot_len] with slot_len = n_sym * n_fft + cp0 + (n_sym - 1) * cp1,
                           cp0 = 352 * n_fft / 4096 (symbol 0), cp1 = 288 * n_fft / 4096 (other symbols);
-                          symbol s's useful part starts at s * (n_fft + cp1) + cp0. Needs n_fft >= 512.  */
+                          symbol s's useful part starts at s * (n_fft + cp1) + cp0. Needs n_fft >= 512.
+                          Not in the ragged batch (nor shift_7p5khz).                                */
     int shift_7p5khz;  /* 1: the transmitter shifted the spectrum up by 7.5 kHz (a quarter of the 30 kHz
                           spacing) with the phase reference at the start of each useful part (TS 38.211
                           5.4): sample n of the useful part is multiplied by exp(-2 pi i n / (4 n_fft))

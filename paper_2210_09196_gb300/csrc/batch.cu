@@ -542,6 +542,8 @@ pusch_status pusch_batch_create(pusch_batch **out, const pusch_cell_cfg *cells, 
         size_t ws;
         pusch_status st = pusch_workspace_size(&cc, 1, &ws);
         if (st != PUSCH_OK) return st;
+        if (cells[c].cp != 0 || cells[c].shift_7p5khz != 0)
+            return bfail(PUSCH_ERR_UNSUPPORTED, "cell %d: the batch takes time samples without prefixes or shift", c);
         if (cells[c].dmrs_type != 0)
             return bfail(PUSCH_ERR_UNSUPPORTED, "cell %d: the batch uses the comb pilot model (dmrs_type 0)", c);
         if (cells[c].chol_every != 0)

@@ -78,3 +78,23 @@ def test_pipelined_and_noalloc_chains_read_the_streams():
     torch.cuda.synchronize()
     assert nrel(x2.cpu().numpy(), x1.cpu().numpy()) < 1e-5
     rx.close()
+
+
+def test_batch_refuses_prefixed_cells():
+    rs = synth.make_ragged_slot(n_cells=2, n_users=4, slot_index=3)
+    good = host.RaggedReceiver(rs, B.PUSCH_FORM_FP32)
+    cells, users = list(good.cells), list(good.users)
+    good.close()
+    for field in ("cp", "shift_7p5khz"):
+        bad = [type(c)() for c in cells]
+        for b_, c in zip(bad, cells):
+            ctypes_copy(b_, c)
+        setattr(bad[1], field, 1)
+        with pytest.raises(B.PuschError) as ei:
+            B.pusch_batch_create(bad, users)
+        assert ei.value.code == B.PUSCH_ERR_UNSUPPORTED
+
+
+def ctypes_copy(dst, src):
+    import ctypes
+    ctypes.memmove(ctypes.addressof(dst), ctypes.addressof(src), ctypes.sizeof(src))
