@@ -172,7 +172,9 @@ pusch_status pusch_beamform(pusch_handle *h, int n_slots, const void *freq_in, c
  * division). For layer l and each of its pilot subcarriers q (q % comb == port[l]):
  *     LS[q][l][b] = 1/2 sum_{j=0,1} Y[dmrs_sym[j]][q][b] / P[l][j][q]
  * and every subcarrier a is linearly interpolated between the neighbouring pilot subcarriers of the
- * layer, holding the first/last pilot's value outside them.
+ * layer, holding the first/last pilot's value outside them. With dmrs_type = 1 the values are the despread
+ * CDM pairs at the pair centres instead (pusch_cell_cfg.dmrs_type); with chol_every > 0 this stage still
+ * returns the two-symbol mean (the time-varying estimates live inside pusch_slot).
  * beam   : [n_sym][n_sc][n_beams] c64 (only the DMRS symbols are read).
  * pilots : [n_layers][2][n_sc] c64 (entries off the layer's comb are not read).
  * H_hat  : [n_sc][n_layers][n_beams] c64.
@@ -306,7 +308,8 @@ pusch_status pusch_chest_cnn(pusch_handle *h, int n_slots, const void *beam, con
  * subcarrier ranges (PRB allocations) and layer counts, processed by one CUDA graph launch.
  *
  * Per cell, cells[c] gives n_rx, n_fft, n_sc, n_beams, comb, noise_var, loading (its n_layers, port and
- * qam_bits are not used); in_fp16, form, n_sym and dmrs_sym must be equal for all cells.
+ * qam_bits are not used); in_fp16, form, n_sym and dmrs_sym must be equal for all cells. Cells with cp,
+ * shift_7p5khz, dmrs_type 1, chol_every > 0 or PUSCH_NOISE_ESTIMATE are refused (PUSCH_ERR_UNSUPPORTED).
  * Users overlap freely: at every subcarrier, all layers of all users whose range covers it are detected
  * jointly (MU-MIMO, Eq. 2 with N_L = those layers). A user's layer l transmits its pilots on the
  * subcarriers a of its range with a % comb == port0 + l; its estimate is interpolated between those pilots
