@@ -50,6 +50,7 @@ def lib():
             "orc_dmrs_type1_pilots": (I, [I, I, I, P, I, P, I, P]),
             "orc_chest_ls_type1": (I, [P, I, I, I, P, I, P, P, P]),
             "orc_chest_ls_type1_sym": (I, [P, I, I, I, P, I, P, P, I, P]),
+            "orc_noise_est_type1": (D, [P, I, I, I, P, I, P, P]),
             "orc_slot_len": (ctypes.c_longlong, [I, I]),
             "orc_ofdm_demod_cp": (I, [P, I, I, I, I, I, P]),
             "orc_beamform": (None, [P, P, I, I, I, I, P]),
@@ -154,6 +155,14 @@ def chest_ls_type1_sym(beam, pilots, ports, j: int, dmrs=DMRS_SYMBOLS) -> np.nda
     if rc != 0:
         raise ValueError(f"orc_chest_ls_type1_sym failed ({rc})")
     return H
+
+
+def noise_est_type1(beam, pilots, ports, dmrs=DMRS_SYMBOLS) -> float:
+    """sigma^2 from the type-1 DMRS residuals (degrees-of-freedom normalised)."""
+    beam, pilots = _c128(beam), _c128(pilots)
+    S, n_sc, B = beam.shape
+    return float(lib().orc_noise_est_type1(_p(beam), S, n_sc, B, _p(_i32(dmrs)), pilots.shape[0], _p(_i32(ports)),
+                                           _p(pilots)))
 
 
 def cp_len(n_fft: int, sym: int) -> int:

@@ -10,7 +10,8 @@
  *   orc_dft         Section II "OFDM demodulation ... via a FFT": the DFT definition itself.
  *   orc_fft         textbook recursive radix-2 decimation-in-time FFT (pinned against orc_dft).
  *   orc_ofdm_demod  Section II: one FFT per antenna and OFDM symbol, keep the N_SC active bins.
- *   orc_gold, orc_dmrs_cinit, orc_dmrs_type1_pilots, orc_chest_ls_type1  3GPP type-1 DMRS (TS 38.211 5.2.1,
+ *   orc_gold, orc_dmrs_cinit, orc_dmrs_type1_pilots, orc_chest_ls_type1, orc_noise_est_type1  3GPP type-1
+ *                   DMRS (TS 38.211 5.2.1,
  *                   6.4.1.1): Gold sequence, pilot mapping with frequency OCC, and the LS estimate with OCC
  *                   despreading over each CDM pair (the paper's element-wise division, then the pair mean).
  *   orc_cp_len, orc_slot_len, orc_ofdm_demod_cp  the same on a slot with NR normal cyclic prefixes and the
@@ -310,6 +311,47 @@ static int chest_ls_type1_weighted(const cplx *beam, int n_sc, int n_beams, cons
         free(ls);
     }
     return 0;
+}
+
+/* Noise variance with type-1 DMRS: the two ports of a CDM group share its REs, so on every pair (k0, k0 + 2)
+ * of a group with m of the layers' ports (m = 1 or 2) the 4 observations y_j(k) (2 REs x 2 DMRS symbols, per
+ * beam) are fitted by the m despread estimates h_l = 1/4 sum_{j,k} y_j(k) / p_{l,j}(k) -- the least-squares fit,
+ * the pilot vectors of a group being orthogonal and of unit modulus -- and the residual
+ * r_j(k) = y_j(k) - sum_l h_l p_{l,j}(k) keeps 4 - m degrees of freedom:
+ *     sigma2 = sum |r|^2 / sum (4 - m)      over groups, pairs and beams (unbiased for white noise). */
+double orc_noise_est_type1(const cplx *beam, int n_sym, int n_sc, int n_beams, const int *dmrs_sym, int n_layers,
+                           const int *ports, const cplx *pilots)
+{
+    (void)n_sym;
+    double sum = 0.0, dof = 0.0;
+    for (int delta = 0; delta < 2; ++delta) {
+        int ls[4], m = 0;
+        for (int l = 0; l < n_layers; ++l)
+            if (ports[l] / 2 == delta) ls[m++] = l;
+        if (m == 0) continue;
+        for (int k0 = delta; k0 + 2 < n_sc; k0 += 4) {
+            const int kk[2] = {k0, k0 + 2};
+            for (int b = 0; b < n_beams; ++b) {
+                cplx h[4];
+                for (int u = 0; u < m; ++u) {
+                    h[u] = 0;
+                    for (int j = 0; j < 2; ++j)
+                        for (int t = 0; t < 2; ++t)
+                            h[u] += beam[((size_t)dmrs_sym[j] * n_sc + kk[t]) * n_beams + b] /
+                                    pilots[((size_t)ls[u] * 2 + j) * n_sc + kk[t]];
+                    h[u] *= 0.25;
+                }
+                for (int j = 0; j < 2; ++j)
+                    for (int t = 0; t < 2; ++t) {
+                        cplx e = beam[((size_t)dmrs_sym[j] * n_sc + kk[t]) * n_beams + b];
+                        for (int u = 0; u < m; ++u) e -= h[u] * pilots[((size_t)ls[u] * 2 + j) * n_sc + kk[t]];
+                        sum += creal(e) * creal(e) + cimag(e) * cimag(e);
+                    }
+                dof += 4 - m;
+            }
+        }
+    }
+    return dof > 0 ? sum / dof : -1.0;
 }
 
 /* ---------------------------------------------------------- beamforming ---- */

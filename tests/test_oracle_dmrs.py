@@ -141,3 +141,29 @@ def test_generator_transmits_the_same_pilots(orc):
     for n_id, n_scid, slot in ((0, 0, 0), (517, 1, 13), (65535, 0, 19)):
         assert np.array_equal(synth.dmrs_type1(n_id, n_scid, slot, [0, 1, 2, 3], 132),
                               orc.dmrs_type1_pilots(n_id, n_scid, slot, [0, 1, 2, 3], 132))
+
+
+@pytest.mark.parametrize("ports", [[0, 1, 2, 3], [0], [0, 2], [0, 1, 3]])
+def test_noise_estimate_type1_zero_and_unbiased(orc, ports):
+    """Zero on a noiseless channel that is flat over each CDM pair; for white noise of variance s2 the
+    degrees-of-freedom normalisation (4 - m per pair, beam and group with m ports) makes the mean estimate s2
+    whatever the number of ports per group."""
+    n_sc, B = 48, 8
+    P = orc.dmrs_type1_pilots(5, 0, 3, ports, n_sc)
+    Hc = RNG.standard_normal((len(ports), B)) + 1j * RNG.standard_normal((len(ports), B))
+    clean = _beams(lambda k: Hc, P, n_sc, B)
+    assert orc.noise_est_type1(clean, P, ports) < 1e-25
+    s2 = 0.037
+    est = []
+    for _ in range(150):
+        n = np.sqrt(s2 / 2) * (RNG.standard_normal(clean.shape) + 1j * RNG.standard_normal(clean.shape))
+        est.append(orc.noise_est_type1(clean + n, P, ports))
+    assert np.mean(est) == pytest.approx(s2, rel=0.02)
+
+
+def test_noise_estimate_type1_phase_invariant(orc):
+    n_sc, B = 48, 4
+    P = orc.dmrs_type1_pilots(2, 1, 9, [0, 1, 2], n_sc)
+    beam = RNG.standard_normal((14, n_sc, B)) + 1j * RNG.standard_normal((14, n_sc, B))
+    a = orc.noise_est_type1(beam, P, [0, 1, 2])
+    assert orc.noise_est_type1(beam * np.exp(0.7j), P, [0, 1, 2]) == pytest.approx(a, rel=1e-12)
