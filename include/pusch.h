@@ -107,8 +107,10 @@ typedef struct {
                           p), so two ports share each comb-2 CDM group. pilots holds those values
                           (pusch_dmrs_type1_pilots). The LS estimate despreads each pair of a group,
                           1/2 (y(k0) / p(k0) + y(k0 + 2) / p(k0 + 2)), placed at k0 + 1, then interpolates
-                          between the pair centres as above. comb is ignored. Not with
-                          PUSCH_NOISE_ESTIMATE, the ragged batch or the learned estimator.            */
+                          between the pair centres as above; the noise estimate fits each CDM group's
+                          ports to the pair's 4 observations and divides the residual energy by its
+                          4 - m degrees of freedom (m ports in the group). comb is ignored. Not in the
+                          ragged batch or the learned estimator.                                      */
 } pusch_cell_cfg;
 
 /* noise_var value that makes the chain estimate sigma^2 per slot (pusch_noise_estimate) instead of using a

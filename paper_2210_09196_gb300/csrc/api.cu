@@ -59,8 +59,6 @@ pusch_status validate_cfg(const pusch_cell_cfg *c) {
             for (int m = 0; m < l; ++m)
                 if (c->port[m] == c->port[l]) return fail(PUSCH_ERR_ARG, "ports must be distinct");
         }
-        if (c->noise_var == PUSCH_NOISE_ESTIMATE)
-            return fail(PUSCH_ERR_UNSUPPORTED, "noise estimation is not available with type-1 DMRS");
     }
     if (c->qam_bits != 2 && c->qam_bits != 4) return fail(PUSCH_ERR_ARG, "qam_bits=%d: 2 or 4", c->qam_bits);
     if (c->in_fp16 != 0 && c->in_fp16 != 1) return fail(PUSCH_ERR_ARG, "in_fp16 must be 0 or 1");

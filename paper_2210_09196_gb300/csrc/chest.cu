@@ -179,9 +179,76 @@ ne_partial_kernel(ChestArgs g, int kmax, const float2 *__restrict__ beam, const 
     }
 }
 
-// Pass 2: one warp per slot adds the parts in a fixed order; sigma2[slot] = 2 * sum / count (the factor 2
-// undoes the two-symbol mean: E|y_j - LS p_j|^2 = sigma^2 / 2 for unit-modulus pilots).
-__global__ void ne_final_kernel(int n_parts, const float2 *__restrict__ partial, float *__restrict__ sigma2) {
+// The same with type-1 DMRS (the two ports of a CDM group share its REs): element (group, pair, beam) fits the
+// group's m = 1 or 2 layers to the pair's 4 observations y_j(k) (k = k0, k0 + 2; j = the two DMRS symbols) by
+// h_l = 1/4 sum y_j(k) / p_{l,j}(k) (least squares: the group's pilot vectors are orthogonal, unit modulus) and
+// sums |y_j(k) - sum_l h_l p_{l,j}(k)|^2 with 4 - m degrees of freedom. partial = {sum, degrees of freedom}.
+struct NeType1Args {
+    int n_sc, n_beams, n_layers, n_sym, dmrs0, dmrs1, n_pairs;
+    int m0, m1;                  // layers in CDM group 0 / 1
+    int l00, l01, l10, l11;      // their indices (group, slot in group)
+};
+
+__global__ void __launch_bounds__(256)
+ne_partial_type1_kernel(NeType1Args g, const float2 *__restrict__ beam, const float2 *__restrict__ pilots,
+                        float2 *__restrict__ partial) {
+    __shared__ float2 red[8];
+    const long long slot = blockIdx.y;
+    const int per_group = g.n_pairs * g.n_beams;
+    const float2 *y0 = beam + (slot * g.n_sym + g.dmrs0) * (long long)g.n_sc * g.n_beams;
+    const float2 *y1 = beam + (slot * g.n_sym + g.dmrs1) * (long long)g.n_sc * g.n_beams;
+    const float2 *pl = pilots + slot * g.n_layers * 2LL * g.n_sc;
+    float sum = 0.f, dof = 0.f;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < 2 * per_group; idx += gridDim.x * blockDim.x) {
+        const int delta = idx >= per_group ? 1 : 0;
+        const int rem = idx - delta * per_group;
+        const int n = rem / g.n_beams, b = rem - n * g.n_beams;
+        const int m = delta ? g.m1 : g.m0;
+        if (m == 0) continue;
+        const int la = delta ? g.l10 : g.l00, lb = delta ? g.l11 : g.l01;
+        const int k0 = 4 * n + delta, k1 = k0 + 2;
+        const float2 v[4] = {__ldg(&y0[(long long)k0 * g.n_beams + b]), __ldg(&y0[(long long)k1 * g.n_beams + b]),
+                             __ldg(&y1[(long long)k0 * g.n_beams + b]), __ldg(&y1[(long long)k1 * g.n_beams + b])};
+        float2 p[2][4], h[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const float2 *pu = pl + (long long)(u == 0 ? la : lb) * 2 * g.n_sc;
+            p[u][0] = __ldg(&pu[k0]);
+            p[u][1] = __ldg(&pu[k1]);
+            p[u][2] = __ldg(&pu[g.n_sc + k0]);
+            p[u][3] = __ldg(&pu[g.n_sc + k1]);
+            h[u] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int o = 0; o < 4; ++o) h[u] = cadd(h[u], cmul(v[o], pilot_inverse(p[u][o])));
+            h[u] = cscale(h[u], 0.25f);
+        }
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+            float2 e = csub(v[o], cmul(h[0], p[0][o]));
+            if (m == 2) e = csub(e, cmul(h[1], p[1][o]));
+            sum += e.x * e.x + e.y * e.y;
+        }
+        dof += (float)(4 - m);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
+        dof += __shfl_xor_sync(0xFFFFFFFFu, dof, o);
+    }
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = make_float2(sum, dof);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float2 t = make_float2(0.f, 0.f);
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = cadd(t, red[w]);
+        partial[slot * gridDim.x + blockIdx.x] = t;
+    }
+}
+
+// Pass 2: one warp per slot adds the parts in a fixed order; sigma2[slot] = factor * sum / count. Comb pilots:
+// factor 2 (it undoes the two-symbol mean: E|y_j - LS p_j|^2 = sigma^2 / 2 for unit-modulus pilots); type-1:
+// factor 1 (the count is already the degrees of freedom).
+__global__ void ne_final_kernel(int n_parts, const float2 *__restrict__ partial, float *__restrict__ sigma2,
+                                float factor) {
     const int slot = blockIdx.x, lane = threadIdx.x;
     float2 t = make_float2(0.f, 0.f);
     for (int p = lane; p < n_parts; p += 32) t = cadd(t, partial[(long long)slot * n_parts + p]);
@@ -190,7 +257,7 @@ __global__ void ne_final_kernel(int n_parts, const float2 *__restrict__ partial,
         t.x += __shfl_xor_sync(0xFFFFFFFFu, t.x, o);
         t.y += __shfl_xor_sync(0xFFFFFFFFu, t.y, o);
     }
-    if (lane == 0) sigma2[slot] = t.y > 0.f ? 2.f * t.x / t.y : 0.f;
+    if (lane == 0) sigma2[slot] = t.y > 0.f ? factor * t.x / t.y : 0.f;
 }
 
 }  // namespace
@@ -201,12 +268,35 @@ cudaError_t launch_noise_est(const Geometry &g, int n_slots, const float2 *beam,
                              float2 *partial, float *sigma2, cudaStream_t st) {
     if (n_slots == 0) return cudaSuccess;
     if (n_slots > 65535) return cudaErrorInvalidValue;
-    const ChestArgs a = chest_args(g);
-    ne_partial_kernel<<<dim3(kNoiseParts, (unsigned)n_slots), 256, 0, st>>>(a, ls_pilots_per_layer(g), beam, pilots,
-                                                                             partial);
+    if (g.dmrs_type == 1) {
+        NeType1Args a{};
+        a.n_sc = g.n_sc;
+        a.n_beams = g.n_beams;
+        a.n_layers = g.n_layers;
+        a.n_sym = g.n_sym;
+        a.dmrs0 = g.dmrs0;
+        a.dmrs1 = g.dmrs1;
+        a.n_pairs = g.n_sc / 4;                    // n_sc % 4 == 0 for type-1 cells: every pair complete
+        int cnt[2] = {0, 0}, lay[2][2] = {{0, 0}, {0, 0}};
+        for (int l = 0; l < g.n_layers; ++l) {
+            const int grp = g.port[l] - 1;         // the geometry's pair-centre offset is 1 + CDM group
+            if (grp >= 0 && grp < 2 && cnt[grp] < 2) lay[grp][cnt[grp]++] = l;
+        }
+        a.m0 = cnt[0];
+        a.m1 = cnt[1];
+        a.l00 = lay[0][0];
+        a.l01 = lay[0][1];
+        a.l10 = lay[1][0];
+        a.l11 = lay[1][1];
+        ne_partial_type1_kernel<<<dim3(kNoiseParts, (unsigned)n_slots), 256, 0, st>>>(a, beam, pilots, partial);
+    } else {
+        const ChestArgs a = chest_args(g);
+        ne_partial_kernel<<<dim3(kNoiseParts, (unsigned)n_slots), 256, 0, st>>>(a, ls_pilots_per_layer(g), beam,
+                                                                                 pilots, partial);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    ne_final_kernel<<<(unsigned)n_slots, 32, 0, st>>>(kNoiseParts, partial, sigma2);
+    ne_final_kernel<<<(unsigned)n_slots, 32, 0, st>>>(kNoiseParts, partial, sigma2, g.dmrs_type == 1 ? 1.f : 2.f);
     return cudaGetLastError();
 }
 

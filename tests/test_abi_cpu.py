@@ -80,7 +80,7 @@ def test_prefix_needs_512_points(B):
 
 @pytest.mark.parametrize("bad,code", [
     (dict(n_layers=5, n_beams=16), -1), (dict(ports=[0, 1, 1, 2]), -1), (dict(ports=[0, 1, 2, 4]), -1),
-    (dict(n_sc=302), -1), (dict(noise_var=-1.0), -5),
+    (dict(n_sc=302), -1),
 ])
 def test_type1_dmrs_rules(B, bad, code):
     kw = dict(dmrs_type=1, ports=[0, 1, 2, 3])
@@ -88,6 +88,12 @@ def test_type1_dmrs_rules(B, bad, code):
     cfg = _good(**kw)
     out = ctypes.c_size_t()
     assert B.lib().pusch_workspace_size(ctypes.byref(cfg), 1, ctypes.byref(out)) == code
+
+
+def test_type1_noise_estimate_mode_is_accepted(B):
+    cfg = _good(dmrs_type=1, ports=[0, 1, 2, 3], noise_var=B.PUSCH_NOISE_ESTIMATE)
+    out = ctypes.c_size_t()
+    assert B.lib().pusch_workspace_size(ctypes.byref(cfg), 1, ctypes.byref(out)) == 0
 
 
 def test_type1_pilot_generator_arguments(B):

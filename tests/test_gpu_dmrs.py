@@ -1,7 +1,8 @@
 """GPU 3GPP type-1 DMRS (TS 38.211 5.2.1, 6.4.1.1): the Gold-sequence pilot generator equals the signal
 generator's transmitted pilots bit for bit, and the chain with OCC-despread LS estimation (mean estimate, and
-the estimate interpolated in time) matches the FP64 oracle chain (orc_chest_ls_type1 + Eq. 2) at 1e-4; the
-paths without type-1 support refuse such cells."""
+the estimate interpolated in time, and with the noise variance estimated from the CDM-group residuals) matches
+the FP64 oracle chain (orc_chest_ls_type1 / orc_noise_est_type1 + Eq. 2) at 1e-4; the paths without type-1
+support refuse such cells."""
 import numpy as np
 import pytest
 import torch
@@ -96,3 +97,34 @@ def test_paths_without_type1_support_refuse_it():
     with pytest.raises(B.PuschError) as ei:
         B.pusch_batch_create(cells, users)
     assert ei.value.code == B.PUSCH_ERR_UNSUPPORTED
+
+
+def test_noise_estimate_type1_matches_oracle(orc):
+    n = 2
+    slots = synth.make_slots(CELL, n)
+    cfg = host.cfg_for(CELL, B.PUSCH_FORM_FP32)
+    rx = host.Receiver(cfg, max_slots=n)
+    pil = gpu_pilots(cfg, CELL, n)
+    beam = rx.beamform(rx.ofdm_fft(host.time_tensor(slots)), host.beam_tensor(slots[0].W))
+    sig = rx.noise_estimate(beam, pil).cpu().numpy()
+    for i, s in enumerate(slots):
+        want = orc.noise_est_type1(beam[i].cpu().numpy().astype(np.complex128), s.pilots, s.ports)
+        assert sig[i] == pytest.approx(want, rel=1e-5)
+    rx.close()
+
+
+def test_chain_type1_with_estimated_noise(orc):
+    n = 2
+    slots = synth.make_slots(CELL, n)
+    cfg = host.cfg_for(CELL, B.PUSCH_FORM_FP32, noise_var=B.PUSCH_NOISE_ESTIMATE)
+    rx = host.Receiver(cfg, max_slots=n)
+    x, _, st = rx.slot(host.time_tensor(slots), host.beam_tensor(slots[0].W), gpu_pilots(cfg, CELL, n))
+    torch.cuda.synchronize()
+    assert list(st.cpu().numpy()) == [0, 0, -1, 0]
+    for i, s in enumerate(slots):
+        beam = orc.beamform(orc.ofdm_demod(s.time_as_complex128(), CELL.n_sc), s.W)
+        sig = orc.noise_est_type1(beam, s.pilots, s.ports)
+        xo, fails = orc.mmse(orc.chest_ls_type1(beam, s.pilots, s.ports), beam, sig)
+        assert fails == 0
+        assert nrel(x[i].cpu().numpy().astype(np.complex128), xo) < 1e-4
+    rx.close()
