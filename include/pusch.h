@@ -62,6 +62,7 @@ typedef enum {
 /* Device status words written by the detection kernels (uint32_t status[4]):
  *   status[0] bit field of PUSCH_STATUS_* flags
  *   status[1] number of (slot, subcarrier) factorisations whose pivot was not a positive finite number
+ *             (with chol_every > 0, counted per detection group)
  *   status[2] smallest failing (slot * n_sc + subcarrier) index, 0xFFFFFFFF if none
  *   status[3] reserved (0)
  * The entry points that take `status` reset it to {0, 0, 0xFFFFFFFF, 0} on the stream first. */

@@ -16,18 +16,31 @@ cudaError_t launch_mmse(const Geometry &g, int n_slots, const float2 *H, const f
     a.load = g.noise_var + g.loading;
     a.loading = g.loading;
     a.sigma2 = sigma2;
-    a.n_groups = time_groups ? g.n_groups : 1;
-    a.group_k = time_groups ? g.chol_every : g.n_data;
-    a.h_group_stride = (long long)n_slots * g.n_sc * g.n_layers * g.n_beams;
     a.dmrs_lo = g.dmrs0 < g.dmrs1 ? g.dmrs0 : g.dmrs1;
     a.dmrs_hi = g.dmrs0 < g.dmrs1 ? g.dmrs1 : g.dmrs0;
     if (g.n_data > 14) return cudaErrorInvalidValue;
     const long long total_sc = (long long)n_slots * g.n_sc;
     if (total_sc == 0) return cudaSuccess;
     const int nl = g.n_layers;
-    if (nl <= 8) return mmse_launch_class(nl <= 2 ? 2 : (nl <= 4 ? 4 : 8), a, total_sc, H, beam, x_hat, bits, status, st);
-    if (nl <= 16) return mmse_launch_class16(a, total_sc, H, beam, x_hat, bits, status, st);
-    return mmse_launch_class32(a, total_sc, H, beam, x_hat, bits, status, st);
+    // one launch per detection group: group q detects data symbols [q K, q K + K) with its own estimate
+    // (H + q * stride); one group of all data symbols when the estimate does not vary in time
+    const int groups = time_groups ? g.n_groups : 1;
+    const int K = time_groups ? g.chol_every : g.n_data;
+    const long long stride = (long long)n_slots * g.n_sc * g.n_layers * g.n_beams;
+    for (int q = 0; q < groups; ++q) {
+        a.d_first = q * K;
+        a.n_det = g.n_data - q * K < K ? g.n_data - q * K : K;
+        const float2 *Hq = H + q * stride;
+        cudaError_t e;
+        if (nl <= 8)
+            e = mmse_launch_class(nl <= 2 ? 2 : (nl <= 4 ? 4 : 8), a, total_sc, Hq, beam, x_hat, bits, status, st);
+        else if (nl <= 16)
+            e = mmse_launch_class16(a, total_sc, Hq, beam, x_hat, bits, status, st);
+        else
+            e = mmse_launch_class32(a, total_sc, Hq, beam, x_hat, bits, status, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace pusch

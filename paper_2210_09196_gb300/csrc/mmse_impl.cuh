@@ -15,8 +15,8 @@
 //      broadcast 16-byte load per complex multiply-add; x returns to lane i (= layer i) through shared memory.
 // With one estimate per slot, G and L are formed once per subcarrier, which gives the same result as forming
 // them per data symbol. With an estimate that varies in time (chol_every = K > 0) the data symbols are taken
-// in groups of K: steps 1-4 run per group with that group's estimate (Section VI's schedule: K = 1 is one
-// factorisation per data symbol). Layers beyond n_layers (up to NL) are padded with identity rows and produce
+// in groups of K and each group is one launch of this kernel with that group's estimate (Section VI's
+// schedule: K = 1 is one factorisation per data symbol); d_first / n_det select the group's symbols. Layers beyond n_layers (up to NL) are padded with identity rows and produce
 // nothing.
 #pragma once
 
@@ -34,8 +34,7 @@ struct MmseArgs {
     float load;  // sigma^2 + extra loading (sigma2 == nullptr)
     float loading;             // extra loading alone
     const float *sigma2;       // per-slot noise variance (device) or nullptr
-    int n_groups, group_k;     // detection groups of group_k data symbols, each with its own estimate
-    long long h_group_stride;  // elements between the groups' estimates
+    int d_first, n_det;        // this launch detects data symbols d_first .. d_first + n_det - 1 (n_data in all)
     int dmrs_lo, dmrs_hi;      // the two DMRS symbols, dmrs_lo < dmrs_hi
 };
 
@@ -87,7 +86,7 @@ __device__ __forceinline__ void stage_H(float2 *Ht, const float2 *__restrict__ H
 
 // Register cap: five CTAs per SM up to 8 layers, seven for 16 layers (128 registers: the shared-memory
 // limit is also seven), none for 32.
-template <int NL, int ND, bool GROUPS>
+template <int NL, int ND>
 __global__ void __launch_bounds__(kMmseWarps * 32, NL <= 8 ? 5 : (NL == 16 ? 7 : 1))
 mmse_kernel(MmseArgs g, long long total_sc, const float2 *__restrict__ H, const float2 *__restrict__ beam,
             float2 *__restrict__ xhat, uint8_t *__restrict__ bits, uint32_t *__restrict__ status) {
@@ -97,7 +96,8 @@ mmse_kernel(MmseArgs g, long long total_sc, const float2 *__restrict__ H, const 
     const int grp = lane / NL, i = lane - grp * NL;
     const int src0 = grp * NL;
     const int nl = g.n_layers, nb = g.n_beams, n_sc = g.n_sc;
-    const int nd = ND > 0 ? ND : g.n_data;
+    // nd: the data symbols this launch detects (ND when compiled in, else n_det)
+    const int nd = ND > 0 ? ND : g.n_det;
     const int hs = row_stride(nb), ht = htile<NL>(nb), ys = y_stride<NL>(nb);
 
     unsigned char *wbase = smem_raw + (size_t)warp * warp_smem_bytes<NL>(nb, nd);
@@ -124,7 +124,8 @@ mmse_kernel(MmseArgs g, long long total_sc, const float2 *__restrict__ H, const 
             float2 *dst = Yt + (gg * nd + d) * ys + (wide ? 2 * c : c);
             if (sc < total_sc) {
                 const long long sl = sc / n_sc, aa = sc - sl * n_sc;
-                const float2 *src = beam + ((sl * g.n_sym + data_symbol(g, d)) * n_sc + aa) * nb + (wide ? 2 * c : c);
+                const float2 *src =
+                    beam + ((sl * g.n_sym + data_symbol(g, g.d_first + d)) * n_sc + aa) * nb + (wide ? 2 * c : c);
                 if (wide)
                     cp_async16(dst, src);
                 else
@@ -149,31 +150,21 @@ mmse_kernel(MmseArgs g, long long total_sc, const float2 *__restrict__ H, const 
     const float2 *hg = Ht + grp * ht;           // the group's rows
     constexpr int NR = ND > 0 ? ND : 14;
     float2 acc[NR];
-    bool bad = false, nonfinite = false;
-    // detection groups: one (all data symbols, one estimate) unless the estimate varies in time; group q holds
-    // data symbols [q K, q K + K) and its own estimate (the H tile is restaged: L of the previous group is dead)
-    // (GROUPS = false: one group of all data symbols, no loop -- the loop costs registers at the cap)
-    const int n_groups = GROUPS ? g.n_groups : 1;
-    for (int q = 0; q < n_groups; ++q) {
-        const int d0 = GROUPS ? q * g.group_k : 0;
-        const int ndq = ND > 0 ? ND : (GROUPS ? min(g.group_k, nd - d0) : nd);
-        // one call site, so that the staging code is inlined
-        if (q > 0) __syncwarp();
-        stage_H<NL>(Ht, GROUPS ? H + q * g.h_group_stride : H, sc0, total_sc, nl, nb, hs, ht, lane);
-        __syncwarp();
-        bad |= detect_group<NL, ND, NR>(hr, hg, Yt + (grp * nd + d0) * ys, Ht + grp * ht, hs, nb, ndq, nl,
-                                                  g.sigma2 ? g.loading : g.load, i, src0, acc, g.sigma2,
-                                                  valid ? slot : 0, ys);
-        if (valid && i < nl) {
-            const long long o0 = (slot * nl + i) * (long long)nd * n_sc + a;
+    stage_H<NL>(Ht, H, sc0, total_sc, nl, nb, hs, ht, lane);
+    __syncwarp();
+    const bool bad = detect_group<NL, ND, NR>(hr, hg, Yt + grp * nd * ys, Ht + grp * ht, hs, nb, nd, nl,
+                                              g.sigma2 ? g.loading : g.load, i, src0, acc, g.sigma2,
+                                              valid ? slot : 0, ys);
+    bool nonfinite = false;
+    if (valid && i < nl) {
+        const long long o0 = ((slot * nl + i) * (long long)g.n_data + g.d_first) * n_sc + a;
 #pragma unroll
-            for (int d = 0; d < NR; ++d) {
-                if (ND > 0 || d < ndq) {
-                    const float2 x = acc[d];
-                    xhat[o0 + (long long)(d0 + d) * n_sc] = x;
-                    bits[o0 + (long long)(d0 + d) * n_sc] = det_demap(x, g.qam_bits);
-                    if (!isfinite(x.x) || !isfinite(x.y)) nonfinite = true;
-                }
+        for (int d = 0; d < NR; ++d) {
+            if (ND > 0 || d < nd) {
+                const float2 x = acc[d];
+                xhat[o0 + (long long)d * n_sc] = x;
+                bits[o0 + (long long)d * n_sc] = det_demap(x, g.qam_bits);
+                if (!isfinite(x.x) || !isfinite(x.y)) nonfinite = true;
             }
         }
     }
@@ -185,15 +176,15 @@ mmse_kernel(MmseArgs g, long long total_sc, const float2 *__restrict__ H, const 
     if (__any_sync(kFull, nonfinite) && lane == 0) atomicOr(&status[0], (unsigned)PUSCH_STATUS_NONFINITE);
 }
 
-template <int NL, int ND, bool GROUPS>
+template <int NL, int ND>
 cudaError_t launch_nl(const MmseArgs &a, long long total_sc, const float2 *H, const float2 *beam, float2 *xhat,
                       uint8_t *bits, uint32_t *status, cudaStream_t st) {
     constexpr int SPW = 32 / NL;
-    const size_t smem = (size_t)kMmseWarps * warp_smem_bytes<NL>(a.n_beams, ND > 0 ? ND : a.n_data);
+    const size_t smem = (size_t)kMmseWarps * warp_smem_bytes<NL>(a.n_beams, ND > 0 ? ND : a.n_det);
     const long long per_cta = (long long)kMmseWarps * SPW;
     const long long grid = (total_sc + per_cta - 1) / per_cta;
     if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    auto k = mmse_kernel<NL, ND, GROUPS>;
+    auto k = mmse_kernel<NL, ND>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -202,14 +193,15 @@ cudaError_t launch_nl(const MmseArgs &a, long long total_sc, const float2 *H, co
     return cudaGetLastError();
 }
 
-// The 12-data-symbol instantiation serves one group of 12, the run-time count any other single group, and the
-// group loop the estimate that varies in time.
+// Compiled-in symbol counts: 12 (one estimate per slot), 4 and 1 (Section VI's schedules, one factorisation per
+// 4 data symbols or per symbol); anything else at run time.
 template <int NL>
 cudaError_t launch_nd(const MmseArgs &a, long long total_sc, const float2 *H, const float2 *beam, float2 *xhat,
                       uint8_t *bits, uint32_t *status, cudaStream_t st) {
-    if (a.n_groups > 1) return launch_nl<NL, 0, true>(a, total_sc, H, beam, xhat, bits, status, st);
-    if (a.n_data == 12) return launch_nl<NL, 12, false>(a, total_sc, H, beam, xhat, bits, status, st);
-    return launch_nl<NL, 0, false>(a, total_sc, H, beam, xhat, bits, status, st);
+    if (a.n_det == 12) return launch_nl<NL, 12>(a, total_sc, H, beam, xhat, bits, status, st);
+    if (a.n_det == 4) return launch_nl<NL, 4>(a, total_sc, H, beam, xhat, bits, status, st);
+    if (a.n_det == 1) return launch_nl<NL, 1>(a, total_sc, H, beam, xhat, bits, status, st);
+    return launch_nl<NL, 0>(a, total_sc, H, beam, xhat, bits, status, st);
 }
 
 }  // namespace mmse_detail
