@@ -2,11 +2,18 @@
 (OFDM FFT -> beamforming -> LS channel estimation -> MMSE detection) on the deployment cell
 (64 antennas, 4096-point FFT, 3276 subcarriers, 32 DFT beams, 16 single-layer 16-QAM users, 30 dB).
 
-python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--slots B] [--form mixed|fp32]
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--slots B]
+                [--form auto|mixed|fp32|fp8] [--workload deploy|massive|small] [--pipeline P] [--e2e-pipeline Q]
+                [--no-cpu-baseline] [--no-e2e] [--no-ragged] [--no-massive]
 
-A step is one pass of the whole chain over a batch of B distinct synthetic slots already resident in HBM
-(B = 16 -> 235 MB of FP16 time samples per step, more than the 129 MB L2, so every step streams from HBM).
-Rank 0 prints one JSON line. --impl reference times the FP64 CPU oracle on the host cores instead.
+A step is one pusch_slot call: the whole chain over a batch of B distinct synthetic slots already resident in
+HBM (B = 16 -> 235 MB of FP16 time samples per step, more than the 129 MB L2, so every step streams from HBM),
+run as P chunk runs over two streams (pusch_set_pipeline; P = 2 by default). Beside the headline the line
+carries the same form with one pass per call, the plain FP32 form, the end-to-end rate through
+pusch_slot_host (host buffers, copies timed), the CPU baseline (the FP64 oracle on every host core and on one),
+the ragged multi-cell batch and the massive-MIMO stream in all three forms. Rank 0 prints one JSON line;
+under torchrun every rank runs a replica and the step time is the max over ranks. --impl reference times the
+FP64 CPU oracle on the host cores instead.
 """
 from __future__ import annotations
 
