@@ -73,3 +73,17 @@ def test_plain_copy_prefix_without_shift(orc):
     parts = [np.concatenate([t[s][:, n_fft - orc.cp_len(n_fft, s):], t[s]], axis=1) for s in range(S)]
     got = orc.ofdm_demod_cp(np.concatenate(parts, axis=1), S, n_fft, n_sc)
     assert np.allclose(got, grid, atol=1e-11)
+
+
+@pytest.mark.parametrize("shift", [False, True])
+def test_generator_waveform_demodulates_to_the_plain_slot(orc, shift):
+    """The signal generator's prefixed (and shifted) stream of a slot, demodulated by the oracle, gives the
+    same grid as the plain slot with the same seed (up to the complex64 rounding of the stored samples)."""
+    from paper_2210_09196_gb300 import synth
+    cell = synth.SMALL_FP32
+    plain = synth.make_slot(cell, 4)
+    cp = synth.make_slot(cell.with_(cp=True, shift_7p5khz=shift), 4)
+    assert cp.time_in.shape == (cell.n_rx, orc.slot_len(14, cell.n_fft)) and cp.time_in.flags["C_CONTIGUOUS"]
+    f_plain = orc.ofdm_demod(plain.time_as_complex128(), cell.n_sc)
+    f_cp = orc.ofdm_demod_cp(cp.time_as_complex128(), 14, cell.n_fft, cell.n_sc, shift=shift)
+    assert np.max(np.abs(f_cp - f_plain)) < 1e-5 * np.max(np.abs(f_plain))
