@@ -391,7 +391,7 @@ def run_ours(args, rank, world, local):
     per_stage["detect"]["TFLOP/s"] = round(stage_flops(cell, n)["detect"] / (stages["detect"] / 1e3) / 1e12, 2)
 
     cpu, quality = None, None
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and world == 1:   # the host baseline is taken at N = 1 only
         cpu1, oracle_out = cpu_baseline(slots, budget_s=12.0)
         quality = evm_gate(outs, oracle_out, cell.qam_bits)
         quality["stage_error_db"] = stage_error_vs_fp64(rx, form, slots[0], time_d, W, pil_d)
