@@ -356,7 +356,7 @@ def run_ours(args, rank, world, local):
                            f"{sorted(tune)} over 8 untimed calls each)"}
 
     ragged = None if args.no_ragged else run_ragged(world)
-    massive = None if args.no_massive else run_massive(world, oracle_check=not args.no_cpu_baseline)
+    massive = None if args.no_massive else run_massive(world, oracle_check=not args.no_cpu_baseline and world == 1)
 
     if rank != 0:
         rx.close()
