@@ -147,3 +147,20 @@ def test_binding_rejects_non_contiguous_buffers(B):
         B._ptr(t)
     c = t.contiguous()
     assert B._ptr(c) == c.data_ptr()
+
+
+def test_header_compiles_as_c99(tmp_path):
+    """The boundary is a C ABI: the public header must compile as strict C99, not only as CUDA C++."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    root = Path(__file__).resolve().parents[1]
+    src = tmp_path / "abi.c"
+    src.write_text('#include "include/pusch.h"\n'
+                   "int main(void) { pusch_cell_cfg c; c.dmrs_type = 1; c.cp = 0; (void)c;\n"
+                   "  return pusch_version() != 0 ? 0 : 1; }\n")
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only", f"-I{root}",
+                        str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
