@@ -7,9 +7,9 @@
 //   * the last pass leaves bin t + T*e in register e, written to global memory in natural order,
 //   * the passes in between exchange through shared memory padded by one slot per 16 (conflict-free).
 // 4096 = 16*16*16 therefore costs one global read, two shared-memory exchanges and one global write.
-// CTAs are persistent: the input rows arrive by bulk (TMA) copies into a 2-3 stage ring issued ahead of
-// the transform, so HBM reads overlap the arithmetic. Twiddles come from a table exp(-2 pi i q / N)
-// (computed in double precision).
+// CTAs are persistent: the next input rows arrive by bulk (TMA) copies into a one-stage ring, issued as soon
+// as the current rows are in registers, so HBM reads overlap the arithmetic (four CTAs per SM for FP16 input).
+// Twiddles come from a table exp(-2 pi i q / N) (computed in double precision).
 #pragma once
 
 #include <float.h>
