@@ -1,6 +1,6 @@
 // LS estimate at a pilot subcarrier and its linear interpolation (Section II: block-type pilots, LS is
-// an element-wise division), shared by the channel-estimation kernel and the fused estimate+detection
-// kernel so both produce identical values.
+// an element-wise division), shared by the channel-estimation kernels, the ragged batch's detector (which
+// interpolates its estimate itself) and the learned estimator's fallback, so that all produce identical values.
 #pragma once
 
 #include "internal.cuh"
