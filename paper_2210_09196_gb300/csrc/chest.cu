@@ -3,9 +3,13 @@
 // followed by linear interpolation between each layer's comb of pilot subcarriers; and the noise-variance
 // estimate from the pilot residuals (Section II "NE").
 //
-// Two passes: the LS values at every layer's pilot subcarriers (a small table, L2-resident), then the full
-// estimate, one thread per output element (slot, subcarrier a, layer l, beam b), beam fastest, so that the
-// [n_sc][n_layers][n_beams] estimate the detector reads is written with fully coalesced stores.
+// Two passes: the LS values at every layer's pilot subcarriers (a small table, L2-resident; with type-1 DMRS
+// the OCC-despread CDM pairs at their centres), then the full estimate: a CTA per (16-subcarrier run, slot)
+// derives each (subcarrier, layer)'s two neighbouring pilots and weight once into shared memory, and each
+// thread writes 16-byte units (two beams) of every subcarrier of the run, so that the [n_sc][n_layers][n_beams]
+// estimate the detector reads is written with fully coalesced stores. For an estimate that varies in time the
+// table pass runs per DMRS symbol and the second pass writes one estimate per detection group (interpolated
+// in time to the group's mean symbol time).
 #include <algorithm>
 
 #include "chest_common.cuh"
