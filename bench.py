@@ -189,7 +189,7 @@ def stage_flops(cell, n):
 KERNELS = {"fft": ("fft_kernel", "fft_impl.cuh"),
            "beamform": {"mixed": ("beamform_tc_kernel", "beamform_tc.cu"), "fp8": ("beamform_tc_kernel", "beamform_tc.cu"),
                         "fp32": ("beamform_fp32_kernel", "beamform.cu")},
-           "ls": ("ls_pilots_kernel", "chest.cu"),
+           "ls": ("ls_pilots_kernel", "chest.cu+chest_common.cuh"),
            "detect": ("mmse_kernel", "mmse_impl.cuh+detect_core.cuh")}
 
 
@@ -364,8 +364,11 @@ def run_ours(args, rank, world, local):
 
     pk = peaks()
     sb = stage_bytes(cell, form, n)
-    dom = max(stages, key=stages.get)
-    dom_ms = stages[dom]
+    # the dominant kernel's roofline from the one-pass timing (its launches do not share the GPU with the other
+    # stream's kernels); the pipelined headline's stage times are reported beside it
+    roof_stages = iso["stage_ms"] if iso is not None else stages
+    dom = max(roof_stages, key=roof_stages.get)
+    dom_ms = roof_stages[dom]
     kname, ksrc = kernel_of(dom, form)
     traffic = measured_traffic(kname, ksrc, n)
     if (dom == "beamform" and form == "fp32") or dom == "detect":
@@ -377,11 +380,17 @@ def run_ours(args, rank, world, local):
                 "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": traffic, "algorithmic_flops": fl,
                 "hbm_frac": round(sb[dom] / (dom_ms / 1e3) / 1e9 / pk["hbm_gbs"], 4),
                 "peak_src": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
+        if iso is not None:
+            roof["timing"] = "one pass per call (CUDA events around the kernel on its stream)"
+            roof["pipelined_achieved"] = round(fl / (stages[dom] / 1e3) / 1e12, 2)
     else:
         ach = sb[dom] / (dom_ms / 1e3) / 1e9
         roof = {"kernel": kname, "bound": "hbm", "achieved": round(ach, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": round(ach / pk["hbm_gbs"], 4), "traffic": traffic, "algorithmic_bytes": sb[dom],
                 "peak_src": pk["src"] + " (MEASURED_PEAKS.json hbm_gbs)"}
+        if iso is not None:
+            roof["timing"] = "one pass per call (CUDA events around the kernel on its stream)"
+            roof["pipelined_achieved"] = round(sb[dom] / (stages[dom] / 1e3) / 1e9, 1)
     per_stage = {}
     for k, v in stages.items():
         gbs = sb[k] / (v / 1e3) / 1e9
@@ -395,6 +404,7 @@ def run_ours(args, rank, world, local):
         cpu1, oracle_out = cpu_baseline(slots, budget_s=12.0)
         quality = evm_gate(outs, oracle_out, cell.qam_bits)
         quality["stage_error_db"] = stage_error_vs_fp64(rx, form, slots[0], time_d, W, pil_d)
+        quality["snr_sweep"] = snr_sweep(cell, form)
         try:
             cpu = cpu_baseline_parallel(args.workload, budget_s=10.0)
             cpu["single_thread"] = cpu1
@@ -626,6 +636,27 @@ def stage_error_vs_fp64(rx, form, slot, time_d, W, pil_d):
     out["estimate"] = db(H[0].cpu().numpy(), h_o)
     out["detect"] = db(x[0].cpu().numpy(), x_o)
     return out
+
+
+def snr_sweep(cell, form, snrs=(0, 5, 10, 15, 20, 25, 30)):
+    """The workload's SNR sweep: one slot per SNR through the timed form, against the FP64 oracle chain on the
+    same inputs (EVM, hard-bit mismatches and those off a decision threshold)."""
+    import torch
+    from paper_2210_09196_gb300 import host, synth
+    import oracle
+    res = []
+    for snr in snrs:
+        c = cell.with_(snr_db=float(snr))
+        s = synth.make_slot(c, 100 + snr)
+        code = {"mixed": 1, "fp8": 2, "fp32": 0}[form]
+        r = host.Receiver(host.cfg_for(c, code), 1)
+        x, b, st = r.slot(host.time_tensor([s]), host.beam_tensor(s.W), host.pilot_tensor([s]))
+        torch.cuda.synchronize()
+        g = evm_gate((x, b, st), [oracle.run_slot(s)], c.qam_bits)
+        res.append({"snr_db": snr, "evm_db": g["evm_db"], "hard_bit_mismatches": g["hard_bit_mismatches"],
+                    "mismatches_off_threshold": g["mismatches_off_threshold"]})
+        r.close()
+    return res
 
 
 def evm_gate(gpu_outs, oracle_outs, q):

@@ -43,7 +43,7 @@ typedef enum {
     PUSCH_ERR_ARG = -1,         /* invalid argument (null pointer, size out of range, bad config)   */
     PUSCH_ERR_CUDA = -2,        /* a CUDA runtime call failed; the message names it                 */
     PUSCH_ERR_NUMERIC = -3,     /* only from pusch_status_check: the status words report a failure  */
-    PUSCH_ERR_TIMEOUT = -4,     /* a bounded device wait expired                                    */
+    PUSCH_ERR_TIMEOUT = -4,     /* only from pusch_status_check: a bounded device wait expired      */
     PUSCH_ERR_UNSUPPORTED = -5  /* valid but outside the shapes this build implements               */
 } pusch_status;
 
@@ -64,10 +64,16 @@ typedef enum {
  *   status[1] number of (slot, subcarrier) factorisations whose pivot was not a positive finite number
  *             (with chol_every > 0, counted per detection group)
  *   status[2] smallest failing (slot * n_sc + subcarrier) index, 0xFFFFFFFF if none
- *   status[3] reserved (0)
- * The entry points that take `status` reset it to {0, 0, 0xFFFFFFFF, 0} on the stream first. */
+ *   status[3] the kernel error bits behind PUSCH_STATUS_TIMEOUT: 1 a wait of a tensor-core kernel, 2 a wait
+ *             of the FFT's copy ring, 4 the wait self-test (pusch_selftest_wait); 0 if none
+ * The entry points that take `status` reset it to {0, 0, 0xFFFFFFFF, 0} on the stream first.
+ * Every kernel that waits on asynchronous copies or MMAs gives up after 2 s and sets a bit in an error word
+ * of its handle (or batch, or no-alloc call) instead of hanging; pusch_slot, pusch_slot_host,
+ * pusch_mmse_detect, pusch_batch_run and pusch_slot_noalloc move that word into status[0] / status[3] at
+ * their end (pusch_mmse_detect also reports expiries of the handle's earlier stage calls) and clear it. */
 #define PUSCH_STATUS_PIVOT 0x1u     /* Cholesky met a non-positive or non-finite pivot            */
 #define PUSCH_STATUS_NONFINITE 0x2u /* a detected symbol came out non-finite                      */
+#define PUSCH_STATUS_TIMEOUT 0x4u   /* a bounded device wait expired: the call's outputs are not valid */
 
 typedef struct {
     int n_rx;          /* N_R receive antennas                                                   */
@@ -388,8 +394,11 @@ pusch_status pusch_batch_tuning(const pusch_batch *b, int *out, int n_out);
  *     PUSCH_ERR_UNSUPPORTED and launches nothing; pusch_last_error() says how many bytes were needed.
  *     (One 16-antenna, 512-point, 300-subcarrier slot needs about 1.3 MB; a 64-antenna, 4096-point,
  *     3276-subcarrier slot does not fit.)
- *   - The first call on a device looks up the buffer's device address (cudaGetSymbolAddress), which may
- *     load the library's device code; make that first call before any stream capture.
+ *   - Every call looks up the buffer's device address in the current context (cudaGetSymbolAddress); the
+ *     first call on a device may load the library's device code there, so make that first call before any
+ *     stream capture.
+ *   - chol_every > 0 (the time-varying estimate) is refused with PUSCH_ERR_UNSUPPORTED: it needs a handle.
+ *   - An expired bounded wait is reported as PUSCH_STATUS_TIMEOUT in `status`, as for pusch_slot.
  *   - All calls share the one buffer, which keeps the last call's contents; each call writes everything
  *     it reads from it. Calls that overlap on the GPU (other streams, other host threads) race on it:
  *     serialise them.
@@ -410,6 +419,29 @@ pusch_status pusch_slot_noalloc(const pusch_cell_cfg *cfg, int n_slots, const vo
  */
 pusch_status pusch_profile_start(pusch_handle *h, int max_calls);
 pusch_status pusch_profile_read(pusch_handle *h, float *stage_ms, int n_stages, int *n_calls);
+
+/*
+ * Synchronous check of finished work (no counterpart in the paper). Waits for `stream`, then reads the
+ * status words `status` (DEVICE, 4 words, may be NULL) and, when h is not NULL, the handle's kernel error
+ * word, which it clears. Returns
+ *   PUSCH_ERR_TIMEOUT  if a bounded device wait expired (status[0] & PUSCH_STATUS_TIMEOUT, or the handle's
+ *                      word: a stage call such as pusch_beamform whose wait expired),
+ *   PUSCH_ERR_NUMERIC  else if the status words report a pivot failure or a non-finite detected symbol,
+ *   PUSCH_OK           otherwise (PUSCH_ERR_CUDA if the stream or the copies fail);
+ * pusch_last_error() then describes the failure (counts, first failing index, error bits).
+ */
+pusch_status pusch_status_check(pusch_handle *h, const uint32_t *status, void *stream);
+
+/*
+ * Health check of the failure-detection path (no counterpart in the paper). Launches on `stream` one
+ * single-thread kernel that waits, with the bounded wait every waiting kernel of the library uses but with a
+ * limit of limit_us microseconds (1 .. 1000000), on a shared-memory barrier that nothing completes. The wait
+ * expires and sets bit 4 of h's kernel error word; the kernel issues no copy, MMA or TMEM allocation, so it
+ * ends cleanly. Afterwards pusch_status_check(h, ...) returns PUSCH_ERR_TIMEOUT, and the next pusch_slot or
+ * pusch_mmse_detect on h reports PUSCH_STATUS_TIMEOUT in its status words. PUSCH_ERR_ARG for a NULL handle or
+ * a limit out of range.
+ */
+pusch_status pusch_selftest_wait(pusch_handle *h, unsigned limit_us, void *stream);
 
 /* Message of the last non-OK status returned on this thread ("" if none). */
 const char *pusch_last_error(void);

@@ -31,6 +31,7 @@ PUSCH_NOISE_ESTIMATE = -1.0
 
 PUSCH_STATUS_PIVOT = 0x1
 PUSCH_STATUS_NONFINITE = 0x2
+PUSCH_STATUS_TIMEOUT = 0x4
 
 # every symbol include/pusch.h declares
 EXPORTS = (
@@ -42,7 +43,7 @@ EXPORTS = (
     "pusch_batch_create", "pusch_batch_destroy", "pusch_batch_sizes", "pusch_batch_run", "pusch_batch_autotune",
     "pusch_batch_tuning",
     "pusch_cnn_param_count", "pusch_cnn_forward", "pusch_cnn_backward", "pusch_cnn_adam", "pusch_ls_grid",
-    "pusch_chest_cnn",
+    "pusch_chest_cnn", "pusch_status_check", "pusch_selftest_wait",
 )
 
 
@@ -130,6 +131,8 @@ def lib():
                                    P]),
             "pusch_ls_grid": (I, [P, I, P, P, P, P, P]),
             "pusch_chest_cnn": (I, [P, I, P, P, P, ctypes.c_float, P, P, P, P]),
+            "pusch_status_check": (I, [P, P, P]),
+            "pusch_selftest_wait": (I, [P, ctypes.c_uint, P]),
             "pusch_last_error": (ctypes.c_char_p, []),
             "pusch_version": (ctypes.c_char_p, []),
         }
@@ -239,6 +242,16 @@ def pusch_slot_noalloc(cfg: pusch_cell_cfg, n_slots, time_in, W, pilots, x_hat, 
     """pusch_slot without a handle and without device allocation (static library buffer)."""
     _check(lib().pusch_slot_noalloc(ctypes.byref(cfg), n_slots, _ptr(time_in), _ptr(W), _ptr(pilots), _ptr(x_hat),
                                     _ptr(bits), _ptr(status), _stream(stream)), "pusch_slot_noalloc")
+
+
+def pusch_status_check(h, status=None, stream=None) -> None:
+    """Waits for the stream and raises PuschError (code PUSCH_ERR_TIMEOUT or PUSCH_ERR_NUMERIC) if the status
+    words or the handle's kernel error word report a failure."""
+    _check(lib().pusch_status_check(h, _ptr(status), _stream(stream)), "pusch_status_check")
+
+
+def pusch_selftest_wait(h, limit_us: int, stream=None) -> None:
+    _check(lib().pusch_selftest_wait(h, int(limit_us), _stream(stream)), "pusch_selftest_wait")
 
 
 SLOT_STAGES = ("fft", "beamform", "ls", "detect")

@@ -369,6 +369,8 @@ pusch_status pusch_mmse_detect(pusch_handle *h, int n_slots, const void *H_hat, 
     cudaError_t e = pusch::launch_mmse(h->geo, n_slots, (const float2 *)H_hat, (const float2 *)beam, (float2 *)x_hat,
                                        bits, stat, s, sg2);
     if (e != cudaSuccess) return cuda_fail(e, "detection launch");
+    // expired waits of this handle's kernels since the last report (stage calls included)
+    if ((e = pusch::launch_status_fold(stat, h->kernel_err, s)) != cudaSuccess) return cuda_fail(e, "status fold");
     return ok();
 }
 
@@ -519,7 +521,10 @@ pusch_status pusch_slot(pusch_handle *h, int n_slots, const void *time_in, const
     uint32_t *stat = status ? status : h->status_sink;
     st = slot_batch(h, n_slots, time_in, W, pilots, x_hat, bits, stat, (cudaStream_t)stream, nullptr, nullptr, nullptr,
                     nullptr);
-    return st == PUSCH_OK ? ok() : st;
+    if (st != PUSCH_OK) return st;
+    const cudaError_t e = pusch::launch_status_fold(stat, h->kernel_err, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "status fold");
+    return ok();
 }
 
 pusch_status pusch_set_pipeline(pusch_handle *h, int n_chunks) {
@@ -614,6 +619,7 @@ pusch_status pusch_slot_host(pusch_handle *h, int n_slots, const void *time_in_h
     st = slot_batch(h, n_slots, h->h_time, W, h->h_pilots, h->h_xhat, h->h_bits, h->h_status, s, time_in_host,
                     pilots_host, x_hat_host, bits_host);
     if (st != PUSCH_OK) return st;
+    if ((e = pusch::launch_status_fold(h->h_status, h->kernel_err, s)) != cudaSuccess) return cuda_fail(e, "status fold");
     if (status_host &&
         (e = cudaMemcpyAsync(status_host, h->h_status, 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s)) !=
             cudaSuccess)

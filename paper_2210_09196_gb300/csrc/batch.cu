@@ -421,6 +421,8 @@ pusch_status enqueue(pusch_batch *b, const void *time_in, const void *W, const v
         }
         ++used;
     }
+    // expired waits of the batch's FFT and tensor-core kernels -> PUSCH_STATUS_TIMEOUT
+    if ((e = pusch::launch_status_fold(status, b->kernel_err, s)) != cudaSuccess) return fail_e("status fold launch");
     return PUSCH_OK;
 }
 

@@ -14,6 +14,7 @@
 
 #include <float.h>
 
+#include "bounded_wait.cuh"
 #include "internal.cuh"
 
 namespace pusch {
@@ -205,34 +206,12 @@ __device__ __forceinline__ float2 to_f2(__half2 v) { return __half22float2(v); }
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ uint64_t globaltimer() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
+using bw::mbar_init;
+using bw::mbar_try_wait;
 
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait (2 s of %globaltimer); false on expiry.
+// Bounded wait (the library's 2 s limit, bounded_wait.cuh); false on expiry.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    const uint64_t deadline = globaltimer() + 2000000000ull;
-    while (!mbar_try_wait(bar, parity))
-        if (globaltimer() > deadline) return false;
-    return true;
+    return bw::mbar_wait_for(bar, parity, bw::kWaitNs);
 }
 
 // Bulk (TMA, non-tensor) copies global -> shared completing on an mbarrier: 16-byte aligned, size % 16 == 0.
@@ -373,7 +352,7 @@ fft_kernel(const TIn *__restrict__ in, void *__restrict__ out, const float2 *__r
         if (__syncthreads_or(!ok)) {
             if (threadIdx.x == 0) {
                 s_abort = 1;
-                if (err) atomicOr(err, 2u);
+                if (err) atomicOr(err, kErrFftWait);
             }
             break;
         }

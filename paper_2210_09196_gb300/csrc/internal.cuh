@@ -100,11 +100,22 @@ inline size_t freq_bytes_of(const Geometry &g, int n_slots) {
 // Sets the thread's pusch_last_error() message.
 void set_last_error(const char *msg);
 
+// Bits of a kernel error word (one uint32 on the device per handle, batch or no-alloc call): a bounded wait
+// (bounded_wait.cuh) expired in a tensor-core kernel, in the FFT's copy ring, or in the wait self-test.
+constexpr uint32_t kErrTensorWait = 1u, kErrFftWait = 2u, kErrSelftest = 4u;
+// One thread, ordered on st after the kernels that may set err: when *err != 0, status[0] |=
+// PUSCH_STATUS_TIMEOUT and status[3] |= *err, then *err = 0.
+cudaError_t launch_status_fold(uint32_t *status, uint32_t *err, cudaStream_t st);
+
 // ------------------------------------------------------------------------------------------ launchers
 // Each returns cudaSuccess or the launch error. All pointers are device pointers.
 // err (device, one uint32): bit 1 is set if a bounded wait of the FFT kernel expired.
 cudaError_t launch_fft(const Geometry &g, int n_slots, const void *time_in, void *freq_out, const float2 *twiddle,
                        uint32_t *err, cudaStream_t st);
+// Mixed form, 4096-point FFTs of FP16 samples without prefixes or shift: the tensor-core FFT (fft_tc.cu).
+bool fft_tc_supported(const Geometry &g);
+cudaError_t launch_fft_tc(const Geometry &g, long long rows, const void *in, void *out, const float2 *tw,
+                          uint32_t *err, cudaStream_t st);
 cudaError_t launch_beamform_fp32(const Geometry &g, int n_slots, const float2 *freq, const float2 *W, float2 *beam,
                                  cudaStream_t st);
 // The full LS estimate (pilot table into ls_scratch, then interpolation); ls_scratch holds
@@ -190,7 +201,7 @@ struct pusch_handle {
     int max_slots = 0;
     int device = 0;
     float2 *twiddle = nullptr;      // FFT twiddle table (fft_twiddle_table)
-    uint32_t *kernel_err = nullptr;   // bounded-wait expiry flags of the tensor-core kernel
+    uint32_t *kernel_err = nullptr;   // error word (kErr* bits) of the handle's kernels, folded into the status
     void *freq = nullptr;           // workspace: FFT output
     float2 *beam = nullptr;         // workspace: beamformed grid
     float2 *ls = nullptr;           // workspace: LS values at the pilot subcarriers

@@ -8,18 +8,12 @@
 // overlaps on the GPU (two streams, or two host threads) race on it.
 #include <stdio.h>
 
-#include <mutex>
-
 #include "internal.cuh"
 
 // The static buffer: every GPU that loads this library holds it until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[PUSCH_NOALLOC_SCRATCH_BYTES];
 
 namespace {
-
-constexpr int kMaxDevices = 256;
-std::mutex g_setup_mutex;
-unsigned char *g_scratch_dev[kMaxDevices] = {};  // device address of g_noalloc_scratch, per device
 
 // Records the message returned by pusch_last_error() on this thread.
 pusch_status na_fail(pusch_status st, const char *msg, cudaError_t e = cudaSuccess) {
@@ -53,20 +47,14 @@ __global__ void noalloc_status_kernel(uint32_t *status, uint32_t *kernel_err) {
 
 size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// Device address of the static buffer on the current device; looked up on the first call per device.
+// Device address of the static buffer in the current device's context, looked up on every call (not cached:
+// after cudaDeviceReset, or in another context on the same device, the library's device code is loaded again
+// and the buffer may sit at another address). Once the module is loaded the lookup is a host-side table read.
 pusch_status scratch_for_current_device(unsigned char **out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return na_fail(PUSCH_ERR_CUDA, "cudaGetDevice", e);
-    if (dev < 0 || dev >= kMaxDevices) return na_fail(PUSCH_ERR_UNSUPPORTED, "device index out of range");
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_dev[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) return na_fail(PUSCH_ERR_CUDA, "cudaGetSymbolAddress of the static buffer", e);
-        g_scratch_dev[dev] = static_cast<unsigned char *>(p);
-    }
-    *out = g_scratch_dev[dev];
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return na_fail(PUSCH_ERR_CUDA, "cudaGetSymbolAddress of the static buffer", e);
+    *out = static_cast<unsigned char *>(p);
     return PUSCH_OK;
 }
 
@@ -86,7 +74,7 @@ extern "C" pusch_status pusch_slot_noalloc(const pusch_cell_cfg *cfg, int n_slot
         return na_fail(PUSCH_ERR_UNSUPPORTED, "pusch_slot_noalloc: chol_every > 0 needs a handle (pusch_slot)");
     const pusch::Geometry g = pusch::make_geometry(*cfg);
     const size_t tw_b = up256((size_t)pusch::fft_twiddle_count(g.n_fft) * sizeof(float2));
-    const size_t words_b = 256;  // status sink (16 B) + tensor-core timeout word (16 B)
+    const size_t words_b = 256;  // status sink (16 B) + kernel error word (16 B)
     const size_t freq_b = up256(pusch::freq_bytes_of(g, n_slots));
     const size_t beam_b = up256((size_t)n_slots * g.n_sym * g.n_sc * g.n_beams * sizeof(float2));
     const size_t H_b = up256((size_t)n_slots * g.n_sc * g.n_layers * g.n_beams * sizeof(float2));
@@ -133,6 +121,8 @@ extern "C" pusch_status pusch_slot_noalloc(const pusch_cell_cfg *cfg, int n_slot
     if ((e = pusch::launch_mmse(g, n_slots, H, beam, static_cast<float2 *>(x_hat), bits, stat, s,
                                 est ? sigma2 : nullptr)) != cudaSuccess)
         return na_fail(PUSCH_ERR_CUDA, "pusch_slot_noalloc detection launch", e);
+    if ((e = pusch::launch_status_fold(stat, tc_err, s)) != cudaSuccess)
+        return na_fail(PUSCH_ERR_CUDA, "pusch_slot_noalloc status fold", e);
     pusch::set_last_error("");
     return PUSCH_OK;
 }

@@ -164,3 +164,19 @@ def test_header_compiles_as_c99(tmp_path):
     r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only", f"-I{root}",
                         str(src)], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_status_and_selftest_arguments_are_checked_on_the_host(B):
+    L = B.lib()
+    assert L.pusch_selftest_wait(None, 1000, None) == B.PUSCH_ERR_ARG
+    assert L.pusch_selftest_wait(123, 0, None) == B.PUSCH_ERR_ARG          # limit below 1 us
+    assert L.pusch_selftest_wait(123, 2000000, None) == B.PUSCH_ERR_ARG    # limit above 1 s
+    assert "limit_us" in B.pusch_last_error()
+
+
+def test_noalloc_refuses_the_time_varying_estimate_on_the_host(B):
+    """chol_every > 0 needs a handle: refused before any CUDA call (the pointers are never touched)."""
+    cfg = _good(chol_every=4)
+    rc = B.lib().pusch_slot_noalloc(ctypes.byref(cfg), 1, 16, 16, 16, 16, 16, None, None)
+    assert rc == B.PUSCH_ERR_UNSUPPORTED
+    assert "chol_every" in B.pusch_last_error()

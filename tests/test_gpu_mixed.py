@@ -119,3 +119,38 @@ def test_deploy_chain_at_bench_batch(orc, deploy_slots, form):
             assert e <= -80.0, e                                            # FP32 end to end
             assert nrel(xg, xo) < 1e-4
     rx.close()
+
+
+SNR_SWEEP = (0.0, 5.0, 10.0, 15.0, 20.0, 25.0, 30.0)
+
+
+def test_deploy_mixed_chain_over_the_snr_sweep(orc):
+    """The deployment cell's SNR sweep (0-30 dB in 5 dB steps): at every SNR the mixed-form chain stays at
+    EVM <= -40 dB against the FP64 oracle chain on the same inputs, and its hard decisions differ only on
+    tie-ambiguous symbols (the oracle's symbol within 4x the observed error of a threshold). The printed
+    table (run with -s) records EVM, the mismatch count and the tie-ambiguous count per SNR."""
+    rows = []
+    for snr in SNR_SWEEP:
+        cell = synth.DEPLOY.with_(snr_db=snr)
+        slots = synth.make_slots(cell, 2, first=int(snr))
+        rx = host.Receiver(host.cfg_for(cell, B.PUSCH_FORM_MIXED), max_slots=2)
+        x, b, st = rx.slot(host.time_tensor(slots), host.beam_tensor(slots[0].W), host.pilot_tensor(slots))
+        torch.cuda.synchronize()
+        assert list(st.cpu().numpy()) == [0, 0, -1, 0]
+        s = slots[1]
+        xo, bo, fails = orc.run_slot(s)
+        assert fails == 0
+        xg = x[1].cpu().numpy().astype(np.complex128)
+        e = evm_db(xg, xo)
+        mism = b[1].cpu().numpy() != bo
+        err = np.max(np.abs(xg - xo))
+        t = 2 / np.sqrt(10)
+        near = np.minimum(np.minimum(np.abs(xo.real), np.abs(np.abs(xo.real) - t)),
+                          np.minimum(np.abs(xo.imag), np.abs(np.abs(xo.imag) - t))) <= 4 * err
+        rows.append((snr, e, int(mism.sum()), int((mism & near).sum())))
+        assert e <= -40.0, (snr, e)
+        assert not np.any(mism & ~near), snr
+        rx.close()
+    print("\nSNR dB, EVM vs FP64 chain dB, hard-bit mismatches, of which tie-ambiguous")
+    for r in rows:
+        print("  %4.0f  %7.2f  %d  %d" % r)
