@@ -356,7 +356,8 @@ fft_kernel(const TIn *__restrict__ in, void *__restrict__ out, const float2 *__r
             }
             break;
         }
-        // the ring slot consumed by the previous block is free (all threads passed a barrier since)
+        // the ring slot consumed by the previous block is free (all threads passed a barrier since, after the
+        // proxy fence that follows their reads of it)
         if (STAGES > 1 && threadIdx.x == 0 && it + STAGES - 1 < n_my) issue(it + STAGES - 1);
 
         const long long row = (blockIdx.x + it * gridDim.x) * F + f;
@@ -366,7 +367,10 @@ fft_kernel(const TIn *__restrict__ in, void *__restrict__ out, const float2 *__r
 #pragma unroll
         for (int e = 0; e < E; ++e) v[e] = to_f2(src[t + T * e]);
         if constexpr (STAGES == 1) {
-            // every thread holds its row in registers: the single ring slot takes the next block's copy
+            // every thread holds its row in registers: the single ring slot takes the next block's copy. The
+            // proxy fence orders this thread's generic reads of the slot before the bulk copy (async proxy)
+            // that overwrites it; without it the copy could land before every read had completed.
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncthreads();
             if (threadIdx.x == 0 && it + 1 < n_my) issue(it + 1);
         }
