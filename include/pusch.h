@@ -380,6 +380,24 @@ pusch_status pusch_batch_autotune(pusch_batch *b, const void *time_in, const voi
 pusch_status pusch_batch_tuning(const pusch_batch *b, int *out, int n_out);
 
 /*
+ * Autotuning of a single-cell handle's launch shapes (no counterpart in the paper; pusch_batch_autotune is the
+ * ragged batch's). Allocates stand-in inputs for max_slots slots (deterministic values: the timings do not
+ * depend on them), runs the chain once, and for each key not found in the cache file times the candidates on
+ * `stream` (synchronising it) and keeps the fastest:
+ *   "slot-fft ..."   FFT CTAs per SM: the kernel's own choice, or at most 3, 2 or 1
+ *   "slot-bf ..."    tensor-core beamforming GEMM (mixed and FP8 forms): K rows per pipeline stage and staged
+ *                    or direct output stores (every shape that fits shared memory)
+ *   "slot-det ..."   detector warps per CTA: 1, 2 or 4 (one estimate per slot, 12 data symbols)
+ *   "slot-pipe ..."  pusch_set_pipeline chunk count: 1, 2 or 4 (at most max_slots)
+ * The choices apply to the handle's later calls; every choice gives bit-identical results (each subcarrier's and
+ * each row's arithmetic is the same whatever the launch shape). cache_path may be NULL (nothing read or written);
+ * otherwise its lines "<key> | <choice>" are read and the newly timed keys appended. *n_timed (if not NULL)
+ * receives the number of keys that were timed. Allocates and frees device memory: not for use inside a stream
+ * capture. PUSCH_ERR_ARG for a NULL handle or a cache file that cannot be appended to.
+ */
+pusch_status pusch_autotune(pusch_handle *h, const char *cache_path, void *stream, int *n_timed);
+
+/*
  * pusch_slot for callers that cannot allocate device memory.
  * The paper has no counterpart of this entry point; it exists for integration. Some callers must not call
  * cudaMalloc: a real-time receiver thread, where the CUDA allocator can synchronise the device and take

@@ -43,7 +43,7 @@ EXPORTS = (
     "pusch_batch_create", "pusch_batch_destroy", "pusch_batch_sizes", "pusch_batch_run", "pusch_batch_autotune",
     "pusch_batch_tuning",
     "pusch_cnn_param_count", "pusch_cnn_forward", "pusch_cnn_backward", "pusch_cnn_adam", "pusch_ls_grid",
-    "pusch_chest_cnn", "pusch_status_check", "pusch_selftest_wait",
+    "pusch_chest_cnn", "pusch_status_check", "pusch_selftest_wait", "pusch_autotune",
 )
 
 
@@ -132,6 +132,7 @@ def lib():
             "pusch_ls_grid": (I, [P, I, P, P, P, P, P]),
             "pusch_chest_cnn": (I, [P, I, P, P, P, ctypes.c_float, P, P, P, P]),
             "pusch_status_check": (I, [P, P, P]),
+            "pusch_autotune": (I, [P, ctypes.c_char_p, P, ctypes.POINTER(I)]),
             "pusch_selftest_wait": (I, [P, ctypes.c_uint, P]),
             "pusch_last_error": (ctypes.c_char_p, []),
             "pusch_version": (ctypes.c_char_p, []),
@@ -248,6 +249,14 @@ def pusch_status_check(h, status=None, stream=None) -> None:
     """Waits for the stream and raises PuschError (code PUSCH_ERR_TIMEOUT or PUSCH_ERR_NUMERIC) if the status
     words or the handle's kernel error word report a failure."""
     _check(lib().pusch_status_check(h, _ptr(status), _stream(stream)), "pusch_status_check")
+
+
+def pusch_autotune(h, cache_path=None, stream=None) -> int:
+    """Tunes the handle's launch shapes (or reads them from cache_path); returns the number of keys timed."""
+    n = ctypes.c_int(0)
+    path = None if cache_path is None else str(cache_path).encode()
+    _check(lib().pusch_autotune(h, path, _stream(stream), ctypes.byref(n)), "pusch_autotune")
+    return n.value
 
 
 def pusch_selftest_wait(h, limit_us: int, stream=None) -> None:

@@ -5,8 +5,11 @@
 #include <string.h>
 
 #include <new>
+#include <string>
+#include <vector>
 
 #include "internal.cuh"
+#include "tune_cache.cuh"
 
 
 namespace {
@@ -319,7 +322,7 @@ pusch_status pusch_beamform(pusch_handle *h, int n_slots, const void *freq_in, c
     if (!freq_in || !W || !beam_out) return fail(PUSCH_ERR_ARG, "pusch_beamform: NULL buffer");
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = pusch::launch_beamform(h->geo, n_slots, freq_in, (const float2 *)W, (float2 *)beam_out,
-                                           h->kernel_err, s);
+                                           h->kernel_err, s, &h->bf_tune);
     if (e != cudaSuccess) return cuda_fail(e, "beamforming launch");
     return ok();
 }
@@ -415,7 +418,7 @@ pusch_status run_chain(pusch_handle *h, int s0, int n, size_t freq_off, const vo
     if ((e = pusch::launch_fft(g, n, tin, freq, h->twiddle, h->kernel_err, s)) != cudaSuccess)
         return cuda_fail(e, "fft launch");
     if (ev) cudaEventRecord(ev[1], s);
-    if ((e = pusch::launch_beamform(g, n, freq, (const float2 *)W, beam, h->kernel_err, s)) != cudaSuccess)
+    if ((e = pusch::launch_beamform(g, n, freq, (const float2 *)W, beam, h->kernel_err, s, &h->bf_tune)) != cudaSuccess)
         return cuda_fail(e, "beamforming launch");
     if (ev) cudaEventRecord(ev[2], s);
     const bool est = h->cfg.noise_var == PUSCH_NOISE_ESTIMATE;
@@ -629,3 +632,197 @@ pusch_status pusch_slot_host(pusch_handle *h, int n_slots, const void *time_in_h
 }
 
 }  // extern "C"
+
+namespace {
+
+// Deterministic stand-in data for pusch_autotune: a hash of the index mapped to [-amp, amp] (as FP16 when fp16),
+// or, for W, unit-modulus DFT-like entries / sqrt(n_rx).
+__global__ void tune_fill_kernel(void *dst, size_t n, float amp, int fp16, uint32_t seed) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        uint32_t x = (uint32_t)i * 2654435761u ^ seed;
+        x ^= x >> 15;
+        x *= 2246822519u;
+        x ^= x >> 13;
+        const float v = amp * ((float)(x & 0xffffu) / 32768.f - 1.f);
+        if (fp16)
+            static_cast<__half *>(dst)[i] = __float2half_rn(v);
+        else
+            static_cast<float *>(dst)[i] = v;
+    }
+}
+
+pusch_status tune_fill(void *dst, size_t n, float amp, int fp16, uint32_t seed, cudaStream_t s) {
+    tune_fill_kernel<<<256, 256, 0, s>>>(dst, n, amp, fp16, seed);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? PUSCH_OK : cuda_fail(e, "autotune fill");
+}
+
+}  // namespace
+
+extern "C" pusch_status pusch_autotune(pusch_handle *h, const char *cache_path, void *stream, int *n_timed) {
+    using namespace pusch::tune;
+    if (!h) return fail(PUSCH_ERR_ARG, "handle is NULL");
+    if (n_timed) *n_timed = 0;
+    pusch::Geometry &g = h->geo;
+    const int n = h->max_slots;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    std::map<std::string, std::string> cache = read_cache(cache_path);
+    std::vector<std::string> lines;
+    int timed = 0;
+    const int reps = 10;
+    char key[192], buf[320];
+
+    // stand-in inputs and outputs of one batch of max_slots slots
+    void *time_in = nullptr, *W = nullptr, *pil = nullptr, *xh = nullptr;
+    uint8_t *bits = nullptr;
+    const size_t t_elems = (size_t)n * pusch::time_elems_per_slot(g) * 2;
+    cudaError_t e = cudaMalloc(&time_in, time_bytes(g, n));
+    if (e == cudaSuccess) e = cudaMalloc(&W, (size_t)g.n_rx * g.n_beams * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMalloc(&pil, pilot_bytes(g, n));
+    if (e == cudaSuccess) e = cudaMalloc(&xh, xhat_count(g, n) * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&bits, xhat_count(g, n));
+    pusch_status st = e == cudaSuccess ? PUSCH_OK : cuda_fail(e, "autotune buffers");
+    if (st == PUSCH_OK) st = tune_fill(time_in, t_elems, 0.03f, g.in_fp16, 1u, s);
+    if (st == PUSCH_OK) st = tune_fill(W, (size_t)g.n_rx * g.n_beams * 2, 1.f / sqrtf((float)g.n_rx), 0, 2u, s);
+    if (st == PUSCH_OK) st = tune_fill(pil, pilot_bytes(g, n) / sizeof(float), 0.7071f, 0, 3u, s);
+    const int pipeline0 = h->pipeline;
+    auto chain = [&]() { return slot_batch(h, n, time_in, W, pil, xh, bits, h->status_sink, s, nullptr, nullptr,
+                                           nullptr, nullptr); };
+    if (st == PUSCH_OK) {
+        h->pipeline = 1;
+        st = chain();   // FFT output, beams and estimate for the per-stage candidates below
+    }
+    if (st == PUSCH_OK && (e = cudaStreamSynchronize(s)) != cudaSuccess) st = cuda_fail(e, "autotune first pass");
+
+    // 1. FFT CTAs per SM (0 = the kernel's own choice, then fewer)
+    if (st == PUSCH_OK) {
+        snprintf(key, sizeof key, "slot-fft form=%d n_fft=%d in_fp16=%d n_rx=%d slots=%d", g.form, g.n_fft, g.in_fp16,
+                 g.n_rx, n);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            g.fft_cap = value_of(it->second, "cap", 0);
+        } else {
+            const int caps[4] = {0, 3, 2, 1};
+            float best = 1e30f;
+            int best_cap = 0;
+            for (int c : caps) {
+                g.fft_cap = c;
+                const float ms = time_ms(s, reps, [&] {
+                    pusch::launch_fft(g, n, time_in, h->freq, h->twiddle, h->kernel_err, s);
+                }, &e);
+                if (e != cudaSuccess) {
+                    st = cuda_fail(e, "autotune FFT");
+                    break;
+                }
+                if (ms < best) best = ms, best_cap = c;
+            }
+            g.fft_cap = best_cap;
+            ++timed;
+            snprintf(buf, sizeof buf, "%s | cap=%d ms=%.5f", key, best_cap, best);
+            lines.push_back(buf);
+        }
+    }
+    // 2. tensor-core GEMM: K rows per pipeline stage and the output path
+    if (st == PUSCH_OK && g.form != PUSCH_FORM_FP32) {
+        snprintf(key, sizeof key, "slot-bf form=%d n_rx=%d n_beams=%d n_sc=%d slots=%d", g.form, g.n_rx, g.n_beams,
+                 g.n_sc, n);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            h->bf_tune.chunk_rows = value_of(it->second, "chunk", 0);
+            h->bf_tune.staged = value_of(it->second, "staged", 0);
+        } else {
+            pusch::TcTune cand[8];
+            const int nc = pusch::bf_tc_candidates(g, cand, 8);
+            float best = 1e30f;
+            pusch::TcTune bt;
+            for (int i = 0; i < nc && st == PUSCH_OK; ++i) {
+                const float ms = time_ms(s, reps, [&] {
+                    pusch::launch_beamform(g, n, h->freq, static_cast<const float2 *>(W), h->beam, h->kernel_err, s,
+                                           &cand[i]);
+                }, &e);
+                if (e != cudaSuccess) st = cuda_fail(e, "autotune beamforming");
+                else if (ms < best) best = ms, bt = cand[i];
+            }
+            h->bf_tune = bt;
+            ++timed;
+            snprintf(buf, sizeof buf, "%s | chunk=%d staged=%d ms=%.5f", key, bt.chunk_rows, bt.staged, best);
+            lines.push_back(buf);
+        }
+    }
+    // 3. detector warps per CTA (the 12-data-symbol kernels of one estimate per slot)
+    if (st == PUSCH_OK && g.chol_every == 0 && g.n_data == 12) {
+        snprintf(key, sizeof key, "slot-det form=%d n_layers=%d n_beams=%d n_sc=%d slots=%d", g.form, g.n_layers,
+                 g.n_beams, g.n_sc, n);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            g.det_warps = value_of(it->second, "warps", 2);
+        } else {
+            const int ws[3] = {2, 1, 4};
+            float best = 1e30f;
+            int bw = 2;
+            const float *sg2 = h->cfg.noise_var == PUSCH_NOISE_ESTIMATE ? h->sigma2 : nullptr;
+            for (int w : ws) {
+                g.det_warps = w;
+                const float ms = time_ms(s, reps, [&] {
+                    pusch::launch_mmse(g, n, h->H, h->beam, static_cast<float2 *>(xh), bits, h->status_sink, s, sg2);
+                }, &e);
+                if (e != cudaSuccess) {
+                    st = cuda_fail(e, "autotune detection");
+                    break;
+                }
+                if (ms < best) best = ms, bw = w;
+            }
+            g.det_warps = bw;
+            ++timed;
+            snprintf(buf, sizeof buf, "%s | warps=%d ms=%.5f", key, bw, best);
+            lines.push_back(buf);
+        }
+    }
+    // 4. chunk runs of pusch_slot over the two pipeline streams
+    if (st == PUSCH_OK) {
+        snprintf(key, sizeof key, "slot-pipe form=%d n_rx=%d n_fft=%d n_sc=%d n_beams=%d n_layers=%d slots=%d", g.form,
+                 g.n_rx, g.n_fft, g.n_sc, g.n_beams, g.n_layers, n);
+        auto it = cache.find(key);
+        int best_k = pipeline0;
+        if (it != cache.end()) {
+            best_k = value_of(it->second, "chunks", pipeline0);
+        } else {
+            float best = 1e30f;
+            for (int k : {1, 2, 4}) {
+                if (k > n) break;
+                if (k > 1 && (st = pusch_set_pipeline(h, k)) != PUSCH_OK) break;
+                h->pipeline = k;
+                pusch_status cst = PUSCH_OK;
+                const float ms = time_ms(s, reps, [&] {
+                    if (cst == PUSCH_OK) cst = chain();
+                }, &e);
+                if (cst != PUSCH_OK) {
+                    st = cst;
+                    break;
+                }
+                if (e != cudaSuccess) {
+                    st = cuda_fail(e, "autotune pipeline");
+                    break;
+                }
+                if (ms < best) best = ms, best_k = k;
+            }
+            ++timed;
+            snprintf(buf, sizeof buf, "%s | chunks=%d ms=%.5f", key, best_k, best);
+            lines.push_back(buf);
+        }
+        h->pipeline = pipeline0;
+        if (st == PUSCH_OK) st = pusch_set_pipeline(h, best_k);
+    } else {
+        h->pipeline = pipeline0;
+    }
+    cudaStreamSynchronize(s);
+    cudaFree(time_in);
+    cudaFree(W);
+    cudaFree(pil);
+    cudaFree(xh);
+    cudaFree(bits);
+    if (st != PUSCH_OK) return st;
+    if (!append_cache(cache_path, lines)) return fail(PUSCH_ERR_ARG, "cannot append to the autotune cache file");
+    if (n_timed) *n_timed = timed;
+    return ok();
+}

@@ -26,6 +26,7 @@
 
 #include "chest_common.cuh"
 #include "detect_core.cuh"
+#include "tune_cache.cuh"
 
 namespace {
 
@@ -323,6 +324,8 @@ struct pusch_batch {
 
 namespace {
 
+using namespace pusch::tune;
+
 pusch_status bfail(pusch_status st, const char *fmt, int a = 0, int b = 0, int c = 0) {
     char buf[512];
     snprintf(buf, sizeof buf, fmt, a, b, c);
@@ -451,54 +454,6 @@ std::string graph_key(const pusch_batch *b) {
     char buf[128];
     snprintf(buf, sizeof buf, "graph form=%d n_cells=%d", b->geo[0].form, (int)b->cells.size());
     return buf;
-}
-
-// Cache file: one "<key> | <value>" line per tuned item; later lines override earlier ones.
-std::map<std::string, std::string> read_cache(const char *path) {
-    std::map<std::string, std::string> m;
-    if (!path) return m;
-    FILE *f = fopen(path, "r");
-    if (!f) return m;
-    char line[512];
-    while (fgets(line, sizeof line, f)) {
-        std::string l(line);
-        while (!l.empty() && (l.back() == '\n' || l.back() == '\r')) l.pop_back();
-        const size_t bar = l.find(" | ");
-        if (l.empty() || l[0] == '#' || bar == std::string::npos) continue;
-        m[l.substr(0, bar)] = l.substr(bar + 3);
-    }
-    fclose(f);
-    return m;
-}
-
-int value_of(const std::string &v, const char *name, int dflt) {
-    const std::string pat = std::string(name) + "=";
-    const size_t p = v.find(pat);
-    if (p == std::string::npos) return dflt;
-    return atoi(v.c_str() + p + pat.size());
-}
-
-// Mean milliseconds of `reps` runs of f on stream s (after one warm-up run).
-template <typename F>
-float time_ms(cudaStream_t s, int reps, F &&f, cudaError_t *err) {
-    cudaEvent_t e0, e1;
-    *err = cudaEventCreate(&e0);
-    if (*err != cudaSuccess) return 0.f;
-    if ((*err = cudaEventCreate(&e1)) != cudaSuccess) {
-        cudaEventDestroy(e0);
-        return 0.f;
-    }
-    f();
-    cudaEventRecord(e0, s);
-    for (int r = 0; r < reps; ++r) f();
-    cudaEventRecord(e1, s);
-    *err = cudaEventSynchronize(e1);
-    float ms = 0.f;
-    if (*err == cudaSuccess) *err = cudaEventElapsedTime(&ms, e0, e1);
-    if (*err == cudaSuccess) *err = cudaGetLastError();
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    return ms / reps;
 }
 
 }  // namespace

@@ -530,7 +530,7 @@ fft_kernel(const TIn *__restrict__ in, void *__restrict__ out, const float2 *__r
 
 template <int N, typename TIn, int OUT>
 cudaError_t launch_n(long long rows, const void *in, void *out, const float2 *tw, int n_sc, int pitch, float *scales,
-                     int n_rx, int n_blk, uint32_t *err, const FftIn &fi, cudaStream_t st) {
+                     int n_rx, int n_blk, uint32_t *err, const FftIn &fi, cudaStream_t st, int cap) {
     constexpr int F = ffts_per_cta<N>();
     constexpr size_t smem = fft_smem_bytes<N, TIn>();
     static_assert(smem <= 227 * 1024, "FFT shared memory");
@@ -542,6 +542,7 @@ cudaError_t launch_n(long long rows, const void *in, void *out, const float2 *tw
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kFftThreads, smem);
     if (per_sm < 1) per_sm = 1;
+    if (cap > 0 && per_sm > cap) per_sm = cap;     // tuned CTAs per SM
     const long long blocks = (rows + F - 1) / F;
     long long grid = (long long)sms * per_sm;
     if (grid > blocks) grid = blocks;
@@ -564,13 +565,13 @@ cudaError_t launch_out(const Geometry &g, long long rows, const void *in, void *
     fi.n_rx = g.n_rx;
     fi.slot_len = g.slot_len;
     switch (g.n_fft) {
-        case 4096: return launch_n<4096, TIn, OUT>(rows, in, out, tw, g.n_sc, g.sc_pitch, scales, g.n_rx, n_blk, err, fi, st);
-        case 2048: return launch_n<2048, TIn, OUT>(rows, in, out, tw, g.n_sc, g.sc_pitch, scales, g.n_rx, n_blk, err, fi, st);
-        case 1024: return launch_n<1024, TIn, OUT>(rows, in, out, tw, g.n_sc, g.sc_pitch, scales, g.n_rx, n_blk, err, fi, st);
-        case 512: return launch_n<512, TIn, OUT>(rows, in, out, tw, g.n_sc, g.sc_pitch, scales, g.n_rx, n_blk, err, fi, st);
-        case 256: return launch_n<256, TIn, OUT>(rows, in, out, tw, g.n_sc, g.sc_pitch, scales, g.n_rx, n_blk, err, fi, st);
-        case 128: return launch_n<128, TIn, OUT>(rows, in, out, tw, g.n_sc, g.sc_pitch, scales, g.n_rx, n_blk, err, fi, st);
-        case 64: return launch_n<64, TIn, OUT>(rows, in, out, tw, g.n_sc, g.sc_pitch, scales, g.n_rx, n_blk, err, fi, st);
+        case 4096: return launch_n<4096, TIn, OUT>(rows, in, out, tw, g.n_sc, g.sc_pitch, scales, g.n_rx, n_blk, err, fi, st, g.fft_cap);
+        case 2048: return launch_n<2048, TIn, OUT>(rows, in, out, tw, g.n_sc, g.sc_pitch, scales, g.n_rx, n_blk, err, fi, st, g.fft_cap);
+        case 1024: return launch_n<1024, TIn, OUT>(rows, in, out, tw, g.n_sc, g.sc_pitch, scales, g.n_rx, n_blk, err, fi, st, g.fft_cap);
+        case 512: return launch_n<512, TIn, OUT>(rows, in, out, tw, g.n_sc, g.sc_pitch, scales, g.n_rx, n_blk, err, fi, st, g.fft_cap);
+        case 256: return launch_n<256, TIn, OUT>(rows, in, out, tw, g.n_sc, g.sc_pitch, scales, g.n_rx, n_blk, err, fi, st, g.fft_cap);
+        case 128: return launch_n<128, TIn, OUT>(rows, in, out, tw, g.n_sc, g.sc_pitch, scales, g.n_rx, n_blk, err, fi, st, g.fft_cap);
+        case 64: return launch_n<64, TIn, OUT>(rows, in, out, tw, g.n_sc, g.sc_pitch, scales, g.n_rx, n_blk, err, fi, st, g.fft_cap);
         default: return cudaErrorInvalidValue;
     }
 }

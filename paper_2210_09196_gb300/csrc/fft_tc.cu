@@ -1,37 +1,36 @@
 // OFDM demodulation on the 5th-generation tensor cores (Section II: one FFT per antenna and OFDM symbol;
-// Table I "OFDM dem."): the mixed form's 4096-point FFTs of FP16 time samples, written as three radix-16
-// stages, each a tcgen05 matrix product with a 16-point DFT matrix (FP16 operands, FP32 accumulation in
-// TMEM), with the twiddles between the stages applied in FP32 by the threads that read the accumulators.
+// Table I "OFDM dem."): the mixed form's 4096-point FFTs of FP16 time samples as two 64-point stages, each a
+// tcgen05 product with the 64-point DFT matrix (FP16 operands, FP32 accumulation in TMEM), the twiddles between
+// the stages applied in FP32 by the threads that read the first accumulator.
 //
-// The transform. With n = 256 a + m (m = 16 b + c) and k = k0 + 16 k1 + 256 k2 (all digits in [0, 16)):
-//   stage 1  Y1[m][k0]      = sum_a x[256 a + m] w16^(a k0),            then * W^(m k0)
-//   stage 2  Y2[k0][c][k1]  = sum_b Y1[16 b + c][k0] w16^(b k1),        then * W^(16 c k1)
-//   stage 3  X[k0 + 16 k1 + 256 k2] = sum_c Y2[k0][c][k1] w16^(c k2)
-// with W = exp(-2 pi i / 4096), w16 = W^256. Each stage is D[M][N] = A[M][K] B[N][K]^T with M the
-// independent vectors (tiles of 128 TMEM lanes), K the 16 inputs of a radix-16 butterfly, N its 16 outputs.
+// The transform. With n = 64 a + m and k = k0 + 64 k1 (a, m, k0, k1 in [0, 64)), W = exp(-2 pi i / 4096) and
+// w = W^64:
+//   stage 1  Y[m][k0]   = W^(m k0) sum_a x[64 a + m] w^(a k0)
+//   stage 2  X[k0 + 64 k1] = sum_m Y[m][k0] w^(m k1)
+// Both stages multiply real rows by the same real matrix B[n = 2 k + o][j] = (cos, -sin)(2 pi j k / 64)
+// (N = 128: 64 outputs x (re, im); K = 64): a real row v gives sum_j v_j w^(j k) for every k.
+//   stage 1  A = the row as TMA loads it, read as a [64 a][128 mu] FP16 matrix, mu = 2 m + (re, im): M = mu
+//            (128 real rows), K = a, MN-major with 128-byte swizzling. Row (m, re) gives P_re[k0] =
+//            sum_a Re(x) w^(a k0), row (m, im) gives P_im[k0]; the two lanes of m combine
+//            Y = P_re + i P_im with one exchange per eight values and apply W^(m k0).
+//   stage 2  A2 = Y written by those lanes as real rows: row 2 k0 = Re Y[.][k0], row 2 k0 + 1 = Im Y[.][k0],
+//            K = m, K-major without swizzle, the core-matrix strides padded (144 B along K, 1168 B between
+//            8-row groups) so that every warp-wide 2-byte store hits distinct banks. The lanes of row pair
+//            (2 k0, 2 k0 + 1) combine X = D_re + i D_im the same way and write bins k0 + 64 k1, consecutive
+//            across lanes, into the FP16 output planes.
+// A 4096-point transform thus costs two MMA passes (8 MMAs of 128 x 128 x 16) and one pass of twiddles and
+// transposition through shared memory.
 //
-// Operands (shared memory, no global round trip between the stages):
-//   stage 1  A = the time samples as loaded by TMA: the row of 4096 interleaved complex values read as a
-//            [16 a][512 mu] FP16 matrix, mu = 2 m + (re, im), so M = mu (512 real rows), K = a (16), MN-major
-//            with 128-byte swizzling; B1 = [cos | -sin] of the DFT angles (N = 32: k0 x (re, im)). A real row
-//            gives sum_a Re(x) w^(a k0) or sum_a Im(x) w^(a k0); the two lanes of a subcarrier pair combine
-//            them (Y1 = P_re + i P_im) with one exchange of eight values.
-//   stage 2  A2 = Y1 written by the threads, M = c + 16 k0, K = (b, re/im) (32), MN-major, 128-byte swizzle,
-//            2-byte stores ordered so that a warp's 32 stores hit distinct banks; B2 = the real embedding of the
-//            complex DFT matrix ([[C, S], [-S, C]] per entry).
-//   stage 3  A3 = Y2 written by the threads, M = k0 + 16 k1, K = (c, re/im), K-major without swizzle with the
-//            core-matrix strides padded (160 B along K, 608 B along M) so that the 4-byte complex stores of a
-//            warp are conflict-free; B = B2. The accumulator row of lane M holds bins M + 256 k2, so
-//            consecutive lanes write consecutive bins of the FP16 output planes.
+// Roles (persistent CTAs, four per SM, 128 TMEM columns each): warps 0-3 read the accumulators (warp q owns TMEM
+// lane quarter q) and write the next operand or the output; warp 4 issues the row copies (TMA, a one-stage ring)
+// and the MMAs. They hand over through mbarriers: the MMA commits signal the accumulator, the four reading
+// warps' arrivals signal the second operand and the free accumulator. Every wait is bounded (2 s); on expiry
+// the CTA sets the tensor-core bit (kErrTensorWait) of the error word, every role leaves its loop, the copies
+// and MMAs in flight are drained (bounded) and TMEM is freed.
 //
-// Each CTA (8 warps, three per SM, 128 TMEM columns) transforms its rows one after another; the rows arrive by
-// TMA into a two-stage ring, one MMA-issuing thread drives the stages, and all eight warps read the
-// accumulators (warp w owns TMEM lane quarter w % 4). Every wait is bounded (2 s); on expiry the CTA sets the
-// tensor-core bit (kErrTensorWait) of the error word, drains its copies and MMAs (bounded) and frees its TMEM.
-//
-// Error: the operands of every stage are FP16 (the input exactly, the two intermediates and the DFT matrices
-// rounded to nearest), so the output carries about 2^-11 relative error per stage (-60 dB or better against
-// the exact transform; measured against the FP64 oracle in the tests), well under the chain's -40 dB gate.
+// Error: the input enters the first product exactly; the intermediate Y and the DFT matrix are rounded to FP16
+// (round to nearest) and the output is stored as FP16, so the transform carries about 2^-11 relative error
+// (measured against the FP64 oracle in the tests), far under the chain's -40 dB gate.
 #include "tc_common.cuh"
 
 namespace pusch {
@@ -40,19 +39,18 @@ namespace {
 using namespace tc;
 
 constexpr int kN = 4096;
-constexpr int kThreads = 256;
-constexpr int kCtasPerSm = 3;
+constexpr int kEpiWarps = 4;
+constexpr int kThreads = 32 * (kEpiWarps + 1);
+constexpr int kCtasPerSm = 4;
 constexpr int kTmemCols = 128;
-constexpr int kStages = 2;
+constexpr int kStages = 1;
 
 constexpr uint32_t kRowBytes = kN * 4;                      // one row of FP16 complex samples: 16 KB
-constexpr uint32_t kOffIn = 0;                              // input ring (stage-1 A operands)
-constexpr uint32_t kOffA2 = kOffIn + kStages * kRowBytes;   // 16 KB, 1024-aligned
-constexpr uint32_t kA3Lbo = 160, kA3Sbo = 608;              // padded K-major strides of A3
-constexpr uint32_t kOffA3 = kOffA2 + 16384;                 // 32 row groups x 608 B
-constexpr uint32_t kOffB1 = kOffA3 + 32 * kA3Sbo;           // [32][16] FP16, K-major
-constexpr uint32_t kOffB2 = kOffB1 + 1024;                  // [32][32] FP16, K-major
-constexpr uint32_t kSmemUsed = kOffB2 + 2048;
+constexpr uint32_t kOffIn = 0;                              // input ring (stage-1 A operands, 1024-aligned)
+constexpr uint32_t kOffB = kOffIn + kStages * kRowBytes;    // B: [128][64] FP16, K-major, 16 KB
+constexpr uint32_t kA2Lbo = 144, kA2Sbo = 1168;             // padded K-major strides of A2
+constexpr uint32_t kOffA2 = kOffB + 16384;                  // 16 row groups x 1168 B
+constexpr uint32_t kSmemUsed = kOffA2 + 16 * kA2Sbo;
 constexpr size_t kSmemBytes = kSmemUsed + 1024;             // + alignment of the base to 1024 B
 
 __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
@@ -69,22 +67,25 @@ __device__ __forceinline__ uint32_t kmajor_off(int n, int k, uint32_t lbo, uint3
     return (uint32_t)(n >> 3) * sbo + (uint32_t)(k >> 3) * lbo + (uint32_t)(n & 7) * 16u + (uint32_t)(k & 7) * 2u;
 }
 
-// A2 (MN-major, 128-byte swizzle, 1024-aligned atoms): element (row M, K row kr), the 64-row halves 4 KB apart.
-__device__ __forceinline__ uint32_t a2_off(int M, int kr) {
-    return (uint32_t)(M >> 6) * 4096u + (uint32_t)kr * 128u + ((uint32_t)(((M & 63) >> 3) ^ (kr & 7)) << 4) +
-           (uint32_t)(M & 7) * 2u;
+// Bounded wait by one lane of the warp, the result broadcast to the warp.
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int *abort, uint32_t *err, int lane) {
+    bool ok = true;
+    if (lane == 0) ok = mbar_wait_sleep(bar, parity, abort, err, 32);
+    return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
 }
 
-// p[i] = w^i for i < 8 (p[0] = 1), by at most three products deep (w^2, w^4 and the rest from them).
-__device__ __forceinline__ void powers8(float2 w, float2 (&p)[8]) {
-    p[0] = make_float2(1.f, 0.f);
-    p[1] = w;
-    p[2] = cmul(w, w);
-    p[3] = cmul(p[2], w);
-    p[4] = cmul(p[2], p[2]);
-    p[5] = cmul(p[4], w);
-    p[6] = cmul(p[4], p[2]);
-    p[7] = cmul(p[4], p[3]);
+// The 16 complex values of one 32-column accumulator chunk of a real row, combined with the partner row's
+// (lane ^ 1): lane 2 j (the row of real parts) returns V[i] = D_re[i] + i D_im[i] for the chunk's outputs
+// 0..7, lane 2 j + 1 (imaginary parts) returns them for outputs 8..15.
+__device__ __forceinline__ void combine_pair(const uint32_t (&r)[32], int odd, float2 (&V)[8]) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const float2 lo = make_float2(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
+        const float2 hi = make_float2(__uint_as_float(r[2 * i + 16]), __uint_as_float(r[2 * i + 17]));
+        const float2 own = odd ? hi : lo, snd = odd ? lo : hi;
+        const float2 rcv = make_float2(__shfl_xor_sync(0xffffffffu, snd.x, 1), __shfl_xor_sync(0xffffffffu, snd.y, 1));
+        V[i] = odd ? make_float2(rcv.x - own.y, rcv.y + own.x) : make_float2(own.x - rcv.y, own.y + rcv.x);
+    }
 }
 
 struct FftTcArgs {
@@ -97,7 +98,8 @@ fft_tc_kernel(const __grid_constant__ CUtensorMap tin, __half *__restrict__ out,
               FftTcArgs g, uint32_t *__restrict__ err) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t bar_full[kStages];
-    __shared__ __align__(8) uint64_t bar_mma;
+    __shared__ __align__(8) uint64_t bar_acc;     // MMA commits: the accumulator holds a finished product
+    __shared__ __align__(8) uint64_t bar_op;      // 4 warp arrivals: A2 written / the accumulator read out
     __shared__ __align__(8) uint64_t bar_drain;
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
@@ -106,36 +108,31 @@ fft_tc_kernel(const __grid_constant__ CUtensorMap tin, __half *__restrict__ out,
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t *gbase = smem_raw + (base - raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int q = warp & 3;     // TMEM lane quarter of this warp
-    const int wh = warp >> 2;   // which of the two warps of that quarter
     volatile int *abort = &s_abort;
-    uint32_t *errw = err;
 
-    // ---------------------------------------------------------------- B operands (resident)
-    for (int e = tid; e < 32 * 16; e += kThreads) {          // B1[n = 2 k0 + o][a]
-        const int n = e >> 4, a = e & 15, k0 = n >> 1;
-        float s, c;
-        sincospif((float)((a * k0) & 15) / 8.f, &s, &c);       // angle 2 pi a k0 / 16
-        *reinterpret_cast<__half *>(gbase + kOffB1 + kmajor_off(n, a, 128, 256)) = __float2half_rn((n & 1) ? -s : c);
-    }
-    for (int e = tid; e < 32 * 32; e += kThreads) {          // B2[n = 2 k1 + o][k = 2 b + i]
-        const int n = e >> 5, k = e & 31, k1 = n >> 1, b = k >> 1;
-        float s, c;
-        sincospif((float)((b * k1) & 15) / 8.f, &s, &c);
-        const int o = n & 1, i = k & 1;
-        const float v = (o == i) ? c : (o == 0 ? s : -s);
-        *reinterpret_cast<__half *>(gbase + kOffB2 + kmajor_off(n, k, 128, 512)) = __float2half_rn(v);
+    // ---------------------------------------------------------------- B (resident): (cos, -sin)(2 pi j k / 64)
+    // from the twiddle table (w^(j k) = W^(64 (j k mod 64))), eight K values (one 16-byte core-matrix row) per
+    // thread and store
+    for (int e = tid; e < 128 * 8; e += kThreads) {
+        const int n = e >> 3, j0 = (e & 7) * 8, k = n >> 1;
+        __align__(16) __half v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const float2 w = __ldg(&tw[64 * (((j0 + u) * k) & 63)]);
+            v[u] = __float2half_rn((n & 1) ? w.y : w.x);     // Im W^q = -sin
+        }
+        *reinterpret_cast<uint4 *>(gbase + kOffB + kmajor_off(n, j0, 128, 1024)) = *reinterpret_cast<const uint4 *>(v);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) mbar_init(smem_u32(&bar_full[s]), 1);
-        mbar_init(smem_u32(&bar_mma), 1);
+        mbar_init(smem_u32(&bar_acc), 1);
+        mbar_init(smem_u32(&bar_op), kEpiWarps);
         mbar_init(smem_u32(&bar_drain), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_abort = 0;
     }
-    if (warp == 0) {
+    if (warp == kEpiWarps) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
                      "r"(kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -144,170 +141,133 @@ fft_tc_kernel(const __grid_constant__ CUtensorMap tin, __half *__restrict__ out,
     __syncthreads();
     fence_after_sync();
     const uint32_t tmem = s_tmem;
-
     const long long n_my = g.rows > blockIdx.x ? (g.rows - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
-    auto issue = [&](long long it) {       // thread 0: the 8 boxes of row `it` into ring stage it % 2
-        const int s = (int)(it & 1);
-        const long long row = blockIdx.x + it * gridDim.x;
-        const uint32_t bar = smem_u32(&bar_full[s]);
-        mbar_expect_tx(bar, kRowBytes);
-        for (int bx = 0; bx < 8; ++bx)
-            tma_load_2d(base + kOffIn + (uint32_t)s * kRowBytes + (uint32_t)bx * 2048u, &tin, 64 * bx, (int)(row * 16),
-                        bar);
-    };
-    long long issued = 0;
-    if (tid == 0)
-        for (; issued < kStages && issued < n_my; ++issued) issue(issued);
 
-    const int h = g.n_sc >> 1;
-    const uint32_t id_mn = idesc_f16(128, 32, true, false), id_k = idesc_f16(128, 32, false, false);
-    const uint32_t tq = tmem + ((uint32_t)(32 * q) << 16);
-    uint32_t mma_phase = 0;
-    long long it = 0;
-    for (; it < n_my; ++it) {
-        const int s = (int)(it & 1);
-        const long long row = blockIdx.x + it * gridDim.x;
-
-        // ------------------------------------------------------------ stage 1: 4 MMAs (M tiles of mu)
-        if (tid == 0 && mbar_wait(smem_u32(&bar_full[s]), (uint32_t)((it >> 1) & 1), abort, errw)) {
-            fence_after_sync();
-            const uint64_t bd = smem_desc(base + kOffB1, 128, 256, 0);
-            for (int t = 0; t < 4; ++t)
-                mma_f16(tmem + 32u * t, smem_desc(base + kOffIn + (uint32_t)s * kRowBytes + (uint32_t)t * 4096u, 2048, 1024, 2),
-                        bd, id_mn, 0u);
-            mma_commit(smem_u32(&bar_mma));
+    if (warp == kEpiWarps) {
+        // ------------------------------------------------------------ control: row copies and MMAs
+        if (lane == 0) {
+            const uint32_t idesc1 = idesc_f16(128, 128, true, false), idesc2 = idesc_f16(128, 128, false, false);
+            auto issue = [&](long long i) {
+                const int s = (int)(i % kStages);
+                const long long row = blockIdx.x + i * gridDim.x;
+                const uint32_t bar = smem_u32(&bar_full[s]);
+                mbar_expect_tx(bar, kRowBytes);
+                for (int h = 0; h < 2; ++h)
+                    tma_load_2d(base + kOffIn + (uint32_t)s * kRowBytes + (uint32_t)h * 8192u, &tin, 64 * h,
+                                (int)(row * 64), bar);
+            };
+            long long issued = 0;
+            for (; issued < kStages && issued < n_my; ++issued) issue(issued);
+            uint32_t op_phase = 0;
+            long long it = 0;
+            bool ok = true;
+            for (; it < n_my && ok; ++it) {
+                const int s = (int)(it % kStages);
+                ok = mbar_wait_sleep(smem_u32(&bar_full[s]), (uint32_t)((it / kStages) & 1), abort, err, 64);
+                if (ok && it > 0) {   // the reading warps have emptied the accumulator of row it - 1
+                    ok = mbar_wait_sleep(smem_u32(&bar_op), op_phase, abort, err, 128);
+                    op_phase ^= 1u;
+                }
+                if (!ok) break;
+                fence_after_sync();
+                const uint32_t a0 = base + kOffIn + (uint32_t)s * kRowBytes;
+                for (int ks = 0; ks < 4; ++ks)
+                    mma_f16(tmem, smem_desc(a0 + (uint32_t)ks * 2048u, 8192, 1024, 2),
+                            smem_desc(base + kOffB + (uint32_t)ks * 256u, 128, 1024, 0), idesc1, ks > 0 ? 1u : 0u);
+                mma_commit(smem_u32(&bar_acc));
+                // the stage-1 products have read the row: its ring slot takes a later row
+                ok = mbar_wait_sleep(smem_u32(&bar_acc), 0u, abort, err, 32);
+                if (!ok) break;
+                if (issued < n_my) issue(issued++);
+                ok = mbar_wait_sleep(smem_u32(&bar_op), op_phase, abort, err, 128);   // A2 written
+                op_phase ^= 1u;
+                if (!ok) break;
+                fence_after_sync();
+                for (int ks = 0; ks < 4; ++ks)
+                    mma_f16(tmem, smem_desc(base + kOffA2 + (uint32_t)ks * 2u * kA2Lbo, kA2Lbo, kA2Sbo, 0),
+                            smem_desc(base + kOffB + (uint32_t)ks * 256u, 128, 1024, 0), idesc2, ks > 0 ? 1u : 0u);
+                mma_commit(smem_u32(&bar_acc));
+            }
+            if (ok && n_my > 0) mbar_wait_sleep(smem_u32(&bar_op), op_phase, abort, err, 128);   // the last row read out
+            if (*abort) {
+                // drain: the row copies still in flight and every MMA issued (bounded waits)
+                for (long long j = it; j < issued; ++j)
+                    mbar_drain(smem_u32(&bar_full[(int)(j % kStages)]), (uint32_t)((j / kStages) & 1));
+                mma_commit(smem_u32(&bar_drain));
+                mbar_drain(smem_u32(&bar_drain), 0);
+            }
         }
-        // one thread polls the MMA barrier (bounded); the others wait at the CTA barrier without issuing
-        bool ok = tid != 0 || mbar_wait(smem_u32(&bar_mma), mma_phase, abort, errw);
-        if (__syncthreads_or(!ok)) break;
-        mma_phase ^= 1u;
-        fence_after_sync();
-        if (tid == 0 && issued < n_my && issued == it + kStages) issue(issued++);   // stage s is free again
-
-        // ------------------------------------------------------------ epilogue 1 -> A2
-        {
-            const int ri = lane & 1, c = lane >> 1;
+    } else {
+        // ------------------------------------------------------------ accumulator readers (warp q = lane quarter)
+        const int q = warp, odd = lane & 1, j = 16 * q + (lane >> 1);   // stage 1: m = j; stage 2: k0 = j
+        const uint32_t tq = tmem + ((uint32_t)(32 * q) << 16);
+        // twiddles W^(m k0), k0 = 16 c + 8 odd + i: W^(m (16 c + 8 odd)) * W^(m i), from exact table entries
+        float2 pw[8], bs[4];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) pw[i] = __ldg(&tw[j * i]);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) bs[c] = __ldg(&tw[j * (16 * c + 8 * odd)]);
+        const int h = g.n_sc >> 1;
+        uint32_t acc_phase = 0;
+        for (long long it = 0; it < n_my; ++it) {
+            const long long row = blockIdx.x + it * gridDim.x;
+            // ---- stage-1 accumulator -> A2 (twiddled, transposed, FP16)
+            if (!warp_wait(smem_u32(&bar_acc), acc_phase, abort, err, lane)) break;
+            acc_phase ^= 1u;
+            fence_after_sync();
 #pragma unroll 1
-            for (int u = 0; u < 2; ++u) {
-                const int t = wh + 2 * u;
+            for (int c = 0; c < 4; ++c) {
                 uint32_t r[32];
-                tmem_ld32(tq + 32u * t, r);
-                const int m = 64 * t + 16 * q + c, b = 4 * t + q;
-                // twiddles W^(m k0), k0 = 8 ri + i: W^(8 ri m) times the powers W^(m i), from two table entries
-                float2 pw[8];
-                powers8(__ldg(&tw[m]), pw);
-                const float2 base8 = ri ? __ldg(&tw[(8 * m) & (kN - 1)]) : make_float2(1.f, 0.f);
+                tmem_ld32(tq + 32u * c, r);
                 float2 Y[8];
+                combine_pair(r, odd, Y);
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
-                    const float2 lo = make_float2(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
-                    const float2 hi = make_float2(__uint_as_float(r[2 * i + 16]), __uint_as_float(r[2 * i + 17]));
-                    const float2 own = ri ? hi : lo, snd = ri ? lo : hi;
-                    const float2 rcv = make_float2(__shfl_xor_sync(0xffffffffu, snd.x, 1),
-                                                   __shfl_xor_sync(0xffffffffu, snd.y, 1));
-                    // Y1 = P_re + i P_im: lane ri = 0 holds P_re (k0 = i), lane ri = 1 holds P_im (k0 = 8 + i)
-                    Y[i] = ri ? make_float2(rcv.x - own.y, rcv.y + own.x) : make_float2(own.x - rcv.y, own.y + rcv.x);
-                    Y[i] = cmul(Y[i], ri ? cmul(base8, pw[i]) : pw[i]);
-                }
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    // store order: lanes ri = 1 take element j ^ 2, so that the two lane halves hit distinct banks
-                    const float2 y = ri ? Y[j ^ 2] : Y[j];
-                    const int M = c + 16 * (ri ? 8 + (j ^ 2) : j);
+                    const float2 y = cmul(cmul(Y[i], pw[i]), bs[c]);
+                    const int k0 = 16 * c + 8 * odd + i;
                     const __half2 v = __floats2half2_rn(y.x, y.y);
-                    *reinterpret_cast<__half *>(gbase + kOffA2 + a2_off(M, 2 * b)) = __low2half(v);
-                    *reinterpret_cast<__half *>(gbase + kOffA2 + a2_off(M, 2 * b + 1)) = __high2half(v);
+                    *reinterpret_cast<__half *>(gbase + kOffA2 + kmajor_off(2 * k0, j, kA2Lbo, kA2Sbo)) = __low2half(v);
+                    *reinterpret_cast<__half *>(gbase + kOffA2 + kmajor_off(2 * k0 + 1, j, kA2Lbo, kA2Sbo)) = __high2half(v);
                 }
             }
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        fence_before_sync();
-        __syncthreads();
-
-        // ------------------------------------------------------------ stage 2: 2 M tiles x 2 K steps
-        if (tid == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            fence_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&bar_op));
+            // ---- stage-2 accumulator -> output planes
+            if (!warp_wait(smem_u32(&bar_acc), acc_phase, abort, err, lane)) break;
+            acc_phase ^= 1u;
             fence_after_sync();
-            for (int t = 0; t < 2; ++t)
-                for (int ks = 0; ks < 2; ++ks)
-                    mma_f16(tmem + 32u * t, smem_desc(base + kOffA2 + (uint32_t)t * 8192u + (uint32_t)ks * 2048u, 4096, 1024, 2),
-                            smem_desc(base + kOffB2 + (uint32_t)ks * 256u, 128, 512, 0), id_mn, ks > 0 ? 1u : 0u);
-            mma_commit(smem_u32(&bar_mma));
-        }
-        ok = tid != 0 || mbar_wait(smem_u32(&bar_mma), mma_phase, abort, errw);
-        if (__syncthreads_or(!ok)) break;
-        mma_phase ^= 1u;
-        fence_after_sync();
-
-        // ------------------------------------------------------------ epilogue 2 -> A3
-        {
-            const int M2 = 128 * wh + 32 * q + lane, c = M2 & 15, k0 = M2 >> 4;
-            // twiddles W^(16 c k1) = v^k1, v = W^(16 c): the powers below 8, then v^8 times them
-            float2 pv[8];
-            powers8(__ldg(&tw[16 * c]), pv);
-            const float2 v8 = cmul(pv[4], pv[4]);
-            uint32_t r[32];
-            tmem_ld32(tq + 32u * wh, r);
-#pragma unroll
-            for (int k1 = 0; k1 < 16; ++k1) {
-                float2 z = make_float2(__uint_as_float(r[2 * k1]), __uint_as_float(r[2 * k1 + 1]));
-                z = cmul(z, k1 < 8 ? pv[k1] : cmul(v8, pv[k1 - 8]));
-                const __half2 v = __floats2half2_rn(z.x, z.y);
-                *reinterpret_cast<__half2 *>(gbase + kOffA3 + kmajor_off(k0 + 16 * k1, 2 * c, kA3Lbo, kA3Sbo)) = v;
-            }
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        fence_before_sync();
-        __syncthreads();
-
-        // ------------------------------------------------------------ stage 3: 2 M tiles x 2 K steps
-        if (tid == 0) {
-            fence_after_sync();
-            for (int t = 0; t < 2; ++t)
-                for (int ks = 0; ks < 2; ++ks)
-                    mma_f16(tmem + 32u * t,
-                            smem_desc(base + kOffA3 + (uint32_t)t * 16u * kA3Sbo + (uint32_t)ks * 2u * kA3Lbo, kA3Lbo, kA3Sbo, 0),
-                            smem_desc(base + kOffB2 + (uint32_t)ks * 256u, 128, 512, 0), id_k, ks > 0 ? 1u : 0u);
-            mma_commit(smem_u32(&bar_mma));
-        }
-        ok = tid != 0 || mbar_wait(smem_u32(&bar_mma), mma_phase, abort, errw);
-        if (__syncthreads_or(!ok)) break;
-        mma_phase ^= 1u;
-        fence_after_sync();
-
-        // ------------------------------------------------------------ epilogue 3 -> FP16 planes
-        {
-            const int M3 = 128 * wh + 32 * q + lane;
-            uint32_t r[32];
-            tmem_ld32(tq + 32u * wh, r);
             __half *o = out + row * 2 * (long long)g.pitch;
+#pragma unroll 1
+            for (int c = 0; c < 4; ++c) {
+                uint32_t r[32];
+                tmem_ld32(tq + 32u * c, r);
+                float2 X[8];
+                combine_pair(r, odd, X);
 #pragma unroll
-            for (int k2 = 0; k2 < 16; ++k2) {
-                const int a = (M3 + 256 * k2 + h) & (kN - 1);
-                if (a < g.n_sc) {
-                    const __half2 v = __floats2half2_rn(__uint_as_float(r[2 * k2]), __uint_as_float(r[2 * k2 + 1]));
-                    o[a] = __low2half(v);
-                    o[g.pitch + a] = __high2half(v);
+                for (int i = 0; i < 8; ++i) {
+                    const int a = (j + 64 * (16 * c + 8 * odd + i) + h) & (kN - 1);
+                    if (a < g.n_sc) {
+                        const __half2 v = __floats2half2_rn(X[i].x, X[i].y);
+                        o[a] = __low2half(v);
+                        o[g.pitch + a] = __high2half(v);
+                    }
                 }
             }
-            for (int a = g.n_sc + tid; a < g.pitch; a += kThreads) {
+            for (int a = g.n_sc + tid; a < g.pitch; a += 32 * kEpiWarps) {
                 o[a] = __float2half_rn(0.f);
                 o[g.pitch + a] = __float2half_rn(0.f);
             }
+            fence_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&bar_op));
         }
-        fence_before_sync();
-        __syncthreads();     // the TMEM columns and A2 / A3 are free for the next row
     }
 
-    if (*abort && tid == 0) {
-        // drain: the row copies still in flight and every MMA issued (bounded waits)
-        for (long long j = it; j < issued; ++j)
-            mbar_drain(smem_u32(&bar_full[(int)(j & 1)]), (uint32_t)((j >> 1) & 1));
-        mma_commit(smem_u32(&bar_drain));
-        mbar_drain(smem_u32(&bar_drain), 0);
-    }
     fence_before_sync();
     __syncthreads();
-    if (warp == 0) {
+    if (warp == kEpiWarps) {
         fence_after_sync();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
     }
@@ -323,13 +283,13 @@ cudaError_t launch_fft_tc(const Geometry &g, long long rows, const void *in, voi
                           uint32_t *err, cudaStream_t st) {
     if (!fft_tc_supported(g)) return cudaErrorNotSupported;
     if (rows == 0) return cudaSuccess;
-    if (rows * 16 > 0x7fffffffLL) return cudaErrorInvalidValue;     // TMA row coordinate is 32-bit
+    if (rows * 64 > 0x7fffffffLL) return cudaErrorInvalidValue;     // TMA row coordinate is 32-bit
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
     CUtensorMap map;
-    cuuint64_t dims[2] = {512, (cuuint64_t)(rows * 16)};
-    cuuint64_t strides[1] = {1024};
-    cuuint32_t box[2] = {64, 16};
+    cuuint64_t dims[2] = {128, (cuuint64_t)(rows * 64)};          // [rows * 64 a][128 mu] FP16
+    cuuint64_t strides[1] = {256};
+    cuuint32_t box[2] = {64, 64};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void *>(in), dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -340,9 +300,9 @@ cudaError_t launch_fft_tc(const Geometry &g, long long rows, const void *in, voi
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    // kCtasPerSm resident CTAs per SM (shared memory and registers allow three; 3 x 128 TMEM columns fit in
-    // 512). The CTAs are independent, so a CTA that cannot be resident at once simply runs later.
-    long long grid = (long long)sms * kCtasPerSm;
+    // kCtasPerSm resident CTAs per SM (4 x 52 KB of shared memory; 4 x 128 TMEM columns = 512). The CTAs are
+    // independent, so a CTA that cannot be resident at once simply runs later.
+    long long grid = (long long)sms * (g.fft_cap > 0 && g.fft_cap < kCtasPerSm ? g.fft_cap : kCtasPerSm);
     if (grid > rows) grid = rows;
     FftTcArgs a;
     a.rows = rows;

@@ -58,6 +58,9 @@ struct Geometry {
     long long slot_len;           // samples of one antenna's slot (cp == 1)
     int shift;                    // 1: undo the 7.5 kHz shift before the FFT
     int dmrs_type;                // 1: 3GPP type-1 DMRS; comb / port then give the CDM pair centres (4, 1 + group)
+    // launch shapes (pusch_autotune; 0 = the built-in choice)
+    int fft_cap;                  // FFT CTAs per SM at most
+    int det_warps;                // warps per CTA of the 12-data-symbol detector (1, 2 or 4)
 };
 
 // Complex time samples of one slot's input.
@@ -128,6 +131,7 @@ cudaError_t launch_chest_time(const Geometry &g, int n_slots, const float2 *beam
 // sigma2 (optional, device, one float per slot): per-slot noise variance replacing g.noise_var.
 // time_groups: H holds g.n_groups estimates (launch_chest_time) and each group of g.chol_every data symbols
 // is detected with its own.
+// The 12-data-symbol kernels run g.det_warps warps per CTA (1, 2 or 4; anything else = 2).
 cudaError_t launch_mmse(const Geometry &g, int n_slots, const float2 *H, const float2 *beam, float2 *x_hat,
                         uint8_t *bits, uint32_t *status, cudaStream_t st, const float *sigma2 = nullptr,
                         bool time_groups = false);
@@ -232,4 +236,6 @@ struct pusch_handle {
     float *cnn_scale = nullptr;     // [grids]
     void *cnn_acts = nullptr;       // [3][grids][32][2][n_sc] bf16
     float *cnn_y = nullptr;         // [grids][2][2][n_sc]
+    // launch shapes chosen by pusch_autotune (the FFT cap and detector warps live in geo)
+    pusch::TcTune bf_tune;
 };

@@ -7,6 +7,7 @@ namespace pusch {
 cudaError_t launch_mmse(const Geometry &g, int n_slots, const float2 *H, const float2 *beam, float2 *x_hat,
                         uint8_t *bits, uint32_t *status, cudaStream_t st, const float *sigma2, bool time_groups) {
     mmse_detail::MmseArgs a;
+    a.warps = (g.det_warps == 1 || g.det_warps == 4) ? g.det_warps : 2;
     a.n_sc = g.n_sc;
     a.n_beams = g.n_beams;
     a.n_layers = g.n_layers;

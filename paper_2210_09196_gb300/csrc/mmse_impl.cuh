@@ -36,6 +36,7 @@ struct MmseArgs {
     const float *sigma2;       // per-slot noise variance (device) or nullptr
     int d_first, n_det;        // this launch detects data symbols d_first .. d_first + n_det - 1 (n_data in all)
     int dmrs_lo, dmrs_hi;      // the two DMRS symbols, dmrs_lo < dmrs_hi
+    int warps;                 // warps per CTA of the 12-symbol kernels: 1, 2 (default) or 4
 };
 
 // Symbol index of data symbol d: the data symbols are all other symbols of the slot in increasing order.
@@ -84,10 +85,15 @@ __device__ __forceinline__ void stage_H(float2 *Ht, const float2 *__restrict__ H
     cp_async_wait_all();  // the H tile (and the earlier y group)
 }
 
-// Register cap: five CTAs per SM up to 8 layers, seven for 16 layers (128 registers: the shared-memory
-// limit is also seven), none for 32.
-template <int NL, int ND>
-__global__ void __launch_bounds__(kMmseWarps * 32, NL <= 8 ? 5 : (NL == 16 ? 7 : 1))
+// Register cap: 10 warps per SM up to 8 layers, 14 for 16 layers (128 registers: the shared-memory limit is
+// also 14 warps of two subcarriers), none for 32; the CTA holds WARPS warps (1, 2 or 4; 2 unless tuned).
+template <int NL, int WARPS>
+constexpr int mmse_min_ctas() {
+    constexpr int w = NL <= 8 ? 10 : (NL == 16 ? 14 : WARPS);
+    return (w + WARPS - 1) / WARPS;
+}
+template <int NL, int ND, int WARPS = kMmseWarps>
+__global__ void __launch_bounds__(WARPS * 32, mmse_min_ctas<NL, WARPS>())
 mmse_kernel(MmseArgs g, long long total_sc, const float2 *__restrict__ H, const float2 *__restrict__ beam,
             float2 *__restrict__ xhat, uint8_t *__restrict__ bits, uint32_t *__restrict__ status) {
     constexpr int SPW = 32 / NL;
@@ -104,7 +110,7 @@ mmse_kernel(MmseArgs g, long long total_sc, const float2 *__restrict__ H, const 
     float2 *Ht = reinterpret_cast<float2 *>(wbase);  // [SPW][ht]
     float2 *Yt = Ht + SPW * ht;                      // [SPW][nd][ys]
 
-    const long long sc0 = ((long long)blockIdx.x * kMmseWarps + warp) * SPW;  // first (slot*n_sc + a) of warp
+    const long long sc0 = ((long long)blockIdx.x * WARPS + warp) * SPW;  // first (slot*n_sc + a) of warp
     if (sc0 >= total_sc) return;                                              // whole warp idle
     const long long my_sc = sc0 + grp;
     const bool valid = my_sc < total_sc;
@@ -176,28 +182,30 @@ mmse_kernel(MmseArgs g, long long total_sc, const float2 *__restrict__ H, const 
     if (__any_sync(kFull, nonfinite) && lane == 0) atomicOr(&status[0], (unsigned)PUSCH_STATUS_NONFINITE);
 }
 
-template <int NL, int ND>
+template <int NL, int ND, int WARPS = kMmseWarps>
 cudaError_t launch_nl(const MmseArgs &a, long long total_sc, const float2 *H, const float2 *beam, float2 *xhat,
                       uint8_t *bits, uint32_t *status, cudaStream_t st) {
     constexpr int SPW = 32 / NL;
-    const size_t smem = (size_t)kMmseWarps * warp_smem_bytes<NL>(a.n_beams, ND > 0 ? ND : a.n_det);
-    const long long per_cta = (long long)kMmseWarps * SPW;
+    const size_t smem = (size_t)WARPS * warp_smem_bytes<NL>(a.n_beams, ND > 0 ? ND : a.n_det);
+    const long long per_cta = (long long)WARPS * SPW;
     const long long grid = (total_sc + per_cta - 1) / per_cta;
     if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    auto k = mmse_kernel<NL, ND>;
+    auto k = mmse_kernel<NL, ND, WARPS>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k<<<(unsigned)grid, kMmseWarps * 32, smem, st>>>(a, total_sc, H, beam, xhat, bits, status);
+    k<<<(unsigned)grid, WARPS * 32, smem, st>>>(a, total_sc, H, beam, xhat, bits, status);
     return cudaGetLastError();
 }
 
-// Compiled-in symbol counts: 12 (one estimate per slot), 4 and 1 (Section VI's schedules, one factorisation per
-// 4 data symbols or per symbol); anything else at run time.
+// Compiled-in symbol counts: 12 (one estimate per slot; 1, 2 or 4 warps per CTA, a.warps), 4 and 1
+// (Section VI's schedules, one factorisation per 4 data symbols or per symbol); anything else at run time.
 template <int NL>
 cudaError_t launch_nd(const MmseArgs &a, long long total_sc, const float2 *H, const float2 *beam, float2 *xhat,
                       uint8_t *bits, uint32_t *status, cudaStream_t st) {
+    if (a.n_det == 12 && a.warps == 1) return launch_nl<NL, 12, 1>(a, total_sc, H, beam, xhat, bits, status, st);
+    if (a.n_det == 12 && a.warps == 4) return launch_nl<NL, 12, 4>(a, total_sc, H, beam, xhat, bits, status, st);
     if (a.n_det == 12) return launch_nl<NL, 12>(a, total_sc, H, beam, xhat, bits, status, st);
     if (a.n_det == 4) return launch_nl<NL, 4>(a, total_sc, H, beam, xhat, bits, status, st);
     if (a.n_det == 1) return launch_nl<NL, 1>(a, total_sc, H, beam, xhat, bits, status, st);

@@ -180,3 +180,8 @@ def test_noalloc_refuses_the_time_varying_estimate_on_the_host(B):
     rc = B.lib().pusch_slot_noalloc(ctypes.byref(cfg), 1, 16, 16, 16, 16, 16, None, None)
     assert rc == B.PUSCH_ERR_UNSUPPORTED
     assert "chol_every" in B.pusch_last_error()
+
+
+def test_autotune_rejects_a_null_handle(B):
+    n = ctypes.c_int(7)
+    assert B.lib().pusch_autotune(None, None, None, ctypes.byref(n)) == B.PUSCH_ERR_ARG
