@@ -4,14 +4,15 @@
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--slots B]
                 [--form auto|mixed|fp32|fp8] [--workload deploy|massive|small] [--pipeline P] [--e2e-pipeline Q]
-                [--no-cpu-baseline] [--no-e2e] [--no-ragged] [--no-massive]
+                [--no-cpu-baseline] [--no-e2e] [--no-ragged] [--no-massive] [--no-denoiser]
 
 A step is one pusch_slot call: the whole chain over a batch of B distinct synthetic slots already resident in
 HBM (B = 16 -> 235 MB of FP16 time samples per step, more than the 129 MB L2, so every step streams from HBM),
 run as P chunk runs over two streams (pusch_set_pipeline; P = 2 by default). Beside the headline the line
 carries the same form with one pass per call, the plain FP32 form, the end-to-end rate through
 pusch_slot_host (host buffers, copies timed), the CPU baseline (the FP64 oracle on every host core and on one),
-the ragged multi-cell batch and the massive-MIMO stream in all three forms. Rank 0 prints one JSON line;
+the ragged multi-cell batch, the massive-MIMO stream in all three forms and the learned channel estimator
+(inference time, post-MMSE EVM gain over LS per SNR). Rank 0 prints one JSON line;
 under torchrun every rank runs a replica and the step time is the max over ranks. --impl reference times the
 FP64 CPU oracle on the host cores instead.
 """
@@ -50,6 +51,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-ragged", action="store_true")
     ap.add_argument("--no-massive", action="store_true")
+    ap.add_argument("--no-denoiser", action="store_true")
     return ap.parse_args()
 
 
@@ -356,6 +358,7 @@ def run_ours(args, rank, world, local):
                            f"{sorted(tune)} over 8 untimed calls each)"}
 
     ragged = None if args.no_ragged else run_ragged(world)
+    denoise = None if args.no_denoiser else run_denoiser(world, evm=not args.no_cpu_baseline)
     massive = None if args.no_massive else run_massive(world, oracle_check=not args.no_cpu_baseline and world == 1)
 
     if rank != 0:
@@ -429,6 +432,7 @@ def run_ours(args, rank, world, local):
         "cpu_baseline": cpu,
         "quality_vs_fp64": quality,
         "ragged_batch": ragged,
+        "learned_estimator": denoise,
         "massive_stream": massive,
         "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps,
@@ -487,6 +491,61 @@ def run_ragged(world, reps=50):
            "autotune": {"keys_timed": n_timed, "seconds": round(tune_s, 2), "choice": rx.tuning()},
            "device_status": [int(v) & 0xffffffff for v in out[2].cpu().numpy()]}
     rx.close()
+    return res
+
+
+def run_denoiser(world, evm=True, n=4, reps=10):
+    """The learned channel estimator (pusch_chest_cnn: LS grid, the BF16 CNN, the estimate with the LS fallback) on
+    the denoiser's evaluation cell (64 antennas, 32 DFT beams, 16 layers, 4096-point FFT, 3276 subcarriers,
+    16-QAM, 300 ns delay spread, 200 Hz Doppler) with the weights trained on the generated-slot recipe (the
+    committed weight file): CUDA-event time of the estimator per slot (n slots per call, 16 x 32 beam-domain grids
+    of 2 x 3276 per slot), and per SNR the post-MMSE EVM of the plain LS and the learned estimate against the
+    transmitted symbols, the gain and the fraction of grids that fell back to LS."""
+    import torch
+    from paper_2210_09196_gb300 import binding as B
+    from paper_2210_09196_gb300 import denoiser as D
+    from paper_2210_09196_gb300 import host, synth
+    path = os.path.join(ROOT, "paper_2210_09196_gb300", "denoiser_c4.pt")
+    if not os.path.exists(path):
+        return {"unavailable": "no trained weight file (python -m paper_2210_09196_gb300.denoiser train)"}
+    pb, meta = D.load_weights(path)
+    cell = synth.DENOISE_EVAL
+    slots = synth.make_slots(cell, n)
+    rx = host.Receiver(host.cfg_for(cell, B.PUSCH_FORM_FP32), max_slots=n)
+    freq = rx.ofdm_fft(host.time_tensor(slots))
+    beam = rx.beamform(freq, host.beam_tensor(slots[0].W))
+    pil = host.pilot_tensor(slots)
+    grids = n * cell.n_layers * cell.n_beams
+    H = rx.H_buffer(n)
+    resid = torch.zeros(grids, dtype=torch.float32, device="cuda")
+    flag = torch.zeros(grids, dtype=torch.uint8, device="cuda")
+    st = torch.cuda.current_stream()
+    for _ in range(3):
+        B.pusch_chest_cnn(rx.h, n, beam, pil, pb, 2.0, H, resid, flag, st)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(reps):
+        B.pusch_chest_cnn(rx.h, n, beam, pil, pb, 2.0, H, resid, flag, st)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1) / reps, world)
+    e0.record(st)
+    for _ in range(reps):
+        rx.chest_ls(beam, pil, H, st)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms_ls = e0.elapsed_time(e1) / reps
+    rx.close()
+    macs = 2 * 3276 * (2 * 32 * 9 + 32 * 32 * 9 * 2 + 32 * 2 * 9)      # per grid: positions x MACs per position
+    res = {"workload": cell.name, "weights": {k: meta[k] for k in ("slots", "step", "slots_per_step", "seconds")
+                                               if k in meta},
+           "slots_per_call": n, "grids_per_slot": cell.n_layers * cell.n_beams,
+           "ms_per_slot": round(ms / n, 4), "slots_per_s": round(world * n * 1e3 / ms, 1),
+           "cnn_TFLOP/s": round(2.0 * macs * grids / (ms / 1e3) / 1e12, 2),
+           "plain_ls_ms_per_slot": round(ms_ls / n, 5)}
+    if evm:
+        res["evm_vs_ls"] = {str(k): v for k, v in D.evaluate(pb, [-5.0, 0.0, 10.0, 20.0, 25.0], n_slots=1).items()}
     return res
 
 

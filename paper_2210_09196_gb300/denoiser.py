@@ -240,3 +240,82 @@ def evaluate(params_bf16, snrs_db, n_slots: int = 2, kappa: float = 2.0, cell=No
         out[float(snr)] = {"evm_ls_db": round(evm_ls, 2), "evm_cnn_db": round(evm_cnn, 2),
                            "gain_db": round(evm_ls - evm_cnn, 2), "fallback_fraction": round(float(np.mean(fb)), 4)}
     return out
+
+
+def save_weights(tr: "Trainer", path, slots_trained: int, seconds: float) -> None:
+    """The trained network for use: FP32 parameters and how they were made (no optimiser state)."""
+    torch.save({"version": 1, "params": tr.p.cpu(), "step": tr.step, "slots": int(slots_trained),
+                "slots_per_step": tr.n_slots, "gen_seed": tr.gen.seed, "seconds": round(float(seconds), 1),
+                "recipe": {"width": tr.gen.w, "layers": tr.gen.L, "beams": tr.gen.B, "snr_db": list(tr.gen.snr),
+                           "delay_spread_s": list(tr.gen.ds), "doppler_hz": list(tr.gen.fd)}}, path)
+
+
+def load_weights(path, device="cuda"):
+    """(bfloat16 parameters on the device, metadata) of a file written by save_weights."""
+    st = torch.load(path, map_location="cpu")
+    if st.get("version") != 1 or st["params"].numel() != PARAMS:
+        raise ValueError("not a denoiser weight file of this version")
+    meta = {k: v for k, v in st.items() if k != "params"}
+    return st["params"].to(device).to(torch.bfloat16), meta
+
+
+def train(slots: int, slots_per_step: int = 8, lr: float = 2e-3, seed: int = 4, checkpoint=None,
+          checkpoint_every: int = 2000, resume: bool = False, log_every: int = 1000):
+    """Trains on `slots` generated slot crops (each: 16 layers x 16 beams of 256 subcarriers, fresh channel, delay
+    spread, Doppler and SNR draws), slots_per_step per Adam step with a cosine learning-rate decay; checkpoints
+    (optimiser state included) every checkpoint_every steps and resumes from `checkpoint` when resume is set."""
+    gen = BeamDomainGenerator(seed=seed)
+    tr = Trainer(gen, slots_per_step=slots_per_step, lr=lr, seed=0)
+    steps = max(1, slots // slots_per_step)
+    if resume and checkpoint is not None:
+        import os
+        if os.path.exists(checkpoint):
+            tr.load(checkpoint)
+            # the generator resumes at a fresh seed derived from the step, so no draw repeats
+            tr.gen.g.manual_seed(seed * 1000003 + tr.step)
+    t0 = time.time()
+    hist = []
+    while tr.step < steps:
+        lr_t = tr.lr * 0.5 * (1 + math.cos(math.pi * tr.step / steps))
+        loss = tr.train_step(lr_t)
+        if log_every and tr.step % log_every == 0:
+            hist.append((tr.step, float(loss)))
+            print(f"step {tr.step}/{steps} loss {float(loss):.5f} {time.time() - t0:.0f} s", flush=True)
+        if checkpoint is not None and tr.step % checkpoint_every == 0:
+            tr.save(checkpoint)
+    torch.cuda.synchronize()
+    return tr, hist, time.time() - t0
+
+
+def _main(argv=None):
+    import argparse
+    ap = argparse.ArgumentParser(description="train or evaluate the learned channel-estimate denoiser")
+    sub = ap.add_subparsers(dest="cmd", required=True)
+    t = sub.add_parser("train")
+    t.add_argument("--slots", type=int, default=200000)
+    t.add_argument("--slots-per-step", type=int, default=8)
+    t.add_argument("--lr", type=float, default=2e-3)
+    t.add_argument("--seed", type=int, default=4)
+    t.add_argument("--out", required=True)
+    t.add_argument("--checkpoint", default=None)
+    t.add_argument("--resume", action="store_true")
+    e = sub.add_parser("evaluate")
+    e.add_argument("--weights", required=True)
+    e.add_argument("--snr", type=float, nargs="+", default=[-5.0, 0.0, 10.0, 20.0, 25.0])
+    e.add_argument("--slots", type=int, default=2)
+    a = ap.parse_args(argv)
+    if a.cmd == "train":
+        tr, hist, secs = train(a.slots, a.slots_per_step, a.lr, a.seed, a.checkpoint, resume=a.resume)
+        save_weights(tr, a.out, tr.step * tr.n_slots, secs)
+        loss, ident = tr.eval_loss(8)
+        print(f"trained {tr.step} steps ({tr.step * tr.n_slots} slots) in {secs:.0f} s; loss {loss:.5f}, "
+              f"per-symbol LS grid {ident:.5f}", flush=True)
+        tr.close()
+    else:
+        pb, meta = load_weights(a.weights)
+        import json
+        print(json.dumps({"weights": meta, "evm": evaluate(pb, a.snr, n_slots=a.slots)}), flush=True)
+
+
+if __name__ == "__main__":
+    _main()
