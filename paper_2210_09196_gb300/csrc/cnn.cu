@@ -41,10 +41,11 @@ struct ConvGeom {
 //   kOutReluBf16: out (bf16) = relu(.)
 //   kOutResidF32: out (f32)  = . + aux[s][co][h][x]          (aux: the CNN input, bf16)
 //   kOutMaskF32 : out (f32)  = aux[s][co][h][x] > 0 ? . : 0   (aux: an activation, bf16; b is NULL)
+// in has rows of in_ld elements, out and aux rows of out_ld (the grid width w <= both).
 template <int CIN, int COUT, typename TIn, int MODE>
 __global__ void __launch_bounds__(kConvThreads)
 conv3x3_kernel(const TIn *__restrict__ in, const __nv_bfloat16 *__restrict__ W, const __nv_bfloat16 *__restrict__ b,
-               void *__restrict__ out, const __nv_bfloat16 *__restrict__ aux, int w, int dil) {
+               void *__restrict__ out, const __nv_bfloat16 *__restrict__ aux, int w, int dil, int in_ld, int out_ld) {
     using G = ConvGeom<CIN, COUT>;
     constexpr int CPT = G::CPT, COG = G::COG, TW = G::TW, kWPT = G::WPT;
     extern __shared__ float sm[];
@@ -59,7 +60,7 @@ conv3x3_kernel(const TIn *__restrict__ in, const __nv_bfloat16 *__restrict__ W, 
         const int rem = i - ci * 2 * TP;
         const int h = rem / TP;
         const int xx = rem - h * TP + x0 - dil;
-        sX[i] = (xx >= 0 && xx < w) ? ldv(in + ((s * CIN + ci) * 2 + h) * (long long)w + xx) : 0.f;
+        sX[i] = (xx >= 0 && xx < w) ? ldv(in + ((s * CIN + ci) * 2 + h) * (long long)in_ld + xx) : 0.f;
     }
     __syncthreads();
     const int cg = threadIdx.x % COG;
@@ -104,7 +105,7 @@ conv3x3_kernel(const TIn *__restrict__ in, const __nv_bfloat16 *__restrict__ W, 
         for (int c = 0; c < CPT; ++c)
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const long long idx = ((s * COUT + co0 + c) * 2 + h) * (long long)w + x;
+                const long long idx = ((s * COUT + co0 + c) * 2 + h) * (long long)out_ld + x;
                 const float v = acc[h][j][c];
                 if constexpr (MODE == kOutReluBf16) {
                     static_cast<__nv_bfloat16 *>(out)[idx] = __float2bfloat16_rn(v > 0.f ? v : 0.f);
@@ -119,7 +120,10 @@ conv3x3_kernel(const TIn *__restrict__ in, const __nv_bfloat16 *__restrict__ W, 
 
 template <int CIN, int COUT, typename TIn, int MODE>
 cudaError_t launch_conv(const TIn *in, const __nv_bfloat16 *W, const __nv_bfloat16 *b, void *out,
-                        const __nv_bfloat16 *aux, int n, int w, int dil, cudaStream_t st) {
+                        const __nv_bfloat16 *aux, int n, int w, int dil, cudaStream_t st, int in_ld = 0,
+                        int out_ld = 0) {
+    if (in_ld <= 0) in_ld = w;
+    if (out_ld <= 0) out_ld = w;
     using G = ConvGeom<CIN, COUT>;
     auto k = conv3x3_kernel<CIN, COUT, TIn, MODE>;
     const size_t smem = G::smem(dil);
@@ -129,7 +133,7 @@ cudaError_t launch_conv(const TIn *in, const __nv_bfloat16 *W, const __nv_bfloat
     }
     if (n > 65535) return cudaErrorInvalidConfiguration;
     dim3 grid((w + G::TW - 1) / G::TW, n);
-    k<<<grid, kConvThreads, smem, st>>>(in, W, b, out, aux, w, dil);
+    k<<<grid, kConvThreads, smem, st>>>(in, W, b, out, aux, w, dil, in_ld, out_ld);
     return cudaGetLastError();
 }
 
@@ -273,24 +277,32 @@ int param_offset(int layer) {
 
 int cnn_param_count() { return param_offset(4); }
 
-// Forward pass of n grids of width w. acts: [3][n][32][2][w] bf16 (post-ReLU activations), y: [n][2][2][w] f32.
+// Forward pass of n grids of width w. acts: [3][n][32][2][ld] bf16 (post-ReLU activations, rows of ld >= w
+// elements), x: [n][2][2][w] bf16, y: [n][2][2][w] f32. The two 32 -> 32 layers run on the tensor cores
+// (cnn_tc.cu) when ld is a multiple of 8 (16-byte rows for the copy engine), on the FP32 pipes otherwise.
 cudaError_t cnn_forward(int n, int w, const __nv_bfloat16 *x, const __nv_bfloat16 *P, float *y, __nv_bfloat16 *acts,
-                        cudaStream_t st) {
-    const size_t big = (size_t)n * 32 * 2 * w;
+                        cudaStream_t st, int ld, uint32_t *err) {
+    if (ld <= 0) ld = w;
+    const size_t big = (size_t)n * 32 * 2 * ld;
     const __nv_bfloat16 *W0 = P + param_offset(0), *W1 = P + param_offset(1), *W2 = P + param_offset(2),
                         *W3 = P + param_offset(3);
     cudaError_t e;
     if ((e = launch_conv<2, 32, __nv_bfloat16, kOutReluBf16>(x, W0, W0 + 32 * 2 * 9, acts, nullptr, n, w, kDil[0],
-                                                             st)) != cudaSuccess)
+                                                             st, w, ld)) != cudaSuccess)
         return e;
-    if ((e = launch_conv<32, 32, __nv_bfloat16, kOutReluBf16>(acts, W1, W1 + 32 * 32 * 9, acts + big, nullptr, n, w,
-                                                              kDil[1], st)) != cudaSuccess)
-        return e;
-    if ((e = launch_conv<32, 32, __nv_bfloat16, kOutReluBf16>(acts + big, W2, W2 + 32 * 32 * 9, acts + 2 * big,
-                                                              nullptr, n, w, kDil[2], st)) != cudaSuccess)
-        return e;
+    for (int k = 1; k <= 2; ++k) {
+        const __nv_bfloat16 *Wk = k == 1 ? W1 : W2;
+        const __nv_bfloat16 *in = acts + (k - 1) * big;
+        __nv_bfloat16 *out = acts + k * big;
+        if (conv32_tc_supported(ld, kDil[k]))
+            e = launch_conv32_tc(in, Wk, Wk + 32 * 32 * 9, out, n, w, ld, kDil[k], err, st);
+        else
+            e = launch_conv<32, 32, __nv_bfloat16, kOutReluBf16>(in, Wk, Wk + 32 * 32 * 9, out, nullptr, n, w, kDil[k],
+                                                                 st, ld, ld);
+        if (e != cudaSuccess) return e;
+    }
     return launch_conv<32, 2, __nv_bfloat16, kOutResidF32>(acts + 2 * big, W3, W3 + 2 * 32 * 9, y, x, n, w, kDil[3],
-                                                           st);
+                                                           st, ld, w);
 }
 
 // Backward pass: grad (zeroed here) = d mean((y - target)^2) / d params; *loss = that mean (if loss != NULL).

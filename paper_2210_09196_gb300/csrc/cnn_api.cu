@@ -96,7 +96,8 @@ pusch_status pusch_chest_cnn(pusch_handle *h, int n_slots, const void *beam, con
         const size_t px = (size_t)grids_max * 2 * g.n_sc;
         if ((e = cudaMalloc(&h->cnn_grid, px * 2 * sizeof(__nv_bfloat16))) != cudaSuccess ||
             (e = cudaMalloc((void **)&h->cnn_scale, (size_t)grids_max * sizeof(float))) != cudaSuccess ||
-            (e = cudaMalloc(&h->cnn_acts, px * 3 * 32 * sizeof(__nv_bfloat16))) != cudaSuccess ||
+            (e = cudaMalloc(&h->cnn_acts, (size_t)grids_max * 2 * ((g.n_sc + 7) & ~7) * 3 * 32 * sizeof(__nv_bfloat16))) !=
+                cudaSuccess ||
             (e = cudaMalloc((void **)&h->cnn_y, px * 2 * sizeof(float))) != cudaSuccess)
             return cfail(PUSCH_ERR_CUDA, "CNN workspace allocation", e);
     }
@@ -109,8 +110,10 @@ pusch_status pusch_chest_cnn(pusch_handle *h, int n_slots, const void *beam, con
     if ((e = pusch::launch_ls_grid(g, n_slots, (const float2 *)beam, (const float2 *)pilots,
                                    (__nv_bfloat16 *)h->cnn_grid, h->cnn_scale, s)) != cudaSuccess)
         return cfail(PUSCH_ERR_CUDA, "LS grid launch", e);
+    // activation rows padded to a multiple of 8 subcarriers, so that the 32 -> 32 layers run on the tensor cores
     if ((e = pusch::cnn_forward(grids, g.n_sc, (const __nv_bfloat16 *)h->cnn_grid, (const __nv_bfloat16 *)params,
-                                h->cnn_y, (__nv_bfloat16 *)h->cnn_acts, s)) != cudaSuccess)
+                                h->cnn_y, (__nv_bfloat16 *)h->cnn_acts, s, (g.n_sc + 7) & ~7, h->kernel_err)) !=
+        cudaSuccess)
         return cfail(PUSCH_ERR_CUDA, "CNN forward launch", e);
     if ((e = pusch::launch_cnn_to_h(g, n_slots, kappa, h->cnn_y, h->cnn_scale, (const float2 *)beam,
                                     (const float2 *)pilots, (float2 *)H_hat, resid, fallback, s)) != cudaSuccess)

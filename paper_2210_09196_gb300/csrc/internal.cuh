@@ -184,8 +184,13 @@ inline cudaError_t launch_beamform(const Geometry &g, int n_slots, const void *f
 
 // Learned channel-estimate denoiser (cnn.cu). Parameters packed per layer as W[co][ci][3][3], b[co].
 int cnn_param_count();
+// acts rows of ld elements (0 = w); err (optional): error word of the tensor-core layers' bounded waits.
 cudaError_t cnn_forward(int n, int w, const __nv_bfloat16 *x, const __nv_bfloat16 *P, float *y, __nv_bfloat16 *acts,
-                        cudaStream_t st);
+                        cudaStream_t st, int ld = 0, uint32_t *err = nullptr);
+// The 32 -> 32 convolution with ReLU on the tensor cores: in, out [n][32][2][ld] bf16 (ld % 8 == 0, dil % 8 == 0).
+bool conv32_tc_supported(int ld, int dil);
+cudaError_t launch_conv32_tc(const __nv_bfloat16 *in, const __nv_bfloat16 *W, const __nv_bfloat16 *b,
+                             __nv_bfloat16 *out, int n, int w, int ld, int dil, uint32_t *err, cudaStream_t st);
 cudaError_t cnn_backward(int n, int w, const __nv_bfloat16 *x, const __nv_bfloat16 *acts, const __nv_bfloat16 *P,
                          const float *y, const float *target, float *grad, float *loss, float *work,
                          __nv_bfloat16 *wflip, cudaStream_t st);

@@ -23,7 +23,7 @@ def test_param_count():
     assert B.pusch_cnn_param_count() == D.PARAMS == 19682
 
 
-@pytest.mark.parametrize("n,w", [(3, 37), (5, 300)])
+@pytest.mark.parametrize("n,w", [(3, 37), (5, 300), (2, 256), (3, 264)])   # 256, 264: tensor-core 32 -> 32 layers
 def test_forward_backward_match_oracle(orc, n, w):
     rng = np.random.default_rng(n * 1000 + w)
     p = D.init_params(seed=n)
