@@ -387,7 +387,8 @@ pusch_status pusch_batch_tuning(const pusch_batch *b, int *out, int n_out);
  *   "slot-fft ..."   FFT CTAs per SM: the kernel's own choice, or at most 3, 2 or 1
  *   "slot-bf ..."    tensor-core beamforming GEMM (mixed and FP8 forms): K rows per pipeline stage and staged
  *                    or direct output stores (every shape that fits shared memory)
- *   "slot-det ..."   detector warps per CTA: 1, 2 or 4 (one estimate per slot, 12 data symbols)
+ *   "slot-det ..."   detector warps per CTA: 1, 2, 4 or 8, where the tiles fit in shared memory (one estimate
+ *                    per slot, 12 data symbols)
  *   "slot-pipe ..."  pusch_set_pipeline chunk count: 1, 2 or 4 (at most max_slots)
  * The choices apply to the handle's later calls; every choice gives bit-identical results (each subcarrier's and
  * each row's arithmetic is the same whatever the launch shape). cache_path may be NULL (nothing read or written);

@@ -755,13 +755,15 @@ extern "C" pusch_status pusch_autotune(pusch_handle *h, const char *cache_path, 
                  g.n_beams, g.n_sc, n);
         auto it = cache.find(key);
         if (it != cache.end()) {
-            g.det_warps = value_of(it->second, "warps", 2);
+            g.det_warps = value_of(it->second, "warps", 0);
         } else {
-            const int ws[3] = {2, 1, 4};
+            int ws[4];
+            const int nw = pusch::mmse_warp_choices_for(g.n_layers, g.n_beams, ws);
             float best = 1e30f;
-            int bw = 2;
+            int bw = ws[0];
             const float *sg2 = h->cfg.noise_var == PUSCH_NOISE_ESTIMATE ? h->sigma2 : nullptr;
-            for (int w : ws) {
+            for (int wi = 0; wi < nw; ++wi) {
+                const int w = ws[wi];
                 g.det_warps = w;
                 const float ms = time_ms(s, reps, [&] {
                     pusch::launch_mmse(g, n, h->H, h->beam, static_cast<float2 *>(xh), bits, h->status_sink, s, sg2);

@@ -60,7 +60,7 @@ struct Geometry {
     int dmrs_type;                // 1: 3GPP type-1 DMRS; comb / port then give the CDM pair centres (4, 1 + group)
     // launch shapes (pusch_autotune; 0 = the built-in choice)
     int fft_cap;                  // FFT CTAs per SM at most
-    int det_warps;                // warps per CTA of the 12-data-symbol detector (1, 2 or 4)
+    int det_warps;                // warps per CTA of the 12-data-symbol detector (0 = the class default)
 };
 
 // Complex time samples of one slot's input.
@@ -131,10 +131,14 @@ cudaError_t launch_chest_time(const Geometry &g, int n_slots, const float2 *beam
 // sigma2 (optional, device, one float per slot): per-slot noise variance replacing g.noise_var.
 // time_groups: H holds g.n_groups estimates (launch_chest_time) and each group of g.chol_every data symbols
 // is detected with its own.
-// The 12-data-symbol kernels run g.det_warps warps per CTA (1, 2 or 4; anything else = 2).
+// The 12-data-symbol kernels run g.det_warps warps per CTA when it is one of mmse_warp_choices_for(n_layers,
+// n_beams), else the layer class's default.
 cudaError_t launch_mmse(const Geometry &g, int n_slots, const float2 *H, const float2 *beam, float2 *x_hat,
                         uint8_t *bits, uint32_t *status, cudaStream_t st, const float *sigma2 = nullptr,
                         bool time_groups = false);
+// The warps per CTA the 12-data-symbol detector of n_layers layers and n_beams beams may run (out: at most 4;
+// the first is the default); returns their count.
+int mmse_warp_choices_for(int n_layers, int n_beams, int *out);
 // LS values at the pilot subcarriers: ls[slot][l][k][b] for pilot q = port[l] + k * comb, k < kmax.
 int ls_pilots_per_layer(const Geometry &g);
 // sym = -1: the mean of the two DMRS symbols; 0 / 1: that DMRS symbol alone.

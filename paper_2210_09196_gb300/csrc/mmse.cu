@@ -7,7 +7,7 @@ namespace pusch {
 cudaError_t launch_mmse(const Geometry &g, int n_slots, const float2 *H, const float2 *beam, float2 *x_hat,
                         uint8_t *bits, uint32_t *status, cudaStream_t st, const float *sigma2, bool time_groups) {
     mmse_detail::MmseArgs a;
-    a.warps = (g.det_warps == 1 || g.det_warps == 4) ? g.det_warps : 2;
+    a.warps = g.det_warps;
     a.n_sc = g.n_sc;
     a.n_beams = g.n_beams;
     a.n_layers = g.n_layers;
@@ -42,6 +42,15 @@ cudaError_t launch_mmse(const Geometry &g, int n_slots, const float2 *H, const f
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+int mmse_warp_choices_for(int n_layers, int n_beams, int *out) {
+    using namespace mmse_detail;
+    if (n_layers <= 2) return mmse_warp_choices<2>(n_beams, out);
+    if (n_layers <= 4) return mmse_warp_choices<4>(n_beams, out);
+    if (n_layers <= 8) return mmse_warp_choices<8>(n_beams, out);
+    if (n_layers <= 16) return mmse_warp_choices<16>(n_beams, out);
+    return mmse_warp_choices<32>(n_beams, out);
 }
 
 }  // namespace pusch

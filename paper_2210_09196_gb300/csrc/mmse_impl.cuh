@@ -26,7 +26,6 @@
 namespace pusch {
 namespace mmse_detail {
 
-constexpr int kMmseWarps = 2;
 constexpr unsigned kFull = 0xffffffffu;
 
 struct MmseArgs {
@@ -36,7 +35,7 @@ struct MmseArgs {
     const float *sigma2;       // per-slot noise variance (device) or nullptr
     int d_first, n_det;        // this launch detects data symbols d_first .. d_first + n_det - 1 (n_data in all)
     int dmrs_lo, dmrs_hi;      // the two DMRS symbols, dmrs_lo < dmrs_hi
-    int warps;                 // warps per CTA of the 12-symbol kernels: 1, 2 (default) or 4
+    int warps;                 // warps per CTA of the 12-symbol kernels (mmse_warp_choices; 0 = default)
 };
 
 // Symbol index of data symbol d: the data symbols are all other symbols of the slot in increasing order.
@@ -85,104 +84,133 @@ __device__ __forceinline__ void stage_H(float2 *Ht, const float2 *__restrict__ H
     cp_async_wait_all();  // the H tile (and the earlier y group)
 }
 
+// Warps per CTA of the 12-data-symbol kernels when not tuned: one (each warp then starts and ends on its own;
+// larger CTAs measured slower for 16 layers, their warps waiting for one another at the output rows), four for
+// 32 layers (one subcarrier per warp).
+template <int NL>
+constexpr int mmse_default_warps() {
+    return NL == 32 ? 4 : 1;
+}
 // Register cap: 10 warps per SM up to 8 layers, 14 for 16 layers (128 registers: the shared-memory limit is
-// also 14 warps of two subcarriers), none for 32; the CTA holds WARPS warps (1, 2 or 4; 2 unless tuned).
+// also 14 warps of two subcarriers), none for 32.
 template <int NL, int WARPS>
 constexpr int mmse_min_ctas() {
     constexpr int w = NL <= 8 ? 10 : (NL == 16 ? 14 : WARPS);
     return (w + WARPS - 1) / WARPS;
 }
-template <int NL, int ND, int WARPS = kMmseWarps>
+// One CTA detects SPC = WARPS * 32 / NL consecutive subcarriers (warp w: SPW = 32 / NL of them from
+// w * SPW). After every warp has left its x_d in its data-symbol rows, the CTA writes x-hat and the bits row by
+// row: the SPC subcarriers of one (slot, layer, data symbol) row are consecutive in both outputs, so each row
+// segment is one contiguous run of SPC elements (a warp per subcarrier pair would write 16-byte pieces of 16
+// rows).
+// NB > 0: compiled for NB beams (every shared-memory offset of the Gram, matched-filter and staging loops is
+// then a constant); 0: g.n_beams at run time.
+template <int NL, int ND, int WARPS, int NB>
 __global__ void __launch_bounds__(WARPS * 32, mmse_min_ctas<NL, WARPS>())
 mmse_kernel(MmseArgs g, long long total_sc, const float2 *__restrict__ H, const float2 *__restrict__ beam,
             float2 *__restrict__ xhat, uint8_t *__restrict__ bits, uint32_t *__restrict__ status) {
     constexpr int SPW = 32 / NL;
+    constexpr int SPC = WARPS * SPW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int grp = lane / NL, i = lane - grp * NL;
     const int src0 = grp * NL;
-    const int nl = g.n_layers, nb = g.n_beams, n_sc = g.n_sc;
+    const int nl = g.n_layers, nb = NB > 0 ? NB : g.n_beams, n_sc = g.n_sc;
     // nd: the data symbols this launch detects (ND when compiled in, else n_det)
     const int nd = ND > 0 ? ND : g.n_det;
     const int hs = row_stride(nb), ht = htile<NL>(nb), ys = y_stride<NL>(nb);
+    const size_t wsb = warp_smem_bytes<NL>(nb, nd);
 
-    unsigned char *wbase = smem_raw + (size_t)warp * warp_smem_bytes<NL>(nb, nd);
+    unsigned char *wbase = smem_raw + (size_t)warp * wsb;
     float2 *Ht = reinterpret_cast<float2 *>(wbase);  // [SPW][ht]
     float2 *Yt = Ht + SPW * ht;                      // [SPW][nd][ys]
 
-    const long long sc0 = ((long long)blockIdx.x * WARPS + warp) * SPW;  // first (slot*n_sc + a) of warp
-    if (sc0 >= total_sc) return;                                              // whole warp idle
-    const long long my_sc = sc0 + grp;
-    const bool valid = my_sc < total_sc;
-    const long long slot = my_sc / n_sc;
-    const int a = (int)(my_sc - slot * n_sc);
+    const long long cta_sc0 = (long long)blockIdx.x * SPC;
+    const long long sc0 = cta_sc0 + warp * SPW;  // first (slot*n_sc + a) of warp
+    if (sc0 < total_sc) {                        // else the whole warp is idle until the output rows
+        const long long my_sc = sc0 + grp;
+        const bool valid = my_sc < total_sc;
+        const long long slot = my_sc / n_sc;
 
-    // ---- 0. the data-symbol rows y_d of the warp's subcarriers -> shared memory, asynchronously (cp.async,
-    //         16-byte pieces when the beam count is even); waited for just before step 2b.
-    {
-        const bool wide = (nb & 1) == 0;
-        const int cpr = wide ? nb >> 1 : nb;  // pieces per row
-        int row = lane / cpr, c = lane - (lane / cpr) * cpr;
-        const int step_r = 32 / cpr, step_c = 32 - (32 / cpr) * cpr;
-        for (; row < SPW * nd;) {
-            const int gg = row / nd, d = row - gg * nd;
-            const long long sc = sc0 + gg;
-            float2 *dst = Yt + (gg * nd + d) * ys + (wide ? 2 * c : c);
-            if (sc < total_sc) {
-                const long long sl = sc / n_sc, aa = sc - sl * n_sc;
-                const float2 *src =
-                    beam + ((sl * g.n_sym + data_symbol(g, g.d_first + d)) * n_sc + aa) * nb + (wide ? 2 * c : c);
-                if (wide)
-                    cp_async16(dst, src);
-                else
-                    cp_async8(dst, src);
-            } else {
-                dst[0] = make_float2(0.f, 0.f);
-                if (wide) dst[1] = make_float2(0.f, 0.f);
+        // ---- 0. the data-symbol rows y_d of the warp's subcarriers -> shared memory, asynchronously (cp.async,
+        //         16-byte pieces when the beam count is even); waited for just before step 2b.
+        {
+            const bool wide = (nb & 1) == 0;
+            const int cpr = wide ? nb >> 1 : nb;  // pieces per row
+            int row = lane / cpr, c = lane - (lane / cpr) * cpr;
+            const int step_r = 32 / cpr, step_c = 32 - (32 / cpr) * cpr;
+            for (; row < SPW * nd;) {
+                const int gg = row / nd, d = row - gg * nd;
+                const long long sc = sc0 + gg;
+                float2 *dst = Yt + (gg * nd + d) * ys + (wide ? 2 * c : c);
+                if (sc < total_sc) {
+                    const long long sl = sc / n_sc, aa = sc - sl * n_sc;
+                    const float2 *src =
+                        beam + ((sl * g.n_sym + data_symbol(g, g.d_first + d)) * n_sc + aa) * nb + (wide ? 2 * c : c);
+                    if (wide)
+                        cp_async16(dst, src);
+                    else
+                        cp_async8(dst, src);
+                } else {
+                    dst[0] = make_float2(0.f, 0.f);
+                    if (wide) dst[1] = make_float2(0.f, 0.f);
+                }
+                row += step_r;
+                c += step_c;
+                if (c >= cpr) {
+                    c -= cpr;
+                    ++row;
+                }
             }
-            row += step_r;
-            c += step_c;
-            if (c >= cpr) {
-                c -= cpr;
-                ++row;
-            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
         }
-        asm volatile("cp.async.commit_group;" ::: "memory");
+
+        // ---- 1. channel estimate rows -> shared memory; 2-4. Gram, matched filter, Cholesky and solves, the
+        //         x_d left in the data-symbol rows (detect_group).
+        const float2 *hr = Ht + grp * ht + i * hs;  // own row
+        const float2 *hg = Ht + grp * ht;           // the group's rows
+        constexpr int NR = ND > 0 ? ND : 14;
+        float2 acc[NR];
+        stage_H<NL>(Ht, H, sc0, total_sc, nl, nb, hs, ht, lane);
+        __syncwarp();
+        const bool bad = detect_group<NL, ND, NR>(hr, hg, Yt + grp * nd * ys, Ht + grp * ht, hs, nb, nd, nl,
+                                                  g.sigma2 ? g.loading : g.load, i, src0, acc, g.sigma2,
+                                                  valid ? slot : 0, ys);
+        if (valid && bad && i == 0) {
+            atomicAdd(&status[1], 1u);
+            atomicMin(&status[2], (unsigned)my_sc);
+            atomicOr(&status[0], (unsigned)PUSCH_STATUS_PIVOT);
+        }
     }
+    __syncthreads();
 
-    // ---- 1. channel estimate rows -> shared memory (stage_H, per detection group, in the loop below).
-
-    const float2 *hr = Ht + grp * ht + i * hs;  // own row
-    const float2 *hg = Ht + grp * ht;           // the group's rows
-    constexpr int NR = ND > 0 ? ND : 14;
-    float2 acc[NR];
-    stage_H<NL>(Ht, H, sc0, total_sc, nl, nb, hs, ht, lane);
-    __syncwarp();
-    const bool bad = detect_group<NL, ND, NR>(hr, hg, Yt + grp * nd * ys, Ht + grp * ht, hs, nb, nd, nl,
-                                              g.sigma2 ? g.loading : g.load, i, src0, acc, g.sigma2,
-                                              valid ? slot : 0, ys);
+    // ---- 5. x-hat and the Gray decisions, row by row: thread t writes subcarrier cta_sc0 + t % SPC of the rows
+    //         (layer l, data symbol d_first + d), l * nd + d = t / SPC, t / SPC + NL, ... (the CTA's WARPS * 32
+    //         threads are NL times its SPC subcarriers), reading x_d[l] from that subcarrier's rows.
     bool nonfinite = false;
-    if (valid && i < nl) {
-        const long long o0 = ((slot * nl + i) * (long long)g.n_data + g.d_first) * n_sc + a;
-#pragma unroll
-        for (int d = 0; d < NR; ++d) {
-            if (ND > 0 || d < nd) {
-                const float2 x = acc[d];
-                xhat[o0 + (long long)d * n_sc] = x;
-                bits[o0 + (long long)d * n_sc] = det_demap(x, g.qam_bits);
+    {
+        const int s = threadIdx.x % SPC;
+        const long long sc = cta_sc0 + s;
+        if (sc < total_sc) {
+            const int w = s / SPW, gg = s - w * SPW;
+            const float2 *yt = reinterpret_cast<const float2 *>(smem_raw + (size_t)w * wsb) + SPW * ht + gg * nd * ys;
+            const long long sl = sc / n_sc, a = sc - sl * n_sc;
+            float2 *xo = xhat + (sl * nl * (long long)g.n_data + g.d_first) * n_sc + a;
+            uint8_t *bo = bits + (sl * nl * (long long)g.n_data + g.d_first) * n_sc + a;
+            for (int ld = threadIdx.x / SPC; ld < nl * nd; ld += NL) {
+                const int l = ld / nd, d = ld - l * nd;
+                const float2 x = yt[d * ys + l];
+                const long long o = ((long long)l * g.n_data + d) * n_sc;
+                xo[o] = x;
+                bo[o] = det_demap(x, g.qam_bits);
                 if (!isfinite(x.x) || !isfinite(x.y)) nonfinite = true;
             }
         }
     }
-    if (valid && bad && i == 0) {
-        atomicAdd(&status[1], 1u);
-        atomicMin(&status[2], (unsigned)my_sc);
-        atomicOr(&status[0], (unsigned)PUSCH_STATUS_PIVOT);
-    }
     if (__any_sync(kFull, nonfinite) && lane == 0) atomicOr(&status[0], (unsigned)PUSCH_STATUS_NONFINITE);
 }
 
-template <int NL, int ND, int WARPS = kMmseWarps>
+template <int NL, int ND, int WARPS, int NB>
 cudaError_t launch_nl(const MmseArgs &a, long long total_sc, const float2 *H, const float2 *beam, float2 *xhat,
                       uint8_t *bits, uint32_t *status, cudaStream_t st) {
     constexpr int SPW = 32 / NL;
@@ -190,7 +218,7 @@ cudaError_t launch_nl(const MmseArgs &a, long long total_sc, const float2 *H, co
     const long long per_cta = (long long)WARPS * SPW;
     const long long grid = (total_sc + per_cta - 1) / per_cta;
     if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    auto k = mmse_kernel<NL, ND, WARPS>;
+    auto k = mmse_kernel<NL, ND, WARPS, NB>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -199,17 +227,50 @@ cudaError_t launch_nl(const MmseArgs &a, long long total_sc, const float2 *H, co
     return cudaGetLastError();
 }
 
-// Compiled-in symbol counts: 12 (one estimate per slot; 1, 2 or 4 warps per CTA, a.warps), 4 and 1
-// (Section VI's schedules, one factorisation per 4 data symbols or per symbol); anything else at run time.
+// Shared memory one CTA may hold (opt-in maximum per block).
+constexpr size_t kMmseSmemMax = 227 * 1024;
+
+// Compiled-in symbol counts: 12 (one estimate per slot; 1, 2, 4 or 8 warps per CTA, a.warps, if that many
+// warps' tiles fit in shared memory, else the default), 4 and 1 (Section VI's schedules, one factorisation per 4
+// data symbols or per symbol); anything else at run time. The defaults fit every supported shape (at most 64
+// beams and 12 data symbols: 120 KB for a 2-layer warp of 16 subcarriers).
+template <int NL, int NB>
+cudaError_t launch_w(const MmseArgs &a, long long total_sc, const float2 *H, const float2 *beam, float2 *xhat,
+                     uint8_t *bits, uint32_t *status, cudaStream_t st) {
+    constexpr int W = mmse_default_warps<NL>();
+    const bool fits = (size_t)a.warps * warp_smem_bytes<NL>(a.n_beams, a.n_det) <= kMmseSmemMax;
+    if (a.n_det == 12 && fits && a.warps == 1) return launch_nl<NL, 12, 1, NB>(a, total_sc, H, beam, xhat, bits, status, st);
+    if (a.n_det == 12 && fits && a.warps == 2) return launch_nl<NL, 12, 2, NB>(a, total_sc, H, beam, xhat, bits, status, st);
+    if (a.n_det == 12 && fits && a.warps == 4) return launch_nl<NL, 12, 4, NB>(a, total_sc, H, beam, xhat, bits, status, st);
+    if (a.n_det == 12 && fits && a.warps == 8) return launch_nl<NL, 12, 8, NB>(a, total_sc, H, beam, xhat, bits, status, st);
+    if (a.n_det == 12) return launch_nl<NL, 12, W, NB>(a, total_sc, H, beam, xhat, bits, status, st);
+    if (a.n_det == 4) return launch_nl<NL, 4, W, NB>(a, total_sc, H, beam, xhat, bits, status, st);
+    if (a.n_det == 1) return launch_nl<NL, 1, W, NB>(a, total_sc, H, beam, xhat, bits, status, st);
+    return launch_nl<NL, 0, W, 0>(a, total_sc, H, beam, xhat, bits, status, st);
+}
+
+// The 16- and 32-layer classes are also compiled for 32 and 64 beams.
 template <int NL>
 cudaError_t launch_nd(const MmseArgs &a, long long total_sc, const float2 *H, const float2 *beam, float2 *xhat,
                       uint8_t *bits, uint32_t *status, cudaStream_t st) {
-    if (a.n_det == 12 && a.warps == 1) return launch_nl<NL, 12, 1>(a, total_sc, H, beam, xhat, bits, status, st);
-    if (a.n_det == 12 && a.warps == 4) return launch_nl<NL, 12, 4>(a, total_sc, H, beam, xhat, bits, status, st);
-    if (a.n_det == 12) return launch_nl<NL, 12>(a, total_sc, H, beam, xhat, bits, status, st);
-    if (a.n_det == 4) return launch_nl<NL, 4>(a, total_sc, H, beam, xhat, bits, status, st);
-    if (a.n_det == 1) return launch_nl<NL, 1>(a, total_sc, H, beam, xhat, bits, status, st);
-    return launch_nl<NL, 0>(a, total_sc, H, beam, xhat, bits, status, st);
+    if constexpr (NL >= 16) {
+        if (a.n_beams == 32) return launch_w<NL, 32>(a, total_sc, H, beam, xhat, bits, status, st);
+        if (a.n_beams == 64) return launch_w<NL, 64>(a, total_sc, H, beam, xhat, bits, status, st);
+    }
+    return launch_w<NL, 0>(a, total_sc, H, beam, xhat, bits, status, st);
+}
+
+// Warps per CTA that a.warps may select for the 12-symbol kernels of a layer class with n_beams beams (the
+// default first, then the other counts of 1, 2, 4 and 8 whose tiles fit); returns their count (at most 4).
+template <int NL>
+int mmse_warp_choices(int n_beams, int *out) {
+    constexpr int W = mmse_default_warps<NL>();
+    const size_t wb = warp_smem_bytes<NL>(n_beams, 12);
+    int n = 0;
+    out[n++] = W;
+    for (int w = 1; w <= 8; w *= 2)
+        if (w != W && w * wb <= kMmseSmemMax) out[n++] = w;
+    return n;
 }
 
 }  // namespace mmse_detail
