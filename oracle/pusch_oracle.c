@@ -33,7 +33,7 @@
  *                   in time and factorised every K data symbols (Section VI's schedule).
  *   orc_e4m3_*,     the FP8 precision form of the beamforming step (not in the paper; the form this
  *   orc_beamform_fp8  project adds): E4M3 rounding, power-of-two block scales, and the block-scaled
- *                   product y = W^H x with its exact power-of-two alignment.
+ *                   product y = W^H x of the dequantised operands.
  *
  * Layouts (complex values interleaved re,im; C99 double complex):
  *   time  [n_sym][n_rx][n_fft]     freq [n_sym][n_rx][n_sc]     beam [n_sym][n_sc][n_beams]
@@ -1042,68 +1042,46 @@ void orc_e4m3_quant_rows(const cplx *x, long long rows, int n, cplx *codes, int 
         }
 }
 
-/* FP8-form beamforming. codes [n_sym][n_rx][n_sc] (E4M3 values) with block exponents exps
- * [n_sym][n_rx][ceil(n_sc / 128)] are the samples; W [n_rx][n_beams] is quantised here with one block
- * exponent per (beam, 128 antennas): ew = orc_e4m3_block_exp(largest |Re|, |Im| of the block),
- * cw = E4M3(W / 2^ew). The product aligns the block scales by powers of two:
- *   the samples of subcarrier block j are brought to E = max over antennas of exps[s][r][j]:
- *       xq = E4M3(code * 2^(exps - E)), sample = xq 2^E;
- *   the weights of beam b are brought to E_b = max over its blocks of ew:
- *       wq = E4M3(cw * 2^(ew - E_b)), weight = wq 2^E_b;
- *   beam[s][a][b] = sum_r conj(weight[r][b]) sample[s][r][a].
- * The alignment changes no value unless a shifted code falls below the smallest normal E4M3 (2^-6).
- * A block exponent of 128 (non-finite block) makes the affected outputs NaN. */
+/* FP8-form beamforming: the block-scaled product of the two quantised operands, summed exactly.
+ *   samples: codes [n_sym][n_rx][n_sc] (E4M3 values) with block exponents exps [n_sym][n_rx][ceil(n_sc / 128)];
+ *            sample[s][r][a] = codes[s][r][a] * 2^exps[s][r][a / 128];
+ *   weights: W [n_rx][n_beams] quantised per (beam, 128 antennas): ew = orc_e4m3_block_exp(largest |Re|, |Im|
+ *            of the block), weight[r][b] = E4M3(W[r][b] / 2^ew) * 2^ew;
+ *   beam[s][a][b] = sum_r conj(weight[r][b]) sample[s][r][a]   (Section II's Y = W^H X), in double.
+ * A block exponent of 128 (a non-finite block) makes every output that block enters NaN. */
 void orc_beamform_fp8(const cplx *codes, const int *exps, const cplx *W, int n_sym, int n_rx, int n_sc, int n_beams,
                       cplx *beam)
 {
-    int n_blk = (n_sc + 127) / 128, n_kb = (n_rx + 127) / 128;
-    cplx *wv = malloc(sizeof(cplx) * (size_t)n_rx * n_beams);
-    double *wscale = malloc(sizeof(double) * (size_t)n_beams);
-    int *ew = malloc(sizeof(int) * (size_t)n_kb);
-    for (int b = 0; b < n_beams; ++b) {
-        int eb = -126, bad = 0;
-        for (int kb = 0; kb < n_kb; ++kb) {
+    int n_blk = (n_sc + 127) / 128;
+    cplx *wq = malloc(sizeof(cplx) * (size_t)n_rx * n_beams);
+    for (int b = 0; b < n_beams; ++b)
+        for (int r0 = 0; r0 < n_rx; r0 += 128) {
             double amax = 0.0;
-            for (int r = 128 * kb; r < n_rx && r < 128 * kb + 128; ++r) {
+            int bad = 0;
+            for (int r = r0; r < n_rx && r < r0 + 128; ++r) {
                 double re = fabs(creal(W[r * n_beams + b])), im = fabs(cimag(W[r * n_beams + b]));
                 if (!isfinite(re) || !isfinite(im)) bad = 1;
                 if (re > amax) amax = re;
                 if (im > amax) amax = im;
             }
-            ew[kb] = orc_e4m3_block_exp(amax);
-            if (ew[kb] > eb) eb = ew[kb];
+            int e = bad ? 128 : orc_e4m3_block_exp(amax);
+            for (int r = r0; r < n_rx && r < r0 + 128; ++r) {
+                cplx w = W[r * n_beams + b];
+                wq[r * n_beams + b] = e >= 128 ? NAN
+                    : ldexp(orc_e4m3_round(ldexp(creal(w), -e)), e) + I * ldexp(orc_e4m3_round(ldexp(cimag(w), -e)), e);
+            }
         }
-        wscale[b] = bad ? NAN : ldexp(1.0, eb);
-        for (int r = 0; r < n_rx; ++r) {
-            cplx w = W[r * n_beams + b];
-            int e = ew[r / 128];
-            double cr = orc_e4m3_round(ldexp(creal(w), -e)), ci = orc_e4m3_round(ldexp(cimag(w), -e));
-            wv[r * n_beams + b] = orc_e4m3_round(ldexp(cr, e - eb)) + I * orc_e4m3_round(ldexp(ci, e - eb));
-        }
-    }
-    cplx *xq = malloc(sizeof(cplx) * (size_t)n_rx);
     for (int s = 0; s < n_sym; ++s)
-        for (int j = 0; j < n_blk; ++j) {
-            int E = -126;
-            for (int r = 0; r < n_rx; ++r) {
-                int e = exps[((long long)s * n_rx + r) * n_blk + j];
-                if (e > E) E = e;
-            }
-            for (int a = 128 * j; a < n_sc && a < 128 * j + 128; ++a) {
-                for (int r = 0; r < n_rx; ++r) {      /* the aligned samples of subcarrier a */
-                    int e = exps[((long long)s * n_rx + r) * n_blk + j];
-                    cplx c = codes[((long long)s * n_rx + r) * n_sc + a];
-                    xq[r] = orc_e4m3_round(ldexp(creal(c), e - E)) + I * orc_e4m3_round(ldexp(cimag(c), e - E));
+        for (int a = 0; a < n_sc; ++a)
+            for (int b = 0; b < n_beams; ++b) {
+                cplx acc = 0;
+                for (int r = 0; r < n_rx; ++r) {
+                    int e = exps[((long long)s * n_rx + r) * n_blk + a / 128];
+                    cplx x = e >= 128 ? NAN : ldexp(creal(codes[((long long)s * n_rx + r) * n_sc + a]), e)
+                                             + I * ldexp(cimag(codes[((long long)s * n_rx + r) * n_sc + a]), e);
+                    acc += conj(wq[r * n_beams + b]) * x;
                 }
-                for (int b = 0; b < n_beams; ++b) {
-                    cplx acc = 0;
-                    for (int r = 0; r < n_rx; ++r) acc += conj(wv[r * n_beams + b]) * xq[r];
-                    beam[((long long)s * n_sc + a) * n_beams + b] = E >= 128 ? NAN : acc * ldexp(1.0, E) * wscale[b];
-                }
+                beam[((long long)s * n_sc + a) * n_beams + b] = acc;
             }
-        }
-    free(xq);
-    free(wv);
-    free(wscale);
-    free(ew);
+    free(wq);
 }

@@ -1,6 +1,7 @@
 """Pins of the oracle's FP8 (E4M3) form of the beamforming product: the rounding against the format's own bit
 definition and a library cast, the power-of-two block scale against its definition, the block quantiser's
-error bound, and the block-scaled product against plain products of exactly known operands."""
+error bound, and the block-scaled product against the pinned FP64 product (orc_beamform) of exactly
+representable operands and of operands quantised by the pinned row quantiser."""
 import numpy as np
 import pytest
 
@@ -102,9 +103,9 @@ def test_nonfinite_block_is_marked(orc):
     assert np.all(np.isnan(codes[0, 128:]))
 
 
-def test_fp8_product_is_the_plain_product_when_alignment_is_exact(orc):
-    """Codes that are E4M3 values on a coarse grid survive every alignment shift exactly, so the block-scaled
-    product must equal the plain W^H x of the dequantised operands (brute force, in the test)."""
+def test_fp8_product_of_coarse_grid_operands_by_brute_force(orc):
+    """Codes on a coarse E4M3 grid and weights k/8 (exact at their block scale): the block-scaled product is
+    W^H x of the dequantised operands, summed here by brute force."""
     n_sym, n_rx, n_sc, n_beams = 2, 20, 260, 3
     codes = (RNG.integers(-7, 8, (n_sym, n_rx, n_sc)) + 1j * RNG.integers(-7, 8, (n_sym, n_rx, n_sc))) * 16.0
     exps = RNG.integers(-3, 3, (n_sym, n_rx, 3)).astype(np.int32)
@@ -117,13 +118,54 @@ def test_fp8_product_is_the_plain_product_when_alignment_is_exact(orc):
     assert np.allclose(beam, want, rtol=0, atol=1e-12)
 
 
-def test_fp8_product_rounds_a_shift_into_the_subnormal_range(orc):
-    """Hand case: two antennas, one subcarrier, W = [1, 1]^T. Antenna 1's block exponent is 8 below antenna
-    0's, so its code 1.125 becomes 1.125 * 2^-8 = 2.25 * 2^-9, which E4M3 rounds to 2 * 2^-9."""
+def test_fp8_product_keeps_small_blocks_exact(orc):
+    """Hand case: two antennas, one subcarrier, W = [1, 1]^T. Antenna 1's block exponent is 8 below antenna 0's;
+    the block-scaled product adds 1.125 * 2^-8 exactly (no operand is re-rounded onto another block's grid)."""
     codes = np.array([[[2.0], [1.125]]], complex)                # [sym][rx][sc]
     exps = np.array([[[0], [-8]]], np.int32)
     W = np.array([[1.0], [1.0]], complex)                        # block max 1 -> exponent -8, code 256
     beam = orc.beamform_fp8(codes, exps, W)
-    assert beam[0, 0, 0] == pytest.approx(2.0 + 2.0 * 2.0 ** -9, abs=0)
+    assert beam[0, 0, 0] == 2.0 + 1.125 * 2.0 ** -8
     exps_nan = np.array([[[0], [128]]], np.int32)
     assert np.isnan(orc.beamform_fp8(codes, exps_nan, W)[0, 0, 0])
+
+
+def _e4m3_values(shape):
+    """Random finite E4M3 values (every code but NaN), from the format definition."""
+    return np.array(FINITE)[RNG.integers(0, len(FINITE), shape)]
+
+
+def test_fp8_product_equals_the_fp64_product_of_representable_operands(orc):
+    """Samples that are E4M3 values times their block scales and weights that are E4M3 values on their own
+    block's scale are reproduced exactly by the quantisation, so the FP8 product must equal the pinned FP64
+    beamforming product orc_beamform of the same operands (130 antennas: two weight blocks)."""
+    n_sym, n_rx, n_sc, n_beams = 2, 130, 200, 3
+    codes = _e4m3_values((n_sym, n_rx, n_sc)) + 1j * _e4m3_values((n_sym, n_rx, n_sc))
+    exps = RNG.integers(-20, 20, (n_sym, n_rx, 2)).astype(np.int32)
+    x = codes * 2.0 ** np.repeat(exps, 128, axis=2)[:, :, :n_sc]
+    # weights: E4M3 values whose block maximum is exactly 448 * 2^e_w, so the block exponent is e_w
+    ew = np.array([[-12, -3], [-9, -9], [0, -20]])                 # [beam][block]
+    W = _e4m3_values((n_rx, n_beams)) + 1j * _e4m3_values((n_rx, n_beams))
+    for b in range(n_beams):
+        W[0, b] = 448.0
+        W[128, b] = 448.0
+        W[:128, b] *= 2.0 ** ew[b, 0]
+        W[128:, b] *= 2.0 ** ew[b, 1]
+    beam = orc.beamform_fp8(codes, exps, W)
+    want = orc.beamform(x, W)
+    assert np.max(np.abs(beam - want)) <= 1e-13 * np.max(np.abs(want))
+
+
+def test_fp8_product_quantises_w_like_the_row_quantiser(orc):
+    """Arbitrary W: the product equals orc_beamform of the samples and of W quantised by the pinned row
+    quantiser (orc_e4m3_quant_rows over W's beam rows: blocks of 128 antennas)."""
+    n_sym, n_rx, n_sc, n_beams = 1, 300, 140, 5
+    codes = _e4m3_values((n_sym, n_rx, n_sc)) + 1j * _e4m3_values((n_sym, n_rx, n_sc))
+    exps = RNG.integers(-6, 6, (n_sym, n_rx, 2)).astype(np.int32)
+    x = codes * 2.0 ** np.repeat(exps, 128, axis=2)[:, :, :n_sc]
+    W = (RNG.standard_normal((n_rx, n_beams)) + 1j * RNG.standard_normal((n_rx, n_beams))) * 10.0 ** RNG.integers(-3, 3, (1, n_beams))
+    cw, ew = orc.e4m3_quant_rows(W.T)
+    Wq = (cw * 2.0 ** np.repeat(ew, 128, axis=1)[:, :n_rx]).T
+    beam = orc.beamform_fp8(codes, exps, W)
+    want = orc.beamform(x, Wq)
+    assert np.max(np.abs(beam - want)) <= 1e-13 * np.max(np.abs(want))
