@@ -24,7 +24,8 @@
  *
  * Supported shapes: n_fft a power of two in [64, 4096]; 1 <= n_sc <= n_fft; 1 <= n_beams <= 64;
  * mixed form: n_rx a multiple of 8 and n_beams a multiple of 8; FP8 form: n_rx a multiple of 16 up to 512
- * and n_beams a multiple of 8;
+ * and n_beams a multiple of 8; in both, W's FP16 image (4 n_rx n_beams FP16 values) must fit in shared
+ * memory with the operand ring (up to 256 antennas at 64 beams);
  * 1 <= n_layers <= 32 and n_layers <= n_beams; 1 <= comb <= n_sc; n_sym = 14 with two distinct DMRS
  * symbols; 1 <= n_rx <= 1024; qam_bits 2 (QPSK) or 4 (16-QAM).
  */
@@ -50,13 +51,16 @@ typedef enum {
 /* Arithmetic form of the chain. */
 typedef enum {
     PUSCH_FORM_FP32 = 0,   /* plain: FFT and beamforming in FP32, intermediates stored as c64           */
-    PUSCH_FORM_MIXED = 1,  /* FFT in FP32 registers with its output stored as FP16; beamforming on the
-                              tcgen05 tensor cores with FP16 operands and FP32 accumulation.              */
+    PUSCH_FORM_MIXED = 1,  /* FFT output stored as FP16 (4096-point rows of FP16 samples on the tcgen05
+                              tensor cores with FP16 operands and FP32 accumulation, other shapes in FP32
+                              registers); beamforming on the tensor cores with FP16 operands and FP32
+                              accumulation.                                                              */
     PUSCH_FORM_FP8 = 2     /* FFT output stored as FP8 E4M3 with one power-of-two scale per 128
                               subcarriers of each (symbol, antenna) row; W quantised to E4M3 with one
-                              power-of-two scale per (beam, 128 antennas); beamforming on the tcgen05
-                              tensor cores (kind::f8f6f4) with FP32 accumulation. Channel estimation and
-                              detection stay FP32 in every form.                                        */
+                              power-of-two scale per (beam, 128 antennas); beamforming is the
+                              block-scaled product of the two quantised operands, on the tcgen05 tensor
+                              cores with FP32 accumulation (the codes enter the MMA as their exact FP16
+                              values). Channel estimation and detection stay FP32 in every form.         */
 } pusch_form;
 
 /* Device status words written by the detection kernels (uint32_t status[4]):

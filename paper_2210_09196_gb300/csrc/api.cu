@@ -91,7 +91,7 @@ pusch_status validate_cfg(const pusch_cell_cfg *c) {
         pusch::Geometry g = pusch::make_geometry(*c);
         if (!pusch::bf_fp8_supported(g))
             return fail(PUSCH_ERR_UNSUPPORTED, "FP8 form needs n_beams a multiple of 8 and n_rx a multiple of 16 "
-                                               "up to 512");
+                                               "up to 512 whose W operand fits in shared memory");
     }
     return PUSCH_OK;
 }

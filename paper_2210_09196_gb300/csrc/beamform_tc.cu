@@ -10,7 +10,7 @@
 //
 // A is the FFT output [rows][2 N_R][pitch] (subcarriers contiguous): an MN-major operand, copied by TMA
 // in K chunks with 128-byte swizzling into a ring of shared-memory stages. B is built once per CTA from W
-// in the no-swizzle K-major core-matrix layout and stays resident.
+// in the no-swizzle K-major core-matrix layout and stays resident. Both operands reach the MMA as FP16.
 //
 // Warp roles (persistent CTAs, one per SM):
 //   warp 0      TMA producer: streams the (tile, K chunk) sequence into the stage ring;
@@ -18,16 +18,20 @@
 //               accumulators and commits the chunk's stage back to the producer;
 //   warps 2-5   epilogue: tcgen05.ld of the finished accumulator (one 32-lane quarter per warp), scaling
 //               (FP8 form), stores of the c64 rows; the other accumulator is being filled meanwhile;
-//   warps 6-9   FP8 form only: align each landed chunk to the tile's common scale (below).
+//   warps 6-9   FP8 form only: convert each landed chunk of E4M3 codes to FP16 for the MMA (below).
 //
 // FP8 form. The FFT stores each (symbol, antenna) row as E4M3 codes with one power-of-two scale 2^e per
-// 128 subcarriers; W is quantised in the kernel with one power-of-two scale per (beam, 128 antennas).
-// Because the M tile is the 128-subcarrier block, a tile's samples carry one exponent e_r per antenna.
-// The rescale warps shift every antenna's codes to the tile's largest exponent E (code * 2^(e_r - E),
-// re-rounded to E4M3, which is exact unless the shifted value leaves the normal range) and W's blocks are
-// likewise shifted to each beam's largest exponent E_b when B is built, so one accumulator holds
-// D * 2^-(E + E_b) and the epilogue multiplies by 2^E * 2^E_b. A non-finite scale (a non-finite sample in
-// the block) makes the tile's output NaN, so detection reports it.
+// 128 subcarriers; W is quantised in the kernel to E4M3 with one power-of-two scale per (beam, 128
+// antennas). The product is the block-scaled product of these two quantised operands: every operand keeps
+// its own scale, nothing is re-rounded. E4M3 codes move through HBM and the TMA ring (one byte each); the
+// convert warps write each landed chunk into a second ring as FP16 values code * 2^(e_r - E), E the
+// largest exponent among the tile's antennas, and B holds W's codes as FP16 values code * 2^(e_w - E_b),
+// E_b the largest block exponent of beam b. FP16 holds a 4-significant-bit E4M3 code shifted down by up
+// to 15 octaves exactly (its smallest step is 2^-24, an E4M3 code's 2^-9 shifted 15 times), so the MMA
+// (kind::f16, FP32 accumulation) sums exact products; one accumulator holds D * 2^-(E + E_b) and the
+// epilogue multiplies by 2^E * 2^E_b. Blocks more than 15 octaves below the largest of their tile round
+// in FP16 (below 2^-15 of the tile's largest sample, well under the FP32 sum's own rounding). A
+// non-finite scale (a non-finite sample in the block) makes the tile's output NaN, so detection reports it.
 //
 // Every wait is bounded (%globaltimer, 2 s); on expiry the CTA records a timeout in err_word bit 0, all
 // roles leave their loops, in-flight copies and MMAs are drained (bounded) and TMEM is freed.
@@ -63,11 +67,6 @@ __device__ __forceinline__ uint32_t h2_from_e4m3x2(uint16_t v) {          // two
     asm("cvt.rn.f16x2.e4m3x2 %0, %1;" : "=r"(r) : "h"(v));
     return r;
 }
-__device__ __forceinline__ uint16_t e4m3x2_from_h2(uint32_t v) {          // f16x2 -> two codes
-    uint16_t r;
-    asm("cvt.rn.satfinite.e4m3x2.f16x2 %0, %1;" : "=h"(r) : "r"(v));
-    return r;
-}
 __device__ __forceinline__ float2 e4m3x2_to_float2(uint16_t v) {
     const uint32_t h = h2_from_e4m3x2(v);
     return __half22float2(*reinterpret_cast<const __half2 *>(&h));
@@ -93,12 +92,14 @@ struct TcArgs {
     int n_rx, n_beams, n_sc, n_mtiles, n_blk;
     int K, N, chunk_rows, n_chunks, n_stages, tmem_cols;
     uint32_t stage_bytes, b_bytes;
+    uint32_t land_bytes, land_off;  // FP8: landing stage of E4M3 codes and the landing ring's offset
+    int n_land;                     // FP8: landing stages (the TMA ring; the FP16 ring has n_stages)
     int stage_out;             // 1: the epilogue writes through shared memory and TMA tensor stores
     long long total_tiles;
 };
 
 struct TcShared {
-    uint64_t full[kMaxStages], ready[kMaxStages], empty[kMaxStages];
+    uint64_t full[kMaxStages], ready[kMaxStages], empty[kMaxStages], lempty[kMaxStages];
     uint64_t tfull[2], tempty[2], drain;
     uint32_t tmem_base;
     int abort;
@@ -114,7 +115,7 @@ beamform_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_consta
                    const float2 *__restrict__ W, const float *__restrict__ scales, float2 *__restrict__ beam,
                    uint32_t *__restrict__ err) {
     constexpr int kThreads = FP8 ? 320 : 192;
-    constexpr int kKStep = FP8 ? 32 : 16;       // K per MMA instruction (32 bytes of K)
+    constexpr int kKStep = 16;                  // K per MMA instruction (32 bytes of FP16)
     extern __shared__ uint8_t smem_raw[];
     __shared__ TcShared sh;
 
@@ -128,7 +129,7 @@ beamform_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_consta
     // output staging (stage_out): per epilogue warp, 32 rows x N floats as N/16 boxes of 32 x 16 floats with
     // 64-byte swizzling (16-byte chunk c of row r at r * 64 + ((c ^ ((r >> 1) & 3)) << 4)), 2 KB each
     const uint32_t out_off = (uint32_t)g.n_stages * g.stage_bytes + ((g.b_bytes + 1023u) & ~1023u);
-    const uint32_t b_sbo = FP8 ? (uint32_t)K * 8 : (uint32_t)K * 16;  // bytes between 8-row groups of B
+    const uint32_t b_sbo = (uint32_t)K * 16;  // bytes between 8-row groups of B
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     volatile int *abort = &sh.abort;
@@ -198,7 +199,8 @@ beamform_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_consta
             sh.wsc[b] = exp2_int(e);
         }
         __syncthreads();
-        // pass 2: element (n, k) at (n/8)*SBO + (k/16)*128 + (n%8)*16 + (k%16)
+        // pass 2: the codes as FP16 values on the beam's scale, element (n, k) at (n/8)*SBO + (k/8)*128 +
+        // (n%8)*16 + (k%8)*2 (as the mixed form)
         for (int base0 = 0; base0 < total; base0 += kThreads * kBatch) {
             float2 w[kBatch];
 #pragma unroll
@@ -213,23 +215,21 @@ beamform_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_consta
                 const int r = idx / g.n_beams, b = idx - r * g.n_beams;
                 const int eb = sh.wexp[b], e_blk = sh.ew[b * 4 + (r >> 7)];
                 const int d = eb - e_blk;                     // shift of this block to the beam exponent
-                uint8_t qr, qi;
-                if (eb >= 128) {
-                    qr = qi = 0;                              // the beam's scale is NaN; codes unused
-                } else {
+                __half qr = __float2half_rn(0.f), qi = qr, nqi = qr;
+                if (eb < 128) {                               // else the beam's scale is NaN; values unused
                     const float inv = exp2_int(-e_blk);      // 2^-e_blk, e_blk in [-126, 120]
                     const float2 c = e4m3x2_to_float2(float2_to_e4m3x2(make_float2(w[u].x * inv, w[u].y * inv)));
                     const float sh2 = exp2_int(d > 40 ? -40 : -d);
-                    const uint16_t q = float2_to_e4m3x2(make_float2(c.x * sh2, c.y * sh2));
-                    qr = (uint8_t)(q & 0xFFu);
-                    qi = (uint8_t)(q >> 8);
+                    qr = __float2half_rn(c.x * sh2);
+                    qi = __float2half_rn(c.y * sh2);
+                    nqi = __float2half_rn(-c.y * sh2);
                 }
-                auto put = [&](int n, int k, uint8_t v) {
-                    gB[(n >> 3) * b_sbo + (k >> 4) * 128 + (n & 7) * 16 + (k & 15)] = v;
+                auto put = [&](int n, int k, __half v) {
+                    *reinterpret_cast<__half *>(gB + (n >> 3) * b_sbo + (k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2) = v;
                 };
                 put(2 * b, 2 * r, qr);
                 put(2 * b, 2 * r + 1, qi);
-                put(2 * b + 1, 2 * r, (uint8_t)(qi ^ 0x80u));   // -Im W: sign flip of the code
+                put(2 * b + 1, 2 * r, nqi);
                 put(2 * b + 1, 2 * r + 1, qr);
             }
         }
@@ -237,10 +237,11 @@ beamform_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_consta
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 
     if (tid == 0) {
-        for (int s = 0; s < g.n_stages; ++s) {
+        for (int s = 0; s < kMaxStages; ++s) {   // both rings (FP8: n_land may exceed n_stages)
             mbar_init(smem_u32(&sh.full[s]), 1);
             mbar_init(smem_u32(&sh.ready[s]), 4);
             mbar_init(smem_u32(&sh.empty[s]), 1);
+            mbar_init(smem_u32(&sh.lempty[s]), 4);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(smem_u32(&sh.tfull[b]), 1);
@@ -263,6 +264,7 @@ beamform_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_consta
     const long long n_my =
         g.total_tiles > blockIdx.x ? (g.total_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
     const int NS = g.n_stages;
+    const int NR = FP8 ? g.n_land : NS;   // stages of the TMA ring
 
     if (warp == 0) {
         // ------------------------------------------------------------------ TMA producer
@@ -274,19 +276,22 @@ beamform_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_consta
                 const long long row = t / g.n_mtiles;
                 const int mt = (int)(t - row * g.n_mtiles);
                 for (int c = 0; c < g.n_chunks; ++c, ++gch) {
-                    const int s = (int)(gch % NS);
-                    const uint32_t ph = (uint32_t)((gch / NS) & 1);
-                    if (!mbar_wait(smem_u32(&sh.empty[s]), ph ^ 1u, abort, err)) {
+                    const int s = (int)(gch % NR);
+                    const uint32_t ph = (uint32_t)((gch / NR) & 1);
+                    // FP8: the landing stage is free once the convert warps have read it; FP16: once the MMAs
+                    // of its previous chunk have completed
+                    if (!mbar_wait(smem_u32(FP8 ? &sh.lempty[s] : &sh.empty[s]), ph ^ 1u, abort, err)) {
                         ok = false;
                         break;
                     }
                     const uint32_t bar = smem_u32(&sh.full[s]);
-                    const uint32_t dst = sA + (uint32_t)s * g.stage_bytes;
                     const int y = (int)(row * K) + c * g.chunk_rows;
-                    mbar_expect_tx(bar, g.stage_bytes);
                     if constexpr (FP8) {
-                        tma_load_2d(dst, &tmap, mt * kTileM, y, bar);
+                        mbar_expect_tx(bar, g.land_bytes);
+                        tma_load_2d(base + g.land_off + (uint32_t)s * g.land_bytes, &tmap, mt * kTileM, y, bar);
                     } else {
+                        const uint32_t dst = sA + (uint32_t)s * g.stage_bytes;
+                        mbar_expect_tx(bar, g.stage_bytes);
                         tma_load_2d(dst, &tmap, mt * kTileM, y, bar);
                         tma_load_2d(dst + (uint32_t)g.chunk_rows * 128, &tmap, mt * kTileM + 64, y, bar);
                     }
@@ -294,8 +299,8 @@ beamform_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_consta
             }
             if (*abort) {
                 // drain: the latest copy issued into each stage (bounded)
-                for (long long j = gch - 1; j >= 0 && j >= gch - NS; --j)
-                    mbar_drain(smem_u32(&sh.full[(int)(j % NS)]), (uint32_t)((j / NS) & 1));
+                for (long long j = gch - 1; j >= 0 && j >= gch - NR; --j)
+                    mbar_drain(smem_u32(&sh.full[(int)(j % NR)]), (uint32_t)((j / NR) & 1));
             }
         }
     } else if (warp == 1) {
@@ -314,15 +319,10 @@ beamform_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_consta
                 for (int c = 0; c < g.n_chunks; ++c, ++gch) {
                     const int s = (int)(gch % NS);
                     const uint32_t ph = (uint32_t)((gch / NS) & 1);
-                    if (!mbar_wait(smem_u32(&sh.full[s]), ph, abort, err)) {
+                    // FP8: the convert warps have written the chunk's FP16 stage (after its landing)
+                    if (!mbar_wait(smem_u32(FP8 ? &sh.ready[s] : &sh.full[s]), ph, abort, err)) {
                         ok = false;
                         break;
-                    }
-                    if constexpr (FP8) {
-                        if (!mbar_wait(smem_u32(&sh.ready[s]), ph, abort, err)) {
-                            ok = false;
-                            break;
-                        }
                     }
                     fence_after_sync();
                     const int rows_here = min(g.chunk_rows, K - c * g.chunk_rows);
@@ -331,7 +331,7 @@ beamform_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_consta
                     for (int ks = 0; ks < rows_here / kKStep; ++ks) {
                         const uint64_t ad = smem_desc(a0 + (uint32_t)ks * (kKStep * 128), a_lbo, 1024, 2);
                         const uint64_t bd = smem_desc(sB + (uint32_t)(kb0 + ks) * 256, 128, b_sbo, 0);
-                        mma<FP8>(d, ad, bd, idesc, (c > 0 || ks > 0) ? 1u : 0u);
+                        mma<false>(d, ad, bd, idesc, (c > 0 || ks > 0) ? 1u : 0u);
                     }
                     mma_commit(smem_u32(&sh.empty[s]));
                 }
@@ -413,9 +413,10 @@ beamform_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_consta
         }
         if (g.stage_out && lane == 0) bulk_wait0();        // stores complete before the CTA's shared memory goes
     } else if constexpr (FP8) {
-        // ------------------------------------------------------------------ FP8: align chunks to the tile scale
+        // ------------------------------------------------------------------ FP8: codes to FP16
         // Each of the four warps derives the tile exponent E itself (no cross-warp barrier, so an abort in
-        // one warp cannot strand the others) and shifts the K rows u = 32 w + lane (mod 128) of each chunk.
+        // one warp cannot strand the others) and converts the 16-byte pieces u = 32 w + lane (mod 128) of
+        // each landed chunk.
         const int w4 = warp - 6;
         long long gch = 0;
         bool ok = true;
@@ -431,62 +432,60 @@ beamform_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_consta
             __syncwarp();                                    // this warp's previous tile no longer reads shift[]
             for (int r = lane; r < g.n_rx; r += 32) {
                 const int d = E - scale_exp(__ldg(&sc[r]));
-                sh.shift[w4][r] = (uint8_t)(d > 19 ? 19 : d);
+                sh.shift[w4][r] = (uint8_t)(d > 25 ? 25 : d);
             }
             __syncwarp();
             for (int c = 0; c < g.n_chunks; ++c, ++gch) {
-                const int s = (int)(gch % NS);
-                const uint32_t ph = (uint32_t)((gch / NS) & 1);
-                const bool okw = mbar_wait(smem_u32(&sh.full[s]), ph, abort, err);
+                const int s = (int)(gch % NS), sl = (int)(gch % NR);
+                const uint32_t ph = (uint32_t)((gch / NS) & 1), phl = (uint32_t)((gch / NR) & 1);
+                // the chunk has landed, and the MMAs of the FP16 stage's previous chunk have completed
+                bool okw = mbar_wait(smem_u32(&sh.full[sl]), phl, abort, err);
+                okw = okw && mbar_wait(smem_u32(&sh.empty[s]), ph ^ 1u, abort, err);
                 if (!__all_sync(0xFFFFFFFFu, okw)) {
                     ok = false;
                     break;
                 }
-                uint8_t *stage = gbase + (size_t)s * g.stage_bytes;
+                const uint8_t *land = gbase + g.land_off + (size_t)sl * g.land_bytes;
+                uint8_t *f16s = gbase + (size_t)s * g.stage_bytes;
                 const int k0 = c * g.chunk_rows;
                 const int rows_here = min(g.chunk_rows, K - k0);
-                // A K row (one antenna's re or im plane over the tile's 128 subcarriers) is 128 contiguous
-                // bytes of the swizzled stage and takes one factor 2^-d, so the swizzle does not matter here.
-                // code * 2^-d is exact in binary16 whenever E4M3 can represent it (4 significant bits,
-                // >= 2^-13); smaller values round to E4M3 zero either way; d >= 19 leaves only zeros.
-                // Every unit takes the same path (a warp covers four rows with different shifts, and a
-                // branch on the shift diverged): 2^-0 = 1 leaves a code unchanged, and a shift of 19 or more
-                // (2^-19 is a binary16 subnormal) rounds every code to zero.
-                for (int u0 = w4 * 32 + lane; u0 < rows_here * 8; u0 += 128 * 4) {
-                    uint4 v[4];
-                    __half2 f2[4];
+                const uint32_t half_off = (uint32_t)g.chunk_rows * 128;
+                // Landed K row k (one antenna's re or im plane over the tile's 128 subcarriers) is 128 bytes
+                // with 16-byte piece j (subcarriers 16 j ..) at piece j ^ (k % 8); its FP16 image is two
+                // 64-subcarrier halves of 128-byte rows with 16-byte piece q (8 subcarriers) at q ^ (k % 8),
+                // the layout a 128-byte-swizzled TMA box of FP16 planes has. Every value of the row takes the
+                // factor 2^-d of its antenna (d = E - e_r): exact in binary16 up to d = 15 (see above).
+                for (int u = w4 * 32 + lane; u < rows_here * 8; u += 128) {
+                    const int k = u >> 3, j = u & 7;
+                    const int d = sh.shift[w4][(k0 + k) >> 1];
+                    // 2^-d in binary16: normal for d <= 14, subnormal 2^-24 * 2^(24 - d) up to 24, zero beyond
+                    __half2_raw fr;
+                    fr.x = fr.y = d <= 14 ? (unsigned short)((15 - d) << 10)
+                                          : (d <= 24 ? (unsigned short)(1u << (24 - d)) : (unsigned short)0);
+                    const __half2 f2 = *reinterpret_cast<const __half2 *>(&fr);
+                    const uint4 v = *reinterpret_cast<const uint4 *>(land + (size_t)k * 128 + ((j ^ (k & 7)) << 4));
+                    const uint32_t in[4] = {v.x, v.y, v.z, v.w};
+                    uint32_t o[8];
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        const int u = u0 + 128 * q;
-                        const int d = u < rows_here * 8 ? sh.shift[w4][(k0 + (u >> 3)) >> 1] : 0;
-                        // 2^-d in binary16: normal for d <= 14, subnormal 2^-24 * 2^(24 - d) beyond
-                        __half2_raw fr;
-                        fr.x = fr.y = d <= 14 ? (unsigned short)((15 - d) << 10) : (unsigned short)(1u << (24 - d));
-                        f2[q] = *reinterpret_cast<const __half2 *>(&fr);
-                        if (u < rows_here * 8)
-                            v[q] = *reinterpret_cast<const uint4 *>(stage + (size_t)(u >> 3) * 128 + (u & 7) * 16);
+                        const uint32_t lo = h2_from_e4m3x2((uint16_t)(in[q] & 0xFFFFu));
+                        const uint32_t hi = h2_from_e4m3x2((uint16_t)(in[q] >> 16));
+                        const __half2 l2 = __hmul2(*reinterpret_cast<const __half2 *>(&lo), f2);
+                        const __half2 h2 = __hmul2(*reinterpret_cast<const __half2 *>(&hi), f2);
+                        o[2 * q] = *reinterpret_cast<const uint32_t *>(&l2);
+                        o[2 * q + 1] = *reinterpret_cast<const uint32_t *>(&h2);
                     }
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int u = u0 + 128 * q;
-                        if (u >= rows_here * 8) continue;
-                        uint32_t w[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            const uint32_t lo = h2_from_e4m3x2((uint16_t)(w[j] & 0xFFFFu));
-                            const uint32_t hi = h2_from_e4m3x2((uint16_t)(w[j] >> 16));
-                            const __half2 l2 = __hmul2(*reinterpret_cast<const __half2 *>(&lo), f2[q]);
-                            const __half2 h2 = __hmul2(*reinterpret_cast<const __half2 *>(&hi), f2[q]);
-                            w[j] = (uint32_t)e4m3x2_from_h2(*reinterpret_cast<const uint32_t *>(&l2)) |
-                                   ((uint32_t)e4m3x2_from_h2(*reinterpret_cast<const uint32_t *>(&h2)) << 16);
-                        }
-                        *reinterpret_cast<uint4 *>(stage + (size_t)(u >> 3) * 128 + (u & 7) * 16) =
-                            make_uint4(w[0], w[1], w[2], w[3]);
-                    }
+                    uint8_t *dst = f16s + (size_t)(j >> 2) * half_off + (size_t)k * 128;
+                    const int q0 = 2 * (j & 3);
+                    *reinterpret_cast<uint4 *>(dst + ((q0 ^ (k & 7)) << 4)) = make_uint4(o[0], o[1], o[2], o[3]);
+                    *reinterpret_cast<uint4 *>(dst + (((q0 + 1) ^ (k & 7)) << 4)) = make_uint4(o[4], o[5], o[6], o[7]);
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(&sh.ready[s]));
+                if (lane == 0) {
+                    mbar_arrive(smem_u32(&sh.ready[s]));
+                    mbar_arrive(smem_u32(&sh.lempty[sl]));
+                }
             }
         }
     }
@@ -504,7 +503,8 @@ beamform_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_consta
 struct Plan {
     bool ok;
     int chunk_rows, n_chunks, n_stages, tmem_cols, stage_out;
-    uint32_t stage_bytes, b_bytes;
+    uint32_t stage_bytes, b_bytes, land_bytes, land_off;
+    int n_land;
     size_t smem;
 };
 
@@ -514,25 +514,40 @@ struct Plan {
 // (2 stages are accepted at 64 rows). A tuning (chunk rows, staged) is taken when it fits with >= 2 stages.
 Plan plan_for(const Geometry &g, bool fp8, int rows, int staged) {
     Plan p{};
-    const int elem = fp8 ? 1 : 2;
     const int K = 2 * g.n_rx, N = 2 * g.n_beams;
-    p.b_bytes = (uint32_t)((size_t)N * K * elem);
+    p.b_bytes = (uint32_t)((size_t)N * K * 2);
     const size_t fixed = 1024 + sizeof(TcShared) + 256 + (((size_t)p.b_bytes + 1023) & ~(size_t)1023);
     int cols = 32;
     while (cols < 2 * N) cols *= 2;
     p.tmem_cols = cols;
     const size_t out_b = staged ? (size_t)512 * N : 0;
     const int cr = K < rows ? K : rows;
-    const uint32_t sb = (uint32_t)kTileM * elem * cr;
+    const uint32_t sb = (uint32_t)kTileM * 2 * cr;           // FP16 stage
+    const uint32_t lb = fp8 ? (uint32_t)kTileM * cr : 0u;    // FP8: E4M3 landing stage
     const long long avail = (long long)kSmemLimit - (long long)(fixed + out_b);
-    int ns = avail > 0 ? (int)(avail / sb) : 0;
-    if (ns > kMaxStages) ns = kMaxStages;
+    int ns = 0, nl = 0;
+    if (!fp8) {
+        ns = avail > 0 ? (int)(avail / sb) : 0;
+        if (ns > kMaxStages) ns = kMaxStages;
+    } else {
+        // three FP16 stages when that leaves at least four landing stages, else two; the rest lands codes
+        for (ns = 3; ns >= 2; --ns) {
+            const long long rest = avail - (long long)ns * sb;
+            nl = rest > 0 ? (int)(rest / lb) : 0;
+            if (nl > kMaxStages) nl = kMaxStages;
+            if (nl >= 4) break;
+        }
+        if (nl < 2) ns = 0;
+    }
     p.chunk_rows = cr;
     p.stage_bytes = sb;
+    p.land_bytes = lb;
     p.n_stages = ns;
+    p.n_land = nl;
     p.stage_out = staged;
     p.n_chunks = (K + cr - 1) / cr;
-    p.smem = 1024 + (size_t)ns * sb + (((size_t)p.b_bytes + 1023) & ~(size_t)1023) + out_b;
+    p.land_off = (uint32_t)((size_t)ns * sb + (((size_t)p.b_bytes + 1023) & ~(size_t)1023) + out_b);
+    p.smem = 1024 + (size_t)ns * sb + (size_t)nl * lb + (((size_t)p.b_bytes + 1023) & ~(size_t)1023) + out_b;
     p.ok = cols <= 256 && ns >= 2;
     return p;
 }
@@ -543,7 +558,7 @@ Plan make_plan(const Geometry &g, bool fp8, const TcTune *tune = nullptr) {
         if (p.ok) return p;
     }
     for (int staged = 1; staged >= 0; --staged)
-        for (int rows = fp8 ? 256 : 128; rows >= 64; rows >>= 1) {
+        for (int rows = 128; rows >= 64; rows >>= 1) {
             const Plan p = plan_for(g, fp8, rows, staged);
             if (p.ok && (p.n_stages >= 3 || (!staged && rows == 64))) return p;
         }
@@ -607,6 +622,9 @@ cudaError_t launch_tc(const Geometry &g, int n_slots, const void *freq, const fl
     a.tmem_cols = p.tmem_cols;
     a.stage_bytes = p.stage_bytes;
     a.b_bytes = p.b_bytes;
+    a.land_bytes = p.land_bytes;
+    a.land_off = p.land_off;
+    a.n_land = p.n_land;
     a.stage_out = p.stage_out;
     a.total_tiles = rows * a.n_mtiles;
     auto kern = beamform_tc_kernel<FP8>;
@@ -631,7 +649,7 @@ int bf_tc_candidates(const Geometry &g, TcTune *out, int max_out) {
     if (g.form == PUSCH_FORM_FP32 || !shape_ok(g, fp8)) return 0;
     int n = 0, last_cr = -1, last_st = -1;
     for (int staged = 1; staged >= 0; --staged)
-        for (int rows = fp8 ? 256 : 128; rows >= 64; rows >>= 1) {
+        for (int rows = 128; rows >= 64; rows >>= 1) {
             const Plan p = plan_for(g, fp8, rows, staged);
             if (!p.ok || (p.chunk_rows == last_cr && staged == last_st) || n >= max_out) continue;
             out[n].chunk_rows = p.chunk_rows;

@@ -104,7 +104,7 @@ __device__ __forceinline__ bool factor_solve_rhs_lanes(float2 (&G)[NL], float2 *
         for (int j = 0; j < NL; ++j) {
             // two partial sums (even and odd k) halve the dependent FMA chain where the registers allow (the
             // 16-layer class is at its 128-register cap and spills with them)
-            constexpr bool kSplit = NL >= 32;
+            constexpr bool kSplit = NL >= 16;
             float2 sj = G[j], sj1 = make_float2(0.f, 0.f);
 #pragma unroll
             for (int k = 0; k < j; ++k) {
@@ -135,7 +135,7 @@ __device__ __forceinline__ bool factor_solve_rhs_lanes(float2 (&G)[NL], float2 *
     // right-hand sides per lane: lane i solves data symbols i, i + NL, ... (one for 16 and 32 lanes; the
     // small classes take several); a lane past the last symbol solves a copy of symbol 0 and discards it
     constexpr int RPL = (NR + NL - 1) / NL;
-    constexpr bool kSplitSolve = NL >= 32;  // as in the factorisation
+    constexpr bool kSplitSolve = NL >= 16;  // as in the factorisation
     float2 X[RPL][NL];
 #pragma unroll
     for (int r = 0; r < RPL; ++r) {
