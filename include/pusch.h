@@ -142,9 +142,10 @@ pusch_status pusch_destroy(pusch_handle *h);
 /* Bytes of device workspace pusch_create allocates for (cfg, max_slots). */
 pusch_status pusch_workspace_size(const pusch_cell_cfg *cfg, int max_slots, size_t *bytes);
 
-/* Number of elements between the re and im planes of one FFT output row of the mixed form (c16 planes:
- * n_sc rounded up to a multiple of 8) or of the FP8 form (byte planes: n_sc rounded up to a multiple of
- * 16), so that every plane starts on a 16-byte boundary. */
+/* Number of elements between the re and im planes of one FFT output row of the mixed form (binary16 planes:
+ * n_sc rounded up to a multiple of 64) or of the FP8 form (byte planes: n_sc rounded up to a multiple of
+ * 128), so that every plane starts on a 128-byte boundary (the tensor-core beamforming reads 128-byte rows
+ * of the planes, one L2 line each). */
 int pusch_sc_pitch(const pusch_cell_cfg *cfg);
 
 /* Bytes of the FFT output buffer (freq_out of pusch_ofdm_fft, freq_in of pusch_beamform) for n_slots slots

@@ -187,7 +187,7 @@ Geometry make_geometry(const pusch_cell_cfg &c) {
     g.cp1 = c.cp ? 288 * c.n_fft / 4096 : 0;
     g.slot_len = (long long)c.n_sym * c.n_fft + (c.cp ? g.cp0 + (long long)(c.n_sym - 1) * g.cp1 : 0);
     g.shift = c.shift_7p5khz;
-    g.sc_pitch = c.form == PUSCH_FORM_FP8 ? (c.n_sc + 15) & ~15 : (c.n_sc + 7) & ~7;
+    g.sc_pitch = sc_pitch_of(c.form, c.n_sc);
     for (int l = 0; l < 32; ++l) g.port[l] = l < c.n_layers ? c.port[l] : 0;
     g.dmrs_type = c.dmrs_type;
     if (c.dmrs_type == 1) {  // the estimate lives at the CDM pair centres: spacing 4, offset 1 + CDM group
@@ -221,7 +221,7 @@ const char *pusch_version(void) { return "pusch-gb300 0.1 (sm_103a)"; }
 
 int pusch_sc_pitch(const pusch_cell_cfg *cfg) {
     if (!cfg) return 0;
-    return cfg->form == PUSCH_FORM_FP8 ? (cfg->n_sc + 15) & ~15 : (cfg->n_sc + 7) & ~7;
+    return pusch::sc_pitch_of(cfg->form, cfg->n_sc);
 }
 
 size_t pusch_freq_bytes(const pusch_cell_cfg *cfg, int n_slots) {

@@ -135,104 +135,95 @@ beamform_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_consta
     volatile int *abort = &sh.abort;
 
     // ---------------------------------------------------------------- B operand (resident) from W
-    // W is read in coalesced batches of kBatch loads per thread in flight (the build is latency-bound
-    // otherwise: every CTA does it before its first MMA).
-    constexpr int kBatch = 8;
-    const int total = g.n_rx * g.n_beams;
-    if constexpr (!FP8) {
-        // element (n, k) at (n/8)*SBO + (k/8)*128 + (n%8)*16 + (k%8)*2
-        for (int base0 = 0; base0 < total; base0 += kThreads * kBatch) {
-            float2 w[kBatch];
-#pragma unroll
-            for (int u = 0; u < kBatch; ++u) {
-                const int idx = base0 + u * kThreads + tid;
-                w[u] = idx < total ? __ldg(&W[idx]) : make_float2(0.f, 0.f);
-            }
-#pragma unroll
-            for (int u = 0; u < kBatch; ++u) {
-                const int idx = base0 + u * kThreads + tid;
-                if (idx >= total) continue;
-                const int r = idx / g.n_beams, b = idx - r * g.n_beams;
-                const __half wr = __float2half_rn(w[u].x), wi = __float2half_rn(w[u].y),
-                             nwi = __float2half_rn(-w[u].y);
-                auto put = [&](int n, int k, __half v) {
-                    *reinterpret_cast<__half *>(gB + (n >> 3) * b_sbo + (k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2) = v;
-                };
-                put(2 * b, 2 * r, wr);
-                put(2 * b, 2 * r + 1, wi);
-                put(2 * b + 1, 2 * r, nwi);
-                put(2 * b + 1, 2 * r + 1, wr);
-            }
-        }
-    } else {
-        // pass 1: largest |Re|, |Im| per (beam, 128-antenna block) by shared atomics on the bit patterns
-        // (non-negative floats order like their bits); a non-finite component records +inf
+    // W [n_rx][n_beams] is staged through the (still unused) FP16 ring in pieces of whole antennas, every
+    // 8-byte element copied by cp.async so that a piece costs one round trip; B's 16-byte chunks (beam row n,
+    // 8 consecutive k = 4 antennas x (re, im)) are then written whole, element (n, k) at (n/8)*SBO +
+    // (k/8)*128 + (n%8)*16 + (k%8)*2. FP8: a first pass over the pieces takes the largest |Re|, |Im| per
+    // (beam, 128-antenna block) (shared atomics on the bit patterns: non-negative floats order like their
+    // bits; a non-finite component records +inf), the second writes the codes as FP16 values on the beam's
+    // scale.
+    {
+        float2 *Ws = reinterpret_cast<float2 *>(gbase);
+        const int nb = g.n_beams;
+        int P = (int)(((size_t)g.n_stages * g.stage_bytes) / ((size_t)nb * 8));
+        P = (P / 4) * 4;
+        if (P > g.n_rx) P = g.n_rx;
+        auto stage_piece = [&](int r0, int np) {
+            __syncthreads();                                 // the previous piece is consumed
+            const float2 *src = W + (size_t)r0 * nb;
+            const int cnt = np * nb;
+            for (int i2 = tid; i2 < cnt; i2 += kThreads)
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(Ws + i2)), "l"(src + i2) : "memory");
+            asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+            __syncthreads();
+        };
         const int n_kb = (g.n_rx + 127) / 128;
-        uint32_t *wmax = reinterpret_cast<uint32_t *>(sh.ew);
-        for (int i2 = tid; i2 < 64 * 4; i2 += kThreads) wmax[i2] = 0u;
-        __syncthreads();
-        for (int base0 = 0; base0 < total; base0 += kThreads * kBatch) {
-            float2 w[kBatch];
-#pragma unroll
-            for (int u = 0; u < kBatch; ++u) {
-                const int idx = base0 + u * kThreads + tid;
-                w[u] = idx < total ? __ldg(&W[idx]) : make_float2(0.f, 0.f);
-            }
-#pragma unroll
-            for (int u = 0; u < kBatch; ++u) {
-                const int idx = base0 + u * kThreads + tid;
-                if (idx >= total) continue;
-                const int r = idx / g.n_beams, b = idx - r * g.n_beams;
-                const float ax = fabsf(w[u].x), ay = fabsf(w[u].y);
-                const bool bad = !(ax <= FLT_MAX) || !(ay <= FLT_MAX);
-                atomicMax(&wmax[b * 4 + (r >> 7)], bad ? 0x7F800000u : __float_as_uint(fmaxf(ax, ay)));
-            }
-        }
-        __syncthreads();
-        for (int i2 = tid; i2 < g.n_beams * 4; i2 += kThreads)
-            sh.ew[i2] = (i2 & 3) < n_kb ? block_exp(__uint_as_float(wmax[i2])) : -126;
-        __syncthreads();
-        for (int b = tid; b < g.n_beams; b += kThreads) {
-            int e = -126;
-            for (int kb = 0; kb < n_kb; ++kb) e = max(e, sh.ew[b * 4 + kb]);
-            sh.wexp[b] = e;
-            sh.wsc[b] = exp2_int(e);
-        }
-        __syncthreads();
-        // pass 2: the codes as FP16 values on the beam's scale, element (n, k) at (n/8)*SBO + (k/8)*128 +
-        // (n%8)*16 + (k%8)*2 (as the mixed form)
-        for (int base0 = 0; base0 < total; base0 += kThreads * kBatch) {
-            float2 w[kBatch];
-#pragma unroll
-            for (int u = 0; u < kBatch; ++u) {
-                const int idx = base0 + u * kThreads + tid;
-                w[u] = idx < total ? __ldg(&W[idx]) : make_float2(0.f, 0.f);
-            }
-#pragma unroll
-            for (int u = 0; u < kBatch; ++u) {
-                const int idx = base0 + u * kThreads + tid;
-                if (idx >= total) continue;
-                const int r = idx / g.n_beams, b = idx - r * g.n_beams;
-                const int eb = sh.wexp[b], e_blk = sh.ew[b * 4 + (r >> 7)];
-                const int d = eb - e_blk;                     // shift of this block to the beam exponent
-                __half qr = __float2half_rn(0.f), qi = qr, nqi = qr;
-                if (eb < 128) {                               // else the beam's scale is NaN; values unused
-                    const float inv = exp2_int(-e_blk);      // 2^-e_blk, e_blk in [-126, 120]
-                    const float2 c = e4m3x2_to_float2(float2_to_e4m3x2(make_float2(w[u].x * inv, w[u].y * inv)));
-                    const float sh2 = exp2_int(d > 40 ? -40 : -d);
-                    qr = __float2half_rn(c.x * sh2);
-                    qi = __float2half_rn(c.y * sh2);
-                    nqi = __float2half_rn(-c.y * sh2);
+        if constexpr (FP8) {
+            uint32_t *wmax = reinterpret_cast<uint32_t *>(sh.ew);
+            for (int i2 = tid; i2 < 64 * 4; i2 += kThreads) wmax[i2] = 0u;
+            for (int r0 = 0; r0 < g.n_rx; r0 += P) {
+                const int np = min(P, g.n_rx - r0);
+                stage_piece(r0, np);
+                for (int i2 = tid; i2 < np * nb; i2 += kThreads) {
+                    const int r = r0 + i2 / nb, b = i2 - (i2 / nb) * nb;
+                    const float2 w = Ws[i2];
+                    const float ax = fabsf(w.x), ay = fabsf(w.y);
+                    const bool bad = !(ax <= FLT_MAX) || !(ay <= FLT_MAX);
+                    atomicMax(&wmax[b * 4 + (r >> 7)], bad ? 0x7F800000u : __float_as_uint(fmaxf(ax, ay)));
                 }
-                auto put = [&](int n, int k, __half v) {
-                    *reinterpret_cast<__half *>(gB + (n >> 3) * b_sbo + (k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2) = v;
-                };
-                put(2 * b, 2 * r, qr);
-                put(2 * b, 2 * r + 1, qi);
-                put(2 * b + 1, 2 * r, nqi);
-                put(2 * b + 1, 2 * r + 1, qr);
+            }
+            __syncthreads();
+            for (int i2 = tid; i2 < nb * 4; i2 += kThreads)
+                sh.ew[i2] = (i2 & 3) < n_kb ? block_exp(__uint_as_float(wmax[i2])) : -126;
+            __syncthreads();
+            for (int b = tid; b < nb; b += kThreads) {
+                int e = -126;
+                for (int kb = 0; kb < n_kb; ++kb) e = max(e, sh.ew[b * 4 + kb]);
+                sh.wexp[b] = e;
+                sh.wsc[b] = exp2_int(e);
             }
         }
+        const bool resident = P >= g.n_rx;                   // W already staged whole (FP8 pass 1)
+        for (int r0 = 0; r0 < g.n_rx; r0 += P) {
+            const int np = min(P, g.n_rx - r0);
+            if (FP8 && resident) __syncthreads();            // pass 1's exponents are visible
+            else stage_piece(r0, np);
+            const int nchunks = (np / 4) * N;
+            for (int c = tid; c < nchunks; c += kThreads) {
+                const int kcl = c / N, n = c - kcl * N;
+                const int b = n >> 1;
+                uint32_t h[4];
+#pragma unroll
+                for (int a4 = 0; a4 < 4; ++a4) {
+                    const float2 w = Ws[(4 * kcl + a4) * nb + b];
+                    __half re, im;
+                    if constexpr (FP8) {
+                        const int r = r0 + 4 * kcl + a4;
+                        const int eb = sh.wexp[b], e_blk = sh.ew[b * 4 + (r >> 7)];
+                        if (eb >= 128) {                     // the beam's scale is NaN; values unused
+                            re = im = __float2half_rn(0.f);
+                        } else {
+                            const float inv = exp2_int(-e_blk);   // 2^-e_blk, e_blk in [-126, 120]
+                            const float2 cq = e4m3x2_to_float2(float2_to_e4m3x2(make_float2(w.x * inv, w.y * inv)));
+                            const int d = eb - e_blk;             // shift of this block to the beam exponent
+                            const float sh2 = exp2_int(d > 40 ? -40 : -d);
+                            re = __float2half_rn(cq.x * sh2);
+                            im = __float2half_rn(cq.y * sh2);
+                        }
+                    } else {
+                        re = __float2half_rn(w.x);
+                        im = __float2half_rn(w.y);
+                    }
+                    // row 2b: (Re, Im); row 2b + 1: (-Im, Re)
+                    const __half lo = (n & 1) ? __hneg(im) : re, hi = (n & 1) ? re : im;
+                    h[a4] = (uint32_t)__half_as_ushort(lo) | ((uint32_t)__half_as_ushort(hi) << 16);
+                }
+                const int kc = r0 / 4 + kcl;
+                *reinterpret_cast<uint4 *>(gB + (size_t)(n >> 3) * b_sbo + (size_t)kc * 128 + (n & 7) * 16) =
+                    make_uint4(h[0], h[1], h[2], h[3]);
+            }
+        }
+        __syncthreads();                                     // B complete; the ring is free again
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 
@@ -455,30 +446,41 @@ beamform_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_consta
                 // 64-subcarrier halves of 128-byte rows with 16-byte piece q (8 subcarriers) at q ^ (k % 8),
                 // the layout a 128-byte-swizzled TMA box of FP16 planes has. Every value of the row takes the
                 // factor 2^-d of its antenna (d = E - e_r): exact in binary16 up to d = 15 (see above).
-                for (int u = w4 * 32 + lane; u < rows_here * 8; u += 128) {
-                    const int k = u >> 3, j = u & 7;
-                    const int d = sh.shift[w4][(k0 + k) >> 1];
-                    // 2^-d in binary16: normal for d <= 14, subnormal 2^-24 * 2^(24 - d) up to 24, zero beyond
-                    __half2_raw fr;
-                    fr.x = fr.y = d <= 14 ? (unsigned short)((15 - d) << 10)
-                                          : (d <= 24 ? (unsigned short)(1u << (24 - d)) : (unsigned short)0);
-                    const __half2 f2 = *reinterpret_cast<const __half2 *>(&fr);
-                    const uint4 v = *reinterpret_cast<const uint4 *>(land + (size_t)k * 128 + ((j ^ (k & 7)) << 4));
-                    const uint32_t in[4] = {v.x, v.y, v.z, v.w};
-                    uint32_t o[8];
+                // Four units per pass, their loads issued together.
+                for (int u0 = w4 * 32 + lane; u0 < rows_here * 8; u0 += 512) {
+                    uint4 v[4];
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        const uint32_t lo = h2_from_e4m3x2((uint16_t)(in[q] & 0xFFFFu));
-                        const uint32_t hi = h2_from_e4m3x2((uint16_t)(in[q] >> 16));
-                        const __half2 l2 = __hmul2(*reinterpret_cast<const __half2 *>(&lo), f2);
-                        const __half2 h2 = __hmul2(*reinterpret_cast<const __half2 *>(&hi), f2);
-                        o[2 * q] = *reinterpret_cast<const uint32_t *>(&l2);
-                        o[2 * q + 1] = *reinterpret_cast<const uint32_t *>(&h2);
+                        const int u = u0 + 128 * q, k = u >> 3, j = u & 7;
+                        if (u < rows_here * 8)
+                            v[q] = *reinterpret_cast<const uint4 *>(land + (size_t)k * 128 + ((j ^ (k & 7)) << 4));
                     }
-                    uint8_t *dst = f16s + (size_t)(j >> 2) * half_off + (size_t)k * 128;
-                    const int q0 = 2 * (j & 3);
-                    *reinterpret_cast<uint4 *>(dst + ((q0 ^ (k & 7)) << 4)) = make_uint4(o[0], o[1], o[2], o[3]);
-                    *reinterpret_cast<uint4 *>(dst + (((q0 + 1) ^ (k & 7)) << 4)) = make_uint4(o[4], o[5], o[6], o[7]);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int u = u0 + 128 * q, k = u >> 3, j = u & 7;
+                        if (u >= rows_here * 8) continue;
+                        const int d = sh.shift[w4][(k0 + k) >> 1];
+                        // 2^-d in binary16: normal for d <= 14, subnormal 2^-24 * 2^(24 - d) up to 24, zero beyond
+                        __half2_raw fr;
+                        fr.x = fr.y = d <= 14 ? (unsigned short)((15 - d) << 10)
+                                              : (d <= 24 ? (unsigned short)(1u << (24 - d)) : (unsigned short)0);
+                        const __half2 f2 = *reinterpret_cast<const __half2 *>(&fr);
+                        const uint32_t in[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
+                        uint32_t o[8];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const uint32_t lo = h2_from_e4m3x2((uint16_t)(in[e] & 0xFFFFu));
+                            const uint32_t hi = h2_from_e4m3x2((uint16_t)(in[e] >> 16));
+                            const __half2 l2 = __hmul2(*reinterpret_cast<const __half2 *>(&lo), f2);
+                            const __half2 h2 = __hmul2(*reinterpret_cast<const __half2 *>(&hi), f2);
+                            o[2 * e] = *reinterpret_cast<const uint32_t *>(&l2);
+                            o[2 * e + 1] = *reinterpret_cast<const uint32_t *>(&h2);
+                        }
+                        uint8_t *dst = f16s + (size_t)(j >> 2) * half_off + (size_t)k * 128;
+                        const int q0 = 2 * (j & 3);
+                        *reinterpret_cast<uint4 *>(dst + ((q0 ^ (k & 7)) << 4)) = make_uint4(o[0], o[1], o[2], o[3]);
+                        *reinterpret_cast<uint4 *>(dst + (((q0 + 1) ^ (k & 7)) << 4)) = make_uint4(o[4], o[5], o[6], o[7]);
+                    }
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
@@ -530,13 +532,12 @@ Plan plan_for(const Geometry &g, bool fp8, int rows, int staged) {
         ns = avail > 0 ? (int)(avail / sb) : 0;
         if (ns > kMaxStages) ns = kMaxStages;
     } else {
-        // three FP16 stages when that leaves at least four landing stages, else two; the rest lands codes
-        for (ns = 3; ns >= 2; --ns) {
-            const long long rest = avail - (long long)ns * sb;
-            nl = rest > 0 ? (int)(rest / lb) : 0;
-            if (nl > kMaxStages) nl = kMaxStages;
-            if (nl >= 4) break;
-        }
+        // two FP16 stages (the convert warps stay ahead of the MMAs); the rest of shared memory lands codes:
+        // the landing ring's bytes in flight set the load bandwidth
+        ns = 2;
+        const long long rest = avail - (long long)ns * sb;
+        nl = rest > 0 ? (int)(rest / lb) : 0;
+        if (nl > kMaxStages) nl = kMaxStages;
         if (nl < 2) ns = 0;
     }
     p.chunk_rows = cr;

@@ -80,6 +80,12 @@ inline std::vector<float2> fft_twiddle_table(int n_fft) {
     return tw;
 }
 
+// Elements between the re and im planes of an FFT output row (mixed and FP8 forms): every plane starts on a
+// 128-byte boundary (one L2 line), because the tensor-core beamforming reads 128-byte rows of the planes.
+inline int sc_pitch_of(int form, int n_sc) {
+    return form == PUSCH_FORM_FP8 ? (n_sc + 127) & ~127 : (n_sc + 63) & ~63;
+}
+
 Geometry make_geometry(const pusch_cell_cfg &c);
 
 // Bytes of the FFT output (pusch_ofdm_fft's freq_out) for n_slots slots of a geometry. FP8 form: the E4M3

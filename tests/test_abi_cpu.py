@@ -39,7 +39,11 @@ def test_library_exports_every_declared_symbol(B):
 def test_version_and_pitch(B):
     assert "sm_103a" in B.pusch_version()
     cfg = B.make_cfg(n_rx=64, n_fft=4096, n_sc=3276, n_beams=32, n_layers=16)
-    assert B.pusch_sc_pitch(cfg) == 3280
+    assert B.pusch_sc_pitch(cfg) == 3328                  # FP32 form: the mixed form's planes, 64-element rows
+    cfg8 = B.make_cfg(n_rx=64, n_fft=4096, n_sc=3276, n_beams=32, n_layers=16, form=B.PUSCH_FORM_FP8)
+    assert B.pusch_sc_pitch(cfg8) == 3328                 # 128-byte rows of E4M3 codes
+    cfgm = B.make_cfg(n_rx=64, n_fft=4096, n_sc=3200, n_beams=32, n_layers=16, form=B.PUSCH_FORM_MIXED)
+    assert B.pusch_sc_pitch(cfgm) == 3200
 
 
 def _good(**kw):
