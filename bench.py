@@ -188,15 +188,23 @@ def stage_flops(cell, n):
     return {"beamform": n * 8.0 * S * sc * R * Bm, "detect": n * 8.0 * sc * det}
 
 
-KERNELS = {"fft": ("fft_kernel", "fft_impl.cuh"),
-           "beamform": {"mixed": ("beamform_tc_kernel", "beamform_tc.cu"), "fp8": ("beamform_tc_kernel", "beamform_tc.cu"),
+# (kernel, its source files) per stage; the sources are hashed to tie profiles/traffic.json to the code
+TC = "tc_common.cuh+bounded_wait.cuh"
+KERNELS = {"fft": {"tc": ("fft_tc_kernel", "fft_tc.cu+" + TC), "simt": ("fft_kernel", "fft_impl.cuh+bounded_wait.cuh")},
+           "beamform": {"mixed": ("beamform_tc_kernel", "beamform_tc.cu+" + TC),
+                        "fp8": ("beamform_tc_kernel", "beamform_tc.cu+" + TC),
                         "fp32": ("beamform_fp32_kernel", "beamform.cu")},
            "ls": ("ls_pilots_kernel", "chest.cu+chest_common.cuh"),
            "detect": ("mmse_kernel", "mmse_impl.cuh+detect_core.cuh")}
 
 
-def kernel_of(stage, form):
+def kernel_of(stage, form, cell=None):
     k = KERNELS[stage]
+    if stage == "fft":
+        # the mixed form's 4096-point FFT of FP16 samples without prefixes runs on the tensor cores
+        tc = (form == "mixed" and cell is not None and cell.n_fft == 4096 and cell.in_fp16
+              and not getattr(cell, "cp", False) and not getattr(cell, "shift_7p5khz", False))
+        return k["tc" if tc else "simt"]
     return k[form] if isinstance(k, dict) else k
 
 
@@ -372,7 +380,7 @@ def run_ours(args, rank, world, local):
     roof_stages = iso["stage_ms"] if iso is not None else stages
     dom = max(roof_stages, key=roof_stages.get)
     dom_ms = roof_stages[dom]
-    kname, ksrc = kernel_of(dom, form)
+    kname, ksrc = kernel_of(dom, form, cell)
     traffic = measured_traffic(kname, ksrc, n)
     if (dom == "beamform" and form == "fp32") or dom == "detect":
         # FP32 arithmetic, not HBM, bounds these kernels: report them against the derived FP32 ALU peak
@@ -397,7 +405,7 @@ def run_ours(args, rank, world, local):
     per_stage = {}
     for k, v in stages.items():
         gbs = sb[k] / (v / 1e3) / 1e9
-        per_stage[k] = {"kernel": kernel_of(k, form)[0], "ms": round(v, 4), "GB/s": round(gbs, 1),
+        per_stage[k] = {"kernel": kernel_of(k, form, cell)[0], "ms": round(v, 4), "GB/s": round(gbs, 1),
                         "hbm_frac": round(gbs / pk["hbm_gbs"], 4)}
     per_stage["beamform"]["TFLOP/s"] = round(stage_flops(cell, n)["beamform"] / (stages["beamform"] / 1e3) / 1e12, 2)
     per_stage["detect"]["TFLOP/s"] = round(stage_flops(cell, n)["detect"] / (stages["detect"] / 1e3) / 1e12, 2)
