@@ -193,7 +193,8 @@ TC = "tc_common.cuh+bounded_wait.cuh"
 KERNELS = {"fft": {"tc": ("fft_tc_kernel", "fft_tc.cu+" + TC), "simt": ("fft_kernel", "fft_impl.cuh+bounded_wait.cuh")},
            "beamform": {"mixed": ("beamform_tc_kernel", "beamform_tc.cu+" + TC),
                         "fp8": ("beamform_tc_kernel", "beamform_tc.cu+" + TC),
-                        "fp32": ("beamform_fp32_kernel", "beamform.cu")},
+                        "fp32": ("beamform_tf32_kernel", "beamform_tf32.cu+" + TC),
+                        "fp32_simt": ("beamform_fp32_kernel", "beamform.cu")},
            "ls": ("ls_pilots_kernel", "chest.cu+chest_common.cuh"),
            "detect": ("mmse_kernel", "mmse_impl.cuh+detect_core.cuh")}
 
@@ -205,6 +206,10 @@ def kernel_of(stage, form, cell=None):
         tc = (form == "mixed" and cell is not None and cell.n_fft == 4096 and cell.in_fp16
               and not getattr(cell, "cp", False) and not getattr(cell, "shift_7p5khz", False))
         return k["tc" if tc else "simt"]
+    if stage == "beamform" and form == "fp32" and cell is not None and not (
+            cell.n_sc % 2 == 0 and cell.n_rx % 16 == 0 and cell.n_beams % 8 == 0 and cell.n_beams <= 64
+            and 32 * cell.n_rx * cell.n_beams <= 96 * 1024):
+        return k["fp32_simt"]                    # the FP32 form's 3xTF32 tensor-core GEMM needs these shapes
     return k[form] if isinstance(k, dict) else k
 
 
@@ -382,7 +387,7 @@ def run_ours(args, rank, world, local):
     dom_ms = roof_stages[dom]
     kname, ksrc = kernel_of(dom, form, cell)
     traffic = measured_traffic(kname, ksrc, n)
-    if (dom == "beamform" and form == "fp32") or dom == "detect":
+    if (dom == "beamform" and kname == "beamform_fp32_kernel") or dom == "detect":
         # FP32 arithmetic, not HBM, bounds these kernels: report them against the derived FP32 ALU peak
         fl = stage_flops(cell, n)[dom]
         ach = fl / (dom_ms / 1e3) / 1e12

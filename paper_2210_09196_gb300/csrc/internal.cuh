@@ -181,7 +181,13 @@ cudaError_t launch_beamform_fp8(const Geometry &g, int n_slots, const uint8_t *f
                                 const float2 *W, float2 *beam, uint32_t *err_word, cudaStream_t st,
                                 const TcTune *tune = nullptr);
 bool bf_fp8_supported(const Geometry &g);
-// Beamforming of the FFT output in the geometry's form (FP32 SIMT, FP16 or FP8 tensor cores).
+// FP32 form on the tensor cores with three TF32 products per FP32 product (beamform_tf32.cu): n_sc even,
+// n_rx a multiple of 16, n_beams a multiple of 8 up to 64, W's operands within shared memory.
+bool bf_tf32_supported(const Geometry &g);
+cudaError_t launch_beamform_tf32(const Geometry &g, int n_slots, const float2 *freq, const float2 *W, float2 *beam,
+                                 uint32_t *err_word, cudaStream_t st);
+// Beamforming of the FFT output in the geometry's form (FP32: 3xTF32 tensor cores where supported and the
+// pointers are 16-byte aligned, else SIMT; FP16 or FP8 tensor cores).
 inline cudaError_t launch_beamform(const Geometry &g, int n_slots, const void *freq, const float2 *W, float2 *beam,
                                    uint32_t *err_word, cudaStream_t st, const TcTune *tune = nullptr) {
     if (g.form == PUSCH_FORM_MIXED)
@@ -189,6 +195,8 @@ inline cudaError_t launch_beamform(const Geometry &g, int n_slots, const void *f
     if (g.form == PUSCH_FORM_FP8)
         return launch_beamform_fp8(g, n_slots, static_cast<const uint8_t *>(freq),
                                    fp8_scales(g, n_slots, const_cast<void *>(freq)), W, beam, err_word, st, tune);
+    if (bf_tf32_supported(g) && reinterpret_cast<uintptr_t>(freq) % 16 == 0 && reinterpret_cast<uintptr_t>(beam) % 16 == 0)
+        return launch_beamform_tf32(g, n_slots, static_cast<const float2 *>(freq), W, beam, err_word, st);
     return launch_beamform_fp32(g, n_slots, static_cast<const float2 *>(freq), W, beam, st);
 }
 
