@@ -18,7 +18,7 @@
 //               accumulators and commits the chunk's stage back to the producer;
 //   warps 2-5   epilogue: tcgen05.ld of the finished accumulator (one 32-lane quarter per warp), scaling
 //               (FP8 form), stores of the c64 rows; the other accumulator is being filled meanwhile;
-//   warps 6-9   FP8 form only: convert each landed chunk of E4M3 codes to FP16 for the MMA (below).
+//   warps 6-13  FP8 form only: convert each landed chunk of E4M3 codes to FP16 for the MMA (below).
 //
 // FP8 form. The FFT stores each (symbol, antenna) row as E4M3 codes with one power-of-two scale 2^e per
 // 128 subcarriers; W is quantised in the kernel to E4M3 with one power-of-two scale per (beam, 128
@@ -48,6 +48,7 @@ constexpr int kTileM = 128;
 constexpr int kMaxStages = 8;
 constexpr int kSmemLimit = 227 * 1024;
 constexpr int kMaxRxFp8 = 512;   // W block exponents are kept for up to 4 blocks of 128 antennas
+constexpr int kConvWarps = 8;     // FP8: warps that convert the landed codes
 
 using namespace tc;
 
@@ -106,15 +107,15 @@ struct TcShared {
     int ew[64 * 4];            // FP8: W block exponents [beam][128-antenna block]
     int wexp[64];              // FP8: E_b, the largest block exponent of beam b
     float wsc[64];             // FP8: 2^E_b
-    uint8_t shift[4][kMaxRxFp8];  // FP8: per rescale warp, the shift E - e_r of each antenna of its tile
+    uint8_t shift[kConvWarps][kMaxRxFp8];  // FP8: per convert warp, the shift E - e_r of each antenna of its tile
 };
 
 template <bool FP8>
-__global__ void __launch_bounds__(FP8 ? 320 : 192, 1)
+__global__ void __launch_bounds__(FP8 ? 192 + 32 * kConvWarps : 192, 1)
 beamform_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap omap, TcArgs g,
                    const float2 *__restrict__ W, const float *__restrict__ scales, float2 *__restrict__ beam,
                    uint32_t *__restrict__ err) {
-    constexpr int kThreads = FP8 ? 320 : 192;
+    constexpr int kThreads = FP8 ? 192 + 32 * kConvWarps : 192;
     constexpr int kKStep = 16;                  // K per MMA instruction (32 bytes of FP16)
     extern __shared__ uint8_t smem_raw[];
     __shared__ TcShared sh;
@@ -230,9 +231,9 @@ beamform_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_consta
     if (tid == 0) {
         for (int s = 0; s < kMaxStages; ++s) {   // both rings (FP8: n_land may exceed n_stages)
             mbar_init(smem_u32(&sh.full[s]), 1);
-            mbar_init(smem_u32(&sh.ready[s]), 4);
+            mbar_init(smem_u32(&sh.ready[s]), kConvWarps);
             mbar_init(smem_u32(&sh.empty[s]), 1);
-            mbar_init(smem_u32(&sh.lempty[s]), 4);
+            mbar_init(smem_u32(&sh.lempty[s]), kConvWarps);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(smem_u32(&sh.tfull[b]), 1);
@@ -405,8 +406,8 @@ beamform_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_consta
         if (g.stage_out && lane == 0) bulk_wait0();        // stores complete before the CTA's shared memory goes
     } else if constexpr (FP8) {
         // ------------------------------------------------------------------ FP8: codes to FP16
-        // Each of the four warps derives the tile exponent E itself (no cross-warp barrier, so an abort in
-        // one warp cannot strand the others) and converts the 16-byte pieces u = 32 w + lane (mod 128) of
+        // Each convert warp derives the tile exponent E itself (no cross-warp barrier, so an abort in one warp
+        // cannot strand the others) and converts the 16-byte pieces u = 32 w + lane (mod 32 kConvWarps) of
         // each landed chunk.
         const int w4 = warp - 6;
         long long gch = 0;
@@ -447,17 +448,18 @@ beamform_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_consta
                 // the layout a 128-byte-swizzled TMA box of FP16 planes has. Every value of the row takes the
                 // factor 2^-d of its antenna (d = E - e_r): exact in binary16 up to d = 15 (see above).
                 // Four units per pass, their loads issued together.
-                for (int u0 = w4 * 32 + lane; u0 < rows_here * 8; u0 += 512) {
+                constexpr int kStride = 32 * kConvWarps;
+                for (int u0 = w4 * 32 + lane; u0 < rows_here * 8; u0 += 4 * kStride) {
                     uint4 v[4];
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        const int u = u0 + 128 * q, k = u >> 3, j = u & 7;
+                        const int u = u0 + kStride * q, k = u >> 3, j = u & 7;
                         if (u < rows_here * 8)
                             v[q] = *reinterpret_cast<const uint4 *>(land + (size_t)k * 128 + ((j ^ (k & 7)) << 4));
                     }
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        const int u = u0 + 128 * q, k = u >> 3, j = u & 7;
+                        const int u = u0 + kStride * q, k = u >> 3, j = u & 7;
                         if (u >= rows_here * 8) continue;
                         const int d = sh.shift[w4][(k0 + k) >> 1];
                         // 2^-d in binary16: normal for d <= 14, subnormal 2^-24 * 2^(24 - d) up to 24, zero beyond
@@ -636,7 +638,7 @@ cudaError_t launch_tc(const Geometry &g, int n_slots, const void *freq, const fl
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     long long grid = sms;
     if (grid > a.total_tiles) grid = a.total_tiles;
-    kern<<<(unsigned)grid, FP8 ? 320 : 192, p.smem, st>>>(map, omap, a, W, scales, beam, err_word);
+    kern<<<(unsigned)grid, FP8 ? 192 + 32 * kConvWarps : 192, p.smem, st>>>(map, omap, a, W, scales, beam, err_word);
     return cudaGetLastError();
 }
 

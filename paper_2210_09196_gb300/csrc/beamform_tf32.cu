@@ -15,7 +15,7 @@
 //               accumulators and commits the chunk's operand stage back to the convert warps;
 //   warps 2-5   epilogue: tcgen05.ld of the finished accumulator (one 32-lane quarter per warp), stores of
 //               the c64 beam rows;
-//   warps 6-9   split each landed chunk into the hi and lo operands (K-major core matrices, no swizzle).
+//   warps 6-13  split each landed chunk into the hi and lo operands (K-major core matrices, no swizzle).
 // B (hi and lo, K-major) is built once per CTA from W staged through the still idle operand ring.
 // Every wait is bounded (%globaltimer, 2 s); on expiry the CTA records a timeout in err_word bit 0, all roles
 // leave their loops, in-flight copies and MMAs are drained (bounded) and TMEM is freed.
@@ -34,7 +34,8 @@ constexpr int kCR = 16;                 // antennas per K chunk
 constexpr int kKC = 2 * kCR;            // K values per chunk
 constexpr int kMaxStages = 8;
 constexpr int kSmemLimit = 227 * 1024;
-constexpr int kThreads = 320;
+constexpr int kConvWarps = 8;        // warps that split the landed chunks (12 measured within 2 %)
+constexpr int kThreads = 192 + 32 * kConvWarps;
 constexpr uint32_t kABytes = (uint32_t)kTileM * kKC * 4;   // one operand (hi or lo) of a chunk: 16 KB
 constexpr uint32_t kASbo = (uint32_t)(kKC / 4) * 128;      // bytes between 8-row groups of an A stage
 constexpr uint32_t kLandBytes = (uint32_t)kCR * kTileM * 8; // landed c64 chunk: 16 KB
@@ -131,8 +132,8 @@ beamform_tf32_kernel(const __grid_constant__ CUtensorMap tmap, Tf32Args g, const
     if (tid == 0) {
         for (int s = 0; s < kMaxStages; ++s) {
             mbar_init(smem_u32(&sh.full[s]), 1);
-            mbar_init(smem_u32(&sh.lempty[s]), 4);
-            mbar_init(smem_u32(&sh.ready[s]), 4);
+            mbar_init(smem_u32(&sh.lempty[s]), kConvWarps);
+            mbar_init(smem_u32(&sh.ready[s]), kConvWarps);
             mbar_init(smem_u32(&sh.empty[s]), 1);
         }
         for (int b = 0; b < 2; ++b) {
@@ -281,7 +282,7 @@ beamform_tf32_kernel(const __grid_constant__ CUtensorMap tmap, Tf32Args g, const
                 uint8_t *ahi = gbase + (size_t)s * 2u * kABytes, *alo = ahi + kABytes;
                 const int r_left = g.n_rx - c * kCR;     // antennas of this chunk that exist
 #pragma unroll 2
-                for (int u = w4 * 32 + lane; u < kTileM * (kCR / 2); u += 128) {
+                for (int u = w4 * 32 + lane; u < kTileM * (kCR / 2); u += 32 * kConvWarps) {
                     const int p = u >> 7, m = u & 127;
                     float2 x0 = *reinterpret_cast<const float2 *>(land + (size_t)(2 * p) * 1024 + m * 8);
                     float2 x1 = *reinterpret_cast<const float2 *>(land + (size_t)(2 * p + 1) * 1024 + m * 8);
