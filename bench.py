@@ -373,6 +373,7 @@ def run_ours(args, rank, world, local):
     ragged = None if args.no_ragged else run_ragged(world)
     denoise = None if args.no_denoiser else run_denoiser(world, evm=not args.no_cpu_baseline)
     massive = None if args.no_massive else run_massive(world, oracle_check=not args.no_cpu_baseline and world == 1)
+    small = None if args.no_massive else run_small(world)
 
     if rank != 0:
         rx.close()
@@ -447,6 +448,7 @@ def run_ours(args, rank, world, local):
         "ragged_batch": ragged,
         "learned_estimator": denoise,
         "massive_stream": massive,
+        "small_cell": small,
         "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
@@ -559,6 +561,39 @@ def run_denoiser(world, evm=True, n=4, reps=10):
            "plain_ls_ms_per_slot": round(ms_ls / n, 5)}
     if evm:
         res["evm_vs_ls"] = {str(k): v for k, v in D.evaluate(pb, [-5.0, 0.0, 10.0, 20.0, 25.0], n_slots=1).items()}
+    return res
+
+
+def run_small(world, n=16, calls=400):
+    """The small cell (16 antennas, 512-point FFT, 300 subcarriers, 16 beams, 4 layers, QPSK) in the plain FP32 form:
+    n slots per pusch_slot call, calls back to back on one stream, CUDA events around them (after warm-up).
+    The inputs (2.3 MB per call) stay in L2: this workload is launch- and latency-bound, not HBM-bound; its
+    parity with the FP64 oracle is in the tests (tests/test_gpu_parity.py)."""
+    import torch
+    from paper_2210_09196_gb300 import binding as B
+    from paper_2210_09196_gb300 import host, synth
+    cell = synth.SMALL_FP32
+    slots = synth.make_slots(cell, n)
+    rx = host.Receiver(host.cfg_for(cell, B.PUSCH_FORM_FP32), max_slots=n)
+    t, p, W = host.time_tensor(slots), host.pilot_tensor(slots), host.beam_tensor(slots[0].W)
+    out = (rx.xhat_buffer(n), rx.bits_buffer(n), rx.status_buffer())
+    cur = torch.cuda.current_stream()
+    for _ in range(10):
+        B.pusch_slot(rx.h, n, t, W, p, *out, cur)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0.record(cur)
+    for _ in range(calls):
+        B.pusch_slot(rx.h, n, t, W, p, *out, cur)
+    e1.record(cur)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1), world)
+    res = {"workload": cell.name, "form": "fp32", "slots_per_call": n, "calls": calls,
+           "value": whole_job_rate(n * calls, world, ms / 1e3), "unit": UNIT,
+           "ms_per_call": round(ms / calls, 4), "device_status": [int(v) for v in out[2].cpu().numpy()]}
+    rx.close()
     return res
 
 

@@ -14,10 +14,10 @@
 //            sum_a Re(x) w^(a k0), row (m, im) gives P_im[k0]; the two lanes of m combine
 //            Y = P_re + i P_im with one exchange per eight values and apply W^(m k0).
 //   stage 2  A2 = Y written by those lanes as real rows: row 2 k0 = Re Y[.][k0], row 2 k0 + 1 = Im Y[.][k0],
-//            K = m, K-major without swizzle, the core-matrix strides padded (144 B along K, 1168 B between
-//            8-row groups) so that every warp-wide 2-byte store hits distinct banks. The lanes of row pair
-//            (2 k0, 2 k0 + 1) combine X = D_re + i D_im the same way and write bins k0 + 64 k1, consecutive
-//            across lanes, into the FP16 output planes.
+//            K = m, MN-major with 128-byte swizzling (the layout of stage 1's operand): a lane holds one m and
+//            eight consecutive k0, i.e. 16 consecutive rows n = 2 k0 + (re, im), and writes them as two
+//            16-byte pieces. The lanes of row pair (2 k0, 2 k0 + 1) combine X = D_re + i D_im the same way and
+//            write bins k0 + 64 k1, consecutive across lanes, into the FP16 output planes.
 // A 4096-point transform thus costs two MMA passes (8 MMAs of 128 x 128 x 16) and one pass of twiddles and
 // transposition through shared memory.
 //
@@ -48,9 +48,8 @@ constexpr int kStages = 1;
 constexpr uint32_t kRowBytes = kN * 4;                      // one row of FP16 complex samples: 16 KB
 constexpr uint32_t kOffIn = 0;                              // input ring (stage-1 A operands, 1024-aligned)
 constexpr uint32_t kOffB = kOffIn + kStages * kRowBytes;    // B: [128][64] FP16, K-major, 16 KB
-constexpr uint32_t kA2Lbo = 144, kA2Sbo = 1168;             // padded K-major strides of A2
-constexpr uint32_t kOffA2 = kOffB + 16384;                  // 16 row groups x 1168 B
-constexpr uint32_t kSmemUsed = kOffA2 + 16 * kA2Sbo;
+constexpr uint32_t kOffA2 = kOffB + 16384;                  // A2: [2 halves of 64 n][64 m][128 B], 16 KB
+constexpr uint32_t kSmemUsed = kOffA2 + 16384;
 constexpr size_t kSmemBytes = kSmemUsed + 1024;             // + alignment of the base to 1024 B
 
 __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
@@ -146,7 +145,7 @@ fft_tc_kernel(const __grid_constant__ CUtensorMap tin, __half *__restrict__ out,
     if (warp == kEpiWarps) {
         // ------------------------------------------------------------ control: row copies and MMAs
         if (lane == 0) {
-            const uint32_t idesc1 = idesc_f16(128, 128, true, false), idesc2 = idesc_f16(128, 128, false, false);
+            const uint32_t idesc = idesc_f16(128, 128, true, false);   // A MN-major in both stages
             auto issue = [&](long long i) {
                 const int s = (int)(i % kStages);
                 const long long row = blockIdx.x + i * gridDim.x;
@@ -173,7 +172,7 @@ fft_tc_kernel(const __grid_constant__ CUtensorMap tin, __half *__restrict__ out,
                 const uint32_t a0 = base + kOffIn + (uint32_t)s * kRowBytes;
                 for (int ks = 0; ks < 4; ++ks)
                     mma_f16(tmem, smem_desc(a0 + (uint32_t)ks * 2048u, 8192, 1024, 2),
-                            smem_desc(base + kOffB + (uint32_t)ks * 256u, 128, 1024, 0), idesc1, ks > 0 ? 1u : 0u);
+                            smem_desc(base + kOffB + (uint32_t)ks * 256u, 128, 1024, 0), idesc, ks > 0 ? 1u : 0u);
                 mma_commit(smem_u32(&bar_acc));
                 // the stage-1 products have read the row: its ring slot takes a later row
                 ok = mbar_wait_sleep(smem_u32(&bar_acc), 0u, abort, err, 32);
@@ -184,8 +183,8 @@ fft_tc_kernel(const __grid_constant__ CUtensorMap tin, __half *__restrict__ out,
                 if (!ok) break;
                 fence_after_sync();
                 for (int ks = 0; ks < 4; ++ks)
-                    mma_f16(tmem, smem_desc(base + kOffA2 + (uint32_t)ks * 2u * kA2Lbo, kA2Lbo, kA2Sbo, 0),
-                            smem_desc(base + kOffB + (uint32_t)ks * 256u, 128, 1024, 0), idesc2, ks > 0 ? 1u : 0u);
+                    mma_f16(tmem, smem_desc(base + kOffA2 + (uint32_t)ks * 2048u, 8192, 1024, 2),
+                            smem_desc(base + kOffB + (uint32_t)ks * 256u, 128, 1024, 0), idesc, ks > 0 ? 1u : 0u);
                 mma_commit(smem_u32(&bar_acc));
             }
             if (ok && n_my > 0) mbar_wait_sleep(smem_u32(&bar_op), op_phase, abort, err, 128);   // the last row read out
@@ -221,14 +220,19 @@ fft_tc_kernel(const __grid_constant__ CUtensorMap tin, __half *__restrict__ out,
                 tmem_ld32(tq + 32u * c, r);
                 float2 Y[8];
                 combine_pair(r, odd, Y);
+                // k0 = 16 c + 8 odd + i: rows n = 2 k0 + (re, im) = 32 c + 16 odd .. + 15, i.e. 16-byte pieces
+                // q0 and q0 + 1 (q0 = (c % 2) 4 + 2 odd) of row half c / 2, K row m = j, swizzled by j % 8
+                uint32_t v[8];
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
                     const float2 y = cmul(cmul(Y[i], pw[i]), bs[c]);
-                    const int k0 = 16 * c + 8 * odd + i;
-                    const __half2 v = __floats2half2_rn(y.x, y.y);
-                    *reinterpret_cast<__half *>(gbase + kOffA2 + kmajor_off(2 * k0, j, kA2Lbo, kA2Sbo)) = __low2half(v);
-                    *reinterpret_cast<__half *>(gbase + kOffA2 + kmajor_off(2 * k0 + 1, j, kA2Lbo, kA2Sbo)) = __high2half(v);
+                    const __half2 hv = __floats2half2_rn(y.x, y.y);
+                    v[i] = *reinterpret_cast<const uint32_t *>(&hv);
                 }
+                uint8_t *rowp = gbase + kOffA2 + (uint32_t)(c >> 1) * 8192u + (uint32_t)j * 128u;
+                const int q0 = (c & 1) * 4 + 2 * odd;
+                *reinterpret_cast<uint4 *>(rowp + ((q0 ^ (j & 7)) << 4)) = make_uint4(v[0], v[1], v[2], v[3]);
+                *reinterpret_cast<uint4 *>(rowp + (((q0 + 1) ^ (j & 7)) << 4)) = make_uint4(v[4], v[5], v[6], v[7]);
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             fence_before_sync();
