@@ -21,6 +21,7 @@
 #pragma once
 
 #include "chest_common.cuh"
+#include "bounded_wait.cuh"
 #include "detect_core.cuh"
 
 namespace pusch {
@@ -104,7 +105,7 @@ constexpr int mmse_min_ctas() {
 // segment is one contiguous run of SPC elements (a warp per subcarrier pair would write 16-byte pieces of 16
 // rows).
 // NB > 0: compiled for NB beams (every shared-memory offset of the Gram, matched-filter and staging loops is
-// then a constant); 0: g.n_beams at run time.
+// then a constant) and staged by bulk copies on one mbarrier per warp; 0: g.n_beams at run time, cp.async.
 template <int NL, int ND, int WARPS, int NB>
 __global__ void __launch_bounds__(WARPS * 32, mmse_min_ctas<NL, WARPS>())
 mmse_kernel(MmseArgs g, long long total_sc, const float2 *__restrict__ H, const float2 *__restrict__ beam,
@@ -132,6 +133,68 @@ mmse_kernel(MmseArgs g, long long total_sc, const float2 *__restrict__ H, const 
         const bool valid = my_sc < total_sc;
         const long long slot = my_sc / n_sc;
 
+        const float2 *hr = Ht + grp * ht + i * hs;  // own row
+        const float2 *hg = Ht + grp * ht;           // the group's rows
+        constexpr int NR = ND > 0 ? ND : 14;
+        float2 acc[NR];
+        if constexpr (NB > 0) {
+            // ---- 0-1. the estimate rows and the data-symbol rows of the warp's subcarriers -> shared memory by
+            //           bulk copies (one 8 NB-byte row each, by the copy engine, completing on the warp's
+            //           mbarrier); rows of absent layers and subcarriers are zeroed. The launcher uses these
+            //           instances only with 16-byte aligned H and beam.
+            const uint32_t bar = smem_addr(reinterpret_cast<uint64_t *>(smem_raw + (size_t)WARPS * wsb) + warp);
+            constexpr uint32_t kRowB = NB * 8;
+            uint32_t my_bytes = 0;
+            for (int r = lane; r < SPW * NL; r += 32)
+                if (r % NL < nl && sc0 + r / NL < total_sc) my_bytes += kRowB;
+            for (int r = lane; r < SPW * nd; r += 32)
+                if (sc0 + r / nd < total_sc) my_bytes += kRowB;
+            const uint32_t total = __reduce_add_sync(kFull, my_bytes);
+            if (lane == 0) {
+                bw::mbar_init(bar, 1);
+                asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(total) : "memory");
+            }
+            __syncwarp();
+            for (int r = lane; r < SPW * NL; r += 32) {
+                const int gg = r / NL, l = r - gg * NL;
+                float2 *dst = Ht + gg * ht + l * hs;
+                if (l < nl && sc0 + gg < total_sc) {
+                    const float2 *src = H + ((sc0 + gg) * nl + l) * (long long)NB;
+                    asm volatile(
+                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                            smem_addr(dst)),
+                        "l"(src), "r"(kRowB), "r"(bar)
+                        : "memory");
+                } else {
+#pragma unroll
+                    for (int b = 0; b < NB; b += 2) *reinterpret_cast<float4 *>(dst + b) = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+            for (int r = lane; r < SPW * nd; r += 32) {
+                const int gg = r / nd, d = r - gg * nd;
+                const long long sc = sc0 + gg;
+                float2 *dst = Yt + (gg * nd + d) * ys;
+                if (sc < total_sc) {
+                    const long long sl = sc / n_sc, aa = sc - sl * n_sc;
+                    const float2 *src = beam + ((sl * g.n_sym + data_symbol(g, g.d_first + d)) * n_sc + aa) * NB;
+                    asm volatile(
+                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                            smem_addr(dst)),
+                        "l"(src), "r"(kRowB), "r"(bar)
+                        : "memory");
+                } else {
+#pragma unroll
+                    for (int b = 0; b < NB; b += 2) *reinterpret_cast<float4 *>(dst + b) = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+            // bounded wait (2 s); on expiry the timeout bit is set and the copies are waited for once more
+            if (!bw::mbar_wait_for(bar, 0, bw::kWaitNs)) {
+                if (lane == 0) atomicOr(&status[0], (unsigned)PUSCH_STATUS_TIMEOUT);
+                bw::mbar_wait_for(bar, 0, bw::kWaitNs);
+            }
+            __syncwarp();
+        } else {
         // ---- 0. the data-symbol rows y_d of the warp's subcarriers -> shared memory, asynchronously (cp.async,
         //         16-byte pieces when the beam count is even); waited for just before step 2b.
         {
@@ -164,15 +227,11 @@ mmse_kernel(MmseArgs g, long long total_sc, const float2 *__restrict__ H, const 
             }
             asm volatile("cp.async.commit_group;" ::: "memory");
         }
-
-        // ---- 1. channel estimate rows -> shared memory; 2-4. Gram, matched filter, Cholesky and solves, the
-        //         x_d left in the data-symbol rows (detect_group).
-        const float2 *hr = Ht + grp * ht + i * hs;  // own row
-        const float2 *hg = Ht + grp * ht;           // the group's rows
-        constexpr int NR = ND > 0 ? ND : 14;
-        float2 acc[NR];
+        // ---- 1. channel estimate rows -> shared memory (waits for both copy groups)
         stage_H<NL>(Ht, H, sc0, total_sc, nl, nb, hs, ht, lane);
         __syncwarp();
+        }
+        // ---- 2-4. Gram, matched filter, Cholesky and solves, the x_d left in the data-symbol rows (detect_group).
         const bool bad = detect_group<NL, ND, NR>(hr, hg, Yt + grp * nd * ys, Ht + grp * ht, hs, nb, nd, nl,
                                                   g.sigma2 ? g.loading : g.load, i, src0, acc, g.sigma2,
                                                   valid ? slot : 0, ys);
@@ -214,7 +273,7 @@ template <int NL, int ND, int WARPS, int NB>
 cudaError_t launch_nl(const MmseArgs &a, long long total_sc, const float2 *H, const float2 *beam, float2 *xhat,
                       uint8_t *bits, uint32_t *status, cudaStream_t st) {
     constexpr int SPW = 32 / NL;
-    const size_t smem = (size_t)WARPS * warp_smem_bytes<NL>(a.n_beams, ND > 0 ? ND : a.n_det);
+    const size_t smem = (size_t)WARPS * warp_smem_bytes<NL>(a.n_beams, ND > 0 ? ND : a.n_det) + (NB > 0 ? 8 * WARPS : 0);
     const long long per_cta = (long long)WARPS * SPW;
     const long long grid = (total_sc + per_cta - 1) / per_cta;
     if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
@@ -254,8 +313,10 @@ template <int NL>
 cudaError_t launch_nd(const MmseArgs &a, long long total_sc, const float2 *H, const float2 *beam, float2 *xhat,
                       uint8_t *bits, uint32_t *status, cudaStream_t st) {
     if constexpr (NL >= 16) {
-        if (a.n_beams == 32) return launch_w<NL, 32>(a, total_sc, H, beam, xhat, bits, status, st);
-        if (a.n_beams == 64) return launch_w<NL, 64>(a, total_sc, H, beam, xhat, bits, status, st);
+        // the beam-count instances stage by bulk copies: 16-byte aligned rows
+        const bool aligned = reinterpret_cast<uintptr_t>(H) % 16 == 0 && reinterpret_cast<uintptr_t>(beam) % 16 == 0;
+        if (aligned && a.n_beams == 32) return launch_w<NL, 32>(a, total_sc, H, beam, xhat, bits, status, st);
+        if (aligned && a.n_beams == 64) return launch_w<NL, 64>(a, total_sc, H, beam, xhat, bits, status, st);
     }
     return launch_w<NL, 0>(a, total_sc, H, beam, xhat, bits, status, st);
 }
