@@ -146,18 +146,28 @@ batch_detect_kernel(DetArgs g, int nbmax, const Segment *__restrict__ segs, cons
         const int a = it.y + grp;
         const bool valid = a < sg.a0 + sg.n;
 
-        // 0. y rows of the group's subcarrier -> shared memory (cp.async, 8-byte pieces)
+        // 0. y rows of the group's subcarrier -> shared memory (cp.async: 16-byte pieces of two beams when the
+        //    segment's beam count and its rows' start are even, else 8-byte pieces)
         {
-            for (int idx = lane; idx < SPW * nd * nb; idx += 32) {
-                const int gg = idx / (nd * nb);
-                const int rem = idx - gg * nd * nb;
-                const int d = rem / nb, b = rem - d * nb;
+            const bool wide = (nb & 1) == 0 && (sg.beam_off & 1) == 0;
+            const int pw = wide ? 2 : 1;                 // beams per piece
+            const int ppr = nb / pw;                     // pieces per row
+            for (int idx = lane; idx < SPW * nd * ppr; idx += 32) {
+                const int gg = idx / (nd * ppr);
+                const int rem = idx - gg * nd * ppr;
+                const int d = rem / ppr, b = (rem - d * ppr) * pw;
                 const int aa = it.y + gg;
                 float2 *dst = Yt + (gg * nd + d) * ys + b;
-                if (aa < sg.a0 + sg.n)
-                    pusch::cp_async8(dst, beam + sg.beam_off + ((long long)data_symbol(g, d) * sg.n_sc + aa) * nb + b);
-                else
-                    *dst = make_float2(0.f, 0.f);
+                const float2 *src = beam + sg.beam_off + ((long long)data_symbol(g, d) * sg.n_sc + aa) * nb + b;
+                if (aa < sg.a0 + sg.n) {
+                    if (wide)
+                        pusch::cp_async16(dst, src);
+                    else
+                        pusch::cp_async8(dst, src);
+                } else {
+                    dst[0] = make_float2(0.f, 0.f);
+                    if (wide) dst[1] = make_float2(0.f, 0.f);
+                }
             }
             asm volatile("cp.async.commit_group;" ::: "memory");
         }
