@@ -169,6 +169,15 @@ def stage_bytes(cell, form, n):
     xh = L * 12 * sc * 8
     bits = L * 12 * sc
     H = sc * L * Bm * 8
+    if 8 < L <= 32 and Bm in (32, 64):
+        # the detector interpolates the estimate from the LS pilot table while it stages: the estimate itself
+        # never goes through memory
+        return {
+            "fft": n * (t_in + f_out),
+            "beamform": n * (f_out + beam) + W,
+            "ls": n * (2 * sc * Bm * 8 + pil + ls),                  # 2 DMRS symbols + pilots in, pilot table out
+            "detect": n * (12 * sc * Bm * 8 + ls + xh + bits),      # 12 data symbols + pilot table in, x_hat + bits
+        }
     return {
         "fft": n * (t_in + f_out),
         "beamform": n * (f_out + beam) + W,

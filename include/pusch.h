@@ -228,10 +228,13 @@ pusch_status pusch_mmse_detect(pusch_handle *h, int n_slots, const void *H_hat, 
  * subcarriers -> interpolated estimate (-> noise estimate when noise_var is PUSCH_NOISE_ESTIMATE) -> MMSE
  * detection. The FFT output, the beamformed grid, the LS table and the estimate live in the handle's
  * workspace (n_slots <= max_slots), with the arithmetic of the stage entry points (the result equals
- * pusch_chest_ls + pusch_mmse_detect on the pusch_beamform output). With chol_every = K > 0 the estimate
- * varies in time and the detector factorises once per group of K data symbols (pusch_cell_cfg).
+ * pusch_chest_ls + pusch_mmse_detect on the pusch_beamform output, bit for bit). With 9 to 32 layers and 32
+ * or 64 beams the detector interpolates the estimate from the LS table while it stages its tiles, so the
+ * estimate is not written to memory (the estimate buffer is then unused). With chol_every = K > 0 the
+ * estimate varies in time and the detector factorises once per group of K data symbols (pusch_cell_cfg).
  * time_in, W, pilots, x_hat, bits, status: as in the stage entry points. Kernels: a one-thread status reset,
- * then per run FFT, beamforming, LS table (+ noise estimate), estimate, detection; see pusch_set_pipeline.
+ * then per run FFT, beamforming, LS table (+ noise estimate), estimate (unless the detector interpolates),
+ * detection; see pusch_set_pipeline.
  */
 pusch_status pusch_slot(pusch_handle *h, int n_slots, const void *time_in, const void *W, const void *pilots,
                         void *x_hat, uint8_t *bits, uint32_t *status, void *stream);
@@ -436,7 +439,7 @@ pusch_status pusch_slot_noalloc(const pusch_cell_cfg *cfg, int n_slots, const vo
  * pusch_profile_start arms timing for the next max_calls calls of pusch_slot / pusch_slot_host on this
  * handle (at the pipelining set when it is called): each run of the chain records CUDA events on its own
  * stream before the FFT, after the FFT, after beamforming, after the estimate (LS table, noise estimate,
- * interpolation) and after the detector. pusch_profile_read waits for the recorded events, writes the
+ * interpolation unless the detector interpolates) and after the detector. pusch_profile_read waits for the recorded events, writes the
  * milliseconds of the four stages summed over all timed runs (FFT, beamforming, estimate, detection) to
  * stage_ms[0..3] (n_stages >= 4) and the number of timed calls to *n_calls, and disarms timing. With
  * pipelining a stage's time is that of its kernels while they share the GPU with the other stream's.

@@ -429,14 +429,18 @@ pusch_status run_chain(pusch_handle *h, int s0, int n, size_t freq_off, const vo
         return cuda_fail(e, "LS pilot table launch");
     if (est && (e = pusch::launch_noise_est(g, n, beam, pil, ne_partial, sigma2, s)) != cudaSuccess)
         return cuda_fail(e, "noise estimation launch");
+    // the detector interpolates the estimate from the LS table itself where it can (the interpolated estimate
+    // then never goes through HBM); else the interpolation kernel writes it
+    const bool fused = !tv && pusch::mmse_interp_supported(g, beam, ls);
     if (tv) {  // per-DMRS-symbol tables and one estimate per detection group
         if ((e = pusch::launch_chest_time(g, n, beam, pil, H, ls, s)) != cudaSuccess)
             return cuda_fail(e, "time-varying estimate launch");
-    } else if ((e = pusch::launch_chest_interp(g, n, ls, H, s)) != cudaSuccess) {
+    } else if (!fused && (e = pusch::launch_chest_interp(g, n, ls, H, s)) != cudaSuccess) {
         return cuda_fail(e, "estimate interpolation launch");
     }
     if (ev) cudaEventRecord(ev[3], s);
-    if ((e = pusch::launch_mmse(g, n, H, beam, xh, bt, stat, s, est ? sigma2 : nullptr, tv)) != cudaSuccess)
+    if ((e = pusch::launch_mmse(g, n, H, beam, xh, bt, stat, s, est ? sigma2 : nullptr, tv, fused ? ls : nullptr)) !=
+        cudaSuccess)
         return cuda_fail(e, "detection launch");
     if (ev) cudaEventRecord(ev[4], s);
     return PUSCH_OK;
@@ -762,11 +766,13 @@ extern "C" pusch_status pusch_autotune(pusch_handle *h, const char *cache_path, 
             float best = 1e30f;
             int bw = ws[0];
             const float *sg2 = h->cfg.noise_var == PUSCH_NOISE_ESTIMATE ? h->sigma2 : nullptr;
+            const bool fused = pusch::mmse_interp_supported(g, h->beam, h->ls);   // as the chain runs it
             for (int wi = 0; wi < nw; ++wi) {
                 const int w = ws[wi];
                 g.det_warps = w;
                 const float ms = time_ms(s, reps, [&] {
-                    pusch::launch_mmse(g, n, h->H, h->beam, static_cast<float2 *>(xh), bits, h->status_sink, s, sg2);
+                    pusch::launch_mmse(g, n, h->H, h->beam, static_cast<float2 *>(xh), bits, h->status_sink, s, sg2,
+                                       false, fused ? h->ls : nullptr);
                 }, &e);
                 if (e != cudaSuccess) {
                     st = cuda_fail(e, "autotune detection");

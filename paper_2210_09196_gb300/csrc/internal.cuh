@@ -141,7 +141,11 @@ cudaError_t launch_chest_time(const Geometry &g, int n_slots, const float2 *beam
 // n_beams), else the layer class's default.
 cudaError_t launch_mmse(const Geometry &g, int n_slots, const float2 *H, const float2 *beam, float2 *x_hat,
                         uint8_t *bits, uint32_t *status, cudaStream_t st, const float *sigma2 = nullptr,
-                        bool time_groups = false);
+                        bool time_groups = false, const float2 *ls = nullptr);
+// Whether launch_mmse can take the LS table at the pilots (ls) instead of the interpolated estimate H and
+// interpolate while staging (16- and 32-layer classes, 32 or 64 beams, one estimate per slot, 16-byte aligned
+// beam and table); H is then not read.
+bool mmse_interp_supported(const Geometry &g, const float2 *beam, const float2 *ls);
 // The warps per CTA the 12-data-symbol detector of n_layers layers and n_beams beams may run (out: at most 4;
 // the first is the default); returns their count.
 int mmse_warp_choices_for(int n_layers, int n_beams, int *out);

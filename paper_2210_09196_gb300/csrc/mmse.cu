@@ -5,8 +5,14 @@
 namespace pusch {
 
 cudaError_t launch_mmse(const Geometry &g, int n_slots, const float2 *H, const float2 *beam, float2 *x_hat,
-                        uint8_t *bits, uint32_t *status, cudaStream_t st, const float *sigma2, bool time_groups) {
+                        uint8_t *bits, uint32_t *status, cudaStream_t st, const float *sigma2, bool time_groups,
+                        const float2 *ls) {
+    if (ls && (time_groups || !mmse_interp_supported(g, beam, ls))) return cudaErrorNotSupported;
     mmse_detail::MmseArgs a;
+    a.ls = ls;
+    a.kmax = ls ? ls_pilots_per_layer(g) : 0;
+    a.comb = g.comb;
+    for (int l = 0; l < 32; ++l) a.port[l] = l < g.n_layers ? g.port[l] : 0;
     a.warps = g.det_warps;
     a.n_sc = g.n_sc;
     a.n_beams = g.n_beams;
@@ -42,6 +48,11 @@ cudaError_t launch_mmse(const Geometry &g, int n_slots, const float2 *H, const f
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+bool mmse_interp_supported(const Geometry &g, const float2 *beam, const float2 *ls) {
+    return g.n_layers > 8 && g.n_layers <= 32 && (g.n_beams == 32 || g.n_beams == 64) && g.chol_every == 0 &&
+           reinterpret_cast<uintptr_t>(beam) % 16 == 0 && reinterpret_cast<uintptr_t>(ls) % 16 == 0;
 }
 
 int mmse_warp_choices_for(int n_layers, int n_beams, int *out) {

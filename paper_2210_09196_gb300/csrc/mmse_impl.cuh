@@ -6,7 +6,8 @@
 //   0. The data-symbol vectors y_d of the warp's subcarriers are copied to shared memory with cp.async
 //      first, so that their latency overlaps step 1.
 //   1. The estimate rows of the warp's subcarriers are copied to shared memory with 16-byte cp.async pieces
-//      (rows padded to an even stride).
+//      (rows padded to an even stride), or, in the chain of pusch_slot (16 and 32 lanes, 32 or 64 beams),
+//      interpolated there from the LS table at the pilots, so that the estimate never goes through HBM.
 //   2. Lane i forms row i of G from 16-byte shared loads, then r_d = H^H y_d for every data symbol d.
 //   3. The r_d go to shared memory (over the group's data-symbol rows); Crout Cholesky of G column by column:
 //      lane i keeps row i of L in registers, the pivot by one shuffle, and publishes every entry over the (now
@@ -37,11 +38,16 @@ struct MmseArgs {
     int d_first, n_det;        // this launch detects data symbols d_first .. d_first + n_det - 1 (n_data in all)
     int dmrs_lo, dmrs_hi;      // the two DMRS symbols, dmrs_lo < dmrs_hi
     int warps;                 // warps per CTA of the 12-symbol kernels (mmse_warp_choices; 0 = default)
+    // LS table at the pilots (ls[slot][l][k][b], pilot q = port[l] + k comb, k < kmax) or nullptr: when set,
+    // the beam-count instances interpolate their estimate rows from it while staging (the same arithmetic as
+    // the interpolation kernel) and the H argument is not read
+    const float2 *ls;
+    int kmax, comb;
+    int port[32];
 };
 
 // Symbol index of data symbol d: the data symbols are all other symbols of the slot in increasing order.
-// (Computed rather than read from a parameter table: a run-time index into a kernel parameter array would
-// copy the whole parameter block to local memory.)
+// (Computed rather than read from a table: one compare per DMRS symbol.)
 __device__ __forceinline__ int data_symbol(const MmseArgs &g, int d) {
     int s = d;
     if (s >= g.dmrs_lo) ++s;
@@ -85,6 +91,74 @@ __device__ __forceinline__ void stage_H(float2 *Ht, const float2 *__restrict__ H
     cp_async_wait_all();  // the H tile (and the earlier y group)
 }
 
+// The interpolated estimate rows of the warp's SPW subcarriers -> the warp's H tile, from the LS table at the
+// pilots (Section II: linear interpolation between the neighbouring pilot subcarriers of each layer, held
+// outside the first and last; the arithmetic of the interpolation kernel, so the tile is bit-identical to
+// staging its output). Lane r finds the bracket of row r (subcarrier sc0 + r / NL, layer r % NL; SPW NL = 32
+// rows); the warp then reads the two table rows of every tile row in 16-byte pieces (NB / 2 per row), issuing
+// kB pieces' loads before using any. Rows of absent layers and subcarriers are zeroed.
+template <int NL, int NB>
+__device__ __forceinline__ void stage_H_interp(float2 *Ht, const MmseArgs &g, long long sc0, long long total_sc,
+                                               int ht, int lane) {
+    constexpr int kU = NB / 2;            // 16-byte pieces per row
+    constexpr int kRows = 32 / kU;        // rows per warp pass (2 for 32 beams, 1 for 64)
+    constexpr int kHs = (NB + 3) & ~1;    // row_stride(NB)
+    constexpr int kB = 4;                 // passes whose loads are issued together
+    long long base = -1;                  // table row of (slot, layer, k = 0), in 16-byte pieces
+    int klo = 0, khi = 0;
+    float w = 0.f;
+    {
+        const int gg = lane / NL, l = lane - gg * NL;
+        const long long sc = sc0 + gg;
+        if (l < g.n_layers && sc < total_sc) {
+            const long long sl = sc / g.n_sc;
+            const int a = (int)(sc - sl * g.n_sc), p = g.port[l];
+            int lo, hi;
+            pilot_bracket(a, p, g.comb, g.n_sc, lo, hi);
+            klo = (lo - p) / g.comb;
+            khi = (hi - p) / g.comb;
+            w = interp_weight(a, lo, hi);
+            base = (sl * g.n_layers + l) * (long long)g.kmax * kU;
+        }
+    }
+    const float4 *tab = reinterpret_cast<const float4 *>(g.ls);
+    const int sub = lane / kU, u = lane - sub * kU;
+    // rows of pass t: when a pass covers SPW rows, the same layer of the warp's SPW subcarriers (neighbouring
+    // subcarriers mostly share the bracket, so the pass reads each table line once); else kRows consecutive rows
+    constexpr int SPW = 32 / NL;
+    auto row_of = [&](int t) { return kRows == SPW ? sub * NL + t : t * kRows + sub; };
+#pragma unroll 1
+    for (int t0 = 0; t0 < 32 / kRows; t0 += kB) {
+        float4 lo4[kB], hi4[kB];
+        float wr[kB];
+        bool on[kB];
+#pragma unroll
+        for (int q = 0; q < kB; ++q) {
+            const int r = row_of(t0 + q);
+            const long long b = __shfl_sync(kFull, base, r);
+            const int kl = __shfl_sync(kFull, klo, r), kh = __shfl_sync(kFull, khi, r);
+            wr[q] = __shfl_sync(kFull, w, r);
+            on[q] = b >= 0;
+            lo4[q] = hi4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (on[q]) {
+                lo4[q] = __ldg(tab + b + (long long)kl * kU + u);
+                hi4[q] = __ldg(tab + b + (long long)kh * kU + u);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kB; ++q) {
+            const int r = row_of(t0 + q);
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (on[q]) {
+                const float2 h0 = interp(make_float2(lo4[q].x, lo4[q].y), make_float2(hi4[q].x, hi4[q].y), wr[q]);
+                const float2 h1 = interp(make_float2(lo4[q].z, lo4[q].w), make_float2(hi4[q].z, hi4[q].w), wr[q]);
+                v = make_float4(h0.x, h0.y, h1.x, h1.y);
+            }
+            *reinterpret_cast<float4 *>(Ht + (r / NL) * ht + (r % NL) * kHs + 2 * u) = v;
+        }
+    }
+}
+
 // Warps per CTA of the 12-data-symbol kernels when not tuned: one (each warp then starts and ends on its own;
 // larger CTAs measured slower for 16 layers, their warps waiting for one another at the output rows), four for
 // 32 layers (one subcarrier per warp).
@@ -108,7 +182,7 @@ constexpr int mmse_min_ctas() {
 // then a constant) and staged by bulk copies on one mbarrier per warp; 0: g.n_beams at run time, cp.async.
 template <int NL, int ND, int WARPS, int NB>
 __global__ void __launch_bounds__(WARPS * 32, mmse_min_ctas<NL, WARPS>())
-mmse_kernel(MmseArgs g, long long total_sc, const float2 *__restrict__ H, const float2 *__restrict__ beam,
+mmse_kernel(const __grid_constant__ MmseArgs g, long long total_sc, const float2 *__restrict__ H, const float2 *__restrict__ beam,
             float2 *__restrict__ xhat, uint8_t *__restrict__ bits, uint32_t *__restrict__ status) {
     constexpr int SPW = 32 / NL;
     constexpr int SPC = WARPS * SPW;
@@ -144,8 +218,9 @@ mmse_kernel(MmseArgs g, long long total_sc, const float2 *__restrict__ H, const 
             //           instances only with 16-byte aligned H and beam.
             const uint32_t bar = smem_addr(reinterpret_cast<uint64_t *>(smem_raw + (size_t)WARPS * wsb) + warp);
             constexpr uint32_t kRowB = NB * 8;
+            const bool interp_h = g.ls != nullptr;   // estimate rows interpolated from the LS table
             uint32_t my_bytes = 0;
-            for (int r = lane; r < SPW * NL; r += 32)
+            for (int r = lane; r < SPW * NL && !interp_h; r += 32)
                 if (r % NL < nl && sc0 + r / NL < total_sc) my_bytes += kRowB;
             for (int r = lane; r < SPW * nd; r += 32)
                 if (sc0 + r / nd < total_sc) my_bytes += kRowB;
@@ -156,7 +231,7 @@ mmse_kernel(MmseArgs g, long long total_sc, const float2 *__restrict__ H, const 
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(total) : "memory");
             }
             __syncwarp();
-            for (int r = lane; r < SPW * NL; r += 32) {
+            for (int r = lane; r < SPW * NL && !interp_h; r += 32) {
                 const int gg = r / NL, l = r - gg * NL;
                 float2 *dst = Ht + gg * ht + l * hs;
                 if (l < nl && sc0 + gg < total_sc) {
@@ -188,6 +263,7 @@ mmse_kernel(MmseArgs g, long long total_sc, const float2 *__restrict__ H, const 
                     for (int b = 0; b < NB; b += 2) *reinterpret_cast<float4 *>(dst + b) = make_float4(0.f, 0.f, 0.f, 0.f);
                 }
             }
+            if (interp_h) stage_H_interp<NL, NB>(Ht, g, sc0, total_sc, ht, lane);   // overlaps the y copies
             // bounded wait (2 s); on expiry the timeout bit is set and the copies are waited for once more
             if (!bw::mbar_wait_for(bar, 0, bw::kWaitNs)) {
                 if (lane == 0) atomicOr(&status[0], (unsigned)PUSCH_STATUS_TIMEOUT);
@@ -314,10 +390,12 @@ cudaError_t launch_nd(const MmseArgs &a, long long total_sc, const float2 *H, co
                       uint8_t *bits, uint32_t *status, cudaStream_t st) {
     if constexpr (NL >= 16) {
         // the beam-count instances stage by bulk copies: 16-byte aligned rows
-        const bool aligned = reinterpret_cast<uintptr_t>(H) % 16 == 0 && reinterpret_cast<uintptr_t>(beam) % 16 == 0;
+        const bool aligned = reinterpret_cast<uintptr_t>(H) % 16 == 0 && reinterpret_cast<uintptr_t>(beam) % 16 == 0 &&
+                             reinterpret_cast<uintptr_t>(a.ls) % 16 == 0;
         if (aligned && a.n_beams == 32) return launch_w<NL, 32>(a, total_sc, H, beam, xhat, bits, status, st);
         if (aligned && a.n_beams == 64) return launch_w<NL, 64>(a, total_sc, H, beam, xhat, bits, status, st);
     }
+    if (a.ls) return cudaErrorNotSupported;   // only the beam-count instances interpolate while staging
     return launch_w<NL, 0>(a, total_sc, H, beam, xhat, bits, status, st);
 }
 

@@ -113,13 +113,18 @@ extern "C" pusch_status pusch_slot_noalloc(const pusch_cell_cfg *cfg, int n_slot
         return na_fail(PUSCH_ERR_CUDA, "pusch_slot_noalloc fft launch", e);
     e = pusch::launch_beamform(g, n_slots, freq, static_cast<const float2 *>(W), beam, tc_err, s);
     if (e != cudaSuccess) return na_fail(PUSCH_ERR_CUDA, "pusch_slot_noalloc beamforming launch", e);
-    if ((e = pusch::launch_chest_ls(g, n_slots, beam, static_cast<const float2 *>(pilots), H, lsw, s)) != cudaSuccess)
-        return na_fail(PUSCH_ERR_CUDA, "pusch_slot_noalloc channel estimation launch", e);
+    // as in pusch_slot: the detector interpolates the estimate from the LS table itself where it can
+    const bool fused = pusch::mmse_interp_supported(g, beam, lsw);
+    if (fused)
+        e = pusch::launch_ls_pilots(g, n_slots, beam, static_cast<const float2 *>(pilots), lsw, s);
+    else
+        e = pusch::launch_chest_ls(g, n_slots, beam, static_cast<const float2 *>(pilots), H, lsw, s);
+    if (e != cudaSuccess) return na_fail(PUSCH_ERR_CUDA, "pusch_slot_noalloc channel estimation launch", e);
     if (est && (e = pusch::launch_noise_est(g, n_slots, beam, static_cast<const float2 *>(pilots), ne_partial, sigma2,
                                             s)) != cudaSuccess)
         return na_fail(PUSCH_ERR_CUDA, "pusch_slot_noalloc noise estimation launch", e);
     if ((e = pusch::launch_mmse(g, n_slots, H, beam, static_cast<float2 *>(x_hat), bits, stat, s,
-                                est ? sigma2 : nullptr)) != cudaSuccess)
+                                est ? sigma2 : nullptr, false, fused ? lsw : nullptr)) != cudaSuccess)
         return na_fail(PUSCH_ERR_CUDA, "pusch_slot_noalloc detection launch", e);
     if ((e = pusch::launch_status_fold(stat, tc_err, s)) != cudaSuccess)
         return na_fail(PUSCH_ERR_CUDA, "pusch_slot_noalloc status fold", e);

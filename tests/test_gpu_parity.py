@@ -159,6 +159,32 @@ def test_fused_chain_equals_staged_estimation_and_detection(orc, small_slots):
         rx.close()
 
 
+@pytest.mark.parametrize("nl,nb,n_sc", [(16, 32, 300), (12, 32, 123), (32, 64, 77), (16, 64, 64), (20, 32, 45)],
+                         ids=lambda v: str(v))
+def test_detector_interpolating_from_the_pilot_table_is_bit_identical(orc, nl, nb, n_sc):
+    """With 16 or 32 lanes per subcarrier and 32 or 64 beams, pusch_slot's detector interpolates the estimate
+    from the LS table at the pilots while it stages (Section II: linear interpolation between a layer's pilot
+    subcarriers), so the interpolated estimate never goes through memory. Its x-hat, bits and status must be
+    bit-identical to pusch_chest_ls (which writes the interpolated estimate) followed by pusch_mmse_detect, over
+    ragged last CTAs, slot boundaries, padded layers (12 and 20 layers) and the held edges before the first and
+    after the last pilot."""
+    cell = synth.DEPLOY.with_(n_rx=nb, n_beams=nb, n_layers=nl, n_fft=512, n_sc=n_sc)
+    slots = synth.make_slots(cell, 3)
+    rx = host.Receiver(host.cfg_for(cell), max_slots=len(slots))
+    freq, beam, H, x, b, st = run_stages(rx, slots, slots[0].W)
+    x2, b2, st2 = rx.slot(host.time_tensor(slots), host.beam_tensor(slots[0].W), host.pilot_tensor(slots))
+    torch.cuda.synchronize()
+    assert torch.equal(x2, x) and torch.equal(b2, b) and torch.equal(st2, st)
+    assert int(st2.cpu().numpy()[0]) == 0
+    for i, s in enumerate(slots):   # and the chain against the oracle's estimate + Eq. 2 on sampled subcarriers
+        Ho = orc.chest_ls(c128(beam[i]), s.pilots, s.ports, cell.comb)
+        sc = np.array([0, 1, n_sc // 2, n_sc - 2, n_sc - 1])
+        xo, fails = orc.mmse(Ho, c128(beam[i]), s.noise_var, sc_list=sc)
+        assert fails == 0
+        assert nrel(c128(x2[i])[:, :, sc], xo[:, :, sc]) < TOL
+    rx.close()
+
+
 def test_profile_hooks_time_pusch_slot(orc, small_slots):
     cell = synth.SMALL_FP32
     rx = host.Receiver(host.cfg_for(cell), max_slots=3)
