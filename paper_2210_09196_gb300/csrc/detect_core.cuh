@@ -87,13 +87,16 @@ __device__ __forceinline__ float4 lds4_ordered(const float4 *p) {
 //     copy of symbol 0 and discards it); the results are written back only after every lane has read;
 //   * x_d[i] returns to lane i through T.
 // Uses the H tile (lt) for L: 120 float4 + NL floats.
-template <int NL, int ND, int NR>
+// kRhsInT: the r_d are already in T (written there by the tensor-core Gram), acc is only the output.
+template <int NL, int ND, int NR, bool kRhsInT = false>
 __device__ __forceinline__ bool factor_solve_rhs_lanes(float2 (&G)[NL], float2 *yt, float2 *lt, int ys, int nd,
                                                        int i, int src0, float2 (&acc)[NR]) {
     constexpr unsigned kFull = kDetFull;
+    if constexpr (!kRhsInT) {
 #pragma unroll
-    for (int d = 0; d < NR; ++d)
-        if (ND > 0 || d < nd) yt[d * ys + i] = acc[d];
+        for (int d = 0; d < NR; ++d)
+            if (ND > 0 || d < nd) yt[d * ys + i] = acc[d];
+    }
     float4 *L4 = reinterpret_cast<float4 *>(lt);                 // L[k][j], j < k, at k (k - 1) / 2 + j
     float *dv = reinterpret_cast<float *>(L4 + NL * (NL - 1) / 2);  // 1 / L[k][k]
     bool bad = false;

@@ -24,6 +24,7 @@
 #include "chest_common.cuh"
 #include "bounded_wait.cuh"
 #include "detect_core.cuh"
+#include "detect_tc.cuh"
 
 namespace pusch {
 namespace mmse_detail {
@@ -308,9 +309,13 @@ mmse_kernel(const __grid_constant__ MmseArgs g, long long total_sc, const float2
         __syncwarp();
         }
         // ---- 2-4. Gram, matched filter, Cholesky and solves, the x_d left in the data-symbol rows (detect_group).
-        const bool bad = detect_group<NL, ND, NR>(hr, hg, Yt + grp * nd * ys, Ht + grp * ht, hs, nb, nd, nl,
-                                                  g.sigma2 ? g.loading : g.load, i, src0, acc, g.sigma2,
-                                                  valid ? slot : 0, ys);
+        bool bad;
+        if constexpr (NB > 0 && ND == 12 && NL >= 16)   // G and r_d on the tensor cores
+            bad = detect_group_tc<NL, NB>(Ht, ht, hs, Yt, ys, nl, g.sigma2 ? g.loading : g.load, grp, i, src0, lane,
+                                          acc, g.sigma2, valid ? slot : 0);
+        else
+            bad = detect_group<NL, ND, NR>(hr, hg, Yt + grp * nd * ys, Ht + grp * ht, hs, nb, nd, nl,
+                                           g.sigma2 ? g.loading : g.load, i, src0, acc, g.sigma2, valid ? slot : 0, ys);
         if (valid && bad && i == 0) {
             atomicAdd(&status[1], 1u);
             atomicMin(&status[2], (unsigned)my_sc);
