@@ -205,7 +205,7 @@ KERNELS = {"fft": {"tc": ("fft_tc_kernel", "fft_tc.cu+" + TC), "simt": ("fft_ker
                         "fp32": ("beamform_tf32_kernel", "beamform_tf32.cu+" + TC),
                         "fp32_simt": ("beamform_fp32_kernel", "beamform.cu")},
            "ls": ("ls_pilots_kernel", "chest.cu+chest_common.cuh"),
-           "detect": ("mmse_kernel", "mmse_impl.cuh+detect_core.cuh")}
+           "detect": ("mmse_kernel", "mmse_impl.cuh+detect_core.cuh+detect_tc.cuh+chest_common.cuh")}
 
 
 def kernel_of(stage, form, cell=None):
