@@ -399,9 +399,10 @@ cudaEvent_t *take_records(pusch_handle *h, int runs) {
 
 // The chain over slots [s0, s0 + n) of a call, on stream s, in the handle's workspace slice of those slots
 // (freq_off: byte offset of the chunk's FFT output buffer). ev: kSlotStages + 1 events or nullptr.
+// fft_ctas > 0: the FFT's CTAs per SM for this run (the pipelined runs' default, see slot_batch).
 pusch_status run_chain(pusch_handle *h, int s0, int n, size_t freq_off, const void *time_in, const void *W,
                        const void *pilots, void *x_hat, uint8_t *bits, uint32_t *stat, cudaStream_t s,
-                       cudaEvent_t *ev) {
+                       cudaEvent_t *ev, int fft_ctas = 0) {
     const pusch::Geometry &g = h->geo;
     const char *tin = (const char *)time_in + time_bytes(g, s0);
     const float2 *pil = (const float2 *)((const char *)pilots + pilot_bytes(g, s0));
@@ -415,8 +416,14 @@ pusch_status run_chain(pusch_handle *h, int s0, int n, size_t freq_off, const vo
     float *sigma2 = h->sigma2 + s0;
     cudaError_t e;
     if (ev) cudaEventRecord(ev[0], s);
-    if ((e = pusch::launch_fft(g, n, tin, freq, h->twiddle, h->kernel_err, s)) != cudaSuccess)
-        return cuda_fail(e, "fft launch");
+    if (fft_ctas > 0) {
+        pusch::Geometry gf = g;
+        gf.fft_cap = fft_ctas;
+        e = pusch::launch_fft(gf, n, tin, freq, h->twiddle, h->kernel_err, s);
+    } else {
+        e = pusch::launch_fft(g, n, tin, freq, h->twiddle, h->kernel_err, s);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "fft launch");
     if (ev) cudaEventRecord(ev[1], s);
     if ((e = pusch::launch_beamform(g, n, freq, (const float2 *)W, beam, h->kernel_err, s, &h->bf_tune)) != cudaSuccess)
         return cuda_fail(e, "beamforming launch");
@@ -491,6 +498,10 @@ pusch_status slot_batch(pusch_handle *h, int n_slots, const void *time_in, const
     pusch_status st;
     if ((st = reset_status(stat, s)) != PUSCH_OK) return st;
     const int k = h->pipeline < n_slots ? h->pipeline : n_slots;
+    // Chunk runs on two streams: unless pusch_autotune chose a cap, the tensor-core FFT takes two CTAs per SM
+    // (of four) so that the other stream's detector CTAs fit beside it (deployment cell, two runs: 35,190
+    // slots/s against 34,657 with four, whose shared memory leaves no room).
+    const int fft_ctas = (k > 1 && h->geo.fft_cap == 0 && pusch::fft_tc_supported(h->geo)) ? 2 : 0;
     cudaEvent_t *ev = h->prof_events.empty() ? nullptr : take_records(h, k);
     if (k > 1 && (st = pipe_fork(h, s)) != PUSCH_OK) return st;
     size_t freq_off = 0;
@@ -501,7 +512,7 @@ pusch_status slot_batch(pusch_handle *h, int n_slots, const void *time_in, const
         if (time_host) st = chunk_copies(h, true, s0, nc, time_host, pil_host, nullptr, nullptr, cs);
         if (st == PUSCH_OK)
             st = run_chain(h, s0, nc, freq_off, time_in, W, pilots, x_hat, bits, stat, cs,
-                           ev ? ev + (size_t)c * (kSlotStages + 1) : nullptr);
+                           ev ? ev + (size_t)c * (kSlotStages + 1) : nullptr, fft_ctas);
         if (st == PUSCH_OK && time_host)
             st = chunk_copies(h, false, s0, nc, nullptr, nullptr, xhat_host, bits_host, cs);
         freq_off += align256(freq_bytes(h->geo, nc));
