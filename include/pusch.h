@@ -258,9 +258,9 @@ pusch_status pusch_dmrs_type1_pilots(const pusch_cell_cfg *cfg, int n_slots, con
  * differing by at most one), issued alternately on two streams owned by the handle; they start after the
  * work already queued on the caller's stream and the caller's stream waits for them (events), so the call is
  * still ordered on `stream`. Runs on the two streams overlap on the GPU (one run's FFT beside the other's
- * detector; in pusch_slot_host one run's copies beside another's kernels). With two or more runs the
- * mixed form's 4096-point tensor-core FFT takes two CTAs per SM instead of four unless pusch_autotune chose
- * a number, so that the other stream's detector finds room beside it. Results are bit-identical for
+ * detector; in pusch_slot_host one run's copies beside another's kernels). With two or more runs of
+ * pusch_slot the mixed form's 4096-point tensor-core FFT takes two CTAs per SM instead of four unless
+ * pusch_autotune chose a number, so that the other stream's detector finds room beside it. Results are bit-identical for
  * every n_chunks: each slot's arithmetic does not depend on the batch it is in. Each run uses the workspace
  * slice of its own slots. Returns PUSCH_ERR_ARG for n_chunks out of range, PUSCH_ERR_CUDA if the streams
  * cannot be created (the setting is then unchanged).

@@ -498,10 +498,12 @@ pusch_status slot_batch(pusch_handle *h, int n_slots, const void *time_in, const
     pusch_status st;
     if ((st = reset_status(stat, s)) != PUSCH_OK) return st;
     const int k = h->pipeline < n_slots ? h->pipeline : n_slots;
-    // Chunk runs on two streams: unless pusch_autotune chose a cap, the tensor-core FFT takes two CTAs per SM
-    // (of four) so that the other stream's detector CTAs fit beside it (deployment cell, two runs: 35,190
-    // slots/s against 34,657 with four, whose shared memory leaves no room).
-    const int fft_ctas = (k > 1 && h->geo.fft_cap == 0 && pusch::fft_tc_supported(h->geo)) ? 2 : 0;
+    // Chunk runs on two streams with device-resident inputs: unless pusch_autotune chose a cap, the tensor-core
+    // FFT takes two CTAs per SM (of four) so that the other stream's detector CTAs fit beside it (deployment
+    // cell, two runs: 35,190 slots/s against 34,657 with four, whose shared memory leaves no room). With host
+    // buffers the other stream carries copies, and the capped FFT only lengthens each run (8,241 against 9,915
+    // slots/s end to end), so it keeps four.
+    const int fft_ctas = (k > 1 && !time_host && h->geo.fft_cap == 0 && pusch::fft_tc_supported(h->geo)) ? 2 : 0;
     cudaEvent_t *ev = h->prof_events.empty() ? nullptr : take_records(h, k);
     if (k > 1 && (st = pipe_fork(h, s)) != PUSCH_OK) return st;
     size_t freq_off = 0;
