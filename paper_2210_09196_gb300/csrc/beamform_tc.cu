@@ -263,6 +263,7 @@ beamform_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_consta
         if (lane == 0) {
             long long gch = 0;
             bool ok = true;
+            const uint64_t pol = l2_policy_evict_first();   // every FFT output tile is read once
             for (long long i = 0; i < n_my && ok; ++i) {
                 const long long t = blockIdx.x + i * gridDim.x;
                 const long long row = t / g.n_mtiles;
@@ -280,12 +281,12 @@ beamform_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_consta
                     const int y = (int)(row * K) + c * g.chunk_rows;
                     if constexpr (FP8) {
                         mbar_expect_tx(bar, g.land_bytes);
-                        tma_load_2d(base + g.land_off + (uint32_t)s * g.land_bytes, &tmap, mt * kTileM, y, bar);
+                        tma_load_2d_hint(base + g.land_off + (uint32_t)s * g.land_bytes, &tmap, mt * kTileM, y, bar, pol);
                     } else {
                         const uint32_t dst = sA + (uint32_t)s * g.stage_bytes;
                         mbar_expect_tx(bar, g.stage_bytes);
-                        tma_load_2d(dst, &tmap, mt * kTileM, y, bar);
-                        tma_load_2d(dst + (uint32_t)g.chunk_rows * 128, &tmap, mt * kTileM + 64, y, bar);
+                        tma_load_2d_hint(dst, &tmap, mt * kTileM, y, bar, pol);
+                        tma_load_2d_hint(dst + (uint32_t)g.chunk_rows * 128, &tmap, mt * kTileM + 64, y, bar, pol);
                     }
                 }
             }

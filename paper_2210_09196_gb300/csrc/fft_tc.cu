@@ -146,14 +146,17 @@ fft_tc_kernel(const __grid_constant__ CUtensorMap tin, __half *__restrict__ out,
         // ------------------------------------------------------------ control: row copies and MMAs
         if (lane == 0) {
             const uint32_t idesc = idesc_f16(128, 128, true, false);   // A MN-major in both stages
+            // the time samples are read once: evict-first, so that they do not push the FFT output (the next
+            // kernel's input) out of L2 (an evict-last hint on the 2-byte output stores measured slower)
+            const uint64_t pol_in = l2_policy_evict_first();
             auto issue = [&](long long i) {
                 const int s = (int)(i % kStages);
                 const long long row = blockIdx.x + i * gridDim.x;
                 const uint32_t bar = smem_u32(&bar_full[s]);
                 mbar_expect_tx(bar, kRowBytes);
                 for (int h = 0; h < 2; ++h)
-                    tma_load_2d(base + kOffIn + (uint32_t)s * kRowBytes + (uint32_t)h * 8192u, &tin, 64 * h,
-                                (int)(row * 64), bar);
+                    tma_load_2d_hint(base + kOffIn + (uint32_t)s * kRowBytes + (uint32_t)h * 8192u, &tin, 64 * h,
+                                     (int)(row * 64), bar, pol_in);
             };
             long long issued = 0;
             for (; issued < kStages && issued < n_my; ++issued) issue(issued);
