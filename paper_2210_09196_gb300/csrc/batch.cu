@@ -26,6 +26,7 @@
 
 #include "chest_common.cuh"
 #include "detect_core.cuh"
+#include "detect_tc.cuh"
 #include "tune_cache.cuh"
 
 namespace {
@@ -227,9 +228,15 @@ batch_detect_kernel(DetArgs g, int nbmax, const Segment *__restrict__ segs, cons
 
         // 2-4. Gram, right-hand sides, Cholesky, solves
         float2 acc[NR];
-        const bool bad = pusch::detect_group<NL, ND, NR>(Ht + grp * ht + i * hs, Ht + grp * ht,
-                                                                     Yt + grp * nd * ys, Ht + grp * ht, hs, nb, nd, nl,
-                                                                     sg.load, i, src0, acc, nullptr, 0, ys);
+        bool bad;
+        bool tc = false;   // 16 and 32 lanes, 12 data symbols, a beam count that is a multiple of 4: G and r_d
+        if constexpr (ND == 12 && NL >= 16) {   // on the tensor cores
+            tc = (nb & 3) == 0 && ht >= NL * (NL + 2);
+            if (tc) bad = pusch::detect_group_tc<NL, 0>(Ht, ht, hs, Yt, ys, nl, sg.load, grp, i, src0, lane, acc, nullptr, 0, nb);
+        }
+        if (!tc)
+            bad = pusch::detect_group<NL, ND, NR>(Ht + grp * ht + i * hs, Ht + grp * ht, Yt + grp * nd * ys,
+                                                  Ht + grp * ht, hs, nb, nd, nl, sg.load, i, src0, acc, nullptr, 0, ys);
         if (valid && bad && i == 0) {
             atomicAdd(&status[1], 1u);
             atomicMin(&status[2], (unsigned)(sg.cell * 65536 + a));

@@ -46,8 +46,10 @@ __device__ __forceinline__ void mma3_tf32(float (&c)[4], const uint32_t (&ah)[4]
 //   Gs: G[i][j] (float2) at Gs + i (NL + 2) + j, over the estimate rows (written after every lane has read them)
 // Fragment layout of m16n8k8 (g = lane / 4, t = lane % 4): A rows g, g + 8 at columns t, t + 4; B column g at
 // rows t, t + 4; the accumulator rows g, g + 8 at columns 2 t, 2 t + 1.
+// NB = 0: the beam count nb at run time (a multiple of 4: K = 2 nb floats in steps of 8).
 template <int NL, int NB>
-__device__ __forceinline__ void gram_rhs_tc(const float *hf, int hsf, float *yf, int ysf, int ys, float2 *Gs, int lane) {
+__device__ __forceinline__ void gram_rhs_tc(const float *hf, int hsf, float *yf, int ysf, int ys, float2 *Gs, int lane,
+                                            int nb = NB) {
     constexpr int MT = NL / 16;     // 16-row tiles of layers
     constexpr int NG = NL / 8;      // 8-column tiles of G's columns (each for Re and for Im)
     constexpr int GS = NL + 2;      // row stride of Gs (float2): the 16-byte row loads below spread over banks
@@ -71,7 +73,7 @@ __device__ __forceinline__ void gram_rhs_tc(const float *hf, int hsf, float *yf,
     }
     constexpr int kUnroll = NL == 16 ? 2 : 1;   // two K steps in flight for 16 layers (measured faster; not for 32)
 #pragma unroll kUnroll
-    for (int k0 = 0; k0 < 2 * NB; k0 += 8) {
+    for (int k0 = 0; k0 < 2 * (NB > 0 ? NB : nb); k0 += 8) {
         uint32_t ah[MT][4], al[MT][4];
 #pragma unroll
         for (int m = 0; m < MT; ++m) {
@@ -148,15 +150,18 @@ __device__ __forceinline__ void gram_rhs_tc(const float *hf, int hsf, float *yf,
 // the diagonal (identity rows past nl), and the Crout factorisation and the solves run as in detect_group.
 //   Hw, Yw: the warp's estimate tiles (stride ht float2 per subcarrier, rows hs) and data-symbol rows (12 per
 //   subcarrier, stride ys). Returns true when a pivot of lane i's subcarrier was not a positive finite number.
+//   NB = 0: nb beams at run time (a multiple of 4; the ragged batch's segments). G overlays the estimate tile:
+//   ht >= NL (NL + 2) float2.
 template <int NL, int NB>
 __device__ __forceinline__ bool detect_group_tc(float2 *Hw, int ht, int hs, float2 *Yw, int ys, int nl, float load,
                                                 int grp, int i, int src0, int lane, float2 (&acc)[12],
-                                                const float *__restrict__ sigma2 = nullptr, long long slot = 0) {
+                                                const float *__restrict__ sigma2 = nullptr, long long slot = 0,
+                                                int nb = NB) {
     constexpr int SPW = 32 / NL, GS = NL + 2;
 #pragma unroll 1
     for (int gg = 0; gg < SPW; ++gg)
         gram_rhs_tc<NL, NB>(reinterpret_cast<const float *>(Hw + gg * ht), 2 * hs,
-                            reinterpret_cast<float *>(Yw + gg * 12 * ys), 2 * ys, ys, Hw + gg * ht, lane);
+                            reinterpret_cast<float *>(Yw + gg * 12 * ys), 2 * ys, ys, Hw + gg * ht, lane, nb);
     __syncwarp();
     float2 G[NL];
     {
