@@ -60,7 +60,10 @@ typedef enum {
                               power-of-two scale per (beam, 128 antennas); beamforming is the
                               block-scaled product of the two quantised operands, on the tcgen05 tensor
                               cores with FP32 accumulation (the codes enter the MMA as their exact FP16
-                              values). Channel estimation and detection stay FP32 in every form.         */
+                              values). Channel estimation and detection keep FP32 accuracy in every
+                              form: FP32 arithmetic, except that the 16- and 32-layer detectors form the
+                              Gram matrix and the right-hand sides on the tensor cores from TF32 operands
+                              split in two parts (three products each, FP32 accumulation).              */
 } pusch_form;
 
 /* Device status words written by the detection kernels (uint32_t status[4]):
